@@ -1,0 +1,391 @@
+"""Pins of the FP64 oracle against facts outside itself (CPU only).
+
+Each test ties an oracle function to something it does not compute itself:
+sizes printed in the paper, finite differences of the cost, the closed form of
+a single softmax layer, and invariants fixed by the mathematics.  The mutation
+tests at the end plant plausible mistakes in the oracle and check that a pin
+catches each of them.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+from oracle import mlp as O
+from synth import make_problem
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _tiny(widths, acts, N=7, seed=11, bias="uniform"):
+    return make_problem(widths, acts, N, seed, "normal", bias)
+
+
+def _relerr(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _fd_grad_per_example(pb, h=1e-4):
+    """Richardson-extrapolated central differences of every C_n."""
+    P = pb.P
+    out = np.empty((pb.N, P))
+
+    def d(hh, j):
+        w1 = pb.omega.copy()
+        w2 = pb.omega.copy()
+        w1[j] += hh
+        w2[j] -= hh
+        c1 = O.per_example_costs(w1, pb.widths, pb.acts, pb.X, pb.Y)
+        c2 = O.per_example_costs(w2, pb.widths, pb.acts, pb.X, pb.Y)
+        return (c1 - c2) / (2 * hh)
+
+    for j in range(P):
+        out[:, j] = (4 * d(h / 2, j) - d(h, j)) / 3
+    return out
+
+
+def _fd_hessian_of_gradient(pb, h=1e-5):
+    P = pb.P
+    H = np.empty((P, P))
+    for j in range(P):
+        w1 = pb.omega.copy()
+        w2 = pb.omega.copy()
+        w1[j] += h
+        w2[j] -= h
+        g1 = O.gradient(w1, pb.widths, pb.acts, pb.X, pb.Y)
+        g2 = O.gradient(w2, pb.widths, pb.acts, pb.X, pb.Y)
+        H[:, j] = (g1 - g2) / (2 * h)
+    return H
+
+
+def _min_abs_preact(pb):
+    f = O.forward(pb.omega, pb.widths, pb.acts, pb.X)
+    return min(np.abs(z).min() for z in f["z"][1:-1]) if len(pb.widths) > 2 else np.inf
+
+
+# ---------------------------------------------------------------- sizes ----
+
+def _golden_sizes():
+    rows = []
+    with open(os.path.join(GOLDEN, "paper_sizes.txt")) as fh:
+        for line in fh:
+            line = line.split("--")[0].strip()
+            if not line or line.startswith("#"):
+                continue
+            key, widths, val = line.split()
+            rows.append((key, [int(t) for t in widths.split(",")], int(val)))
+    return rows
+
+
+def test_parameter_count_matches_paper():
+    rows = [r for r in _golden_sizes() if r[0] == "P"]
+    assert len(rows) >= 4
+    for _, widths, P in rows:
+        assert O.num_params(widths) == P
+        omega = np.arange(P, dtype=np.float64)
+        assert np.array_equal(O.flatten(O.unflatten(omega, widths)), omega)
+
+
+def test_hessian_block_shapes_match_paper():
+    """Sec. 3.3: for the 64->32 softmax layer, the W-W block is 2048 x 2048 and
+    the b-b block 32 x 32; the off-diagonal (W, b) blocks are what the per-tensor
+    routine misses, and they are not zero."""
+    sizes = {r[0]: r[2] for r in _golden_sizes() if r[1] == [64, 32]}
+    pb = make_problem([64, 32], [], 3, 5, "normal", "uniform")
+    cols = [0, 1, 2047, 2048, 2079]
+    Hc = O.hessian_columns(pb.omega, pb.widths, pb.acts, pb.X, pb.Y, cols)
+    nW, nb = sizes["HU"], sizes["HL"]
+    assert nW + nb == sizes["P"] == pb.P
+    # column 0 is a weight direction: it has nonzero entries in the bias rows
+    assert np.abs(Hc[nW:, 0]).max() > 1e-6
+    # column 2048 is a bias direction: it has nonzero entries in the weight rows
+    assert np.abs(Hc[:nW, 3]).max() > 1e-6
+
+
+# ------------------------------------------------------------ forward ----
+
+def test_cost_zero_network_is_log_classes():
+    widths = [5, 4, 6]
+    pb = make_problem(widths, ["tanh"], 9, 3, "normal")
+    omega = np.zeros(pb.P)
+    assert abs(O.cost(omega, widths, pb.acts, pb.X, pb.Y) - np.log(6.0)) < 1e-15
+
+
+def test_cost_matches_cross_entropy_of_softmax():
+    pb = _tiny([4, 6, 5], ["sigmoid"])
+    f = O.forward(pb.omega, pb.widths, pb.acts, pb.X)
+    zL = f["z"][-1]
+    yhat = np.exp(zL) / np.exp(zL).sum(axis=1, keepdims=True)
+    naive = -(pb.Y * np.log(yhat)).sum(axis=1)
+    assert _relerr(O.per_example_costs(pb.omega, pb.widths, pb.acts, pb.X, pb.Y), naive) < 1e-14
+    # a hand evaluation of the network for example 0
+    params = O.unflatten(pb.omega, pb.widths)
+    x = pb.X[0]
+    h = 1.0 / (1.0 + np.exp(-(params[0][0] @ x + params[0][1])))
+    z = params[1][0] @ h + params[1][1]
+    c0 = -np.log(np.exp(z[pb.labels[0]]) / np.exp(z).sum())
+    assert abs(naive[0] - c0) < 1e-13
+
+
+# -------------------------------------------------------- first order ----
+
+@pytest.mark.parametrize("act", ["sigmoid", "tanh", "relu"])
+def test_per_example_grads_match_finite_differences(act):
+    pb = _tiny([3, 4, 3, 3], [act, act])
+    assert _min_abs_preact(pb) > 1e-3
+    G = O.per_example_grads(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
+    Gfd = _fd_grad_per_example(pb)
+    assert _relerr(G, Gfd) < 1e-9
+
+
+def test_single_layer_gradient_closed_form():
+    """L = 2: g_n = (p_n - y_n) (x) [x_n; 1] in augmented-row order."""
+    pb = _tiny([5, 4], [])
+    G = O.per_example_grads(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
+    f = O.forward(pb.omega, pb.widths, pb.acts, pb.X)
+    perm = O.param_permutation(pb.widths)
+    xt = np.hstack([pb.X, np.ones((pb.N, 1))])
+    for n in range(pb.N):
+        ref = np.kron(f["p"][n] - pb.Y[n], xt[n])
+        assert np.allclose(G[n, perm], ref, rtol=0, atol=1e-15)
+
+
+def test_per_example_rows_versus_summed_gradient():
+    """The summed gradient is the mean of the per-example rows, and each row
+    equals the gradient of the single-example cost (Sec. 3.1)."""
+    pb = _tiny([4, 3, 3], ["tanh"], N=5)
+    G = O.per_example_grads(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
+    for n in range(pb.N):
+        gn = O.gradient(pb.omega, pb.widths, pb.acts, pb.X[n:n + 1], pb.Y[n:n + 1])
+        assert _relerr(G[n], gn) < 1e-15
+    h = 1e-5
+    fd = np.empty(pb.P)
+    for j in range(pb.P):
+        w1, w2 = pb.omega.copy(), pb.omega.copy()
+        w1[j] += h
+        w2[j] -= h
+        fd[j] = (O.cost(w1, pb.widths, pb.acts, pb.X, pb.Y)
+                 - O.cost(w2, pb.widths, pb.acts, pb.X, pb.Y)) / (2 * h)
+    assert _relerr(G.mean(axis=0), fd) < 1e-8
+
+
+# ------------------------------------------------------- second order ----
+
+@pytest.mark.parametrize("act", ["sigmoid", "tanh", "relu"])
+def test_hessian_matches_finite_differences_of_gradient(act):
+    pb = _tiny([3, 4, 3, 3], [act, act], N=6, seed=21)
+    assert _min_abs_preact(pb) > 1e-3
+    H = O.hessian(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
+    Hfd = _fd_hessian_of_gradient(pb)
+    assert _relerr(H, Hfd) < 1e-8
+
+
+def test_hessian_matches_second_differences_of_cost():
+    """Independent of the back-propagation code: second central differences of
+    the scalar cost C itself."""
+    pb = _tiny([3, 3, 2], ["sigmoid"], N=4, seed=5)
+    H = O.hessian(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
+    h = 1e-4
+    P = pb.P
+    Hfd = np.empty((P, P))
+
+    def C(w):
+        return O.cost(w, pb.widths, pb.acts, pb.X, pb.Y)
+
+    for i in range(P):
+        for j in range(P):
+            s = 0.0
+            for si, sj, sg in ((1, 1, 1), (1, -1, -1), (-1, 1, -1), (-1, -1, 1)):
+                w = pb.omega.copy()
+                w[i] += si * h
+                w[j] += sj * h
+                s += sg * C(w)
+            Hfd[i, j] = s / (4 * h * h)
+    assert _relerr(H, Hfd) < 1e-5
+
+
+def test_single_softmax_layer_closed_form():
+    """L = 2: H = (1/N) sum_n (diag p_n - p_n p_n^T) (x) xt_n xt_n^T with
+    xt = [x; 1], in augmented-row order."""
+    pb = _tiny([6, 5], [], N=9, seed=3)
+    H = O.hessian(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
+    f = O.forward(pb.omega, pb.widths, pb.acts, pb.X)
+    xt = np.hstack([pb.X, np.ones((pb.N, 1))])
+    ref = np.zeros((pb.P, pb.P))
+    for n in range(pb.N):
+        p = f["p"][n]
+        ref += np.kron(np.diag(p) - np.outer(p, p), np.outer(xt[n], xt[n]))
+    ref /= pb.N
+    perm = O.param_permutation(pb.widths)
+    assert _relerr(H[np.ix_(perm, perm)], ref) < 1e-13
+
+
+def test_hessian_symmetry_and_hvp_reciprocity():
+    pb = _tiny([4, 5, 4, 3], ["tanh", "sigmoid"], N=8, seed=9)
+    H = O.hessian(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
+    assert np.linalg.norm(H - H.T) / np.linalg.norm(H) < 1e-14
+    rng = np.random.default_rng(0)
+    u, v = rng.standard_normal(pb.P), rng.standard_normal(pb.P)
+    Hu = O.hvp(pb.omega, pb.widths, pb.acts, pb.X, pb.Y, u)
+    Hv = O.hvp(pb.omega, pb.widths, pb.acts, pb.X, pb.Y, v)
+    assert abs(u @ Hv - v @ Hu) <= 1e-13 * np.linalg.norm(Hu) * np.linalg.norm(v)
+    assert np.allclose(Hv, H @ v, rtol=0, atol=1e-13 * np.linalg.norm(Hv))
+
+
+def _shift_null_vectors(widths):
+    """Softmax is invariant to adding a constant to all logits (Sec. 2), so the
+    direction that adds 1 to every output bias and, for each input unit r of the
+    last layer, the direction adding 1 to column r of every row of W^(L-1) leave
+    every C_n unchanged."""
+    offs = O.layer_offsets(widths)
+    ow, ob = offs[-1]
+    t_in, t_out = widths[-2], widths[-1]
+    P = O.num_params(widths)
+    vecs = []
+    u = np.zeros(P)
+    u[ob:ob + t_out] = 1.0
+    vecs.append(u)
+    for r in range(t_in):
+        u = np.zeros(P)
+        for i in range(t_out):
+            u[ow + i * t_in + r] = 1.0
+        vecs.append(u)
+    return vecs
+
+
+def test_softmax_shift_null_space():
+    pb = _tiny([4, 5, 3], ["tanh"], N=6, seed=2)
+    H = O.hessian(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
+    Gm = O.opg(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
+    for u in _shift_null_vectors(pb.widths):
+        assert np.linalg.norm(H @ u) <= 1e-14 * np.linalg.norm(H) * np.linalg.norm(u)
+        assert np.linalg.norm(Gm @ u) <= 1e-14 * np.linalg.norm(Gm) * np.linalg.norm(u)
+
+
+# --------------------------------------------------------------- OPG ----
+
+def test_opg_invariants():
+    pb = _tiny([5, 6, 4], ["sigmoid"], N=9, seed=4)
+    G = O.per_example_grads(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
+    M = O.opg_from_grads(G)
+    assert np.linalg.norm(M - M.T) == 0.0 or np.linalg.norm(M - M.T) < 1e-15 * np.linalg.norm(M)
+    ev = np.linalg.eigvalsh(M)
+    assert ev.min() >= -1e-12 * ev.max()
+    assert abs(np.trace(M) - (G * G).sum(axis=1).mean()) < 1e-13 * np.trace(M)
+    rank = int((ev > 1e-10 * ev.max()).sum())
+    assert rank <= min(pb.N, pb.P - (pb.widths[-2] + 1))
+    # explicit sum of per-example outer products (Eq. hesseq2)
+    ref = sum(np.outer(G[n], G[n]) for n in range(pb.N)) / pb.N
+    assert _relerr(M, ref) < 1e-15
+    # one example: OPG = g g^T
+    g1 = O.per_example_grads(pb.omega, pb.widths, pb.acts, pb.X[:1], pb.Y[:1])[0]
+    assert _relerr(O.opg(pb.omega, pb.widths, pb.acts, pb.X[:1], pb.Y[:1]), np.outer(g1, g1)) < 1e-15
+
+
+def test_opg_is_not_gradient_outer_product():
+    """Eq. hesseq4: the OPG differs from grad C grad C^T for N > 1."""
+    pb = _tiny([3, 3, 3], ["tanh"], N=6)
+    G = O.per_example_grads(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
+    g = G.mean(axis=0)
+    assert _relerr(O.opg_from_grads(G), np.outer(g, g)) > 0.1
+
+
+# --------------------------------------------------------------- eig ----
+
+def test_gram_routes_agree():
+    pb = _tiny([6, 5, 4, 3], ["relu", "tanh"], N=10, seed=8)
+    G = O.per_example_grads(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
+    assert _relerr(O.gram_factored(pb.omega, pb.widths, pb.acts, pb.X, pb.Y),
+                   O.gram_from_grads(G)) < 1e-14
+
+
+def test_opg_topk_eig_against_full_eigendecomposition():
+    pb = _tiny([6, 5, 4], ["tanh"], N=12, seed=6)
+    G = O.per_example_grads(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
+    OPG = O.opg_from_grads(G)
+    k = 5
+    mu, Q, deficient = O.opg_topk_eig_from_grads(G, k)
+    assert not deficient
+    lam, V = np.linalg.eigh(OPG)
+    lam, V = lam[::-1], V[:, ::-1]
+    assert np.allclose(mu, lam[:k], rtol=0, atol=1e-13 * lam[0])
+    assert np.all(np.diff(mu) <= 0)
+    for c in range(k):
+        assert abs(abs(Q[:, c] @ V[:, c]) - 1.0) < 1e-10
+        assert np.linalg.norm(OPG @ Q[:, c] - mu[c] * Q[:, c]) < 1e-12 * lam[0]
+        assert Q[np.argmax(np.abs(Q[:, c])), c] > 0
+    assert np.allclose(Q.T @ Q, np.eye(k), atol=1e-12)
+    mu_all, _, _ = O.opg_topk_eig_from_grads(G, pb.N)
+    assert abs(mu_all.sum() - np.trace(OPG)) < 1e-12 * np.trace(OPG)
+
+
+def test_opg_topk_eig_rank_deficient():
+    """Three examples of which two are identical: the Gram matrix has rank 2,
+    so asking for 3 pairs flags the null space and returns a zero vector."""
+    pb = _tiny([4, 3, 3], ["sigmoid"], N=3)
+    X, Y = pb.X.copy(), pb.Y.copy()
+    X[2], Y[2] = X[0], Y[0]
+    mu, Q, deficient = O.opg_topk_eig(pb.omega, pb.widths, pb.acts, X, Y, 3)
+    assert deficient
+    assert np.all(Q[:, 2] == 0.0)
+    assert abs(mu[2]) < 1e-13 * mu[0]
+    assert np.linalg.norm(Q[:, :2].T @ Q[:, :2] - np.eye(2)) < 1e-12
+
+
+# ---------------------------------------------------------- mutations ----
+
+def test_pins_catch_dropped_second_derivative(monkeypatch):
+    """Planting sigma'' = 0 for tanh (a dropped term) breaks the FD pin."""
+    pb = _tiny([3, 4, 3], ["tanh"], N=5, seed=21)
+    real = O.activation
+
+    def broken(name, z):
+        a, d1, d2 = real(name, z)
+        return a, d1, np.zeros_like(d2)
+
+    Hfd = _fd_hessian_of_gradient(pb)
+    monkeypatch.setattr(O, "activation", broken)
+    H = O.hessian(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
+    assert _relerr(H, Hfd) > 1e-4
+
+
+def test_pins_catch_transposed_weight_direction(monkeypatch):
+    """Planting a transposed V^(l) in the R-forward breaks the FD pin."""
+    pb = _tiny([3, 3, 3], ["sigmoid"], N=5, seed=22)
+    Hfd = _fd_hessian_of_gradient(pb)
+    real = O.unflatten
+    state = {"calls": 0}
+
+    def broken(omega, widths):
+        out = real(omega, widths)
+        state["calls"] += 1
+        # the first call unflattens omega (forward pass); every later call
+        # unflattens a direction vector inside hvp()
+        if state["calls"] > 1:
+            out = [(W.T.copy() if W.shape[0] == W.shape[1] else W, b) for W, b in out]
+        return out
+
+    monkeypatch.setattr(O, "unflatten", broken)
+    H = O.hessian(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
+    assert _relerr(H, Hfd) > 1e-4
+
+
+def test_pins_catch_unnormalised_softmax(monkeypatch):
+    """Planting a softmax output that no longer sums to one (a dropped
+    log-sum-exp normalisation) breaks the single-layer closed form."""
+    pb = _tiny([4, 3], [], N=6, seed=3)
+    f = O.forward(pb.omega, pb.widths, pb.acts, pb.X)
+    xt = np.hstack([pb.X, np.ones((pb.N, 1))])
+    ref = sum(np.kron(np.diag(p) - np.outer(p, p), np.outer(x, x)) for p, x in zip(f["p"], xt)) / pb.N
+    perm = O.param_permutation(pb.widths)
+    real_forward = O.forward
+
+    def broken_forward(*a, **k):
+        out = real_forward(*a, **k)
+        out["p"] = out["p"] * 1.5
+        return out
+
+    monkeypatch.setattr(O, "forward", broken_forward)
+    H = O.hessian(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
+    assert _relerr(H[np.ix_(perm, perm)], ref) > 1e-3
