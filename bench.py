@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Benchmark of the curvature-matrix hot path on one GB300.
+
+Workload: MLP [784, 16, 10] with tanh hidden layer, P = 12730 parameters,
+N = 1024 synthetic examples (x ~ U[0,1], uniform one-hot labels over 10
+classes, Glorot-uniform weights, zero biases, seed 1).  One step is one pass
+of the whole hot path: the OPG (forward, per-example gradients, symmetric
+rank-N update), the exact Hessian (batched R-operator over blocks of unit
+directions and its contraction) and the top-32 OPG eigenpairs (FP64 Gram
+matrix, Lanczos, back-projection).
+
+metric: exact-Hessian & OPG entries/s = 2 P^2 delivered entries per step over
+the step time.  The plain FP64 path on the same GPU is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P]
+  python bench.py --impl reference ...   (the FP64 CPU oracle, timed on the
+                                          host cores on a bounded sample)
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "exact-Hessian & OPG entries/s"
+UNIT = "entries/s"
+WORKLOAD = "mlp_784_16_10"
+K_EIG = 32
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16", "bf16x3"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------- CPU oracle ----
+def cpu_worker(sample_cols: int) -> dict:
+    """Runs in a fresh process: the FP64 oracle on a bounded sample of the
+    workload -- `sample_cols` Hessian columns (one Hessian-vector product
+    each) and the same OPG columns -- timed on the host cores."""
+    import numpy as np
+
+    from oracle import mlp as O
+    from synth import named_config
+
+    pb = named_config(WORKLOAD)
+    rng = np.random.default_rng(0)
+    cols = np.sort(rng.choice(pb.P, size=sample_cols, replace=False))
+    t0 = time.perf_counter()
+    G = O.per_example_grads(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
+    opg_cols = (G.T @ G[:, cols]) / pb.N
+    Hc = O.hessian_columns(pb.omega, pb.widths, pb.acts, pb.X, pb.Y, cols)
+    dt = time.perf_counter() - t0
+    entries = opg_cols.size + Hc.size
+    return {"value": entries / dt, "seconds": dt, "entries": int(entries),
+            "sample": f"{sample_cols} Hessian columns (unit-vector HVPs) + {sample_cols} OPG "
+                      f"columns of the {WORKLOAD} workload, N={pb.N}, FP64 numpy",
+            "cores": os.cpu_count()}
+
+
+def run_cpu_baseline(sample_cols: int) -> dict:
+    env = dict(os.environ)
+    env.pop("CUDA_VISIBLE_DEVICES", None)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker",
+                        str(sample_cols)], capture_output=True, text=True, env=env, cwd=ROOT,
+                       timeout=900)
+    if r.returncode != 0:
+        return {"error": r.stderr[-400:]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    res = []
+    for _ in range(args.warmup):
+        run_cpu_baseline(64)
+    for _ in range(args.steps):
+        res.append(run_cpu_baseline(256))
+    vals = [r["value"] for r in res if "value" in r]
+    secs = [r["seconds"] for r in res if "seconds" in r]
+    value = statistics.median(vals) if vals else None
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.mean(secs) if secs else None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD} tanh N=1024 (bounded sample per step)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle",
+                         "cores": res[0].get("cores") if res else None,
+                         "sample": res[0].get("sample") if res else None},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- clocks ----
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu_index), "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i] == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def gpu_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [v for v in vis.split(",") if v.strip()]
+    if ids and ids[local_rank % len(ids)].strip().isdigit():
+        return int(ids[local_rank % len(ids)])
+    return local_rank
+
+
+# ------------------------------------------------------------------ GPU ----
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def main():
+    args = parse()
+    if args.cpu_worker:
+        print(json.dumps(cpu_worker(args.cpu_worker)), flush=True)
+        return
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    # the CPU baseline runs first, in a fresh process, before this process
+    # uses the GPU heavily (rank 0, one GPU only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = run_cpu_baseline(2048)
+
+    from paper_1905_05559_gb300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    import paper_1905_05559_gb300 as hm
+    from synth import named_config
+
+    pb = named_config(WORKLOAD)
+    P, N = pb.P, pb.N
+    stream = torch.cuda.current_stream()
+    net = hm.HessMLP(pb.widths, pb.acts, pb.omega, stream=stream.cuda_stream)
+    lib = hm.load()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def make_io(prec):
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        X = torch.as_tensor(pb.X, dtype=dt, device="cuda")
+        Y = torch.as_tensor(pb.Y, dtype=dt, device="cuda")
+        H = torch.empty((P, P), dtype=dt, device="cuda")
+        OPG = torch.empty((P, P), dtype=dt, device="cuda")
+        ev = torch.empty(K_EIG, dtype=torch.float64, device="cuda")
+        Q = torch.empty((K_EIG, P), dtype=torch.float64, device="cuda")
+        return X, Y, H, OPG, ev, Q
+
+    def step(prec, io):
+        X, Y, H, OPG, ev, Q = io
+        net.opg(X, Y, prec, out=OPG)
+        net.exact_hessian(X, Y, prec, out=H)
+        net.opg_topk_eig(X, Y, K_EIG, prec, evals=ev, evecs=Q)
+
+    def timed(prec, steps, warmup, sampler=None):
+        io = make_io(prec)
+        for _ in range(warmup):
+            step(prec, io)
+        torch.cuda.synchronize()
+        for cls in hm._lib.KERNEL_CLASS:
+            net.read_timing(cls)
+        net.timing(True)
+        l0 = lib.hess_launch_count()
+        if sampler:
+            sampler.start()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()  # evicts L2 (256 MiB > 129 MB); outside the events
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(prec, io)
+            b.record(stream)
+            ms.append((a, b))
+        torch.cuda.synchronize()
+        barrier()
+        wall = time.perf_counter() - t0
+        clocks = sampler.stop() if sampler else None
+        launches = lib.hess_launch_count() - l0
+        net.timing(False)
+        kern = {cls: net.read_timing(cls) for cls in hm._lib.KERNEL_CLASS}
+        per = [x.elapsed_time(y) for x, y in ms]
+        t = torch.tensor([sum(per) / len(per)], device="cuda")
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        del io
+        return float(t.item()), wall, launches, kern, clocks
+
+    sampler = ClockSampler(gpu_index(local_rank)) if rank == 0 else None
+    ms_step, wall, launches, kern, clocks = timed(args.precision, args.steps, args.warmup, sampler)
+    entries = 2.0 * P * P
+    value = world * entries / (ms_step * 1e-3)
+
+    fp64 = None
+    if not args.no_fp64 and args.precision != "fp64":
+        ms64, _, _, kern64, _ = timed("fp64", args.fp64_steps, 1)
+        fp64 = {"value": world * entries / (ms64 * 1e-3), "ms_per_step": ms64,
+                "kernels_ms": {k: v["ms"] for k, v in kern64.items()}}
+
+    # end to end through the C ABI with host buffers: the library stages the
+    # pinned host inputs to the device and the outputs back every step
+    e2e = None
+    if not args.no_e2e:
+        npdt = np.float64 if args.precision == "fp64" else np.float32
+        pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()  # noqa: E731
+        tdt = torch.float64 if args.precision == "fp64" else torch.float32
+        Xh = pin(pb.X.shape, tdt)
+        Xh[:] = pb.X.astype(npdt)
+        Yh = pin(pb.Y.shape, tdt)
+        Yh[:] = pb.Y.astype(npdt)
+        Hh = pin((P, P), tdt)
+        Oh = pin((P, P), tdt)
+        evh = pin((K_EIG,), torch.float64)
+        Qh = pin((K_EIG, P), torch.float64)
+
+        def host_step():
+            net.opg(Xh, Yh, args.precision, out=Oh)
+            net.exact_hessian(Xh, Yh, args.precision, out=Hh)
+            net.opg_topk_eig(Xh, Yh, K_EIG, args.precision, evals=evh, evecs=Qh)
+
+        host_step()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            host_step()
+        torch.cuda.synchronize()
+        barrier()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        t = torch.tensor([e2e_s], device="cuda")
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+        isz = Xh.itemsize
+        e2e = {"value": world * entries / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": 3 * (Xh.size + Yh.size) * isz,
+               "d2h_bytes_per_step": (Hh.size + Oh.size) * isz + (evh.size + Qh.size) * 8}
+
+    peaks, peak_src = measured_peaks()
+    # dominant kernel class of the step
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    dk = kern[dom]
+    if args.precision in ("bf16", "bf16x3") and dom in ("syrk", "hcontract"):
+        mult = 3.0 if args.precision == "bf16x3" else 1.0
+        achieved = mult * dk["flops"] / (dk["ms"] * 1e-3) / 1e12
+        roof = {"bound": "tensor", "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                "peak_source": f"{peak_src} bf16 sustained"}
+    elif dom in ("syrk", "hcontract"):
+        achieved = dk["flops"] / (dk["ms"] * 1e-3) / 1e12
+        # FP32/FP64 SIMT: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock
+        smx = peaks.get("sm_max_mhz", 2070.0) * 1e6
+        pk = 152 * 128 * 2 * smx / 1e12 if args.precision != "fp64" else None
+        roof = {"bound": "alu", "peak": pk, "unit": "TFLOP/s",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+    else:
+        achieved = dk["bytes"] / (dk["ms"] * 1e-3) / 1e9 if dk["bytes"] else None
+        roof = {"bound": "hbm", "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "peak_source": f"{peak_src} copy bandwidth"}
+    roof.update({"kernel_class": dom, "achieved": achieved,
+                 "frac": (achieved / roof["peak"]) if (achieved and roof.get("peak")) else None,
+                 "traffic": None,
+                 "launches_per_step": dk["launches"] / max(args.steps, 1),
+                 "ms_per_step": dk["ms"] / max(args.steps, 1)})
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: MLP [784,16,10] tanh, P={P}, N={N}; OPG + exact "
+                                   f"Hessian + top-{K_EIG} OPG eig per step",
+                       "precision": args.precision, "P": P, "N": N, "k": K_EIG,
+                       "l2": "flushed between steps (256 MiB write outside the timed events)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof,
+            "cpu_baseline": ({"value": cpu["value"], "unit": UNIT, "cores": cpu["cores"],
+                              "kind": "oracle", "sample": cpu["sample"]}
+                             if cpu and "value" in cpu else cpu),
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "fp64_plain": fp64,
+            "kernels_ms_per_step": {k: v["ms"] / max(args.steps, 1) for k, v in kern.items()},
+            "wall_s": wall,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

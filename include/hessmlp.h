@@ -1,0 +1,194 @@
+/*
+ * hessmlp.h -- C ABI of the GB300 curvature-matrix library.
+ *
+ * Computes, for a dense feed-forward network with softmax cross-entropy cost
+ * (Nilsen et al., "Efficient Computation of Hessian Matrices in TensorFlow",
+ * Sec. 2: Eq. modelfunc, Eq. cost), the per-example gradient matrix G, the
+ * outer product of gradients OPG = G^T G / N (Sec. 3, Eq. hesseq2/hesseq3),
+ * the exact Hessian H (Sec. 3, Eq. hesseq1; built from Hessian-vector
+ * products with unit directions, Sec. 5.1 and Appendix A.1) and the top-k
+ * eigenpairs of the OPG (Sec. 4.1, Sec. 5.4, Eq. J).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Network:   layers l = 1..L with widths T_1..T_L; weight layer l-1 maps
+ *            layer l-1 to layer l: z^(l) = W^(l-1) a^(l-1) + b^(l), with
+ *            W^(l-1) of shape T_l x T_{l-1}; hidden layers apply sigma^(l),
+ *            the output layer applies softmax (Sec. 2).
+ * Parameters: omega has P = sum_{l=2..L} (T_{l-1} T_l + T_l) entries, laid out
+ *            layer by layer as W^(l-1) row-major (entry (i,j) at offset
+ *            i*T_{l-1} + j) followed by b^(l) (Sec. 2, Eq. flatten, read as a
+ *            row-wise flatten of each matrix).  Every row and column index of
+ *            G, OPG, H and of the eigenvectors follows this order.
+ * Inputs:    X is N x T_1 row-major, Y is N x T_L row-major one-hot labels
+ *            (rows may be any probability vector; the library uses
+ *            dC_n/dz^(L) = p_n - y_n, exact when each row sums to one).
+ * Precision: HESS_FP64 -- X, Y and outputs are double; all arithmetic FP64.
+ *            HESS_FP32 -- X, Y and outputs are float; arithmetic FP32 (the
+ *                         softmax log-sum-exp in FP64).
+ *            HESS_BF16, HESS_BF16X3 -- X, Y and outputs are float; forward and
+ *                         backward passes in FP32; the OPG and Hessian
+ *                         contractions on the tensor cores with BF16 operands
+ *                         (one product) or split-BF16 operands
+ *                         (hi*hi + hi*lo + lo*hi) and FP32 accumulation.
+ * Memory:    every data pointer may point to host or device memory; the
+ *            library asks the CUDA runtime which.  Device pointers must be on
+ *            the handle's device.  The caller owns every buffer it passes;
+ *            the handle owns omega's device copy and all workspace.
+ * Streams:   work is queued on the handle's stream.  A call whose pointers are
+ *            all device pointers returns without waiting; a call with any host
+ *            pointer waits for its own work before returning.
+ * Errors:    every entry point returns a hess_status; nothing aborts or
+ *            throws.  Arguments are checked before any work is queued.
+ *            hess_last_error() gives a message for the calling thread's most
+ *            recent failure.
+ * Threads:   a handle must not be used by two threads at once.
+ */
+#ifndef HESSMLP_H
+#define HESSMLP_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HESS_API __attribute__((visibility("default")))
+#else
+#define HESS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HESS_OK = 0,
+  HESS_ERR_INVALID_ARG = 1,    /* bad pointer, size, enum or layout */
+  HESS_ERR_OOM = 2,            /* device allocation failed */
+  HESS_ERR_CUDA = 3,           /* a CUDA runtime or kernel error */
+  HESS_ERR_RANK_DEFICIENT = 4, /* opg_topk_eig: some of the k eigenvalues are
+                                  null (results still written) */
+  HESS_ERR_NOT_CONVERGED = 5,  /* opg_topk_eig: iteration limit reached */
+  HESS_ERR_TIMEOUT = 6,        /* a bounded device wait gave up */
+  HESS_ERR_ADMISSION = 7,      /* request exceeds the memory budget */
+  HESS_ERR_UNSUPPORTED = 8     /* valid request this build cannot serve */
+} hess_status;
+
+typedef enum { HESS_ACT_SIGMOID = 0, HESS_ACT_TANH = 1, HESS_ACT_RELU = 2 } hess_act;
+
+typedef enum { HESS_FP64 = 0, HESS_FP32 = 1, HESS_BF16 = 2, HESS_BF16X3 = 3 } hess_precision;
+
+typedef struct hess_mlp hess_mlp;
+
+/* Network description (Sec. 2).  widths: L entries T_1..T_L (L >= 2, each
+ * T_l >= 1, T_L >= 2); act: L-2 hidden activations (may be NULL when L == 2).
+ * The arrays are copied at create time. */
+typedef struct {
+  int L;
+  const int* widths;
+  const int* act; /* hess_act values */
+} hess_mlp_desc;
+
+/* Create a handle for the network and parameter point omega (P doubles, host or
+ * device, order of Eq. flatten).  omega is copied to the device (FP64 and FP32
+ * copies); the caller keeps ownership of its buffer.  stream: a cudaStream_t
+ * (NULL = the legacy default stream).  The current CUDA device becomes the
+ * handle's device.  Errors: INVALID_ARG (bad desc, NULL out/omega),
+ * OOM, CUDA. */
+HESS_API hess_status hess_mlp_create(const hess_mlp_desc* desc, const double* omega, void* stream,
+                            hess_mlp** out);
+
+/* Release the handle and its device memory (waits for its stream first).
+ * NULL is accepted and ignored. */
+HESS_API hess_status hess_mlp_destroy(hess_mlp* h);
+
+/* P, the number of parameters (Sec. 2, after Eq. flatten); -1 for NULL. */
+HESS_API int64_t hess_mlp_num_params(const hess_mlp* h);
+
+/* Replace the parameter point (P doubles, host or device). */
+HESS_API hess_status hess_mlp_set_params(hess_mlp* h, const double* omega);
+
+/* Change the stream used by later calls. */
+HESS_API hess_status hess_mlp_set_stream(hess_mlp* h, void* stream);
+
+/* Per-example gradient matrix (Sec. 3.1 and Sec. 5.2 "get_J_op"; the matrix J
+ * of Eq. hesseq3 read with one example per ROW): G is N x P row-major,
+ * G[n, :] = dC_n/domega^T with C_n the per-example cross-entropy of Eq. cost.
+ * Precision FP64 (double X, Y, G) or FP32 (float X, Y, G); BF16/BF16X3 are
+ * accepted and compute as FP32.  N >= 1.  Errors: INVALID_ARG, OOM, CUDA. */
+HESS_API hess_status per_example_grads(hess_mlp* h, const void* X, const void* Y, int64_t N,
+                              hess_precision prec, void* G);
+
+/* OPG = (1/N) sum_n g_n g_n^T = G^T G / N (Sec. 3, Eq. hesseq2 and hesseq3),
+ * written in full (both triangles) as a P x P row-major matrix, double for
+ * FP64 and float otherwise.  The contraction is a symmetric rank-N update:
+ * FP64/FP32 on the SIMT pipes, BF16/BF16X3 on the tensor cores.  The 1/N
+ * weighting always uses the true N.  Errors: INVALID_ARG, OOM, CUDA. */
+HESS_API hess_status opg(hess_mlp* h, const void* X, const void* Y, int64_t N, hess_precision prec,
+                void* OPG);
+
+/* Exact Hessian H = (1/N) sum_n d^2 C_n / domega domega^T (Sec. 3, Eq.
+ * hesseq1), P x P row-major, both triangles, double for FP64 and float
+ * otherwise.  Computed as in Sec. 5.1 from Hessian-vector products with the
+ * unit vectors of R^P, batched over blocks of directions: each block runs the
+ * forward-over-reverse R-operator (Pearlmutter; Appendix A.1 shows the
+ * product equals the second derivative applied to the direction) and a
+ * contraction over the N examples.  Errors: INVALID_ARG, OOM, CUDA. */
+HESS_API hess_status exact_hessian(hess_mlp* h, const void* X, const void* Y, int64_t N,
+                          hess_precision prec, void* H);
+
+/* Top-k eigenpairs of the OPG (Sec. 4.1 low-rank factors, Sec. 5.4 Eq. J):
+ * with M = G G^T / N (N x N), the OPG eigenvalues are the eigenvalues mu of M
+ * and the eigenvectors are q = G^T u / sqrt(N mu).  evals: k doubles in
+ * descending (algebraic) order; evecs: P x k column-major doubles (column c is
+ * q_c, unit norm, sign chosen so that its largest-magnitude entry is
+ * positive).  X and Y are double for FP64 and float otherwise; the Gram
+ * matrix, the eigensolver (Lanczos with full reorthogonalisation) and the
+ * back-projection run in FP64 for every precision.  Requires 1 <= k <=
+ * min(N, P).  Returns HESS_ERR_RANK_DEFICIENT (after writing every output)
+ * when mu_c <= 1e-13 mu_1 for some c; those columns are zero.  Errors:
+ * INVALID_ARG, OOM, CUDA, NOT_CONVERGED. */
+HESS_API hess_status opg_topk_eig(hess_mlp* h, const void* X, const void* Y, int64_t N, int k,
+                         hess_precision prec, double* evals, double* evecs);
+
+/* Host helper: perm[i] = the index in the order of Eq. flatten of the i-th
+ * parameter in "augmented row" order, where each output unit's weight row is
+ * followed by its bias ([W_i,: , b_i] for every layer).  perm has P entries. */
+HESS_API hess_status hess_param_permutation(int L, const int* widths, int64_t* perm);
+
+/* ----------------------------------------------------------------------
+ * Measurement hooks (no counterpart in the paper).  When timing is enabled
+ * the library brackets every launch of the kernel classes below with CUDA
+ * events on the handle's stream, and records the algorithmic work of each
+ * launch (flops of the contraction, or bytes that must cross HBM).
+ * hess_timing_read waits for the handle's stream, returns the totals since
+ * the last read for one class and resets them.
+ * -------------------------------------------------------------------- */
+typedef enum {
+  HESS_K_SYRK = 0,      /* OPG contraction G^T G / N */
+  HESS_K_HCONTRACT = 1, /* Hessian contraction over the N examples */
+  HESS_K_GRADS = 2,     /* per-example gradient rows (HBM write) */
+  HESS_K_ROP = 3,       /* R-operator over a block of directions */
+  HESS_K_EIG = 4,       /* Gram matrix, Lanczos and back-projection */
+  HESS_K_COUNT = 5
+} hess_kernel_class;
+
+typedef struct {
+  int64_t launches;
+  double ms;    /* summed device time of the bracketed launches */
+  double flops; /* summed algorithmic flops */
+  double bytes; /* summed algorithmic HBM bytes */
+} hess_kernel_stats;
+
+HESS_API hess_status hess_timing_enable(hess_mlp* h, int enable);
+HESS_API hess_status hess_timing_read(hess_mlp* h, int kernel_class, hess_kernel_stats* out);
+
+/* Number of kernels this library has launched in the process so far. */
+HESS_API int64_t hess_launch_count(void);
+
+/* Message for the calling thread's most recent error ("" if none). */
+HESS_API const char* hess_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HESSMLP_H */

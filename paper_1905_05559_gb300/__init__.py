@@ -1,0 +1,5 @@
+"""GB300-native curvature matrices (G, OPG, exact Hessian, OPG eigenpairs) for
+dense MLPs with softmax cross-entropy, behind the C ABI in include/hessmlp.h."""
+
+from ._lib import EXPORTS, HessError, load, last_error  # noqa: F401
+from .api import HessMLP, param_permutation  # noqa: F401

@@ -1,0 +1,109 @@
+"""ctypes declarations of the C ABI in include/hessmlp.h."""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhessmlp.so")
+
+HESS_OK = 0
+HESS_ERR_INVALID_ARG = 1
+HESS_ERR_OOM = 2
+HESS_ERR_CUDA = 3
+HESS_ERR_RANK_DEFICIENT = 4
+HESS_ERR_NOT_CONVERGED = 5
+HESS_ERR_TIMEOUT = 6
+HESS_ERR_ADMISSION = 7
+HESS_ERR_UNSUPPORTED = 8
+
+STATUS_NAMES = {
+    0: "HESS_OK", 1: "HESS_ERR_INVALID_ARG", 2: "HESS_ERR_OOM", 3: "HESS_ERR_CUDA",
+    4: "HESS_ERR_RANK_DEFICIENT", 5: "HESS_ERR_NOT_CONVERGED", 6: "HESS_ERR_TIMEOUT",
+    7: "HESS_ERR_ADMISSION", 8: "HESS_ERR_UNSUPPORTED",
+}
+
+ACT = {"sigmoid": 0, "tanh": 1, "relu": 2}
+PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 3}
+
+# every symbol the header declares
+EXPORTS = (
+    "hess_mlp_create", "hess_mlp_destroy", "hess_mlp_num_params", "hess_mlp_set_params",
+    "hess_mlp_set_stream", "per_example_grads", "opg", "exact_hessian", "opg_topk_eig",
+    "hess_param_permutation", "hess_last_error", "hess_timing_enable", "hess_timing_read",
+    "hess_launch_count",
+)
+
+KERNEL_CLASS = {"syrk": 0, "hcontract": 1, "grads": 2, "rop": 3, "eig": 4}
+
+
+class KernelStats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+class HessDesc(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("widths", ctypes.POINTER(ctypes.c_int)),
+                ("act", ctypes.POINTER(ctypes.c_int))]
+
+
+class HessError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load the in-tree library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: run paper_1905_05559_gb300.build.build() first")
+    lib = ctypes.CDLL(p)
+    vp, i64 = ctypes.c_void_p, ctypes.c_int64
+    st = ctypes.c_int
+    lib.hess_mlp_create.argtypes = [ctypes.POINTER(HessDesc), vp, vp, ctypes.POINTER(vp)]
+    lib.hess_mlp_create.restype = st
+    lib.hess_mlp_destroy.argtypes = [vp]
+    lib.hess_mlp_destroy.restype = st
+    lib.hess_mlp_num_params.argtypes = [vp]
+    lib.hess_mlp_num_params.restype = i64
+    lib.hess_mlp_set_params.argtypes = [vp, vp]
+    lib.hess_mlp_set_params.restype = st
+    lib.hess_mlp_set_stream.argtypes = [vp, vp]
+    lib.hess_mlp_set_stream.restype = st
+    for name in ("per_example_grads", "opg", "exact_hessian"):
+        f = getattr(lib, name)
+        f.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp]
+        f.restype = st
+    lib.opg_topk_eig.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, vp, vp]
+    lib.opg_topk_eig.restype = st
+    lib.hess_param_permutation.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int64)]
+    lib.hess_param_permutation.restype = st
+    lib.hess_timing_enable.argtypes = [vp, ctypes.c_int]
+    lib.hess_timing_enable.restype = st
+    lib.hess_timing_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(KernelStats)]
+    lib.hess_timing_read.restype = st
+    lib.hess_launch_count.argtypes = []
+    lib.hess_launch_count.restype = ctypes.c_int64
+    lib.hess_last_error.argtypes = []
+    lib.hess_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().hess_last_error().decode(errors="replace")
+
+
+def check(status: int, allow=()) -> int:
+    if status != HESS_OK and status not in allow:
+        raise HessError(status, last_error())
+    return status

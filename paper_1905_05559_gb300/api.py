@@ -1,0 +1,148 @@
+"""Python face of the C ABI: argument marshalling only.
+
+Tensors are passed to the library as raw pointers; every computation runs in
+the CUDA library.  Device tensors (torch, on the handle's device) are used in
+place; numpy arrays are passed as host pointers and the library stages them.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+
+try:  # torch is plumbing only: device memory and streams
+    import torch
+except Exception:  # pragma: no cover
+    torch = None
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if torch is not None and isinstance(a, torch.Tensor):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _dtype_of(prec: str):
+    return "float64" if prec == "fp64" else "float32"
+
+
+def _check_dtype(a, prec, name):
+    want = _dtype_of(prec)
+    got = str(a.dtype).replace("torch.", "")
+    if got != want:
+        raise TypeError(f"{name} must be {want} for precision {prec} (got {got})")
+
+
+def param_permutation(widths) -> np.ndarray:
+    lib = _lib.load()
+    w = (ctypes.c_int * len(widths))(*widths)
+    P = sum(widths[i] * widths[i + 1] + widths[i + 1] for i in range(len(widths) - 1))
+    out = np.empty(P, dtype=np.int64)
+    _lib.check(lib.hess_param_permutation(len(widths), w,
+                                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return out
+
+
+class HessMLP:
+    """Handle on a network and a parameter point (hess_mlp_create)."""
+
+    def __init__(self, widths, acts, omega, stream=None):
+        self._lib = _lib.load()
+        self.widths = [int(t) for t in widths]
+        self.acts = list(acts)
+        w = (ctypes.c_int * len(self.widths))(*self.widths)
+        a = (ctypes.c_int * max(1, len(self.acts)))(*[_lib.ACT[x] for x in self.acts] or [0])
+        desc = _lib.HessDesc(len(self.widths), w, a)
+        self._keep = (w, a)
+        if isinstance(omega, np.ndarray):
+            omega = np.ascontiguousarray(omega, dtype=np.float64)
+        h = ctypes.c_void_p()
+        _lib.check(self._lib.hess_mlp_create(ctypes.byref(desc), _ptr(omega),
+                                             ctypes.c_void_p(stream or 0), ctypes.byref(h)))
+        self.h = h
+        self.P = int(self._lib.hess_mlp_num_params(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.hess_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, omega):
+        if isinstance(omega, np.ndarray):
+            omega = np.ascontiguousarray(omega, dtype=np.float64)
+        _lib.check(self._lib.hess_mlp_set_params(self.h, _ptr(omega)))
+
+    def set_stream(self, stream):
+        _lib.check(self._lib.hess_mlp_set_stream(self.h, ctypes.c_void_p(stream or 0)))
+
+    def timing(self, enable: bool):
+        _lib.check(self._lib.hess_timing_enable(self.h, 1 if enable else 0))
+
+    def read_timing(self, kernel_class: str) -> dict:
+        st = _lib.KernelStats()
+        _lib.check(self._lib.hess_timing_read(self.h, _lib.KERNEL_CLASS[kernel_class],
+                                              ctypes.byref(st)))
+        return {"launches": st.launches, "ms": st.ms, "flops": st.flops, "bytes": st.bytes}
+
+    # ------------------------------------------------------------ calls
+    def _io(self, X, Y, prec):
+        _check_dtype(X, prec, "X")
+        _check_dtype(Y, prec, "Y")
+        return int(X.shape[0])
+
+    def per_example_grads(self, X, Y, prec="fp64", out=None):
+        N = self._io(X, Y, prec)
+        out = self._alloc_like(X, (N, self.P), prec) if out is None else out
+        _lib.check(self._lib.per_example_grads(self.h, _ptr(X), _ptr(Y), N,
+                                               _lib.PRECISION[prec], _ptr(out)))
+        return out
+
+    def opg(self, X, Y, prec="fp64", out=None):
+        N = self._io(X, Y, prec)
+        out = self._alloc_like(X, (self.P, self.P), prec) if out is None else out
+        _lib.check(self._lib.opg(self.h, _ptr(X), _ptr(Y), N, _lib.PRECISION[prec], _ptr(out)))
+        return out
+
+    def exact_hessian(self, X, Y, prec="fp64", out=None):
+        N = self._io(X, Y, prec)
+        out = self._alloc_like(X, (self.P, self.P), prec) if out is None else out
+        _lib.check(self._lib.exact_hessian(self.h, _ptr(X), _ptr(Y), N, _lib.PRECISION[prec],
+                                           _ptr(out)))
+        return out
+
+    def opg_topk_eig(self, X, Y, k, prec="fp64", evals=None, evecs=None, allow_deficient=False):
+        """Returns (evals (k,), evecs (k, P) whose row c is q_c, status)."""
+        N = self._io(X, Y, prec)
+        if evals is None:
+            evals = self._alloc_like(X, (k,), "fp64")
+        if evecs is None:
+            evecs = self._alloc_like(X, (k, self.P), "fp64")
+        allow = (_lib.HESS_ERR_RANK_DEFICIENT,) if allow_deficient else ()
+        st = _lib.check(self._lib.opg_topk_eig(self.h, _ptr(X), _ptr(Y), N, int(k),
+                                               _lib.PRECISION[prec], _ptr(evals), _ptr(evecs)),
+                        allow)
+        return evals, evecs, st
+
+    @staticmethod
+    def _alloc_like(X, shape, prec):
+        dt = _dtype_of(prec)
+        if torch is not None and isinstance(X, torch.Tensor):
+            return torch.empty(shape, dtype=getattr(torch, dt), device=X.device)
+        return np.empty(shape, dtype=dt)

@@ -1,0 +1,219 @@
+// Internal declarations shared by the translation units of libhessmlp.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <vector>
+
+#include "../../include/hessmlp.h"
+
+namespace hm {
+
+// ---------------------------------------------------------------- errors ----
+hess_status set_error(hess_status s, const char* fmt, ...);
+void clear_error();
+
+#define HM_CUDA(expr)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (expr);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return ::hm::set_error(e_ == cudaErrorMemoryAllocation ? HESS_ERR_OOM : HESS_ERR_CUDA, \
+                             "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_),     \
+                             __FILE__, __LINE__);                                       \
+  } while (0)
+
+#define HM_TRY(expr)                 \
+  do {                               \
+    hess_status s_ = (expr);         \
+    if (s_ != HESS_OK) return s_;    \
+  } while (0)
+
+extern std::atomic<int64_t> g_launches;
+#define HM_LAUNCHED()                                         \
+  do {                                                        \
+    ::hm::g_launches.fetch_add(1, std::memory_order_relaxed); \
+    HM_CUDA(cudaGetLastError());                              \
+  } while (0)
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ------------------------------------------------------------ workspace ----
+// Two-pass bump allocator: a plan is run once with base == nullptr to size it,
+// then again on the real buffer.
+struct Arena {
+  char* base = nullptr;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t n) {
+    off = align_up(off, 256);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+// --------------------------------------------------------------- network ----
+struct Net {
+  int L = 0;
+  std::vector<int> T;         // widths T_1..T_L stored at T[0..L-1]
+  std::vector<int> act;       // hidden activations for layers 2..L-1 at act[0..L-3]
+  std::vector<int64_t> woff;  // offset of W^(j) (j = 1..L-1) at woff[j-1]
+  std::vector<int64_t> boff;  // offset of b^(j+1) at boff[j-1]
+  int64_t P = 0;
+};
+
+}  // namespace hm
+
+namespace hm {
+struct TimingRec {
+  cudaEvent_t a, b;
+  int cls;
+  double flops, bytes;
+};
+}  // namespace hm
+
+struct hess_mlp {
+  hm::Net net;
+  bool timing = false;
+  std::vector<hm::TimingRec> pending;
+  std::vector<cudaEvent_t> event_pool;
+  hess_kernel_stats acc[HESS_K_COUNT] = {};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  double* omega64 = nullptr;  // device, P
+  float* omega32 = nullptr;   // device, P
+  char* ws = nullptr;         // device workspace
+  size_t ws_bytes = 0;
+  double* host_pinned = nullptr;  // small pinned scratch for scalars
+  int sm_count = 0;
+};
+
+namespace hm {
+
+hess_status ensure_ws(hess_mlp* h, size_t bytes);
+
+// Brackets launches with CUDA events when the handle's timing is enabled.
+class Tick {
+ public:
+  Tick(hess_mlp* h, int cls, double flops, double bytes);
+  void stop();
+  ~Tick() { stop(); }
+
+ private:
+  hess_mlp* h_;
+  TimingRec rec_{};
+  bool live_ = false;
+};
+
+// ------------------------------------------------------- SIMT launchers ----
+// Generic strided GEMM: C(m,n) = alpha * sum_k A(m,k) B(k,n) + beta * C(m,n),
+// A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn], C(m,n) = C[m*scm + n*scn],
+// batched over blockIdx.z with element strides bsa/bsb/bsc.  upper: M == N and
+// only the tiles on or above the diagonal are computed.
+template <typename T>
+struct Gemm {
+  int M = 0, N = 0, K = 0;
+  T alpha = 1, beta = 0;
+  const T* A = nullptr;
+  int64_t sam = 0, sak = 0, bsa = 0;
+  const T* B = nullptr;
+  int64_t sbk = 0, sbn = 0, bsb = 0;
+  T* C = nullptr;
+  int64_t scm = 0, scn = 0, bsc = 0;
+  int batch = 1;
+  int upper = 0;
+};
+template <typename T>
+hess_status gemm(const Gemm<T>& g, cudaStream_t s);
+
+// Forward/backward caches of one call (all device, row-major N x T_l).
+template <typename T>
+struct Caches {
+  int64_t N = 0;
+  std::vector<const T*> a;  // a[j] j = 0..L-2 (a[0] = X)
+  std::vector<T*> s1, s2;   // sigma', sigma'' for hidden positions j = 1..L-2
+  std::vector<T*> d;        // delta for positions j = 1..L-1
+  std::vector<T*> e;        // W^T delta before sigma' for hidden j
+  T* p = nullptr;           // softmax output N x T_L
+  T* ysum = nullptr;        // row sums of Y (N)
+  T* z = nullptr;           // scratch for pre-activations (N x max T)
+};
+template <typename T>
+void plan_caches(Arena& ar, const Net& net, int64_t N, Caches<T>& c);
+template <typename T>
+hess_status forward_backward(const Net& net, const T* omega, const T* X, const T* Y, Caches<T>& c,
+                             cudaStream_t s);
+template <typename T>
+hess_status write_grads(const Net& net, const Caches<T>& c, T* G, int64_t ldg, cudaStream_t s);
+template <typename T>
+hess_status mirror_upper(T* C, int64_t n, int64_t ldc, cudaStream_t s);
+template <typename T>
+hess_status fill(T* p, int64_t n, T v, cudaStream_t s);
+template <typename Ti, typename To>
+hess_status convert(const Ti* in, To* out, int64_t n, cudaStream_t s);
+
+// R-operator over a block of B unit directions d0..d0+B-1, all inside the
+// parameters of weight layer jm (1-based, W^(jm) and b^(jm+1)).
+template <typename T>
+struct RopBufs {
+  int B = 0;
+  std::vector<T*> rz;  // positions j >= jm: B x N x T
+  std::vector<T*> ra;  // hidden positions j >= jm
+  std::vector<T*> rd;  // positions j >= jm
+  T* tmp = nullptr;    // B x N x max T
+};
+template <typename T>
+void plan_rop(Arena& ar, const Net& net, int64_t N, int jm, int B, RopBufs<T>& r);
+template <typename T>
+hess_status rop_block(const Net& net, const T* omega, const Caches<T>& c, int jm, int64_t d0, int B,
+                      RopBufs<T>& r, cudaStream_t s);
+// H[d][c] for the block's rows and the columns of weight layer jl (>= jm),
+// masked to c >= d0 and mirrored to H[c][d] for c >= d0 + B.  tmp: B x P_l.
+template <typename T>
+hess_status contract_layer(const Net& net, const Caches<T>& c, const RopBufs<T>& r, int jm, int jl,
+                           int64_t d0, T* tmp, const T* ones, T* H, cudaStream_t s);
+template <typename T>
+hess_status scatter_sym(const T* tmp, int B, int64_t cols, int64_t c0, int64_t d0, T* H, int64_t P,
+                        cudaStream_t s);
+
+// -------------------------------------------------------- eigensolver ----
+struct EigResult {
+  int converged = 0;
+  int rank_deficient = 0;
+  int lanczos_steps = 0;
+};
+hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, int64_t N, int k,
+                          double* evals_d, double* evecs_d, Arena& ar, bool dry, EigResult* res);
+
+// ------------------------------------------------------ tensor cores ----
+// bf16 operands: Ahi/Alo: M x K, Bhi/Blo: Nn x K, both K-major with leading
+// dimension ld (elements, multiple of 64).  D(m, n) = scale * sum_k A(m,k) B(n,k)
+// with terms hi*hi (+ hi*lo + lo*hi when x3).  Output mapping, per tile row m:
+//   out_row = rbase + (m % rgroup), out_col = cbase + (m / rgroup) * cgstride + n
+//   direct write  out[out_row * ldo + out_col]  if out_col >= dmin
+//   mirror write  out[out_col * ldo + out_row]  if out_col >= mmin
+struct TcGemm {
+  int M = 0, Nn = 0, K = 0, ld = 0;
+  const void* Ahi = nullptr;
+  const void* Alo = nullptr;
+  const void* Bhi = nullptr;
+  const void* Blo = nullptr;
+  int x3 = 0;
+  float scale = 1.f;
+  float* out = nullptr;
+  int64_t ldo = 0;
+  int64_t rbase = 0, rgroup = 1 << 30, cbase = 0, cgstride = 0;
+  int64_t dmin = 0, mmin = 0;
+  int syrk = 0;  // A == B: only tiles whose column range reaches the diagonal
+};
+hess_status tc_available(hess_mlp* h);
+hess_status tc_gemm(hess_mlp* h, const TcGemm& g, cudaStream_t s);
+hess_status split_bf16(const float* in, int64_t rows, int64_t cols, int64_t ldin, int transpose,
+                       void* hi, void* lo, int64_t ld, cudaStream_t s);
+
+}  // namespace hm

@@ -1,0 +1,726 @@
+// SIMT kernels of the plain FP64 / FP32 path: strided GEMM, the forward and
+// backward passes of the MLP, the per-example gradient writer, the batched
+// R-operator over blocks of unit directions, and the symmetric scatter that
+// places Hessian row blocks and their mirror images.
+#include "internal.h"
+
+namespace hm {
+
+// ====================================================================== GEMM
+template <typename T>
+struct GemmCfg;
+template <>
+struct GemmCfg<double> {
+  static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
+};
+template <>
+struct GemmCfg<float> {
+  static constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8;
+};
+
+// Row of the upper-triangular tile enumeration: row r holds nt - r tiles and
+// S(r) = r*nt - r*(r-1)/2 tiles come before it.
+__device__ __forceinline__ void upper_tile(long long t, int nt, int& tm, int& tn) {
+  double b = 2.0 * nt + 1.0;
+  int r = (int)floor((b - sqrt(fmax(b * b - 8.0 * (double)t, 0.0))) * 0.5);
+  if (r < 0) r = 0;
+  if (r > nt - 1) r = nt - 1;
+  auto S = [nt](long long rr) { return rr * nt - rr * (rr - 1) / 2; };
+  while (r > 0 && S(r) > t) --r;
+  while (r + 1 < nt && S(r + 1) <= t) ++r;
+  tm = r;
+  tn = r + (int)(t - S(r));
+}
+
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__(256) gemm_kernel(Gemm<T> g) {
+  constexpr int NT = (BM / TM) * (BN / TN);
+  static_assert(NT == 256, "256 threads");
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+  int tm, tn;
+  if (g.upper) {
+    upper_tile(blockIdx.x, (g.M + BM - 1) / BM, tm, tn);
+  } else {
+    tm = blockIdx.x;
+    tn = blockIdx.y;
+  }
+  const T* A = g.A + (int64_t)blockIdx.z * g.bsa;
+  const T* B = g.B + (int64_t)blockIdx.z * g.bsb;
+  T* C = g.C + (int64_t)blockIdx.z * g.bsc;
+  const int tid = threadIdx.x;
+  const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+  const int64_t m0 = (int64_t)tm * BM, n0 = (int64_t)tn * BN;
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+  const bool a_m_fast = (g.sam == 1);
+  const bool b_n_fast = (g.sbn == 1);
+  for (int k0 = 0; k0 < g.K; k0 += BK) {
+#pragma unroll
+    for (int it = 0; it < BM * BK / NT; ++it) {
+      int e = tid + it * NT;
+      int mm, kk;
+      if (a_m_fast) {
+        mm = e % BM;
+        kk = e / BM;
+      } else {
+        kk = e % BK;
+        mm = e / BK;
+      }
+      int64_t m = m0 + mm;
+      int k = k0 + kk;
+      As[kk][mm] = (m < g.M && k < g.K) ? A[m * g.sam + (int64_t)k * g.sak] : T(0);
+    }
+#pragma unroll
+    for (int it = 0; it < BN * BK / NT; ++it) {
+      int e = tid + it * NT;
+      int nn, kk;
+      if (b_n_fast) {
+        nn = e % BN;
+        kk = e / BN;
+      } else {
+        kk = e % BK;
+        nn = e / BK;
+      }
+      int64_t n = n0 + nn;
+      int k = k0 + kk;
+      Bs[kk][nn] = (n < g.N && k < g.K) ? B[(int64_t)k * g.sbk + n * g.sbn] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + i * (BM / TM)];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + j * (BN / TN)];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    int64_t m = m0 + ty + i * (BM / TM);
+    if (m >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      int64_t n = n0 + tx + j * (BN / TN);
+      if (n >= g.N) continue;
+      T* c = C + m * g.scm + n * g.scn;
+      T v = g.alpha * acc[i][j];
+      if (g.beta != T(0)) v += g.beta * (*c);
+      *c = v;
+    }
+  }
+}
+
+template <typename T>
+hess_status gemm(const Gemm<T>& g, cudaStream_t s) {
+  using Cfg = GemmCfg<T>;
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return HESS_OK;
+  if (g.batch > 65535) return set_error(HESS_ERR_INVALID_ARG, "gemm batch %d too large", g.batch);
+  dim3 grid;
+  if (g.upper) {
+    int64_t nt = cdiv(g.M, Cfg::BM);
+    grid = dim3((unsigned)(nt * (nt + 1) / 2), 1, g.batch);
+  } else {
+    int64_t gy = cdiv(g.N, Cfg::BN);
+    if (gy > 65535) return set_error(HESS_ERR_INVALID_ARG, "gemm N %d too large", g.N);
+    grid = dim3((unsigned)cdiv(g.M, Cfg::BM), (unsigned)gy, g.batch);
+  }
+  if (g.K <= 0) {
+    // empty contraction: C = beta * C
+    Gemm<T> z = g;
+    gemm_kernel<T, Cfg::BM, Cfg::BN, Cfg::BK, Cfg::TM, Cfg::TN><<<grid, 256, 0, s>>>(z);
+    HM_LAUNCHED();
+    return HESS_OK;
+  }
+  gemm_kernel<T, Cfg::BM, Cfg::BN, Cfg::BK, Cfg::TM, Cfg::TN><<<grid, 256, 0, s>>>(g);
+  HM_LAUNCHED();
+  return HESS_OK;
+}
+template hess_status gemm<double>(const Gemm<double>&, cudaStream_t);
+template hess_status gemm<float>(const Gemm<float>&, cudaStream_t);
+
+// ============================================================= elementwise
+template <typename T>
+__global__ void fill_kernel(T* p, int64_t n, T v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+template <typename T>
+hess_status fill(T* p, int64_t n, T v, cudaStream_t s) {
+  if (n <= 0) return HESS_OK;
+  int64_t blocks = cdiv(n, 256);
+  if (blocks > 65536) blocks = 65536;
+  fill_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(p, n, v);
+  HM_LAUNCHED();
+  return HESS_OK;
+}
+template hess_status fill<double>(double*, int64_t, double, cudaStream_t);
+template hess_status fill<float>(float*, int64_t, float, cudaStream_t);
+
+template <typename Ti, typename To>
+__global__ void convert_kernel(const Ti* in, To* out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (To)in[i];
+}
+template <typename Ti, typename To>
+hess_status convert(const Ti* in, To* out, int64_t n, cudaStream_t s) {
+  if (n <= 0) return HESS_OK;
+  int64_t blocks = cdiv(n, 256);
+  if (blocks > 65536) blocks = 65536;
+  convert_kernel<Ti, To><<<(unsigned)blocks, 256, 0, s>>>(in, out, n);
+  HM_LAUNCHED();
+  return HESS_OK;
+}
+template hess_status convert<double, float>(const double*, float*, int64_t, cudaStream_t);
+template hess_status convert<float, double>(const float*, double*, int64_t, cudaStream_t);
+
+// =========================================================== activations
+// Hidden activation value and its first two derivatives (ReLU: sigma'(0) = 0).
+__device__ __forceinline__ void act_eval(int act, double z, double& a, double& d1, double& d2) {
+  if (act == HESS_ACT_SIGMOID) {
+    double s = 1.0 / (1.0 + exp(-z));
+    a = s;
+    d1 = s * (1.0 - s);
+    d2 = d1 * (1.0 - 2.0 * s);
+  } else if (act == HESS_ACT_TANH) {
+    double t = tanh(z);
+    a = t;
+    d1 = 1.0 - t * t;
+    d2 = -2.0 * t * d1;
+  } else {
+    a = z > 0.0 ? z : 0.0;
+    d1 = z > 0.0 ? 1.0 : 0.0;
+    d2 = 0.0;
+  }
+}
+__device__ __forceinline__ void act_eval(int act, float z, float& a, float& d1, float& d2) {
+  if (act == HESS_ACT_SIGMOID) {
+    float s = 1.0f / (1.0f + expf(-z));
+    a = s;
+    d1 = s * (1.0f - s);
+    d2 = d1 * (1.0f - 2.0f * s);
+  } else if (act == HESS_ACT_TANH) {
+    float t = tanhf(z);
+    a = t;
+    d1 = 1.0f - t * t;
+    d2 = -2.0f * t * d1;
+  } else {
+    a = z > 0.0f ? z : 0.0f;
+    d1 = z > 0.0f ? 1.0f : 0.0f;
+    d2 = 0.0f;
+  }
+}
+
+template <typename T>
+__global__ void bias_act_kernel(const T* Z, const T* b, int64_t N, int Tn, int act, T* A, T* S1,
+                                T* S2) {
+  int64_t n_el = N * Tn;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n_el;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(idx % Tn);
+    T a, d1, d2;
+    act_eval(act, Z[idx] + b[i], a, d1, d2);
+    A[idx] = a;
+    S1[idx] = d1;
+    S2[idx] = d2;
+  }
+}
+
+// Softmax output with the log-sum-exp in FP64; delta^(L) = p * sum(y) - y.
+template <typename T>
+__global__ void softmax_kernel(const T* Z, const T* b, const T* Y, int64_t N, int TL, T* Pout,
+                               T* D, T* ysum) {
+  int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const T* z = Z + n * TL;
+  const T* y = Y + n * TL;
+  double m = -INFINITY;
+  for (int i = 0; i < TL; ++i) m = fmax(m, (double)z[i] + (double)b[i]);
+  double s = 0.0, ys = 0.0;
+  for (int i = 0; i < TL; ++i) {
+    s += exp((double)z[i] + (double)b[i] - m);
+    ys += (double)y[i];
+  }
+  double lse = m + log(s);
+  for (int i = 0; i < TL; ++i) {
+    double p = exp((double)z[i] + (double)b[i] - lse);
+    Pout[n * TL + i] = (T)p;
+    D[n * TL + i] = (T)(p * ys - (double)y[i]);
+  }
+  ysum[n] = (T)ys;
+}
+
+template <typename T>
+__global__ void mul_kernel(const T* a, const T* b, T* out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = a[i] * b[i];
+}
+
+static unsigned grid1d(int64_t n, int threads = 256) {
+  int64_t b = cdiv(n, threads);
+  if (b > 1 << 20) b = 1 << 20;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+template <typename T>
+void plan_caches(Arena& ar, const Net& net, int64_t N, Caches<T>& c) {
+  const int L = net.L;
+  c.N = N;
+  c.a.assign(L - 1, nullptr);
+  c.s1.assign(L, nullptr);
+  c.s2.assign(L, nullptr);
+  c.e.assign(L, nullptr);
+  c.d.assign(L, nullptr);
+  int maxT = 0;
+  for (int j = 0; j < L; ++j) maxT = net.T[j] > maxT ? net.T[j] : maxT;
+  for (int j = 1; j <= L - 2; ++j) {
+    c.a[j] = ar.take<T>(N * net.T[j]);
+    c.s1[j] = ar.take<T>(N * net.T[j]);
+    c.s2[j] = ar.take<T>(N * net.T[j]);
+    c.e[j] = ar.take<T>(N * net.T[j]);
+  }
+  for (int j = 1; j <= L - 1; ++j) c.d[j] = ar.take<T>(N * net.T[j]);
+  c.p = ar.take<T>(N * net.T[L - 1]);
+  c.ysum = ar.take<T>(N);
+  c.z = ar.take<T>(N * maxT);
+}
+template void plan_caches<double>(Arena&, const Net&, int64_t, Caches<double>&);
+template void plan_caches<float>(Arena&, const Net&, int64_t, Caches<float>&);
+
+// Forward pass (Sec. 2, Eq. modelfunc) and per-example back-propagation of
+// dC_n/dz^(l) (the per-example errors delta^(l)).
+template <typename T>
+hess_status forward_backward(const Net& net, const T* omega, const T* X, const T* Y, Caches<T>& c,
+                             cudaStream_t s) {
+  const int L = net.L;
+  const int64_t N = c.N;
+  c.a[0] = X;
+  for (int w = 1; w <= L - 1; ++w) {
+    const int Tin = net.T[w - 1], Tout = net.T[w];
+    Gemm<T> g;
+    g.M = (int)N;
+    g.N = Tout;
+    g.K = Tin;
+    g.A = c.a[w - 1];
+    g.sam = Tin;
+    g.sak = 1;
+    g.B = omega + net.woff[w - 1];
+    g.sbk = 1;
+    g.sbn = Tin;
+    g.C = c.z;
+    g.scm = Tout;
+    g.scn = 1;
+    HM_TRY(gemm(g, s));
+    const T* b = omega + net.boff[w - 1];
+    if (w < L - 1) {
+      bias_act_kernel<T><<<grid1d(N * Tout), 256, 0, s>>>(c.z, b, N, Tout, net.act[w - 1],
+                                                          const_cast<T*>(c.a[w]), c.s1[w], c.s2[w]);
+      HM_LAUNCHED();
+    } else {
+      softmax_kernel<T><<<(unsigned)cdiv(N, 128), 128, 0, s>>>(c.z, b, Y, N, Tout, c.p, c.d[w],
+                                                                c.ysum);
+      HM_LAUNCHED();
+    }
+  }
+  for (int j = L - 2; j >= 1; --j) {
+    // e_j = delta_{j+1} W^(j+1)   (W^(j+1) is T[j+1] x T[j])
+    Gemm<T> g;
+    g.M = (int)N;
+    g.N = net.T[j];
+    g.K = net.T[j + 1];
+    g.A = c.d[j + 1];
+    g.sam = net.T[j + 1];
+    g.sak = 1;
+    g.B = omega + net.woff[j];
+    g.sbk = net.T[j];
+    g.sbn = 1;
+    g.C = c.e[j];
+    g.scm = net.T[j];
+    g.scn = 1;
+    HM_TRY(gemm(g, s));
+    mul_kernel<T><<<grid1d(N * net.T[j]), 256, 0, s>>>(c.s1[j], c.e[j], c.d[j], N * net.T[j]);
+    HM_LAUNCHED();
+  }
+  return HESS_OK;
+}
+template hess_status forward_backward<double>(const Net&, const double*, const double*,
+                                              const double*, Caches<double>&, cudaStream_t);
+template hess_status forward_backward<float>(const Net&, const float*, const float*, const float*,
+                                             Caches<float>&, cudaStream_t);
+
+// ================================================== per-example gradients
+// G[n, woff + i*Tin + k] = delta[n,i] a[n,k];  G[n, boff + i] = delta[n,i].
+// One block row per example; consecutive threads write consecutive columns.
+template <typename T>
+__global__ void write_grads_kernel(const T* D, const T* A, int Tin, int Tout, T* G, int64_t ldg,
+                                   int64_t woff, int64_t boff) {
+  const int64_t n = blockIdx.x;
+  const int64_t nW = (int64_t)Tin * Tout;
+  const T* d = D + n * Tout;
+  const T* a = A + n * Tin;
+  T* g = G + n * ldg;
+  const int64_t per_block = 2048;
+  int64_t c0 = (int64_t)blockIdx.y * per_block;
+#pragma unroll 4
+  for (int it = 0; it < per_block / 256; ++it) {
+    int64_t c = c0 + threadIdx.x + it * 256;
+    if (c < nW) {
+      int i = (int)(c / Tin);
+      int k = (int)(c - (int64_t)i * Tin);
+      g[woff + c] = d[i] * a[k];
+    } else if (c < nW + Tout) {
+      g[boff + (c - nW)] = d[c - nW];
+    }
+  }
+}
+
+template <typename T>
+hess_status write_grads(const Net& net, const Caches<T>& c, T* G, int64_t ldg, cudaStream_t s) {
+  for (int w = 1; w <= net.L - 1; ++w) {
+    const int Tin = net.T[w - 1], Tout = net.T[w];
+    int64_t cols = (int64_t)Tin * Tout + Tout;
+    int64_t gy = cdiv(cols, 2048);
+    int64_t n0 = 0;
+    while (n0 < c.N) {
+      int64_t nb = c.N - n0 < 2147483647 ? c.N - n0 : 2147483647;
+      write_grads_kernel<T><<<dim3((unsigned)nb, (unsigned)gy), 256, 0, s>>>(
+          c.d[w] + n0 * Tout, c.a[w - 1] + n0 * Tin, Tin, Tout, G + n0 * ldg, ldg, net.woff[w - 1],
+          net.boff[w - 1]);
+      HM_LAUNCHED();
+      n0 += nb;
+    }
+  }
+  return HESS_OK;
+}
+template hess_status write_grads<double>(const Net&, const Caches<double>&, double*, int64_t,
+                                         cudaStream_t);
+template hess_status write_grads<float>(const Net&, const Caches<float>&, float*, int64_t,
+                                        cudaStream_t);
+
+// ======================================================= mirror / scatter
+// Copy the strict upper triangle of an n x n matrix onto the lower one,
+// through a 32 x 32 shared-memory tile so both sides are coalesced.
+template <typename T>
+__global__ void mirror_upper_kernel(T* C, int64_t n, int64_t ldc) {
+  __shared__ T tile[32][33];
+  int64_t ti = blockIdx.y, tj = blockIdx.x;
+  if (ti > tj) return;
+  int64_t r0 = ti * 32, c0 = tj * 32;
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    int64_t r = r0 + y, cc = c0 + threadIdx.x;
+    if (r < n && cc < n) tile[y][threadIdx.x] = C[r * ldc + cc];
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    int64_t r = c0 + y, cc = r0 + threadIdx.x;  // destination (r, cc) = source (cc, r)
+    if (r < n && cc < n && r > cc) C[r * ldc + cc] = tile[threadIdx.x][y];
+  }
+}
+template <typename T>
+hess_status mirror_upper(T* C, int64_t n, int64_t ldc, cudaStream_t s) {
+  int64_t nt = cdiv(n, 32);
+  if (nt > 65535) return set_error(HESS_ERR_INVALID_ARG, "mirror: n too large");
+  mirror_upper_kernel<T><<<dim3((unsigned)nt, (unsigned)nt), dim3(32, 8), 0, s>>>(C, n, ldc);
+  HM_LAUNCHED();
+  return HESS_OK;
+}
+template hess_status mirror_upper<double>(double*, int64_t, int64_t, cudaStream_t);
+template hess_status mirror_upper<float>(float*, int64_t, int64_t, cudaStream_t);
+
+// tmp is B x cols (row d holds H[d0 + d, c0 .. c0 + cols)).  Direct entries
+// with column >= d0 go to row d0 + d; entries with column >= d0 + B are also
+// written to row c (the mirror image), coalesced through a shared tile.
+template <typename T>
+__global__ void scatter_sym_kernel(const T* tmp, int B, int64_t cols, int64_t c0, int64_t d0, T* H,
+                                   int64_t P) {
+  __shared__ T tile[32][33];
+  int64_t dt = (int64_t)blockIdx.y * 32, ct = (int64_t)blockIdx.x * 32;
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    int64_t d = dt + y, cl = ct + threadIdx.x;
+    T v = T(0);
+    if (d < B && cl < cols) {
+      v = tmp[d * cols + cl];
+      int64_t c = c0 + cl;
+      if (c >= d0) H[(d0 + d) * P + c] = v;
+    }
+    tile[y][threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    int64_t cl = ct + y, d = dt + threadIdx.x;
+    if (d < B && cl < cols) {
+      int64_t c = c0 + cl;
+      if (c >= d0 + B) H[c * P + d0 + d] = tile[threadIdx.x][y];
+    }
+  }
+}
+template <typename T>
+hess_status scatter_sym(const T* tmp, int B, int64_t cols, int64_t c0, int64_t d0, T* H, int64_t P,
+                        cudaStream_t s) {
+  int64_t gx = cdiv(cols, 32), gy = cdiv(B, 32);
+  if (gy > 65535) return set_error(HESS_ERR_INVALID_ARG, "scatter: block too large");
+  scatter_sym_kernel<T><<<dim3((unsigned)gx, (unsigned)gy), dim3(32, 8), 0, s>>>(tmp, B, cols, c0,
+                                                                                d0, H, P);
+  HM_LAUNCHED();
+  return HESS_OK;
+}
+template hess_status scatter_sym<double>(const double*, int, int64_t, int64_t, int64_t, double*,
+                                         int64_t, cudaStream_t);
+template hess_status scatter_sym<float>(const float*, int, int64_t, int64_t, int64_t, float*,
+                                        int64_t, cudaStream_t);
+
+// ============================================================ R-operator
+// Layout of every R-quantity: [n][d][t] (example, direction, unit).
+//
+// Seed: a unit direction inside weight layer jm only moves z at position jm:
+//   direction W^(jm)_{pq}:  R{z}[n, d, t] = [t == p] a^(jm-1)[n, q]
+//   direction b^(jm+1)_p:   R{z}[n, d, t] = [t == p]
+template <typename T>
+__global__ void rop_seed_kernel(T* rz, int B, int64_t N, int Tm, int Tin, const T* aprev,
+                                int64_t loc0) {
+  const int64_t n_el = N * B * Tm;
+  const int64_t nW = (int64_t)Tm * Tin;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n_el;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int t = (int)(idx % Tm);
+    int64_t r = idx / Tm;
+    int d = (int)(r % B);
+    int64_t n = r / B;
+    int64_t loc = loc0 + d;
+    T v = T(0);
+    if (loc < nW) {
+      int p = (int)(loc / Tin), q = (int)(loc % Tin);
+      if (t == p) v = aprev[n * Tin + q];
+    } else if (t == (int)(loc - nW)) {
+      v = T(1);
+    }
+    rz[idx] = v;
+  }
+}
+
+// R{a} = sigma'(z) R{z}
+template <typename T>
+__global__ void rop_act_kernel(const T* rz, const T* s1, T* ra, int B, int64_t N, int Tn) {
+  const int64_t n_el = N * B * Tn;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n_el;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int t = (int)(idx % Tn);
+    int64_t n = idx / ((int64_t)Tn * B);
+    ra[idx] = s1[n * Tn + t] * rz[idx];
+  }
+}
+
+// Softmax output: R{delta^(L)} = (diag p - p p^T) R{z^(L)} * sum(y).
+template <typename T>
+__global__ void rop_softmax_kernel(const T* rz, const T* p, const T* ysum, T* rd, int B, int64_t N,
+                                   int TL) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= N * B) return;
+  int64_t n = r / B;
+  const T* z = rz + r * TL;
+  const T* pn = p + n * TL;
+  T sdot = T(0);
+  for (int i = 0; i < TL; ++i) sdot += pn[i] * z[i];
+  T ys = ysum[n];
+  for (int i = 0; i < TL; ++i) rd[r * TL + i] = pn[i] * (z[i] - sdot) * ys;
+}
+
+// R{delta^(l-1)} = sigma''(z) R{z} e + sigma'(z) (W^T R{delta^(l)})
+template <typename T>
+__global__ void rop_back_kernel(const T* rz, const T* tmp, const T* s1, const T* s2, const T* e,
+                                T* rd, int B, int64_t N, int Tn) {
+  const int64_t n_el = N * B * Tn;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n_el;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int t = (int)(idx % Tn);
+    int64_t n = idx / ((int64_t)Tn * B);
+    int64_t q = n * Tn + t;
+    rd[idx] = s2[q] * rz[idx] * e[q] + s1[q] * tmp[idx];
+  }
+}
+
+template <typename T>
+void plan_rop(Arena& ar, const Net& net, int64_t N, int jm, int B, RopBufs<T>& r) {
+  const int L = net.L;
+  r.B = B;
+  r.rz.assign(L, nullptr);
+  r.ra.assign(L, nullptr);
+  r.rd.assign(L, nullptr);
+  int maxT = 0;
+  for (int j = jm; j <= L - 1; ++j) {
+    r.rz[j] = ar.take<T>(N * B * net.T[j]);
+    r.rd[j] = ar.take<T>(N * B * net.T[j]);
+    if (j <= L - 2) r.ra[j] = ar.take<T>(N * B * net.T[j]);
+    maxT = net.T[j] > maxT ? net.T[j] : maxT;
+  }
+  r.tmp = ar.take<T>(N * B * maxT);
+}
+template void plan_rop<double>(Arena&, const Net&, int64_t, int, int, RopBufs<double>&);
+template void plan_rop<float>(Arena&, const Net&, int64_t, int, int, RopBufs<float>&);
+
+// Forward-over-reverse R-operator for the unit directions d0..d0+B-1 (all in
+// weight layer jm).  Only positions >= jm are touched: below the direction's
+// layer every R-quantity is zero, and the Hessian columns needed for the upper
+// triangle all lie in layers >= jm.
+template <typename T>
+hess_status rop_block(const Net& net, const T* omega, const Caches<T>& c, int jm, int64_t d0, int B,
+                      RopBufs<T>& r, cudaStream_t s) {
+  const int L = net.L;
+  const int64_t N = c.N;
+  {
+    const int Tm = net.T[jm], Tin = net.T[jm - 1];
+    rop_seed_kernel<T><<<grid1d(N * B * Tm), 256, 0, s>>>(r.rz[jm], B, N, Tm, Tin, c.a[jm - 1],
+                                                         d0 - net.woff[jm - 1]);
+    HM_LAUNCHED();
+  }
+  for (int j = jm; j <= L - 2; ++j) {
+    const int Tj = net.T[j], Tn = net.T[j + 1];
+    rop_act_kernel<T><<<grid1d(N * B * Tj), 256, 0, s>>>(r.rz[j], c.s1[j], r.ra[j], B, N, Tj);
+    HM_LAUNCHED();
+    // R{z}_{j+1} = R{a}_j W^(j+1)^T  (W^(j+1) is Tn x Tj); V^(j+1) = 0 here
+    Gemm<T> g;
+    g.M = (int)(N * B);
+    g.N = Tn;
+    g.K = Tj;
+    g.A = r.ra[j];
+    g.sam = Tj;
+    g.sak = 1;
+    g.B = omega + net.woff[j];
+    g.sbk = 1;
+    g.sbn = Tj;
+    g.C = r.rz[j + 1];
+    g.scm = Tn;
+    g.scn = 1;
+    HM_TRY(gemm(g, s));
+  }
+  {
+    const int TL = net.T[L - 1];
+    rop_softmax_kernel<T><<<(unsigned)cdiv(N * B, 128), 128, 0, s>>>(r.rz[L - 1], c.p, c.ysum,
+                                                                      r.rd[L - 1], B, N, TL);
+    HM_LAUNCHED();
+  }
+  for (int j = L - 2; j >= jm; --j) {
+    const int Tj = net.T[j], Tn = net.T[j + 1];
+    // tmp = R{delta}_{j+1} W^(j+1)
+    Gemm<T> g;
+    g.M = (int)(N * B);
+    g.N = Tj;
+    g.K = Tn;
+    g.A = r.rd[j + 1];
+    g.sam = Tn;
+    g.sak = 1;
+    g.B = omega + net.woff[j];
+    g.sbk = Tj;
+    g.sbn = 1;
+    g.C = r.tmp;
+    g.scm = Tj;
+    g.scn = 1;
+    HM_TRY(gemm(g, s));
+    rop_back_kernel<T><<<grid1d(N * B * Tj), 256, 0, s>>>(r.rz[j], r.tmp, c.s1[j], c.s2[j], c.e[j],
+                                                         r.rd[j], B, N, Tj);
+    HM_LAUNCHED();
+  }
+  return HESS_OK;
+}
+template hess_status rop_block<double>(const Net&, const double*, const Caches<double>&, int,
+                                       int64_t, int, RopBufs<double>&, cudaStream_t);
+template hess_status rop_block<float>(const Net&, const float*, const Caches<float>&, int, int64_t,
+                                      int, RopBufs<float>&, cudaStream_t);
+
+// Hessian rows d0..d0+B-1 against the columns of weight layer jl:
+//   H[d, W(i,k)] = (1/N) sum_n R{delta}[n,d,i] a[n,k] + delta[n,i] R{a}[n,d,k]
+//   H[d, b(i)]   = (1/N) sum_n R{delta}[n,d,i]
+// (the R-operator applied to dC_n/dW = delta a^T and dC_n/db = delta).
+template <typename T>
+hess_status contract_layer(const Net& net, const Caches<T>& c, const RopBufs<T>& r, int jm, int jl,
+                           int64_t d0, T* tmp, const T* ones, T* H, cudaStream_t s) {
+  const int64_t N = c.N;
+  const int B = r.B;
+  const int Tin = net.T[jl - 1], Tout = net.T[jl];
+  const int64_t nW = (int64_t)Tin * Tout;
+  T* tmpW = tmp;
+  T* tmpB = tmp + (int64_t)B * nW;
+  const T invN = T(1) / T(N);
+  {
+    // rows (d, i), columns k
+    Gemm<T> g;
+    g.M = B * Tout;
+    g.N = Tin;
+    g.K = (int)N;
+    g.alpha = invN;
+    g.A = r.rd[jl];
+    g.sam = 1;
+    g.sak = (int64_t)B * Tout;
+    g.B = c.a[jl - 1];
+    g.sbk = Tin;
+    g.sbn = 1;
+    g.C = tmpW;
+    g.scm = Tin;
+    g.scn = 1;
+    HM_TRY(gemm(g, s));
+  }
+  if (jl > jm) {
+    // batched over d: rows k, columns i
+    Gemm<T> g;
+    g.M = Tin;
+    g.N = Tout;
+    g.K = (int)N;
+    g.alpha = invN;
+    g.beta = T(1);
+    g.A = r.ra[jl - 1];
+    g.sam = 1;
+    g.sak = (int64_t)B * Tin;
+    g.bsa = Tin;
+    g.B = c.d[jl];
+    g.sbk = Tout;
+    g.sbn = 1;
+    g.bsb = 0;
+    g.C = tmpW;
+    g.scm = 1;
+    g.scn = Tin;
+    g.bsc = nW;
+    g.batch = B;
+    HM_TRY(gemm(g, s));
+  }
+  {
+    Gemm<T> g;
+    g.M = B * Tout;
+    g.N = 1;
+    g.K = (int)N;
+    g.alpha = invN;
+    g.A = r.rd[jl];
+    g.sam = 1;
+    g.sak = (int64_t)B * Tout;
+    g.B = ones;
+    g.sbk = 1;
+    g.sbn = 0;
+    g.C = tmpB;
+    g.scm = 1;
+    g.scn = 0;
+    HM_TRY(gemm(g, s));
+  }
+  HM_TRY(scatter_sym(tmpW, B, nW, net.woff[jl - 1], d0, H, net.P, s));
+  HM_TRY(scatter_sym(tmpB, B, (int64_t)Tout, net.boff[jl - 1], d0, H, net.P, s));
+  return HESS_OK;
+}
+template hess_status contract_layer<double>(const Net&, const Caches<double>&,
+                                            const RopBufs<double>&, int, int, int64_t, double*,
+                                            const double*, double*, cudaStream_t);
+template hess_status contract_layer<float>(const Net&, const Caches<float>&, const RopBufs<float>&,
+                                           int, int, int64_t, float*, const float*, float*,
+                                           cudaStream_t);
+
+}  // namespace hm

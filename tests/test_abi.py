@@ -1,0 +1,79 @@
+"""The C-ABI library: it builds, loads without a GPU, exports every symbol the
+header declares, and its host-only helper and argument checks behave."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import mlp as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hessmlp.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1905_05559_gb300 import build, _lib
+    build.build()
+    return _lib.load()
+
+
+def header_symbols():
+    txt = open(HEADER).read()
+    return re.findall(r"HESS_API\s+[\w\s\*]+?\b(\w+)\s*\(", txt)
+
+
+def test_header_declares_the_boundary():
+    syms = set(header_symbols())
+    assert {"hess_mlp_create", "per_example_grads", "opg", "exact_hessian", "opg_topk_eig"} <= syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_1905_05559_gb300 import _lib
+    for name in header_symbols():
+        assert hasattr(lib, name), name
+    assert set(header_symbols()) == set(_lib.EXPORTS)
+
+
+def test_param_permutation_matches_oracle(lib):
+    from paper_1905_05559_gb300 import param_permutation
+    for widths in ([4, 5, 3], [7, 2], [3, 6, 5, 4]):
+        assert np.array_equal(param_permutation(widths), O.param_permutation(widths))
+
+
+def test_create_rejects_bad_descriptions_before_touching_cuda(lib):
+    from paper_1905_05559_gb300 import _lib
+    h = ctypes.c_void_p()
+    omega = np.zeros(43)
+    w = (ctypes.c_int * 3)(4, 5, 3)
+    bad_act = (ctypes.c_int * 1)(7)
+    ok_act = (ctypes.c_int * 1)(0)
+    cases = [
+        (None, omega),
+        (_lib.HessDesc(1, w, ok_act), omega),
+        (_lib.HessDesc(3, w, bad_act), omega),
+        (_lib.HessDesc(3, (ctypes.c_int * 3)(4, 0, 3), ok_act), omega),
+        (_lib.HessDesc(3, (ctypes.c_int * 3)(4, 5, 1), ok_act), omega),
+        (_lib.HessDesc(3, w, ok_act), None),
+    ]
+    for desc, om in cases:
+        st = lib.hess_mlp_create(ctypes.byref(desc) if desc is not None else None,
+                                 om.ctypes.data if om is not None else None, None, ctypes.byref(h))
+        assert st == _lib.HESS_ERR_INVALID_ARG
+        assert lib.hess_last_error()
+
+
+def test_calls_reject_null_handle_and_bad_sizes(lib):
+    from paper_1905_05559_gb300 import _lib
+    x = np.zeros(8)
+    assert lib.per_example_grads(None, x.ctypes.data, x.ctypes.data, 1, 0, x.ctypes.data) == \
+        _lib.HESS_ERR_INVALID_ARG
+    assert lib.opg(None, x.ctypes.data, x.ctypes.data, 1, 0, x.ctypes.data) == _lib.HESS_ERR_INVALID_ARG
+    assert lib.exact_hessian(None, None, None, 1, 0, None) == _lib.HESS_ERR_INVALID_ARG
+    assert lib.opg_topk_eig(None, None, None, 1, 1, 0, None, None) == _lib.HESS_ERR_INVALID_ARG
+    assert lib.hess_mlp_num_params(None) == -1
+    assert lib.hess_mlp_destroy(None) == _lib.HESS_OK
+    assert lib.hess_param_permutation(1, None, None) == _lib.HESS_ERR_INVALID_ARG
