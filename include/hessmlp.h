@@ -168,7 +168,8 @@ typedef enum {
   HESS_K_GRADS = 2,     /* per-example gradient rows (HBM write) */
   HESS_K_ROP = 3,       /* R-operator over a block of directions */
   HESS_K_EIG = 4,       /* Gram matrix, Lanczos and back-projection */
-  HESS_K_COUNT = 5
+  HESS_K_HREST = 5,     /* Hessian columns outside the tensor-core blocks */
+  HESS_K_COUNT = 6
 } hess_kernel_class;
 
 typedef struct {

@@ -35,7 +35,7 @@ EXPORTS = (
     "hess_launch_count",
 )
 
-KERNEL_CLASS = {"syrk": 0, "hcontract": 1, "grads": 2, "rop": 3, "eig": 4}
+KERNEL_CLASS = {"syrk": 0, "hcontract": 1, "grads": 2, "rop": 3, "eig": 4, "hrest": 5}
 
 
 class KernelStats(ctypes.Structure):
