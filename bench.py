@@ -43,11 +43,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16", "bf16x3"])
+    ap.add_argument("--precision", default="bf16x3", choices=["fp64", "fp32", "bf16", "bf16x3"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--only", default=None, choices=["opg", "hessian", "eig"],
+                    help="run one call of the step (for profiling); the line is then partial")
     ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -239,9 +241,12 @@ def main():
 
     def step(prec, io):
         X, Y, H, OPG, ev, Q = io
-        net.opg(X, Y, prec, out=OPG)
-        net.exact_hessian(X, Y, prec, out=H)
-        net.opg_topk_eig(X, Y, K_EIG, prec, evals=ev, evecs=Q)
+        if args.only in (None, "opg"):
+            net.opg(X, Y, prec, out=OPG)
+        if args.only in (None, "hessian"):
+            net.exact_hessian(X, Y, prec, out=H)
+        if args.only in (None, "eig"):
+            net.opg_topk_eig(X, Y, K_EIG, prec, evals=ev, evecs=Q)
 
     def timed(prec, steps, warmup, sampler=None):
         io = make_io(prec)
@@ -332,7 +337,11 @@ def main():
 
     peaks, peak_src = measured_peaks()
     # dominant kernel class of the step
-    dom = max(kern, key=lambda k: kern[k]["ms"])
+    # the roofline is taken for the most expensive class whose algorithmic
+    # work is known (a contraction's flops or a store's bytes)
+    overall = max(kern, key=lambda k: kern[k]["ms"])
+    known = [k for k in kern if kern[k]["flops"] > 0 or kern[k]["bytes"] > 0]
+    dom = max(known, key=lambda k: kern[k]["ms"]) if known else overall
     dk = kern[dom]
     if args.precision in ("bf16", "bf16x3") and dom in ("syrk", "hcontract"):
         mult = 3.0 if args.precision == "bf16x3" else 1.0
@@ -350,7 +359,8 @@ def main():
         achieved = dk["bytes"] / (dk["ms"] * 1e-3) / 1e9 if dk["bytes"] else None
         roof = {"bound": "hbm", "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "peak_source": f"{peak_src} copy bandwidth"}
-    roof.update({"kernel_class": dom, "achieved": achieved,
+    roof.update({"kernel_class": dom, "step_share": dk["ms"] / max(sum(v["ms"] for v in kern.values()), 1e-9),
+                 "largest_class": overall, "achieved": achieved,
                  "frac": (achieved / roof["peak"]) if (achieved and roof.get("peak")) else None,
                  "traffic": None,
                  "launches_per_step": dk["launches"] / max(args.steps, 1),
@@ -367,7 +377,8 @@ def main():
                                    f"Hessian + top-{K_EIG} OPG eig per step",
                        "precision": args.precision, "P": P, "N": N, "k": K_EIG,
                        "l2": "flushed between steps (256 MiB write outside the timed events)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}",
+                       **({"only": args.only} if args.only else {})},
             "roofline": roof,
             "cpu_baseline": ({"value": cpu["value"], "unit": UNIT, "cores": cpu["cores"],
                               "kind": "oracle", "sample": cpu["sample"]}

@@ -192,7 +192,7 @@ __device__ __forceinline__ void row_map(const Params& p, int64_t m, int64_t& oro
 }
 
 __global__ void __launch_bounds__(THREADS, 1)
-    gemm_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
+    umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                 const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
                 const Params p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -568,7 +568,7 @@ hess_status launch_tc(hess_mlp* h, const TcOperands& op, tc::Params p, int BN, c
   HM_TRY(make_map(&mb, op.Bhi, op.ld, op.brows, BN));
   HM_TRY(make_map(&mbl, op.Blo, op.ld, op.brows, BN));
   if (!g_attr_set) {
-    HM_CUDA(cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    HM_CUDA(cudaFuncSetAttribute(umma_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     g_attr_set = true;
   }
   p.BN = BN;
@@ -576,7 +576,7 @@ hess_status launch_tc(hess_mlp* h, const TcOperands& op, tc::Params p, int BN, c
   p.idesc = make_idesc(BN);
   int grid = p.ntiles < h->sm_count ? p.ntiles : h->sm_count;
   if (grid < 1) return HESS_OK;
-  gemm_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(ma, mal, mb, mbl, p);
+  umma_gemm_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(ma, mal, mb, mbl, p);
   HM_LAUNCHED();
   return HESS_OK;
 }
