@@ -186,11 +186,13 @@ static hess_status run_grads(hess_mlp* h, const void* X, const void* Y, int64_t 
   HM_TRY(classify(h, Y, "Y", &y.on_dev));
   HM_TRY(classify(h, Gout, "G", &g_dev));
   const int64_t T1 = net.T[0], TL = net.T[net.L - 1];
+  char* split = nullptr;
   auto plan = [&](Arena& ar, Caches<T>& c, T*& G) {
     plan_in(ar, x, N * T1);
     plan_in(ar, y, N * TL);
     plan_caches(ar, net, N, c);
     G = g_dev ? (T*)Gout : ar.take<T>(N * net.P);
+    split = ar.take<char>(kSplitBytes);
   };
   Arena ar;
   Caches<T> c;
@@ -199,6 +201,7 @@ static hess_status run_grads(hess_mlp* h, const void* X, const void* Y, int64_t 
   HM_TRY(ensure_ws(h, ar.off));
   ar = Arena{h->ws, 0};
   plan(ar, c, G);
+  SplitGuard sg(split, kSplitBytes, h->sm_count);
   cudaStream_t s = h->stream;
   HM_TRY(upload(x, N * T1, s));
   HM_TRY(upload(y, N * TL, s));
@@ -226,12 +229,14 @@ static hess_status run_opg(hess_mlp* h, const void* X, const void* Y, int64_t N,
   HM_TRY(classify(h, Y, "Y", &y.on_dev));
   HM_TRY(classify(h, Oout, "OPG", &o_dev));
   const int64_t T1 = net.T[0], TL = net.T[net.L - 1], P = net.P;
+  char* split = nullptr;
   auto plan = [&](Arena& ar, Caches<T>& c, T*& G, T*& O) {
     plan_in(ar, x, N * T1);
     plan_in(ar, y, N * TL);
     plan_caches(ar, net, N, c);
     G = ar.take<T>(N * P);
     O = o_dev ? (T*)Oout : ar.take<T>(P * P);
+    split = ar.take<char>(kSplitBytes);
   };
   Arena ar;
   Caches<T> c;
@@ -240,6 +245,7 @@ static hess_status run_opg(hess_mlp* h, const void* X, const void* Y, int64_t N,
   HM_TRY(ensure_ws(h, ar.off));
   ar = Arena{h->ws, 0};
   plan(ar, c, G, O);
+  SplitGuard sg(split, kSplitBytes, h->sm_count);
   cudaStream_t s = h->stream;
   HM_TRY(upload(x, N * T1, s));
   HM_TRY(upload(y, N * TL, s));
@@ -305,27 +311,28 @@ static hess_status run_hessian(hess_mlp* h, const void* X, const void* Y, int64_
     int64_t pl = (int64_t)net.T[w - 1] * net.T[w] + net.T[w];
     maxPl = pl > maxPl ? pl : maxPl;
   }
-  auto plan = [&](Arena& ar, Caches<T>& c, RopBufs<T>& r, T*& tmp, T*& ones, T*& O) {
+  char* split = nullptr;
+  auto plan = [&](Arena& ar, Caches<T>& c, RopBufs<T>& r, T*& tmp, T*& O) {
     plan_in(ar, x, N * T1);
     plan_in(ar, y, N * TL);
     plan_caches(ar, net, N, c);
     plan_rop(ar, net, N, 1, Bmax, r);
     tmp = ar.take<T>((int64_t)Bmax * maxPl);
-    ones = ar.take<T>(N);
     O = o_dev ? (T*)Hout : ar.take<T>(P * P);
+    split = ar.take<char>(kSplitBytes);
   };
   Arena ar;
   Caches<T> c;
   RopBufs<T> r;
-  T *tmp = nullptr, *ones = nullptr, *O = nullptr;
-  plan(ar, c, r, tmp, ones, O);
+  T *tmp = nullptr, *O = nullptr;
+  plan(ar, c, r, tmp, O);
   HM_TRY(ensure_ws(h, ar.off));
   ar = Arena{h->ws, 0};
-  plan(ar, c, r, tmp, ones, O);
+  plan(ar, c, r, tmp, O);
+  SplitGuard sg(split, kSplitBytes, h->sm_count);
   cudaStream_t s = h->stream;
   HM_TRY(upload(x, N * T1, s));
   HM_TRY(upload(y, N * TL, s));
-  HM_TRY(fill(ones, N, T(1), s));
   HM_TRY(forward_backward(net, omega, x.dev, y.dev, c, s));
   for (int jm = 1; jm < net.L; ++jm) {
     const int64_t lo = net.woff[jm - 1], hi = net.boff[jm - 1] + net.T[jm];
@@ -340,7 +347,7 @@ static hess_status run_hessian(hess_mlp* h, const void* X, const void* Y, int64_
       for (int jl = jm; jl < net.L; ++jl) {
         // one product over N per computed Hessian entry of this row block
         Tick t(h, HESS_K_HCONTRACT, hcontract_flops(net, N, jm, jl, d0, B), 0.0);
-        HM_TRY(contract_layer(net, c, rb, jm, jl, d0, tmp, ones, O, s));
+        HM_TRY(contract_layer(net, c, rb, jm, jl, d0, tmp, O, s));
       }
     }
   }
@@ -360,6 +367,7 @@ static hess_status run_eig(hess_mlp* h, const void* X, const void* Y, int64_t N,
   HM_TRY(classify(h, Y, "Y", &y_dev));
   HM_TRY(classify(h, evals, "evals", &ev_dev));
   HM_TRY(classify(h, evecs, "evecs", &q_dev));
+  char* split = nullptr;
   auto plan = [&](Arena& ar, void*& xs, void*& ys, double*& xd, double*& yd, Caches<double>& c,
                   double*& evd, double*& eqd) {
     xs = (x_dev ? nullptr : ar.take<char>(N * T1 * es));
@@ -369,6 +377,7 @@ static hess_status run_eig(hess_mlp* h, const void* X, const void* Y, int64_t N,
     plan_caches(ar, net, N, c);
     evd = ev_dev ? evals : ar.take<double>(k);
     eqd = q_dev ? evecs : ar.take<double>(P * (int64_t)k);
+    split = ar.take<char>(kSplitBytes);
   };
   Arena ar;
   void *xs, *ys;
@@ -380,6 +389,7 @@ static hess_status run_eig(hess_mlp* h, const void* X, const void* Y, int64_t N,
   HM_TRY(ensure_ws(h, ar.off));
   ar = Arena{h->ws, 0};
   plan(ar, xs, ys, xd, yd, c, evd, eqd);
+  SplitGuard sg(split, kSplitBytes, h->sm_count);
   cudaStream_t s = h->stream;
   const void* xsrc = X;
   const void* ysrc = Y;

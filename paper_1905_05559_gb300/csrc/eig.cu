@@ -59,87 +59,6 @@ __global__ void gram_acc_kernel(double* M, const double* DD, const double* AA, i
     M[i] += DD[i] * (AA[i] + 1.0) * invN;
 }
 
-// ---------------------------------------------------------------- BLAS-2
-// y[r] = sum_c A[r*lda + c] x[c]; one warp per row.  cond: skip unless *cond.
-__global__ void gemv_rows_kernel(const double* A, int64_t lda, int rows, int64_t cols,
-                                 const double* x, double* y, const int* cond) {
-  if (cond && !*cond) return;
-  int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (r >= rows) return;
-  const double* a = A + (int64_t)r * lda;
-  double s = 0.0;
-  for (int64_t c = threadIdx.x & 31; c < cols; c += 32) s = fma(a[c], x[c], s);
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) y[r] = s;
-}
-
-// w[n] -= sum_i Q[i*ldq + n] h[i]
-__global__ void gemv_sub_kernel(const double* Q, int64_t ldq, int nvec, int64_t N, const double* h,
-                                double* w, const int* cond) {
-  if (cond && !*cond) return;
-  int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (n >= N) return;
-  double s = 0.0;
-  for (int i = 0; i < nvec; ++i) s = fma(Q[(int64_t)i * ldq + n], h[i], s);
-  w[n] -= s;
-}
-
-// ---------------------------------------------------------------- Lanczos
-// After the two reorthogonalisation passes: alpha_j = h1[j] + h2[j],
-// beta_j = ||w||; q_{j+1} = w / beta_j, or on breakdown a random vector that
-// the gated kernels then orthonormalise (flag = 1) with beta_j = 0.
-__global__ void lanczos_norm_kernel(const double* w, double* qn, int64_t N, int j,
-                                    const double* h1, const double* h2, double* alpha,
-                                    double* beta, int* flag, uint64_t key) {
-  __shared__ double sh[32];
-  double s = 0.0;
-  for (int64_t n = threadIdx.x; n < N; n += blockDim.x) s = fma(w[n], w[n], s);
-  s = block_sum(s, sh);
-  double nrm = sqrt(s);
-  double a = h1[j] + h2[j];
-  // scale of T so far
-  double scale = fabs(a);
-  for (int i = threadIdx.x; i < j; i += blockDim.x) scale = fmax(scale, fmax(fabs(alpha[i]), beta[i]));
-  __shared__ double shm[32];
-  {
-    double v = scale;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double m = 0.0;
-      for (int i = 0; i < (int)((blockDim.x + 31) >> 5); ++i) m = fmax(m, shm[i]);
-      shm[0] = m;
-    }
-    __syncthreads();
-    scale = shm[0];
-  }
-  bool breakdown = !(nrm > 1e-12 * scale) || scale == 0.0;
-  if (!breakdown) {
-    double inv = 1.0 / nrm;
-    for (int64_t n = threadIdx.x; n < N; n += blockDim.x) qn[n] = w[n] * inv;
-  } else {
-    for (int64_t n = threadIdx.x; n < N; n += blockDim.x) qn[n] = rnd_sym(key, (uint64_t)j * 0x100000000ull + n);
-  }
-  if (threadIdx.x == 0) {
-    alpha[j] = a;
-    beta[j] = breakdown ? 0.0 : nrm;
-    *flag = breakdown ? 1 : 0;
-  }
-}
-
-// gated: q /= ||q||
-__global__ void normalize_gated_kernel(double* q, int64_t N, const int* cond) {
-  if (cond && !*cond) return;
-  __shared__ double sh[32];
-  double s = 0.0;
-  for (int64_t n = threadIdx.x; n < N; n += blockDim.x) s = fma(q[n], q[n], s);
-  s = block_sum(s, sh);
-  double inv = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
-  for (int64_t n = threadIdx.x; n < N; n += blockDim.x) q[n] *= inv;
-}
-
 __global__ void init_start_kernel(double* q, int64_t N, uint64_t key) {
   __shared__ double sh[32];
   double s = 0.0;
@@ -151,6 +70,183 @@ __global__ void init_start_kernel(double* q, int64_t N, uint64_t key) {
   s = block_sum(s, sh);
   double inv = 1.0 / sqrt(s);
   for (int64_t n = threadIdx.x; n < N; n += blockDim.x) q[n] *= inv;
+}
+
+// ------------------------------------------------ cooperative Lanczos
+// All Lanczos steps of one extension run in a single cooperative launch (all
+// blocks co-resident); the phases of a step are separated by a grid barrier
+// whose waits are bounded: on timeout the kernel raises *err and returns.
+struct LzArgs {
+  const double* M;
+  int64_t N;
+  double* Q;  // Lanczos vectors, rows of length N
+  double* w;
+  double* h1;
+  double* h2;
+  double* alpha;
+  double* beta;
+  double* part;  // one partial sum per block
+  unsigned* bar_count;
+  unsigned* bar_gen;
+  int* err;
+  int m0, m1, mcap;
+  uint64_t key;
+};
+
+constexpr long long BAR_TIMEOUT = 4000000000ll;
+
+__device__ bool grid_barrier(const LzArgs& a) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* gen = a.bar_gen;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(a.bar_count, 1u) == gridDim.x - 1) {
+      *a.bar_count = 0;
+      __threadfence();
+      atomicAdd(a.bar_gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g) {
+        if (clock64() - t0 > BAR_TIMEOUT || *(volatile int*)a.err) {
+          atomicExch(a.err, 1);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// h[i] = Q_i . v for i <= j (one warp per dot product)
+__device__ void dots_against_q(const LzArgs& a, int j, const double* v, double* h) {
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  for (int i = gw; i <= j; i += nw) {
+    const double* qi = a.Q + (int64_t)i * a.N;
+    double s = 0.0;
+    for (int64_t n = lane; n < a.N; n += 32) s = fma(qi[n], v[n], s);
+    s = warp_sum(s);
+    if (lane == 0) h[i] = s;
+  }
+}
+// v[n] -= sum_{i <= j} Q_i[n] h[i]
+__device__ void sub_q(const LzArgs& a, int j, const double* h, double* v) {
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t n = gt; n < a.N; n += nt) {
+    double s = 0.0;
+    for (int i = 0; i <= j; ++i) s = fma(a.Q[(int64_t)i * a.N + n], h[i], s);
+    v[n] -= s;
+  }
+}
+// ||v||^2 summed in the same order by every block
+__device__ bool norm2_all(const LzArgs& a, const double* v, double* out) {
+  __shared__ double sh[32];
+  __shared__ double tot;
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+  double s = 0.0;
+  for (int64_t n = gt; n < a.N; n += nt) s = fma(v[n], v[n], s);
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) a.part[blockIdx.x] = s;
+  if (!grid_barrier(a)) return false;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) t += ((volatile double*)a.part)[b];
+    tot = t;
+  }
+  __syncthreads();
+  *out = tot;
+  return true;
+}
+
+__global__ void __launch_bounds__(256) lanczos_coop_kernel(LzArgs a) {
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+  const int gw = (int)(gt >> 5), nw = (int)(nt >> 5), lane = threadIdx.x & 31;
+  __shared__ double s_scale;
+  for (int j = a.m0; j < a.m1; ++j) {
+    const double* qj = a.Q + (int64_t)j * a.N;
+    // w = M q_j
+    for (int64_t r = gw; r < a.N; r += nw) {
+      const double* mr = a.M + r * a.N;
+      double s = 0.0;
+      for (int64_t c = lane; c < a.N; c += 32) s = fma(mr[c], qj[c], s);
+      s = warp_sum(s);
+      if (lane == 0) a.w[r] = s;
+    }
+    if (!grid_barrier(a)) return;
+    // two passes of classical Gram-Schmidt against q_0..q_j
+    dots_against_q(a, j, a.w, a.h1);
+    if (!grid_barrier(a)) return;
+    sub_q(a, j, a.h1, a.w);
+    if (!grid_barrier(a)) return;
+    dots_against_q(a, j, a.w, a.h2);
+    if (!grid_barrier(a)) return;
+    sub_q(a, j, a.h2, a.w);
+    if (!grid_barrier(a)) return;
+    double nn;
+    if (!norm2_all(a, a.w, &nn)) return;
+    const double nrm = sqrt(nn);
+    const double alph = ((volatile double*)a.h1)[j] + ((volatile double*)a.h2)[j];
+    if (threadIdx.x == 0) {
+      double sc = fabs(alph);
+      for (int i = 0; i < j; ++i)
+        sc = fmax(sc, fmax(fabs(((volatile double*)a.alpha)[i]), ((volatile double*)a.beta)[i]));
+      s_scale = sc;
+    }
+    __syncthreads();
+    const bool brk = !(nrm > 1e-12 * s_scale) || s_scale == 0.0;
+    const bool more = j + 1 < a.mcap;
+    double* qn = a.Q + (int64_t)(j + 1) * a.N;
+    if (more) {
+      if (!brk) {
+        const double inv = 1.0 / nrm;
+        for (int64_t n = gt; n < a.N; n += nt) qn[n] = a.w[n] * inv;
+      } else {
+        for (int64_t n = gt; n < a.N; n += nt) qn[n] = rnd_sym(a.key, (uint64_t)j * 0x100000000ull + n);
+      }
+    }
+    if (gt == 0) {
+      a.alpha[j] = alph;
+      a.beta[j] = brk ? 0.0 : nrm;
+    }
+    if (brk && more) {
+      if (!grid_barrier(a)) return;  // the random vector is complete
+      // a fresh direction orthogonal to the Krylov basis
+      for (int pass = 0; pass < 2; ++pass) {
+        dots_against_q(a, j, qn, a.h1);
+        if (!grid_barrier(a)) return;
+        sub_q(a, j, a.h1, qn);
+        if (!grid_barrier(a)) return;
+      }
+      double q2;
+      if (!norm2_all(a, qn, &q2)) return;
+      const double inv = q2 > 0.0 ? 1.0 / sqrt(q2) : 0.0;
+      for (int64_t n = gt; n < a.N; n += nt) qn[n] *= inv;
+    }
+    if (!grid_barrier(a)) return;
+  }
+}
+
+// Cluster boundaries of the Ritz values (descending): eigenvalues closer
+// than ortol to their predecessor share a cluster whose eigenvectors are
+// orthogonalised against each other during inverse iteration.
+__global__ void clusters_kernel(const double* theta, int k, double rel, int* start) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double ortol = rel * fabs(theta[0]);
+  int s = 0;
+  for (int c = 0; c < k; ++c) {
+    if (c > 0 && theta[c - 1] - theta[c] > ortol) s = c;
+    start[c] = s;
+  }
 }
 
 // ----------------------------------------------------- tridiagonal eigen
@@ -168,42 +264,59 @@ __device__ int sturm_count(const double* a, const double* b, int m, double x, do
   return cnt;
 }
 
-// theta[c] = c-th largest eigenvalue of T_m (bisection to full precision).
+// theta[c] = c-th largest eigenvalue of T_m, one warp per eigenvalue: each
+// iteration evaluates the Sturm count at 32 interior points (multisection),
+// shrinking the bracket 33-fold, until it is a few ulps wide.
 __global__ void bisect_kernel(const double* a, const double* b, int m, int k, double* theta) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (c >= k) return;
   double lo = DBL_MAX, hi = -DBL_MAX, bmax2 = 0.0;
-  for (int i = 0; i < m; ++i) {
-    double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < m - 1 ? fabs(b[i]) : 0.0);
+  for (int i = lane; i < m; i += 32) {
+    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < m - 1 ? fabs(b[i]) : 0.0);
     lo = fmin(lo, a[i] - r);
     hi = fmax(hi, a[i] + r);
     if (i < m - 1) bmax2 = fmax(bmax2, b[i] * b[i]);
   }
-  double tnorm = fmax(fabs(lo), fabs(hi));
-  double pivmin = DBL_MIN * fmax(1.0, bmax2);
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    bmax2 = fmax(bmax2, __shfl_xor_sync(0xffffffffu, bmax2, o));
+  }
+  const double tnorm = fmax(fabs(lo), fabs(hi));
+  const double pivmin = DBL_MIN * fmax(1.0, bmax2);
   lo -= 2.0 * DBL_EPSILON * tnorm + pivmin;
   hi += 2.0 * DBL_EPSILON * tnorm + pivmin;
-  int t = m - 1 - c;  // index from the smallest
-  for (int it = 0; it < 200; ++it) {
-    double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (sturm_count(a, b, m, mid, pivmin) <= t)
-      lo = mid;
-    else
-      hi = mid;
+  const int t = m - 1 - c;  // index from the smallest
+  for (int it = 0; it < 64; ++it) {
     if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin) break;
+    const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+    const int cnt = sturm_count(a, b, m, x, pivmin);
+    const unsigned above = __ballot_sync(0xffffffffu, cnt > t);
+    const int first = above ? __ffs(above) - 1 : 32;
+    const double nhi = first < 32 ? __shfl_sync(0xffffffffu, x, first) : hi;
+    const double nlo = first > 0 ? __shfl_sync(0xffffffffu, x, first - 1) : lo;
+    if (!(nlo < nhi)) break;
+    lo = nlo;
+    hi = nhi;
   }
-  theta[c] = 0.5 * (lo + hi);
+  if (lane == 0) theta[c] = 0.5 * (lo + hi);
 }
 
 // Eigenvectors of T_m for theta[0..k-1] by inverse iteration with a
-// partially pivoted tridiagonal LU of (T - theta I).  One block; thread 0 runs
-// the O(m) recurrences, all threads share the orthogonalisation against the
-// vectors already found.  Y: k rows of length ldy.  res[c] = |beta_m y_c[m-1]|.
+// partially pivoted tridiagonal LU of (T - theta I).  One block per cluster
+// (block c works only if c starts a cluster); inside a cluster the vectors
+// are found in order, each orthogonalised against the earlier ones at every
+// iteration.  Thread 0 runs the O(m) recurrences.  Y: k rows of length ldy.
+// res[c] = |beta_m y_c[m-1]| bounds the residual of Ritz pair c.
 __global__ void inviter_kernel(const double* a, const double* b, int m, int k, const double* theta,
-                               double* Y, int64_t ldy, double* scratch, double beta_m,
-                               double* res, uint64_t key) {
+                               const int* cstart, double* Y, int64_t ldy, double* scratch_all,
+                               const double* beta_last, double* res, uint64_t key) {
+  const int c0 = blockIdx.x;
+  if (cstart[c0] != c0) return;
   __shared__ double sh[32];
+  __shared__ double sdot[1024];
+  double* scratch = scratch_all + (int64_t)c0 * 5 * (ldy + 1);
   double* d = scratch;
   double* du = scratch + m;
   double* dl = scratch + 2 * m;
@@ -212,9 +325,11 @@ __global__ void inviter_kernel(const double* a, const double* b, int m, int k, c
   double tnorm = 0.0;
   for (int i = 0; i < m; ++i)
     tnorm = fmax(tnorm, fabs(a[i]) + (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < m - 1 ? fabs(b[i]) : 0.0));
-  double tiny = DBL_EPSILON * fmax(tnorm, DBL_MIN);
-  for (int c = 0; c < k; ++c) {
-    double th = theta[c];
+  const double tiny = DBL_EPSILON * fmax(tnorm, DBL_MIN);
+  const double beta_m = *beta_last;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  for (int c = c0; c < k && cstart[c] == c0; ++c) {
+    const double th = theta[c];
     double* y = Y + (int64_t)c * ldy;
     if (threadIdx.x == 0) {
       for (int i = 0; i < m; ++i) {
@@ -229,15 +344,15 @@ __global__ void inviter_kernel(const double* a, const double* b, int m, int k, c
         if (fabs(d[i]) >= fabs(dl[i])) {
           piv[i] = 0;
           if (fabs(d[i]) < tiny) d[i] = d[i] < 0 ? -tiny : tiny;
-          double f = dl[i] / d[i];
+          const double f = dl[i] / d[i];
           dl[i] = f;
           d[i + 1] -= f * du[i];
         } else {
           piv[i] = 1;
-          double f = d[i] / dl[i];
+          const double f = d[i] / dl[i];
           d[i] = dl[i];
           dl[i] = f;
-          double tmp = du[i];
+          const double tmp = du[i];
           du[i] = d[i + 1];
           d[i + 1] = tmp - f * d[i + 1];
           if (i < m - 2) {
@@ -247,6 +362,7 @@ __global__ void inviter_kernel(const double* a, const double* b, int m, int k, c
         }
       }
       if (fabs(d[m - 1]) < tiny) d[m - 1] = d[m - 1] < 0 ? -tiny : tiny;
+      for (int i = 0; i < m; ++i) d[i] = 1.0 / d[i];  // the solves multiply
     }
     for (int i = threadIdx.x; i < m; i += blockDim.x) y[i] = 1.0 + 0.25 * rnd_sym(key + c, i);
     __syncthreads();
@@ -254,52 +370,49 @@ __global__ void inviter_kernel(const double* a, const double* b, int m, int k, c
       if (threadIdx.x == 0) {
         for (int i = 0; i < m - 1; ++i) {
           if (piv[i]) {
-            double t = y[i];
+            const double t = y[i];
             y[i] = y[i + 1];
             y[i + 1] = t;
           }
           y[i + 1] -= dl[i] * y[i];
         }
-        y[m - 1] /= d[m - 1];
-        if (m >= 2) y[m - 2] = (y[m - 2] - du[m - 2] * y[m - 1]) / d[m - 2];
-        for (int i = m - 3; i >= 0; --i) y[i] = (y[i] - du[i] * y[i + 1] - du2[i] * y[i + 2]) / d[i];
+        y[m - 1] *= d[m - 1];
+        if (m >= 2) y[m - 2] = (y[m - 2] - du[m - 2] * y[m - 1]) * d[m - 2];
+        for (int i = m - 3; i >= 0; --i) y[i] = (y[i] - du[i] * y[i + 1] - du2[i] * y[i + 2]) * d[i];
+        double mx = 0.0;
+        for (int i = 0; i < m; ++i) mx = fmax(mx, fabs(y[i]));
+        sh[0] = mx > 0.0 ? 1.0 / mx : 1.0;
       }
       __syncthreads();
-      // scale to avoid overflow, then orthogonalise against earlier vectors (twice)
-      double s = 0.0;
-      for (int i = threadIdx.x; i < m; i += blockDim.x) s = fmax(s, fabs(y[i]));
-      {
-        double v = s;
-        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-        __syncthreads();
-        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          double mm = 0.0;
-          for (int i = 0; i < (int)((blockDim.x + 31) >> 5); ++i) mm = fmax(mm, sh[i]);
-          sh[0] = mm;
-        }
-        __syncthreads();
-        s = sh[0];
-        __syncthreads();
-      }
-      double inv = s > 0.0 ? 1.0 / s : 1.0;
+      const double inv = sh[0];
+      __syncthreads();
       for (int i = threadIdx.x; i < m; i += blockDim.x) y[i] *= inv;
       __syncthreads();
-      for (int pass = 0; pass < 2; ++pass) {
-        for (int p = 0; p < c; ++p) {
-          const double* yp = Y + (int64_t)p * ldy;
-          double dot = 0.0;
-          for (int i = threadIdx.x; i < m; i += blockDim.x) dot = fma(yp[i], y[i], dot);
-          dot = block_sum(dot, sh);
-          for (int i = threadIdx.x; i < m; i += blockDim.x) y[i] -= dot * yp[i];
+      // orthogonalise against the cluster's earlier vectors (twice)
+      const int nprev = c - c0;
+      for (int pass = 0; pass < 2 && nprev > 0; ++pass) {
+        for (int pb = 0; pb < nprev; pb += 1024) {
+          const int cnt = nprev - pb < 1024 ? nprev - pb : 1024;
+          for (int pi = warp; pi < cnt; pi += nwarp) {
+            const double* yp = Y + (int64_t)(c0 + pb + pi) * ldy;
+            double dot = 0.0;
+            for (int i = lane; i < m; i += 32) dot = fma(yp[i], y[i], dot);
+            dot = warp_sum(dot);
+            if (lane == 0) sdot[pi] = dot;
+          }
+          __syncthreads();
+          for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            double s = 0.0;
+            for (int pi = 0; pi < cnt; ++pi) s = fma(sdot[pi], Y[(int64_t)(c0 + pb + pi) * ldy + i], s);
+            y[i] -= s;
+          }
           __syncthreads();
         }
       }
       double nn = 0.0;
       for (int i = threadIdx.x; i < m; i += blockDim.x) nn = fma(y[i], y[i], nn);
       nn = block_sum(nn, sh);
-      double inv2 = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+      const double inv2 = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
       for (int i = threadIdx.x; i < m; i += blockDim.x) y[i] *= inv2;
       __syncthreads();
     }
@@ -391,7 +504,11 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   double* theta = ar.take<double>(k);
   double* Y = ar.take<double>((int64_t)k * mcap);
   double* U = ar.take<double>(N * k);
-  double* scratch = ar.take<double>(5 * (mcap + 1));
+  double* scratch = ar.take<double>((int64_t)k * 5 * (mcap + 1));
+  double* part = ar.take<double>(4096);
+  unsigned* bar = ar.take<unsigned>(4);
+  int* err = ar.take<int>(1);
+  int* cstart = ar.take<int>(k);
   double* rr = ar.take<double>(k);
   double* mx = ar.take<double>(2);
   int* flag = ar.take<int>(2);
@@ -435,56 +552,55 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   const uint64_t key = 0x5DEECE66Dull;
   init_start_kernel<<<1, 1024, 0, s>>>(Q, N, key);
   HM_LAUNCHED();
+  HM_CUDA(cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), s));
+  HM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  int per_sm = 0;
+  HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lanczos_coop_kernel, 256, 0));
+  if (per_sm < 1) return set_error(HESS_ERR_CUDA, "Lanczos kernel cannot be resident");
+  const int grid = (per_sm < 2 ? per_sm : 2) * h->sm_count;
   int m = 0;
   int64_t target = N < (int64_t)2 * k + 32 ? N : (int64_t)2 * k + 32;
   if (target < k) target = k;
-  const unsigned rows_blocks_N = (unsigned)cdiv(N, 8);
-  const unsigned cols_blocks = (unsigned)cdiv(N, 256);
   bool converged = false;
   double* hp = h->host_pinned;
   while (true) {
-    for (; m < target; ++m) {
-      double* qj = Q + (int64_t)m * N;
-      double* qn = Q + (int64_t)(m + 1) * N;
-      gemv_rows_kernel<<<rows_blocks_N, 256, 0, s>>>(M, N, (int)N, N, qj, w, nullptr);
-      HM_LAUNCHED();
-      double* hs[2] = {h1, h2};
-      for (int pass = 0; pass < 2; ++pass) {
-        gemv_rows_kernel<<<(unsigned)cdiv(m + 1, 8), 256, 0, s>>>(Q, N, m + 1, N, w, hs[pass],
-                                                                 nullptr);
-        HM_LAUNCHED();
-        gemv_sub_kernel<<<cols_blocks, 256, 0, s>>>(Q, N, m + 1, N, hs[pass], w, nullptr);
-        HM_LAUNCHED();
-      }
-      if (m + 1 < mcap) {
-        lanczos_norm_kernel<<<1, 1024, 0, s>>>(w, qn, N, m, h1, h2, alpha, beta, flag, key + 7);
-        HM_LAUNCHED();
-        for (int pass = 0; pass < 2; ++pass) {
-          gemv_rows_kernel<<<(unsigned)cdiv(m + 1, 8), 256, 0, s>>>(Q, N, m + 1, N, qn, h1, flag);
-          HM_LAUNCHED();
-          gemv_sub_kernel<<<cols_blocks, 256, 0, s>>>(Q, N, m + 1, N, h1, qn, flag);
-          HM_LAUNCHED();
-        }
-        normalize_gated_kernel<<<1, 1024, 0, s>>>(qn, N, flag);
-        HM_LAUNCHED();
-      } else {
-        // last vector of the workspace: only alpha_m and beta_m are needed
-        lanczos_norm_kernel<<<1, 1024, 0, s>>>(w, w, N, m, h1, h2, alpha, beta, flag, key + 7);
-        HM_LAUNCHED();
-      }
-    }
-    bisect_kernel<<<(unsigned)cdiv(k, 64), 64, 0, s>>>(alpha, beta, m, k, theta);
+    LzArgs la;
+    la.M = M;
+    la.N = N;
+    la.Q = Q;
+    la.w = w;
+    la.h1 = h1;
+    la.h2 = h2;
+    la.alpha = alpha;
+    la.beta = beta;
+    la.part = part;
+    la.bar_count = bar;
+    la.bar_gen = bar + 1;
+    la.err = err;
+    la.m0 = m;
+    la.m1 = (int)target;
+    la.mcap = (int)mcap;
+    la.key = key + 7;
+    void* kargs[] = {&la};
+    HM_CUDA(cudaLaunchCooperativeKernel((void*)lanczos_coop_kernel, grid, 256, kargs, 0, s));
     HM_LAUNCHED();
-    // beta[m-1] couples T_m to the next Lanczos vector
-    HM_CUDA(cudaMemcpyAsync(hp, beta + (m - 1), sizeof(double), cudaMemcpyDeviceToHost, s));
-    HM_CUDA(cudaStreamSynchronize(s));
-    double beta_m = hp[0];
-    inviter_kernel<<<1, 256, 0, s>>>(alpha, beta, m, k, theta, Y, mcap, scratch, beta_m, rr, key + 11);
+    m = (int)target;
+    bisect_kernel<<<(unsigned)cdiv(k, 4), 128, 0, s>>>(alpha, beta, m, k, theta);
+    HM_LAUNCHED();
+    // the cluster tolerance of inverse iteration: 1e-3 of ||T||, bounded by
+    // the largest Ritz value (T is positive semi-definite here)
+    clusters_kernel<<<1, 32, 0, s>>>(theta, k, 1e-3, cstart);
+    HM_LAUNCHED();
+    inviter_kernel<<<k, 256, 0, s>>>(alpha, beta, m, k, theta, cstart, Y, mcap, scratch,
+                                     beta + (m - 1), rr, key + 11);
     HM_LAUNCHED();
     max_res_kernel<<<1, 32, 0, s>>>(rr, k, theta, mx);
     HM_LAUNCHED();
     HM_CUDA(cudaMemcpyAsync(hp, mx, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaMemcpyAsync(reinterpret_cast<int*>(hp + 2), err, sizeof(int), cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaStreamSynchronize(s));
+    if (*reinterpret_cast<int*>(hp + 2))
+      return set_error(HESS_ERR_TIMEOUT, "Lanczos grid barrier gave up");
     if (hp[0] <= 1e-11 * hp[1] || m >= N) {
       converged = true;
       break;

@@ -131,6 +131,25 @@ struct Gemm {
 template <typename T>
 hess_status gemm(const Gemm<T>& g, cudaStream_t s);
 
+// Scratch for split-K partial tiles of the SIMT GEMM, set by each entry point
+// from its workspace for the duration of the call (none: no split).
+struct SplitScratch {
+  void* p = nullptr;
+  size_t bytes = 0;
+  int sms = 0;
+};
+extern thread_local SplitScratch g_split;
+struct SplitGuard {
+  explicit SplitGuard(void* p, size_t bytes, int sms) { g_split = SplitScratch{p, bytes, sms}; }
+  ~SplitGuard() { g_split = SplitScratch{}; }
+};
+constexpr size_t kSplitBytes = (size_t)64 << 20;
+
+// out[r] = alpha * sum_{n < K} A[n * lda + r]  for r < R (deterministic)
+template <typename T>
+hess_status colsum(const T* A, int64_t lda, int64_t R, int64_t K, T alpha, T* out, int64_t ostride,
+                   cudaStream_t s);
+
 // Forward/backward caches of one call (all device, row-major N x T_l).
 template <typename T>
 struct Caches {
@@ -176,7 +195,7 @@ hess_status rop_block(const Net& net, const T* omega, const Caches<T>& c, int jm
 // masked to c >= d0 and mirrored to H[c][d] for c >= d0 + B.  tmp: B x P_l.
 template <typename T>
 hess_status contract_layer(const Net& net, const Caches<T>& c, const RopBufs<T>& r, int jm, int jl,
-                           int64_t d0, T* tmp, const T* ones, T* H, cudaStream_t s);
+                           int64_t d0, T* tmp, T* H, cudaStream_t s);
 template <typename T>
 hess_status scatter_sym(const T* tmp, int B, int64_t cols, int64_t c0, int64_t d0, T* H, int64_t P,
                         cudaStream_t s);

@@ -33,7 +33,7 @@ __device__ __forceinline__ void upper_tile(long long t, int nt, int& tm, int& tn
 }
 
 template <typename T, int BM, int BN, int BK, int TM, int TN>
-__global__ void __launch_bounds__(256) gemm_kernel(Gemm<T> g) {
+__global__ void __launch_bounds__(256) gemm_kernel(Gemm<T> g, int splits, T* part) {
   constexpr int NT = (BM / TM) * (BN / TN);
   static_assert(NT == 256, "256 threads");
   __shared__ T As[BK][BM + 1];
@@ -45,9 +45,14 @@ __global__ void __launch_bounds__(256) gemm_kernel(Gemm<T> g) {
     tm = blockIdx.x;
     tn = blockIdx.y;
   }
-  const T* A = g.A + (int64_t)blockIdx.z * g.bsa;
-  const T* B = g.B + (int64_t)blockIdx.z * g.bsb;
-  T* C = g.C + (int64_t)blockIdx.z * g.bsc;
+  // blockIdx.z = batch * splits + slice; a slice owns K range [kbeg, kend)
+  const int bz = blockIdx.z / splits, slice = blockIdx.z % splits;
+  const T* A = g.A + (int64_t)bz * g.bsa;
+  const T* B = g.B + (int64_t)bz * g.bsb;
+  T* C = g.C + (int64_t)bz * g.bsc;
+  const int kchunk = ((g.K + splits - 1) / splits + BK - 1) / BK * BK;
+  const int kbeg = slice * kchunk;
+  const int kend = min(g.K, kbeg + kchunk);
   const int tid = threadIdx.x;
   const int tx = tid % (BN / TN), ty = tid / (BN / TN);
   const int64_t m0 = (int64_t)tm * BM, n0 = (int64_t)tn * BN;
@@ -58,7 +63,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(Gemm<T> g) {
     for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
   const bool a_m_fast = (g.sam == 1);
   const bool b_n_fast = (g.sbn == 1);
-  for (int k0 = 0; k0 < g.K; k0 += BK) {
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
     for (int it = 0; it < BM * BK / NT; ++it) {
       int e = tid + it * NT;
@@ -72,7 +77,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(Gemm<T> g) {
       }
       int64_t m = m0 + mm;
       int k = k0 + kk;
-      As[kk][mm] = (m < g.M && k < g.K) ? A[m * g.sam + (int64_t)k * g.sak] : T(0);
+      As[kk][mm] = (m < g.M && k < kend) ? A[m * g.sam + (int64_t)k * g.sak] : T(0);
     }
 #pragma unroll
     for (int it = 0; it < BN * BK / NT; ++it) {
@@ -87,7 +92,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(Gemm<T> g) {
       }
       int64_t n = n0 + nn;
       int k = k0 + kk;
-      Bs[kk][nn] = (n < g.N && k < g.K) ? B[(int64_t)k * g.sbk + n * g.sbn] : T(0);
+      Bs[kk][nn] = (n < g.N && k < kend) ? B[(int64_t)k * g.sbk + n * g.sbn] : T(0);
     }
     __syncthreads();
 #pragma unroll
@@ -103,6 +108,21 @@ __global__ void __launch_bounds__(256) gemm_kernel(Gemm<T> g) {
         for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
+  }
+  if (part) {
+    // split-K: raw partial sums, [slice][batch][M][N]
+    T* pp = part + ((int64_t)slice * (gridDim.z / splits) + bz) * (int64_t)g.M * g.N;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      int64_t m = m0 + ty + i * (BM / TM);
+      if (m >= g.M) continue;
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        int64_t n = n0 + tx + j * (BN / TN);
+        if (n < g.N) pp[m * g.N + n] = acc[i][j];
+      }
+    }
+    return;
   }
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
@@ -120,28 +140,92 @@ __global__ void __launch_bounds__(256) gemm_kernel(Gemm<T> g) {
   }
 }
 
+// Sum the split-K partials in slice order and apply alpha / beta.
+template <typename T>
+__global__ void splitk_reduce_kernel(Gemm<T> g, int splits, const T* part) {
+  const int64_t mn = (int64_t)g.M * g.N;
+  const int64_t total = mn * g.batch;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = idx / mn, r = idx % mn;
+    const int64_t m = r / g.N, n = r % g.N;
+    T acc = T(0);
+    for (int sl = 0; sl < splits; ++sl) acc += part[((int64_t)sl * g.batch + b) * mn + r];
+    T* c = g.C + b * g.bsc + m * g.scm + n * g.scn;
+    T v = g.alpha * acc;
+    if (g.beta != T(0)) v += g.beta * (*c);
+    *c = v;
+  }
+}
+
+thread_local SplitScratch g_split;
+
+template <typename T>
+__global__ void colsum_kernel(const T* A, int64_t lda, int64_t R, int64_t K, T alpha, T* out,
+                              int64_t ostride) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  T acc = T(0);
+  for (int64_t n = 0; n < K; ++n) acc += A[n * lda + r];
+  out[r * ostride] = alpha * acc;
+}
+template <typename T>
+hess_status colsum(const T* A, int64_t lda, int64_t R, int64_t K, T alpha, T* out, int64_t ostride,
+                   cudaStream_t s) {
+  if (R <= 0) return HESS_OK;
+  colsum_kernel<T><<<(unsigned)cdiv(R, 128), 128, 0, s>>>(A, lda, R, K, alpha, out, ostride);
+  HM_LAUNCHED();
+  return HESS_OK;
+}
+template hess_status colsum<double>(const double*, int64_t, int64_t, int64_t, double, double*,
+                                    int64_t, cudaStream_t);
+template hess_status colsum<float>(const float*, int64_t, int64_t, int64_t, float, float*, int64_t,
+                                   cudaStream_t);
+
 template <typename T>
 hess_status gemm(const Gemm<T>& g, cudaStream_t s) {
   using Cfg = GemmCfg<T>;
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return HESS_OK;
   if (g.batch > 65535) return set_error(HESS_ERR_INVALID_ARG, "gemm batch %d too large", g.batch);
+  int64_t tiles;
   dim3 grid;
   if (g.upper) {
     int64_t nt = cdiv(g.M, Cfg::BM);
-    grid = dim3((unsigned)(nt * (nt + 1) / 2), 1, g.batch);
+    tiles = nt * (nt + 1) / 2;
+    grid = dim3((unsigned)tiles, 1, g.batch);
   } else {
     int64_t gy = cdiv(g.N, Cfg::BN);
     if (gy > 65535) return set_error(HESS_ERR_INVALID_ARG, "gemm N %d too large", g.N);
+    tiles = cdiv(g.M, Cfg::BM) * gy;
     grid = dim3((unsigned)cdiv(g.M, Cfg::BM), (unsigned)gy, g.batch);
   }
-  if (g.K <= 0) {
-    // empty contraction: C = beta * C
-    Gemm<T> z = g;
-    gemm_kernel<T, Cfg::BM, Cfg::BN, Cfg::BK, Cfg::TM, Cfg::TN><<<grid, 256, 0, s>>>(z);
+  // split K when the output tiles cannot fill the GPU (deterministic: the
+  // partials are summed in slice order by a second kernel)
+  int splits = 1;
+  const int sms = g_split.sms > 0 ? g_split.sms : 148;
+  if (!g.upper && g_split.p && tiles * g.batch < 2 * sms && g.K >= 256) {
+    int64_t want = cdiv(2 * sms, tiles * g.batch);
+    int64_t maxs = g.K / 128;
+    int64_t cap = (int64_t)(g_split.bytes / ((size_t)g.M * g.N * g.batch * sizeof(T)));
+    int64_t sp = want < maxs ? want : maxs;
+    sp = sp < cap ? sp : cap;
+    if (sp > 64) sp = 64;
+    if ((int64_t)g.batch * sp > 65535) sp = 65535 / g.batch;
+    if (sp >= 2) splits = (int)sp;
+  }
+  if (splits > 1) {
+    grid.z = g.batch * splits;
+    T* part = reinterpret_cast<T*>(g_split.p);
+    gemm_kernel<T, Cfg::BM, Cfg::BN, Cfg::BK, Cfg::TM, Cfg::TN><<<grid, 256, 0, s>>>(g, splits, part);
+    HM_LAUNCHED();
+    int64_t total = (int64_t)g.M * g.N * g.batch;
+    int64_t blocks = cdiv(total, 256);
+    if (blocks > 65536) blocks = 65536;
+    splitk_reduce_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(g, splits, part);
     HM_LAUNCHED();
     return HESS_OK;
   }
-  gemm_kernel<T, Cfg::BM, Cfg::BN, Cfg::BK, Cfg::TM, Cfg::TN><<<grid, 256, 0, s>>>(g);
+  gemm_kernel<T, Cfg::BM, Cfg::BN, Cfg::BK, Cfg::TM, Cfg::TN><<<grid, 256, 0, s>>>(g, 1, nullptr);
   HM_LAUNCHED();
   return HESS_OK;
 }
@@ -646,7 +730,7 @@ template hess_status rop_block<float>(const Net&, const float*, const Caches<flo
 // (the R-operator applied to dC_n/dW = delta a^T and dC_n/db = delta).
 template <typename T>
 hess_status contract_layer(const Net& net, const Caches<T>& c, const RopBufs<T>& r, int jm, int jl,
-                           int64_t d0, T* tmp, const T* ones, T* H, cudaStream_t s) {
+                           int64_t d0, T* tmp, T* H, cudaStream_t s) {
   const int64_t N = c.N;
   const int B = r.B;
   const int Tin = net.T[jl - 1], Tout = net.T[jl];
@@ -695,32 +779,16 @@ hess_status contract_layer(const Net& net, const Caches<T>& c, const RopBufs<T>&
     g.batch = B;
     HM_TRY(gemm(g, s));
   }
-  {
-    Gemm<T> g;
-    g.M = B * Tout;
-    g.N = 1;
-    g.K = (int)N;
-    g.alpha = invN;
-    g.A = r.rd[jl];
-    g.sam = 1;
-    g.sak = (int64_t)B * Tout;
-    g.B = ones;
-    g.sbk = 1;
-    g.sbn = 0;
-    g.C = tmpB;
-    g.scm = 1;
-    g.scn = 0;
-    HM_TRY(gemm(g, s));
-  }
+  // bias columns: (1/N) sum_n R{delta}[n, d, i]
+  HM_TRY(colsum(r.rd[jl], (int64_t)B * Tout, (int64_t)B * Tout, N, invN, tmpB, (int64_t)1, s));
   HM_TRY(scatter_sym(tmpW, B, nW, net.woff[jl - 1], d0, H, net.P, s));
   HM_TRY(scatter_sym(tmpB, B, (int64_t)Tout, net.boff[jl - 1], d0, H, net.P, s));
   return HESS_OK;
 }
 template hess_status contract_layer<double>(const Net&, const Caches<double>&,
                                             const RopBufs<double>&, int, int, int64_t, double*,
-                                            const double*, double*, cudaStream_t);
+                                            double*, cudaStream_t);
 template hess_status contract_layer<float>(const Net&, const Caches<float>&, const RopBufs<float>&,
-                                           int, int, int64_t, float*, const float*, float*,
-                                           cudaStream_t);
+                                           int, int, int64_t, float*, float*, cudaStream_t);
 
 }  // namespace hm

@@ -638,6 +638,7 @@ hess_status run_opg_tc(hess_mlp* h, const void* X, const void* Y, int64_t N, boo
     for (int64_t tn = 0; tn < nt; ++tn)
       for (int64_t tm = g0; tm < g0 + 8 && tm < mt; ++tm)
         if (tn * BN + BN - 1 >= tm * BM) tiles.push_back(make_int2((int)tm, (int)tn));
+  char* split = nullptr;
   auto plan = [&](Arena& ar, float*& xs, float*& ys, Caches<float>& c, float*& G, __nv_bfloat16*& hi,
                   __nv_bfloat16*& lo, float*& O, int2*& tl, int*& err) {
     xs = x_dev ? nullptr : ar.take<float>(N * T1);
@@ -649,6 +650,7 @@ hess_status run_opg_tc(hess_mlp* h, const void* X, const void* Y, int64_t N, boo
     O = o_dev ? (float*)Oout : ar.take<float>(P * P);
     tl = ar.take<int2>(tiles.size());
     err = ar.take<int>(1);
+    split = ar.take<char>(kSplitBytes);
   };
   Arena ar;
   float *xs, *ys, *G, *O;
@@ -660,6 +662,7 @@ hess_status run_opg_tc(hess_mlp* h, const void* X, const void* Y, int64_t N, boo
   HM_TRY(ensure_ws(h, ar.off));
   ar = Arena{h->ws, 0};
   plan(ar, xs, ys, c, G, hi, lo, O, tl, err);
+  SplitGuard sg(split, kSplitBytes, h->sm_count);
   cudaStream_t s = h->stream;
   const float* xd = (const float*)X;
   const float* yd = (const float*)Y;
@@ -748,6 +751,7 @@ hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N,
   if (pchunk < 1) pchunk = 1;
   (void)per_unit;
   const int64_t max_tiles = cdiv(arows_max, BM) * cdiv(Tinmax, 64);
+  char* split = nullptr;
   auto plan = [&](Arena& ar, float*& xs, float*& ys, Caches<float>& c, RopBufs<float>& r,
                   float*& tmp, float*& ones, __nv_bfloat16*& bhi, __nv_bfloat16*& blo,
                   __nv_bfloat16*& ahi, __nv_bfloat16*& alo, float*& F, float*& C2, float*& O,
@@ -767,6 +771,7 @@ hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N,
     O = o_dev ? (float*)Hout : ar.take<float>(P * P);
     tl = ar.take<int2>(max_tiles);
     err = ar.take<int>(1);
+    split = ar.take<char>(kSplitBytes);
   };
   Arena ar;
   float *xs, *ys, *tmp, *ones, *F, *C2, *O;
@@ -779,6 +784,7 @@ hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N,
   HM_TRY(ensure_ws(h, ar.off));
   ar = Arena{h->ws, 0};
   plan(ar, xs, ys, c, r, tmp, ones, bhi, blo, ahi, alo, F, C2, O, tl, err);
+  SplitGuard sg(split, kSplitBytes, h->sm_count);
   cudaStream_t s = h->stream;
   const float* xd = (const float*)X;
   const float* yd = (const float*)Y;
@@ -806,7 +812,7 @@ hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N,
     }
     {
       Tick t(h, HESS_K_HREST, 0.0, 0.0);
-      for (int jl = jm; jl < L; ++jl) HM_TRY(contract_layer(net, c, rb, jm, jl, boff, tmp, ones, O, s));
+      for (int jl = jm; jl < L; ++jl) HM_TRY(contract_layer(net, c, rb, jm, jl, boff, tmp, O, s));
     }
     // W x W block on the tensor cores
     transpose_split_kernel<<<dim3((unsigned)cdiv(ld, 32), (unsigned)cdiv(Tin, 32)), dim3(32, 8), 0, s>>>(
