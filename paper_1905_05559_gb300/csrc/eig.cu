@@ -34,6 +34,19 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// 1/x to about one ulp: the hardware reciprocal estimate refined by two
+// Newton-Raphson steps r <- r + r (1 - x r) (quadratic convergence from the
+// estimate's ~2^-23 relative error).  Used inside the long dependent chains of
+// the tridiagonal recurrences, where a full-precision division would dominate.
+__device__ __forceinline__ double rcp64(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
 // sum over a block of up to 1024 threads
 __device__ double block_sum(double v, double* sh) {
   v = warp_sum(v);
@@ -59,57 +72,77 @@ __global__ void gram_acc_kernel(double* M, const double* DD, const double* AA, i
     M[i] += DD[i] * (AA[i] + 1.0) * invN;
 }
 
-__global__ void init_start_kernel(double* q, int64_t N, uint64_t key) {
-  __shared__ double sh[32];
-  double s = 0.0;
-  for (int64_t n = threadIdx.x; n < N; n += blockDim.x) {
-    double v = rnd_sym(key, n);
-    q[n] = v;
-    s = fma(v, v, s);
-  }
-  s = block_sum(s, sh);
-  double inv = 1.0 / sqrt(s);
-  for (int64_t n = threadIdx.x; n < N; n += blockDim.x) q[n] *= inv;
-}
 
 // ------------------------------------------------ cooperative Lanczos
 // All Lanczos steps of one extension run in a single cooperative launch (all
-// blocks co-resident); the phases of a step are separated by a grid barrier
-// whose waits are bounded: on timeout the kernel raises *err and returns.
+// blocks co-resident).  A step is four phases separated by grid barriers:
+//   A  beta_{j-1} = ||w||, q_j = w / beta, M q_j (= M w / beta) stored in MQ_j,
+//      first-pass coefficients h_i = (M q_i) . q_j for i < j and block
+//      partials of h_j = q_j . (M q_j)
+//   B  w' = M q_j - sum_{i<=j} h_i q_i
+//   C  second-pass dot products d_i = q_i . w' (i <= j), as chunk partials
+//   D  alpha_j = h_j + d_j, w = w' - sum_{i<=j} d_i q_i, block partials of ||w||^2
+// (classical Gram-Schmidt applied twice against every earlier vector).  A
+// breakdown (||w|| ~ 0) restarts from a random vector orthogonalised against
+// the basis.  Barrier waits are bounded: on timeout the kernel raises *err
+// and returns.
 struct LzArgs {
   const double* M;
   int64_t N;
-  double* Q;  // Lanczos vectors, rows of length N
-  double* w;
-  double* h1;
-  double* h2;
+  double* Q;     // Lanczos vectors, rows of length N (mcap rows)
+  double* MQ;    // M q_i, rows of length N
+  double* w;     // current residual vector
+  double* wt;    // w' of the step
+  double* h;     // first-pass coefficients (mcap)
+  double* dpart; // [mcap][nchunk] partial dot products
+  double* npart; // [gridDim] partial squared norms of w
+  double* apart; // [gridDim] partial sums of q_j . (M q_j)
   double* alpha;
   double* beta;
-  double* part;  // one partial sum per block
-  unsigned* bar_count;
-  unsigned* bar_gen;
+  unsigned* bar;  // [0]: generation, [1..]: group arrival counters
   int* err;
-  int m0, m1, mcap;
+  int m0, m1, mcap, nchunk;
   uint64_t key;
 };
 
 constexpr long long BAR_TIMEOUT = 4000000000ll;
+constexpr int BAR_GROUP = 16;
 
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned atom_add_acqrel(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+// Two-level arrival (groups of BAR_GROUP blocks, then the groups), one
+// generation word that every block polls.
 __device__ bool grid_barrier(const LzArgs& a) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
-    volatile unsigned* gen = a.bar_gen;
-    const unsigned g = *gen;
-    __threadfence();
-    if (atomicAdd(a.bar_count, 1u) == gridDim.x - 1) {
-      *a.bar_count = 0;
-      __threadfence();
-      atomicAdd(a.bar_gen, 1u);
-    } else {
+    const unsigned g = ld_acquire(a.bar);
+    const unsigned ngroups = (gridDim.x + BAR_GROUP - 1) / BAR_GROUP;
+    const unsigned grp = blockIdx.x / BAR_GROUP;
+    const unsigned gsize = min((unsigned)BAR_GROUP, gridDim.x - grp * BAR_GROUP);
+    unsigned* gcount = a.bar + 2 + grp;
+    bool last = false;
+    if (atom_add_acqrel(gcount, 1u) == gsize - 1) {
+      asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(gcount) : "memory");
+      if (atom_add_acqrel(a.bar + 1, 1u) == ngroups - 1) {
+        asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(a.bar + 1) : "memory");
+        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(a.bar), "r"(g + 1) : "memory");
+        last = true;
+      }
+    }
+    if (!last) {
       const long long t0 = clock64();
-      while (*gen == g) {
+      while (ld_acquire(a.bar) == g) {
         if (clock64() - t0 > BAR_TIMEOUT || *(volatile int*)a.err) {
           atomicExch(a.err, 1);
           ok = 0;
@@ -117,122 +150,188 @@ __device__ bool grid_barrier(const LzArgs& a) {
         }
       }
     }
-    __threadfence();
   }
   __syncthreads();
   return ok != 0;
 }
 
-// h[i] = Q_i . v for i <= j (one warp per dot product)
-__device__ void dots_against_q(const LzArgs& a, int j, const double* v, double* h) {
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  for (int i = gw; i <= j; i += nw) {
-    const double* qi = a.Q + (int64_t)i * a.N;
+// sum_b npart[b] by warp 0 of the block (same order in every block)
+__device__ double sum_partials(const double* part, int n, double* out_sh) {
+  if (threadIdx.x < 32) {
     double s = 0.0;
-    for (int64_t n = lane; n < a.N; n += 32) s = fma(qi[n], v[n], s);
+    for (int b = threadIdx.x; b < n; b += 32) s += ((volatile const double*)part)[b];
     s = warp_sum(s);
-    if (lane == 0) h[i] = s;
-  }
-}
-// v[n] -= sum_{i <= j} Q_i[n] h[i]
-__device__ void sub_q(const LzArgs& a, int j, const double* h, double* v) {
-  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t nt = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t n = gt; n < a.N; n += nt) {
-    double s = 0.0;
-    for (int i = 0; i <= j; ++i) s = fma(a.Q[(int64_t)i * a.N + n], h[i], s);
-    v[n] -= s;
-  }
-}
-// ||v||^2 summed in the same order by every block
-__device__ bool norm2_all(const LzArgs& a, const double* v, double* out) {
-  __shared__ double sh[32];
-  __shared__ double tot;
-  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t nt = (int64_t)gridDim.x * blockDim.x;
-  double s = 0.0;
-  for (int64_t n = gt; n < a.N; n += nt) s = fma(v[n], v[n], s);
-  s = block_sum(s, sh);
-  if (threadIdx.x == 0) a.part[blockIdx.x] = s;
-  if (!grid_barrier(a)) return false;
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) t += ((volatile double*)a.part)[b];
-    tot = t;
+    if (threadIdx.x == 0) *out_sh = s;
   }
   __syncthreads();
-  *out = tot;
-  return true;
+  return *out_sh;
 }
 
-__global__ void __launch_bounds__(256) lanczos_coop_kernel(LzArgs a) {
-  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t nt = (int64_t)gridDim.x * blockDim.x;
-  const int gw = (int)(gt >> 5), nw = (int)(nt >> 5), lane = threadIdx.x & 31;
-  __shared__ double s_scale;
+__global__ void __launch_bounds__(512, 1) lanczos_coop_kernel(LzArgs a) {
+  extern __shared__ double d_sh[];  // second-pass coefficients d_0..d_j
+  const int64_t N = a.N;
+  // work is dealt block-major (consecutive items go to different blocks) so
+  // that small N still spreads over every SM
+  const int64_t tI = (int64_t)threadIdx.x * gridDim.x + blockIdx.x;
+  const int64_t nT = (int64_t)gridDim.x * blockDim.x;
+  const int wI = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+  const int nW = (int)(nT >> 5);
+  const int lane = threadIdx.x & 31;
+  const int64_t chunk = (N + a.nchunk - 1) / a.nchunk;
+  __shared__ double s_tmp, s_scale;
+  __shared__ double sh[32];
   for (int j = a.m0; j < a.m1; ++j) {
-    const double* qj = a.Q + (int64_t)j * a.N;
-    // w = M q_j
-    for (int64_t r = gw; r < a.N; r += nw) {
-      const double* mr = a.M + r * a.N;
-      double s = 0.0;
-      for (int64_t c = lane; c < a.N; c += 32) s = fma(mr[c], qj[c], s);
-      s = warp_sum(s);
-      if (lane == 0) a.w[r] = s;
-    }
-    if (!grid_barrier(a)) return;
-    // two passes of classical Gram-Schmidt against q_0..q_j
-    dots_against_q(a, j, a.w, a.h1);
-    if (!grid_barrier(a)) return;
-    sub_q(a, j, a.h1, a.w);
-    if (!grid_barrier(a)) return;
-    dots_against_q(a, j, a.w, a.h2);
-    if (!grid_barrier(a)) return;
-    sub_q(a, j, a.h2, a.w);
-    if (!grid_barrier(a)) return;
-    double nn;
-    if (!norm2_all(a, a.w, &nn)) return;
-    const double nrm = sqrt(nn);
-    const double alph = ((volatile double*)a.h1)[j] + ((volatile double*)a.h2)[j];
+    // ---- A
+    double bprev = sqrt(sum_partials(a.npart, gridDim.x, &s_tmp));
     if (threadIdx.x == 0) {
-      double sc = fabs(alph);
+      double sc = 0.0;
       for (int i = 0; i < j; ++i)
-        sc = fmax(sc, fmax(fabs(((volatile double*)a.alpha)[i]), ((volatile double*)a.beta)[i]));
+        sc = fmax(sc, fmax(fabs(((volatile double*)a.alpha)[i]),
+                           i + 1 < j ? ((volatile double*)a.beta)[i] : 0.0));
       s_scale = sc;
     }
     __syncthreads();
-    const bool brk = !(nrm > 1e-12 * s_scale) || s_scale == 0.0;
-    const bool more = j + 1 < a.mcap;
-    double* qn = a.Q + (int64_t)(j + 1) * a.N;
-    if (more) {
-      if (!brk) {
-        const double inv = 1.0 / nrm;
-        for (int64_t n = gt; n < a.N; n += nt) qn[n] = a.w[n] * inv;
-      } else {
-        for (int64_t n = gt; n < a.N; n += nt) qn[n] = rnd_sym(a.key, (uint64_t)j * 0x100000000ull + n);
-      }
-    }
-    if (gt == 0) {
-      a.alpha[j] = alph;
-      a.beta[j] = brk ? 0.0 : nrm;
-    }
-    if (brk && more) {
-      if (!grid_barrier(a)) return;  // the random vector is complete
-      // a fresh direction orthogonal to the Krylov basis
+    if (j > 0 && (!(bprev > 1e-12 * s_scale) || s_scale == 0.0)) {
+      // breakdown: a random direction orthogonal to q_0..q_{j-1}
+      if (tI == 0) a.beta[j - 1] = 0.0;
+      for (int64_t n = tI; n < N; n += nT) a.w[n] = rnd_sym(a.key, (uint64_t)j * 0x100000000ull + n);
+      if (!grid_barrier(a)) return;
       for (int pass = 0; pass < 2; ++pass) {
-        dots_against_q(a, j, qn, a.h1);
+        for (int i = wI; i < j; i += nW) {
+          const double* qi = a.Q + (int64_t)i * N;
+          double sd = 0.0;
+          for (int64_t n = lane; n < N; n += 32) sd = fma(qi[n], a.w[n], sd);
+          sd = warp_sum(sd);
+          if (lane == 0) a.h[i] = sd;
+        }
         if (!grid_barrier(a)) return;
-        sub_q(a, j, a.h1, qn);
+        for (int64_t n = tI; n < N; n += nT) {
+          double sd = 0.0;
+          for (int i = 0; i < j; ++i) sd = fma(a.Q[(int64_t)i * N + n], ((volatile double*)a.h)[i], sd);
+          a.w[n] -= sd;
+        }
         if (!grid_barrier(a)) return;
       }
-      double q2;
-      if (!norm2_all(a, qn, &q2)) return;
-      const double inv = q2 > 0.0 ? 1.0 / sqrt(q2) : 0.0;
-      for (int64_t n = gt; n < a.N; n += nt) qn[n] *= inv;
+      double sn = 0.0;
+      for (int64_t n = tI; n < N; n += nT) sn = fma(a.w[n], a.w[n], sn);
+      sn = block_sum(sn, sh);
+      if (threadIdx.x == 0) a.npart[blockIdx.x] = sn;
+      if (!grid_barrier(a)) return;
+      bprev = sqrt(sum_partials(a.npart, gridDim.x, &s_tmp));
+    } else if (j > 0 && tI == 0) {
+      a.beta[j - 1] = bprev;
+    }
+    const double inv = bprev > 0.0 ? 1.0 / bprev : 0.0;
+    double* qj = a.Q + (int64_t)j * N;
+    for (int64_t n = tI; n < N; n += nT) qj[n] = a.w[n] * inv;
+    double* mqj = a.MQ + (int64_t)j * N;
+    // M q_j (one warp per row) and h_i = (M q_i) . q_j (one warp per i < j)
+    double hj_part = 0.0;
+    for (int64_t task = wI; task < N + j; task += nW) {
+      const double* row = task < N ? a.M + task * N : a.MQ + (task - N) * N;
+      double s0 = 0.0, s1 = 0.0;
+      int64_t c = lane;
+      for (; c + 32 < N; c += 64) {
+        s0 = fma(row[c], a.w[c], s0);
+        s1 = fma(row[c + 32], a.w[c + 32], s1);
+      }
+      if (c < N) s0 = fma(row[c], a.w[c], s0);
+      const double sr = warp_sum(s0 + s1) * inv;
+      if (lane == 0) {
+        if (task < N) {
+          mqj[task] = sr;
+          hj_part = fma(a.w[task] * inv, sr, hj_part);
+        } else {
+          a.h[task - N] = sr;
+        }
+      }
+    }
+    hj_part = block_sum(hj_part, sh);
+    if (threadIdx.x == 0) a.apart[blockIdx.x] = hj_part;
+    if (!grid_barrier(a)) return;
+    const double hj = sum_partials(a.apart, gridDim.x, &s_tmp);
+    // ---- B: w' = M q_j - sum_{i<=j} h_i q_i
+    for (int64_t n = tI; n < N; n += nT) {
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int i = 0;
+      for (; i + 3 < j; i += 4) {
+        s0 = fma(a.Q[(int64_t)i * N + n], a.h[i], s0);
+        s1 = fma(a.Q[(int64_t)(i + 1) * N + n], a.h[i + 1], s1);
+        s2 = fma(a.Q[(int64_t)(i + 2) * N + n], a.h[i + 2], s2);
+        s3 = fma(a.Q[(int64_t)(i + 3) * N + n], a.h[i + 3], s3);
+      }
+      for (; i < j; ++i) s0 = fma(a.Q[(int64_t)i * N + n], a.h[i], s0);
+      s0 = fma(qj[n], hj, s0);
+      a.wt[n] = mqj[n] - ((s0 + s1) + (s2 + s3));
     }
     if (!grid_barrier(a)) return;
+    // ---- C: partial dot products q_i . w' over chunks, one warp per (i, chunk)
+    for (int task = wI; task < (j + 1) * a.nchunk; task += nW) {
+      const int i = task / a.nchunk, ch = task % a.nchunk;
+      const int64_t n0 = ch * chunk, n1 = min(N, n0 + chunk);
+      const double* qi = a.Q + (int64_t)i * N;
+      double s0 = 0.0, s1 = 0.0;
+      int64_t n = n0 + lane;
+      for (; n + 32 < n1; n += 64) {
+        s0 = fma(qi[n], a.wt[n], s0);
+        s1 = fma(qi[n + 32], a.wt[n + 32], s1);
+      }
+      if (n < n1) s0 = fma(qi[n], a.wt[n], s0);
+      const double sr = warp_sum(s0 + s1);
+      if (lane == 0) a.dpart[(int64_t)i * a.nchunk + ch] = sr;
+    }
+    if (!grid_barrier(a)) return;
+    // ---- D: w = w' - sum_{i<=j} d_i q_i, alpha_j = d_j
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+      double di = 0.0;
+      for (int ch = 0; ch < a.nchunk; ++ch) di += a.dpart[(int64_t)i * a.nchunk + ch];
+      d_sh[i] = di;
+    }
+    __syncthreads();
+    double sn = 0.0;
+    for (int64_t n = tI; n < N; n += nT) {
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int i = 0;
+      for (; i + 3 <= j; i += 4) {
+        s0 = fma(a.Q[(int64_t)i * N + n], d_sh[i], s0);
+        s1 = fma(a.Q[(int64_t)(i + 1) * N + n], d_sh[i + 1], s1);
+        s2 = fma(a.Q[(int64_t)(i + 2) * N + n], d_sh[i + 2], s2);
+        s3 = fma(a.Q[(int64_t)(i + 3) * N + n], d_sh[i + 3], s3);
+      }
+      for (; i <= j; ++i) s0 = fma(a.Q[(int64_t)i * N + n], d_sh[i], s0);
+      const double v = a.wt[n] - ((s0 + s1) + (s2 + s3));
+      a.w[n] = v;
+      sn = fma(v, v, sn);
+    }
+    sn = block_sum(sn, sh);
+    if (threadIdx.x == 0) a.npart[blockIdx.x] = sn;
+    if (tI == 0) a.alpha[j] = hj + d_sh[j];
+    if (!grid_barrier(a)) return;
+  }
+}
+
+// Start vector: w = random unit vector, npart = (1, 0, 0, ...) so that the
+// first step reads ||w|| = 1.
+__global__ void init_start_kernel(double* w, double* npart, int nparts, int64_t N, uint64_t key) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int64_t n = threadIdx.x; n < N; n += blockDim.x) {
+    double v = rnd_sym(key, n);
+    w[n] = v;
+    s = fma(v, v, s);
+  }
+  s = block_sum(s, sh);
+  double inv = 1.0 / sqrt(s);
+  for (int64_t n = threadIdx.x; n < N; n += blockDim.x) w[n] *= inv;
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) npart[b] = b == 0 ? 1.0 : 0.0;
+}
+
+// beta of the last completed step (the coupling of T_m to the next vector)
+__global__ void last_beta_kernel(const double* npart, int nparts, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < nparts; ++b) s += npart[b];
+    *out = sqrt(s);
   }
 }
 
@@ -257,7 +356,7 @@ __device__ int sturm_count(const double* a, const double* b, int m, double x, do
   if (fabs(q) < pivmin) q = -pivmin;
   if (q < 0) ++cnt;
   for (int i = 1; i < m; ++i) {
-    q = (a[i] - x) - b[i - 1] * b[i - 1] / q;
+    q = (a[i] - x) - b[i - 1] * b[i - 1] * rcp64(q);
     if (fabs(q) < pivmin) q = -pivmin;
     if (q < 0) ++cnt;
   }
@@ -344,12 +443,12 @@ __global__ void inviter_kernel(const double* a, const double* b, int m, int k, c
         if (fabs(d[i]) >= fabs(dl[i])) {
           piv[i] = 0;
           if (fabs(d[i]) < tiny) d[i] = d[i] < 0 ? -tiny : tiny;
-          const double f = dl[i] / d[i];
+          const double f = dl[i] * rcp64(d[i]);
           dl[i] = f;
           d[i + 1] -= f * du[i];
         } else {
           piv[i] = 1;
-          const double f = d[i] / dl[i];
+          const double f = d[i] * rcp64(dl[i]);
           d[i] = dl[i];
           dl[i] = f;
           const double tmp = du[i];
@@ -362,11 +461,11 @@ __global__ void inviter_kernel(const double* a, const double* b, int m, int k, c
         }
       }
       if (fabs(d[m - 1]) < tiny) d[m - 1] = d[m - 1] < 0 ? -tiny : tiny;
-      for (int i = 0; i < m; ++i) d[i] = 1.0 / d[i];  // the solves multiply
+      for (int i = 0; i < m; ++i) d[i] = rcp64(d[i]);  // the solves multiply
     }
     for (int i = threadIdx.x; i < m; i += blockDim.x) y[i] = 1.0 + 0.25 * rnd_sym(key + c, i);
     __syncthreads();
-    for (int it = 0; it < 4; ++it) {
+    for (int it = 0; it < 3; ++it) {
       if (threadIdx.x == 0) {
         for (int i = 0; i < m - 1; ++i) {
           if (piv[i]) {
@@ -495,8 +594,13 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   double* DD = ar.take<double>(N * N);
   double* AA = ar.take<double>(N * N);
   double* G = ar.take<double>(N * P);
-  double* Q = AA;  // reused once the Gram matrix is formed (mcap <= N)
+  double* Q = AA;   // reused once the Gram matrix is formed (mcap <= N)
+  double* MQ = DD;  // likewise
   double* w = ar.take<double>(N);
+  double* wt = ar.take<double>(N);
+  double* dpart = ar.take<double>((mcap + 1) * 8);
+  double* npart = ar.take<double>(4096);
+  double* apart = ar.take<double>(4096);
   double* h1 = ar.take<double>(mcap + 1);
   double* h2 = ar.take<double>(mcap + 1);
   double* alpha = ar.take<double>(mcap + 1);
@@ -505,8 +609,7 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   double* Y = ar.take<double>((int64_t)k * mcap);
   double* U = ar.take<double>(N * k);
   double* scratch = ar.take<double>((int64_t)k * 5 * (mcap + 1));
-  double* part = ar.take<double>(4096);
-  unsigned* bar = ar.take<unsigned>(4);
+  unsigned* bar = ar.take<unsigned>(64);
   int* err = ar.take<int>(1);
   int* cstart = ar.take<int>(k);
   double* rr = ar.take<double>(k);
@@ -550,14 +653,18 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   // 2-3. Lanczos with full reorthogonalisation, extended until the top-k
   // residual bounds converge
   const uint64_t key = 0x5DEECE66Dull;
-  init_start_kernel<<<1, 1024, 0, s>>>(Q, N, key);
-  HM_LAUNCHED();
-  HM_CUDA(cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), s));
-  HM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
   int per_sm = 0;
-  HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lanczos_coop_kernel, 256, 0));
+  const size_t dyn = (size_t)(mcap + 1) * sizeof(double);
+  if (dyn > 48 * 1024)
+    HM_CUDA(cudaFuncSetAttribute(lanczos_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+  HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lanczos_coop_kernel, 512, dyn));
   if (per_sm < 1) return set_error(HESS_ERR_CUDA, "Lanczos kernel cannot be resident");
-  const int grid = (per_sm < 2 ? per_sm : 2) * h->sm_count;
+  const int grid = h->sm_count;
+  init_start_kernel<<<1, 1024, 0, s>>>(w, npart, grid, N, key);
+  HM_LAUNCHED();
+  HM_CUDA(cudaMemsetAsync(bar, 0, 64 * sizeof(unsigned), s));
+  HM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  const int nchunk = (int)(N < 1024 ? cdiv(N, 128) : 8);
   int m = 0;
   int64_t target = N < (int64_t)2 * k + 32 ? N : (int64_t)2 * k + 32;
   if (target < k) target = k;
@@ -568,31 +675,35 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
     la.M = M;
     la.N = N;
     la.Q = Q;
+    la.MQ = MQ;
     la.w = w;
-    la.h1 = h1;
-    la.h2 = h2;
+    la.wt = wt;
+    la.h = h1;
+    la.dpart = dpart;
+    la.npart = npart;
+    la.apart = apart;
     la.alpha = alpha;
     la.beta = beta;
-    la.part = part;
-    la.bar_count = bar;
-    la.bar_gen = bar + 1;
+    la.bar = bar;
     la.err = err;
     la.m0 = m;
     la.m1 = (int)target;
     la.mcap = (int)mcap;
+    la.nchunk = nchunk < 1 ? 1 : nchunk;
     la.key = key + 7;
     void* kargs[] = {&la};
-    HM_CUDA(cudaLaunchCooperativeKernel((void*)lanczos_coop_kernel, grid, 256, kargs, 0, s));
+    HM_CUDA(cudaLaunchCooperativeKernel((void*)lanczos_coop_kernel, grid, 512, kargs, dyn, s));
     HM_LAUNCHED();
     m = (int)target;
+    last_beta_kernel<<<1, 32, 0, s>>>(npart, grid, h2);
+    HM_LAUNCHED();
     bisect_kernel<<<(unsigned)cdiv(k, 4), 128, 0, s>>>(alpha, beta, m, k, theta);
     HM_LAUNCHED();
-    // the cluster tolerance of inverse iteration: 1e-3 of ||T||, bounded by
-    // the largest Ritz value (T is positive semi-definite here)
-    clusters_kernel<<<1, 32, 0, s>>>(theta, k, 1e-3, cstart);
+    // eigenvalues closer than 1e-6 of the largest share a cluster
+    clusters_kernel<<<1, 32, 0, s>>>(theta, k, 1e-6, cstart);
     HM_LAUNCHED();
-    inviter_kernel<<<k, 256, 0, s>>>(alpha, beta, m, k, theta, cstart, Y, mcap, scratch,
-                                     beta + (m - 1), rr, key + 11);
+    inviter_kernel<<<k, 256, 0, s>>>(alpha, beta, m, k, theta, cstart, Y, mcap, scratch, h2, rr,
+                                     key + 11);
     HM_LAUNCHED();
     max_res_kernel<<<1, 32, 0, s>>>(rr, k, theta, mx);
     HM_LAUNCHED();
@@ -601,7 +712,7 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
     HM_CUDA(cudaStreamSynchronize(s));
     if (*reinterpret_cast<int*>(hp + 2))
       return set_error(HESS_ERR_TIMEOUT, "Lanczos grid barrier gave up");
-    if (hp[0] <= 1e-11 * hp[1] || m >= N) {
+    if (hp[0] <= 1e-10 * hp[1] || m >= N) {
       converged = true;
       break;
     }

@@ -2,6 +2,8 @@
 // backward passes of the MLP, the per-example gradient writer, the batched
 // R-operator over blocks of unit directions, and the symmetric scatter that
 // places Hessian row blocks and their mirror images.
+#include <type_traits>
+
 #include "internal.h"
 
 namespace hm {
@@ -16,6 +18,10 @@ struct GemmCfg<double> {
 template <>
 struct GemmCfg<float> {
   static constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8;
+};
+// narrow outputs (<= 32 columns, e.g. the k eigenvector columns)
+struct GemmCfgNarrow64 {
+  static constexpr int BM = 128, BN = 32, BK = 16, TM = 8, TN = 2;
 };
 
 // Row of the upper-triangular tile enumeration: row r holds nt - r tiles and
@@ -182,10 +188,8 @@ template hess_status colsum<double>(const double*, int64_t, int64_t, int64_t, do
 template hess_status colsum<float>(const float*, int64_t, int64_t, int64_t, float, float*, int64_t,
                                    cudaStream_t);
 
-template <typename T>
-hess_status gemm(const Gemm<T>& g, cudaStream_t s) {
-  using Cfg = GemmCfg<T>;
-  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return HESS_OK;
+template <typename T, typename Cfg>
+static hess_status gemm_cfg(const Gemm<T>& g, cudaStream_t s) {
   if (g.batch > 65535) return set_error(HESS_ERR_INVALID_ARG, "gemm batch %d too large", g.batch);
   int64_t tiles;
   dim3 grid;
@@ -228,6 +232,12 @@ hess_status gemm(const Gemm<T>& g, cudaStream_t s) {
   gemm_kernel<T, Cfg::BM, Cfg::BN, Cfg::BK, Cfg::TM, Cfg::TN><<<grid, 256, 0, s>>>(g, 1, nullptr);
   HM_LAUNCHED();
   return HESS_OK;
+}
+template <typename T>
+hess_status gemm(const Gemm<T>& g, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return HESS_OK;
+  if (std::is_same<T, double>::value && !g.upper && g.N <= 32) return gemm_cfg<T, GemmCfgNarrow64>(g, s);
+  return gemm_cfg<T, GemmCfg<T>>(g, s);
 }
 template hess_status gemm<double>(const Gemm<double>&, cudaStream_t);
 template hess_status gemm<float>(const Gemm<float>&, cudaStream_t);

@@ -7,8 +7,9 @@
 // The accumulator is double-buffered in TMEM (2 x 256 fp32 columns) so the
 // epilogue of one tile overlaps the main loop of the next.
 //
-// Split-BF16 ("x3") products run as one K loop over three passes of the same
-// k-block: hi*hi, hi*lo and lo*hi accumulate into the same FP32 accumulator.
+// Split-BF16 ("x3") products: one stage holds A_hi, A_lo, B_hi and B_lo of a
+// k-block and the MMA thread issues hi*hi, hi*lo and lo*hi from it into the
+// same FP32 accumulator.
 //
 // Both users write a symmetric matrix from row blocks: an entry computed at
 // (orow, ocol) is stored directly when ocol >= orow and mirrored to
@@ -28,14 +29,16 @@ namespace tc {
 constexpr int BM = 128;  // UMMA M (rows of A per tile = TMEM lanes)
 constexpr int BK = 64;   // bf16 elements per 128-byte swizzle row
 constexpr int MAXBN = 256;
-constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = MAXBN * BK * 2;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+// operand ring: BF16 runs 4 stages of {A, B}; split-BF16 runs 2 stages of
+// {A_hi, A_lo, B_hi, B_lo} and issues the three products from one stage
+constexpr int RING_BYTES = 4 * (A_BYTES + B_BYTES);
+constexpr int MAXSTAGES = 4;
 constexpr int EPI_LD = 17;  // 16 columns + 1 pad
 constexpr int EPI_BYTES = 4 * 32 * EPI_LD * 4;
 constexpr int BAR_BYTES = 256;
-constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + EPI_BYTES + BAR_BYTES;
+constexpr int SMEM_BYTES = 1024 + RING_BYTES + EPI_BYTES + BAR_BYTES;
 constexpr int THREADS = 192;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr long long TIMEOUT_CYCLES = 4000000000ll;  // ~2 s at 2 GHz
@@ -45,7 +48,7 @@ struct Params {
   int64_t Nn;     // valid rows of B (= columns of the product)
   int BN;         // tile columns (multiple of 16, <= 256)
   int nkb;        // k-blocks of 64
-  int passes;     // 1: hi*hi;  3: hi*hi + hi*lo + lo*hi
+  int passes;     // 1: hi*hi;  3: hi*hi + hi*lo + lo*hi (one stage holds all four tiles)
   uint32_t idesc; // instruction descriptor
   const int2* tiles;
   int ntiles;
@@ -198,16 +201,22 @@ __global__ void __launch_bounds__(THREADS, 1)
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  float* epi = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES + EPI_BYTES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
+  float* epi = reinterpret_cast<float*>(smem + RING_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + RING_BYTES + EPI_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * MAXSTAGES + 4);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
+  const bool x3 = p.passes == 3;
+  const int STAGES = x3 ? 2 : 4;
+  const int STAGE_BYTES = x3 ? 2 * (A_BYTES + B_BYTES) : (A_BYTES + B_BYTES);
+  // offsets inside a stage (all multiples of 1024 bytes)
+  const int OFF_ALO = A_BYTES, OFF_BHI = x3 ? 2 * A_BYTES : A_BYTES,
+            OFF_BLO = 2 * A_BYTES + B_BYTES;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   auto full = [&](int s) { return smem_u32(bars + s); };
-  auto empty = [&](int s) { return smem_u32(bars + STAGES + s); };
-  auto tfull = [&](int a) { return smem_u32(bars + 2 * STAGES + a); };
-  auto tempty = [&](int a) { return smem_u32(bars + 2 * STAGES + 2 + a); };
+  auto empty = [&](int s) { return smem_u32(bars + MAXSTAGES + s); };
+  auto tfull = [&](int a) { return smem_u32(bars + 2 * MAXSTAGES + a); };
+  auto tempty = [&](int a) { return smem_u32(bars + 2 * MAXSTAGES + 2 + a); };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -234,8 +243,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  const int nvk = p.nkb * p.passes;
-  const uint32_t tx_bytes = A_BYTES + p.BN * BK * 2;
+  const int nvk = p.nkb;
+  const uint32_t tx_bytes = (A_BYTES + p.BN * BK * 2) * (x3 ? 2 : 1);
 
   if (warp == 0) {
     if (lane == 0) {
@@ -250,12 +259,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             ok = false;
             break;
           }
-          const int kb = j / p.passes, pass = j % p.passes;
-          uint8_t* a_s = smem + s * STAGE_BYTES;
-          uint8_t* b_s = a_s + A_BYTES;
+          uint8_t* st = smem + s * STAGE_BYTES;
           mbar_expect_tx(full(s), tx_bytes);
-          tma_load_2d(smem_u32(a_s), pass == 2 ? &tmA_lo : &tmA_hi, kb * BK, tile.x * BM, full(s));
-          tma_load_2d(smem_u32(b_s), pass == 1 ? &tmB_lo : &tmB_hi, kb * BK, tile.y * p.BN, full(s));
+          tma_load_2d(smem_u32(st), &tmA_hi, j * BK, tile.x * BM, full(s));
+          tma_load_2d(smem_u32(st + OFF_BHI), &tmB_hi, j * BK, tile.y * p.BN, full(s));
+          if (x3) {
+            tma_load_2d(smem_u32(st + OFF_ALO), &tmA_lo, j * BK, tile.x * BM, full(s));
+            tma_load_2d(smem_u32(st + OFF_BLO), &tmB_lo, j * BK, tile.y * p.BN, full(s));
+          }
         }
       }
       if (!ok) {
@@ -287,12 +298,20 @@ __global__ void __launch_bounds__(THREADS, 1)
             break;
           }
           tc_fence_after();
-          const uint8_t* a_s = smem + s * STAGE_BYTES;
-          const uint64_t ad = sdesc(smem_u32(a_s));
-          const uint64_t bd = sdesc(smem_u32(a_s + A_BYTES));
+          const uint8_t* st = smem + s * STAGE_BYTES;
+          const uint64_t ah = sdesc(smem_u32(st));
+          const uint64_t bh = sdesc(smem_u32(st + OFF_BHI));
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk)
-            umma_bf16(d_tmem, ad + 2 * kk, bd + 2 * kk, p.idesc, (j > 0 || kk > 0) ? 1u : 0u);
+            umma_bf16(d_tmem, ah + 2 * kk, bh + 2 * kk, p.idesc, (j > 0 || kk > 0) ? 1u : 0u);
+          if (x3) {
+            const uint64_t al = sdesc(smem_u32(st + OFF_ALO));
+            const uint64_t bl = sdesc(smem_u32(st + OFF_BLO));
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) umma_bf16(d_tmem, ah + 2 * kk, bl + 2 * kk, p.idesc, 1u);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) umma_bf16(d_tmem, al + 2 * kk, bh + 2 * kk, p.idesc, 1u);
+          }
           umma_commit(empty(s));
         }
         if (ok) umma_commit(tfull(acc));
