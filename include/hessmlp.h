@@ -154,6 +154,30 @@ HESS_API hess_status opg_topk_eig(hess_mlp* h, const void* X, const void* Y, int
  * followed by its bias ([W_i,: , b_i] for every layer).  perm has P entries. */
 HESS_API hess_status hess_param_permutation(int L, const int* widths, int64_t* perm);
 
+/* Allocation-free per-example gradients (no counterpart in the paper).
+ *
+ * For callers that cannot call cudaMalloc -- their device memory belongs to
+ * another allocator (a framework's caching allocator, a fixed pool with a hard
+ * budget), or they run a latency-bound loop where an allocation, with its
+ * implicit synchronisation and possible failure, is not acceptable.  Computes
+ * the same G as per_example_grads in FP64 (N x P row-major, one row per
+ * example) without a handle and without allocating: desc describes the
+ * network (validated as in hess_mlp_create); omega (P doubles), X (N x T_1),
+ * Y (N x T_L) and G (N x P) must all be device memory on the current device.
+ * The forward/backward caches live in a file-scope device array of 32 MiB
+ * that every GPU loading the library holds until the process exits; a request
+ * whose caches exceed it, N * (4 (T_2 + ... + T_{L-1}) + (T_2 + ... + T_L) +
+ * T_L + max_l T_l + 1) doubles plus alignment, is rejected with
+ * HESS_ERR_INVALID_ARG before any GPU work.  The first call on a device looks
+ * up that array's device address (cudaGetSymbolAddress) with the device
+ * current; make that first call before any stream capture.  Work is queued on
+ * `stream` (a cudaStream_t, NULL = legacy default stream) and the call returns
+ * without waiting.  All calls share the array: calls whose work overlaps on
+ * the GPU (on different streams or from different threads) race on it. */
+HESS_API hess_status per_example_grads_noalloc(const hess_mlp_desc* desc, const double* omega,
+                                               const double* X, const double* Y, int64_t N,
+                                               double* G, void* stream);
+
 /* ----------------------------------------------------------------------
  * Measurement hooks (no counterpart in the paper).  When timing is enabled
  * the library brackets every launch of the kernel classes below with CUDA

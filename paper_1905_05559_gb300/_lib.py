@@ -32,7 +32,7 @@ EXPORTS = (
     "hess_mlp_create", "hess_mlp_destroy", "hess_mlp_num_params", "hess_mlp_set_params",
     "hess_mlp_set_stream", "per_example_grads", "opg", "exact_hessian", "opg_topk_eig",
     "hess_param_permutation", "hess_last_error", "hess_timing_enable", "hess_timing_read",
-    "hess_launch_count",
+    "hess_launch_count", "per_example_grads_noalloc",
 )
 
 KERNEL_CLASS = {"syrk": 0, "hcontract": 1, "grads": 2, "rop": 3, "eig": 4, "hrest": 5}
@@ -91,6 +91,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.hess_timing_enable.restype = st
     lib.hess_timing_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(KernelStats)]
     lib.hess_timing_read.restype = st
+    lib.per_example_grads_noalloc.argtypes = [ctypes.POINTER(HessDesc), vp, vp, vp, i64, vp, vp]
+    lib.per_example_grads_noalloc.restype = st
     lib.hess_launch_count.argtypes = []
     lib.hess_launch_count.restype = ctypes.c_int64
     lib.hess_last_error.argtypes = []

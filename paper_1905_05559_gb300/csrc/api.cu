@@ -51,6 +51,37 @@ hess_status set_error(hess_status s, const char* fmt, ...) {
 }
 void clear_error() { g_err[0] = 0; }
 
+hess_status make_net(const hess_mlp_desc* desc, Net* out) {
+  if (!desc) return set_error(HESS_ERR_INVALID_ARG, "desc is NULL");
+  if (desc->L < 2 || !desc->widths) return set_error(HESS_ERR_INVALID_ARG, "need L >= 2 and widths");
+  if (desc->L > kMaxLayers) return set_error(HESS_ERR_INVALID_ARG, "at most %d layers", kMaxLayers);
+  if (desc->L > 2 && !desc->act) return set_error(HESS_ERR_INVALID_ARG, "hidden activations missing");
+  Net net;
+  net.L = desc->L;
+  for (int l = 0; l < desc->L; ++l) {
+    if (desc->widths[l] < 1 || desc->widths[l] > (1 << 20))
+      return set_error(HESS_ERR_INVALID_ARG, "width T_%d = %d out of range", l + 1, desc->widths[l]);
+    net.T[l] = desc->widths[l];
+  }
+  if (net.T[net.L - 1] < 2) return set_error(HESS_ERR_INVALID_ARG, "softmax output needs T_L >= 2");
+  for (int l = 0; l < desc->L - 2; ++l) {
+    int a = desc->act[l];
+    if (a < HESS_ACT_SIGMOID || a > HESS_ACT_RELU)
+      return set_error(HESS_ERR_INVALID_ARG, "unknown activation %d for layer %d", a, l + 2);
+    net.act[l] = a;
+  }
+  int64_t o = 0;
+  for (int w = 1; w < net.L; ++w) {
+    net.woff[w - 1] = o;
+    net.boff[w - 1] = o + (int64_t)net.T[w - 1] * net.T[w];
+    o += (int64_t)net.T[w - 1] * net.T[w] + net.T[w];
+  }
+  net.P = o;
+  if (net.P > (1ll << 31) - 1) return set_error(HESS_ERR_INVALID_ARG, "P = %lld too large", (long long)net.P);
+  *out = net;
+  return HESS_OK;
+}
+
 hess_status ensure_ws(hess_mlp* h, size_t bytes) {
   if (bytes <= h->ws_bytes) return HESS_OK;
   if (h->ws) {
@@ -435,30 +466,8 @@ hess_status hess_mlp_create(const hess_mlp_desc* desc, const double* omega, void
   clear_error();
   if (!desc || !out || !omega) return set_error(HESS_ERR_INVALID_ARG, "desc, omega and out must be non-NULL");
   *out = nullptr;
-  if (desc->L < 2 || !desc->widths) return set_error(HESS_ERR_INVALID_ARG, "need L >= 2 and widths");
-  if (desc->L > 2 && !desc->act) return set_error(HESS_ERR_INVALID_ARG, "hidden activations missing");
   Net net;
-  net.L = desc->L;
-  for (int l = 0; l < desc->L; ++l) {
-    if (desc->widths[l] < 1 || desc->widths[l] > (1 << 20))
-      return set_error(HESS_ERR_INVALID_ARG, "width T_%d = %d out of range", l + 1, desc->widths[l]);
-    net.T.push_back(desc->widths[l]);
-  }
-  if (net.T[net.L - 1] < 2) return set_error(HESS_ERR_INVALID_ARG, "softmax output needs T_L >= 2");
-  for (int l = 0; l < desc->L - 2; ++l) {
-    int a = desc->act[l];
-    if (a < HESS_ACT_SIGMOID || a > HESS_ACT_RELU)
-      return set_error(HESS_ERR_INVALID_ARG, "unknown activation %d for layer %d", a, l + 2);
-    net.act.push_back(a);
-  }
-  int64_t o = 0;
-  for (int w = 1; w < net.L; ++w) {
-    net.woff.push_back(o);
-    net.boff.push_back(o + (int64_t)net.T[w - 1] * net.T[w]);
-    o += (int64_t)net.T[w - 1] * net.T[w] + net.T[w];
-  }
-  net.P = o;
-  if (net.P > (1ll << 31) - 1) return set_error(HESS_ERR_INVALID_ARG, "P = %lld too large", (long long)net.P);
+  HM_TRY(make_net(desc, &net));
   hess_mlp* h = new hess_mlp();
   h->net = net;
   h->stream = (cudaStream_t)stream;

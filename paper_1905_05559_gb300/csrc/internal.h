@@ -58,14 +58,21 @@ struct Arena {
 };
 
 // --------------------------------------------------------------- network ----
+constexpr int kMaxLayers = 32;
+
+// Fixed-capacity description (no heap use, so it can be built by every entry
+// point, including the allocation-free one).
 struct Net {
   int L = 0;
-  std::vector<int> T;         // widths T_1..T_L stored at T[0..L-1]
-  std::vector<int> act;       // hidden activations for layers 2..L-1 at act[0..L-3]
-  std::vector<int64_t> woff;  // offset of W^(j) (j = 1..L-1) at woff[j-1]
-  std::vector<int64_t> boff;  // offset of b^(j+1) at boff[j-1]
+  int T[kMaxLayers] = {};        // widths T_1..T_L stored at T[0..L-1]
+  int act[kMaxLayers] = {};      // hidden activations for layers 2..L-1 at act[0..L-3]
+  int64_t woff[kMaxLayers] = {}; // offset of W^(j) (j = 1..L-1) at woff[j-1]
+  int64_t boff[kMaxLayers] = {}; // offset of b^(j+1) at boff[j-1]
   int64_t P = 0;
 };
+
+// Validate a description and fill a Net (HESS_ERR_INVALID_ARG on failure).
+hess_status make_net(const hess_mlp_desc* desc, Net* net);
 
 }  // namespace hm
 
@@ -154,13 +161,14 @@ hess_status colsum(const T* A, int64_t lda, int64_t R, int64_t K, T alpha, T* ou
 template <typename T>
 struct Caches {
   int64_t N = 0;
-  std::vector<const T*> a;  // a[j] j = 0..L-2 (a[0] = X)
-  std::vector<T*> s1, s2;   // sigma', sigma'' for hidden positions j = 1..L-2
-  std::vector<T*> d;        // delta for positions j = 1..L-1
-  std::vector<T*> e;        // W^T delta before sigma' for hidden j
-  T* p = nullptr;           // softmax output N x T_L
-  T* ysum = nullptr;        // row sums of Y (N)
-  T* z = nullptr;           // scratch for pre-activations (N x max T)
+  const T* a[kMaxLayers] = {};  // a[j] j = 0..L-2 (a[0] = X)
+  T* s1[kMaxLayers] = {};       // sigma' for hidden positions j = 1..L-2
+  T* s2[kMaxLayers] = {};       // sigma''
+  T* d[kMaxLayers] = {};        // delta for positions j = 1..L-1
+  T* e[kMaxLayers] = {};        // W^T delta before sigma' for hidden j
+  T* p = nullptr;               // softmax output N x T_L
+  T* ysum = nullptr;            // row sums of Y (N)
+  T* z = nullptr;               // scratch for pre-activations (N x max T)
 };
 template <typename T>
 void plan_caches(Arena& ar, const Net& net, int64_t N, Caches<T>& c);

@@ -373,11 +373,6 @@ template <typename T>
 void plan_caches(Arena& ar, const Net& net, int64_t N, Caches<T>& c) {
   const int L = net.L;
   c.N = N;
-  c.a.assign(L - 1, nullptr);
-  c.s1.assign(L, nullptr);
-  c.s2.assign(L, nullptr);
-  c.e.assign(L, nullptr);
-  c.d.assign(L, nullptr);
   int maxT = 0;
   for (int j = 0; j < L; ++j) maxT = net.T[j] > maxT ? net.T[j] : maxT;
   for (int j = 1; j <= L - 2; ++j) {
