@@ -47,6 +47,16 @@ __device__ __forceinline__ double rcp64(double x) {
   return fma(r, e, r);
 }
 
+// 1/x to about 2^-46 relative (one Newton-Raphson step): enough for the
+// inertia counts of the Sturm sequence, which tolerate relative perturbations
+// of this size.
+__device__ __forceinline__ double rcp64_sign(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  const double e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
 // sum over a block of up to 1024 threads
 __device__ double block_sum(double v, double* sh) {
   v = warp_sum(v);
@@ -99,50 +109,44 @@ struct LzArgs {
   double* apart; // [gridDim] partial sums of q_j . (M q_j)
   double* alpha;
   double* beta;
-  unsigned* bar;  // [0]: generation, [1..]: group arrival counters
+  unsigned* bar;  // [0]: published epoch, [1]: arrival counter
   int* err;
   int m0, m1, mcap, nchunk;
   uint64_t key;
 };
 
 constexpr long long BAR_TIMEOUT = 4000000000ll;
-constexpr int BAR_GROUP = 16;
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ unsigned atom_add_acqrel(unsigned* p, unsigned v) {
-  unsigned old;
-  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-  return old;
-}
 
-// Two-level arrival (groups of BAR_GROUP blocks, then the groups), one
-// generation word that every block polls.
-__device__ bool grid_barrier(const LzArgs& a) {
+// Grid barrier: every block adds 1 to a monotonic arrival counter with a
+// release reduction; block 0 waits for epoch * gridDim.x arrivals and then
+// publishes the epoch, which the other blocks poll with acquire loads.  Each
+// block counts its own epochs (the counters start at zero for every launch).
+__device__ bool grid_barrier(const LzArgs& a, unsigned& epoch) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
-    const unsigned g = ld_acquire(a.bar);
-    const unsigned ngroups = (gridDim.x + BAR_GROUP - 1) / BAR_GROUP;
-    const unsigned grp = blockIdx.x / BAR_GROUP;
-    const unsigned gsize = min((unsigned)BAR_GROUP, gridDim.x - grp * BAR_GROUP);
-    unsigned* gcount = a.bar + 2 + grp;
-    bool last = false;
-    if (atom_add_acqrel(gcount, 1u) == gsize - 1) {
-      asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(gcount) : "memory");
-      if (atom_add_acqrel(a.bar + 1, 1u) == ngroups - 1) {
-        asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(a.bar + 1) : "memory");
-        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(a.bar), "r"(g + 1) : "memory");
-        last = true;
+    ++epoch;
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(a.bar + 1) : "memory");
+    const long long t0 = clock64();
+    if (blockIdx.x == 0) {
+      const unsigned want = epoch * gridDim.x;
+      while (ld_acquire(a.bar + 1) < want) {
+        if (clock64() - t0 > BAR_TIMEOUT || *(volatile int*)a.err) {
+          atomicExch(a.err, 1);
+          ok = 0;
+          break;
+        }
       }
-    }
-    if (!last) {
-      const long long t0 = clock64();
-      while (ld_acquire(a.bar) == g) {
+      if (ok) asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(a.bar), "r"(epoch) : "memory");
+    } else {
+      while (ld_acquire(a.bar) < epoch) {
         if (clock64() - t0 > BAR_TIMEOUT || *(volatile int*)a.err) {
           atomicExch(a.err, 1);
           ok = 0;
@@ -153,6 +157,55 @@ __device__ bool grid_barrier(const LzArgs& a) {
   }
   __syncthreads();
   return ok != 0;
+}
+
+// sum_c x[c] y[c] over one warp, eight independent accumulators per lane so
+// that eight loads per lane are in flight
+__device__ __forceinline__ double warp_dot(const double* x, const double* y, int64_t n0, int64_t n1) {
+  const int lane = threadIdx.x & 31;
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t c = n0 + lane;
+  for (; c + 7 * 32 < n1; c += 8 * 32) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = fma(x[c + u * 32], y[c + u * 32], acc[u]);
+  }
+  for (; c < n1; c += 32) acc[0] = fma(x[c], y[c], acc[0]);
+  const double s = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+  return warp_sum(s);
+}
+
+// For the 32-entry chunks starting at blockIdx.x * 32, step gridDim.x * 32:
+// out[n] = base[n] - sum_{i < nv} Q_i[n] coef[i].  The block's warps split the
+// i range (independent loads in flight), partial sums meet in shared memory.
+__device__ void subtract_combination(const double* Q, int64_t N, const double* coef, int nv,
+                                     const double* base, double* out, double* red, double* sqnorm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  double nn = 0.0;
+  for (int64_t c0 = (int64_t)blockIdx.x * 32; c0 < N; c0 += (int64_t)gridDim.x * 32) {
+    const int64_t n = c0 + lane;
+    double s0 = 0.0, s1 = 0.0;
+    if (n < N) {
+      int i = warp;
+      for (; i + nwarp < nv; i += 2 * nwarp) {
+        s0 = fma(Q[(int64_t)i * N + n], coef[i], s0);
+        s1 = fma(Q[(int64_t)(i + nwarp) * N + n], coef[i + nwarp], s1);
+      }
+      if (i < nv) s0 = fma(Q[(int64_t)i * N + n], coef[i], s0);
+    }
+    red[warp * 32 + lane] = s0 + s1;
+    __syncthreads();
+    if (warp == 0) {
+      double t = 0.0;
+      for (int w = 0; w < nwarp; ++w) t += red[w * 32 + lane];
+      if (n < N) {
+        const double v = base[n] - t;
+        out[n] = v;
+        nn = fma(v, v, nn);
+      }
+    }
+    __syncthreads();
+  }
+  if (sqnorm) *sqnorm = nn;  // meaningful in warp 0
 }
 
 // sum_b npart[b] by warp 0 of the block (same order in every block)
@@ -180,22 +233,25 @@ __global__ void __launch_bounds__(512, 1) lanczos_coop_kernel(LzArgs a) {
   const int64_t chunk = (N + a.nchunk - 1) / a.nchunk;
   __shared__ double s_tmp, s_scale;
   __shared__ double sh[32];
+  __shared__ double red_sh[16 * 32];
+  unsigned epoch = 0;  // meaningful in thread 0 only
+  // running scale of T (max |alpha_i|, beta_i so far), kept per block
+  if (threadIdx.x == 0) {
+    double sc = 0.0;
+    for (int i = 0; i < a.m0; ++i)
+      sc = fmax(sc, fmax(fabs(a.alpha[i]), i + 1 < a.m0 ? a.beta[i] : 0.0));
+    s_scale = sc;
+  }
+  __syncthreads();
   for (int j = a.m0; j < a.m1; ++j) {
     // ---- A
     double bprev = sqrt(sum_partials(a.npart, gridDim.x, &s_tmp));
-    if (threadIdx.x == 0) {
-      double sc = 0.0;
-      for (int i = 0; i < j; ++i)
-        sc = fmax(sc, fmax(fabs(((volatile double*)a.alpha)[i]),
-                           i + 1 < j ? ((volatile double*)a.beta)[i] : 0.0));
-      s_scale = sc;
-    }
-    __syncthreads();
-    if (j > 0 && (!(bprev > 1e-12 * s_scale) || s_scale == 0.0)) {
+    const bool brk = j > 0 && (!(bprev > 1e-12 * s_scale) || s_scale == 0.0);
+    if (brk) {
       // breakdown: a random direction orthogonal to q_0..q_{j-1}
       if (tI == 0) a.beta[j - 1] = 0.0;
       for (int64_t n = tI; n < N; n += nT) a.w[n] = rnd_sym(a.key, (uint64_t)j * 0x100000000ull + n);
-      if (!grid_barrier(a)) return;
+      if (!grid_barrier(a, epoch)) return;
       for (int pass = 0; pass < 2; ++pass) {
         for (int i = wI; i < j; i += nW) {
           const double* qi = a.Q + (int64_t)i * N;
@@ -204,23 +260,25 @@ __global__ void __launch_bounds__(512, 1) lanczos_coop_kernel(LzArgs a) {
           sd = warp_sum(sd);
           if (lane == 0) a.h[i] = sd;
         }
-        if (!grid_barrier(a)) return;
+        if (!grid_barrier(a, epoch)) return;
         for (int64_t n = tI; n < N; n += nT) {
           double sd = 0.0;
           for (int i = 0; i < j; ++i) sd = fma(a.Q[(int64_t)i * N + n], ((volatile double*)a.h)[i], sd);
           a.w[n] -= sd;
         }
-        if (!grid_barrier(a)) return;
+        if (!grid_barrier(a, epoch)) return;
       }
       double sn = 0.0;
       for (int64_t n = tI; n < N; n += nT) sn = fma(a.w[n], a.w[n], sn);
       sn = block_sum(sn, sh);
       if (threadIdx.x == 0) a.npart[blockIdx.x] = sn;
-      if (!grid_barrier(a)) return;
+      if (!grid_barrier(a, epoch)) return;
       bprev = sqrt(sum_partials(a.npart, gridDim.x, &s_tmp));
     } else if (j > 0 && tI == 0) {
       a.beta[j - 1] = bprev;
     }
+    __syncthreads();  // every thread has read s_scale
+    if (threadIdx.x == 0 && j > 0 && !brk) s_scale = fmax(s_scale, bprev);
     const double inv = bprev > 0.0 ? 1.0 / bprev : 0.0;
     double* qj = a.Q + (int64_t)j * N;
     for (int64_t n = tI; n < N; n += nT) qj[n] = a.w[n] * inv;
@@ -229,14 +287,7 @@ __global__ void __launch_bounds__(512, 1) lanczos_coop_kernel(LzArgs a) {
     double hj_part = 0.0;
     for (int64_t task = wI; task < N + j; task += nW) {
       const double* row = task < N ? a.M + task * N : a.MQ + (task - N) * N;
-      double s0 = 0.0, s1 = 0.0;
-      int64_t c = lane;
-      for (; c + 32 < N; c += 64) {
-        s0 = fma(row[c], a.w[c], s0);
-        s1 = fma(row[c + 32], a.w[c + 32], s1);
-      }
-      if (c < N) s0 = fma(row[c], a.w[c], s0);
-      const double sr = warp_sum(s0 + s1) * inv;
+      const double sr = warp_dot(row, a.w, 0, N) * inv;
       if (lane == 0) {
         if (task < N) {
           mqj[task] = sr;
@@ -248,40 +299,23 @@ __global__ void __launch_bounds__(512, 1) lanczos_coop_kernel(LzArgs a) {
     }
     hj_part = block_sum(hj_part, sh);
     if (threadIdx.x == 0) a.apart[blockIdx.x] = hj_part;
-    if (!grid_barrier(a)) return;
+    if (!grid_barrier(a, epoch)) return;
     const double hj = sum_partials(a.apart, gridDim.x, &s_tmp);
     // ---- B: w' = M q_j - sum_{i<=j} h_i q_i
-    for (int64_t n = tI; n < N; n += nT) {
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      int i = 0;
-      for (; i + 3 < j; i += 4) {
-        s0 = fma(a.Q[(int64_t)i * N + n], a.h[i], s0);
-        s1 = fma(a.Q[(int64_t)(i + 1) * N + n], a.h[i + 1], s1);
-        s2 = fma(a.Q[(int64_t)(i + 2) * N + n], a.h[i + 2], s2);
-        s3 = fma(a.Q[(int64_t)(i + 3) * N + n], a.h[i + 3], s3);
-      }
-      for (; i < j; ++i) s0 = fma(a.Q[(int64_t)i * N + n], a.h[i], s0);
-      s0 = fma(qj[n], hj, s0);
-      a.wt[n] = mqj[n] - ((s0 + s1) + (s2 + s3));
-    }
-    if (!grid_barrier(a)) return;
+    if (threadIdx.x == 0) d_sh[j] = hj;
+    for (int i = threadIdx.x; i < j; i += blockDim.x) d_sh[i] = a.h[i];
+    __syncthreads();
+    subtract_combination(a.Q, N, d_sh, j + 1, mqj, a.wt, red_sh, nullptr);
+    if (!grid_barrier(a, epoch)) return;
     // ---- C: partial dot products q_i . w' over chunks, one warp per (i, chunk)
     for (int task = wI; task < (j + 1) * a.nchunk; task += nW) {
       const int i = task / a.nchunk, ch = task % a.nchunk;
       const int64_t n0 = ch * chunk, n1 = min(N, n0 + chunk);
-      const double* qi = a.Q + (int64_t)i * N;
-      double s0 = 0.0, s1 = 0.0;
-      int64_t n = n0 + lane;
-      for (; n + 32 < n1; n += 64) {
-        s0 = fma(qi[n], a.wt[n], s0);
-        s1 = fma(qi[n + 32], a.wt[n + 32], s1);
-      }
-      if (n < n1) s0 = fma(qi[n], a.wt[n], s0);
-      const double sr = warp_sum(s0 + s1);
+      const double sr = warp_dot(a.Q + (int64_t)i * N, a.wt, n0, n1);
       if (lane == 0) a.dpart[(int64_t)i * a.nchunk + ch] = sr;
     }
-    if (!grid_barrier(a)) return;
-    // ---- D: w = w' - sum_{i<=j} d_i q_i, alpha_j = d_j
+    if (!grid_barrier(a, epoch)) return;
+    // ---- D: w = w' - sum_{i<=j} d_i q_i, alpha_j = h_j + d_j
     for (int i = threadIdx.x; i <= j; i += blockDim.x) {
       double di = 0.0;
       for (int ch = 0; ch < a.nchunk; ++ch) di += a.dpart[(int64_t)i * a.nchunk + ch];
@@ -289,24 +323,12 @@ __global__ void __launch_bounds__(512, 1) lanczos_coop_kernel(LzArgs a) {
     }
     __syncthreads();
     double sn = 0.0;
-    for (int64_t n = tI; n < N; n += nT) {
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      int i = 0;
-      for (; i + 3 <= j; i += 4) {
-        s0 = fma(a.Q[(int64_t)i * N + n], d_sh[i], s0);
-        s1 = fma(a.Q[(int64_t)(i + 1) * N + n], d_sh[i + 1], s1);
-        s2 = fma(a.Q[(int64_t)(i + 2) * N + n], d_sh[i + 2], s2);
-        s3 = fma(a.Q[(int64_t)(i + 3) * N + n], d_sh[i + 3], s3);
-      }
-      for (; i <= j; ++i) s0 = fma(a.Q[(int64_t)i * N + n], d_sh[i], s0);
-      const double v = a.wt[n] - ((s0 + s1) + (s2 + s3));
-      a.w[n] = v;
-      sn = fma(v, v, sn);
-    }
-    sn = block_sum(sn, sh);
+    subtract_combination(a.Q, N, d_sh, j + 1, a.wt, a.w, red_sh, &sn);
+    sn = block_sum(threadIdx.x < 32 ? sn : 0.0, sh);
     if (threadIdx.x == 0) a.npart[blockIdx.x] = sn;
     if (tI == 0) a.alpha[j] = hj + d_sh[j];
-    if (!grid_barrier(a)) return;
+    if (threadIdx.x == 0) s_scale = fmax(s_scale, fabs(hj + d_sh[j]));
+    if (!grid_barrier(a, epoch)) return;
   }
 }
 
@@ -356,7 +378,7 @@ __device__ int sturm_count(const double* a, const double* b, int m, double x, do
   if (fabs(q) < pivmin) q = -pivmin;
   if (q < 0) ++cnt;
   for (int i = 1; i < m; ++i) {
-    q = (a[i] - x) - b[i - 1] * b[i - 1] * rcp64(q);
+    q = (a[i] - x) - b[i - 1] * b[i - 1] * rcp64_sign(q);
     if (fabs(q) < pivmin) q = -pivmin;
     if (q < 0) ++cnt;
   }
@@ -666,8 +688,9 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   HM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
   const int nchunk = (int)(N < 1024 ? cdiv(N, 128) : 8);
   int m = 0;
-  int64_t target = N < (int64_t)2 * k + 32 ? N : (int64_t)2 * k + 32;
+  int64_t target = N < (int64_t)3 * k + 32 ? N : (int64_t)3 * k + 32;
   if (target < k) target = k;
+  if (target > mcap) target = mcap;
   bool converged = false;
   double* hp = h->host_pinned;
   while (true) {
@@ -692,6 +715,7 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
     la.nchunk = nchunk < 1 ? 1 : nchunk;
     la.key = key + 7;
     void* kargs[] = {&la};
+    HM_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
     HM_CUDA(cudaLaunchCooperativeKernel((void*)lanczos_coop_kernel, grid, 512, kargs, dyn, s));
     HM_LAUNCHED();
     m = (int)target;
