@@ -166,20 +166,35 @@ __global__ void splitk_reduce_kernel(Gemm<T> g, int splits, const T* part) {
 
 thread_local SplitScratch g_split;
 
+// Block (32 x 32): threadIdx.x over 32 adjacent columns r (coalesced),
+// threadIdx.y over 32 slices of n; the slices meet in shared memory.
 template <typename T>
 __global__ void colsum_kernel(const T* A, int64_t lda, int64_t R, int64_t K, T alpha, T* out,
                               int64_t ostride) {
-  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (r >= R) return;
-  T acc = T(0);
-  for (int64_t n = 0; n < K; ++n) acc += A[n * lda + r];
-  out[r * ostride] = alpha * acc;
+  __shared__ T part[32][33];
+  const int64_t r = blockIdx.x * (int64_t)32 + threadIdx.x;
+  T a0 = T(0), a1 = T(0);
+  if (r < R) {
+    int64_t n = threadIdx.y;
+    for (; n + 32 < K; n += 64) {
+      a0 += A[n * lda + r];
+      a1 += A[(n + 32) * lda + r];
+    }
+    if (n < K) a0 += A[n * lda + r];
+  }
+  part[threadIdx.y][threadIdx.x] = a0 + a1;
+  __syncthreads();
+  if (threadIdx.y == 0 && r < R) {
+    T acc = T(0);
+    for (int y = 0; y < 32; ++y) acc += part[y][threadIdx.x];
+    out[r * ostride] = alpha * acc;
+  }
 }
 template <typename T>
 hess_status colsum(const T* A, int64_t lda, int64_t R, int64_t K, T alpha, T* out, int64_t ostride,
                    cudaStream_t s) {
   if (R <= 0) return HESS_OK;
-  colsum_kernel<T><<<(unsigned)cdiv(R, 128), 128, 0, s>>>(A, lda, R, K, alpha, out, ostride);
+  colsum_kernel<T><<<(unsigned)cdiv(R, 32), dim3(32, 32), 0, s>>>(A, lda, R, K, alpha, out, ostride);
   HM_LAUNCHED();
   return HESS_OK;
 }
@@ -743,7 +758,10 @@ hess_status contract_layer(const Net& net, const Caches<T>& c, const RopBufs<T>&
   T* tmpW = tmp;
   T* tmpB = tmp + (int64_t)B * nW;
   const T invN = T(1) / T(N);
-  {
+  // W columns all left of the block's first direction lie below the diagonal
+  // (their values arrive through the mirror of earlier blocks): skip them
+  const bool w_needed = net.woff[jl - 1] + nW > d0;
+  if (w_needed) {
     // rows (d, i), columns k
     Gemm<T> g;
     g.M = B * Tout;
@@ -761,7 +779,7 @@ hess_status contract_layer(const Net& net, const Caches<T>& c, const RopBufs<T>&
     g.scn = 1;
     HM_TRY(gemm(g, s));
   }
-  if (jl > jm) {
+  if (w_needed && jl > jm) {
     // batched over d: rows k, columns i
     Gemm<T> g;
     g.M = Tin;
@@ -786,7 +804,7 @@ hess_status contract_layer(const Net& net, const Caches<T>& c, const RopBufs<T>&
   }
   // bias columns: (1/N) sum_n R{delta}[n, d, i]
   HM_TRY(colsum(r.rd[jl], (int64_t)B * Tout, (int64_t)B * Tout, N, invN, tmpB, (int64_t)1, s));
-  HM_TRY(scatter_sym(tmpW, B, nW, net.woff[jl - 1], d0, H, net.P, s));
+  if (w_needed) HM_TRY(scatter_sym(tmpW, B, nW, net.woff[jl - 1], d0, H, net.P, s));
   HM_TRY(scatter_sym(tmpB, B, (int64_t)Tout, net.boff[jl - 1], d0, H, net.P, s));
   return HESS_OK;
 }

@@ -56,10 +56,14 @@ struct Params {
   float* out;
   int64_t ldo;
   int mode;       // 0: symmetric rank-K update (orow = m, ocol = n)
-                  // 1: Hessian rows of one weight layer (see row_map)
-  int64_t woff;   // mode 1: offset of W in omega
+                  // 1: Hessian rows of one weight layer, W columns (see row_map)
+                  // 2: Hessian rows of one weight layer, columns after W (see row_map)
+  int64_t woff;   // modes 1, 2: offset of W in omega
+  int64_t boff;   // mode 2: first column (the layer's bias)
   int Tin, Tout, p0;
   int64_t R0;     // mode 1: first concatenated row of unit p0
+  int ntn;        // mode 2: column tiles per unit
+  int64_t brow;   // mode 2: B rows per unit
   int* err;
 };
 
@@ -173,14 +177,22 @@ __host__ __device__ __forceinline__ int64_t rows_before(int64_t p, int64_t Tin, 
 // (orow, ocolb + n).  Mode 1: rows are the weight directions W_(p,q) of one
 // layer, repeated for every output unit i >= p (the Hessian columns that can
 // lie on or above the diagonal); the product column n is the input unit k of
-// the Hessian column W_(i,k).
-__device__ __forceinline__ void row_map(const Params& p, int64_t m, int64_t& orow, int64_t& ocolb) {
+// the Hessian column W_(i,k).  Mode 2: the tile's unit u = tile_y / ntn; rows
+// are the directions W_(u,q) and the product column n is the n-th Hessian
+// column from the layer's bias on.
+__device__ __forceinline__ void row_map(const Params& p, int64_t m, int tile_y, int64_t& orow,
+                                        int64_t& ocolb) {
   if (p.mode == 0) {
     orow = m;
     ocolb = 0;
     return;
   }
   const int64_t Tin = p.Tin, Tout = p.Tout;
+  if (p.mode == 2) {
+    orow = p.woff + (int64_t)(p.p0 + tile_y / p.ntn) * Tin + m;
+    ocolb = p.boff;
+    return;
+  }
   const int64_t r = m + p.R0;
   const double b = 2.0 * Tout + 1.0;
   int64_t u = (int64_t)floor((b - sqrt(fmax(b * b - 8.0 * (double)r / (double)Tin, 0.0))) * 0.5);
@@ -262,10 +274,12 @@ __global__ void __launch_bounds__(THREADS, 1)
           uint8_t* st = smem + s * STAGE_BYTES;
           mbar_expect_tx(full(s), tx_bytes);
           tma_load_2d(smem_u32(st), &tmA_hi, j * BK, tile.x * BM, full(s));
-          tma_load_2d(smem_u32(st + OFF_BHI), &tmB_hi, j * BK, tile.y * p.BN, full(s));
+          const int brow0 = p.mode == 2 ? (int)((tile.y / p.ntn) * p.brow + (tile.y % p.ntn) * p.BN)
+                                        : tile.y * p.BN;
+          tma_load_2d(smem_u32(st + OFF_BHI), &tmB_hi, j * BK, brow0, full(s));
           if (x3) {
             tma_load_2d(smem_u32(st + OFF_ALO), &tmA_lo, j * BK, tile.x * BM, full(s));
-            tma_load_2d(smem_u32(st + OFF_BLO), &tmB_lo, j * BK, tile.y * p.BN, full(s));
+            tma_load_2d(smem_u32(st + OFF_BLO), &tmB_lo, j * BK, brow0, full(s));
           }
         }
       }
@@ -332,13 +346,14 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int64_t m = (int64_t)tile.x * BM + q * 32 + lane;
       const bool rvalid = m < p.M;
       int64_t orow = 0, ocolb = 0;
-      if (rvalid) row_map(p, m, orow, ocolb);
+      if (rvalid) row_map(p, m, tile.y, orow, ocolb);
+      const int64_t nbase = p.mode == 2 ? (int64_t)(tile.y % p.ntn) * p.BN : (int64_t)tile.y * p.BN;
       __syncwarp();
       const uint32_t tbase = tmem_base + acc * MAXBN + (static_cast<uint32_t>(q * 32) << 16);
       for (int c = 0; c < p.BN / 16; ++c) {
         float v[16];
         tmem_ld16(tbase + c * 16, v);
-        const int64_t n0 = (int64_t)tile.y * p.BN + c * 16;
+        const int64_t n0 = nbase + c * 16;
         // mirror image: for a fixed column, the warp's 32 rows are adjacent
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) {
@@ -452,9 +467,9 @@ __global__ void build_wrows_kernel(const float* U, const float* a, int64_t N, in
   }
 }
 
-// F[n][p][c] over the Hessian columns after W^(jm): the bias b^(jm+1) and all
+// F[n, p, c] over the Hessian columns after W^(jm): the bias b^(jm+1) and all
 // later layers, for the bias directions b_p of layer jm (the weight
-// directions W_(p,q) then follow as a[n,q] F[n][p][c]):
+// directions W_(p,q) then follow as a[n,q] F[n, p, c]):
 //   column b_i of layer jl:     R{delta^(jl)}[n,p,i]
 //   column W_(i,k) of layer jl: R{delta^(jl)}[n,p,i] a^(jl-1)[n,k]
 //                               + delta^(jl)[n,i] R{a^(jl-1)}[n,p,k]
@@ -474,28 +489,36 @@ struct FArgs {
   int64_t cols;
   int B;  // bias directions (= T of layer jm)
 };
-__global__ void build_f_kernel(FArgs f, int64_t N, float* F) {
-  const int64_t total = N * f.B * f.cols;
+// The same F as split-BF16 planes, K-major for the tensor cores: row
+// (p - p0) * cols + c holds F[., p, c] over the examples n (zero-padded to ld).
+__global__ void build_f_bf16_kernel(FArgs f, int64_t N, int p0, int np, __nv_bfloat16* hi,
+                                    __nv_bfloat16* lo, int64_t ld) {
+  const int64_t rows = (int64_t)np * f.cols;
+  const int64_t total = rows * ld;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = idx % f.cols;
-    const int64_t np = idx / f.cols;
-    const int pp = (int)(np % f.B);
-    const int64_t n = np / f.B;
-    int s = 0;
-    while (s + 1 < f.nseg && f.seg[s + 1].c0 <= c) ++s;
-    const FSeg& g = f.seg[s];
-    const int64_t cl = c - g.c0;
-    float v;
-    if (cl < g.nW) {
-      const int i = (int)(cl / g.Tin), k = (int)(cl % g.Tin);
-      v = g.rd[(n * f.B + pp) * g.Tout + i] * g.a[n * g.Tin + k];
-      if (g.ra) v += g.dlt[n * g.Tout + i] * g.ra[(n * f.B + pp) * g.Tin + k];
-    } else {
-      const int i = (int)(cl - g.nW);
-      v = g.rd[(n * f.B + pp) * g.Tout + i];
+    const int64_t n = idx % ld;
+    const int64_t row = idx / ld;
+    const int64_t c = row % f.cols;
+    const int pp = p0 + (int)(row / f.cols);
+    float v = 0.f;
+    if (n < N) {
+      int s = 0;
+      while (s + 1 < f.nseg && f.seg[s + 1].c0 <= c) ++s;
+      const FSeg& g = f.seg[s];
+      const int64_t cl = c - g.c0;
+      if (cl < g.nW) {
+        const int i = (int)(cl / g.Tin), k = (int)(cl % g.Tin);
+        v = g.rd[(n * f.B + pp) * g.Tout + i] * g.a[n * g.Tin + k];
+        if (g.ra) v += g.dlt[n * g.Tout + i] * g.ra[(n * f.B + pp) * g.Tin + k];
+      } else {
+        v = g.rd[(n * f.B + pp) * g.Tout + (int)(cl - g.nW)];
+      }
     }
-    F[idx] = v;
+    __nv_bfloat16 h, l;
+    split2(v, h, l);
+    hi[idx] = h;
+    lo[idx] = l;
   }
 }
 
@@ -765,15 +788,21 @@ hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N,
     arows_max = need > arows_max ? need : arows_max;
   }
   int64_t per_unit = N * maxRest * 4 + maxTinRest * 4 / (Tmax > 0 ? 1 : 1);
-  int pchunk = (int)(budget / (double)(N * maxRest * 4 + (int64_t)Tinmax * maxRest * 4));
+  int pchunk = (int)(budget / (double)(ld * maxRest * 4));
   if (pchunk > Tmax) pchunk = Tmax;
   if (pchunk < 1) pchunk = 1;
   (void)per_unit;
-  const int64_t max_tiles = cdiv(arows_max, BM) * cdiv(Tinmax, 64);
+  int64_t max_tiles = cdiv(arows_max, BM) * cdiv(Tinmax, 64);
+  for (int jm = 1; jm < L; ++jm) {
+    const int64_t rest = P - net.boff[jm - 1];
+    const int64_t t2 = cdiv(net.T[jm - 1], BM) * pchunk * cdiv(rest, pick_bn(rest));
+    max_tiles = t2 > max_tiles ? t2 : max_tiles;
+  }
   char* split = nullptr;
   auto plan = [&](Arena& ar, float*& xs, float*& ys, Caches<float>& c, RopBufs<float>& r,
                   float*& tmp, float*& ones, __nv_bfloat16*& bhi, __nv_bfloat16*& blo,
-                  __nv_bfloat16*& ahi, __nv_bfloat16*& alo, float*& F, float*& C2, float*& O,
+                  __nv_bfloat16*& ahi, __nv_bfloat16*& alo, __nv_bfloat16*& fhi,
+                  __nv_bfloat16*& flo, float*& O,
                   int2*& tl, int*& err) {
     xs = x_dev ? nullptr : ar.take<float>(N * T1);
     ys = y_dev ? nullptr : ar.take<float>(N * TL);
@@ -785,24 +814,24 @@ hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N,
     blo = ar.take<__nv_bfloat16>((int64_t)Tinmax * ld);
     ahi = ar.take<__nv_bfloat16>(arows_max * ld);
     alo = ar.take<__nv_bfloat16>(arows_max * ld);
-    F = ar.take<float>(N * pchunk * maxRest);
-    C2 = ar.take<float>((int64_t)pchunk * maxTinRest);
+    fhi = ar.take<__nv_bfloat16>((int64_t)pchunk * maxRest * ld);
+    flo = ar.take<__nv_bfloat16>((int64_t)pchunk * maxRest * ld);
     O = o_dev ? (float*)Hout : ar.take<float>(P * P);
     tl = ar.take<int2>(max_tiles);
     err = ar.take<int>(1);
     split = ar.take<char>(kSplitBytes);
   };
   Arena ar;
-  float *xs, *ys, *tmp, *ones, *F, *C2, *O;
-  __nv_bfloat16 *bhi, *blo, *ahi, *alo;
+  float *xs, *ys, *tmp, *ones, *O;
+  __nv_bfloat16 *bhi, *blo, *ahi, *alo, *fhi, *flo;
   int2* tl;
   int* err;
   Caches<float> c;
   RopBufs<float> r;
-  plan(ar, xs, ys, c, r, tmp, ones, bhi, blo, ahi, alo, F, C2, O, tl, err);
+  plan(ar, xs, ys, c, r, tmp, ones, bhi, blo, ahi, alo, fhi, flo, O, tl, err);
   HM_TRY(ensure_ws(h, ar.off));
   ar = Arena{h->ws, 0};
-  plan(ar, xs, ys, c, r, tmp, ones, bhi, blo, ahi, alo, F, C2, O, tl, err);
+  plan(ar, xs, ys, c, r, tmp, ones, bhi, blo, ahi, alo, fhi, flo, O, tl, err);
   SplitGuard sg(split, kSplitBytes, h->sm_count);
   cudaStream_t s = h->stream;
   const float* xd = (const float*)X;
@@ -911,45 +940,44 @@ hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N,
       g.ra = rb.ra[jl - 1];
       fa.seg[fa.nseg++] = g;
     }
-    Tick t(h, HESS_K_HREST, 0.0, 0.0);
+    fa.B = Tout;
+    const int BN2 = pick_bn(rest);
+    const int ntn = (int)cdiv(rest, BN2);
     for (int q0 = 0; q0 < Tout; q0 += pchunk) {
       const int pc = Tout - q0 < pchunk ? Tout - q0 : pchunk;
-      // F for units q0..q0+pc-1: view the [n][p][t] buffers at unit offset q0
-      FArgs fc = fa;
-      fc.B = Tout;
-      // build for all Tout units but only the chunk is used: keep it simple
-      // when the whole layer fits (the common case)
-      if (pc != Tout) {
-        // chunked: rebuild F per chunk from offset views
-        for (int sgi = 0; sgi < fc.nseg; ++sgi) {
-          (void)sgi;
-        }
-      }
-      fc.B = Tout;
-      const int64_t total = N * (int64_t)Tout * rest;
-      if (pc != Tout) return set_error(HESS_ERR_UNSUPPORTED, "layer too large for one F chunk");
-      build_f_kernel<<<(unsigned)(cdiv(total, 256) < 1048576 ? cdiv(total, 256) : 1048576), 256, 0, s>>>(fc, N, F);
+      const int64_t total = (int64_t)pc * rest * ld;
+      build_f_bf16_kernel<<<(unsigned)(cdiv(total, 256) < 1048576 ? cdiv(total, 256) : 1048576), 256, 0,
+                            s>>>(fa, N, q0, pc, fhi, flo, ld);
       HM_LAUNCHED();
-      Gemm<float> g;
-      g.M = Tin;
-      g.N = (int)rest;
-      g.K = (int)N;
-      g.alpha = 1.0f / (float)N;
-      g.A = c.a[jm - 1];
-      g.sam = 1;
-      g.sak = Tin;
-      g.bsa = 0;
-      g.B = F;
-      g.sbk = (int64_t)Tout * rest;
-      g.sbn = 1;
-      g.bsb = rest;
-      g.C = C2;
-      g.scm = rest;
-      g.scn = 1;
-      g.bsc = (int64_t)Tin * rest;
-      g.batch = pc;
-      HM_TRY(gemm(g, s));
-      HM_TRY(scatter_sym(C2, pc * Tin, rest, boff, woff + (int64_t)q0 * Tin, O, P, s));
+      tiles.clear();
+      for (int64_t tm = 0; tm < cdiv(Tin, BM); ++tm)
+        for (int u = 0; u < pc; ++u)
+          for (int tn = 0; tn < ntn; ++tn) tiles.push_back(make_int2((int)tm, u * ntn + tn));
+      HM_CUDA(cudaMemcpyAsync(tl, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+      Params p{};
+      p.M = Tin;
+      p.Nn = rest;
+      p.passes = x3 ? 3 : 1;
+      p.tiles = tl;
+      p.ntiles = (int)tiles.size();
+      p.scale = 1.0f / (float)N;
+      p.out = O;
+      p.ldo = P;
+      p.mode = 2;
+      p.woff = woff;
+      p.boff = boff;
+      p.Tin = Tin;
+      p.Tout = Tout;
+      p.p0 = q0;
+      p.ntn = ntn;
+      p.brow = rest;
+      p.err = err;
+      TcOperands op{bhi, blo, Tin, fhi, flo, (int64_t)pc * rest, ld};
+      {
+        Tick t(h, HESS_K_HCONTRACT, 2.0 * N * (double)pc * Tin * rest, 0.0);
+        HM_TRY(launch_tc(h, op, p, BN2, s));
+      }
+      HM_CUDA(cudaStreamSynchronize(s));
     }
   }
   if (!o_dev) HM_CUDA(cudaMemcpyAsync(Hout, O, P * P * 4, cudaMemcpyDeviceToHost, s));
