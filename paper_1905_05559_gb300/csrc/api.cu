@@ -443,6 +443,7 @@ static hess_status run_eig(hess_mlp* h, const void* X, const void* Y, int64_t N,
   {
     Tick t(h, HESS_K_EIG, 0.0, 0.0);
     HM_TRY(topk_eig_gram(h, net, c, N, k, evd, eqd, ar, false, &res));
+    t.set_work(res.flops, 0.0);
   }
   if (!ev_dev) HM_CUDA(cudaMemcpyAsync(evals, evd, k * sizeof(double), cudaMemcpyDeviceToHost, s));
   if (!q_dev) HM_CUDA(cudaMemcpyAsync(evecs, eqd, P * k * sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -747,6 +747,13 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
     if (target > N) target = N;
   }
   res->lanczos_steps = m;
+  {
+    double f = 0.0;
+    for (int wl = 1; wl <= L - 1; ++wl) f += (double)N * (N + 1) * (net.T[wl - 1] + net.T[wl]);
+    for (int j = 0; j < m; ++j) f += 2.0 * N * N + 8.0 * N * (j + 1);
+    f += 2.0 * N * m * k + 2.0 * P * N * k;
+    res->flops = f;
+  }
   res->converged = converged ? 1 : 0;
 
   // 4. Ritz vectors U = Q_m^T Y (N x k), back-projection through G

@@ -108,6 +108,10 @@ hess_status ensure_ws(hess_mlp* h, size_t bytes);
 class Tick {
  public:
   Tick(hess_mlp* h, int cls, double flops, double bytes);
+  void set_work(double flops, double bytes) {
+    rec_.flops = flops;
+    rec_.bytes = bytes;
+  }
   void stop();
   ~Tick() { stop(); }
 
@@ -213,6 +217,7 @@ struct EigResult {
   int converged = 0;
   int rank_deficient = 0;
   int lanczos_steps = 0;
+  double flops = 0.0;  // algorithmic FP64 flops of the Gram matrix, Lanczos and back-projection
 };
 hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, int64_t N, int k,
                           double* evals_d, double* evecs_d, Arena& ar, bool dry, EigResult* res);
