@@ -35,6 +35,12 @@ METRIC = "exact-Hessian & OPG entries/s"
 UNIT = "entries/s"
 WORKLOAD = "mlp_784_16_10"
 K_EIG = 32
+# workload -> (calls in one step, k of the eigenpairs)
+WORKLOADS = {
+    "mlp_784_16_10": (("opg", "hessian", "eig"), 32),
+    # the precision workload: OPG in BF16 / split-BF16 and the top-100 eigenpairs
+    "mlp_1024_64_64_10": (("opg", "eig"), 100),
+}
 
 
 def parse():
@@ -50,6 +56,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--only", default=None, choices=["opg", "hessian", "eig"],
                     help="run one call of the step (for profiling); the line is then partial")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -227,7 +234,7 @@ def main():
     # the CPU baseline runs first, in a fresh process, before this process
     # uses the GPU heavily (rank 0, one GPU only)
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD:
         cpu = run_cpu_baseline(2048)
 
     from paper_1905_05559_gb300 import build
@@ -238,7 +245,10 @@ def main():
     import paper_1905_05559_gb300 as hm
     from synth import named_config
 
-    pb = named_config(WORKLOAD)
+    calls, K_EIG_W = WORKLOADS[args.workload]
+    if args.only:
+        calls = tuple(c for c in calls if c == args.only)
+    pb = named_config(args.workload)
     P, N = pb.P, pb.N
     stream = torch.cuda.current_stream()
     net = hm.HessMLP(pb.widths, pb.acts, pb.omega, stream=stream.cuda_stream)
@@ -253,20 +263,20 @@ def main():
         dt = torch.float64 if prec == "fp64" else torch.float32
         X = torch.as_tensor(pb.X, dtype=dt, device="cuda")
         Y = torch.as_tensor(pb.Y, dtype=dt, device="cuda")
-        H = torch.empty((P, P), dtype=dt, device="cuda")
-        OPG = torch.empty((P, P), dtype=dt, device="cuda")
-        ev = torch.empty(K_EIG, dtype=torch.float64, device="cuda")
-        Q = torch.empty((K_EIG, P), dtype=torch.float64, device="cuda")
+        H = torch.empty((P, P), dtype=dt, device="cuda") if "hessian" in calls else None
+        OPG = torch.empty((P, P), dtype=dt, device="cuda") if "opg" in calls else None
+        ev = torch.empty(K_EIG_W, dtype=torch.float64, device="cuda")
+        Q = torch.empty((K_EIG_W, P), dtype=torch.float64, device="cuda")
         return X, Y, H, OPG, ev, Q
 
     def step(prec, io):
         X, Y, H, OPG, ev, Q = io
-        if args.only in (None, "opg"):
+        if "opg" in calls:
             net.opg(X, Y, prec, out=OPG)
-        if args.only in (None, "hessian"):
+        if "hessian" in calls:
             net.exact_hessian(X, Y, prec, out=H)
-        if args.only in (None, "eig"):
-            net.opg_topk_eig(X, Y, K_EIG, prec, evals=ev, evecs=Q)
+        if "eig" in calls:
+            net.opg_topk_eig(X, Y, K_EIG_W, prec, evals=ev, evecs=Q)
 
     def timed(prec, steps, warmup, sampler=None):
         io = make_io(prec)
@@ -307,7 +317,7 @@ def main():
 
     sampler = ClockSampler(gpu_index(local_rank)) if rank == 0 else None
     ms_step, wall, launches, kern, clocks = timed(args.precision, args.steps, args.warmup, sampler)
-    entries = 2.0 * P * P
+    entries = float(P) * P * sum(1 for c in calls if c in ("opg", "hessian"))
     value = world * entries / (ms_step * 1e-3)
 
     fp64 = None
@@ -327,15 +337,18 @@ def main():
         Xh[:] = pb.X.astype(npdt)
         Yh = pin(pb.Y.shape, tdt)
         Yh[:] = pb.Y.astype(npdt)
-        Hh = pin((P, P), tdt)
-        Oh = pin((P, P), tdt)
-        evh = pin((K_EIG,), torch.float64)
-        Qh = pin((K_EIG, P), torch.float64)
+        Hh = pin((P, P), tdt) if "hessian" in calls else None
+        Oh = pin((P, P), tdt) if "opg" in calls else None
+        evh = pin((K_EIG_W,), torch.float64)
+        Qh = pin((K_EIG_W, P), torch.float64)
 
         def host_step():
-            net.opg(Xh, Yh, args.precision, out=Oh)
-            net.exact_hessian(Xh, Yh, args.precision, out=Hh)
-            net.opg_topk_eig(Xh, Yh, K_EIG, args.precision, evals=evh, evecs=Qh)
+            if "opg" in calls:
+                net.opg(Xh, Yh, args.precision, out=Oh)
+            if "hessian" in calls:
+                net.exact_hessian(Xh, Yh, args.precision, out=Hh)
+            if "eig" in calls:
+                net.opg_topk_eig(Xh, Yh, K_EIG_W, args.precision, evals=evh, evecs=Qh)
 
         host_step()
         torch.cuda.synchronize()
@@ -351,9 +364,11 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
         isz = Xh.itemsize
+        outs = [a for a in (Hh, Oh) if a is not None]
         e2e = {"value": world * entries / e2e_s, "unit": UNIT,
-               "h2d_bytes_per_step": 3 * (Xh.size + Yh.size) * isz,
-               "d2h_bytes_per_step": (Hh.size + Oh.size) * isz + (evh.size + Qh.size) * 8}
+               "h2d_bytes_per_step": len(calls) * (Xh.size + Yh.size) * isz,
+               "d2h_bytes_per_step": sum(a.size for a in outs) * isz
+               + ((evh.size + Qh.size) * 8 if "eig" in calls else 0)}
 
     peaks, peak_src = measured_peaks()
     smx = peaks.get("sm_max_mhz", 2070.0) * 1e6
@@ -403,9 +418,11 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.precision],
             "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD}: MLP [784,16,10] tanh, P={P}, N={N}; OPG + exact "
-                                   f"Hessian + top-{K_EIG} OPG eig per step",
-                       "precision": args.precision, "P": P, "N": N, "k": K_EIG,
+            "config": {"workload": f"{args.workload}: MLP {pb.widths} {'/'.join(pb.acts)}, P={P}, "
+                                   f"N={N}; " + " + ".join({"opg": "OPG", "hessian": "exact Hessian",
+                                                            "eig": f"top-{K_EIG_W} OPG eig"}[c]
+                                                           for c in calls) + " per step",
+                       "precision": args.precision, "P": P, "N": N, "k": K_EIG_W,
                        "l2": "flushed between steps (256 MiB write outside the timed events)",
                        "parallelism": f"replicas x{world}",
                        **({"only": args.only} if args.only else {})},

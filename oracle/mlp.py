@@ -344,3 +344,84 @@ def opg_topk_eig_from_grads(G, k, rank_tol=1e-13):
 
 def opg_topk_eig(omega, widths, acts, X, Y, k, rank_tol=1e-13):
     return opg_topk_eig_from_grads(per_example_grads(omega, widths, acts, X, Y), k, rank_tol)
+
+
+# ----------------------------------------------------------------------------
+# Memory-light routes for large P (same definitions, no N x P matrix)
+# ----------------------------------------------------------------------------
+
+def _param_coords(widths):
+    """For every parameter index: (weight layer j = 1..L-1, output unit i,
+    input unit k or -1 for the bias) in the order of Eq. flatten."""
+    coords = []
+    for j, (ow, ob) in zip(range(1, len(widths)), layer_offsets(widths)):
+        t_in, t_out = widths[j - 1], widths[j]
+        for i in range(t_out):
+            for k in range(t_in):
+                coords.append((j, i, k))
+        for i in range(t_out):
+            coords.append((j, i, -1))
+    return coords
+
+
+def per_example_grads_columns(omega, widths, acts, X, Y, cols) -> np.ndarray:
+    """Columns G[:, cols] of the per-example gradient matrix:
+    G[n, W^(j)_{ik}] = delta_n^(j+1)_i a_n^(j)_k and G[n, b^(j+1)_i] = delta_n^(j+1)_i."""
+    f = forward(omega, widths, acts, X)
+    delta, _ = backprop(f, Y)
+    coords = _param_coords(widths)
+    N = f["a"][0].shape[0]
+    out = np.empty((N, len(cols)))
+    for c, col in enumerate(cols):
+        j, i, k = coords[col]
+        out[:, c] = delta[j][:, i] * (f["a"][j - 1][:, k] if k >= 0 else 1.0)
+    return out
+
+
+def grads_transpose_times(f, delta, widths, V) -> np.ndarray:
+    """G^T V for V of shape (N, m) without forming G: the block of layer j is
+    sum_n V[n] delta_n^(j+1) [a_n^(j); 1]^T."""
+    blocks = []
+    for j in range(1, len(widths)):
+        d, a = delta[j], f["a"][j - 1]
+        dV = V[:, :, None] * d[:, None, :]            # (N, m, T_out)
+        W = np.tensordot(dV, a, axes=([0], [0]))       # (m, T_out, T_in)
+        blocks.append(W.reshape(V.shape[1], -1))
+        blocks.append(V.T @ d)
+    return np.concatenate(blocks, axis=1).T  # (P, m)
+
+
+def grads_times(f, delta, widths, Qm) -> np.ndarray:
+    """G Q for Q of shape (P, m) without forming G:
+    (G q)_n = sum_j delta_n^(j+1) . (W_q^(j) a_n^(j) + b_q^(j+1))."""
+    N = f["a"][0].shape[0]
+    out = np.zeros((N, Qm.shape[1]))
+    for j, (ow, ob) in zip(range(1, len(widths)), layer_offsets(widths)):
+        t_in, t_out = widths[j - 1], widths[j]
+        Wq = Qm[ow:ob].reshape(t_out, t_in, -1)
+        bq = Qm[ob:ob + t_out]
+        za = np.tensordot(f["a"][j - 1], Wq, axes=([1], [1])) + bq[None, :, :]  # (N, T_out, m)
+        out += (delta[j][:, :, None] * za).sum(axis=1)
+    return out
+
+
+def opg_topk_eig_factored(omega, widths, acts, X, Y, k, rank_tol=1e-13):
+    """The top-k OPG eigenpairs of Sec. 5.4 (Eq. J) without forming G: Gram
+    matrix in factored form, numpy.linalg.eigh, back-projection
+    q = G^T u / sqrt(N mu) in factored form."""
+    f = forward(omega, widths, acts, X)
+    delta, _ = backprop(f, Y)
+    N = f["a"][0].shape[0]
+    M = np.zeros((N, N))
+    for j in range(1, len(widths)):
+        M += (delta[j] @ delta[j].T) * (f["a"][j - 1] @ f["a"][j - 1].T + 1.0)
+    M /= N
+    mu, U = np.linalg.eigh(M)
+    order = np.argsort(mu)[::-1][:k]
+    mu, U = mu[order], U[:, order]
+    top = mu[0]
+    keep = (mu > rank_tol * top) & (mu > 0)
+    Q = np.zeros((num_params(widths), k))
+    if keep.any():
+        Q[:, keep] = grads_transpose_times(f, delta, widths, U[:, keep]) / np.sqrt(N * mu[keep])
+    return mu, canonical_sign(Q), bool((~keep).any())

@@ -42,6 +42,11 @@ constexpr int SMEM_BYTES = 1024 + RING_BYTES + EPI_BYTES + BAR_BYTES;
 constexpr int THREADS = 192;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr long long TIMEOUT_CYCLES = 4000000000ll;  // ~2 s at 2 GHz
+// K is accumulated in chunks of CHUNK_KB k-blocks (1024 products): each chunk
+// goes to a fresh TMEM accumulator and the epilogue warps add it into the
+// tile's main accumulator with round-to-nearest FP32 adds, so the error of the
+// tensor cores' own accumulation does not grow with N.
+constexpr int CHUNK_KB = 16;
 
 struct Params {
   int64_t M;      // valid rows of A
@@ -165,6 +170,20 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
       : "memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16};\n\t"
+      "tcgen05.wait::st.sync.aligned;" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15]))
+      : "memory");
 }
 
 // First concatenated A row of unit p for the Hessian layer mapping:
@@ -297,38 +316,49 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       int it = 0, tcount = 0;
+      unsigned uses[2] = {0u, 0u};  // chunks written into each TMEM buffer so far
       bool ok = true;
+      const int nchunk = (nvk + CHUNK_KB - 1) / CHUNK_KB;
       for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x, ++tcount) {
-        const int acc = tcount & 1;
-        const uint32_t aph = (tcount >> 1) & 1;
-        if (!mbar_wait(tempty(acc), aph ^ 1, p.err, abort_flag)) break;
-        tc_fence_after();
-        const uint32_t d_tmem = tmem_base + acc * MAXBN;
-        for (int j = 0; j < nvk; ++j, ++it) {
-          const int s = it % STAGES;
-          const uint32_t ph = (it / STAGES) & 1;
-          if (!mbar_wait(full(s), ph, p.err, abort_flag)) {
+        // the first chunk goes to the tile's main buffer, the others to the
+        // second buffer, which the epilogue merges into the main one
+        const int mainb = tcount & 1;
+        for (int ch = 0; ch < nchunk && ok; ++ch) {
+          const int buf = ch == 0 ? mainb : mainb ^ 1;
+          if (!mbar_wait(tempty(buf), (uses[buf] & 1u) ^ 1u, p.err, abort_flag)) {
             ok = false;
             break;
           }
+          ++uses[buf];
           tc_fence_after();
-          const uint8_t* st = smem + s * STAGE_BYTES;
-          const uint64_t ah = sdesc(smem_u32(st));
-          const uint64_t bh = sdesc(smem_u32(st + OFF_BHI));
+          const uint32_t d_tmem = tmem_base + buf * MAXBN;
+          const int j0 = ch * CHUNK_KB, j1 = min(nvk, j0 + CHUNK_KB);
+          for (int j = j0; j < j1; ++j, ++it) {
+            const int s = it % STAGES;
+            const uint32_t ph = (it / STAGES) & 1;
+            if (!mbar_wait(full(s), ph, p.err, abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint8_t* st = smem + s * STAGE_BYTES;
+            const uint64_t ah = sdesc(smem_u32(st));
+            const uint64_t bh = sdesc(smem_u32(st + OFF_BHI));
 #pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk)
-            umma_bf16(d_tmem, ah + 2 * kk, bh + 2 * kk, p.idesc, (j > 0 || kk > 0) ? 1u : 0u);
-          if (x3) {
-            const uint64_t al = sdesc(smem_u32(st + OFF_ALO));
-            const uint64_t bl = sdesc(smem_u32(st + OFF_BLO));
+            for (int kk = 0; kk < BK / 16; ++kk)
+              umma_bf16(d_tmem, ah + 2 * kk, bh + 2 * kk, p.idesc, (j > j0 || kk > 0) ? 1u : 0u);
+            if (x3) {
+              const uint64_t al = sdesc(smem_u32(st + OFF_ALO));
+              const uint64_t bl = sdesc(smem_u32(st + OFF_BLO));
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) umma_bf16(d_tmem, ah + 2 * kk, bl + 2 * kk, p.idesc, 1u);
+              for (int kk = 0; kk < BK / 16; ++kk) umma_bf16(d_tmem, ah + 2 * kk, bl + 2 * kk, p.idesc, 1u);
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) umma_bf16(d_tmem, al + 2 * kk, bh + 2 * kk, p.idesc, 1u);
+              for (int kk = 0; kk < BK / 16; ++kk) umma_bf16(d_tmem, al + 2 * kk, bh + 2 * kk, p.idesc, 1u);
+            }
+            umma_commit(empty(s));
           }
-          umma_commit(empty(s));
+          if (ok) umma_commit(tfull(buf));
         }
-        if (ok) umma_commit(tfull(acc));
       }
     }
     __syncwarp();
@@ -336,12 +366,40 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int q = warp & 3;  // TMEM lane quadrant of this warp
     float* e = epi + (warp - 2) * 32 * EPI_LD;
     int tcount = 0;
-    for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++tcount) {
+    unsigned fulls[2] = {0u, 0u};  // chunk results consumed from each TMEM buffer
+    const int nchunk = (p.nkb + CHUNK_KB - 1) / CHUNK_KB;
+    const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
+    bool alive = true;
+    for (int t = blockIdx.x; t < p.ntiles && alive; t += gridDim.x, ++tcount) {
       const int acc = tcount & 1;
-      const uint32_t aph = (tcount >> 1) & 1;
-      const bool got = mbar_wait(tfull(acc), aph, p.err, abort_flag);
+      const bool got = mbar_wait(tfull(acc), fulls[acc] & 1u, p.err, abort_flag);
       if (__any_sync(0xffffffffu, !got)) break;
+      ++fulls[acc];
       tc_fence_after();
+      // merge the later K chunks into the main accumulator
+      const int part = acc ^ 1;
+      for (int ch = 1; ch < nchunk; ++ch) {
+        const bool g2 = mbar_wait(tfull(part), fulls[part] & 1u, p.err, abort_flag);
+        if (__any_sync(0xffffffffu, !g2)) {
+          alive = false;
+          break;
+        }
+        ++fulls[part];
+        tc_fence_after();
+        const uint32_t pm = tmem_base + acc * MAXBN + lane_off;
+        const uint32_t pp = tmem_base + part * MAXBN + lane_off;
+        for (int c = 0; c < p.BN / 16; ++c) {
+          float vm[16], vp[16];
+          tmem_ld16(pp + c * 16, vp);
+          tmem_ld16(pm + c * 16, vm);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) vm[i] += vp[i];
+          tmem_st16(pm + c * 16, vm);
+        }
+        tc_fence_before();
+        mbar_arrive(tempty(part));
+      }
+      if (!alive) break;
       const int2 tile = p.tiles[t];
       const int64_t m = (int64_t)tile.x * BM + q * 32 + lane;
       const bool rvalid = m < p.M;

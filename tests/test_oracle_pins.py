@@ -389,3 +389,24 @@ def test_pins_catch_unnormalised_softmax(monkeypatch):
     monkeypatch.setattr(O, "forward", broken_forward)
     H = O.hessian(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
     assert _relerr(H[np.ix_(perm, perm)], ref) > 1e-3
+
+
+# ------------------------------------------------- memory-light routes ----
+
+def test_memory_light_routes_match_full_matrices():
+    pb = _tiny([7, 5, 4, 3], ["relu", "tanh"], N=11, seed=13)
+    G = O.per_example_grads(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
+    cols = [0, 5, 34, 35, 39, 40, 60, 61, 62, pb.P - 1]
+    assert np.array_equal(O.per_example_grads_columns(pb.omega, pb.widths, pb.acts, pb.X, pb.Y, cols),
+                          G[:, cols])
+    f = O.forward(pb.omega, pb.widths, pb.acts, pb.X)
+    delta, _ = O.backprop(f, pb.Y)
+    rng = np.random.default_rng(1)
+    V = rng.standard_normal((pb.N, 3))
+    Qm = rng.standard_normal((pb.P, 2))
+    assert _relerr(O.grads_transpose_times(f, delta, pb.widths, V), G.T @ V) < 1e-14
+    assert _relerr(O.grads_times(f, delta, pb.widths, Qm), G @ Qm) < 1e-14
+    mu, Q, d = O.opg_topk_eig_factored(pb.omega, pb.widths, pb.acts, pb.X, pb.Y, 4)
+    mu2, Q2, d2 = O.opg_topk_eig_from_grads(G, 4)
+    assert d == d2 and np.allclose(mu, mu2, rtol=0, atol=1e-14 * mu2[0])
+    assert np.allclose(Q, Q2, rtol=0, atol=1e-10)
