@@ -181,6 +181,23 @@ def gpu_index(local_rank):
     return local_rank
 
 
+# -------------------------------------------------------------- replicas ----
+def max_over_ranks(value: float, dist=None, device="cpu") -> float:
+    """Replicas only: every rank runs the whole workload on its own GPU and
+    the job's time is the slowest rank's (no collective on the data path)."""
+    if dist is None or not dist.is_available() or not dist.is_initialized():
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(entries_per_rank: float, step_seconds_max: float, world: int) -> float:
+    """Whole-job rate: the units all ranks processed over the slowest rank's time."""
+    return world * entries_per_rank / step_seconds_max
+
+
 # ------------------------------------------------------------------ GPU ----
 def measured_peaks():
     try:
@@ -309,21 +326,19 @@ def main():
         net.timing(False)
         kern = {cls: net.read_timing(cls) for cls in hm._lib.KERNEL_CLASS}
         per = [x.elapsed_time(y) for x, y in ms]
-        t = torch.tensor([sum(per) / len(per)], device="cuda")
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t = max_over_ranks(sum(per) / len(per), dist if world > 1 else None, "cuda")
         del io
-        return float(t.item()), wall, launches, kern, clocks
+        return t, wall, launches, kern, clocks
 
     sampler = ClockSampler(gpu_index(local_rank)) if rank == 0 else None
     ms_step, wall, launches, kern, clocks = timed(args.precision, args.steps, args.warmup, sampler)
     entries = float(P) * P * sum(1 for c in calls if c in ("opg", "hessian"))
-    value = world * entries / (ms_step * 1e-3)
+    value = job_throughput(entries, ms_step * 1e-3, world)
 
     fp64 = None
     if not args.no_fp64 and args.precision != "fp64":
         ms64, _, _, kern64, _ = timed("fp64", args.fp64_steps, 1)
-        fp64 = {"value": world * entries / (ms64 * 1e-3), "ms_per_step": ms64,
+        fp64 = {"value": job_throughput(entries, ms64 * 1e-3, world), "ms_per_step": ms64,
                 "kernels_ms": {k: v["ms"] for k, v in kern64.items()}}
 
     # end to end through the C ABI with host buffers: the library stages the
@@ -358,14 +373,11 @@ def main():
             host_step()
         torch.cuda.synchronize()
         barrier()
-        e2e_s = (time.perf_counter() - t0) / args.steps
-        t = torch.tensor([e2e_s], device="cuda")
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, dist if world > 1 else None,
+                               "cuda")
         isz = Xh.itemsize
         outs = [a for a in (Hh, Oh) if a is not None]
-        e2e = {"value": world * entries / e2e_s, "unit": UNIT,
+        e2e = {"value": job_throughput(entries, e2e_s, world), "unit": UNIT,
                "h2d_bytes_per_step": len(calls) * (Xh.size + Yh.size) * isz,
                "d2h_bytes_per_step": sum(a.size for a in outs) * isz
                + ((evh.size + Qh.size) * 8 if "eig" in calls else 0)}
