@@ -57,6 +57,11 @@ def parse():
     ap.add_argument("--only", default=None, choices=["opg", "hessian", "eig"],
                     help="run one call of the step (for profiling); the line is then partial")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--serve", action="store_true",
+                    help="serving benchmark: Poisson request stream through the request server")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -181,6 +186,107 @@ def gpu_index(local_rank):
     return local_rank
 
 
+# --------------------------------------------------------------- serving ----
+def serve_bench(args):
+    """Poisson arrivals (seed 4) of exact-Hessian, OPG and top-32 eigenpair
+    requests, uniform over the three kinds and over 16 networks of the
+    batching distribution, through the continuous-batching request server
+    with a 100 GB workspace budget.  Latency = submit to completion."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import paper_1905_05559_gb300 as hm
+    from paper_1905_05559_gb300 import build
+    from synth import SplitMix64Stream, make_problem, make_random_mlp
+
+    build.build()
+    torch.cuda.set_device(0)
+    nets = []
+    for i in range(16):
+        widths, acts, N = make_random_mlp(4, i)
+        pb = make_problem(widths, acts, N, 400 + i, "normal", "zero")
+        nets.append((pb, torch.as_tensor(pb.X, dtype=torch.float32, device="cuda"),
+                     torch.as_tensor(pb.Y, dtype=torch.float32, device="cuda")))
+    srv = hm.HessServer(slots=args.serve_slots, budget_bytes=100 * (1 << 30))
+    ids = [srv.add_network(pb.widths, pb.acts, pb.omega) for pb, _, _ in nets]
+    rs = SplitMix64Stream(4, 1)
+    n_req = int(args.serve_rate * args.serve_seconds)
+    gaps = -np.log(1.0 - rs.uniform(n_req)) / args.serve_rate
+    arrivals = np.cumsum(gaps)
+    kinds = rs.integers(n_req, 0, 2)
+    which = rs.integers(n_req, 0, len(nets) - 1)
+    # warm-up: one request of each kind on each network
+    for i, (pb, X, Y) in enumerate(nets):
+        for kind in ("hessian", "opg", "eig"):
+            if kind == "eig":
+                out = torch.empty((32, pb.P), dtype=torch.float64, device="cuda")
+                ev = torch.empty(32, dtype=torch.float64, device="cuda")
+                srv.wait(srv.submit(kind, ids[i], X, Y, "fp32", out, k=32, evals=ev))
+            else:
+                out = torch.empty((pb.P, pb.P), device="cuda")
+                srv.wait(srv.submit(kind, ids[i], X, Y, "bf16x3", out))
+    torch.cuda.synchronize()
+    lat = [None] * n_req
+    entries = [0.0] * n_req
+    sem = threading.Semaphore(64)  # the client keeps at most 64 requests in flight
+    lock = threading.Lock()
+    pending = []
+
+    def waiter(j, ticket, t_submit, keep):
+        st = srv.wait(ticket)
+        t_done = time.perf_counter()
+        with lock:
+            lat[j] = (t_done - t_submit, st)
+        del keep
+        sem.release()
+
+    t0 = time.perf_counter()
+    for j in range(n_req):
+        now = time.perf_counter() - t0
+        if arrivals[j] > now:
+            time.sleep(arrivals[j] - now)
+        sem.acquire()
+        pb, X, Y = nets[which[j]]
+        kind = ("hessian", "opg", "eig")[kinds[j]]
+        t_sub = time.perf_counter()
+        if kind == "eig":
+            out = torch.empty((32, pb.P), dtype=torch.float64, device="cuda")
+            ev = torch.empty(32, dtype=torch.float64, device="cuda")
+            tk = srv.submit(kind, ids[which[j]], X, Y, "fp32", out, k=32, evals=ev)
+            keep = (out, ev)
+            entries[j] = 32.0 * pb.P
+        else:
+            out = torch.empty((pb.P, pb.P), device="cuda")
+            tk = srv.submit(kind, ids[which[j]], X, Y, "bf16x3", out)
+            keep = (out,)
+            entries[j] = float(pb.P) * pb.P
+        th = threading.Thread(target=waiter, args=(j, tk, t_sub, keep))
+        th.start()
+        pending.append(th)
+    for th in pending:
+        th.join()
+    wall = time.perf_counter() - t0
+    srv.close()
+    ok = [l for l, st in lat if st in (0, 4)]
+    ls = np.sort(np.asarray(ok)) * 1e3
+    line = {
+        "metric": "served p50/p99 latency (ms) and delivered entries/s", "impl": "ours",
+        "value": float(np.percentile(ls, 50)), "unit": "ms (p50)",
+        "p50_ms": float(np.percentile(ls, 50)), "p99_ms": float(np.percentile(ls, 99)),
+        "entries_per_s": float(sum(entries) / wall), "requests": n_req,
+        "completed": len(ok), "wall_s": wall, "offered_rate": args.serve_rate,
+        "achieved_rate": n_req / wall, "higher_is_better": False, "n_gpus": 1,
+        "config": {"workload": "Poisson request stream (seed 4): exact Hessian (split-BF16), OPG "
+                               "(split-BF16), top-32 OPG eig (FP64 Gram), 16 networks of the "
+                               "batching distribution, 100 GB workspace budget",
+                   "slots": args.serve_slots, "seconds": args.serve_seconds},
+        "data": "synthetic",
+    }
+    print(json.dumps(line), flush=True)
+
+
 # -------------------------------------------------------------- replicas ----
 def max_over_ranks(value: float, dist=None, device="cpu") -> float:
     """Replicas only: every rank runs the whole workload on its own GPU and
@@ -235,6 +341,9 @@ def main():
         return
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.serve:
+        serve_bench(args)
         return
 
     import numpy as np

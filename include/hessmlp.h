@@ -179,6 +179,54 @@ HESS_API hess_status per_example_grads_noalloc(const hess_mlp_desc* desc, const 
                                                double* G, void* stream);
 
 /* ----------------------------------------------------------------------
+ * Request server (no counterpart in the paper: the paper computes one matrix
+ * per call).  Continuous batching on one GPU: requests for Hessians, OPGs and
+ * top-k OPG eigenpairs of registered networks are admitted in arrival order
+ * as soon as a slot is free and their workspace fits the memory budget; each
+ * slot runs on its own CUDA stream, so admitted requests overlap on the
+ * device.  Network weights stay on the device.  Results are the same as the
+ * single calls above (same kernels, deterministic).
+ * -------------------------------------------------------------------- */
+typedef struct hess_server hess_server;
+
+typedef enum { HESS_REQ_HESSIAN = 0, HESS_REQ_OPG = 1, HESS_REQ_EIG = 2 } hess_request_kind;
+
+typedef struct {
+  int kind;         /* hess_request_kind */
+  int net;          /* id returned by hess_server_add_network */
+  const void* X;    /* N x T_1, host or device; must stay valid until the wait returns */
+  const void* Y;    /* N x T_L */
+  int64_t N;
+  int prec;         /* hess_precision */
+  int k;            /* HESS_REQ_EIG: number of eigenpairs */
+  void* out;        /* P x P (Hessian, OPG) or P x k column-major doubles (eigenvectors) */
+  double* evals;    /* HESS_REQ_EIG: k doubles */
+} hess_request;
+
+/* slots: concurrent requests (1..64); budget_bytes: device memory the slots'
+ * workspaces may hold together.  The current device becomes the server's. */
+HESS_API hess_status hess_server_create(int slots, int64_t budget_bytes, hess_server** out);
+
+/* Copy a network and its parameter point to the device; net_id names it in
+ * requests.  Errors as hess_mlp_create. */
+HESS_API hess_status hess_server_add_network(hess_server* s, const hess_mlp_desc* desc,
+                                             const double* omega, int* net_id);
+
+/* Queue a request.  Its arguments are checked and its workspace planned at
+ * once: HESS_ERR_ADMISSION if it alone exceeds the budget, the usual errors
+ * for bad arguments.  ticket identifies it for hess_server_wait. */
+HESS_API hess_status hess_server_submit(hess_server* s, const hess_request* req, int64_t* ticket);
+
+/* Wait up to timeout_seconds (< 0: no limit) for a request; *result is the
+ * status the request's call returned.  HESS_ERR_TIMEOUT if it is not done
+ * (the ticket stays valid); a finished ticket is released by this call. */
+HESS_API hess_status hess_server_wait(hess_server* s, int64_t ticket, double timeout_seconds,
+                                      hess_status* result);
+
+/* Finish the running requests, fail the queued ones, release everything. */
+HESS_API hess_status hess_server_destroy(hess_server* s);
+
+/* ----------------------------------------------------------------------
  * Measurement hooks (no counterpart in the paper).  When timing is enabled
  * the library brackets every launch of the kernel classes below with CUDA
  * events on the handle's stream, and records the algorithmic work of each

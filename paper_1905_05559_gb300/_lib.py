@@ -32,8 +32,18 @@ EXPORTS = (
     "hess_mlp_create", "hess_mlp_destroy", "hess_mlp_num_params", "hess_mlp_set_params",
     "hess_mlp_set_stream", "per_example_grads", "opg", "exact_hessian", "opg_topk_eig",
     "hess_param_permutation", "hess_last_error", "hess_timing_enable", "hess_timing_read",
-    "hess_launch_count", "per_example_grads_noalloc",
+    "hess_launch_count", "per_example_grads_noalloc", "hess_server_create",
+    "hess_server_add_network", "hess_server_submit", "hess_server_wait", "hess_server_destroy",
 )
+
+REQUEST_KIND = {"hessian": 0, "opg": 1, "eig": 2}
+
+
+class HessRequest(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("net", ctypes.c_int), ("X", ctypes.c_void_p),
+                ("Y", ctypes.c_void_p), ("N", ctypes.c_int64), ("prec", ctypes.c_int),
+                ("k", ctypes.c_int), ("out", ctypes.c_void_p),
+                ("evals", ctypes.POINTER(ctypes.c_double))]
 
 KERNEL_CLASS = {"syrk": 0, "hcontract": 1, "grads": 2, "rop": 3, "eig": 4, "hrest": 5}
 
@@ -93,6 +103,16 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.hess_timing_read.restype = st
     lib.per_example_grads_noalloc.argtypes = [ctypes.POINTER(HessDesc), vp, vp, vp, i64, vp, vp]
     lib.per_example_grads_noalloc.restype = st
+    lib.hess_server_create.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.POINTER(vp)]
+    lib.hess_server_create.restype = st
+    lib.hess_server_add_network.argtypes = [vp, ctypes.POINTER(HessDesc), vp, ctypes.POINTER(ctypes.c_int)]
+    lib.hess_server_add_network.restype = st
+    lib.hess_server_submit.argtypes = [vp, ctypes.POINTER(HessRequest), ctypes.POINTER(ctypes.c_int64)]
+    lib.hess_server_submit.restype = st
+    lib.hess_server_wait.argtypes = [vp, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]
+    lib.hess_server_wait.restype = st
+    lib.hess_server_destroy.argtypes = [vp]
+    lib.hess_server_destroy.restype = st
     lib.hess_launch_count.argtypes = []
     lib.hess_launch_count.restype = ctypes.c_int64
     lib.hess_last_error.argtypes = []

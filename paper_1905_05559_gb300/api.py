@@ -146,3 +146,53 @@ class HessMLP:
         if torch is not None and isinstance(X, torch.Tensor):
             return torch.empty(shape, dtype=getattr(torch, dt), device=X.device)
         return np.empty(shape, dtype=dt)
+
+
+class HessServer:
+    """Continuous-batching request server (hess_server_*): marshalling only."""
+
+    def __init__(self, slots=4, budget_bytes=100 << 30):
+        self._lib = _lib.load()
+        s = ctypes.c_void_p()
+        _lib.check(self._lib.hess_server_create(int(slots), int(budget_bytes), ctypes.byref(s)))
+        self.s = s
+        self._keep = {}
+
+    def add_network(self, widths, acts, omega):
+        w = (ctypes.c_int * len(widths))(*[int(t) for t in widths])
+        a = (ctypes.c_int * max(1, len(acts)))(*([_lib.ACT[x] for x in acts] or [0]))
+        desc = _lib.HessDesc(len(widths), w, a)
+        omega = np.ascontiguousarray(omega, dtype=np.float64)
+        nid = ctypes.c_int()
+        _lib.check(self._lib.hess_server_add_network(self.s, ctypes.byref(desc), _ptr(omega),
+                                                     ctypes.byref(nid)))
+        return nid.value
+
+    def submit(self, kind, net, X, Y, prec, out, k=0, evals=None):
+        """Queue a request; X, Y, out (and evals) must stay alive until wait()."""
+        r = _lib.HessRequest(_lib.REQUEST_KIND[kind], int(net), _ptr(X), _ptr(Y), int(X.shape[0]),
+                             _lib.PRECISION[prec], int(k), _ptr(out),
+                             ctypes.cast(_ptr(evals), ctypes.POINTER(ctypes.c_double))
+                             if evals is not None else None)
+        t = ctypes.c_int64()
+        _lib.check(self._lib.hess_server_submit(self.s, ctypes.byref(r), ctypes.byref(t)))
+        self._keep[t.value] = (X, Y, out, evals)
+        return t.value
+
+    def wait(self, ticket, timeout=-1.0):
+        """Returns the request's status (raises on a wait timeout)."""
+        res = ctypes.c_int()
+        _lib.check(self._lib.hess_server_wait(self.s, int(ticket), float(timeout), ctypes.byref(res)))
+        self._keep.pop(ticket, None)
+        return res.value
+
+    def close(self):
+        if getattr(self, "s", None):
+            self._lib.hess_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

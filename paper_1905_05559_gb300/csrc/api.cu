@@ -82,7 +82,13 @@ hess_status make_net(const hess_mlp_desc* desc, Net* out) {
   return HESS_OK;
 }
 
+thread_local size_t* g_dry_bytes = nullptr;
+
 hess_status ensure_ws(hess_mlp* h, size_t bytes) {
+  if (g_dry_bytes) {
+    *g_dry_bytes = bytes;
+    return kDryRun;
+  }
   if (bytes <= h->ws_bytes) return HESS_OK;
   if (h->ws) {
     HM_CUDA(cudaStreamSynchronize(h->stream));
@@ -499,8 +505,10 @@ hess_status hess_mlp_destroy(hess_mlp* h) {
   if (!h) return HESS_OK;
   Guard g(h->device);
   cudaStreamSynchronize(h->stream);
-  cudaFree(h->omega64);
-  cudaFree(h->omega32);
+  if (h->owns_params) {
+    cudaFree(h->omega64);
+    cudaFree(h->omega32);
+  }
   cudaFree(h->ws);
   if (h->host_pinned) cudaFreeHost(h->host_pinned);
   for (auto& r : h->pending) {

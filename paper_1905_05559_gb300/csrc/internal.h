@@ -86,6 +86,7 @@ struct TimingRec {
 
 struct hess_mlp {
   hm::Net net;
+  bool owns_params = true;  // false: omega64/omega32 borrowed from another handle
   bool timing = false;
   std::vector<hm::TimingRec> pending;
   std::vector<cudaEvent_t> event_pool;
@@ -103,6 +104,12 @@ struct hess_mlp {
 namespace hm {
 
 hess_status ensure_ws(hess_mlp* h, size_t bytes);
+
+// Planning without work: while a dry run is active on this thread, ensure_ws
+// records the workspace a call needs and makes the call return kDryRun before
+// any GPU work is queued.
+constexpr hess_status kDryRun = static_cast<hess_status>(100);
+extern thread_local size_t* g_dry_bytes;
 
 // Brackets launches with CUDA events when the handle's timing is enabled.
 class Tick {
