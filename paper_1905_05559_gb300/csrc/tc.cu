@@ -48,27 +48,35 @@ constexpr long long TIMEOUT_CYCLES = 4000000000ll;  // ~2 s at 2 GHz
 // tensor cores' own accumulation does not grow with N.
 constexpr int CHUNK_KB = 16;
 
-struct Params {
+// One contraction: its four operand tensor maps, shape, K and output mapping.
+// A persistent launch walks a list of tiles (job, row tile, column tile), so
+// one launch can serve many contractions of different shapes.
+struct alignas(64) Job {
+  CUtensorMap a_hi, a_lo, b_hi, b_lo;
   int64_t M;      // valid rows of A
   int64_t Nn;     // valid rows of B (= columns of the product)
   int BN;         // tile columns (multiple of 16, <= 256)
   int nkb;        // k-blocks of 64
-  int passes;     // 1: hi*hi;  3: hi*hi + hi*lo + lo*hi (one stage holds all four tiles)
-  uint32_t idesc; // instruction descriptor
-  const int2* tiles;
-  int ntiles;
-  float scale;
-  float* out;
-  int64_t ldo;
+  uint32_t idesc; // instruction descriptor (N = BN)
   int mode;       // 0: symmetric rank-K update (orow = m, ocol = n)
                   // 1: Hessian rows of one weight layer, W columns (see row_map)
                   // 2: Hessian rows of one weight layer, columns after W (see row_map)
+  float scale;
+  float* out;
+  int64_t ldo;
   int64_t woff;   // modes 1, 2: offset of W in omega
   int64_t boff;   // mode 2: first column (the layer's bias)
   int Tin, Tout, p0;
   int64_t R0;     // mode 1: first concatenated row of unit p0
   int ntn;        // mode 2: column tiles per unit
   int64_t brow;   // mode 2: B rows per unit
+};
+
+struct Launch {
+  const Job* jobs;
+  const int4* tiles;  // (job, row tile, column tile, 0)
+  int ntiles;
+  int passes;         // 1: hi*hi;  3: hi*hi + hi*lo + lo*hi (one stage holds all four tiles)
   int* err;
 };
 
@@ -199,7 +207,7 @@ __host__ __device__ __forceinline__ int64_t rows_before(int64_t p, int64_t Tin, 
 // the Hessian column W_(i,k).  Mode 2: the tile's unit u = tile_y / ntn; rows
 // are the directions W_(u,q) and the product column n is the n-th Hessian
 // column from the layer's bias on.
-__device__ __forceinline__ void row_map(const Params& p, int64_t m, int tile_y, int64_t& orow,
+__device__ __forceinline__ void row_map(const Job& p, int64_t m, int tile_y, int64_t& orow,
                                         int64_t& ocolb) {
   if (p.mode == 0) {
     orow = m;
@@ -226,9 +234,7 @@ __device__ __forceinline__ void row_map(const Params& p, int64_t m, int tile_y, 
 }
 
 __global__ void __launch_bounds__(THREADS, 1)
-    umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
-                const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
-                const Params p) {
+    umma_gemm_kernel(const Launch L) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -237,7 +243,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * MAXSTAGES + 4);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
-  const bool x3 = p.passes == 3;
+  const bool x3 = L.passes == 3;
   const int STAGES = x3 ? 2 : 4;
   const int STAGE_BYTES = x3 ? 2 * (A_BYTES + B_BYTES) : (A_BYTES + B_BYTES);
   // offsets inside a stage (all multiples of 1024 bytes)
@@ -260,8 +266,6 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA_hi)) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB_hi)) : "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -274,31 +278,44 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  const int nvk = p.nkb;
-  const uint32_t tx_bytes = (A_BYTES + p.BN * BK * 2) * (x3 ? 2 : 1);
 
   if (warp == 0) {
     if (lane == 0) {
       int it = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
-        const int2 tile = p.tiles[t];
-        for (int j = 0; j < nvk; ++j, ++it) {
+      int last_job = -1;
+      for (int t = blockIdx.x; t < L.ntiles && ok; t += gridDim.x) {
+        const int4 tile = L.tiles[t];
+        const Job& jb = L.jobs[tile.x];
+        if (tile.x != last_job) {
+          // the maps live in global memory, written before the launch
+          const CUtensorMap* maps[4] = {&jb.a_hi, &jb.a_lo, &jb.b_hi, &jb.b_lo};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                             reinterpret_cast<uint64_t>(maps[q]))
+                         : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(maps[q])) : "memory");
+          }
+          last_job = tile.x;
+        }
+        const uint32_t tx_bytes = (A_BYTES + jb.BN * BK * 2) * (x3 ? 2 : 1);
+        const int brow0 = jb.mode == 2 ? (int)((tile.z / jb.ntn) * jb.brow + (tile.z % jb.ntn) * jb.BN)
+                                       : tile.z * jb.BN;
+        for (int j = 0; j < jb.nkb; ++j, ++it) {
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1;
-          if (!mbar_wait(empty(s), ph ^ 1, p.err, abort_flag)) {
+          if (!mbar_wait(empty(s), ph ^ 1, L.err, abort_flag)) {
             ok = false;
             break;
           }
           uint8_t* st = smem + s * STAGE_BYTES;
           mbar_expect_tx(full(s), tx_bytes);
-          tma_load_2d(smem_u32(st), &tmA_hi, j * BK, tile.x * BM, full(s));
-          const int brow0 = p.mode == 2 ? (int)((tile.y / p.ntn) * p.brow + (tile.y % p.ntn) * p.BN)
-                                        : tile.y * p.BN;
-          tma_load_2d(smem_u32(st + OFF_BHI), &tmB_hi, j * BK, brow0, full(s));
+          tma_load_2d(smem_u32(st), &jb.a_hi, j * BK, tile.y * BM, full(s));
+          tma_load_2d(smem_u32(st + OFF_BHI), &jb.b_hi, j * BK, brow0, full(s));
           if (x3) {
-            tma_load_2d(smem_u32(st + OFF_ALO), &tmA_lo, j * BK, tile.x * BM, full(s));
-            tma_load_2d(smem_u32(st + OFF_BLO), &tmB_lo, j * BK, brow0, full(s));
+            tma_load_2d(smem_u32(st + OFF_ALO), &jb.a_lo, j * BK, tile.y * BM, full(s));
+            tma_load_2d(smem_u32(st + OFF_BLO), &jb.b_lo, j * BK, brow0, full(s));
           }
         }
       }
@@ -318,14 +335,16 @@ __global__ void __launch_bounds__(THREADS, 1)
       int it = 0, tcount = 0;
       unsigned uses[2] = {0u, 0u};  // chunks written into each TMEM buffer so far
       bool ok = true;
-      const int nchunk = (nvk + CHUNK_KB - 1) / CHUNK_KB;
-      for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x, ++tcount) {
+      for (int t = blockIdx.x; t < L.ntiles && ok; t += gridDim.x, ++tcount) {
+        const Job& jb = L.jobs[L.tiles[t].x];
+        const int nvk = jb.nkb;
+        const int nchunk = (nvk + CHUNK_KB - 1) / CHUNK_KB;
         // the first chunk goes to the tile's main buffer, the others to the
         // second buffer, which the epilogue merges into the main one
         const int mainb = tcount & 1;
         for (int ch = 0; ch < nchunk && ok; ++ch) {
           const int buf = ch == 0 ? mainb : mainb ^ 1;
-          if (!mbar_wait(tempty(buf), (uses[buf] & 1u) ^ 1u, p.err, abort_flag)) {
+          if (!mbar_wait(tempty(buf), (uses[buf] & 1u) ^ 1u, L.err, abort_flag)) {
             ok = false;
             break;
           }
@@ -336,7 +355,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int j = j0; j < j1; ++j, ++it) {
             const int s = it % STAGES;
             const uint32_t ph = (it / STAGES) & 1;
-            if (!mbar_wait(full(s), ph, p.err, abort_flag)) {
+            if (!mbar_wait(full(s), ph, L.err, abort_flag)) {
               ok = false;
               break;
             }
@@ -346,14 +365,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             const uint64_t bh = sdesc(smem_u32(st + OFF_BHI));
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk)
-              umma_bf16(d_tmem, ah + 2 * kk, bh + 2 * kk, p.idesc, (j > j0 || kk > 0) ? 1u : 0u);
+              umma_bf16(d_tmem, ah + 2 * kk, bh + 2 * kk, jb.idesc, (j > j0 || kk > 0) ? 1u : 0u);
             if (x3) {
               const uint64_t al = sdesc(smem_u32(st + OFF_ALO));
               const uint64_t bl = sdesc(smem_u32(st + OFF_BLO));
 #pragma unroll
-              for (int kk = 0; kk < BK / 16; ++kk) umma_bf16(d_tmem, ah + 2 * kk, bl + 2 * kk, p.idesc, 1u);
+              for (int kk = 0; kk < BK / 16; ++kk) umma_bf16(d_tmem, ah + 2 * kk, bl + 2 * kk, jb.idesc, 1u);
 #pragma unroll
-              for (int kk = 0; kk < BK / 16; ++kk) umma_bf16(d_tmem, al + 2 * kk, bh + 2 * kk, p.idesc, 1u);
+              for (int kk = 0; kk < BK / 16; ++kk) umma_bf16(d_tmem, al + 2 * kk, bh + 2 * kk, jb.idesc, 1u);
             }
             umma_commit(empty(s));
           }
@@ -367,19 +386,21 @@ __global__ void __launch_bounds__(THREADS, 1)
     float* e = epi + (warp - 2) * 32 * EPI_LD;
     int tcount = 0;
     unsigned fulls[2] = {0u, 0u};  // chunk results consumed from each TMEM buffer
-    const int nchunk = (p.nkb + CHUNK_KB - 1) / CHUNK_KB;
     const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
     bool alive = true;
-    for (int t = blockIdx.x; t < p.ntiles && alive; t += gridDim.x, ++tcount) {
+    for (int t = blockIdx.x; t < L.ntiles && alive; t += gridDim.x, ++tcount) {
+      const int4 tile = L.tiles[t];
+      const Job& p = L.jobs[tile.x];
+      const int nchunk = (p.nkb + CHUNK_KB - 1) / CHUNK_KB;
       const int acc = tcount & 1;
-      const bool got = mbar_wait(tfull(acc), fulls[acc] & 1u, p.err, abort_flag);
+      const bool got = mbar_wait(tfull(acc), fulls[acc] & 1u, L.err, abort_flag);
       if (__any_sync(0xffffffffu, !got)) break;
       ++fulls[acc];
       tc_fence_after();
       // merge the later K chunks into the main accumulator
       const int part = acc ^ 1;
       for (int ch = 1; ch < nchunk; ++ch) {
-        const bool g2 = mbar_wait(tfull(part), fulls[part] & 1u, p.err, abort_flag);
+        const bool g2 = mbar_wait(tfull(part), fulls[part] & 1u, L.err, abort_flag);
         if (__any_sync(0xffffffffu, !g2)) {
           alive = false;
           break;
@@ -400,12 +421,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         mbar_arrive(tempty(part));
       }
       if (!alive) break;
-      const int2 tile = p.tiles[t];
-      const int64_t m = (int64_t)tile.x * BM + q * 32 + lane;
+      const int64_t m = (int64_t)tile.y * BM + q * 32 + lane;
       const bool rvalid = m < p.M;
       int64_t orow = 0, ocolb = 0;
-      if (rvalid) row_map(p, m, tile.y, orow, ocolb);
-      const int64_t nbase = p.mode == 2 ? (int64_t)(tile.y % p.ntn) * p.BN : (int64_t)tile.y * p.BN;
+      if (rvalid) row_map(p, m, tile.z, orow, ocolb);
+      const int64_t nbase = p.mode == 2 ? (int64_t)(tile.z % p.ntn) * p.BN : (int64_t)tile.z * p.BN;
       __syncwarp();
       const uint32_t tbase = tmem_base + acc * MAXBN + (static_cast<uint32_t>(q * 32) << 16);
       for (int c = 0; c < p.BN / 16; ++c) {
@@ -659,24 +679,35 @@ struct TcOperands {
   int64_t ld;
 };
 
-// Launch the persistent kernel over the given tile list (device int2 array).
-hess_status launch_tc(hess_mlp* h, const TcOperands& op, tc::Params p, int BN, cudaStream_t s) {
+// Fill a job's operand maps, K and instruction descriptor; the caller sets
+// the shape and output mapping.
+hess_status make_job(const TcOperands& op, int BN, tc::Job* j) {
   using namespace tc;
-  CUtensorMap ma, mal, mb, mbl;
-  HM_TRY(make_map(&ma, op.Ahi, op.ld, op.arows, BM));
-  HM_TRY(make_map(&mal, op.Alo, op.ld, op.arows, BM));
-  HM_TRY(make_map(&mb, op.Bhi, op.ld, op.brows, BN));
-  HM_TRY(make_map(&mbl, op.Blo, op.ld, op.brows, BN));
+  HM_TRY(make_map(&j->a_hi, op.Ahi, op.ld, op.arows, BM));
+  HM_TRY(make_map(&j->a_lo, op.Alo, op.ld, op.arows, BM));
+  HM_TRY(make_map(&j->b_hi, op.Bhi, op.ld, op.brows, BN));
+  HM_TRY(make_map(&j->b_lo, op.Blo, op.ld, op.brows, BN));
+  j->BN = BN;
+  j->nkb = (int)(op.ld / BK);
+  j->idesc = make_idesc(BN);
+  return HESS_OK;
+}
+
+// Copy jobs and tiles to the device regions given and launch the
+// persistent kernel over them.
+hess_status launch_jobs(hess_mlp* h, const tc::Job* jobs, int njobs, const int4* tiles, int ntiles,
+                        tc::Job* jobs_d, int4* tiles_d, bool x3, int* err, cudaStream_t s) {
+  using namespace tc;
+  if (ntiles < 1) return HESS_OK;
   if (!g_attr_set) {
     HM_CUDA(cudaFuncSetAttribute(umma_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     g_attr_set = true;
   }
-  p.BN = BN;
-  p.nkb = (int)(op.ld / BK);
-  p.idesc = make_idesc(BN);
-  int grid = p.ntiles < h->sm_count ? p.ntiles : h->sm_count;
-  if (grid < 1) return HESS_OK;
-  umma_gemm_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(ma, mal, mb, mbl, p);
+  HM_CUDA(cudaMemcpyAsync(jobs_d, jobs, njobs * sizeof(Job), cudaMemcpyHostToDevice, s));
+  HM_CUDA(cudaMemcpyAsync(tiles_d, tiles, ntiles * sizeof(int4), cudaMemcpyHostToDevice, s));
+  Launch L{jobs_d, tiles_d, ntiles, x3 ? 3 : 1, err};
+  const int grid = ntiles < h->sm_count ? ntiles : h->sm_count;
+  umma_gemm_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(L);
   HM_LAUNCHED();
   return HESS_OK;
 }
@@ -718,6 +749,18 @@ hess_status classify_ptr(const hess_mlp* h, const void* p, int* on_dev) {
 
 double hcontract_flops(const Net& net, int64_t N, int jm, int jl, int64_t d0, int B);
 
+// Upper tiles of a P x P symmetric update with BM x BN tiles (the column
+// range reaches the diagonal), grouped by 8 tile rows so that concurrent tiles
+// share operand panels in L2.
+void syrk_tiles(int64_t P, int BN, int job, std::vector<int4>& tiles) {
+  using namespace tc;
+  const int64_t mt = cdiv(P, BM), nt = cdiv(P, BN);
+  for (int64_t g0 = 0; g0 < mt; g0 += 8)
+    for (int64_t tn = 0; tn < nt; ++tn)
+      for (int64_t tm = g0; tm < g0 + 8 && tm < mt; ++tm)
+        if (tn * BN + BN - 1 >= tm * BM) tiles.push_back(make_int4(job, (int)tm, (int)tn, 0));
+}
+
 // OPG = G^T G / N with split-BF16 (or BF16) operands on the tensor cores.
 hess_status run_opg_tc(hess_mlp* h, const void* X, const void* Y, int64_t N, bool x3, void* Oout) {
   using namespace tc;
@@ -730,17 +773,11 @@ hess_status run_opg_tc(hess_mlp* h, const void* X, const void* Y, int64_t N, boo
   HM_TRY(classify_ptr(h, Oout, &o_dev));
   const int64_t ld = align_up((size_t)N, BK);
   const int BN = 256;
-  const int64_t mt = cdiv(P, BM), nt = cdiv(P, BN);
-  std::vector<int2> tiles;
-  // upper tiles (the column range reaches the diagonal), grouped by 8 tile
-  // rows so that concurrent tiles share operand panels in L2
-  for (int64_t g0 = 0; g0 < mt; g0 += 8)
-    for (int64_t tn = 0; tn < nt; ++tn)
-      for (int64_t tm = g0; tm < g0 + 8 && tm < mt; ++tm)
-        if (tn * BN + BN - 1 >= tm * BM) tiles.push_back(make_int2((int)tm, (int)tn));
+  std::vector<int4> tiles;
+  syrk_tiles(P, BN, 0, tiles);
   char* split = nullptr;
   auto plan = [&](Arena& ar, float*& xs, float*& ys, Caches<float>& c, float*& G, __nv_bfloat16*& hi,
-                  __nv_bfloat16*& lo, float*& O, int2*& tl, int*& err) {
+                  __nv_bfloat16*& lo, float*& O, int4*& tl, Job*& jd, int*& err) {
     xs = x_dev ? nullptr : ar.take<float>(N * T1);
     ys = y_dev ? nullptr : ar.take<float>(N * TL);
     plan_caches(ar, net, N, c);
@@ -748,20 +785,22 @@ hess_status run_opg_tc(hess_mlp* h, const void* X, const void* Y, int64_t N, boo
     hi = ar.take<__nv_bfloat16>(P * ld);
     lo = ar.take<__nv_bfloat16>(P * ld);
     O = o_dev ? (float*)Oout : ar.take<float>(P * P);
-    tl = ar.take<int2>(tiles.size());
+    tl = ar.take<int4>(tiles.size());
+    jd = ar.take<Job>(1);
     err = ar.take<int>(1);
     split = ar.take<char>(kSplitBytes);
   };
   Arena ar;
   float *xs, *ys, *G, *O;
   __nv_bfloat16 *hi, *lo;
-  int2* tl;
+  int4* tl;
+  Job* jd;
   int* err;
   Caches<float> c;
-  plan(ar, xs, ys, c, G, hi, lo, O, tl, err);
+  plan(ar, xs, ys, c, G, hi, lo, O, tl, jd, err);
   HM_TRY(ensure_ws(h, ar.off));
   ar = Arena{h->ws, 0};
-  plan(ar, xs, ys, c, G, hi, lo, O, tl, err);
+  plan(ar, xs, ys, c, G, hi, lo, O, tl, jd, err);
   SplitGuard sg(split, kSplitBytes, h->sm_count);
   cudaStream_t s = h->stream;
   const float* xd = (const float*)X;
@@ -774,7 +813,6 @@ hess_status run_opg_tc(hess_mlp* h, const void* X, const void* Y, int64_t N, boo
     HM_CUDA(cudaMemcpyAsync(ys, Y, N * TL * 4, cudaMemcpyHostToDevice, s));
     yd = ys;
   }
-  HM_CUDA(cudaMemcpyAsync(tl, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
   HM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
   HM_TRY(forward_backward(net, (const float*)h->omega32, xd, yd, c, s));
   {
@@ -784,21 +822,18 @@ hess_status run_opg_tc(hess_mlp* h, const void* X, const void* Y, int64_t N, boo
   transpose_split_kernel<<<dim3((unsigned)cdiv(ld, 32), (unsigned)cdiv(P, 32)), dim3(32, 8), 0, s>>>(
       G, N, P, P, hi, lo, ld);
   HM_LAUNCHED();
-  Params p{};
-  p.M = P;
-  p.Nn = P;
-  p.passes = x3 ? 3 : 1;
-  p.tiles = tl;
-  p.ntiles = (int)tiles.size();
-  p.scale = 1.0f / (float)N;
-  p.out = O;
-  p.ldo = P;
-  p.mode = 0;
-  p.err = err;
+  Job job{};
   TcOperands op{hi, lo, P, hi, lo, P, ld};
+  HM_TRY(make_job(op, BN, &job));
+  job.M = P;
+  job.Nn = P;
+  job.scale = 1.0f / (float)N;
+  job.out = O;
+  job.ldo = P;
+  job.mode = 0;
   {
     Tick t(h, HESS_K_SYRK, (double)N * P * (P + 1), 0.0);
-    HM_TRY(launch_tc(h, op, p, BN, s));
+    HM_TRY(launch_jobs(h, &job, 1, tiles.data(), (int)tiles.size(), jd, tl, x3, err, s));
   }
   if (!o_dev) HM_CUDA(cudaMemcpyAsync(Oout, O, P * P * 4, cudaMemcpyDeviceToHost, s));
   return check_err_flag(h, err);
@@ -861,7 +896,7 @@ hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N,
                   float*& tmp, float*& ones, __nv_bfloat16*& bhi, __nv_bfloat16*& blo,
                   __nv_bfloat16*& ahi, __nv_bfloat16*& alo, __nv_bfloat16*& fhi,
                   __nv_bfloat16*& flo, float*& O,
-                  int2*& tl, int*& err) {
+                  int4*& tl, Job*& jd, int*& err) {
     xs = x_dev ? nullptr : ar.take<float>(N * T1);
     ys = y_dev ? nullptr : ar.take<float>(N * TL);
     plan_caches(ar, net, N, c);
@@ -875,21 +910,23 @@ hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N,
     fhi = ar.take<__nv_bfloat16>((int64_t)pchunk * maxRest * ld);
     flo = ar.take<__nv_bfloat16>((int64_t)pchunk * maxRest * ld);
     O = o_dev ? (float*)Hout : ar.take<float>(P * P);
-    tl = ar.take<int2>(max_tiles);
+    tl = ar.take<int4>(max_tiles);
+    jd = ar.take<Job>(1);
     err = ar.take<int>(1);
     split = ar.take<char>(kSplitBytes);
   };
   Arena ar;
   float *xs, *ys, *tmp, *ones, *O;
   __nv_bfloat16 *bhi, *blo, *ahi, *alo, *fhi, *flo;
-  int2* tl;
+  int4* tl;
+  Job* jd;
   int* err;
   Caches<float> c;
   RopBufs<float> r;
-  plan(ar, xs, ys, c, r, tmp, ones, bhi, blo, ahi, alo, fhi, flo, O, tl, err);
+  plan(ar, xs, ys, c, r, tmp, ones, bhi, blo, ahi, alo, fhi, flo, O, tl, jd, err);
   HM_TRY(ensure_ws(h, ar.off));
   ar = Arena{h->ws, 0};
-  plan(ar, xs, ys, c, r, tmp, ones, bhi, blo, ahi, alo, fhi, flo, O, tl, err);
+  plan(ar, xs, ys, c, r, tmp, ones, bhi, blo, ahi, alo, fhi, flo, O, tl, jd, err);
   SplitGuard sg(split, kSplitBytes, h->sm_count);
   cudaStream_t s = h->stream;
   const float* xd = (const float*)X;
@@ -906,7 +943,7 @@ hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N,
   HM_TRY(fill(ones, N, 1.0f, s));
   const float* omega = h->omega32;
   HM_TRY(forward_backward(net, omega, xd, yd, c, s));
-  std::vector<int2> tiles;
+  std::vector<int4> tiles;
   for (int jm = 1; jm < L; ++jm) {
     const int Tin = net.T[jm - 1], Tout = net.T[jm];
     const int64_t woff = net.woff[jm - 1], boff = net.boff[jm - 1];
@@ -935,25 +972,21 @@ hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N,
       HM_LAUNCHED();
       tiles.clear();
       for (int64_t tm = 0; tm < cdiv(rows, BM); ++tm)
-        for (int64_t tn = 0; tn < cdiv(Tin, BN); ++tn) tiles.push_back(make_int2((int)tm, (int)tn));
-      HM_CUDA(cudaMemcpyAsync(tl, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
-      Params p{};
-      p.M = rows;
-      p.Nn = Tin;
-      p.passes = x3 ? 3 : 1;
-      p.tiles = tl;
-      p.ntiles = (int)tiles.size();
-      p.scale = 1.0f / (float)N;
-      p.out = O;
-      p.ldo = P;
-      p.mode = 1;
-      p.woff = woff;
-      p.Tin = Tin;
-      p.Tout = Tout;
-      p.p0 = p0;
-      p.R0 = R0;
-      p.err = err;
+        for (int64_t tn = 0; tn < cdiv(Tin, BN); ++tn) tiles.push_back(make_int4(0, (int)tm, (int)tn, 0));
+      Job job{};
       TcOperands op{ahi, alo, rows, bhi, blo, Tin, ld};
+      HM_TRY(make_job(op, BN, &job));
+      job.M = rows;
+      job.Nn = Tin;
+      job.scale = 1.0f / (float)N;
+      job.out = O;
+      job.ldo = P;
+      job.mode = 1;
+      job.woff = woff;
+      job.Tin = Tin;
+      job.Tout = Tout;
+      job.p0 = p0;
+      job.R0 = R0;
       {
         // upper-triangle entries of this block's rows: 2N flops each
         double ent = 0.0;
@@ -961,11 +994,8 @@ hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N,
           for (int q = 0; q < Tin; ++q)
             ent += (double)(Tout - u) * Tin - q;
         Tick t(h, HESS_K_HCONTRACT, 2.0 * N * ent, 0.0);
-        HM_TRY(launch_tc(h, op, p, BN, s));
+        HM_TRY(launch_jobs(h, &job, 1, tiles.data(), (int)tiles.size(), jd, tl, x3, err, s));
       }
-      // the copy of the tile list must not be overwritten before the kernel
-      // has read it
-      HM_CUDA(cudaStreamSynchronize(s));
       p0 = p1;
     }
     // columns after W: the bias of this layer and every later layer
@@ -1010,32 +1040,27 @@ hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N,
       tiles.clear();
       for (int64_t tm = 0; tm < cdiv(Tin, BM); ++tm)
         for (int u = 0; u < pc; ++u)
-          for (int tn = 0; tn < ntn; ++tn) tiles.push_back(make_int2((int)tm, u * ntn + tn));
-      HM_CUDA(cudaMemcpyAsync(tl, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
-      Params p{};
-      p.M = Tin;
-      p.Nn = rest;
-      p.passes = x3 ? 3 : 1;
-      p.tiles = tl;
-      p.ntiles = (int)tiles.size();
-      p.scale = 1.0f / (float)N;
-      p.out = O;
-      p.ldo = P;
-      p.mode = 2;
-      p.woff = woff;
-      p.boff = boff;
-      p.Tin = Tin;
-      p.Tout = Tout;
-      p.p0 = q0;
-      p.ntn = ntn;
-      p.brow = rest;
-      p.err = err;
+          for (int tn = 0; tn < ntn; ++tn) tiles.push_back(make_int4(0, (int)tm, u * ntn + tn, 0));
+      Job job{};
       TcOperands op{bhi, blo, Tin, fhi, flo, (int64_t)pc * rest, ld};
+      HM_TRY(make_job(op, BN2, &job));
+      job.M = Tin;
+      job.Nn = rest;
+      job.scale = 1.0f / (float)N;
+      job.out = O;
+      job.ldo = P;
+      job.mode = 2;
+      job.woff = woff;
+      job.boff = boff;
+      job.Tin = Tin;
+      job.Tout = Tout;
+      job.p0 = q0;
+      job.ntn = ntn;
+      job.brow = rest;
       {
         Tick t(h, HESS_K_HCONTRACT, 2.0 * N * (double)pc * Tin * rest, 0.0);
-        HM_TRY(launch_tc(h, op, p, BN2, s));
+        HM_TRY(launch_jobs(h, &job, 1, tiles.data(), (int)tiles.size(), jd, tl, x3, err, s));
       }
-      HM_CUDA(cudaStreamSynchronize(s));
     }
   }
   if (!o_dev) HM_CUDA(cudaMemcpyAsync(Hout, O, P * P * 4, cudaMemcpyDeviceToHost, s));
