@@ -62,6 +62,11 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--batch", action="store_true",
+                    help="the many-networks workload: OPG + exact Hessian of 256 networks in waves")
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--batch-workspace-gb", type=float, default=64.0)
+    ap.add_argument("--batch-out-gb", type=float, default=96.0)
     ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -287,6 +292,133 @@ def serve_bench(args):
     print(json.dumps(line), flush=True)
 
 
+def batch_bench(args):
+    """The many-networks workload: networks 0..count-1 of the batching
+    distribution (seed 3; 2-4 weight layers, P in [500, 20000], N in
+    [64, 2048]), the OPG and the exact Hessian of each in split-BF16 through
+    hess_batch_run.  The outputs of all 256 networks (~273 GB in FP32) do not
+    fit in HBM, so a step runs the list in groups whose outputs fit an output
+    pool; inside a group the batch forms waves of one persistent tensor-core
+    launch each.  Every finished matrix is checked outside the timed region
+    (finite, sampled symmetry, trace(OPG) = ||G||_F^2 / N with G from
+    per_example_grads) before its memory is reused by the next group."""
+    import numpy as np
+    import torch
+
+    import paper_1905_05559_gb300 as hm
+    from paper_1905_05559_gb300 import build
+    from synth.inputs import make_batch_problem
+
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    lib = hm.load()
+    pbs = [make_batch_problem(3, i) for i in range(args.batch_count)]
+    nets = [hm.HessMLP(pb.widths, pb.acts, pb.omega, stream=stream.cuda_stream) for pb in pbs]
+    Xs = [torch.as_tensor(pb.X, dtype=torch.float32, device="cuda") for pb in pbs]
+    Ys = [torch.as_tensor(pb.Y, dtype=torch.float32, device="cuda") for pb in pbs]
+    pool = torch.empty(int(args.batch_out_gb * (1 << 30)) // 4, dtype=torch.float32, device="cuda")
+    groups, cur, used = [], [], 0
+    for i, pb in enumerate(pbs):
+        need = 2 * ((pb.P * pb.P + 63) // 64 * 64)
+        if cur and used + need > pool.numel():
+            groups.append(cur)
+            cur, used = [], 0
+        cur.append(i)
+        used += need
+    groups.append(cur)
+    batch = hm.HessBatch(int(args.batch_workspace_gb * (1 << 30)), stream=stream.cuda_stream)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rng = np.random.default_rng(3)
+
+    def group_outputs(g):
+        off, outs = 0, []
+        for i in g:
+            P = pbs[i].P
+            sz = (P * P + 63) // 64 * 64
+            o = pool[off:off + P * P].view(P, P)
+            off += sz
+            h = pool[off:off + P * P].view(P, P)
+            off += sz
+            outs.append((o, h))
+        return outs
+
+    def check(i, o, h):
+        pb = pbs[i]
+        assert bool(torch.isfinite(o).all()) and bool(torch.isfinite(h).all()), i
+        r = torch.as_tensor(rng.choice(pb.P, size=min(64, pb.P), replace=False), device="cuda")
+        c = torch.as_tensor(rng.choice(pb.P, size=min(64, pb.P), replace=False), device="cuda")
+        for m in (o, h):
+            assert torch.equal(m[r][:, c], m[c][:, r].T), i
+        G = nets[i].per_example_grads(Xs[i], Ys[i], "fp32")
+        tr = float((G.double() ** 2).sum()) / pb.N
+        rel = abs(float(torch.trace(o.double())) - tr) / tr
+        # split-BF16 drops the lo*lo term, a bias of about 2^-16 / 3 on
+        # diagonal entries: a loose sanity bound here, parity is in the tests
+        assert rel <= 3e-5, (i, rel)
+        return rel
+
+    def one_pass(do_check):
+        ms = launch_ms = flops = 0.0
+        waves = chunked = 0
+        worst = 0.0
+        for g in groups:
+            outs = group_outputs(g)
+            items = [(nets[i], Xs[i], Ys[i], o, h) for i, (o, h) in zip(g, outs)]
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            info = batch.run(items, "bf16x3")
+            ev1.record(stream)
+            ev1.synchronize()
+            ms += ev0.elapsed_time(ev1)
+            launch_ms += info["launch_ms"]
+            flops += info["flops"]
+            waves += info["waves"]
+            chunked += info["items_chunked"]
+            if do_check:
+                for i, (o, h) in zip(g, outs):
+                    worst = max(worst, check(i, o, h))
+        return ms, launch_ms, flops, waves, chunked, worst
+
+    for _ in range(args.warmup):
+        one_pass(False)
+    sampler = ClockSampler(gpu_index(0))
+    sampler.start()
+    l0 = lib.hess_launch_count()
+    runs = [one_pass(True) for _ in range(args.steps)]
+    launches = (lib.hess_launch_count() - l0) / args.steps
+    clocks = sampler.stop()
+    ms = statistics.median(r[0] for r in runs)
+    launch_ms = statistics.median(r[1] for r in runs)
+    flops, waves, chunked = runs[0][2], runs[0][3], runs[0][4]
+    entries = float(sum(2.0 * pb.P * pb.P for pb in pbs))
+    peaks, src = measured_peaks()
+    peak = peaks.get("bf16_tflops_sustained") or 1700.0
+    achieved = flops / (launch_ms * 1e-3) / 1e12
+    line = {
+        "metric": "exact-Hessian & OPG entries/s (many networks)", "impl": "ours",
+        "value": entries / (ms * 1e-3), "unit": "entries/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3",
+        "data": "synthetic",
+        "config": {"workload": f"{args.batch_count} MLPs of the batching distribution (seed 3), "
+                               "OPG + exact Hessian each, split-BF16",
+                   "networks": args.batch_count, "groups": len(groups), "waves": waves,
+                   "items_alone": chunked,
+                   "workspace_gb": args.batch_workspace_gb, "output_pool_gb": args.batch_out_gb,
+                   "l2": "outputs and operands far larger than L2"},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel_class": "wave launches",
+                     "peak_source": f"{src} bf16 sustained",
+                     "note": "split-BF16 counts three BF16 products per multiply-add"},
+        "launch_ms_per_step": launch_ms, "prep_ms_per_step": ms - launch_ms,
+        "max_trace_rel": max(r[5] for r in runs), "gpu_launches": launches, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    batch.close()
+
+
+
 # -------------------------------------------------------------- replicas ----
 def max_over_ranks(value: float, dist=None, device="cpu") -> float:
     """Replicas only: every rank runs the whole workload on its own GPU and
@@ -344,6 +476,9 @@ def main():
         return
     if args.serve:
         serve_bench(args)
+        return
+    if args.batch:
+        batch_bench(args)
         return
 
     import numpy as np

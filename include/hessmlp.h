@@ -109,6 +109,12 @@ HESS_API hess_status hess_mlp_set_params(hess_mlp* h, const double* omega);
 /* Change the stream used by later calls. */
 HESS_API hess_status hess_mlp_set_stream(hess_mlp* h, void* stream);
 
+/* Device bytes of split-BF16 operands above which the tensor-core Hessian
+ * (BF16/BF16X3) is built and contracted in chunks, one launch per chunk,
+ * instead of all at once in one launch (default 4 GiB; at least 1 MiB).
+ * Results do not depend on it. */
+HESS_API hess_status hess_mlp_set_operand_limit(hess_mlp* h, int64_t bytes);
+
 /* Per-example gradient matrix (Sec. 3.1 and Sec. 5.2 "get_J_op"; the matrix J
  * of Eq. hesseq3 read with one example per ROW): G is N x P row-major,
  * G[n, :] = dC_n/domega^T with C_n the per-example cross-entropy of Eq. cost.
@@ -225,6 +231,53 @@ HESS_API hess_status hess_server_wait(hess_server* s, int64_t ticket, double tim
 
 /* Finish the running requests, fail the queued ones, release everything. */
 HESS_API hess_status hess_server_destroy(hess_server* s);
+
+/* ----------------------------------------------------------------------
+ * Batched curvature matrices (no counterpart in the paper, which computes the
+ * matrices of one network per call).  The OPG and/or exact Hessian of many
+ * networks, each with its own data, in waves: a wave builds the operands of
+ * as many items (in list order) as fit the batch's workspace, then contracts
+ * every item of the wave in ONE persistent tensor-core launch.  An item whose
+ * operands exceed the workspace alone runs by itself through opg() and
+ * exact_hessian().  Each matrix is bit-identical to the single-network call
+ * at the same precision.
+ * -------------------------------------------------------------------- */
+typedef struct hess_batch hess_batch;
+
+typedef struct {
+  hess_mlp* net;      /* network and parameter point (its stream is not used) */
+  const float* X;     /* N x T_1 row-major, device */
+  const float* Y;     /* N x T_L row-major one-hot, device */
+  int64_t N;          /* >= 1 */
+  float* opg;         /* P x P row-major device output, or NULL */
+  float* hessian;     /* P x P row-major device output, or NULL */
+} hess_batch_item;
+
+typedef struct {
+  int waves;          /* persistent tensor-core launches */
+  int items_chunked;  /* items run alone (larger than the workspace) */
+  int64_t tiles;      /* output tiles of the wave launches */
+  double flops;       /* tensor-core flops of the wave launches (3 products for BF16X3) */
+  double launch_ms;   /* summed device time of the wave launches (CUDA events) */
+} hess_batch_info;
+
+/* workspace_bytes: device memory the batch allocates now and reuses for every
+ * wave (at least 65 MiB; the wave size follows from it).  stream: cudaStream_t
+ * for all batch work.  The current device becomes the batch's.  Errors:
+ * INVALID_ARG, OOM, CUDA. */
+HESS_API hess_status hess_batch_create(int64_t workspace_bytes, void* stream, hess_batch** out);
+
+/* Computes every requested matrix of items[0..count).  All buffers must be
+ * device memory on the batch's device; at least one output per item.
+ * Precision BF16 or BF16X3 (INVALID_ARG otherwise).  Every item is checked
+ * before any work is queued.  Waits for its work before returning; info (may
+ * be NULL) receives the wave statistics.  Errors: INVALID_ARG, OOM, CUDA,
+ * TIMEOUT (a pipeline wait of the tensor-core kernel gave up). */
+HESS_API hess_status hess_batch_run(hess_batch* b, const hess_batch_item* items, int count,
+                                    hess_precision prec, hess_batch_info* info);
+
+/* Waits for the batch stream and releases the workspace.  NULL is ignored. */
+HESS_API hess_status hess_batch_destroy(hess_batch* b);
 
 /* ----------------------------------------------------------------------
  * Measurement hooks (no counterpart in the paper).  When timing is enabled

@@ -2,4 +2,4 @@
 dense MLPs with softmax cross-entropy, behind the C ABI in include/hessmlp.h."""
 
 from ._lib import EXPORTS, HessError, load, last_error  # noqa: F401
-from .api import HessMLP, HessServer, param_permutation  # noqa: F401
+from .api import HessBatch, HessMLP, HessServer, param_permutation  # noqa: F401

@@ -34,6 +34,7 @@ EXPORTS = (
     "hess_param_permutation", "hess_last_error", "hess_timing_enable", "hess_timing_read",
     "hess_launch_count", "per_example_grads_noalloc", "hess_server_create",
     "hess_server_add_network", "hess_server_submit", "hess_server_wait", "hess_server_destroy",
+    "hess_mlp_set_operand_limit", "hess_batch_create", "hess_batch_run", "hess_batch_destroy",
 )
 
 REQUEST_KIND = {"hessian": 0, "opg": 1, "eig": 2}
@@ -44,6 +45,17 @@ class HessRequest(ctypes.Structure):
                 ("Y", ctypes.c_void_p), ("N", ctypes.c_int64), ("prec", ctypes.c_int),
                 ("k", ctypes.c_int), ("out", ctypes.c_void_p),
                 ("evals", ctypes.POINTER(ctypes.c_double))]
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("net", ctypes.c_void_p), ("X", ctypes.c_void_p), ("Y", ctypes.c_void_p),
+                ("N", ctypes.c_int64), ("opg", ctypes.c_void_p), ("hessian", ctypes.c_void_p)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("waves", ctypes.c_int), ("items_chunked", ctypes.c_int),
+                ("tiles", ctypes.c_int64), ("flops", ctypes.c_double),
+                ("launch_ms", ctypes.c_double)]
+
 
 KERNEL_CLASS = {"syrk": 0, "hcontract": 1, "grads": 2, "rop": 3, "eig": 4, "hrest": 5}
 
@@ -113,6 +125,15 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.hess_server_wait.restype = st
     lib.hess_server_destroy.argtypes = [vp]
     lib.hess_server_destroy.restype = st
+    lib.hess_mlp_set_operand_limit.argtypes = [vp, i64]
+    lib.hess_mlp_set_operand_limit.restype = st
+    lib.hess_batch_create.argtypes = [i64, vp, ctypes.POINTER(vp)]
+    lib.hess_batch_create.restype = st
+    lib.hess_batch_run.argtypes = [vp, ctypes.POINTER(BatchItem), ctypes.c_int, ctypes.c_int,
+                                   ctypes.POINTER(BatchInfo)]
+    lib.hess_batch_run.restype = st
+    lib.hess_batch_destroy.argtypes = [vp]
+    lib.hess_batch_destroy.restype = st
     lib.hess_launch_count.argtypes = []
     lib.hess_launch_count.restype = ctypes.c_int64
     lib.hess_last_error.argtypes = []

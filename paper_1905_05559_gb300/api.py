@@ -92,6 +92,9 @@ class HessMLP:
     def set_stream(self, stream):
         _lib.check(self._lib.hess_mlp_set_stream(self.h, ctypes.c_void_p(stream or 0)))
 
+    def set_operand_limit(self, nbytes: int):
+        _lib.check(self._lib.hess_mlp_set_operand_limit(self.h, int(nbytes)))
+
     def timing(self, enable: bool):
         _lib.check(self._lib.hess_timing_enable(self.h, 1 if enable else 0))
 
@@ -146,6 +149,40 @@ class HessMLP:
         if torch is not None and isinstance(X, torch.Tensor):
             return torch.empty(shape, dtype=getattr(torch, dt), device=X.device)
         return np.empty(shape, dtype=dt)
+
+
+class HessBatch:
+    """Batched OPG / exact Hessian of many networks (hess_batch_*): marshalling only."""
+
+    def __init__(self, workspace_bytes=16 << 30, stream=None):
+        self._lib = _lib.load()
+        b = ctypes.c_void_p()
+        _lib.check(self._lib.hess_batch_create(int(workspace_bytes), ctypes.c_void_p(stream or 0),
+                                               ctypes.byref(b)))
+        self.b = b
+
+    def run(self, items, prec="bf16x3"):
+        """items: sequence of (HessMLP, X, Y, opg_out or None, hessian_out or None) with
+        device float32 tensors.  Returns the wave statistics as a dict."""
+        arr = (_lib.BatchItem * max(1, len(items)))()
+        for i, (net, X, Y, o, hs) in enumerate(items):
+            arr[i] = _lib.BatchItem(net.h, _ptr(X), _ptr(Y), int(X.shape[0]), _ptr(o), _ptr(hs))
+        info = _lib.BatchInfo()
+        _lib.check(self._lib.hess_batch_run(self.b, arr, len(items), _lib.PRECISION[prec],
+                                            ctypes.byref(info)))
+        return {"waves": info.waves, "items_chunked": info.items_chunked, "tiles": info.tiles,
+                "flops": info.flops, "launch_ms": info.launch_ms}
+
+    def close(self):
+        if getattr(self, "b", None):
+            self._lib.hess_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class HessServer:

@@ -26,7 +26,7 @@ static cudaEvent_t take_event(hess_mlp* h) {
 }
 
 Tick::Tick(hess_mlp* h, int cls, double flops, double bytes) : h_(h) {
-  if (!h->timing) return;
+  if (!h || !h->timing) return;
   rec_.a = take_event(h);
   rec_.b = take_event(h);
   if (!rec_.a || !rec_.b) return;
@@ -128,17 +128,6 @@ hess_status classify(const hess_mlp* h, const void* p, const char* name, int* on
   }
   return HESS_OK;
 }
-
-struct Guard {
-  int prev = -1;
-  explicit Guard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) cudaSetDevice(dev);
-  }
-  ~Guard() {
-    if (prev >= 0) cudaSetDevice(prev);
-  }
-};
 
 hess_status check_common(hess_mlp* h, const void* X, const void* Y, int64_t N, hess_precision prec,
                          const void* out) {
@@ -540,6 +529,14 @@ hess_status hess_mlp_set_stream(hess_mlp* h, void* stream) {
   clear_error();
   if (!h) return set_error(HESS_ERR_INVALID_ARG, "handle is NULL");
   h->stream = (cudaStream_t)stream;
+  return HESS_OK;
+}
+
+hess_status hess_mlp_set_operand_limit(hess_mlp* h, int64_t bytes) {
+  clear_error();
+  if (!h) return set_error(HESS_ERR_INVALID_ARG, "handle is NULL");
+  if (bytes < (1 << 20)) return set_error(HESS_ERR_INVALID_ARG, "operand limit must be at least 1 MiB");
+  h->op_limit = (size_t)bytes;
   return HESS_OK;
 }
 

@@ -1,0 +1,208 @@
+// Batched curvature matrices: the OPG and exact Hessian of many networks,
+// each with its own data, contracted in waves of one persistent tensor-core
+// launch each.
+//
+//   * the batch owns one device workspace, allocated at create time;
+//   * a wave takes items in order while their planned operands (the same
+//     layout the single-network call uses, found by a planning pass of
+//     tc_prep) fit the workspace; each item's forward/backward pass, operand
+//     builders and SIMT Hessian parts run on the batch stream, then one launch
+//     walks the tiles of every job of every item in the wave, longest first;
+//   * an item that does not fit the workspace even alone runs by itself
+//     through the single-network call (chunked when its operands exceed its
+//     handle's operand limit);
+//   * the per-tile arithmetic does not depend on the schedule, so every matrix
+//     is bit-identical to what the single-network call returns.
+#include "internal.h"
+
+struct hess_batch {
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t stream = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  double* host_pinned = nullptr;
+  std::vector<cudaEvent_t> events;  // pairs bracketing the wave launches
+};
+
+namespace hm {
+namespace {
+
+hess_status check_item(const hess_batch* b, const hess_batch_item& it, int idx) {
+  if (!it.net) return set_error(HESS_ERR_INVALID_ARG, "item %d: network handle is NULL", idx);
+  if (it.net->device != b->device)
+    return set_error(HESS_ERR_INVALID_ARG, "item %d: network on device %d, batch on device %d", idx,
+                     it.net->device, b->device);
+  if (it.N < 1) return set_error(HESS_ERR_INVALID_ARG, "item %d: N must be >= 1", idx);
+  if (!it.X || !it.Y) return set_error(HESS_ERR_INVALID_ARG, "item %d: X and Y must be non-NULL", idx);
+  if (!it.opg && !it.hessian) return set_error(HESS_ERR_INVALID_ARG, "item %d: no output requested", idx);
+  const void* ptrs[4] = {it.X, it.Y, it.opg, it.hessian};
+  for (int q = 0; q < 4; ++q) {
+    if (!ptrs[q]) continue;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptrs[q]) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(HESS_ERR_INVALID_ARG, "item %d: buffers must be device memory", idx);
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+      return set_error(HESS_ERR_INVALID_ARG, "item %d: buffers must be device memory", idx);
+    if (at.type == cudaMemoryTypeDevice && at.device != b->device)
+      return set_error(HESS_ERR_INVALID_ARG, "item %d: buffer on device %d, batch on device %d", idx,
+                       at.device, b->device);
+    if (reinterpret_cast<uintptr_t>(ptrs[q]) & 3)
+      return set_error(HESS_ERR_INVALID_ARG, "item %d: buffers must be 4-byte aligned", idx);
+  }
+  return HESS_OK;
+}
+
+// Workspace bytes of one item inside a wave (its arena share).
+size_t item_bytes(const hess_batch_item& it, TcPlan& plan) {
+  Arena ar;
+  TcItem ti{it.X, it.Y, it.N, it.opg, it.hessian};
+  tc_prep(it.net, ti, ar, false, plan, nullptr);
+  return align_up(ar.off, 256);
+}
+
+// Bytes of a wave's job and tile tables (the layout tc_launch_plan takes).
+size_t table_bytes(size_t njobs, size_t ntiles) {
+  Arena ar;
+  ar.take<tc::Job>(njobs ? njobs : 1);
+  ar.take<int4>(ntiles ? ntiles : 1);
+  return align_up(ar.off, 256);
+}
+
+// Runs one item alone through the single-network calls on the batch stream.
+hess_status run_alone(hess_batch* b, const hess_batch_item& it, hess_precision prec) {
+  hess_mlp* h = it.net;
+  cudaStream_t keep = h->stream;
+  h->stream = b->stream;
+  hess_status st = HESS_OK;
+  if (it.opg) st = opg(h, it.X, it.Y, it.N, prec, it.opg);
+  if (st == HESS_OK && it.hessian) st = exact_hessian(h, it.X, it.Y, it.N, prec, it.hessian);
+  h->stream = keep;
+  return st;
+}
+
+}  // namespace
+}  // namespace hm
+
+using namespace hm;
+
+extern "C" {
+
+hess_status hess_batch_create(int64_t workspace_bytes, void* stream, hess_batch** out) {
+  clear_error();
+  if (!out) return set_error(HESS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (workspace_bytes < ((int64_t)kSplitBytes + (1 << 20)))
+    return set_error(HESS_ERR_INVALID_ARG, "workspace must be at least %lld bytes",
+                     (long long)(kSplitBytes + (1 << 20)));
+  hess_batch* b = new hess_batch();
+  b->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&b->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return set_error(HESS_ERR_CUDA, "no CUDA device");
+  }
+  cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device);
+  if (cudaMalloc(&b->ws, (size_t)workspace_bytes) != cudaSuccess ||
+      cudaMallocHost(&b->host_pinned, 64) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(b->ws);
+    delete b;
+    return set_error(HESS_ERR_OOM, "cannot allocate a %lld-byte batch workspace", (long long)workspace_bytes);
+  }
+  b->ws_bytes = (size_t)workspace_bytes;
+  *out = b;
+  return HESS_OK;
+}
+
+hess_status hess_batch_run(hess_batch* b, const hess_batch_item* items, int count, hess_precision prec,
+                           hess_batch_info* info) {
+  clear_error();
+  if (!b) return set_error(HESS_ERR_INVALID_ARG, "batch is NULL");
+  if (count < 0 || (count > 0 && !items)) return set_error(HESS_ERR_INVALID_ARG, "bad item list");
+  if (prec != HESS_BF16 && prec != HESS_BF16X3)
+    return set_error(HESS_ERR_INVALID_ARG, "batches run on the tensor cores: precision BF16 or BF16X3");
+  for (int i = 0; i < count; ++i) HM_TRY(check_item(b, items[i], i));
+  Guard g(b->device);
+  hess_batch_info inf{};
+  if (count > 0) {
+    HM_TRY(tc_available(items[0].net));
+    const bool x3 = prec == HESS_BF16X3;
+    cudaStream_t s = b->stream;
+    // fixed head of the workspace: error flag and split-K scratch
+    Arena head{b->ws, 0};
+    int* err = head.take<int>(1);
+    char* split = head.take<char>(kSplitBytes);
+    const size_t base = align_up(head.off, 256);
+    HM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    SplitGuard sg(split, kSplitBytes, b->sm_count);
+    int i = 0;
+    while (i < count) {
+      // gather the wave
+      size_t used = base, njobs = 0, ntiles = 0;
+      int j = i;
+      while (j < count) {
+        TcPlan one;
+        const size_t need = item_bytes(items[j], one);
+        const size_t nj = njobs + one.jobs.size(), nt = ntiles + one.tiles.size();
+        if (used + need + table_bytes(nj, nt) > b->ws_bytes) break;
+        used += need;
+        njobs = nj;
+        ntiles = nt;
+        ++j;
+      }
+      if (j == i) {
+        // too large for the workspace: alone, through the single-network calls
+        HM_TRY(run_alone(b, items[i], prec));
+        ++inf.items_chunked;
+        ++i;
+        continue;
+      }
+      TcPlan plan;
+      Arena ar{b->ws, base};
+      for (int q = i; q < j; ++q) {
+        const hess_batch_item& it = items[q];
+        TcItem ti{it.X, it.Y, it.N, it.opg, it.hessian};
+        const size_t at = ar.off;
+        HM_TRY(tc_prep(it.net, ti, ar, true, plan, s));
+        ar.off = at + align_up(ar.off - at, 256);
+      }
+      const size_t e0 = 2 * (size_t)inf.waves;
+      while (b->events.size() < e0 + 2) {
+        cudaEvent_t e;
+        HM_CUDA(cudaEventCreate(&e));
+        b->events.push_back(e);
+      }
+      HM_CUDA(cudaEventRecord(b->events[e0], s));
+      HM_TRY(tc_launch_plan(b->sm_count, plan, ar, true, x3, err, s));
+      HM_CUDA(cudaEventRecord(b->events[e0 + 1], s));
+      inf.tiles += (int64_t)plan.tiles.size();
+      inf.flops += (plan.syrk_flops + plan.hess_flops) * (x3 ? 3.0 : 1.0);
+      ++inf.waves;
+      i = j;
+    }
+    HM_TRY(tc_check_err(s, b->host_pinned, err));
+    for (int w = 0; w < inf.waves; ++w) {
+      float ms = 0.f;
+      HM_CUDA(cudaEventElapsedTime(&ms, b->events[2 * w], b->events[2 * w + 1]));
+      inf.launch_ms += ms;
+    }
+  }
+  if (info) *info = inf;
+  return HESS_OK;
+}
+
+hess_status hess_batch_destroy(hess_batch* b) {
+  if (!b) return HESS_OK;
+  Guard g(b->device);
+  cudaStreamSynchronize(b->stream);
+  for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+  cudaFree(b->ws);
+  cudaFreeHost(b->host_pinned);
+  delete b;
+  return HESS_OK;
+}
+
+}  // extern "C"

@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libhessmlp.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -38,6 +39,18 @@ extern std::atomic<int64_t> g_launches;
     ::hm::g_launches.fetch_add(1, std::memory_order_relaxed); \
     HM_CUDA(cudaGetLastError());                              \
   } while (0)
+
+// Makes a device current for a scope.
+struct Guard {
+  int prev = -1;
+  explicit Guard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~Guard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
 
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -99,6 +112,9 @@ struct hess_mlp {
   size_t ws_bytes = 0;
   double* host_pinned = nullptr;  // small pinned scratch for scalars
   int sm_count = 0;
+  // operand bytes above which the tensor-core Hessian is built and contracted
+  // in chunks (one launch per chunk) instead of in one launch
+  size_t op_limit = (size_t)4 << 30;
 };
 
 namespace hm {
@@ -111,7 +127,8 @@ hess_status ensure_ws(hess_mlp* h, size_t bytes);
 constexpr hess_status kDryRun = static_cast<hess_status>(100);
 extern thread_local size_t* g_dry_bytes;
 
-// Brackets launches with CUDA events when the handle's timing is enabled.
+// Brackets launches with CUDA events when the handle's timing is enabled (a
+// null handle times nothing).
 class Tick {
  public:
   Tick(hess_mlp* h, int cls, double flops, double bytes);
@@ -150,7 +167,8 @@ template <typename T>
 hess_status gemm(const Gemm<T>& g, cudaStream_t s);
 
 // Scratch for split-K partial tiles of the SIMT GEMM, set by each entry point
-// from its workspace for the duration of the call (none: no split).
+// from its workspace for the duration of the call (none: no split).  Guards
+// nest: a call made inside another's scope restores the outer scratch.
 struct SplitScratch {
   void* p = nullptr;
   size_t bytes = 0;
@@ -158,8 +176,11 @@ struct SplitScratch {
 };
 extern thread_local SplitScratch g_split;
 struct SplitGuard {
-  explicit SplitGuard(void* p, size_t bytes, int sms) { g_split = SplitScratch{p, bytes, sms}; }
-  ~SplitGuard() { g_split = SplitScratch{}; }
+  explicit SplitGuard(void* p, size_t bytes, int sms) : prev_(g_split) { g_split = SplitScratch{p, bytes, sms}; }
+  ~SplitGuard() { g_split = prev_; }
+
+ private:
+  SplitScratch prev_;
 };
 constexpr size_t kSplitBytes = (size_t)64 << 20;
 
@@ -211,7 +232,7 @@ template <typename T>
 hess_status rop_block(const Net& net, const T* omega, const Caches<T>& c, int jm, int64_t d0, int B,
                       RopBufs<T>& r, cudaStream_t s);
 // H[d][c] for the block's rows and the columns of weight layer jl (>= jm),
-// masked to c >= d0 and mirrored to H[c][d] for c >= d0 + B.  tmp: B x P_l.
+// kept where c >= d and mirrored to H[c][d] where c > d.  tmp: B x P_l.
 template <typename T>
 hess_status contract_layer(const Net& net, const Caches<T>& c, const RopBufs<T>& r, int jm, int jl,
                            int64_t d0, T* tmp, T* H, cudaStream_t s);
@@ -230,29 +251,62 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
                           double* evals_d, double* evecs_d, Arena& ar, bool dry, EigResult* res);
 
 // ------------------------------------------------------ tensor cores ----
-// bf16 operands: Ahi/Alo: M x K, Bhi/Blo: Nn x K, both K-major with leading
-// dimension ld (elements, multiple of 64).  D(m, n) = scale * sum_k A(m,k) B(n,k)
-// with terms hi*hi (+ hi*lo + lo*hi when x3).  Output mapping, per tile row m:
-//   out_row = rbase + (m % rgroup), out_col = cbase + (m / rgroup) * cgstride + n
-//   direct write  out[out_row * ldo + out_col]  if out_col >= dmin
-//   mirror write  out[out_col * ldo + out_row]  if out_col >= mmin
-struct TcGemm {
-  int M = 0, Nn = 0, K = 0, ld = 0;
-  const void* Ahi = nullptr;
-  const void* Alo = nullptr;
-  const void* Bhi = nullptr;
-  const void* Blo = nullptr;
-  int x3 = 0;
-  float scale = 1.f;
-  float* out = nullptr;
-  int64_t ldo = 0;
-  int64_t rbase = 0, rgroup = 1 << 30, cbase = 0, cgstride = 0;
-  int64_t dmin = 0, mmin = 0;
-  int syrk = 0;  // A == B: only tiles whose column range reaches the diagonal
+namespace tc {
+// One contraction of the persistent tcgen05 kernel: its four operand tensor
+// maps (bf16 hi/lo planes of A: M x K and B: Nn x K, K-major), K, and where its
+// tiles land in a symmetric output.  A launch walks a list of tiles (job, row
+// tile, column tile), so one launch serves many contractions of different
+// shapes and networks.
+struct Job {
+  CUtensorMap a_hi, a_lo, b_hi, b_lo;
+  int64_t M;      // valid rows of A
+  int64_t Nn;     // valid rows of B (= columns of the product)
+  int BN;         // tile columns (multiple of 16, <= 256)
+  int nkb;        // k-blocks of 64
+  uint32_t idesc; // instruction descriptor (N = BN)
+  int mode;       // 0: symmetric rank-K update (orow = m, ocol = n)
+                  // 1: Hessian rows of one weight layer, W columns
+                  // 2: Hessian rows of one weight layer, columns after W
+  float scale;
+  float* out;
+  int64_t ldo;
+  int64_t woff;   // modes 1, 2: offset of W in omega
+  int64_t boff;   // mode 2: first column (the layer's bias)
+  int Tin, Tout, p0;
+  int64_t R0;     // mode 1: first concatenated row of unit p0
+  int ntn;        // mode 2: column tiles per unit
+  int64_t brow;   // mode 2: B rows per unit
 };
+}  // namespace tc
+
+// Jobs and tiles gathered for one persistent launch.
+struct TcPlan {
+  std::vector<tc::Job> jobs;
+  std::vector<int4> tiles;  // (job, row tile, column tile, 0)
+  double syrk_flops = 0.0, hess_flops = 0.0;
+};
+
+// One network's request: device X (N x T_1), Y (N x T_L) and P x P device
+// outputs (either may be null).
+struct TcItem {
+  const float* X = nullptr;
+  const float* Y = nullptr;
+  int64_t N = 0;
+  float* opg = nullptr;
+  float* hess = nullptr;
+};
+
 hess_status tc_available(hess_mlp* h);
-hess_status tc_gemm(hess_mlp* h, const TcGemm& g, cudaStream_t s);
-hess_status split_bf16(const float* in, int64_t rows, int64_t cols, int64_t ldin, int transpose,
-                       void* hi, void* lo, int64_t ld, cudaStream_t s);
+// Lays out (live = false) or builds (live = true, on stream s) everything the
+// item's contractions read: forward/backward caches, split-BF16 operands, and
+// the Hessian entries outside the tensor-core blocks; appends the item's
+// jobs to the plan.  The caller provides the split-K scratch (SplitGuard).
+hess_status tc_prep(hess_mlp* h, const TcItem& it, Arena& ar, bool live, TcPlan& plan, cudaStream_t s);
+// Takes arena memory for the plan's job and tile tables; when live, copies
+// them there and starts one persistent launch over all tiles (longest first).
+hess_status tc_launch_plan(int sm_count, const TcPlan& plan, Arena& ar, bool live, bool x3, int* err,
+                           cudaStream_t s);
+// Reads the kernels' error flag (synchronises the stream).
+hess_status tc_check_err(cudaStream_t s, double* host_scratch, int* err_d);
 
 }  // namespace hm

@@ -544,9 +544,11 @@ hess_status mirror_upper(T* C, int64_t n, int64_t ldc, cudaStream_t s) {
 template hess_status mirror_upper<double>(double*, int64_t, int64_t, cudaStream_t);
 template hess_status mirror_upper<float>(float*, int64_t, int64_t, cudaStream_t);
 
-// tmp is B x cols (row d holds H[d0 + d, c0 .. c0 + cols)).  Direct entries
-// with column >= d0 go to row d0 + d; entries with column >= d0 + B are also
-// written to row c (the mirror image), coalesced through a shared tile.
+// tmp is B x cols (row d holds H[d0 + d, c0 .. c0 + cols)).  Entries on or
+// above the diagonal (column >= d0 + d) go to row d0 + d; those strictly
+// above it are also written to row c (the mirror image), coalesced through a
+// shared tile.  Every entry of H is thus written once from one computation
+// and once as its mirror, so H is exactly symmetric.
 template <typename T>
 __global__ void scatter_sym_kernel(const T* tmp, int B, int64_t cols, int64_t c0, int64_t d0, T* H,
                                    int64_t P) {
@@ -558,7 +560,7 @@ __global__ void scatter_sym_kernel(const T* tmp, int B, int64_t cols, int64_t c0
     if (d < B && cl < cols) {
       v = tmp[d * cols + cl];
       int64_t c = c0 + cl;
-      if (c >= d0) H[(d0 + d) * P + c] = v;
+      if (c >= d0 + d) H[(d0 + d) * P + c] = v;
     }
     tile[y][threadIdx.x] = v;
   }
@@ -567,7 +569,7 @@ __global__ void scatter_sym_kernel(const T* tmp, int B, int64_t cols, int64_t c0
     int64_t cl = ct + y, d = dt + threadIdx.x;
     if (d < B && cl < cols) {
       int64_t c = c0 + cl;
-      if (c >= d0 + B) H[c * P + d0 + d] = tile[threadIdx.x][y];
+      if (c > d0 + d) H[c * P + d0 + d] = tile[threadIdx.x][y];
     }
   }
 }

@@ -18,6 +18,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "internal.h"
@@ -47,30 +48,6 @@ constexpr long long TIMEOUT_CYCLES = 4000000000ll;  // ~2 s at 2 GHz
 // tile's main accumulator with round-to-nearest FP32 adds, so the error of the
 // tensor cores' own accumulation does not grow with N.
 constexpr int CHUNK_KB = 16;
-
-// One contraction: its four operand tensor maps, shape, K and output mapping.
-// A persistent launch walks a list of tiles (job, row tile, column tile), so
-// one launch can serve many contractions of different shapes.
-struct alignas(64) Job {
-  CUtensorMap a_hi, a_lo, b_hi, b_lo;
-  int64_t M;      // valid rows of A
-  int64_t Nn;     // valid rows of B (= columns of the product)
-  int BN;         // tile columns (multiple of 16, <= 256)
-  int nkb;        // k-blocks of 64
-  uint32_t idesc; // instruction descriptor (N = BN)
-  int mode;       // 0: symmetric rank-K update (orow = m, ocol = n)
-                  // 1: Hessian rows of one weight layer, W columns (see row_map)
-                  // 2: Hessian rows of one weight layer, columns after W (see row_map)
-  float scale;
-  float* out;
-  int64_t ldo;
-  int64_t woff;   // modes 1, 2: offset of W in omega
-  int64_t boff;   // mode 2: first column (the layer's bias)
-  int Tin, Tout, p0;
-  int64_t R0;     // mode 1: first concatenated row of unit p0
-  int ntn;        // mode 2: column tiles per unit
-  int64_t brow;   // mode 2: B rows per unit
-};
 
 struct Launch {
   const Job* jobs;
@@ -695,7 +672,7 @@ hess_status make_job(const TcOperands& op, int BN, tc::Job* j) {
 
 // Copy jobs and tiles to the device regions given and launch the
 // persistent kernel over them.
-hess_status launch_jobs(hess_mlp* h, const tc::Job* jobs, int njobs, const int4* tiles, int ntiles,
+hess_status launch_jobs(int sm_count, const tc::Job* jobs, int njobs, const int4* tiles, int ntiles,
                         tc::Job* jobs_d, int4* tiles_d, bool x3, int* err, cudaStream_t s) {
   using namespace tc;
   if (ntiles < 1) return HESS_OK;
@@ -706,17 +683,9 @@ hess_status launch_jobs(hess_mlp* h, const tc::Job* jobs, int njobs, const int4*
   HM_CUDA(cudaMemcpyAsync(jobs_d, jobs, njobs * sizeof(Job), cudaMemcpyHostToDevice, s));
   HM_CUDA(cudaMemcpyAsync(tiles_d, tiles, ntiles * sizeof(int4), cudaMemcpyHostToDevice, s));
   Launch L{jobs_d, tiles_d, ntiles, x3 ? 3 : 1, err};
-  const int grid = ntiles < h->sm_count ? ntiles : h->sm_count;
+  const int grid = ntiles < sm_count ? ntiles : sm_count;
   umma_gemm_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(L);
   HM_LAUNCHED();
-  return HESS_OK;
-}
-
-hess_status check_err_flag(hess_mlp* h, int* err_d) {
-  HM_CUDA(cudaMemcpyAsync(h->host_pinned, err_d, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-  HM_CUDA(cudaStreamSynchronize(h->stream));
-  if (*reinterpret_cast<int*>(h->host_pinned))
-    return set_error(HESS_ERR_TIMEOUT, "a tensor-core pipeline wait gave up");
   return HESS_OK;
 }
 
@@ -752,7 +721,7 @@ double hcontract_flops(const Net& net, int64_t N, int jm, int jl, int64_t d0, in
 // Upper tiles of a P x P symmetric update with BM x BN tiles (the column
 // range reaches the diagonal), grouped by 8 tile rows so that concurrent tiles
 // share operand panels in L2.
-void syrk_tiles(int64_t P, int BN, int job, std::vector<int4>& tiles) {
+static void syrk_tiles(int64_t P, int BN, int job, std::vector<int4>& tiles) {
   using namespace tc;
   const int64_t mt = cdiv(P, BM), nt = cdiv(P, BN);
   for (int64_t g0 = 0; g0 < mt; g0 += 8)
@@ -761,93 +730,295 @@ void syrk_tiles(int64_t P, int BN, int job, std::vector<int4>& tiles) {
         if (tn * BN + BN - 1 >= tm * BM) tiles.push_back(make_int4(job, (int)tm, (int)tn, 0));
 }
 
-// OPG = G^T G / N with split-BF16 (or BF16) operands on the tensor cores.
-hess_status run_opg_tc(hess_mlp* h, const void* X, const void* Y, int64_t N, bool x3, void* Oout) {
-  using namespace tc;
-  HM_TRY(tc_available(h));
-  const Net& net = h->net;
-  const int64_t P = net.P, T1 = net.T[0], TL = net.T[net.L - 1];
-  int x_dev, y_dev, o_dev;
-  HM_TRY(classify_ptr(h, X, &x_dev));
-  HM_TRY(classify_ptr(h, Y, &y_dev));
-  HM_TRY(classify_ptr(h, Oout, &o_dev));
-  const int64_t ld = align_up((size_t)N, BK);
-  const int BN = 256;
-  std::vector<int4> tiles;
-  syrk_tiles(P, BN, 0, tiles);
-  char* split = nullptr;
-  auto plan = [&](Arena& ar, float*& xs, float*& ys, Caches<float>& c, float*& G, __nv_bfloat16*& hi,
-                  __nv_bfloat16*& lo, float*& O, int4*& tl, Job*& jd, int*& err) {
-    xs = x_dev ? nullptr : ar.take<float>(N * T1);
-    ys = y_dev ? nullptr : ar.take<float>(N * TL);
-    plan_caches(ar, net, N, c);
-    G = ar.take<float>(N * P);
-    hi = ar.take<__nv_bfloat16>(P * ld);
-    lo = ar.take<__nv_bfloat16>(P * ld);
-    O = o_dev ? (float*)Oout : ar.take<float>(P * P);
-    tl = ar.take<int4>(tiles.size());
-    jd = ar.take<Job>(1);
-    err = ar.take<int>(1);
-    split = ar.take<char>(kSplitBytes);
-  };
-  Arena ar;
-  float *xs, *ys, *G, *O;
-  __nv_bfloat16 *hi, *lo;
-  int4* tl;
-  Job* jd;
-  int* err;
-  Caches<float> c;
-  plan(ar, xs, ys, c, G, hi, lo, O, tl, jd, err);
-  HM_TRY(ensure_ws(h, ar.off));
-  ar = Arena{h->ws, 0};
-  plan(ar, xs, ys, c, G, hi, lo, O, tl, jd, err);
-  SplitGuard sg(split, kSplitBytes, h->sm_count);
-  cudaStream_t s = h->stream;
-  const float* xd = (const float*)X;
-  const float* yd = (const float*)Y;
-  if (!x_dev) {
-    HM_CUDA(cudaMemcpyAsync(xs, X, N * T1 * 4, cudaMemcpyHostToDevice, s));
-    xd = xs;
-  }
-  if (!y_dev) {
-    HM_CUDA(cudaMemcpyAsync(ys, Y, N * TL * 4, cudaMemcpyHostToDevice, s));
-    yd = ys;
-  }
-  HM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-  HM_TRY(forward_backward(net, (const float*)h->omega32, xd, yd, c, s));
-  {
-    Tick t(h, HESS_K_GRADS, 0.0, (double)N * P * 4.0);
-    HM_TRY(write_grads(net, c, G, P, s));
-  }
-  transpose_split_kernel<<<dim3((unsigned)cdiv(ld, 32), (unsigned)cdiv(P, 32)), dim3(32, 8), 0, s>>>(
-      G, N, P, P, hi, lo, ld);
-  HM_LAUNCHED();
-  Job job{};
-  TcOperands op{hi, lo, P, hi, lo, P, ld};
-  HM_TRY(make_job(op, BN, &job));
-  job.M = P;
-  job.Nn = P;
-  job.scale = 1.0f / (float)N;
-  job.out = O;
-  job.ldo = P;
-  job.mode = 0;
-  {
-    Tick t(h, HESS_K_SYRK, (double)N * P * (P + 1), 0.0);
-    HM_TRY(launch_jobs(h, &job, 1, tiles.data(), (int)tiles.size(), jd, tl, x3, err, s));
-  }
-  if (!o_dev) HM_CUDA(cudaMemcpyAsync(Oout, O, P * P * 4, cudaMemcpyDeviceToHost, s));
-  return check_err_flag(h, err);
+hess_status tc_check_err(cudaStream_t s, double* host_scratch, int* err_d) {
+  int* hv = reinterpret_cast<int*>(host_scratch);
+  HM_CUDA(cudaMemcpyAsync(hv, err_d, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HM_CUDA(cudaStreamSynchronize(s));
+  if (*hv) return set_error(HESS_ERR_TIMEOUT, "a tensor-core pipeline wait gave up");
+  return HESS_OK;
 }
 
-// Exact Hessian with the tensor-core contraction for each weight layer's own
-// W x W block and FP32 SIMT for the remaining columns.  For weight layer jm
-// (W: T_out x T_in, bias b) the R-operator runs once, for the T_out bias
-// directions b_p; the weight direction W_(p,q) only moves z_p, by a[n,q], so
-// all its R-quantities are a[n,q] times those of b_p:
-//   H[W_pq, W_ik] = (1/N) sum_n R{delta}[n,b_p,i] a[n,q] a[n,k]   (tcgen05)
-//   H[W_pq, c]    = (1/N) sum_n a[n,q] F[n,p,c]  for c >= b        (SIMT)
-//   H[b_p, c]     = contraction of the bias directions themselves  (SIMT)
-hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N, bool x3, void* Hout) {
+
+// Upper-triangle entries of the W x W block of a weight layer (rows (u, i, q)
+// with i >= u, columns from the row's own entry on): 2N flops each.
+static double wblock_entries(int64_t Tin, int64_t Tout, int64_t p0, int64_t p1) {
+  double ent = 0.0;
+  for (int64_t u = p0; u < p1; ++u)
+    ent += (double)(Tout - u) * Tin * Tin - (double)Tin * (Tin - 1) / 2.0;
+  return ent;
+}
+
+// F segments of weight layer jm: the bias b^(jm+1) and every later layer.
+static hess_status f_args(const Net& net, const Caches<float>& c, const RopBufs<float>& rb, int jm,
+                          tc::FArgs& fa) {
+  using namespace tc;
+  const int L = net.L;
+  const int64_t boff = net.boff[jm - 1];
+  fa = FArgs{};
+  fa.cols = net.P - boff;
+  fa.B = net.T[jm];
+  FSeg g{};
+  g.Tin = net.T[jm - 1];
+  g.Tout = net.T[jm];
+  g.rd = rb.rd[jm];
+  fa.seg[fa.nseg++] = g;
+  for (int jl = jm + 1; jl < L; ++jl) {
+    if (fa.nseg >= MAXSEG) return set_error(HESS_ERR_UNSUPPORTED, "too many layers for the tensor-core Hessian");
+    FSeg q{};
+    q.c0 = net.woff[jl - 1] - boff;
+    q.nW = (int64_t)net.T[jl - 1] * net.T[jl];
+    q.Tin = net.T[jl - 1];
+    q.Tout = net.T[jl];
+    q.rd = rb.rd[jl];
+    q.a = c.a[jl - 1];
+    q.dlt = c.d[jl];
+    q.ra = rb.ra[jl - 1];
+    fa.seg[fa.nseg++] = q;
+  }
+  return HESS_OK;
+}
+
+hess_status tc_prep(hess_mlp* h, const TcItem& it, Arena& ar, bool live, TcPlan& plan, cudaStream_t s) {
+  using namespace tc;
+  using bf = __nv_bfloat16;
+  const Net& net = h->net;
+  const int L = net.L;
+  const int64_t P = net.P, N = it.N;
+  const int64_t ld = align_up((size_t)N, BK);
+  const float* omega = h->omega32;
+  hess_mlp* th = s == h->stream ? h : nullptr;  // per-class timing on the handle's own stream
+  Caches<float> c;
+  plan_caches(ar, net, N, c);
+  if (live) HM_TRY(forward_backward(net, omega, it.X, it.Y, c, s));
+  if (it.opg) {
+    // OPG = G^T G / N (Sec. 3, the outer-product approximation): G is written
+    // once in FP32, then split into K-major bf16 planes
+    float* G = ar.take<float>(N * P);
+    bf* hi = ar.take<bf>(P * ld);
+    bf* lo = ar.take<bf>(P * ld);
+    const double fl = (double)N * P * (P + 1);
+    plan.syrk_flops += fl;
+    if (live) {
+      {
+        Tick t(th, HESS_K_GRADS, 0.0, (double)N * P * 4.0);
+        HM_TRY(write_grads(net, c, G, P, s));
+      }
+      transpose_split_kernel<<<dim3((unsigned)cdiv(ld, 32), (unsigned)cdiv(P, 32)), dim3(32, 8), 0, s>>>(
+          G, N, P, P, hi, lo, ld);
+      HM_LAUNCHED();
+    }
+    Job job{};
+    if (live) HM_TRY(make_job(TcOperands{hi, lo, P, hi, lo, P, ld}, 256, &job));
+    job.BN = 256;
+    job.M = P;
+    job.Nn = P;
+    job.scale = 1.0f / (float)N;
+    job.out = it.opg;
+    job.ldo = P;
+    job.mode = 0;
+    syrk_tiles(P, 256, (int)plan.jobs.size(), plan.tiles);
+    plan.jobs.push_back(job);
+  }
+  if (it.hess) {
+    // exact Hessian (Sec. 3, Eq. for H_ij): R-operator over the bias
+    // directions of each weight layer, the W x W block and the columns after
+    // W on the tensor cores, the remaining entries by SIMT contractions
+    int Tmax = 0;
+    int64_t maxPl = 0;
+    for (int jm = 1; jm < L; ++jm) {
+      Tmax = net.T[jm] > Tmax ? net.T[jm] : Tmax;
+      const int64_t pl = (int64_t)net.T[jm - 1] * net.T[jm] + net.T[jm];
+      maxPl = pl > maxPl ? pl : maxPl;
+    }
+    RopBufs<float> r;
+    plan_rop(ar, net, N, 1, Tmax, r);
+    float* tmp = ar.take<float>((int64_t)Tmax * maxPl);
+    for (int jm = 1; jm < L; ++jm) {
+      const int Tin = net.T[jm - 1], Tout = net.T[jm];
+      const int64_t woff = net.woff[jm - 1], boff = net.boff[jm - 1];
+      const int64_t rows = rows_before(Tout, Tin, Tout);
+      const int64_t rest = P - boff;
+      bf* bhi = ar.take<bf>((int64_t)Tin * ld);
+      bf* blo = ar.take<bf>((int64_t)Tin * ld);
+      bf* ahi = ar.take<bf>(rows * ld);
+      bf* alo = ar.take<bf>(rows * ld);
+      bf* fhi = ar.take<bf>((int64_t)Tout * rest * ld);
+      bf* flo = ar.take<bf>((int64_t)Tout * rest * ld);
+      const double fw = 2.0 * N * wblock_entries(Tin, Tout, 0, Tout);
+      const double ff = 2.0 * N * (double)Tout * Tin * rest;
+      plan.hess_flops += fw + ff;
+      RopBufs<float> rb = r;
+      rb.B = Tout;
+      FArgs fa;
+      HM_TRY(f_args(net, c, rb, jm, fa));
+      if (live) {
+        {
+          Tick t(th, HESS_K_ROP, 0.0, 0.0);
+          HM_TRY(rop_block(net, omega, c, jm, boff, Tout, rb, s));
+        }
+        {
+          Tick t(th, HESS_K_HREST, 0.0, 0.0);
+          for (int jl = jm; jl < L; ++jl) HM_TRY(contract_layer(net, c, rb, jm, jl, boff, tmp, it.hess, s));
+        }
+        transpose_split_kernel<<<dim3((unsigned)cdiv(ld, 32), (unsigned)cdiv(Tin, 32)), dim3(32, 8), 0, s>>>(
+            c.a[jm - 1], N, Tin, Tin, bhi, blo, ld);
+        HM_LAUNCHED();
+        build_wrows_kernel<<<dim3((unsigned)cdiv(ld, 32), (unsigned)cdiv(Tin, 32), (unsigned)Tout),
+                             dim3(32, 8), 0, s>>>(rb.rd[jm], c.a[jm - 1], N, Tin, Tout, 0, 0, ahi, alo, ld);
+        HM_LAUNCHED();
+        const int64_t total = (int64_t)Tout * rest * ld;
+        build_f_bf16_kernel<<<(unsigned)(cdiv(total, 256) < 1048576 ? cdiv(total, 256) : 1048576), 256, 0,
+                              s>>>(fa, N, 0, Tout, fhi, flo, ld);
+        HM_LAUNCHED();
+      }
+      // W x W block: rows (u, i, q), columns q' of W_(i, q')
+      {
+        const int BN = pick_bn(Tin);
+        Job job{};
+        if (live) HM_TRY(make_job(TcOperands{ahi, alo, rows, bhi, blo, Tin, ld}, BN, &job));
+        job.BN = BN;
+        job.M = rows;
+        job.Nn = Tin;
+        job.scale = 1.0f / (float)N;
+        job.out = it.hess;
+        job.ldo = P;
+        job.mode = 1;
+        job.woff = woff;
+        job.Tin = Tin;
+        job.Tout = Tout;
+        const int jid = (int)plan.jobs.size();
+        for (int64_t tm = 0; tm < cdiv(rows, BM); ++tm)
+          for (int64_t tn = 0; tn < cdiv(Tin, BN); ++tn) plan.tiles.push_back(make_int4(jid, (int)tm, (int)tn, 0));
+        plan.jobs.push_back(job);
+      }
+      // columns after W: rows q of unit u against F[., u, c]
+      {
+        const int BN2 = pick_bn(rest);
+        const int ntn = (int)cdiv(rest, BN2);
+        Job job{};
+        if (live) HM_TRY(make_job(TcOperands{bhi, blo, Tin, fhi, flo, (int64_t)Tout * rest, ld}, BN2, &job));
+        job.BN = BN2;
+        job.M = Tin;
+        job.Nn = rest;
+        job.scale = 1.0f / (float)N;
+        job.out = it.hess;
+        job.ldo = P;
+        job.mode = 2;
+        job.woff = woff;
+        job.boff = boff;
+        job.Tin = Tin;
+        job.Tout = Tout;
+        job.p0 = 0;
+        job.ntn = ntn;
+        job.brow = rest;
+        const int jid = (int)plan.jobs.size();
+        for (int64_t tm = 0; tm < cdiv(Tin, BM); ++tm)
+          for (int u = 0; u < Tout; ++u)
+            for (int tn = 0; tn < ntn; ++tn) plan.tiles.push_back(make_int4(jid, (int)tm, u * ntn + tn, 0));
+        plan.jobs.push_back(job);
+      }
+    }
+  }
+  return HESS_OK;
+}
+
+hess_status tc_launch_plan(int sm_count, const TcPlan& plan, Arena& ar, bool live, bool x3, int* err,
+                           cudaStream_t s) {
+  using namespace tc;
+  tc::Job* jd = ar.take<tc::Job>(plan.jobs.size() ? plan.jobs.size() : 1);
+  int4* td = ar.take<int4>(plan.tiles.size() ? plan.tiles.size() : 1);
+  if (!live || plan.tiles.empty()) return HESS_OK;
+  // longest tiles first (K and tile width), so that a static round-robin over
+  // the CTAs ends with short tiles; the stable order keeps each job's L2
+  // grouping
+  std::vector<int4> order(plan.tiles);
+  std::stable_sort(order.begin(), order.end(), [&](const int4& a, const int4& b) {
+    const Job& ja = plan.jobs[a.x];
+    const Job& jb = plan.jobs[b.x];
+    return (int64_t)ja.nkb * ja.BN > (int64_t)jb.nkb * jb.BN;
+  });
+  return launch_jobs(sm_count, plan.jobs.data(), (int)plan.jobs.size(), order.data(), (int)order.size(), jd,
+                     td, x3, err, s);
+}
+
+// Stages host inputs and outputs for the single-network calls.
+struct Staged {
+  const float* X;
+  const float* Y;
+  float* out;
+  int x_dev, y_dev, o_dev;
+};
+
+static hess_status stage(hess_mlp* h, Arena& ar, bool live, const void* X, const void* Y, void* out, int64_t N,
+                         const Staged& st, Staged& d) {
+  const Net& net = h->net;
+  const int64_t P = net.P, T1 = net.T[0], TL = net.T[net.L - 1];
+  d = st;
+  float* xs = st.x_dev ? nullptr : ar.take<float>(N * T1);
+  float* ys = st.y_dev ? nullptr : ar.take<float>(N * TL);
+  float* os = st.o_dev ? nullptr : ar.take<float>(P * P);
+  if (!st.x_dev) d.X = xs;
+  if (!st.y_dev) d.Y = ys;
+  if (!st.o_dev) d.out = os;
+  if (live && !st.x_dev) HM_CUDA(cudaMemcpyAsync(xs, X, N * T1 * 4, cudaMemcpyHostToDevice, h->stream));
+  if (live && !st.y_dev) HM_CUDA(cudaMemcpyAsync(ys, Y, N * TL * 4, cudaMemcpyHostToDevice, h->stream));
+  return HESS_OK;
+}
+
+// One network through tc_prep + one persistent launch (kind 0: OPG, 1: H).
+static hess_status run_single(hess_mlp* h, const void* X, const void* Y, int64_t N, bool x3, void* out,
+                              int kind) {
+  Staged st{(const float*)X, (const float*)Y, (float*)out, 0, 0, 0};
+  HM_TRY(classify_ptr(h, X, &st.x_dev));
+  HM_TRY(classify_ptr(h, Y, &st.y_dev));
+  HM_TRY(classify_ptr(h, out, &st.o_dev));
+  cudaStream_t s = h->stream;
+  int* err = nullptr;
+  char* split = nullptr;
+  TcPlan plan;
+  auto build = [&](Arena& ar, bool live) -> hess_status {
+    Staged d;
+    HM_TRY(stage(h, ar, live, X, Y, out, N, st, d));
+    err = ar.take<int>(1);
+    split = ar.take<char>(kSplitBytes);
+    TcItem it{d.X, d.Y, N, kind == 0 ? d.out : nullptr, kind == 1 ? d.out : nullptr};
+    if (live) HM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    SplitGuard sg(split, kSplitBytes, h->sm_count);
+    HM_TRY(tc_prep(h, it, ar, live, plan, s));
+    Tick t(live ? h : nullptr, kind == 0 ? HESS_K_SYRK : HESS_K_HCONTRACT,
+           kind == 0 ? plan.syrk_flops : plan.hess_flops, 0.0);
+    return tc_launch_plan(h->sm_count, plan, ar, live, x3, err, s);
+  };
+  Arena ar;
+  HM_TRY(build(ar, false));
+  HM_TRY(ensure_ws(h, ar.off));
+  plan = TcPlan{};
+  ar = Arena{h->ws, 0};
+  HM_TRY(build(ar, true));
+  if (!st.o_dev) {
+    const int64_t P = h->net.P;
+    Staged d;
+    Arena a2{h->ws, 0};
+    HM_TRY(stage(h, a2, false, X, Y, out, N, st, d));
+    HM_CUDA(cudaMemcpyAsync(out, d.out, P * P * 4, cudaMemcpyDeviceToHost, s));
+  }
+  return tc_check_err(s, h->host_pinned, err);
+}
+
+// Bytes of the whole-operand Hessian plan (caches, R-op buffers, operands).
+static size_t hessian_plan_bytes(hess_mlp* h, int64_t N) {
+  TcPlan plan;
+  Arena ar;
+  TcItem it{nullptr, nullptr, N, nullptr, reinterpret_cast<float*>(16)};
+  tc_prep(h, it, ar, false, plan, h->stream);
+  return ar.off;
+}
+
+// Chunked Hessian for problems whose whole operand set exceeds the handle's
+// operand limit: W-row blocks and F units are built and contracted a chunk at
+// a time in reused buffers (one launch per chunk).
+hess_status run_hessian_chunked(hess_mlp* h, const void* X, const void* Y, int64_t N, bool x3,
+                                void* Hout) {
   using namespace tc;
   HM_TRY(tc_available(h));
   const Net& net = h->net;
@@ -859,7 +1030,7 @@ hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N,
   HM_TRY(classify_ptr(h, Hout, &o_dev));
   const int64_t ld = align_up((size_t)N, BK);
   int Tmax = 0, Tinmax = 0;
-  int64_t maxPl = 0, maxRest = 0, maxTinRest = 0;
+  int64_t maxPl = 0, maxRest = 0;
   for (int jm = 1; jm < L; ++jm) {
     Tmax = net.T[jm] > Tmax ? net.T[jm] : Tmax;
     Tinmax = net.T[jm - 1] > Tinmax ? net.T[jm - 1] : Tinmax;
@@ -867,10 +1038,9 @@ hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N,
     maxPl = pl > maxPl ? pl : maxPl;
     int64_t rest = P - net.boff[jm - 1];
     maxRest = rest > maxRest ? rest : maxRest;
-    maxTinRest = (int64_t)net.T[jm - 1] * rest > maxTinRest ? (int64_t)net.T[jm - 1] * rest : maxTinRest;
   }
   // operand budget: A rows per chunk and bias units per F chunk
-  const double budget = 3.0e9;
+  const double budget = (double)h->op_limit;
   int64_t arows_cap = (int64_t)(budget / (double)(ld * 4));
   if (arows_cap < BM) arows_cap = BM;
   int64_t arows_max = 0;
@@ -880,11 +1050,9 @@ hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N,
     int64_t need = tot < arows_cap ? tot : (Tout * Tin > arows_cap ? Tout * Tin : arows_cap);
     arows_max = need > arows_max ? need : arows_max;
   }
-  int64_t per_unit = N * maxRest * 4 + maxTinRest * 4 / (Tmax > 0 ? 1 : 1);
   int pchunk = (int)(budget / (double)(ld * maxRest * 4));
   if (pchunk > Tmax) pchunk = Tmax;
   if (pchunk < 1) pchunk = 1;
-  (void)per_unit;
   int64_t max_tiles = cdiv(arows_max, BM) * cdiv(Tinmax, 64);
   for (int jm = 1; jm < L; ++jm) {
     const int64_t rest = P - net.boff[jm - 1];
@@ -893,7 +1061,7 @@ hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N,
   }
   char* split = nullptr;
   auto plan = [&](Arena& ar, float*& xs, float*& ys, Caches<float>& c, RopBufs<float>& r,
-                  float*& tmp, float*& ones, __nv_bfloat16*& bhi, __nv_bfloat16*& blo,
+                  float*& tmp, __nv_bfloat16*& bhi, __nv_bfloat16*& blo,
                   __nv_bfloat16*& ahi, __nv_bfloat16*& alo, __nv_bfloat16*& fhi,
                   __nv_bfloat16*& flo, float*& O,
                   int4*& tl, Job*& jd, int*& err) {
@@ -902,7 +1070,6 @@ hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N,
     plan_caches(ar, net, N, c);
     plan_rop(ar, net, N, 1, Tmax, r);
     tmp = ar.take<float>((int64_t)Tmax * maxPl);
-    ones = ar.take<float>(N);
     bhi = ar.take<__nv_bfloat16>((int64_t)Tinmax * ld);
     blo = ar.take<__nv_bfloat16>((int64_t)Tinmax * ld);
     ahi = ar.take<__nv_bfloat16>(arows_max * ld);
@@ -916,17 +1083,17 @@ hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N,
     split = ar.take<char>(kSplitBytes);
   };
   Arena ar;
-  float *xs, *ys, *tmp, *ones, *O;
+  float *xs, *ys, *tmp, *O;
   __nv_bfloat16 *bhi, *blo, *ahi, *alo, *fhi, *flo;
   int4* tl;
   Job* jd;
   int* err;
   Caches<float> c;
   RopBufs<float> r;
-  plan(ar, xs, ys, c, r, tmp, ones, bhi, blo, ahi, alo, fhi, flo, O, tl, jd, err);
+  plan(ar, xs, ys, c, r, tmp, bhi, blo, ahi, alo, fhi, flo, O, tl, jd, err);
   HM_TRY(ensure_ws(h, ar.off));
   ar = Arena{h->ws, 0};
-  plan(ar, xs, ys, c, r, tmp, ones, bhi, blo, ahi, alo, fhi, flo, O, tl, jd, err);
+  plan(ar, xs, ys, c, r, tmp, bhi, blo, ahi, alo, fhi, flo, O, tl, jd, err);
   SplitGuard sg(split, kSplitBytes, h->sm_count);
   cudaStream_t s = h->stream;
   const float* xd = (const float*)X;
@@ -940,7 +1107,6 @@ hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N,
     yd = ys;
   }
   HM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-  HM_TRY(fill(ones, N, 1.0f, s));
   const float* omega = h->omega32;
   HM_TRY(forward_backward(net, omega, xd, yd, c, s));
   std::vector<int4> tiles;
@@ -994,7 +1160,7 @@ hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N,
           for (int q = 0; q < Tin; ++q)
             ent += (double)(Tout - u) * Tin - q;
         Tick t(h, HESS_K_HCONTRACT, 2.0 * N * ent, 0.0);
-        HM_TRY(launch_jobs(h, &job, 1, tiles.data(), (int)tiles.size(), jd, tl, x3, err, s));
+        HM_TRY(launch_jobs(h->sm_count, &job, 1, tiles.data(), (int)tiles.size(), jd, tl, x3, err, s));
       }
       p0 = p1;
     }
@@ -1059,12 +1225,28 @@ hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N,
       job.brow = rest;
       {
         Tick t(h, HESS_K_HCONTRACT, 2.0 * N * (double)pc * Tin * rest, 0.0);
-        HM_TRY(launch_jobs(h, &job, 1, tiles.data(), (int)tiles.size(), jd, tl, x3, err, s));
+        HM_TRY(launch_jobs(h->sm_count, &job, 1, tiles.data(), (int)tiles.size(), jd, tl, x3, err, s));
       }
     }
   }
   if (!o_dev) HM_CUDA(cudaMemcpyAsync(Hout, O, P * P * 4, cudaMemcpyDeviceToHost, s));
-  return check_err_flag(h, err);
+  return tc_check_err(s, h->host_pinned, err);
+}
+
+
+// OPG = G^T G / N with split-BF16 (or BF16) operands on the tensor cores.
+hess_status run_opg_tc(hess_mlp* h, const void* X, const void* Y, int64_t N, bool x3, void* Oout) {
+  HM_TRY(tc_available(h));
+  return run_single(h, X, Y, N, x3, Oout, 0);
+}
+
+// Exact Hessian on the tensor cores: one persistent launch over every weight
+// layer's blocks when the whole operand set fits the handle's operand limit,
+// else the chunked schedule.
+hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N, bool x3, void* Hout) {
+  HM_TRY(tc_available(h));
+  if (hessian_plan_bytes(h, N) <= h->op_limit) return run_single(h, X, Y, N, x3, Hout, 1);
+  return run_hessian_chunked(h, X, Y, N, x3, Hout);
 }
 
 }  // namespace hm

@@ -185,3 +185,13 @@ def make_random_mlp(seed: int, index: int, p_lo: int = 500, p_hi: int = 20000):
         P = sum(widths[i] * widths[i + 1] + widths[i + 1] for i in range(len(widths) - 1))
         if p_lo <= P <= p_hi:
             return widths, acts, N
+
+
+
+def make_batch_problem(seed: int, index: int) -> Problem:
+    """Network `index` of the many-networks workload drawn with `seed`: the
+    structure and N from make_random_mlp(seed, index), then a problem with
+    x ~ N(0,1), uniform labels over 10 classes and Glorot weights, all from the
+    seed seed * 100000 + index."""
+    widths, acts, N = make_random_mlp(seed, index)
+    return make_problem(widths, acts, N, seed * 100000 + index, "normal", "zero")

@@ -77,3 +77,15 @@ def test_calls_reject_null_handle_and_bad_sizes(lib):
     assert lib.hess_mlp_num_params(None) == -1
     assert lib.hess_mlp_destroy(None) == _lib.HESS_OK
     assert lib.hess_param_permutation(1, None, None) == _lib.HESS_ERR_INVALID_ARG
+
+
+def test_batch_entry_points_reject_bad_arguments_before_touching_cuda(lib):
+    from paper_1905_05559_gb300 import _lib
+    b = ctypes.c_void_p()
+    assert lib.hess_batch_create(1 << 20, None, ctypes.byref(b)) == _lib.HESS_ERR_INVALID_ARG
+    assert "workspace" in _lib.last_error()
+    assert lib.hess_batch_create(1 << 30, None, None) == _lib.HESS_ERR_INVALID_ARG
+    info = _lib.BatchInfo()
+    assert lib.hess_batch_run(None, None, 0, 3, ctypes.byref(info)) == _lib.HESS_ERR_INVALID_ARG
+    assert lib.hess_batch_destroy(None) == _lib.HESS_OK
+    assert lib.hess_mlp_set_operand_limit(None, 1 << 30) == _lib.HESS_ERR_INVALID_ARG

@@ -68,6 +68,7 @@ def test_tc_opg_and_hessian(hm, case, prec):
     H = net.exact_hessian(Xd, Yd, prec).cpu().numpy()
     Hr = O.hessian(om, widths, acts, X, Y)
     assert relerr(H, Hr) <= TOL[prec]
+    assert np.array_equal(H, H.T)
     # every entry written: no NaN from uninitialised memory
     assert np.isfinite(H).all() and np.isfinite(OPG).all()
 
