@@ -58,7 +58,7 @@ hess_status check_item(const hess_batch* b, const hess_batch_item& it, int idx) 
 // Workspace bytes of one item inside a wave (its arena share).
 size_t item_bytes(const hess_batch_item& it, TcPlan& plan) {
   Arena ar;
-  TcItem ti{it.X, it.Y, it.N, it.opg, it.hessian};
+  TcItem ti{it.X, it.Y, it.N, it.opg != nullptr, it.hessian != nullptr, it.opg, it.hessian};
   tc_prep(it.net, ti, ar, false, plan, nullptr);
   return align_up(ar.off, 256);
 }
@@ -164,7 +164,7 @@ hess_status hess_batch_run(hess_batch* b, const hess_batch_item* items, int coun
       Arena ar{b->ws, base};
       for (int q = i; q < j; ++q) {
         const hess_batch_item& it = items[q];
-        TcItem ti{it.X, it.Y, it.N, it.opg, it.hessian};
+        TcItem ti{it.X, it.Y, it.N, it.opg != nullptr, it.hessian != nullptr, it.opg, it.hessian};
         const size_t at = ar.off;
         HM_TRY(tc_prep(it.net, ti, ar, true, plan, s));
         ar.off = at + align_up(ar.off - at, 256);

@@ -266,7 +266,8 @@ struct Job {
   uint32_t idesc; // instruction descriptor (N = BN)
   int mode;       // 0: symmetric rank-K update (orow = m, ocol = n)
                   // 1: Hessian rows of one weight layer, W columns
-                  // 2: Hessian rows of one weight layer, columns after W
+                  // 2: Hessian rows of one weight layer (W rows and, from the
+                  //    ones row of A, bias rows), columns after W
   float scale;
   float* out;
   int64_t ldo;
@@ -286,12 +287,14 @@ struct TcPlan {
   double syrk_flops = 0.0, hess_flops = 0.0;
 };
 
-// One network's request: device X (N x T_1), Y (N x T_L) and P x P device
-// outputs (either may be null).
+// One network's request: device X (N x T_1), Y (N x T_L) and the P x P
+// device outputs of the requested matrices (the pointers are not consulted to
+// decide what is requested: a planning pass may pass placeholders).
 struct TcItem {
   const float* X = nullptr;
   const float* Y = nullptr;
   int64_t N = 0;
+  bool want_opg = false, want_hess = false;
   float* opg = nullptr;
   float* hess = nullptr;
 };

@@ -184,6 +184,18 @@ __host__ __device__ __forceinline__ int64_t rows_before(int64_t p, int64_t Tin, 
 // the Hessian column W_(i,k).  Mode 2: the tile's unit u = tile_y / ntn; rows
 // are the directions W_(u,q) and the product column n is the n-th Hessian
 // column from the layer's bias on.
+// Unit u of concatenated W row r: rows_before(u) <= r < rows_before(u + 1)
+// (the root of the quadratic rows_before, then corrected by whole steps).
+__device__ __forceinline__ int64_t wrow_unit(int64_t r, int64_t Tin, int64_t Tout) {
+  const double b = 2.0 * Tout + 1.0;
+  int64_t u = (int64_t)floor((b - sqrt(fmax(b * b - 8.0 * (double)r / (double)Tin, 0.0))) * 0.5);
+  if (u < 0) u = 0;
+  if (u > Tout - 1) u = Tout - 1;
+  while (u > 0 && rows_before(u, Tin, Tout) > r) --u;
+  while (u + 1 < Tout && rows_before(u + 1, Tin, Tout) <= r) ++u;
+  return u;
+}
+
 __device__ __forceinline__ void row_map(const Job& p, int64_t m, int tile_y, int64_t& orow,
                                         int64_t& ocolb) {
   if (p.mode == 0) {
@@ -193,17 +205,14 @@ __device__ __forceinline__ void row_map(const Job& p, int64_t m, int tile_y, int
   }
   const int64_t Tin = p.Tin, Tout = p.Tout;
   if (p.mode == 2) {
-    orow = p.woff + (int64_t)(p.p0 + tile_y / p.ntn) * Tin + m;
+    // rows q < Tin: W_(u,q); row Tin: the bias b_u (the ones row of A)
+    const int64_t u = p.p0 + tile_y / p.ntn;
+    orow = m < Tin ? p.woff + u * Tin + m : p.boff + u;
     ocolb = p.boff;
     return;
   }
   const int64_t r = m + p.R0;
-  const double b = 2.0 * Tout + 1.0;
-  int64_t u = (int64_t)floor((b - sqrt(fmax(b * b - 8.0 * (double)r / (double)Tin, 0.0))) * 0.5);
-  if (u < 0) u = 0;
-  if (u > Tout - 1) u = Tout - 1;
-  while (u > 0 && rows_before(u, Tin, Tout) > r) --u;
-  while (u + 1 < Tout && rows_before(u + 1, Tin, Tout) <= r) ++u;
+  const int64_t u = wrow_unit(r, Tin, Tout);
   const int64_t rr = r - rows_before(u, Tin, Tout);
   const int64_t i = u + rr / Tin, q = rr % Tin;
   orow = p.woff + u * Tin + q;
@@ -481,99 +490,135 @@ __global__ void transpose_split_kernel(const float* in, int64_t rows, int64_t co
   }
 }
 
-// A operand of the Hessian rows of weight layer W (T_out x T_in) for units
-// p in [p0, p1): row (p, i, q) with i = p..Tout-1 holds, at column n,
-//   R{delta}[n, b_p, i] * a[n, q]
-// -- the R-operator of the weight direction W_(p,q) is a[n,q] times that of
-// the bias direction b_p, because a unit direction only moves z_p.
-// U: [n][p][i] (N x Tout x Tout), a: N x Tin.  Grid (n tiles, q tiles, p).
-__global__ void build_wrows_kernel(const float* U, const float* a, int64_t N, int Tin, int Tout,
-                                   int p0, int64_t R0, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                                   int64_t ld) {
-  __shared__ float sa[32][33];
-  __shared__ float su[32];
-  const int p = p0 + blockIdx.z;
-  const int64_t n0 = (int64_t)blockIdx.x * 32;
-  const int q0 = blockIdx.y * 32;
+// out[c * ld + r] = in[r * ldin + c] for r < rows, 0 for rows <= r < ld: an
+// example-major array turned example-fastest, so that the operand builders
+// below read and write along the examples with whole-warp accesses.
+__global__ void transpose_pad_kernel(const float* in, int64_t rows, int64_t cols, int64_t ldin, float* out,
+                                     int64_t ld) {
+  __shared__ float t[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
   for (int y = threadIdx.y; y < 32; y += 8) {
-    const int64_t n = n0 + y;
-    const int q = q0 + threadIdx.x;
-    sa[y][threadIdx.x] = (n < N && q < Tin) ? a[n * Tin + q] : 0.f;
+    const int64_t r = r0 + y, c = c0 + threadIdx.x;
+    t[y][threadIdx.x] = (r < rows && c < cols) ? in[r * ldin + c] : 0.f;
   }
-  const int64_t rbase = rows_before(p, Tin, Tout) - R0;
-  for (int i = p; i < Tout; ++i) {
-    __syncthreads();
-    if (threadIdx.y == 0) {
-      const int64_t n = n0 + threadIdx.x;
-      su[threadIdx.x] = n < N ? U[(n * Tout + p) * Tout + i] : 0.f;
-    }
-    __syncthreads();
-    const int64_t n = n0 + threadIdx.x;
-    if (n >= ld) continue;
-    for (int y = threadIdx.y; y < 32; y += 8) {
-      const int q = q0 + y;
-      if (q >= Tin) continue;
-      __nv_bfloat16 h, l;
-      split2(su[threadIdx.x] * sa[threadIdx.x][y], h, l);
-      const int64_t row = rbase + (int64_t)(i - p) * Tin + q;
-      hi[row * ld + n] = h;
-      lo[row * ld + n] = l;
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const int64_t c = c0 + y, r = r0 + threadIdx.x;
+    if (c < cols && r < ld) out[c * ld + r] = t[threadIdx.x][y];
+  }
+}
+
+__device__ __forceinline__ void split2_store(float2 v, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t at) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
+  *reinterpret_cast<__nv_bfloat162*>(hi + at) = h;
+  *reinterpret_cast<__nv_bfloat162*>(lo + at) = l;
+}
+
+// Row Tin of the mode-2 A operand: ones over the examples (zero padding
+// beyond N), so that the same job also yields the bias rows:
+// H[b_u, c] = (1/N) sum_n F[n, u, c].
+__global__ void ones_row_kernel(__nv_bfloat16* hi, __nv_bfloat16* lo, int64_t N, int64_t ld) {
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < ld; n += (int64_t)gridDim.x * blockDim.x) {
+    hi[n] = __float2bfloat16_rn(n < N ? 1.f : 0.f);
+    lo[n] = __float2bfloat16_rn(0.f);
+  }
+}
+
+// A operand of the Hessian rows of weight layer W (T_out x T_in): rows
+// R0 .. R0 + nrows - 1 of the concatenation over units u of the rows
+// (u, i, q), i = u..Tout-1, each holding, at example n,
+//   R{delta}[n, b_u, i] * a[n, q]
+// -- the R-operator of the weight direction W_(u,q) is a[n,q] times that of
+// the bias direction b_u, because a unit direction only moves z_u.
+// rdT: [u][i][ld] and aT: [q][ld], example-fastest and zero-padded.
+__global__ void build_wrows_kernel(const float* rdT, const float* aT, int Tin, int Tout, int64_t R0,
+                                   int64_t nrows, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ld) {
+  // one warp per row, lanes along the examples
+  const int lane = threadIdx.x & 31;
+  const int64_t half = ld / 2;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = w0; r < nrows; r += nw) {
+    const int64_t g = r + R0;
+    const int64_t u = wrow_unit(g, Tin, Tout);
+    const int64_t rr = g - rows_before(u, Tin, Tout);
+    const int64_t i = u + rr / Tin, q = rr % Tin;
+    const float2* x = reinterpret_cast<const float2*>(rdT + (u * Tout + i) * ld);
+    const float2* y = reinterpret_cast<const float2*>(aT + q * ld);
+    const int64_t at = r * ld;
+    for (int64_t j = lane; j < half; j += 32) {
+      const float2 p = x[j], w = y[j];
+      split2_store(make_float2(p.x * w.x, p.y * w.y), hi, lo, at + 2 * j);
     }
   }
 }
 
-// F[n, p, c] over the Hessian columns after W^(jm): the bias b^(jm+1) and all
-// later layers, for the bias directions b_p of layer jm (the weight
-// directions W_(p,q) then follow as a[n,q] F[n, p, c]):
-//   column b_i of layer jl:     R{delta^(jl)}[n,p,i]
-//   column W_(i,k) of layer jl: R{delta^(jl)}[n,p,i] a^(jl-1)[n,k]
-//                               + delta^(jl)[n,i] R{a^(jl-1)}[n,p,k]
+// F[n, u, c] over the Hessian columns after W^(jm): the bias b^(jm+1) and all
+// later layers, for the bias directions b_u of layer jm (the weight
+// directions W_(u,q) then follow as a[n,q] F[n, u, c]):
+//   column b_i of layer jl:     R{delta^(jl)}[n,u,i]
+//   column W_(i,k) of layer jl: R{delta^(jl)}[n,u,i] a^(jl-1)[n,k]
+//                               + delta^(jl)[n,i] R{a^(jl-1)}[n,u,k]
+// Every input is example-fastest and zero-padded to ld.
 struct FSeg {
   int64_t c0;  // first column of the segment (relative)
   int64_t nW;  // Tout*Tin of the layer (0 for the first segment)
   int Tin, Tout;
-  const float* rd;    // [n][p][Tout]
-  const float* a;     // N x Tin
-  const float* dlt;   // N x Tout
-  const float* ra;    // [n][p][Tin] or null
+  const float* rd;    // [u][Tout][ld]
+  const float* a;     // [Tin][ld]
+  const float* dlt;   // [Tout][ld]
+  const float* ra;    // [u][Tin][ld] or null
 };
 constexpr int MAXSEG = 8;
 struct FArgs {
   int nseg;
   FSeg seg[MAXSEG];
   int64_t cols;
-  int B;  // bias directions (= T of layer jm)
 };
 // The same F as split-BF16 planes, K-major for the tensor cores: row
-// (p - p0) * cols + c holds F[., p, c] over the examples n (zero-padded to ld).
-__global__ void build_f_bf16_kernel(FArgs f, int64_t N, int p0, int np, __nv_bfloat16* hi,
-                                    __nv_bfloat16* lo, int64_t ld) {
+// (u - p0) * cols + c holds F[., u, c] over the examples (zero-padded to ld).
+__global__ void build_f_bf16_kernel(FArgs f, int p0, int np, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                                    int64_t ld) {
+  // one warp per row, lanes along the examples
+  const int lane = threadIdx.x & 31;
   const int64_t rows = (int64_t)np * f.cols;
-  const int64_t total = rows * ld;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t n = idx % ld;
-    const int64_t row = idx / ld;
+  const int64_t half = ld / 2;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = w0; row < rows; row += nw) {
+    const int u = p0 + (int)(row / f.cols);
     const int64_t c = row % f.cols;
-    const int pp = p0 + (int)(row / f.cols);
-    float v = 0.f;
-    if (n < N) {
-      int s = 0;
-      while (s + 1 < f.nseg && f.seg[s + 1].c0 <= c) ++s;
-      const FSeg& g = f.seg[s];
-      const int64_t cl = c - g.c0;
-      if (cl < g.nW) {
-        const int i = (int)(cl / g.Tin), k = (int)(cl % g.Tin);
-        v = g.rd[(n * f.B + pp) * g.Tout + i] * g.a[n * g.Tin + k];
-        if (g.ra) v += g.dlt[n * g.Tout + i] * g.ra[(n * f.B + pp) * g.Tin + k];
-      } else {
-        v = g.rd[(n * f.B + pp) * g.Tout + (int)(cl - g.nW)];
+    int s = 0;
+    while (s + 1 < f.nseg && f.seg[s + 1].c0 <= c) ++s;
+    const FSeg& g = f.seg[s];
+    const int64_t cl = c - g.c0;
+    const float2 *x1, *y1 = nullptr, *x2 = nullptr, *y2 = nullptr;
+    if (cl < g.nW) {
+      const int i = (int)(cl / g.Tin), k = (int)(cl % g.Tin);
+      x1 = reinterpret_cast<const float2*>(g.rd + ((int64_t)u * g.Tout + i) * ld);
+      y1 = reinterpret_cast<const float2*>(g.a + (int64_t)k * ld);
+      if (g.ra) {
+        x2 = reinterpret_cast<const float2*>(g.dlt + (int64_t)i * ld);
+        y2 = reinterpret_cast<const float2*>(g.ra + ((int64_t)u * g.Tin + k) * ld);
       }
+    } else {
+      x1 = reinterpret_cast<const float2*>(g.rd + ((int64_t)u * g.Tout + (cl - g.nW)) * ld);
     }
-    __nv_bfloat16 h, l;
-    split2(v, h, l);
-    hi[idx] = h;
-    lo[idx] = l;
+    const int64_t at = row * ld;
+    for (int64_t j = lane; j < half; j += 32) {
+      float2 v = x1[j];
+      if (y1) {
+        const float2 w = y1[j];
+        v = make_float2(v.x * w.x, v.y * w.y);
+      }
+      if (x2) {
+        const float2 d = x2[j], r = y2[j];
+        v = make_float2(fmaf(d.x, r.x, v.x), fmaf(d.y, r.y, v.y));
+      }
+      split2_store(v, hi, lo, at + 2 * j);
+    }
   }
 }
 
@@ -748,19 +793,61 @@ static double wblock_entries(int64_t Tin, int64_t Tout, int64_t p0, int64_t p1) 
   return ent;
 }
 
+// Example-fastest copies (zero-padded to ld) of what the Hessian operand
+// builders read: activations a^(j) and errors delta^(j) of the network, and
+// R{delta^(j)}, R{a^(j)} of the current weight layer's bias directions.
+struct TQ {
+  float* a[kMaxLayers] = {};   // positions 0..L-2: [T_j][ld]
+  float* d[kMaxLayers] = {};   // positions 2..L-1: [T_j][ld]
+  float* rd[kMaxLayers] = {};  // positions 1..L-1: [u][T_j][ld] (reused for every weight layer)
+  float* ra[kMaxLayers] = {};  // positions 1..L-2: [u][T_j][ld]
+};
+
+static void plan_tq(Arena& ar, const Net& net, int64_t ld, int Bmax, TQ& t) {
+  const int L = net.L;
+  for (int j = 0; j + 1 < L; ++j) t.a[j] = ar.take<float>((int64_t)net.T[j] * ld);
+  for (int j = 2; j < L; ++j) t.d[j] = ar.take<float>((int64_t)net.T[j] * ld);
+  for (int j = 1; j < L; ++j) t.rd[j] = ar.take<float>((int64_t)Bmax * net.T[j] * ld);
+  for (int j = 1; j + 1 < L; ++j) t.ra[j] = ar.take<float>((int64_t)Bmax * net.T[j] * ld);
+}
+
+static hess_status transpose_pad(const float* in, int64_t rows, int64_t cols, float* out, int64_t ld,
+                                 cudaStream_t s) {
+  tc::transpose_pad_kernel<<<dim3((unsigned)cdiv(ld, 32), (unsigned)cdiv(cols, 32)), dim3(32, 8), 0, s>>>(
+      in, rows, cols, cols, out, ld);
+  HM_LAUNCHED();
+  return HESS_OK;
+}
+
+static hess_status transpose_caches(const Net& net, const Caches<float>& c, int64_t N, int64_t ld, TQ& t,
+                                    cudaStream_t s) {
+  const int L = net.L;
+  for (int j = 0; j + 1 < L; ++j) HM_TRY(transpose_pad(c.a[j], N, net.T[j], t.a[j], ld, s));
+  for (int j = 2; j < L; ++j) HM_TRY(transpose_pad(c.d[j], N, net.T[j], t.d[j], ld, s));
+  return HESS_OK;
+}
+
+// R-quantities of weight layer jm's B = T_jm bias directions, [n][u][t] ->
+// [u][t][n].
+static hess_status transpose_rop(const Net& net, const RopBufs<float>& rb, int jm, int64_t N, int64_t ld,
+                                 TQ& t, cudaStream_t s) {
+  const int L = net.L, B = net.T[jm];
+  for (int j = jm; j < L; ++j) HM_TRY(transpose_pad(rb.rd[j], N, (int64_t)B * net.T[j], t.rd[j], ld, s));
+  for (int j = jm; j + 1 < L; ++j) HM_TRY(transpose_pad(rb.ra[j], N, (int64_t)B * net.T[j], t.ra[j], ld, s));
+  return HESS_OK;
+}
+
 // F segments of weight layer jm: the bias b^(jm+1) and every later layer.
-static hess_status f_args(const Net& net, const Caches<float>& c, const RopBufs<float>& rb, int jm,
-                          tc::FArgs& fa) {
+static hess_status f_args(const Net& net, const TQ& t, int jm, tc::FArgs& fa) {
   using namespace tc;
   const int L = net.L;
   const int64_t boff = net.boff[jm - 1];
   fa = FArgs{};
   fa.cols = net.P - boff;
-  fa.B = net.T[jm];
   FSeg g{};
   g.Tin = net.T[jm - 1];
   g.Tout = net.T[jm];
-  g.rd = rb.rd[jm];
+  g.rd = t.rd[jm];
   fa.seg[fa.nseg++] = g;
   for (int jl = jm + 1; jl < L; ++jl) {
     if (fa.nseg >= MAXSEG) return set_error(HESS_ERR_UNSUPPORTED, "too many layers for the tensor-core Hessian");
@@ -769,13 +856,113 @@ static hess_status f_args(const Net& net, const Caches<float>& c, const RopBufs<
     q.nW = (int64_t)net.T[jl - 1] * net.T[jl];
     q.Tin = net.T[jl - 1];
     q.Tout = net.T[jl];
-    q.rd = rb.rd[jl];
-    q.a = c.a[jl - 1];
-    q.dlt = c.d[jl];
-    q.ra = rb.ra[jl - 1];
+    q.rd = t.rd[jl];
+    q.a = t.a[jl - 1];
+    q.dlt = t.d[jl];
+    q.ra = t.ra[jl - 1];
     fa.seg[fa.nseg++] = q;
   }
   return HESS_OK;
+}
+
+// Blocks of 256 threads (a warp per row) for an operand builder over `rows`
+// rows: enough to fill every SM several times, each warp looping over rows.
+static unsigned builder_blocks(int64_t rows, int sms) {
+  const int64_t want = cdiv(rows, 8), cap = (int64_t)sms * 16;
+  return (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+// Operands of weight layer jm shared by its W-row and F contractions: the
+// layer input a^(jm-1) as split planes, rows 0..Tin-1, and the ones row Tin.
+static hess_status build_layer_b(const Net& net, const Caches<float>& c, int jm, int64_t N, int64_t ld,
+                                 __nv_bfloat16* bhi, __nv_bfloat16* blo, cudaStream_t s) {
+  const int Tin = net.T[jm - 1];
+  tc::transpose_split_kernel<<<dim3((unsigned)cdiv(ld, 32), (unsigned)cdiv(Tin, 32)), dim3(32, 8), 0, s>>>(
+      c.a[jm - 1], N, Tin, Tin, bhi, blo, ld);
+  HM_LAUNCHED();
+  tc::ones_row_kernel<<<(unsigned)cdiv(ld, 256), 256, 0, s>>>(bhi + (int64_t)Tin * ld, blo + (int64_t)Tin * ld,
+                                                               N, ld);
+  HM_LAUNCHED();
+  return HESS_OK;
+}
+
+// W rows of units [p0, p1), where R0 = rows_before(p0).
+static hess_status build_wrows(const Net& net, const TQ& t, int jm, int p1, int64_t R0, int64_t ld, int sms,
+                               __nv_bfloat16* ahi, __nv_bfloat16* alo, cudaStream_t s) {
+  const int Tin = net.T[jm - 1], Tout = net.T[jm];
+  const int64_t nrows = tc::rows_before(p1, Tin, Tout) - R0;
+  tc::build_wrows_kernel<<<builder_blocks(nrows, sms), 256, 0, s>>>(t.rd[jm], t.a[jm - 1], Tin, Tout, R0, nrows,
+                                                                      ahi, alo, ld);
+  HM_LAUNCHED();
+  return HESS_OK;
+}
+
+static hess_status build_f(const tc::FArgs& fa, int p0, int np, int64_t ld, int sms, __nv_bfloat16* fhi,
+                           __nv_bfloat16* flo, cudaStream_t s) {
+  tc::build_f_bf16_kernel<<<builder_blocks((int64_t)np * fa.cols, sms), 256, 0, s>>>(fa, p0, np, fhi, flo, ld);
+  HM_LAUNCHED();
+  return HESS_OK;
+}
+
+// Jobs of weight layer jm: W rows (u, i, q) for units [p0, p1) against the
+// W columns (mode 1); W and bias rows of units [q0, q0 + np) against the
+// columns after W (mode 2).
+static void wrow_job(const Net& net, int jm, int p0, int p1, int64_t R0, float* out, int64_t N, tc::Job& job,
+                     std::vector<int4>& tiles, int jid) {
+  using namespace tc;
+  const int Tin = net.T[jm - 1], Tout = net.T[jm];
+  const int64_t rows = rows_before(p1, Tin, Tout) - R0;
+  const int BN = pick_bn(Tin);
+  job.BN = BN;
+  job.M = rows;
+  job.Nn = Tin;
+  job.scale = 1.0f / (float)N;
+  job.out = out;
+  job.ldo = net.P;
+  job.mode = 1;
+  job.woff = net.woff[jm - 1];
+  job.Tin = Tin;
+  job.Tout = Tout;
+  job.p0 = p0;
+  job.R0 = R0;
+  for (int64_t tm = 0; tm < cdiv(rows, BM); ++tm)
+    for (int64_t tn = 0; tn < cdiv(Tin, BN); ++tn) tiles.push_back(make_int4(jid, (int)tm, (int)tn, 0));
+}
+
+static void f_job(const Net& net, int jm, int q0, int np, float* out, int64_t N, tc::Job& job,
+                  std::vector<int4>& tiles, int jid) {
+  using namespace tc;
+  const int Tin = net.T[jm - 1], Tout = net.T[jm];
+  const int64_t boff = net.boff[jm - 1], rest = net.P - boff;
+  const int BN = pick_bn(rest);
+  const int ntn = (int)cdiv(rest, BN);
+  job.BN = BN;
+  job.M = Tin + 1;
+  job.Nn = rest;
+  job.scale = 1.0f / (float)N;
+  job.out = out;
+  job.ldo = net.P;
+  job.mode = 2;
+  job.woff = net.woff[jm - 1];
+  job.boff = boff;
+  job.Tin = Tin;
+  job.Tout = Tout;
+  job.p0 = q0;
+  job.ntn = ntn;
+  job.brow = rest;
+  for (int64_t tm = 0; tm < cdiv(Tin + 1, BM); ++tm)
+    for (int u = 0; u < np; ++u)
+      for (int tn = 0; tn < ntn; ++tn) tiles.push_back(make_int4(jid, (int)tm, u * ntn + tn, 0));
+}
+
+// Algorithmic flops of weight layer jm's contractions: the upper triangle of
+// the W x W block for units [p0, p1), and the W and bias rows of np units
+// against the columns after W, 2N each.
+static double wrow_flops(int64_t Tin, int64_t Tout, int64_t p0, int64_t p1, int64_t N) {
+  return 2.0 * N * wblock_entries(Tin, Tout, p0, p1);
+}
+static double f_flops(int64_t Tin, int64_t rest, int64_t np, int64_t N) {
+  return 2.0 * N * (double)np * (Tin + 1) * rest;
 }
 
 hess_status tc_prep(hess_mlp* h, const TcItem& it, Arena& ar, bool live, TcPlan& plan, cudaStream_t s) {
@@ -790,7 +977,7 @@ hess_status tc_prep(hess_mlp* h, const TcItem& it, Arena& ar, bool live, TcPlan&
   Caches<float> c;
   plan_caches(ar, net, N, c);
   if (live) HM_TRY(forward_backward(net, omega, it.X, it.Y, c, s));
-  if (it.opg) {
+  if (it.want_opg) {
     // OPG = G^T G / N (Sec. 3, the outer-product approximation): G is written
     // once in FP32, then split into K-major bf16 planes
     float* G = ar.take<float>(N * P);
@@ -819,104 +1006,52 @@ hess_status tc_prep(hess_mlp* h, const TcItem& it, Arena& ar, bool live, TcPlan&
     syrk_tiles(P, 256, (int)plan.jobs.size(), plan.tiles);
     plan.jobs.push_back(job);
   }
-  if (it.hess) {
-    // exact Hessian (Sec. 3, Eq. for H_ij): R-operator over the bias
-    // directions of each weight layer, the W x W block and the columns after
-    // W on the tensor cores, the remaining entries by SIMT contractions
+  if (it.want_hess) {
+    // exact Hessian (Sec. 3, Eq. for H_ij) from the R-operator over the bias
+    // directions of each weight layer: the W x W block (mode 1) and the W and
+    // bias rows against the columns after W (mode 2), all on the tensor cores
     int Tmax = 0;
-    int64_t maxPl = 0;
-    for (int jm = 1; jm < L; ++jm) {
-      Tmax = net.T[jm] > Tmax ? net.T[jm] : Tmax;
-      const int64_t pl = (int64_t)net.T[jm - 1] * net.T[jm] + net.T[jm];
-      maxPl = pl > maxPl ? pl : maxPl;
-    }
+    for (int jm = 1; jm < L; ++jm) Tmax = net.T[jm] > Tmax ? net.T[jm] : Tmax;
     RopBufs<float> r;
     plan_rop(ar, net, N, 1, Tmax, r);
-    float* tmp = ar.take<float>((int64_t)Tmax * maxPl);
+    TQ tq;
+    plan_tq(ar, net, ld, Tmax, tq);
+    if (live) HM_TRY(transpose_caches(net, c, N, ld, tq, s));
     for (int jm = 1; jm < L; ++jm) {
       const int Tin = net.T[jm - 1], Tout = net.T[jm];
-      const int64_t woff = net.woff[jm - 1], boff = net.boff[jm - 1];
+      const int64_t boff = net.boff[jm - 1];
       const int64_t rows = rows_before(Tout, Tin, Tout);
       const int64_t rest = P - boff;
-      bf* bhi = ar.take<bf>((int64_t)Tin * ld);
-      bf* blo = ar.take<bf>((int64_t)Tin * ld);
+      bf* bhi = ar.take<bf>((int64_t)(Tin + 1) * ld);
+      bf* blo = ar.take<bf>((int64_t)(Tin + 1) * ld);
       bf* ahi = ar.take<bf>(rows * ld);
       bf* alo = ar.take<bf>(rows * ld);
       bf* fhi = ar.take<bf>((int64_t)Tout * rest * ld);
       bf* flo = ar.take<bf>((int64_t)Tout * rest * ld);
-      const double fw = 2.0 * N * wblock_entries(Tin, Tout, 0, Tout);
-      const double ff = 2.0 * N * (double)Tout * Tin * rest;
-      plan.hess_flops += fw + ff;
-      RopBufs<float> rb = r;
-      rb.B = Tout;
+      plan.hess_flops += wrow_flops(Tin, Tout, 0, Tout, N) + f_flops(Tin, rest, Tout, N);
       FArgs fa;
-      HM_TRY(f_args(net, c, rb, jm, fa));
+      HM_TRY(f_args(net, tq, jm, fa));
       if (live) {
+        RopBufs<float> rb = r;
+        rb.B = Tout;
         {
           Tick t(th, HESS_K_ROP, 0.0, 0.0);
           HM_TRY(rop_block(net, omega, c, jm, boff, Tout, rb, s));
         }
-        {
-          Tick t(th, HESS_K_HREST, 0.0, 0.0);
-          for (int jl = jm; jl < L; ++jl) HM_TRY(contract_layer(net, c, rb, jm, jl, boff, tmp, it.hess, s));
-        }
-        transpose_split_kernel<<<dim3((unsigned)cdiv(ld, 32), (unsigned)cdiv(Tin, 32)), dim3(32, 8), 0, s>>>(
-            c.a[jm - 1], N, Tin, Tin, bhi, blo, ld);
-        HM_LAUNCHED();
-        build_wrows_kernel<<<dim3((unsigned)cdiv(ld, 32), (unsigned)cdiv(Tin, 32), (unsigned)Tout),
-                             dim3(32, 8), 0, s>>>(rb.rd[jm], c.a[jm - 1], N, Tin, Tout, 0, 0, ahi, alo, ld);
-        HM_LAUNCHED();
-        const int64_t total = (int64_t)Tout * rest * ld;
-        build_f_bf16_kernel<<<(unsigned)(cdiv(total, 256) < 1048576 ? cdiv(total, 256) : 1048576), 256, 0,
-                              s>>>(fa, N, 0, Tout, fhi, flo, ld);
-        HM_LAUNCHED();
+        HM_TRY(transpose_rop(net, rb, jm, N, ld, tq, s));
+        HM_TRY(build_layer_b(net, c, jm, N, ld, bhi, blo, s));
+        HM_TRY(build_wrows(net, tq, jm, Tout, 0, ld, h->sm_count, ahi, alo, s));
+        HM_TRY(build_f(fa, 0, Tout, ld, h->sm_count, fhi, flo, s));
       }
-      // W x W block: rows (u, i, q), columns q' of W_(i, q')
-      {
-        const int BN = pick_bn(Tin);
-        Job job{};
-        if (live) HM_TRY(make_job(TcOperands{ahi, alo, rows, bhi, blo, Tin, ld}, BN, &job));
-        job.BN = BN;
-        job.M = rows;
-        job.Nn = Tin;
-        job.scale = 1.0f / (float)N;
-        job.out = it.hess;
-        job.ldo = P;
-        job.mode = 1;
-        job.woff = woff;
-        job.Tin = Tin;
-        job.Tout = Tout;
-        const int jid = (int)plan.jobs.size();
-        for (int64_t tm = 0; tm < cdiv(rows, BM); ++tm)
-          for (int64_t tn = 0; tn < cdiv(Tin, BN); ++tn) plan.tiles.push_back(make_int4(jid, (int)tm, (int)tn, 0));
-        plan.jobs.push_back(job);
+      Job jw{}, jf{};
+      if (live) {
+        HM_TRY(make_job(TcOperands{ahi, alo, rows, bhi, blo, Tin, ld}, pick_bn(Tin), &jw));
+        HM_TRY(make_job(TcOperands{bhi, blo, Tin + 1, fhi, flo, (int64_t)Tout * rest, ld}, pick_bn(rest), &jf));
       }
-      // columns after W: rows q of unit u against F[., u, c]
-      {
-        const int BN2 = pick_bn(rest);
-        const int ntn = (int)cdiv(rest, BN2);
-        Job job{};
-        if (live) HM_TRY(make_job(TcOperands{bhi, blo, Tin, fhi, flo, (int64_t)Tout * rest, ld}, BN2, &job));
-        job.BN = BN2;
-        job.M = Tin;
-        job.Nn = rest;
-        job.scale = 1.0f / (float)N;
-        job.out = it.hess;
-        job.ldo = P;
-        job.mode = 2;
-        job.woff = woff;
-        job.boff = boff;
-        job.Tin = Tin;
-        job.Tout = Tout;
-        job.p0 = 0;
-        job.ntn = ntn;
-        job.brow = rest;
-        const int jid = (int)plan.jobs.size();
-        for (int64_t tm = 0; tm < cdiv(Tin, BM); ++tm)
-          for (int u = 0; u < Tout; ++u)
-            for (int tn = 0; tn < ntn; ++tn) plan.tiles.push_back(make_int4(jid, (int)tm, u * ntn + tn, 0));
-        plan.jobs.push_back(job);
-      }
+      wrow_job(net, jm, 0, Tout, 0, it.hess, N, jw, plan.tiles, (int)plan.jobs.size());
+      plan.jobs.push_back(jw);
+      f_job(net, jm, 0, Tout, it.hess, N, jf, plan.tiles, (int)plan.jobs.size());
+      plan.jobs.push_back(jf);
     }
   }
   return HESS_OK;
@@ -981,7 +1116,7 @@ static hess_status run_single(hess_mlp* h, const void* X, const void* Y, int64_t
     HM_TRY(stage(h, ar, live, X, Y, out, N, st, d));
     err = ar.take<int>(1);
     split = ar.take<char>(kSplitBytes);
-    TcItem it{d.X, d.Y, N, kind == 0 ? d.out : nullptr, kind == 1 ? d.out : nullptr};
+    TcItem it{d.X, d.Y, N, kind == 0, kind == 1, kind == 0 ? d.out : nullptr, kind == 1 ? d.out : nullptr};
     if (live) HM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     SplitGuard sg(split, kSplitBytes, h->sm_count);
     HM_TRY(tc_prep(h, it, ar, live, plan, s));
@@ -1009,230 +1144,140 @@ static hess_status run_single(hess_mlp* h, const void* X, const void* Y, int64_t
 static size_t hessian_plan_bytes(hess_mlp* h, int64_t N) {
   TcPlan plan;
   Arena ar;
-  TcItem it{nullptr, nullptr, N, nullptr, reinterpret_cast<float*>(16)};
+  TcItem it{nullptr, nullptr, N, false, true, nullptr, nullptr};
   tc_prep(h, it, ar, false, plan, h->stream);
   return ar.off;
 }
 
 // Chunked Hessian for problems whose whole operand set exceeds the handle's
 // operand limit: W-row blocks and F units are built and contracted a chunk at
-// a time in reused buffers (one launch per chunk).
+// a time in reused buffers (one launch per chunk).  Same operands and tiles
+// per entry as the one-launch schedule, so the same bits.
 hess_status run_hessian_chunked(hess_mlp* h, const void* X, const void* Y, int64_t N, bool x3,
                                 void* Hout) {
   using namespace tc;
-  HM_TRY(tc_available(h));
+  using bf = __nv_bfloat16;
   const Net& net = h->net;
   const int L = net.L;
-  const int64_t P = net.P, T1 = net.T[0], TL = net.T[L - 1];
-  int x_dev, y_dev, o_dev;
-  HM_TRY(classify_ptr(h, X, &x_dev));
-  HM_TRY(classify_ptr(h, Y, &y_dev));
-  HM_TRY(classify_ptr(h, Hout, &o_dev));
+  const int64_t P = net.P;
+  Staged st{(const float*)X, (const float*)Y, (float*)Hout, 0, 0, 0};
+  HM_TRY(classify_ptr(h, X, &st.x_dev));
+  HM_TRY(classify_ptr(h, Y, &st.y_dev));
+  HM_TRY(classify_ptr(h, Hout, &st.o_dev));
   const int64_t ld = align_up((size_t)N, BK);
   int Tmax = 0, Tinmax = 0;
-  int64_t maxPl = 0, maxRest = 0;
+  int64_t maxRest = 0;
   for (int jm = 1; jm < L; ++jm) {
     Tmax = net.T[jm] > Tmax ? net.T[jm] : Tmax;
     Tinmax = net.T[jm - 1] > Tinmax ? net.T[jm - 1] : Tinmax;
-    int64_t pl = (int64_t)net.T[jm - 1] * net.T[jm] + net.T[jm];
-    maxPl = pl > maxPl ? pl : maxPl;
-    int64_t rest = P - net.boff[jm - 1];
+    const int64_t rest = P - net.boff[jm - 1];
     maxRest = rest > maxRest ? rest : maxRest;
   }
-  // operand budget: A rows per chunk and bias units per F chunk
+  // operand budget: A rows per chunk and units per F chunk
   const double budget = (double)h->op_limit;
   int64_t arows_cap = (int64_t)(budget / (double)(ld * 4));
-  if (arows_cap < BM) arows_cap = BM;
   int64_t arows_max = 0;
   for (int jm = 1; jm < L; ++jm) {
     const int64_t Tin = net.T[jm - 1], Tout = net.T[jm];
-    int64_t tot = rows_before(Tout, Tin, Tout);
-    int64_t need = tot < arows_cap ? tot : (Tout * Tin > arows_cap ? Tout * Tin : arows_cap);
+    const int64_t tot = rows_before(Tout, Tin, Tout);
+    // at least one unit (the first is the largest: Tout * Tin rows)
+    const int64_t need = tot < arows_cap ? tot : (Tout * Tin > arows_cap ? Tout * Tin : arows_cap);
     arows_max = need > arows_max ? need : arows_max;
   }
   int pchunk = (int)(budget / (double)(ld * maxRest * 4));
-  if (pchunk > Tmax) pchunk = Tmax;
-  if (pchunk < 1) pchunk = 1;
+  pchunk = pchunk > Tmax ? Tmax : (pchunk < 1 ? 1 : pchunk);
   int64_t max_tiles = cdiv(arows_max, BM) * cdiv(Tinmax, 64);
   for (int jm = 1; jm < L; ++jm) {
     const int64_t rest = P - net.boff[jm - 1];
-    const int64_t t2 = cdiv(net.T[jm - 1], BM) * pchunk * cdiv(rest, pick_bn(rest));
+    const int64_t t2 = cdiv(net.T[jm - 1] + 1, BM) * pchunk * cdiv(rest, pick_bn(rest));
     max_tiles = t2 > max_tiles ? t2 : max_tiles;
   }
-  char* split = nullptr;
-  auto plan = [&](Arena& ar, float*& xs, float*& ys, Caches<float>& c, RopBufs<float>& r,
-                  float*& tmp, __nv_bfloat16*& bhi, __nv_bfloat16*& blo,
-                  __nv_bfloat16*& ahi, __nv_bfloat16*& alo, __nv_bfloat16*& fhi,
-                  __nv_bfloat16*& flo, float*& O,
-                  int4*& tl, Job*& jd, int*& err) {
-    xs = x_dev ? nullptr : ar.take<float>(N * T1);
-    ys = y_dev ? nullptr : ar.take<float>(N * TL);
+  cudaStream_t s = h->stream;
+  Staged d;
+  Caches<float> c;
+  RopBufs<float> r;
+  TQ tq;
+  bf *bhi, *blo, *ahi, *alo, *fhi, *flo;
+  int4* tl;
+  Job* jd;
+  int* err;
+  char* split;
+  auto plan = [&](Arena& ar, bool live) -> hess_status {
+    HM_TRY(stage(h, ar, live, X, Y, Hout, N, st, d));
     plan_caches(ar, net, N, c);
     plan_rop(ar, net, N, 1, Tmax, r);
-    tmp = ar.take<float>((int64_t)Tmax * maxPl);
-    bhi = ar.take<__nv_bfloat16>((int64_t)Tinmax * ld);
-    blo = ar.take<__nv_bfloat16>((int64_t)Tinmax * ld);
-    ahi = ar.take<__nv_bfloat16>(arows_max * ld);
-    alo = ar.take<__nv_bfloat16>(arows_max * ld);
-    fhi = ar.take<__nv_bfloat16>((int64_t)pchunk * maxRest * ld);
-    flo = ar.take<__nv_bfloat16>((int64_t)pchunk * maxRest * ld);
-    O = o_dev ? (float*)Hout : ar.take<float>(P * P);
+    plan_tq(ar, net, ld, Tmax, tq);
+    bhi = ar.take<bf>((int64_t)(Tinmax + 1) * ld);
+    blo = ar.take<bf>((int64_t)(Tinmax + 1) * ld);
+    ahi = ar.take<bf>(arows_max * ld);
+    alo = ar.take<bf>(arows_max * ld);
+    fhi = ar.take<bf>((int64_t)pchunk * maxRest * ld);
+    flo = ar.take<bf>((int64_t)pchunk * maxRest * ld);
     tl = ar.take<int4>(max_tiles);
     jd = ar.take<Job>(1);
     err = ar.take<int>(1);
     split = ar.take<char>(kSplitBytes);
+    return HESS_OK;
   };
   Arena ar;
-  float *xs, *ys, *tmp, *O;
-  __nv_bfloat16 *bhi, *blo, *ahi, *alo, *fhi, *flo;
-  int4* tl;
-  Job* jd;
-  int* err;
-  Caches<float> c;
-  RopBufs<float> r;
-  plan(ar, xs, ys, c, r, tmp, bhi, blo, ahi, alo, fhi, flo, O, tl, jd, err);
+  HM_TRY(plan(ar, false));
   HM_TRY(ensure_ws(h, ar.off));
   ar = Arena{h->ws, 0};
-  plan(ar, xs, ys, c, r, tmp, bhi, blo, ahi, alo, fhi, flo, O, tl, jd, err);
+  HM_TRY(plan(ar, true));
   SplitGuard sg(split, kSplitBytes, h->sm_count);
-  cudaStream_t s = h->stream;
-  const float* xd = (const float*)X;
-  const float* yd = (const float*)Y;
-  if (!x_dev) {
-    HM_CUDA(cudaMemcpyAsync(xs, X, N * T1 * 4, cudaMemcpyHostToDevice, s));
-    xd = xs;
-  }
-  if (!y_dev) {
-    HM_CUDA(cudaMemcpyAsync(ys, Y, N * TL * 4, cudaMemcpyHostToDevice, s));
-    yd = ys;
-  }
+  float* O = d.out;
   HM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
   const float* omega = h->omega32;
-  HM_TRY(forward_backward(net, omega, xd, yd, c, s));
+  HM_TRY(forward_backward(net, omega, d.X, d.Y, c, s));
+  HM_TRY(transpose_caches(net, c, N, ld, tq, s));
   std::vector<int4> tiles;
   for (int jm = 1; jm < L; ++jm) {
     const int Tin = net.T[jm - 1], Tout = net.T[jm];
-    const int64_t woff = net.woff[jm - 1], boff = net.boff[jm - 1];
+    const int64_t boff = net.boff[jm - 1], rest = P - boff;
     RopBufs<float> rb = r;
     rb.B = Tout;
     {
       Tick t(h, HESS_K_ROP, 0.0, 0.0);
       HM_TRY(rop_block(net, omega, c, jm, boff, Tout, rb, s));
     }
-    {
-      Tick t(h, HESS_K_HREST, 0.0, 0.0);
-      for (int jl = jm; jl < L; ++jl) HM_TRY(contract_layer(net, c, rb, jm, jl, boff, tmp, O, s));
-    }
-    // W x W block on the tensor cores
-    transpose_split_kernel<<<dim3((unsigned)cdiv(ld, 32), (unsigned)cdiv(Tin, 32)), dim3(32, 8), 0, s>>>(
-        c.a[jm - 1], N, Tin, Tin, bhi, blo, ld);
-    HM_LAUNCHED();
-    const int BN = pick_bn(Tin);
+    HM_TRY(transpose_rop(net, rb, jm, N, ld, tq, s));
+    HM_TRY(build_layer_b(net, c, jm, N, ld, bhi, blo, s));
+    // W x W block, a run of whole units at a time
     for (int p0 = 0; p0 < Tout;) {
       int p1 = p0 + 1;
       while (p1 < Tout && rows_before(p1 + 1, Tin, Tout) - rows_before(p0, Tin, Tout) <= arows_max) ++p1;
       const int64_t R0 = rows_before(p0, Tin, Tout);
-      const int64_t rows = rows_before(p1, Tin, Tout) - R0;
-      build_wrows_kernel<<<dim3((unsigned)cdiv(ld, 32), (unsigned)cdiv(Tin, 32), (unsigned)(p1 - p0)),
-                           dim3(32, 8), 0, s>>>(rb.rd[jm], c.a[jm - 1], N, Tin, Tout, p0, R0, ahi, alo, ld);
-      HM_LAUNCHED();
-      tiles.clear();
-      for (int64_t tm = 0; tm < cdiv(rows, BM); ++tm)
-        for (int64_t tn = 0; tn < cdiv(Tin, BN); ++tn) tiles.push_back(make_int4(0, (int)tm, (int)tn, 0));
+      HM_TRY(build_wrows(net, tq, jm, p1, R0, ld, h->sm_count, ahi, alo, s));
       Job job{};
-      TcOperands op{ahi, alo, rows, bhi, blo, Tin, ld};
-      HM_TRY(make_job(op, BN, &job));
-      job.M = rows;
-      job.Nn = Tin;
-      job.scale = 1.0f / (float)N;
-      job.out = O;
-      job.ldo = P;
-      job.mode = 1;
-      job.woff = woff;
-      job.Tin = Tin;
-      job.Tout = Tout;
-      job.p0 = p0;
-      job.R0 = R0;
+      HM_TRY(make_job(TcOperands{ahi, alo, rows_before(p1, Tin, Tout) - R0, bhi, blo, Tin, ld}, pick_bn(Tin),
+                      &job));
+      tiles.clear();
+      wrow_job(net, jm, p0, p1, R0, O, N, job, tiles, 0);
       {
-        // upper-triangle entries of this block's rows: 2N flops each
-        double ent = 0.0;
-        for (int u = p0; u < p1; ++u)
-          for (int q = 0; q < Tin; ++q)
-            ent += (double)(Tout - u) * Tin - q;
-        Tick t(h, HESS_K_HCONTRACT, 2.0 * N * ent, 0.0);
+        Tick t(h, HESS_K_HCONTRACT, wrow_flops(Tin, Tout, p0, p1, N), 0.0);
         HM_TRY(launch_jobs(h->sm_count, &job, 1, tiles.data(), (int)tiles.size(), jd, tl, x3, err, s));
       }
       p0 = p1;
     }
     // columns after W: the bias of this layer and every later layer
-    const int64_t rest = P - boff;
-    FArgs fa{};
-    fa.cols = rest;
-    fa.nseg = 0;
-    {
-      FSeg g{};
-      g.c0 = 0;
-      g.nW = 0;
-      g.Tin = Tin;
-      g.Tout = Tout;
-      g.rd = rb.rd[jm];
-      g.a = nullptr;
-      g.dlt = nullptr;
-      g.ra = nullptr;
-      fa.seg[fa.nseg++] = g;
-    }
-    for (int jl = jm + 1; jl < L; ++jl) {
-      if (fa.nseg >= MAXSEG) return set_error(HESS_ERR_UNSUPPORTED, "too many layers for the tensor-core Hessian");
-      FSeg g{};
-      g.c0 = net.woff[jl - 1] - boff;
-      g.nW = (int64_t)net.T[jl - 1] * net.T[jl];
-      g.Tin = net.T[jl - 1];
-      g.Tout = net.T[jl];
-      g.rd = rb.rd[jl];
-      g.a = c.a[jl - 1];
-      g.dlt = c.d[jl];
-      g.ra = rb.ra[jl - 1];
-      fa.seg[fa.nseg++] = g;
-    }
-    fa.B = Tout;
-    const int BN2 = pick_bn(rest);
-    const int ntn = (int)cdiv(rest, BN2);
+    FArgs fa;
+    HM_TRY(f_args(net, tq, jm, fa));
     for (int q0 = 0; q0 < Tout; q0 += pchunk) {
       const int pc = Tout - q0 < pchunk ? Tout - q0 : pchunk;
-      const int64_t total = (int64_t)pc * rest * ld;
-      build_f_bf16_kernel<<<(unsigned)(cdiv(total, 256) < 1048576 ? cdiv(total, 256) : 1048576), 256, 0,
-                            s>>>(fa, N, q0, pc, fhi, flo, ld);
-      HM_LAUNCHED();
-      tiles.clear();
-      for (int64_t tm = 0; tm < cdiv(Tin, BM); ++tm)
-        for (int u = 0; u < pc; ++u)
-          for (int tn = 0; tn < ntn; ++tn) tiles.push_back(make_int4(0, (int)tm, u * ntn + tn, 0));
+      HM_TRY(build_f(fa, q0, pc, ld, h->sm_count, fhi, flo, s));
       Job job{};
-      TcOperands op{bhi, blo, Tin, fhi, flo, (int64_t)pc * rest, ld};
-      HM_TRY(make_job(op, BN2, &job));
-      job.M = Tin;
-      job.Nn = rest;
-      job.scale = 1.0f / (float)N;
-      job.out = O;
-      job.ldo = P;
-      job.mode = 2;
-      job.woff = woff;
-      job.boff = boff;
-      job.Tin = Tin;
-      job.Tout = Tout;
-      job.p0 = q0;
-      job.ntn = ntn;
-      job.brow = rest;
+      HM_TRY(make_job(TcOperands{bhi, blo, Tin + 1, fhi, flo, (int64_t)pc * rest, ld}, pick_bn(rest), &job));
+      tiles.clear();
+      f_job(net, jm, q0, pc, O, N, job, tiles, 0);
       {
-        Tick t(h, HESS_K_HCONTRACT, 2.0 * N * (double)pc * Tin * rest, 0.0);
+        Tick t(h, HESS_K_HCONTRACT, f_flops(Tin, rest, pc, N), 0.0);
         HM_TRY(launch_jobs(h->sm_count, &job, 1, tiles.data(), (int)tiles.size(), jd, tl, x3, err, s));
       }
     }
   }
-  if (!o_dev) HM_CUDA(cudaMemcpyAsync(Hout, O, P * P * 4, cudaMemcpyDeviceToHost, s));
+  if (!st.o_dev) HM_CUDA(cudaMemcpyAsync(Hout, O, P * P * 4, cudaMemcpyDeviceToHost, s));
   return tc_check_err(s, h->host_pinned, err);
 }
-
 
 // OPG = G^T G / N with split-BF16 (or BF16) operands on the tensor cores.
 hess_status run_opg_tc(hess_mlp* h, const void* X, const void* Y, int64_t N, bool x3, void* Oout) {

@@ -116,3 +116,16 @@ def test_tc_mlp_784_16_10_sampled(hm, cfg784, prec):
     assert relerr(H[:, cols].cpu().numpy(), Href) <= TOL[prec]
     assert relerr(H[cols].cpu().numpy(), Href.T) <= TOL[prec]
     assert bool(torch.isfinite(H).all())
+
+
+@pytest.mark.parametrize("kind", ["opg", "exact_hessian"])
+def test_tc_host_buffers_match_device_buffers(hm, kind):
+    # host X, Y and output: the library stages them in its workspace
+    pb = make_problem([70, 33, 10], ["tanh"], 129, 7, "normal", "uniform")
+    net = hm.HessMLP(pb.widths, pb.acts, pb.omega)
+    Xh = np.ascontiguousarray(pb.X, dtype=np.float32)
+    Yh = np.ascontiguousarray(pb.Y, dtype=np.float32)
+    host = getattr(net, kind)(Xh, Yh, "bf16x3")
+    assert isinstance(host, np.ndarray)
+    devo = getattr(net, kind)(dev(pb.X), dev(pb.Y), "bf16x3").cpu().numpy()
+    assert np.array_equal(host, devo)
