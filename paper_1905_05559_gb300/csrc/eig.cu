@@ -85,13 +85,18 @@ __global__ void gram_acc_kernel(double* M, const double* DD, const double* AA, i
 
 // ------------------------------------------------ cooperative Lanczos
 // All Lanczos steps of one extension run in a single cooperative launch (all
-// blocks co-resident).  A step is four phases separated by grid barriers:
-//   A  beta_{j-1} = ||w||, q_j = w / beta, M q_j (= M w / beta) stored in MQ_j,
-//      first-pass coefficients h_i = (M q_i) . q_j for i < j and block
-//      partials of h_j = q_j . (M q_j)
-//   B  w' = M q_j - sum_{i<=j} h_i q_i
+// blocks co-resident).  Block b owns the entries [b E, (b + 1) E) of every
+// vector: it computes them, and keeps its rows of M and its slice of the
+// Lanczos vectors in shared memory when they fit.  A step is four phases
+// separated by grid barriers:
+//   A  beta_{j-1} = ||w||, q_j = w / beta (owned slice), M q_j on the owned
+//      rows (stored in MQ_j), first-pass coefficients h_i = (M q_i) . q_j for
+//      i < j (one warp each, over full rows) and block partials of
+//      h_j = q_j . (M q_j)
+//   B  w' = M q_j - sum_{i<=j} h_i q_i (owned slice)
 //   C  second-pass dot products d_i = q_i . w' (i <= j), as chunk partials
-//   D  alpha_j = h_j + d_j, w = w' - sum_{i<=j} d_i q_i, block partials of ||w||^2
+//   D  alpha_j = h_j + d_j, w = w' - sum_{i<=j} d_i q_i (owned slice), block
+//      partials of ||w||^2
 // (classical Gram-Schmidt applied twice against every earlier vector).  A
 // breakdown (||w|| ~ 0) restarts from a random vector orthogonalised against
 // the basis.  Barrier waits are bounded: on timeout the kernel raises *err
@@ -109,110 +114,125 @@ struct LzArgs {
   double* apart; // [gridDim] partial sums of q_j . (M q_j)
   double* alpha;
   double* beta;
-  unsigned* bar;  // [0]: published epoch, [1]: arrival counter
+  unsigned* bar;  // arrival counter (zero at launch)
   int* err;
   int m0, m1, mcap, nchunk;
+  int E;          // entries owned per block
+  int cache_m;    // the block's rows of M in shared memory
+  int cache_q;    // the block's slice of Q in shared memory
+  int cache_w;    // a copy of w in shared memory for the owned rows of M w
   uint64_t key;
 };
 
 constexpr long long BAR_TIMEOUT = 4000000000ll;
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Grid barrier: every block adds 1 to a monotonic arrival counter with a
-// release reduction; block 0 waits for epoch * gridDim.x arrivals and then
-// publishes the epoch, which the other blocks poll with acquire loads.  Each
-// block counts its own epochs (the counters start at zero for every launch).
+// Grid barrier: thread 0 of every block adds to one counter, block 0 adding
+// 2^31 - (gridDim.x - 1) and the others 1, so that the counter's top bit
+// flips exactly when the last block arrives; each block waits (bounded) for
+// the flip from the value it saw on arrival.  Fences on both sides publish
+// the block's writes and make the other blocks' writes visible.
 __device__ bool grid_barrier(const LzArgs& a, unsigned& epoch) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
     ++epoch;
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(a.bar + 1) : "memory");
+    const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
+    __threadfence();
+    const unsigned old = atomicAdd(a.bar, add);
     const long long t0 = clock64();
-    if (blockIdx.x == 0) {
-      const unsigned want = epoch * gridDim.x;
-      while (ld_acquire(a.bar + 1) < want) {
-        if (clock64() - t0 > BAR_TIMEOUT || *(volatile int*)a.err) {
-          atomicExch(a.err, 1);
-          ok = 0;
-          break;
-        }
-      }
-      if (ok) asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(a.bar), "r"(epoch) : "memory");
-    } else {
-      while (ld_acquire(a.bar) < epoch) {
-        if (clock64() - t0 > BAR_TIMEOUT || *(volatile int*)a.err) {
-          atomicExch(a.err, 1);
-          ok = 0;
-          break;
-        }
+    while (((old ^ *(volatile unsigned*)a.bar) & 0x80000000u) == 0u) {
+      if (clock64() - t0 > BAR_TIMEOUT || *(volatile int*)a.err) {
+        atomicExch(a.err, 1);
+        ok = 0;
+        break;
       }
     }
+    __threadfence();
   }
   __syncthreads();
   return ok != 0;
 }
 
-// sum_c x[c] y[c] over one warp, eight independent accumulators per lane so
-// that eight loads per lane are in flight
+// sum_c x[c] y[c] over one warp for c in [n0, n1); x in global memory, y in
+// shared or global memory; sixteen loads per lane in flight
 __device__ __forceinline__ double warp_dot(const double* x, const double* y, int64_t n0, int64_t n1) {
   const int lane = threadIdx.x & 31;
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int64_t c = n0 + lane;
-  for (; c + 7 * 32 < n1; c += 8 * 32) {
+  for (; c + 15 * 32 < n1; c += 16 * 32) {
+    double xv[16];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) acc[u] = fma(x[c + u * 32], y[c + u * 32], acc[u]);
+    for (int u = 0; u < 16; ++u) xv[u] = x[c + u * 32];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) acc[u & 7] = fma(xv[u], y[c + u * 32], acc[u & 7]);
   }
-  for (; c < n1; c += 32) acc[0] = fma(x[c], y[c], acc[0]);
+  for (; c + 3 * 32 < n1; c += 4 * 32) {
+    double xv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) xv[u] = x[c + u * 32];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] = fma(xv[u], y[c + u * 32], acc[u]);
+  }
+  for (; c < n1; c += 32) acc[4] = fma(x[c], y[c], acc[4]);
   const double s = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
   return warp_sum(s);
 }
 
-// For the 32-entry chunks starting at blockIdx.x * 32, step gridDim.x * 32:
-// out[n] = base[n] - sum_{i < nv} Q_i[n] coef[i].  The block's warps split the
-// i range (independent loads in flight), partial sums meet in shared memory.
-__device__ void subtract_combination(const double* Q, int64_t N, const double* coef, int nv,
-                                     const double* base, double* out, double* red, double* sqnorm) {
+// For the block's owned entries e < ne (global n0 + e):
+//   out[e] = base[e] - sum_{i < nv} coef[i] Q[i][e]
+// in 32-entry chunks: lanes along the entries, the block's warps split the i
+// range, partial sums meet in shared memory.  Q[i][e] comes from the block's
+// shared slice (stride E) or from global rows.  Writes out to shared memory
+// and to out_g[n0 + e]; returns (in warp 0) the sum of out[e]^2.
+__device__ double combine_slice(const LzArgs& a, const double* Qsh, const double* coef, int nv,
+                                const double* base, double* out, double* out_g, int64_t n0, int ne,
+                                double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   double nn = 0.0;
-  for (int64_t c0 = (int64_t)blockIdx.x * 32; c0 < N; c0 += (int64_t)gridDim.x * 32) {
-    const int64_t n = c0 + lane;
+  for (int c0 = 0; c0 < ne; c0 += 32) {
+    const int e = c0 + lane;
     double s0 = 0.0, s1 = 0.0;
-    if (n < N) {
-      int i = warp;
-      for (; i + nwarp < nv; i += 2 * nwarp) {
-        s0 = fma(Q[(int64_t)i * N + n], coef[i], s0);
-        s1 = fma(Q[(int64_t)(i + nwarp) * N + n], coef[i + nwarp], s1);
+    if (e < ne) {
+      if (a.cache_q) {
+        for (int i = warp; i < nv; i += nwarp) s0 = fma(Qsh[(int64_t)i * a.E + e], coef[i], s0);
+      } else {
+        const double* q = a.Q + n0 + e;
+        int i = warp;
+        for (; i + nwarp < nv; i += 2 * nwarp) {
+          s0 = fma(q[(int64_t)i * a.N], coef[i], s0);
+          s1 = fma(q[(int64_t)(i + nwarp) * a.N], coef[i + nwarp], s1);
+        }
+        if (i < nv) s0 = fma(q[(int64_t)i * a.N], coef[i], s0);
       }
-      if (i < nv) s0 = fma(Q[(int64_t)i * N + n], coef[i], s0);
     }
     red[warp * 32 + lane] = s0 + s1;
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 0 && e < ne) {
       double t = 0.0;
       for (int w = 0; w < nwarp; ++w) t += red[w * 32 + lane];
-      if (n < N) {
-        const double v = base[n] - t;
-        out[n] = v;
-        nn = fma(v, v, nn);
-      }
+      const double v = base[e] - t;
+      out[e] = v;
+      out_g[n0 + e] = v;
+      nn = fma(v, v, nn);
     }
     __syncthreads();
   }
-  if (sqnorm) *sqnorm = nn;  // meaningful in warp 0
+  return nn;
 }
 
-// sum_b npart[b] by warp 0 of the block (same order in every block)
+// sum_b part[b] by warp 0 of the block (same order in every block); every
+// lane issues its loads before adding
 __device__ double sum_partials(const double* part, int n, double* out_sh) {
   if (threadIdx.x < 32) {
-    double s = 0.0;
-    for (int b = threadIdx.x; b < n; b += 32) s += ((volatile const double*)part)[b];
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int b = threadIdx.x + 32 * u;
+      v[u] = b < n ? part[b] : 0.0;
+    }
+    double s = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+    for (int b = threadIdx.x + 256; b < n; b += 32) s += part[b];
     s = warp_sum(s);
     if (threadIdx.x == 0) *out_sh = s;
   }
@@ -221,20 +241,35 @@ __device__ double sum_partials(const double* part, int n, double* out_sh) {
 }
 
 __global__ void __launch_bounds__(512, 1) lanczos_coop_kernel(LzArgs a) {
-  extern __shared__ double d_sh[];  // second-pass coefficients d_0..d_j
+  extern __shared__ double dyn[];
   const int64_t N = a.N;
-  // work is dealt block-major (consecutive items go to different blocks) so
-  // that small N still spreads over every SM
-  const int64_t tI = (int64_t)threadIdx.x * gridDim.x + blockIdx.x;
-  const int64_t nT = (int64_t)gridDim.x * blockDim.x;
-  const int wI = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
-  const int nW = (int)(nT >> 5);
-  const int lane = threadIdx.x & 31;
+  const int E = a.E;
+  double* d_sh = dyn;                  // coefficients, mcap + 1
+  double* wsh_s = d_sh + (a.mcap + 1);                // full w, N (cache_w)
+  double* ysh = wsh_s + (a.cache_w ? N : 0);          // owned slice of M q_j, E
+  double* wps = ysh + E;               // owned slice of w', E
+  double* wsl = wps + E;               // owned slice of w, E
+  double* Msh = wsl + E;               // owned rows of M, E x N (cache_m)
+  double* Qsh = Msh + (a.cache_m ? (int64_t)E * N : 0);  // owned slice of Q, mcap x E (cache_q)
+  const int64_t n0 = (int64_t)blockIdx.x * E;
+  const int ne = (int)(N - n0 < E ? (N - n0 > 0 ? N - n0 : 0) : E);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  // warp-level tasks over the whole grid, dealt block-major and starting from
+  // each block's last warp (the first warps carry the owned rows)
+  const int wI = (nwarp - 1 - warp) * gridDim.x + blockIdx.x;
+  const int nW = nwarp * gridDim.x;
   const int64_t chunk = (N + a.nchunk - 1) / a.nchunk;
   __shared__ double s_tmp, s_scale;
   __shared__ double sh[32];
   __shared__ double red_sh[16 * 32];
   unsigned epoch = 0;  // meaningful in thread 0 only
+  if (a.cache_m)
+    for (int e = 0; e < ne; ++e)
+      for (int64_t n = threadIdx.x; n < N; n += blockDim.x) Msh[(int64_t)e * N + n] = a.M[(n0 + e) * N + n];
+  if (a.cache_q)
+    for (int i = warp; i < a.m0; i += nwarp)
+      for (int e = lane; e < ne; e += 32) Qsh[(int64_t)i * E + e] = a.Q[(int64_t)i * N + n0 + e];
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) wsl[e] = a.w[n0 + e];
   // running scale of T (max |alpha_i|, beta_i so far), kept per block
   if (threadIdx.x == 0) {
     double sc = 0.0;
@@ -245,88 +280,109 @@ __global__ void __launch_bounds__(512, 1) lanczos_coop_kernel(LzArgs a) {
   __syncthreads();
   for (int j = a.m0; j < a.m1; ++j) {
     // ---- A
+    // full w for the owned rows of M w (warps 1..) while warp 0 sums the
+    // norm partials
+    if (a.cache_w && warp > 0)
+      for (int64_t n = threadIdx.x - 32; n < N; n += blockDim.x - 32) wsh_s[n] = a.w[n];
     double bprev = sqrt(sum_partials(a.npart, gridDim.x, &s_tmp));
     const bool brk = j > 0 && (!(bprev > 1e-12 * s_scale) || s_scale == 0.0);
     if (brk) {
       // breakdown: a random direction orthogonal to q_0..q_{j-1}
-      if (tI == 0) a.beta[j - 1] = 0.0;
-      for (int64_t n = tI; n < N; n += nT) a.w[n] = rnd_sym(a.key, (uint64_t)j * 0x100000000ull + n);
+      if (blockIdx.x == 0 && threadIdx.x == 0) a.beta[j - 1] = 0.0;
+      for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+        wsl[e] = rnd_sym(a.key, (uint64_t)j * 0x100000000ull + (uint64_t)(n0 + e));
+        a.w[n0 + e] = wsl[e];
+      }
       if (!grid_barrier(a, epoch)) return;
       for (int pass = 0; pass < 2; ++pass) {
         for (int i = wI; i < j; i += nW) {
-          const double* qi = a.Q + (int64_t)i * N;
-          double sd = 0.0;
-          for (int64_t n = lane; n < N; n += 32) sd = fma(qi[n], a.w[n], sd);
-          sd = warp_sum(sd);
+          const double sd = warp_dot(a.Q + (int64_t)i * N, a.w, 0, N);
           if (lane == 0) a.h[i] = sd;
         }
         if (!grid_barrier(a, epoch)) return;
-        for (int64_t n = tI; n < N; n += nT) {
-          double sd = 0.0;
-          for (int i = 0; i < j; ++i) sd = fma(a.Q[(int64_t)i * N + n], ((volatile double*)a.h)[i], sd);
-          a.w[n] -= sd;
-        }
+        for (int i = threadIdx.x; i < j; i += blockDim.x) d_sh[i] = a.h[i];
+        __syncthreads();
+        combine_slice(a, Qsh, d_sh, j, wsl, wsl, a.w, n0, ne, red_sh);
         if (!grid_barrier(a, epoch)) return;
       }
       double sn = 0.0;
-      for (int64_t n = tI; n < N; n += nT) sn = fma(a.w[n], a.w[n], sn);
+      for (int e = threadIdx.x; e < ne; e += blockDim.x) sn = fma(wsl[e], wsl[e], sn);
       sn = block_sum(sn, sh);
       if (threadIdx.x == 0) a.npart[blockIdx.x] = sn;
       if (!grid_barrier(a, epoch)) return;
+      if (a.cache_w)
+        for (int64_t n = threadIdx.x; n < N; n += blockDim.x) wsh_s[n] = a.w[n];
       bprev = sqrt(sum_partials(a.npart, gridDim.x, &s_tmp));
-    } else if (j > 0 && tI == 0) {
+    } else if (j > 0 && blockIdx.x == 0 && threadIdx.x == 0) {
       a.beta[j - 1] = bprev;
     }
     __syncthreads();  // every thread has read s_scale
     if (threadIdx.x == 0 && j > 0 && !brk) s_scale = fmax(s_scale, bprev);
     const double inv = bprev > 0.0 ? 1.0 / bprev : 0.0;
-    double* qj = a.Q + (int64_t)j * N;
-    for (int64_t n = tI; n < N; n += nT) qj[n] = a.w[n] * inv;
+    // owned slice of q_j
+    const double* wsh = a.cache_w ? wsh_s : a.w;
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+      const double q = wsl[e] * inv;
+      a.Q[(int64_t)j * N + n0 + e] = q;
+      if (a.cache_q) Qsh[(int64_t)j * E + e] = q;
+    }
+    __syncthreads();
     double* mqj = a.MQ + (int64_t)j * N;
-    // M q_j (one warp per row) and h_i = (M q_i) . q_j (one warp per i < j)
-    double hj_part = 0.0;
-    for (int64_t task = wI; task < N + j; task += nW) {
-      const double* row = task < N ? a.M + task * N : a.MQ + (task - N) * N;
-      const double sr = warp_dot(row, a.w, 0, N) * inv;
+    for (int e = warp; e < ne; e += nwarp) {
+      const double* row = a.cache_m ? Msh + (int64_t)e * N : a.M + (n0 + e) * N;
+      double acc = 0.0;
+      if (a.cache_m) {
+        for (int64_t n = lane; n < N; n += 32) acc = fma(row[n], wsh[n], acc);
+        acc = warp_sum(acc);
+      } else {
+        acc = warp_dot(row, wsh, 0, N);
+      }
       if (lane == 0) {
-        if (task < N) {
-          mqj[task] = sr;
-          hj_part = fma(a.w[task] * inv, sr, hj_part);
-        } else {
-          a.h[task - N] = sr;
-        }
+        ysh[e] = acc * inv;
+        mqj[n0 + e] = acc * inv;
       }
     }
-    hj_part = block_sum(hj_part, sh);
-    if (threadIdx.x == 0) a.apart[blockIdx.x] = hj_part;
-    if (!grid_barrier(a, epoch)) return;
-    const double hj = sum_partials(a.apart, gridDim.x, &s_tmp);
-    // ---- B: w' = M q_j - sum_{i<=j} h_i q_i
-    if (threadIdx.x == 0) d_sh[j] = hj;
-    for (int i = threadIdx.x; i < j; i += blockDim.x) d_sh[i] = a.h[i];
+    for (int i = wI; i < j; i += nW) {
+      const double sr = warp_dot(a.MQ + (int64_t)i * N, wsh, 0, N) * inv;
+      if (lane == 0) a.h[i] = sr;
+    }
     __syncthreads();
-    subtract_combination(a.Q, N, d_sh, j + 1, mqj, a.wt, red_sh, nullptr);
+    if (warp == 0) {
+      double v = 0.0;
+      for (int e = lane; e < ne; e += 32) v = fma(wsl[e] * inv, ysh[e], v);
+      v = warp_sum(v);
+      if (lane == 0) a.apart[blockIdx.x] = v;
+    }
+    if (!grid_barrier(a, epoch)) return;
+    // ---- B: w' = M q_j - sum_{i<=j} h_i q_i on the owned slice (warps 1..
+    // fetch h_i while warp 0 sums the partials of h_j)
+    if (warp > 0)
+      for (int i = threadIdx.x - 32; i < j; i += blockDim.x - 32) d_sh[i] = a.h[i];
+    const double hj = sum_partials(a.apart, gridDim.x, &s_tmp);
+    if (threadIdx.x == 0) d_sh[j] = hj;
+    __syncthreads();
+    combine_slice(a, Qsh, d_sh, j + 1, ysh, wps, a.wt, n0, ne, red_sh);
     if (!grid_barrier(a, epoch)) return;
     // ---- C: partial dot products q_i . w' over chunks, one warp per (i, chunk)
     for (int task = wI; task < (j + 1) * a.nchunk; task += nW) {
       const int i = task / a.nchunk, ch = task % a.nchunk;
-      const int64_t n0 = ch * chunk, n1 = min(N, n0 + chunk);
-      const double sr = warp_dot(a.Q + (int64_t)i * N, a.wt, n0, n1);
+      const int64_t c0 = ch * chunk, c1 = min(N, c0 + chunk);
+      const double sr = warp_dot(a.Q + (int64_t)i * N, a.wt, c0, c1);
       if (lane == 0) a.dpart[(int64_t)i * a.nchunk + ch] = sr;
     }
     if (!grid_barrier(a, epoch)) return;
     // ---- D: w = w' - sum_{i<=j} d_i q_i, alpha_j = h_j + d_j
     for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-      double di = 0.0;
-      for (int ch = 0; ch < a.nchunk; ++ch) di += a.dpart[(int64_t)i * a.nchunk + ch];
-      d_sh[i] = di;
+      double v[8];  // nchunk <= 8
+#pragma unroll
+      for (int ch = 0; ch < 8; ++ch) v[ch] = ch < a.nchunk ? a.dpart[(int64_t)i * a.nchunk + ch] : 0.0;
+      d_sh[i] = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
     }
     __syncthreads();
-    double sn = 0.0;
-    subtract_combination(a.Q, N, d_sh, j + 1, a.wt, a.w, red_sh, &sn);
+    double sn = combine_slice(a, Qsh, d_sh, j + 1, wps, wsl, a.w, n0, ne, red_sh);
     sn = block_sum(threadIdx.x < 32 ? sn : 0.0, sh);
     if (threadIdx.x == 0) a.npart[blockIdx.x] = sn;
-    if (tI == 0) a.alpha[j] = hj + d_sh[j];
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.alpha[j] = hj + d_sh[j];
     if (threadIdx.x == 0) s_scale = fmax(s_scale, fabs(hj + d_sh[j]));
     if (!grid_barrier(a, epoch)) return;
   }
@@ -371,34 +427,43 @@ __global__ void clusters_kernel(const double* theta, int k, double rel, int* sta
 }
 
 // ----------------------------------------------------- tridiagonal eigen
-// Number of eigenvalues of T (diag a, off-diagonal b) below x (Sturm count).
-__device__ int sturm_count(const double* a, const double* b, int m, double x, double pivmin) {
+// Number of eigenvalues of T (diag a, squared off-diagonal b2) below x
+// (Sturm count).
+__device__ int sturm_count(const double* a, const double* b2, int m, double x, double pivmin) {
   int cnt = 0;
   double q = a[0] - x;
   if (fabs(q) < pivmin) q = -pivmin;
   if (q < 0) ++cnt;
+#pragma unroll 4
   for (int i = 1; i < m; ++i) {
-    q = (a[i] - x) - b[i - 1] * b[i - 1] * rcp64_sign(q);
+    q = (a[i] - x) - b2[i - 1] * rcp64_sign(q);
     if (fabs(q) < pivmin) q = -pivmin;
     if (q < 0) ++cnt;
   }
   return cnt;
 }
 
-// theta[c] = c-th largest eigenvalue of T_m, one warp per eigenvalue: each
-// iteration evaluates the Sturm count at 32 interior points (multisection),
-// shrinking the bracket 33-fold, until it is a few ulps wide.
+// theta[c] = c-th largest eigenvalue of T_m, one warp (one block) per
+// eigenvalue: each iteration evaluates the Sturm count at 32 interior points
+// (multisection), shrinking the bracket 33-fold, until it is a few ulps wide.
+// T is staged in shared memory (2 m doubles).
 __global__ void bisect_kernel(const double* a, const double* b, int m, int k, double* theta) {
-  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  extern __shared__ double tsh[];
+  double* sa = tsh;
+  double* sb2 = tsh + m;
+  const int c = blockIdx.x;
   const int lane = threadIdx.x & 31;
   if (c >= k) return;
   double lo = DBL_MAX, hi = -DBL_MAX, bmax2 = 0.0;
   for (int i = lane; i < m; i += 32) {
     const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < m - 1 ? fabs(b[i]) : 0.0);
+    sa[i] = a[i];
+    sb2[i] = i < m - 1 ? b[i] * b[i] : 0.0;
     lo = fmin(lo, a[i] - r);
     hi = fmax(hi, a[i] + r);
     if (i < m - 1) bmax2 = fmax(bmax2, b[i] * b[i]);
   }
+  __syncwarp();
   for (int o = 16; o > 0; o >>= 1) {
     lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
     hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
@@ -412,7 +477,7 @@ __global__ void bisect_kernel(const double* a, const double* b, int m, int k, do
   for (int it = 0; it < 64; ++it) {
     if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin) break;
     const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
-    const int cnt = sturm_count(a, b, m, x, pivmin);
+    const int cnt = sturm_count(sa, sb2, m, x, pivmin);
     const unsigned above = __ballot_sync(0xffffffffu, cnt > t);
     const int first = above ? __ffs(above) - 1 : 32;
     const double nhi = first < 32 ? __shfl_sync(0xffffffffu, x, first) : hi;
@@ -431,18 +496,20 @@ __global__ void bisect_kernel(const double* a, const double* b, int m, int k, do
 // iteration.  Thread 0 runs the O(m) recurrences.  Y: k rows of length ldy.
 // res[c] = |beta_m y_c[m-1]| bounds the residual of Ritz pair c.
 __global__ void inviter_kernel(const double* a, const double* b, int m, int k, const double* theta,
-                               const int* cstart, double* Y, int64_t ldy, double* scratch_all,
-                               const double* beta_last, double* res, uint64_t key) {
+                               const int* cstart, double* Y, int64_t ldy, const double* beta_last,
+                               double* res, uint64_t key) {
   const int c0 = blockIdx.x;
   if (cstart[c0] != c0) return;
   __shared__ double sh[32];
   __shared__ double sdot[1024];
-  double* scratch = scratch_all + (int64_t)c0 * 5 * (ldy + 1);
-  double* d = scratch;
-  double* du = scratch + m;
-  double* dl = scratch + 2 * m;
-  double* du2 = scratch + 3 * m;
-  int* piv = reinterpret_cast<int*>(scratch + 4 * m);
+  // the O(m) recurrences run on shared-memory copies (5 m doubles + m ints)
+  extern __shared__ double ish[];
+  double* d = ish;
+  double* du = ish + m;
+  double* dl = ish + 2 * m;
+  double* du2 = ish + 3 * m;
+  double* ys = ish + 4 * m;
+  int* piv = reinterpret_cast<int*>(ish + 5 * m);
   double tnorm = 0.0;
   for (int i = 0; i < m; ++i)
     tnorm = fmax(tnorm, fabs(a[i]) + (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < m - 1 ? fabs(b[i]) : 0.0));
@@ -451,7 +518,7 @@ __global__ void inviter_kernel(const double* a, const double* b, int m, int k, c
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   for (int c = c0; c < k && cstart[c] == c0; ++c) {
     const double th = theta[c];
-    double* y = Y + (int64_t)c * ldy;
+    double* y = ys;
     if (threadIdx.x == 0) {
       for (int i = 0; i < m; ++i) {
         d[i] = a[i] - th;
@@ -538,6 +605,7 @@ __global__ void inviter_kernel(const double* a, const double* b, int m, int k, c
       __syncthreads();
     }
     if (threadIdx.x == 0) res[c] = fabs(beta_m * y[m - 1]);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) Y[(int64_t)c * ldy + i] = y[i];
     __syncthreads();
   }
 }
@@ -630,7 +698,6 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   double* theta = ar.take<double>(k);
   double* Y = ar.take<double>((int64_t)k * mcap);
   double* U = ar.take<double>(N * k);
-  double* scratch = ar.take<double>((int64_t)k * 5 * (mcap + 1));
   unsigned* bar = ar.take<unsigned>(64);
   int* err = ar.take<int>(1);
   int* cstart = ar.take<int>(k);
@@ -675,13 +742,38 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   // 2-3. Lanczos with full reorthogonalisation, extended until the top-k
   // residual bounds converge
   const uint64_t key = 0x5DEECE66Dull;
+  // ownership: E entries per block over at most one block per SM; shared
+  // memory holds the coefficients and the owned slices, then, as far as they
+  // fit, w, the owned rows of M and the owned slice of Q
+  const int64_t E = cdiv(N, h->sm_count);
+  const int grid = (int)cdiv(N, E);
+  const size_t cap = (size_t)208 << 10;
+  size_t dyn = ((size_t)(mcap + 1) + 3 * (size_t)E) * sizeof(double);
+  int cache_w = 0, cache_m = 0, cache_q = 0;
+  if (dyn + (size_t)N * 8 <= cap) {
+    cache_w = 1;
+    dyn += (size_t)N * 8;
+  }
+  if (cache_w && dyn + (size_t)E * N * 8 <= cap) {
+    cache_m = 1;
+    dyn += (size_t)E * N * 8;
+  }
+  if (dyn + (size_t)mcap * E * 8 <= cap) {
+    cache_q = 1;
+    dyn += (size_t)mcap * E * 8;
+  }
+  if (dyn > cap) return set_error(HESS_ERR_UNSUPPORTED, "Lanczos workspace exceeds shared memory (N = %lld)",
+                                  (long long)N);
   int per_sm = 0;
-  const size_t dyn = (size_t)(mcap + 1) * sizeof(double);
-  if (dyn > 48 * 1024)
-    HM_CUDA(cudaFuncSetAttribute(lanczos_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+  HM_CUDA(cudaFuncSetAttribute(lanczos_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
   HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lanczos_coop_kernel, 512, dyn));
-  if (per_sm < 1) return set_error(HESS_ERR_CUDA, "Lanczos kernel cannot be resident");
-  const int grid = h->sm_count;
+  if (per_sm < 1 || grid > per_sm * h->sm_count) return set_error(HESS_ERR_CUDA, "Lanczos kernel cannot be resident");
+  const size_t inv_smem = (size_t)6 * mcap * sizeof(double);
+  if (inv_smem > 48 * 1024)
+    HM_CUDA(cudaFuncSetAttribute(inviter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem));
+  if ((size_t)2 * mcap * sizeof(double) > 48 * 1024)
+    HM_CUDA(cudaFuncSetAttribute(bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(2 * mcap * sizeof(double))));
   init_start_kernel<<<1, 1024, 0, s>>>(w, npart, grid, N, key);
   HM_LAUNCHED();
   HM_CUDA(cudaMemsetAsync(bar, 0, 64 * sizeof(unsigned), s));
@@ -713,6 +805,10 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
     la.m1 = (int)target;
     la.mcap = (int)mcap;
     la.nchunk = nchunk < 1 ? 1 : nchunk;
+    la.E = (int)E;
+    la.cache_m = cache_m;
+    la.cache_q = cache_q;
+    la.cache_w = cache_w;
     la.key = key + 7;
     void* kargs[] = {&la};
     HM_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
@@ -721,12 +817,14 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
     m = (int)target;
     last_beta_kernel<<<1, 32, 0, s>>>(npart, grid, h2);
     HM_LAUNCHED();
-    bisect_kernel<<<(unsigned)cdiv(k, 4), 128, 0, s>>>(alpha, beta, m, k, theta);
+    // one warp per block: the FP64 Sturm recurrences of different eigenvalues
+    // then run on different SMs
+    bisect_kernel<<<(unsigned)k, 32, (size_t)2 * m * sizeof(double), s>>>(alpha, beta, m, k, theta);
     HM_LAUNCHED();
     // eigenvalues closer than 1e-6 of the largest share a cluster
     clusters_kernel<<<1, 32, 0, s>>>(theta, k, 1e-6, cstart);
     HM_LAUNCHED();
-    inviter_kernel<<<k, 256, 0, s>>>(alpha, beta, m, k, theta, cstart, Y, mcap, scratch, h2, rr,
+    inviter_kernel<<<k, 256, inv_smem, s>>>(alpha, beta, m, k, theta, cstart, Y, mcap, h2, rr,
                                      key + 11);
     HM_LAUNCHED();
     max_res_kernel<<<1, 32, 0, s>>>(rr, k, theta, mx);

@@ -222,9 +222,13 @@ static hess_status gemm_cfg(const Gemm<T>& g, cudaStream_t s) {
   // partials are summed in slice order by a second kernel)
   int splits = 1;
   const int sms = g_split.sms > 0 ? g_split.sms : 148;
-  if (!g.upper && g_split.p && tiles * g.batch < 2 * sms && g.K >= 256) {
+  // (FP64 runs at a small fraction of the FP32 rate, so FP64 products split
+  // down to slices of 32)
+  const int64_t kmin = std::is_same<T, double>::value ? 64 : 256;
+  const int64_t kslice = std::is_same<T, double>::value ? 32 : 128;
+  if (!g.upper && g_split.p && tiles * g.batch < 2 * sms && g.K >= kmin) {
     int64_t want = cdiv(2 * sms, tiles * g.batch);
-    int64_t maxs = g.K / 128;
+    int64_t maxs = g.K / kslice;
     int64_t cap = (int64_t)(g_split.bytes / ((size_t)g.M * g.N * g.batch * sizeof(T)));
     int64_t sp = want < maxs ? want : maxs;
     sp = sp < cap ? sp : cap;
