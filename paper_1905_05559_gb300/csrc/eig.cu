@@ -47,14 +47,16 @@ __device__ __forceinline__ double rcp64(double x) {
   return fma(r, e, r);
 }
 
-// 1/x to about 2^-46 relative (one Newton-Raphson step): enough for the
-// inertia counts of the Sturm sequence, which tolerate relative perturbations
-// of this size.
-__device__ __forceinline__ double rcp64_sign(double x) {
+// 1/sqrt(x) for x > 0: the hardware estimate refined by two Newton-Raphson
+// steps r <- r (3 - x r^2) / 2.  On this GPU an FP64 operation has a long
+// dependent latency, and this chain is shorter than a square root followed
+// by a division.
+__device__ __forceinline__ double rsqrt64(double x) {
   double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  const double e = fma(-x, r, 1.0);
-  return fma(r, e, r);
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  const double hx = 0.5 * x;
+  r = r * fma(-hx * r, r, 1.5);
+  return r * fma(-hx * r, r, 1.5);
 }
 
 // sum over a block of up to 1024 threads
@@ -97,10 +99,10 @@ __global__ void gram_acc_kernel(double* M, const double* DD, const double* AA, i
 //   C  second-pass dot products d_i = q_i . w' (i <= j), as chunk partials
 //   D  alpha_j = h_j + d_j, w = w' - sum_{i<=j} d_i q_i (owned slice), block
 //      partials of ||w||^2
-// (classical Gram-Schmidt applied twice against every earlier vector).  A
-// breakdown (||w|| ~ 0) restarts from a random vector orthogonalised against
-// the basis.  Barrier waits are bounded: on timeout the kernel raises *err
-// and returns.
+// (classical Gram-Schmidt applied twice against every earlier vector).  At a
+// breakdown (||w|| ~ 0) the kernel stops; restart_* below draw a random vector
+// orthogonal to the basis and the next launch resumes.  Barrier waits are
+// bounded: on timeout the kernel raises *err and returns.
 struct LzArgs {
   const double* M;
   int64_t N;
@@ -121,6 +123,8 @@ struct LzArgs {
   int cache_m;    // the block's rows of M in shared memory
   int cache_q;    // the block's slice of Q in shared memory
   int cache_w;    // a copy of w in shared memory for the owned rows of M w
+  int* stop;      // set to j when step j meets a breakdown (the kernel returns)
+  int resumed;    // m0 follows a restart: beta_{m0-1} = 0 is already set
   uint64_t key;
 };
 
@@ -207,10 +211,14 @@ __device__ double combine_slice(const LzArgs& a, const double* Qsh, const double
       }
     }
     red[warp * 32 + lane] = s0 + s1;
+    // pairwise tree over the warps' partial sums (nwarp is a power of two)
+    for (int half = nwarp >> 1; half > 0; half >>= 1) {
+      __syncthreads();
+      if (warp < half) red[warp * 32 + lane] += red[(warp + half) * 32 + lane];
+    }
     __syncthreads();
     if (warp == 0 && e < ne) {
-      double t = 0.0;
-      for (int w = 0; w < nwarp; ++w) t += red[w * 32 + lane];
+      const double t = red[lane];
       const double v = base[e] - t;
       out[e] = v;
       out_g[n0 + e] = v;
@@ -259,8 +267,8 @@ __global__ void __launch_bounds__(512, 1) lanczos_coop_kernel(LzArgs a) {
   const int wI = (nwarp - 1 - warp) * gridDim.x + blockIdx.x;
   const int nW = nwarp * gridDim.x;
   const int64_t chunk = (N + a.nchunk - 1) / a.nchunk;
-  __shared__ double s_tmp, s_scale;
-  __shared__ double sh[32];
+  __shared__ double s_tmp, s_scale, s_rs, s_b;
+  __shared__ int s_brk;
   __shared__ double red_sh[16 * 32];
   unsigned epoch = 0;  // meaningful in thread 0 only
   if (a.cache_m)
@@ -284,41 +292,30 @@ __global__ void __launch_bounds__(512, 1) lanczos_coop_kernel(LzArgs a) {
     // norm partials
     if (a.cache_w && warp > 0)
       for (int64_t n = threadIdx.x - 32; n < N; n += blockDim.x - 32) wsh_s[n] = a.w[n];
-    double bprev = sqrt(sum_partials(a.npart, gridDim.x, &s_tmp));
-    const bool brk = j > 0 && (!(bprev > 1e-12 * s_scale) || s_scale == 0.0);
-    if (brk) {
-      // breakdown: a random direction orthogonal to q_0..q_{j-1}
-      if (blockIdx.x == 0 && threadIdx.x == 0) a.beta[j - 1] = 0.0;
-      for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-        wsl[e] = rnd_sym(a.key, (uint64_t)j * 0x100000000ull + (uint64_t)(n0 + e));
-        a.w[n0 + e] = wsl[e];
-      }
-      if (!grid_barrier(a, epoch)) return;
-      for (int pass = 0; pass < 2; ++pass) {
-        for (int i = wI; i < j; i += nW) {
-          const double sd = warp_dot(a.Q + (int64_t)i * N, a.w, 0, N);
-          if (lane == 0) a.h[i] = sd;
-        }
-        if (!grid_barrier(a, epoch)) return;
-        for (int i = threadIdx.x; i < j; i += blockDim.x) d_sh[i] = a.h[i];
-        __syncthreads();
-        combine_slice(a, Qsh, d_sh, j, wsl, wsl, a.w, n0, ne, red_sh);
-        if (!grid_barrier(a, epoch)) return;
-      }
-      double sn = 0.0;
-      for (int e = threadIdx.x; e < ne; e += blockDim.x) sn = fma(wsl[e], wsl[e], sn);
-      sn = block_sum(sn, sh);
-      if (threadIdx.x == 0) a.npart[blockIdx.x] = sn;
-      if (!grid_barrier(a, epoch)) return;
-      if (a.cache_w)
-        for (int64_t n = threadIdx.x; n < N; n += blockDim.x) wsh_s[n] = a.w[n];
-      bprev = sqrt(sum_partials(a.npart, gridDim.x, &s_tmp));
-    } else if (j > 0 && blockIdx.x == 0 && threadIdx.x == 0) {
-      a.beta[j - 1] = bprev;
+    // An FP64 instruction occupies its SM partition for many cycles per
+    // warp, so block-wide scalars are computed once, by thread 0, and read
+    // from shared memory by the others.
+    double nsum = sum_partials(a.npart, gridDim.x, &s_tmp);
+    if (threadIdx.x == 0) {
+      const double r = nsum > 0.0 ? rsqrt64(nsum) : 0.0;  // 1 / ||w||
+      s_rs = r;
+      s_b = nsum * r;
+      s_brk = j > 0 && !(a.resumed && j == a.m0) && (!(nsum * r > 1e-12 * s_scale) || s_scale == 0.0);
     }
-    __syncthreads();  // every thread has read s_scale
-    if (threadIdx.x == 0 && j > 0 && !brk) s_scale = fmax(s_scale, bprev);
-    const double inv = bprev > 0.0 ? 1.0 / bprev : 0.0;
+    __syncthreads();
+    // breakdown (||w|| ~ 0): stop here; the host draws a new direction
+    // orthogonal to q_0..q_{j-1} and resumes at step j.  (Kept out of the
+    // loop: code on this path slows every step.)
+    if (s_brk) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) *a.stop = j;
+      return;
+    }
+    const double rs = s_rs;
+    const double bprev = s_b;
+    if (j > 0 && !(a.resumed && j == a.m0) && blockIdx.x == 0 && threadIdx.x == 0) a.beta[j - 1] = bprev;
+    __syncthreads();  // every thread has read s_rs, s_b
+    if (threadIdx.x == 0 && j > 0 && !(a.resumed && j == a.m0)) s_scale = fmax(s_scale, bprev);
+    const double inv = rs;  // 0 when ||w|| = 0
     // owned slice of q_j
     const double* wsh = a.cache_w ? wsh_s : a.w;
     for (int e = threadIdx.x; e < ne; e += blockDim.x) {
@@ -332,8 +329,14 @@ __global__ void __launch_bounds__(512, 1) lanczos_coop_kernel(LzArgs a) {
       const double* row = a.cache_m ? Msh + (int64_t)e * N : a.M + (n0 + e) * N;
       double acc = 0.0;
       if (a.cache_m) {
-        for (int64_t n = lane; n < N; n += 32) acc = fma(row[n], wsh[n], acc);
-        acc = warp_sum(acc);
+        double c4[4] = {0.0, 0.0, 0.0, 0.0};
+        int64_t n = lane;
+        for (; n + 96 < N; n += 128) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) c4[u] = fma(row[n + 32 * u], wsh[n + 32 * u], c4[u]);
+        }
+        for (; n < N; n += 32) c4[0] = fma(row[n], wsh[n], c4[0]);
+        acc = warp_sum((c4[0] + c4[1]) + (c4[2] + c4[3]));
       } else {
         acc = warp_dot(row, wsh, 0, N);
       }
@@ -380,10 +383,15 @@ __global__ void __launch_bounds__(512, 1) lanczos_coop_kernel(LzArgs a) {
     }
     __syncthreads();
     double sn = combine_slice(a, Qsh, d_sh, j + 1, wps, wsl, a.w, n0, ne, red_sh);
-    sn = block_sum(threadIdx.x < 32 ? sn : 0.0, sh);
-    if (threadIdx.x == 0) a.npart[blockIdx.x] = sn;
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.alpha[j] = hj + d_sh[j];
-    if (threadIdx.x == 0) s_scale = fmax(s_scale, fabs(hj + d_sh[j]));
+    if (warp == 0) {
+      sn = warp_sum(sn);  // the slice's sum of squares lives in warp 0
+      if (lane == 0) {
+        a.npart[blockIdx.x] = sn;
+        const double al = hj + d_sh[j];
+        if (blockIdx.x == 0) a.alpha[j] = al;
+        s_scale = fmax(s_scale, fabs(al));
+      }
+    }
     if (!grid_barrier(a, epoch)) return;
   }
 }
@@ -402,6 +410,43 @@ __global__ void init_start_kernel(double* w, double* npart, int nparts, int64_t 
   double inv = 1.0 / sqrt(s);
   for (int64_t n = threadIdx.x; n < N; n += blockDim.x) w[n] *= inv;
   for (int b = threadIdx.x; b < nparts; b += blockDim.x) npart[b] = b == 0 ? 1.0 : 0.0;
+}
+
+// Restart after a breakdown at step j: w = a random vector (the same
+// counter-based draw on every run), beta_{j-1} = 0.
+__global__ void restart_fill_kernel(double* w, int64_t N, uint64_t key, int j, double* beta) {
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
+    w[n] = rnd_sym(key, (uint64_t)j * 0x100000000ull + (uint64_t)n);
+  if (blockIdx.x == 0 && threadIdx.x == 0) beta[j - 1] = 0.0;
+}
+
+// c_i = q_i . w for i < j, one warp per i
+__global__ void restart_coef_kernel(const double* Q, const double* w, int64_t N, int j, double* c) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= j) return;
+  double s = 0.0;
+  for (int64_t n = lane; n < N; n += 32) s = fma(Q[(int64_t)i * N + n], w[n], s);
+  s = warp_sum(s);
+  if (lane == 0) c[i] = s;
+}
+
+// w -= sum_{i<j} c_i q_i
+__global__ void restart_sub_kernel(const double* Q, const double* c, int64_t N, int j, double* w) {
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int i = 0; i < j; ++i) s = fma(Q[(int64_t)i * N + n], c[i], s);
+    w[n] -= s;
+  }
+}
+
+// npart = (||w||^2, 0, 0, ...) for the resumed launch
+__global__ void restart_norm_kernel(const double* w, int64_t N, double* npart, int nparts) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int64_t n = threadIdx.x; n < N; n += blockDim.x) s = fma(w[n], w[n], s);
+  s = block_sum(s, sh);
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) npart[b] = b == 0 ? s : 0.0;
 }
 
 // beta of the last completed step (the coupling of T_m to the next vector)
@@ -427,66 +472,182 @@ __global__ void clusters_kernel(const double* theta, int k, double rel, int* sta
 }
 
 // ----------------------------------------------------- tridiagonal eigen
-// Number of eigenvalues of T (diag a, squared off-diagonal b2) below x
-// (Sturm count).
-__device__ int sturm_count(const double* a, const double* b2, int m, double x, double pivmin) {
+// Number of eigenvalues of T below x (Sturm count) from the signs of the
+// leading principal minors p_i = det(T_i - x I):
+//   p_0 = 1,  p_1 = a_0 - x,  p_{i+1} = (a_i - x) p_i - b_{i-1}^2 p_{i-1},
+// the count being the number of sign changes along p_0 .. p_m (Sturm
+// sequence property).  The recurrence needs no division: its dependent
+// chain is one FMA per step (b^2 p_{i-1} is ready a step early), which
+// matters where an FP64 operation waits tens of cycles for its inputs.
+// Every 8 steps the pair (p_i, p_{i-1}) is rescaled by a power of two (exact,
+// signs unchanged); a and b2 arrive scaled so that ||T|| <= 1.  A minor that
+// comes out exactly zero is replaced by a tiny value of the opposite sign of
+// its predecessor (it counts as one change).
+__device__ int sturm_count(const double* a, const double* b2, int m, double x) {
+  double pm1 = 1.0;
+  double p = a[0] - x;
   int cnt = 0;
-  double q = a[0] - x;
-  if (fabs(q) < pivmin) q = -pivmin;
-  if (q < 0) ++cnt;
-#pragma unroll 4
+  unsigned long long sprev = 0ull;  // sign bit of p_0
+  auto step_sign = [&](double& v) {
+    unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    if ((bits & 0x7fffffffffffffffull) == 0ull) {
+      bits = 0x0010000000000000ull | ((sprev ^ 1ull) << 63);  // +-DBL_MIN
+      v = __longlong_as_double((long long)bits);
+    }
+    const unsigned long long sb = bits >> 63;
+    cnt += (int)(sb ^ sprev);
+    sprev = sb;
+  };
+  step_sign(p);
+#pragma unroll 8
   for (int i = 1; i < m; ++i) {
-    q = (a[i] - x) - b2[i - 1] * rcp64_sign(q);
-    if (fabs(q) < pivmin) q = -pivmin;
-    if (q < 0) ++cnt;
+    const double t = b2[i - 1] * pm1;
+    double pn = fma(a[i] - x, p, -t);
+    step_sign(pn);
+    pm1 = p;
+    p = pn;
+    if ((i & 7) == 0) {
+      const int ep = (int)(((unsigned long long)__double_as_longlong(p) >> 52) & 0x7ff);
+      const int eq = (int)(((unsigned long long)__double_as_longlong(pm1) >> 52) & 0x7ff);
+      const int e = ep > eq ? ep : eq;
+      if (e > 1023 + 256 || e < 1023 - 256) {
+        const double sc = __longlong_as_double((long long)(2046 - e) << 52);  // 2^(1023 - e)
+        p *= sc;
+        pm1 *= sc;
+      }
+    }
   }
   return cnt;
 }
 
-// theta[c] = c-th largest eigenvalue of T_m, one warp (one block) per
-// eigenvalue: each iteration evaluates the Sturm count at 32 interior points
-// (multisection), shrinking the bracket 33-fold, until it is a few ulps wide.
-// T is staged in shared memory (2 m doubles).
+// The same count in FP32 (rescaled every 4 steps), for coarse brackets.
+__device__ int sturm_count_f32(const float* a, const float* b2, int m, float x) {
+  float pm1 = 1.0f;
+  float p = a[0] - x;
+  int cnt = 0;
+  unsigned sprev = 0u;
+  auto step_sign = [&](float& v) {
+    unsigned bits = __float_as_uint(v);
+    if ((bits & 0x7fffffffu) == 0u) {
+      bits = 0x00800000u | ((sprev ^ 1u) << 31);  // +-FLT_MIN
+      v = __uint_as_float(bits);
+    }
+    const unsigned sb = bits >> 31;
+    cnt += (int)(sb ^ sprev);
+    sprev = sb;
+  };
+  step_sign(p);
+#pragma unroll 4
+  for (int i = 1; i < m; ++i) {
+    const float t = b2[i - 1] * pm1;
+    float pn = fmaf(a[i] - x, p, -t);
+    step_sign(pn);
+    pm1 = p;
+    p = pn;
+    if ((i & 3) == 0) {
+      const int ep = (int)((__float_as_uint(p) >> 23) & 0xff);
+      const int eq = (int)((__float_as_uint(pm1) >> 23) & 0xff);
+      const int e = ep > eq ? ep : eq;
+      if (e > 127 + 40 || e < 127 - 40) {
+        const float sc = __uint_as_float((unsigned)(254 - e) << 23);  // 2^(127 - e)
+        p *= sc;
+        pm1 *= sc;
+      }
+    }
+  }
+  return cnt;
+}
+
+// Smallest thread index of the block whose predicate holds (blockDim.x if
+// none); every thread gets the answer.
+__device__ int block_first(bool pred, int* s4) {
+  const unsigned bal = __ballot_sync(0xffffffffu, pred);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) s4[warp] = bal ? warp * 32 + __ffs(bal) - 1 : (int)blockDim.x;
+  __syncthreads();
+  int f = (int)blockDim.x;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) f = min(f, s4[w]);
+  __syncthreads();
+  return f;
+}
+
+// theta[c] = c-th largest eigenvalue of T_m, one block of 128 threads per
+// eigenvalue (one warp per SM partition): each sweep evaluates the Sturm
+// count at 128 interior points of the bracket (multisection), shrinking it
+// 129-fold.  T is staged in shared memory, scaled by a power of two so that
+// ||T|| <= 1.  Two coarse sweeps run in FP32; their bracket is widened by
+// 4e-6 (well above the FP32 backward error of the count, a few float ulps of
+// ||T||) before the FP64 sweeps take it down to a few ulps.
 __global__ void bisect_kernel(const double* a, const double* b, int m, int k, double* theta) {
   extern __shared__ double tsh[];
   double* sa = tsh;
   double* sb2 = tsh + m;
+  float* fa = reinterpret_cast<float*>(tsh + 2 * m);
+  float* fb2 = fa + m;
+  __shared__ double s_lo, s_hi, s_sc;
+  __shared__ int s4[32];
   const int c = blockIdx.x;
-  const int lane = threadIdx.x & 31;
+  const int tid = threadIdx.x, nt = blockDim.x;
   if (c >= k) return;
-  double lo = DBL_MAX, hi = -DBL_MAX, bmax2 = 0.0;
-  for (int i = lane; i < m; i += 32) {
-    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < m - 1 ? fabs(b[i]) : 0.0);
-    sa[i] = a[i];
-    sb2[i] = i < m - 1 ? b[i] * b[i] : 0.0;
-    lo = fmin(lo, a[i] - r);
-    hi = fmax(hi, a[i] + r);
-    if (i < m - 1) bmax2 = fmax(bmax2, b[i] * b[i]);
+  if (tid < 32) {
+    double lo = DBL_MAX, hi = -DBL_MAX;
+    for (int i = tid; i < m; i += 32) {
+      const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < m - 1 ? fabs(b[i]) : 0.0);
+      lo = fmin(lo, a[i] - r);
+      hi = fmax(hi, a[i] + r);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (tid == 0) {
+      const double tnorm = fmax(fabs(lo), fabs(hi));
+      int E = 0;
+      if (tnorm > 0.0) frexp(tnorm, &E);
+      const double sc = ldexp(1.0, -E);  // 2^-E with 2^E >= tnorm: exact
+      s_sc = sc;
+      s_lo = lo * sc - (2.0 * DBL_EPSILON + 4.0 * DBL_MIN);
+      s_hi = hi * sc + (2.0 * DBL_EPSILON + 4.0 * DBL_MIN);
+    }
   }
-  __syncwarp();
-  for (int o = 16; o > 0; o >>= 1) {
-    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-    bmax2 = fmax(bmax2, __shfl_xor_sync(0xffffffffu, bmax2, o));
+  __syncthreads();
+  const double sc = s_sc;
+  for (int i = tid; i < m; i += nt) {
+    const double ai = a[i] * sc;
+    const double bi = i < m - 1 ? b[i] * sc : 0.0;
+    sa[i] = ai;
+    sb2[i] = bi * bi;
+    fa[i] = (float)ai;
+    fb2[i] = (float)(bi * bi);
   }
-  const double tnorm = fmax(fabs(lo), fabs(hi));
-  const double pivmin = DBL_MIN * fmax(1.0, bmax2);
-  lo -= 2.0 * DBL_EPSILON * tnorm + pivmin;
-  hi += 2.0 * DBL_EPSILON * tnorm + pivmin;
+  __syncthreads();
   const int t = m - 1 - c;  // index from the smallest
+  double lo = s_lo, hi = s_hi;
+  const double lo0 = lo, hi0 = hi;
+  const double inv_n = 1.0 / (double)(nt + 1);
+  // coarse FP32 sweeps
+  for (int it = 0; it < 2; ++it) {
+    const float xf = (float)(lo + (hi - lo) * (double)(tid + 1) * inv_n);
+    const int f = block_first(sturm_count_f32(fa, fb2, m, xf) > t, s4);
+    const double nhi = f < nt ? lo + (hi - lo) * (double)(f + 1) * inv_n : hi;
+    const double nlo = f > 0 ? lo + (hi - lo) * (double)f * inv_n : lo;
+    lo = nlo;
+    hi = nhi;
+  }
+  lo = fmax(lo0, lo - 4e-6);
+  hi = fmin(hi0, hi + 4e-6);
+  const double tiny = 4.0 * DBL_MIN;
   for (int it = 0; it < 64; ++it) {
-    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin) break;
-    const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
-    const int cnt = sturm_count(sa, sb2, m, x, pivmin);
-    const unsigned above = __ballot_sync(0xffffffffu, cnt > t);
-    const int first = above ? __ffs(above) - 1 : 32;
-    const double nhi = first < 32 ? __shfl_sync(0xffffffffu, x, first) : hi;
-    const double nlo = first > 0 ? __shfl_sync(0xffffffffu, x, first - 1) : lo;
+    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + tiny) break;
+    const double x = lo + (hi - lo) * (double)(tid + 1) * inv_n;
+    const int f = block_first(sturm_count(sa, sb2, m, x) > t, s4);
+    const double nhi = f < nt ? lo + (hi - lo) * (double)(f + 1) * inv_n : hi;
+    const double nlo = f > 0 ? lo + (hi - lo) * (double)f * inv_n : lo;
     if (!(nlo < nhi)) break;
     lo = nlo;
     hi = nhi;
   }
-  if (lane == 0) theta[c] = 0.5 * (lo + hi);
+  if (tid == 0) theta[c] = 0.5 * (lo + hi) / sc;
 }
 
 // Eigenvectors of T_m for theta[0..k-1] by inverse iteration with a
@@ -510,12 +671,20 @@ __global__ void inviter_kernel(const double* a, const double* b, int m, int k, c
   double* du2 = ish + 3 * m;
   double* ys = ish + 4 * m;
   int* piv = reinterpret_cast<int*>(ish + 5 * m);
-  double tnorm = 0.0;
-  for (int i = 0; i < m; ++i)
-    tnorm = fmax(tnorm, fabs(a[i]) + (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < m - 1 ? fabs(b[i]) : 0.0));
-  const double tiny = DBL_EPSILON * fmax(tnorm, DBL_MIN);
-  const double beta_m = *beta_last;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  // block-wide FP64 scalars are computed by one warp (an FP64 instruction
+  // occupies its SM partition for many cycles) and shared
+  __shared__ double s_tiny, s_inv;
+  if (warp == 0) {
+    double tn = 0.0;
+    for (int i = lane; i < m; i += 32)
+      tn = fmax(tn, fabs(a[i]) + (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < m - 1 ? fabs(b[i]) : 0.0));
+    for (int o = 16; o > 0; o >>= 1) tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
+    if (lane == 0) s_tiny = DBL_EPSILON * fmax(tn, DBL_MIN);
+  }
+  __syncthreads();
+  const double tiny = s_tiny;
+  const double beta_m = *beta_last;
   for (int c = c0; c < k && cstart[c] == c0; ++c) {
     const double th = theta[c];
     double* y = ys;
@@ -554,7 +723,9 @@ __global__ void inviter_kernel(const double* a, const double* b, int m, int k, c
     }
     for (int i = threadIdx.x; i < m; i += blockDim.x) y[i] = 1.0 + 0.25 * rnd_sym(key + c, i);
     __syncthreads();
-    for (int it = 0; it < 3; ++it) {
+    // two solves: with a shift accurate to a few ulps the first leaves an
+    // error of about eps ||T|| / gap, the second removes it
+    for (int it = 0; it < 2; ++it) {
       if (threadIdx.x == 0) {
         for (int i = 0; i < m - 1; ++i) {
           if (piv[i]) {
@@ -600,7 +771,9 @@ __global__ void inviter_kernel(const double* a, const double* b, int m, int k, c
       double nn = 0.0;
       for (int i = threadIdx.x; i < m; i += blockDim.x) nn = fma(y[i], y[i], nn);
       nn = block_sum(nn, sh);
-      const double inv2 = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+      if (threadIdx.x == 0) s_inv = nn > 0.0 ? rsqrt64(nn) : 0.0;
+      __syncthreads();
+      const double inv2 = s_inv;
       for (int i = threadIdx.x; i < m; i += blockDim.x) y[i] *= inv2;
       __syncthreads();
     }
@@ -704,6 +877,7 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   double* rr = ar.take<double>(k);
   double* mx = ar.take<double>(2);
   int* flag = ar.take<int>(2);
+  int* stop = ar.take<int>(1);
   if (dry) return HESS_OK;
   cudaStream_t s = h->stream;
 
@@ -771,9 +945,9 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   const size_t inv_smem = (size_t)6 * mcap * sizeof(double);
   if (inv_smem > 48 * 1024)
     HM_CUDA(cudaFuncSetAttribute(inviter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem));
-  if ((size_t)2 * mcap * sizeof(double) > 48 * 1024)
+  if ((size_t)3 * mcap * sizeof(double) > 48 * 1024)
     HM_CUDA(cudaFuncSetAttribute(bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(2 * mcap * sizeof(double))));
+                                 (int)(3 * mcap * sizeof(double))));
   init_start_kernel<<<1, 1024, 0, s>>>(w, npart, grid, N, key);
   HM_LAUNCHED();
   HM_CUDA(cudaMemsetAsync(bar, 0, 64 * sizeof(unsigned), s));
@@ -785,6 +959,7 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   if (target > mcap) target = mcap;
   bool converged = false;
   double* hp = h->host_pinned;
+  int resumed = 0;
   while (true) {
     LzArgs la;
     la.M = M;
@@ -809,17 +984,20 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
     la.cache_m = cache_m;
     la.cache_q = cache_q;
     la.cache_w = cache_w;
+    la.stop = stop;
+    la.resumed = resumed;
     la.key = key + 7;
     void* kargs[] = {&la};
     HM_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
+    HM_CUDA(cudaMemsetAsync(stop, 0xff, sizeof(int), s));
     HM_CUDA(cudaLaunchCooperativeKernel((void*)lanczos_coop_kernel, grid, 512, kargs, dyn, s));
     HM_LAUNCHED();
     m = (int)target;
     last_beta_kernel<<<1, 32, 0, s>>>(npart, grid, h2);
     HM_LAUNCHED();
-    // one warp per block: the FP64 Sturm recurrences of different eigenvalues
-    // then run on different SMs
-    bisect_kernel<<<(unsigned)k, 32, (size_t)2 * m * sizeof(double), s>>>(alpha, beta, m, k, theta);
+    // one block per eigenvalue: the FP64 Sturm recurrences of different
+    // eigenvalues run on different SMs
+    bisect_kernel<<<(unsigned)k, 128, (size_t)3 * m * sizeof(double), s>>>(alpha, beta, m, k, theta);
     HM_LAUNCHED();
     // eigenvalues closer than 1e-6 of the largest share a cluster
     clusters_kernel<<<1, 32, 0, s>>>(theta, k, 1e-6, cstart);
@@ -831,9 +1009,31 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
     HM_LAUNCHED();
     HM_CUDA(cudaMemcpyAsync(hp, mx, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaMemcpyAsync(reinterpret_cast<int*>(hp + 2), err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaMemcpyAsync(reinterpret_cast<int*>(hp + 2) + 1, stop, sizeof(int), cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaStreamSynchronize(s));
     if (*reinterpret_cast<int*>(hp + 2))
       return set_error(HESS_ERR_TIMEOUT, "Lanczos grid barrier gave up");
+    const int stopped = reinterpret_cast<int*>(hp + 2)[1];
+    resumed = 0;
+    if (stopped >= 0) {
+      // breakdown at step `stopped` (the eigen pass above saw an incomplete
+      // T and is discarded): a random vector orthogonalised twice against
+      // q_0..q_{stopped-1}, then resume there
+      m = stopped;
+      const unsigned gb = (unsigned)(cdiv(N, 256) < 4096 ? cdiv(N, 256) : 4096);
+      restart_fill_kernel<<<gb, 256, 0, s>>>(w, N, key + 7, m, beta);
+      HM_LAUNCHED();
+      for (int pass = 0; pass < 2; ++pass) {
+        restart_coef_kernel<<<(unsigned)cdiv(m, 8), 256, 0, s>>>(Q, w, N, m, h1);
+        HM_LAUNCHED();
+        restart_sub_kernel<<<gb, 256, 0, s>>>(Q, h1, N, m, w);
+        HM_LAUNCHED();
+      }
+      restart_norm_kernel<<<1, 1024, 0, s>>>(w, N, npart, grid);
+      HM_LAUNCHED();
+      resumed = 1;
+      continue;
+    }
     if (hp[0] <= 1e-10 * hp[1] || m >= N) {
       converged = true;
       break;
