@@ -41,7 +41,10 @@
  * Errors:    every entry point returns a hess_status; nothing aborts or
  *            throws.  Arguments are checked before any work is queued.
  *            hess_last_error() gives a message for the calling thread's most
- *            recent failure.
+ *            recent failure.  The tensor-core kernels bound every pipeline
+ *            wait; one that gives up sets a flag on the handle that the call
+ *            reports as HESS_ERR_TIMEOUT when it waits for its work, and
+ *            otherwise the next call on the handle reports.
  * Threads:   a handle must not be used by two threads at once.
  */
 #ifndef HESSMLP_H

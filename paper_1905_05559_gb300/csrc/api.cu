@@ -84,6 +84,68 @@ hess_status make_net(const hess_mlp_desc* desc, Net* out) {
 
 thread_local size_t* g_dry_bytes = nullptr;
 
+hess_status host_side_init(hess_mlp* h) {
+  if (cudaMallocHost(&h->host_pinned, 4096) != cudaSuccess) return set_error(HESS_ERR_OOM, "pinned scratch");
+  if (cudaHostAlloc(&h->err_host, 64, cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer(&h->err_dev, h->err_host, 0) != cudaSuccess)
+    return set_error(HESS_ERR_OOM, "mapped error flag");
+  *h->err_host = 0;
+  return HESS_OK;
+}
+
+void host_side_free(hess_mlp* h) {
+  if (h->host_pinned) cudaFreeHost(h->host_pinned);
+  if (h->err_host) cudaFreeHost(h->err_host);
+  h->host_pinned = nullptr;
+  h->err_host = h->err_dev = nullptr;
+  stage_free(h->stage);
+}
+
+hess_status take_sticky_error(hess_mlp* h) {
+  if (h->err_host && *(volatile int*)h->err_host) {
+    *(volatile int*)h->err_host = 0;
+    return set_error(HESS_ERR_TIMEOUT,
+                     "a tensor-core pipeline wait gave up (in this or an earlier call on the handle)");
+  }
+  return HESS_OK;
+}
+
+hess_status stage_copy(PinnedStage& st, const void* const* src, const size_t* bytes, void* const* dst, int n,
+                       cudaStream_t s) {
+  size_t total = 0;
+  for (int i = 0; i < n; ++i) total += align_up(bytes[i], 256);
+  if (st.ev) {
+    HM_CUDA(cudaEventSynchronize(st.ev));  // the previous copy has left the buffer
+  } else {
+    HM_CUDA(cudaEventCreateWithFlags(&st.ev, cudaEventDisableTiming));
+  }
+  if (total > st.cap) {
+    if (st.p) cudaFreeHost(st.p);
+    st.p = nullptr;
+    st.cap = 0;
+    const size_t want = total > ((size_t)64 << 10) ? total : ((size_t)64 << 10);
+    HM_CUDA(cudaHostAlloc(&st.p, want, cudaHostAllocDefault));
+    st.cap = want;
+  }
+  size_t off = 0;
+  for (int i = 0; i < n; ++i) {
+    memcpy(st.p + off, src[i], bytes[i]);
+    HM_CUDA(cudaMemcpyAsync(dst[i], st.p + off, bytes[i], cudaMemcpyHostToDevice, s));
+    off += align_up(bytes[i], 256);
+  }
+  HM_CUDA(cudaEventRecord(st.ev, s));
+  return HESS_OK;
+}
+
+void stage_free(PinnedStage& st) {
+  if (st.ev) {
+    cudaEventSynchronize(st.ev);
+    cudaEventDestroy(st.ev);
+  }
+  if (st.p) cudaFreeHost(st.p);
+  st = PinnedStage{};
+}
+
 hess_status ensure_ws(hess_mlp* h, size_t bytes) {
   if (g_dry_bytes) {
     *g_dry_bytes = bytes;
@@ -138,7 +200,7 @@ hess_status check_common(hess_mlp* h, const void* X, const void* Y, int64_t N, h
     return set_error(HESS_ERR_INVALID_ARG, "N must be < 2^31 (got %lld)", (long long)N);
   if (prec < HESS_FP64 || prec > HESS_BF16X3)
     return set_error(HESS_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
-  return HESS_OK;
+  return take_sticky_error(h);
 }
 
 // An input buffer: device pointer used as is, host pointer staged.
@@ -477,7 +539,7 @@ hess_status hess_mlp_create(const hess_mlp_desc* desc, const double* omega, void
   hess_status st = HESS_OK;
   if (cudaMalloc(&h->omega64, net.P * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&h->omega32, net.P * sizeof(float)) != cudaSuccess ||
-      cudaMallocHost(&h->host_pinned, 4096) != cudaSuccess) {
+      host_side_init(h) != HESS_OK) {
     cudaGetLastError();
     st = set_error(HESS_ERR_OOM, "cannot allocate parameters");
   }
@@ -499,7 +561,7 @@ hess_status hess_mlp_destroy(hess_mlp* h) {
     cudaFree(h->omega32);
   }
   cudaFree(h->ws);
-  if (h->host_pinned) cudaFreeHost(h->host_pinned);
+  host_side_free(h);
   for (auto& r : h->pending) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);

@@ -21,7 +21,9 @@ struct hess_batch {
   cudaStream_t stream = nullptr;
   char* ws = nullptr;
   size_t ws_bytes = 0;
-  double* host_pinned = nullptr;
+  int* err_host = nullptr;  // mapped pinned error flag of the tensor-core kernels
+  int* err_dev = nullptr;
+  hm::PinnedStage stage;
   std::vector<cudaEvent_t> events;  // pairs bracketing the wave launches
 };
 
@@ -79,6 +81,9 @@ hess_status run_alone(hess_batch* b, const hess_batch_item& it, hess_precision p
   hess_status st = HESS_OK;
   if (it.opg) st = opg(h, it.X, it.Y, it.N, prec, it.opg);
   if (st == HESS_OK && it.hessian) st = exact_hessian(h, it.X, it.Y, it.N, prec, it.hessian);
+  if (st == HESS_OK && cudaStreamSynchronize(b->stream) != cudaSuccess)
+    st = set_error(HESS_ERR_CUDA, "batch stream: %s", cudaGetErrorString(cudaGetLastError()));
+  if (st == HESS_OK) st = take_sticky_error(h);
   h->stream = keep;
   return st;
 }
@@ -106,13 +111,16 @@ hess_status hess_batch_create(int64_t workspace_bytes, void* stream, hess_batch*
   }
   cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device);
   if (cudaMalloc(&b->ws, (size_t)workspace_bytes) != cudaSuccess ||
-      cudaMallocHost(&b->host_pinned, 64) != cudaSuccess) {
+      cudaHostAlloc(&b->err_host, 64, cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer(&b->err_dev, b->err_host, 0) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(b->ws);
+    if (b->err_host) cudaFreeHost(b->err_host);
     delete b;
     return set_error(HESS_ERR_OOM, "cannot allocate a %lld-byte batch workspace", (long long)workspace_bytes);
   }
   b->ws_bytes = (size_t)workspace_bytes;
+  *b->err_host = 0;
   *out = b;
   return HESS_OK;
 }
@@ -131,12 +139,10 @@ hess_status hess_batch_run(hess_batch* b, const hess_batch_item* items, int coun
     HM_TRY(tc_available(items[0].net));
     const bool x3 = prec == HESS_BF16X3;
     cudaStream_t s = b->stream;
-    // fixed head of the workspace: error flag and split-K scratch
+    // fixed head of the workspace: split-K scratch
     Arena head{b->ws, 0};
-    int* err = head.take<int>(1);
     char* split = head.take<char>(kSplitBytes);
     const size_t base = align_up(head.off, 256);
-    HM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     SplitGuard sg(split, kSplitBytes, b->sm_count);
     int i = 0;
     while (i < count) {
@@ -176,14 +182,18 @@ hess_status hess_batch_run(hess_batch* b, const hess_batch_item* items, int coun
         b->events.push_back(e);
       }
       HM_CUDA(cudaEventRecord(b->events[e0], s));
-      HM_TRY(tc_launch_plan(b->sm_count, plan, ar, true, x3, err, s));
+      HM_TRY(tc_launch_plan(b->sm_count, plan, ar, true, x3, b->err_dev, b->stage, s));
       HM_CUDA(cudaEventRecord(b->events[e0 + 1], s));
       inf.tiles += (int64_t)plan.tiles.size();
       inf.flops += (plan.syrk_flops + plan.hess_flops) * (x3 ? 3.0 : 1.0);
       ++inf.waves;
       i = j;
     }
-    HM_TRY(tc_check_err(s, b->host_pinned, err));
+    HM_CUDA(cudaStreamSynchronize(s));
+    if (*(volatile int*)b->err_host) {
+      *(volatile int*)b->err_host = 0;
+      return set_error(HESS_ERR_TIMEOUT, "a tensor-core pipeline wait gave up");
+    }
     for (int w = 0; w < inf.waves; ++w) {
       float ms = 0.f;
       HM_CUDA(cudaEventElapsedTime(&ms, b->events[2 * w], b->events[2 * w + 1]));
@@ -200,7 +210,8 @@ hess_status hess_batch_destroy(hess_batch* b) {
   cudaStreamSynchronize(b->stream);
   for (cudaEvent_t e : b->events) cudaEventDestroy(e);
   cudaFree(b->ws);
-  cudaFreeHost(b->host_pinned);
+  cudaFreeHost(b->err_host);
+  stage_free(b->stage);
   delete b;
   return HESS_OK;
 }

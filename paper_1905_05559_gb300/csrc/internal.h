@@ -97,6 +97,17 @@ struct TimingRec {
 };
 }  // namespace hm
 
+namespace hm {
+// Pinned host staging for the small tables a launch reads (jobs, tiles), so
+// that their copies are asynchronous.  The buffer is reused once its previous
+// copy has completed (event).
+struct PinnedStage {
+  char* p = nullptr;
+  size_t cap = 0;
+  cudaEvent_t ev = nullptr;
+};
+}  // namespace hm
+
 struct hess_mlp {
   hm::Net net;
   bool owns_params = true;  // false: omega64/omega32 borrowed from another handle
@@ -111,6 +122,11 @@ struct hess_mlp {
   char* ws = nullptr;         // device workspace
   size_t ws_bytes = 0;
   double* host_pinned = nullptr;  // small pinned scratch for scalars
+  // sticky error flag in mapped pinned memory: kernels set it when a bounded
+  // pipeline wait gives up; calls report it without synchronising
+  int* err_host = nullptr;
+  int* err_dev = nullptr;
+  hm::PinnedStage stage;
   int sm_count = 0;
   // operand bytes above which the tensor-core Hessian is built and contracted
   // in chunks (one launch per chunk) instead of in one launch
@@ -120,6 +136,17 @@ struct hess_mlp {
 namespace hm {
 
 hess_status ensure_ws(hess_mlp* h, size_t bytes);
+
+// Host-side resources of a handle (pinned scratch, mapped error flag).
+hess_status host_side_init(hess_mlp* h);
+void host_side_free(hess_mlp* h);
+// HESS_ERR_TIMEOUT (and clears the flag) if a kernel of an earlier call on
+// the handle gave up a pipeline wait.
+hess_status take_sticky_error(hess_mlp* h);
+// Copies n host tables through the pinned stage to device memory on s.
+hess_status stage_copy(PinnedStage& st, const void* const* src, const size_t* bytes, void* const* dst, int n,
+                       cudaStream_t s);
+void stage_free(PinnedStage& st);
 
 // Planning without work: while a dry run is active on this thread, ensure_ws
 // records the workspace a call needs and makes the call return kDryRun before
@@ -308,8 +335,6 @@ hess_status tc_prep(hess_mlp* h, const TcItem& it, Arena& ar, bool live, TcPlan&
 // Takes arena memory for the plan's job and tile tables; when live, copies
 // them there and starts one persistent launch over all tiles (longest first).
 hess_status tc_launch_plan(int sm_count, const TcPlan& plan, Arena& ar, bool live, bool x3, int* err,
-                           cudaStream_t s);
-// Reads the kernels' error flag (synchronises the stream).
-hess_status tc_check_err(cudaStream_t s, double* host_scratch, int* err_d);
+                           PinnedStage& stage, cudaStream_t s);
 
 }  // namespace hm

@@ -98,6 +98,7 @@ void worker_loop(hess_server* sv, Slot* sl) {
     if (st == HESS_OK || st == HESS_ERR_RANK_DEFICIENT) {
       cudaError_t e = cudaStreamSynchronize(sl->stream);
       if (e != cudaSuccess) st = set_error(HESS_ERR_CUDA, "request stream: %s", cudaGetErrorString(e));
+      else if (take_sticky_error(h) != HESS_OK) st = HESS_ERR_TIMEOUT;
     }
     const char* msg = hess_last_error();
     lk.lock();
@@ -240,8 +241,9 @@ hess_status hess_server_add_network(hess_server* sv, const hess_mlp_desc* desc, 
     v->omega64 = master->omega64;
     v->omega32 = master->omega32;
     v->owns_params = false;
-    if (cudaMallocHost(&v->host_pinned, 4096) != cudaSuccess) {
+    if (host_side_init(v) != HESS_OK) {
       cudaGetLastError();
+      host_side_free(v);
       delete v;
       return set_error(HESS_ERR_OOM, "pinned scratch");
     }

@@ -37,7 +37,10 @@ constexpr int B_BYTES = MAXBN * BK * 2;
 constexpr int RING_BYTES = 4 * (A_BYTES + B_BYTES);
 constexpr int MAXSTAGES = 4;
 constexpr int EPI_LD = 17;  // 16 columns + 1 pad
-constexpr int EPI_BYTES = 4 * 32 * EPI_LD * 4;
+// per epilogue warp: a 32 x 16 transpose tile, then the 32 rows' output row
+// and column base (int64 each)
+constexpr int EPI_WARP_BYTES = 32 * EPI_LD * 4 + 32 * 16;
+constexpr int EPI_BYTES = 4 * EPI_WARP_BYTES;
 constexpr int BAR_BYTES = 256;
 constexpr int SMEM_BYTES = 1024 + RING_BYTES + EPI_BYTES + BAR_BYTES;
 constexpr int THREADS = 192;
@@ -92,7 +95,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* er
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
     if (clock64() - t0 > TIMEOUT_CYCLES) {
-      atomicExch(err, 1);
+      *(volatile int*)err = 1;  // mapped host memory: read by the host without a sync
       *abort_flag = 1;
       return false;
     }
@@ -155,6 +158,26 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
       : "memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Two 16-column loads and one wait (the wait covers both).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%32];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, "
+      "%27, %28, %29, %30, %31}, [%33];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr), "r"(taddr + 16)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
@@ -285,10 +308,17 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
           last_job = tile.x;
         }
-        const uint32_t tx_bytes = (A_BYTES + jb.BN * BK * 2) * (x3 ? 2 : 1);
-        const int brow0 = jb.mode == 2 ? (int)((tile.z / jb.ntn) * jb.brow + (tile.z % jb.ntn) * jb.BN)
-                                       : tile.z * jb.BN;
-        for (int j = 0; j < jb.nkb; ++j, ++it) {
+        // job fields in registers: the asm statements below clobber memory,
+        // which would make every use of jb.* a fresh global load
+        const int jbn = jb.BN, jnkb = jb.nkb;
+        const uint32_t tx_bytes = (A_BYTES + jbn * BK * 2) * (x3 ? 2 : 1);
+        const int brow0 = jb.mode == 2 ? (int)((tile.z / jb.ntn) * jb.brow + (tile.z % jb.ntn) * jbn)
+                                       : tile.z * jbn;
+        const CUtensorMap* m_ahi = &jb.a_hi;
+        const CUtensorMap* m_alo = &jb.a_lo;
+        const CUtensorMap* m_bhi = &jb.b_hi;
+        const CUtensorMap* m_blo = &jb.b_lo;
+        for (int j = 0; j < jnkb; ++j, ++it) {
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1;
           if (!mbar_wait(empty(s), ph ^ 1, L.err, abort_flag)) {
@@ -297,11 +327,11 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
           uint8_t* st = smem + s * STAGE_BYTES;
           mbar_expect_tx(full(s), tx_bytes);
-          tma_load_2d(smem_u32(st), &jb.a_hi, j * BK, tile.y * BM, full(s));
-          tma_load_2d(smem_u32(st + OFF_BHI), &jb.b_hi, j * BK, brow0, full(s));
+          tma_load_2d(smem_u32(st), m_ahi, j * BK, tile.y * BM, full(s));
+          tma_load_2d(smem_u32(st + OFF_BHI), m_bhi, j * BK, brow0, full(s));
           if (x3) {
-            tma_load_2d(smem_u32(st + OFF_ALO), &jb.a_lo, j * BK, tile.y * BM, full(s));
-            tma_load_2d(smem_u32(st + OFF_BLO), &jb.b_lo, j * BK, brow0, full(s));
+            tma_load_2d(smem_u32(st + OFF_ALO), m_alo, j * BK, tile.y * BM, full(s));
+            tma_load_2d(smem_u32(st + OFF_BLO), m_blo, j * BK, brow0, full(s));
           }
         }
       }
@@ -324,6 +354,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int t = blockIdx.x; t < L.ntiles && ok; t += gridDim.x, ++tcount) {
         const Job& jb = L.jobs[L.tiles[t].x];
         const int nvk = jb.nkb;
+        const uint32_t idesc = jb.idesc;
         const int nchunk = (nvk + CHUNK_KB - 1) / CHUNK_KB;
         // the first chunk goes to the tile's main buffer, the others to the
         // second buffer, which the epilogue merges into the main one
@@ -351,14 +382,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             const uint64_t bh = sdesc(smem_u32(st + OFF_BHI));
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk)
-              umma_bf16(d_tmem, ah + 2 * kk, bh + 2 * kk, jb.idesc, (j > j0 || kk > 0) ? 1u : 0u);
+              umma_bf16(d_tmem, ah + 2 * kk, bh + 2 * kk, idesc, (j > j0 || kk > 0) ? 1u : 0u);
             if (x3) {
               const uint64_t al = sdesc(smem_u32(st + OFF_ALO));
               const uint64_t bl = sdesc(smem_u32(st + OFF_BLO));
 #pragma unroll
-              for (int kk = 0; kk < BK / 16; ++kk) umma_bf16(d_tmem, ah + 2 * kk, bl + 2 * kk, jb.idesc, 1u);
+              for (int kk = 0; kk < BK / 16; ++kk) umma_bf16(d_tmem, ah + 2 * kk, bl + 2 * kk, idesc, 1u);
 #pragma unroll
-              for (int kk = 0; kk < BK / 16; ++kk) umma_bf16(d_tmem, al + 2 * kk, bh + 2 * kk, jb.idesc, 1u);
+              for (int kk = 0; kk < BK / 16; ++kk) umma_bf16(d_tmem, al + 2 * kk, bh + 2 * kk, idesc, 1u);
             }
             umma_commit(empty(s));
           }
@@ -369,7 +400,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     __syncwarp();
   } else {
     const int q = warp & 3;  // TMEM lane quadrant of this warp
-    float* e = epi + (warp - 2) * 32 * EPI_LD;
+    float* e = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(epi) + (warp - 2) * EPI_WARP_BYTES);
+    int64_t* srow = reinterpret_cast<int64_t*>(e + 32 * EPI_LD);  // [32] output row (-1: invalid)
+    int64_t* scol = srow + 32;                                     // [32] output column base
     int tcount = 0;
     unsigned fulls[2] = {0u, 0u};  // chunk results consumed from each TMEM buffer
     const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
@@ -377,6 +410,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int t = blockIdx.x; t < L.ntiles && alive; t += gridDim.x, ++tcount) {
       const int4 tile = L.tiles[t];
       const Job& p = L.jobs[tile.x];
+      // job fields in registers (see the producer)
+      const int BN = p.BN;
+      const int64_t pM = p.M, Nn = p.Nn, ldo = p.ldo;
+      const float scale = p.scale;
+      float* const out = p.out;
       const int nchunk = (p.nkb + CHUNK_KB - 1) / CHUNK_KB;
       const int acc = tcount & 1;
       const bool got = mbar_wait(tfull(acc), fulls[acc] & 1u, L.err, abort_flag);
@@ -395,7 +433,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         tc_fence_after();
         const uint32_t pm = tmem_base + acc * MAXBN + lane_off;
         const uint32_t pp = tmem_base + part * MAXBN + lane_off;
-        for (int c = 0; c < p.BN / 16; ++c) {
+        for (int c = 0; c < BN / 16; ++c) {
           float vm[16], vp[16];
           tmem_ld16(pp + c * 16, vp);
           tmem_ld16(pm + c * 16, vm);
@@ -408,45 +446,54 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       if (!alive) break;
       const int64_t m = (int64_t)tile.y * BM + q * 32 + lane;
-      const bool rvalid = m < p.M;
+      const bool rvalid = m < pM;
       int64_t orow = 0, ocolb = 0;
       if (rvalid) row_map(p, m, tile.z, orow, ocolb);
-      const int64_t nbase = p.mode == 2 ? (int64_t)(tile.z % p.ntn) * p.BN : (int64_t)tile.z * p.BN;
+      const int64_t nbase = p.mode == 2 ? (int64_t)(tile.z % p.ntn) * BN : (int64_t)tile.z * BN;
+      srow[lane] = rvalid ? orow : -1;
+      scol[lane] = ocolb;
       __syncwarp();
       const uint32_t tbase = tmem_base + acc * MAXBN + (static_cast<uint32_t>(q * 32) << 16);
-      for (int c = 0; c < p.BN / 16; ++c) {
-        float v[16];
-        tmem_ld16(tbase + c * 16, v);
-        const int64_t n0 = nbase + c * 16;
-        // mirror image: for a fixed column, the warp's 32 rows are adjacent
+      // 16 columns of the tile: the mirror image (for a fixed column the
+      // warp's 32 rows are adjacent), then the direct entries transposed
+      // through shared memory so that each half warp writes 16 adjacent
+      // columns of one row
+      auto emit16 = [&](const float* v, int64_t n0) {
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) {
           const int64_t n = n0 + jj;
-          const float val = v[jj] * p.scale;
+          const float val = v[jj] * scale;
           e[lane * EPI_LD + jj] = val;
-          if (rvalid && n < p.Nn) {
+          if (rvalid && n < Nn) {
             const int64_t ocol = ocolb + n;
-            if (ocol > orow) p.out[ocol * p.ldo + orow] = val;
+            if (ocol > orow) out[ocol * ldo + orow] = val;
           }
         }
         __syncwarp();
-        // direct entries: transpose through shared memory so that each half
-        // warp writes 16 adjacent columns of one row
+        const int jj = lane & 15;
+        const int64_t n = n0 + jj;
 #pragma unroll 4
         for (int r = 0; r < 16; ++r) {
           const int i = (lane >> 4) + 2 * r;
-          const int jj = lane & 15;
-          const float val = e[i * EPI_LD + jj];
-          const int64_t orow_i = __shfl_sync(0xffffffffu, orow, i);
-          const int64_t ocolb_i = __shfl_sync(0xffffffffu, ocolb, i);
-          const int valid_i = __shfl_sync(0xffffffffu, rvalid ? 1 : 0, i);
-          const int64_t n = n0 + jj;
-          if (valid_i && n < p.Nn) {
-            const int64_t ocol = ocolb_i + n;
-            if (ocol >= orow_i) p.out[orow_i * p.ldo + ocol] = val;
+          const int64_t orow_i = srow[i];
+          if (orow_i >= 0 && n < Nn) {
+            const int64_t ocol = scol[i] + n;
+            if (ocol >= orow_i) out[orow_i * ldo + ocol] = e[i * EPI_LD + jj];
           }
         }
         __syncwarp();
+      };
+      int c = 0;
+      for (; c + 2 <= BN / 16; c += 2) {
+        float v[32];
+        tmem_ld32(tbase + c * 16, v);
+        emit16(v, nbase + c * 16);
+        emit16(v + 16, nbase + c * 16 + 16);
+      }
+      if (c < BN / 16) {
+        float v[16];
+        tmem_ld16(tbase + c * 16, v);
+        emit16(v, nbase + c * 16);
       }
       tc_fence_before();
       mbar_arrive(tempty(acc));
@@ -718,15 +765,17 @@ hess_status make_job(const TcOperands& op, int BN, tc::Job* j) {
 // Copy jobs and tiles to the device regions given and launch the
 // persistent kernel over them.
 hess_status launch_jobs(int sm_count, const tc::Job* jobs, int njobs, const int4* tiles, int ntiles,
-                        tc::Job* jobs_d, int4* tiles_d, bool x3, int* err, cudaStream_t s) {
+                        tc::Job* jobs_d, int4* tiles_d, bool x3, int* err, PinnedStage& stage, cudaStream_t s) {
   using namespace tc;
   if (ntiles < 1) return HESS_OK;
   if (!g_attr_set) {
     HM_CUDA(cudaFuncSetAttribute(umma_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     g_attr_set = true;
   }
-  HM_CUDA(cudaMemcpyAsync(jobs_d, jobs, njobs * sizeof(Job), cudaMemcpyHostToDevice, s));
-  HM_CUDA(cudaMemcpyAsync(tiles_d, tiles, ntiles * sizeof(int4), cudaMemcpyHostToDevice, s));
+  const void* src[2] = {jobs, tiles};
+  const size_t bytes[2] = {njobs * sizeof(Job), ntiles * sizeof(int4)};
+  void* dst[2] = {jobs_d, tiles_d};
+  HM_TRY(stage_copy(stage, src, bytes, dst, 2, s));
   Launch L{jobs_d, tiles_d, ntiles, x3 ? 3 : 1, err};
   const int grid = ntiles < sm_count ? ntiles : sm_count;
   umma_gemm_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(L);
@@ -775,13 +824,6 @@ static void syrk_tiles(int64_t P, int BN, int job, std::vector<int4>& tiles) {
         if (tn * BN + BN - 1 >= tm * BM) tiles.push_back(make_int4(job, (int)tm, (int)tn, 0));
 }
 
-hess_status tc_check_err(cudaStream_t s, double* host_scratch, int* err_d) {
-  int* hv = reinterpret_cast<int*>(host_scratch);
-  HM_CUDA(cudaMemcpyAsync(hv, err_d, sizeof(int), cudaMemcpyDeviceToHost, s));
-  HM_CUDA(cudaStreamSynchronize(s));
-  if (*hv) return set_error(HESS_ERR_TIMEOUT, "a tensor-core pipeline wait gave up");
-  return HESS_OK;
-}
 
 
 // Upper-triangle entries of the W x W block of a weight layer (rows (u, i, q)
@@ -1058,7 +1100,7 @@ hess_status tc_prep(hess_mlp* h, const TcItem& it, Arena& ar, bool live, TcPlan&
 }
 
 hess_status tc_launch_plan(int sm_count, const TcPlan& plan, Arena& ar, bool live, bool x3, int* err,
-                           cudaStream_t s) {
+                           PinnedStage& stage, cudaStream_t s) {
   using namespace tc;
   tc::Job* jd = ar.take<tc::Job>(plan.jobs.size() ? plan.jobs.size() : 1);
   int4* td = ar.take<int4>(plan.tiles.size() ? plan.tiles.size() : 1);
@@ -1073,7 +1115,7 @@ hess_status tc_launch_plan(int sm_count, const TcPlan& plan, Arena& ar, bool liv
     return (int64_t)ja.nkb * ja.BN > (int64_t)jb.nkb * jb.BN;
   });
   return launch_jobs(sm_count, plan.jobs.data(), (int)plan.jobs.size(), order.data(), (int)order.size(), jd,
-                     td, x3, err, s);
+                     td, x3, err, stage, s);
 }
 
 // Stages host inputs and outputs for the single-network calls.
@@ -1108,21 +1150,18 @@ static hess_status run_single(hess_mlp* h, const void* X, const void* Y, int64_t
   HM_TRY(classify_ptr(h, Y, &st.y_dev));
   HM_TRY(classify_ptr(h, out, &st.o_dev));
   cudaStream_t s = h->stream;
-  int* err = nullptr;
   char* split = nullptr;
   TcPlan plan;
   auto build = [&](Arena& ar, bool live) -> hess_status {
     Staged d;
     HM_TRY(stage(h, ar, live, X, Y, out, N, st, d));
-    err = ar.take<int>(1);
     split = ar.take<char>(kSplitBytes);
     TcItem it{d.X, d.Y, N, kind == 0, kind == 1, kind == 0 ? d.out : nullptr, kind == 1 ? d.out : nullptr};
-    if (live) HM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     SplitGuard sg(split, kSplitBytes, h->sm_count);
     HM_TRY(tc_prep(h, it, ar, live, plan, s));
     Tick t(live ? h : nullptr, kind == 0 ? HESS_K_SYRK : HESS_K_HCONTRACT,
            kind == 0 ? plan.syrk_flops : plan.hess_flops, 0.0);
-    return tc_launch_plan(h->sm_count, plan, ar, live, x3, err, s);
+    return tc_launch_plan(h->sm_count, plan, ar, live, x3, h->err_dev, h->stage, s);
   };
   Arena ar;
   HM_TRY(build(ar, false));
@@ -1136,8 +1175,10 @@ static hess_status run_single(hess_mlp* h, const void* X, const void* Y, int64_t
     Arena a2{h->ws, 0};
     HM_TRY(stage(h, a2, false, X, Y, out, N, st, d));
     HM_CUDA(cudaMemcpyAsync(out, d.out, P * P * 4, cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaStreamSynchronize(s));
+    return take_sticky_error(h);
   }
-  return tc_check_err(s, h->host_pinned, err);
+  return HESS_OK;
 }
 
 // Bytes of the whole-operand Hessian plan (caches, R-op buffers, operands).
@@ -1200,7 +1241,6 @@ hess_status run_hessian_chunked(hess_mlp* h, const void* X, const void* Y, int64
   bf *bhi, *blo, *ahi, *alo, *fhi, *flo;
   int4* tl;
   Job* jd;
-  int* err;
   char* split;
   auto plan = [&](Arena& ar, bool live) -> hess_status {
     HM_TRY(stage(h, ar, live, X, Y, Hout, N, st, d));
@@ -1215,7 +1255,6 @@ hess_status run_hessian_chunked(hess_mlp* h, const void* X, const void* Y, int64
     flo = ar.take<bf>((int64_t)pchunk * maxRest * ld);
     tl = ar.take<int4>(max_tiles);
     jd = ar.take<Job>(1);
-    err = ar.take<int>(1);
     split = ar.take<char>(kSplitBytes);
     return HESS_OK;
   };
@@ -1226,7 +1265,6 @@ hess_status run_hessian_chunked(hess_mlp* h, const void* X, const void* Y, int64
   HM_TRY(plan(ar, true));
   SplitGuard sg(split, kSplitBytes, h->sm_count);
   float* O = d.out;
-  HM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
   const float* omega = h->omega32;
   HM_TRY(forward_backward(net, omega, d.X, d.Y, c, s));
   HM_TRY(transpose_caches(net, c, N, ld, tq, s));
@@ -1255,7 +1293,7 @@ hess_status run_hessian_chunked(hess_mlp* h, const void* X, const void* Y, int64
       wrow_job(net, jm, p0, p1, R0, O, N, job, tiles, 0);
       {
         Tick t(h, HESS_K_HCONTRACT, wrow_flops(Tin, Tout, p0, p1, N), 0.0);
-        HM_TRY(launch_jobs(h->sm_count, &job, 1, tiles.data(), (int)tiles.size(), jd, tl, x3, err, s));
+        HM_TRY(launch_jobs(h->sm_count, &job, 1, tiles.data(), (int)tiles.size(), jd, tl, x3, h->err_dev, h->stage, s));
       }
       p0 = p1;
     }
@@ -1271,12 +1309,16 @@ hess_status run_hessian_chunked(hess_mlp* h, const void* X, const void* Y, int64
       f_job(net, jm, q0, pc, O, N, job, tiles, 0);
       {
         Tick t(h, HESS_K_HCONTRACT, f_flops(Tin, rest, pc, N), 0.0);
-        HM_TRY(launch_jobs(h->sm_count, &job, 1, tiles.data(), (int)tiles.size(), jd, tl, x3, err, s));
+        HM_TRY(launch_jobs(h->sm_count, &job, 1, tiles.data(), (int)tiles.size(), jd, tl, x3, h->err_dev, h->stage, s));
       }
     }
   }
-  if (!st.o_dev) HM_CUDA(cudaMemcpyAsync(Hout, O, P * P * 4, cudaMemcpyDeviceToHost, s));
-  return tc_check_err(s, h->host_pinned, err);
+  if (!st.o_dev) {
+    HM_CUDA(cudaMemcpyAsync(Hout, O, P * P * 4, cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaStreamSynchronize(s));
+    return take_sticky_error(h);
+  }
+  return HESS_OK;
 }
 
 // OPG = G^T G / N with split-BF16 (or BF16) operands on the tensor cores.
