@@ -102,13 +102,21 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* er
   }
 }
 
+// Operand tile load with an L2 evict-last policy: the operands are re-read by
+// many tiles, while the output streams past them.
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                            uint32_t bar) {
+                                            uint32_t bar, uint64_t policy) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
-      "%3}], [%4];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], "
+      "[%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "l"(policy)
       : "memory");
+}
+
+__device__ __forceinline__ uint64_t evict_last_policy() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
 }
 
 __device__ __forceinline__ void tc_fence_before() {
@@ -293,6 +301,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       int it = 0;
       bool ok = true;
       int last_job = -1;
+      const uint64_t pol = evict_last_policy();
       for (int t = blockIdx.x; t < L.ntiles && ok; t += gridDim.x) {
         const int4 tile = L.tiles[t];
         const Job& jb = L.jobs[tile.x];
@@ -327,11 +336,11 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
           uint8_t* st = smem + s * STAGE_BYTES;
           mbar_expect_tx(full(s), tx_bytes);
-          tma_load_2d(smem_u32(st), m_ahi, j * BK, tile.y * BM, full(s));
-          tma_load_2d(smem_u32(st + OFF_BHI), m_bhi, j * BK, brow0, full(s));
+          tma_load_2d(smem_u32(st), m_ahi, j * BK, tile.y * BM, full(s), pol);
+          tma_load_2d(smem_u32(st + OFF_BHI), m_bhi, j * BK, brow0, full(s), pol);
           if (x3) {
-            tma_load_2d(smem_u32(st + OFF_ALO), m_alo, j * BK, tile.y * BM, full(s));
-            tma_load_2d(smem_u32(st + OFF_BLO), m_blo, j * BK, brow0, full(s));
+            tma_load_2d(smem_u32(st + OFF_ALO), m_alo, j * BK, tile.y * BM, full(s), pol);
+            tma_load_2d(smem_u32(st + OFF_BLO), m_blo, j * BK, brow0, full(s), pol);
           }
         }
       }
@@ -466,7 +475,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           e[lane * EPI_LD + jj] = val;
           if (rvalid && n < Nn) {
             const int64_t ocol = ocolb + n;
-            if (ocol > orow) out[ocol * ldo + orow] = val;
+            if (ocol > orow) __stcs(out + ocol * ldo + orow, val);
           }
         }
         __syncwarp();
@@ -478,7 +487,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int64_t orow_i = srow[i];
           if (orow_i >= 0 && n < Nn) {
             const int64_t ocol = scol[i] + n;
-            if (ocol >= orow_i) out[orow_i * ldo + ocol] = e[i * EPI_LD + jj];
+            if (ocol >= orow_i) __stcs(out + orow_i * ldo + ocol, e[i * EPI_LD + jj]);
           }
         }
         __syncwarp();
