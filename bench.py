@@ -239,11 +239,17 @@ def serve_bench(args):
     lock = threading.Lock()
     pending = []
 
+    failures = {}
+
     def waiter(j, ticket, t_submit, keep):
         st = srv.wait(ticket)
         t_done = time.perf_counter()
+        msg = hm.last_error() if st not in (0, 4) else ""
         with lock:
             lat[j] = (t_done - t_submit, st)
+            if msg:
+                failures.setdefault(f"{st}: {msg[:120]}", 0)
+                failures[f"{st}: {msg[:120]}"] += 1
         del keep
         sem.release()
 
@@ -281,7 +287,7 @@ def serve_bench(args):
         "value": float(np.percentile(ls, 50)), "unit": "ms (p50)",
         "p50_ms": float(np.percentile(ls, 50)), "p99_ms": float(np.percentile(ls, 99)),
         "entries_per_s": float(sum(entries) / wall), "requests": n_req,
-        "completed": len(ok), "wall_s": wall, "offered_rate": args.serve_rate,
+        "completed": len(ok), "failures": failures, "wall_s": wall, "offered_rate": args.serve_rate,
         "achieved_rate": n_req / wall, "higher_is_better": False, "n_gpus": 1,
         "config": {"workload": "Poisson request stream (seed 4): exact Hessian (split-BF16), OPG "
                                "(split-BF16), top-32 OPG eig (FP64 Gram), 16 networks of the "

@@ -10,6 +10,7 @@
 //      ones), residual bound |beta_m y_m| for convergence
 //   4. Ritz vectors U = Q_m Y, back-projection q = G^T u / sqrt(N mu)
 #include <cfloat>
+#include <mutex>
 
 #include "internal.h"
 
@@ -578,8 +579,11 @@ __device__ int block_first(bool pred, int* s4) {
 // ||T|| <= 1.  Two coarse sweeps run in FP32; their bracket is widened by
 // 4e-6 (well above the FP32 backward error of the count, a few float ulps of
 // ||T||) before the FP64 sweeps take it down to a few ulps.
-__global__ void bisect_kernel(const double* a, const double* b, int m, int k, double* theta) {
-  extern __shared__ double tsh[];
+__global__ void bisect_kernel(const double* a, const double* b, int m, int k, double* theta, double* gscratch) {
+  extern __shared__ double tsh_s[];
+  // T's copies in shared memory, or (when 3 m doubles exceed it) in a global
+  // scratch of 3 m doubles per block
+  double* tsh = gscratch ? gscratch + (int64_t)blockIdx.x * 3 * m : tsh_s;
   double* sa = tsh;
   double* sb2 = tsh + m;
   float* fa = reinterpret_cast<float*>(tsh + 2 * m);
@@ -658,13 +662,15 @@ __global__ void bisect_kernel(const double* a, const double* b, int m, int k, do
 // res[c] = |beta_m y_c[m-1]| bounds the residual of Ritz pair c.
 __global__ void inviter_kernel(const double* a, const double* b, int m, int k, const double* theta,
                                const int* cstart, double* Y, int64_t ldy, const double* beta_last,
-                               double* res, uint64_t key) {
+                               double* res, uint64_t key, double* gscratch) {
   const int c0 = blockIdx.x;
   if (cstart[c0] != c0) return;
   __shared__ double sh[32];
   __shared__ double sdot[1024];
-  // the O(m) recurrences run on shared-memory copies (5 m doubles + m ints)
-  extern __shared__ double ish[];
+  // the O(m) recurrences run on copies in shared memory (5 m doubles + m
+  // ints), or in a global scratch of 6 m doubles per block when too large
+  extern __shared__ double ish_s[];
+  double* ish = gscratch ? gscratch + (int64_t)blockIdx.x * 6 * m : ish_s;
   double* d = ish;
   double* du = ish + m;
   double* dl = ish + 2 * m;
@@ -848,6 +854,24 @@ __global__ void max_res_kernel(const double* res, int k, const double* theta, do
 
 }  // namespace
 
+// Dynamic shared memory the eigen kernels may use (their attribute is set
+// once to this, so that concurrent calls with different sizes do not race).
+constexpr size_t kEigSmemCap = (size_t)208 << 10;
+
+hess_status eig_kernel_attributes() {
+  static std::once_flag once;
+  static cudaError_t e = cudaSuccess;
+  std::call_once(once, [] {
+    e = cudaFuncSetAttribute(lanczos_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEigSmemCap);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEigSmemCap);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(inviter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEigSmemCap);
+  });
+  if (e != cudaSuccess) return set_error(HESS_ERR_CUDA, "eigen kernel attributes: %s", cudaGetErrorString(e));
+  return HESS_OK;
+}
+
 hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, int64_t N, int k,
                           double* evals_d, double* evecs_d, Arena& ar, bool dry, EigResult* res) {
   const int64_t P = net.P;
@@ -878,6 +902,10 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   double* mx = ar.take<double>(2);
   int* flag = ar.take<int>(2);
   int* stop = ar.take<int>(1);
+  // global scratch of the tridiagonal kernels when shared memory is too small
+  double* tri_scratch = (size_t)3 * mcap * sizeof(double) > kEigSmemCap || (size_t)6 * mcap * sizeof(double) > kEigSmemCap
+                            ? ar.take<double>((int64_t)k * 6 * (mcap + 1))
+                            : nullptr;
   if (dry) return HESS_OK;
   cudaStream_t s = h->stream;
 
@@ -921,7 +949,7 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   // fit, w, the owned rows of M and the owned slice of Q
   const int64_t E = cdiv(N, h->sm_count);
   const int grid = (int)cdiv(N, E);
-  const size_t cap = (size_t)208 << 10;
+  const size_t cap = kEigSmemCap;
   size_t dyn = ((size_t)(mcap + 1) + 3 * (size_t)E) * sizeof(double);
   int cache_w = 0, cache_m = 0, cache_q = 0;
   if (dyn + (size_t)N * 8 <= cap) {
@@ -939,15 +967,13 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   if (dyn > cap) return set_error(HESS_ERR_UNSUPPORTED, "Lanczos workspace exceeds shared memory (N = %lld)",
                                   (long long)N);
   int per_sm = 0;
-  HM_CUDA(cudaFuncSetAttribute(lanczos_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+  HM_TRY(eig_kernel_attributes());
   HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lanczos_coop_kernel, 512, dyn));
   if (per_sm < 1 || grid > per_sm * h->sm_count) return set_error(HESS_ERR_CUDA, "Lanczos kernel cannot be resident");
-  const size_t inv_smem = (size_t)6 * mcap * sizeof(double);
-  if (inv_smem > 48 * 1024)
-    HM_CUDA(cudaFuncSetAttribute(inviter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem));
-  if ((size_t)3 * mcap * sizeof(double) > 48 * 1024)
-    HM_CUDA(cudaFuncSetAttribute(bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(3 * mcap * sizeof(double))));
+  // shared memory of the tridiagonal kernels, or their global scratch
+  const bool inv_g = (size_t)6 * mcap * sizeof(double) > kEigSmemCap;
+  const bool bis_g = (size_t)3 * mcap * sizeof(double) > kEigSmemCap;
+  const size_t inv_smem = inv_g ? 0 : (size_t)6 * mcap * sizeof(double);
   init_start_kernel<<<1, 1024, 0, s>>>(w, npart, grid, N, key);
   HM_LAUNCHED();
   HM_CUDA(cudaMemsetAsync(bar, 0, 64 * sizeof(unsigned), s));
@@ -997,13 +1023,14 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
     HM_LAUNCHED();
     // one block per eigenvalue: the FP64 Sturm recurrences of different
     // eigenvalues run on different SMs
-    bisect_kernel<<<(unsigned)k, 128, (size_t)3 * m * sizeof(double), s>>>(alpha, beta, m, k, theta);
+    bisect_kernel<<<(unsigned)k, 128, bis_g ? 0 : (size_t)3 * m * sizeof(double), s>>>(alpha, beta, m, k, theta,
+                                                                                 bis_g ? tri_scratch : nullptr);
     HM_LAUNCHED();
     // eigenvalues closer than 1e-6 of the largest share a cluster
     clusters_kernel<<<1, 32, 0, s>>>(theta, k, 1e-6, cstart);
     HM_LAUNCHED();
-    inviter_kernel<<<k, 256, inv_smem, s>>>(alpha, beta, m, k, theta, cstart, Y, mcap, h2, rr,
-                                     key + 11);
+    inviter_kernel<<<k, 256, inv_smem, s>>>(alpha, beta, m, k, theta, cstart, Y, mcap, h2, rr, key + 11,
+                                            inv_g ? tri_scratch : nullptr);
     HM_LAUNCHED();
     max_res_kernel<<<1, 32, 0, s>>>(rr, k, theta, mx);
     HM_LAUNCHED();

@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 
 #include "internal.h"
@@ -680,19 +681,20 @@ __global__ void build_f_bf16_kernel(FArgs f, int p0, int np, __nv_bfloat16* hi, 
 
 // --------------------------------------------------------------- host ----
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
-bool g_attr_set = false;
 
 hess_status get_encode() {
-  if (g_encode) return HESS_OK;
-  void* fn = nullptr;
-  cudaDriverEntryPointQueryResult q;
-  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
-                                                   cudaEnableDefault, &q);
-  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
-    cudaGetLastError();
-    return set_error(HESS_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
-  }
-  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return;
+    }
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  if (!g_encode) return set_error(HESS_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
   return HESS_OK;
 }
 
@@ -777,9 +779,14 @@ hess_status launch_jobs(int sm_count, const tc::Job* jobs, int njobs, const int4
                         tc::Job* jobs_d, int4* tiles_d, bool x3, int* err, PinnedStage& stage, cudaStream_t s) {
   using namespace tc;
   if (ntiles < 1) return HESS_OK;
-  if (!g_attr_set) {
-    HM_CUDA(cudaFuncSetAttribute(umma_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    g_attr_set = true;
+  {
+    // once per process (calls from several threads must not race on it)
+    static std::once_flag once;
+    static cudaError_t e = cudaSuccess;
+    std::call_once(once, [] {
+      e = cudaFuncSetAttribute(umma_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    });
+    HM_CUDA(e);
   }
   const void* src[2] = {jobs, tiles};
   const size_t bytes[2] = {njobs * sizeof(Job), ntiles * sizeof(int4)};

@@ -113,3 +113,31 @@ def _plan(hm, pb):
             lo = mid
         srv.close()
     return hi
+
+
+def test_concurrent_eigen_requests_of_different_sizes(hm):
+    # eigen requests with different N run on several slots at once; each
+    # must succeed (a per-call kernel attribute would race between slots)
+    pbs = []
+    for i in range(6):
+        widths, acts, N = make_random_mlp(5, i)
+        pbs.append(make_problem(widths, acts, min(N, 700) + 37 * i, 60 + i, "normal", "uniform"))
+    srv = hm.HessServer(slots=4, budget_bytes=40 << 30)
+    ids = [srv.add_network(pb.widths, pb.acts, pb.omega) for pb in pbs]
+    jobs = []
+    for rep in range(3):
+        for i, pb in enumerate(pbs):
+            X = torch.as_tensor(pb.X, dtype=torch.float32, device="cuda")
+            Y = torch.as_tensor(pb.Y, dtype=torch.float32, device="cuda")
+            out = torch.empty((16, pb.P), dtype=torch.float64, device="cuda")
+            ev = torch.empty(16, dtype=torch.float64, device="cuda")
+            jobs.append((i, srv.submit("eig", ids[i], X, Y, "fp32", out, k=16, evals=ev), out, ev))
+    results = {}
+    for i, t, out, ev in jobs:
+        assert srv.wait(t) in (0, 4), hm.last_error()
+        results.setdefault(i, []).append((ev.cpu().numpy(), out.cpu().numpy()))
+    srv.close()
+    for i, runs in results.items():
+        ref = _alone(hm, pbs[i], "eig", "fp32", 16).cpu().numpy()
+        for ev, Q in runs:
+            assert np.array_equal(ev, runs[0][0]) and np.array_equal(Q, ref)
