@@ -195,6 +195,33 @@ __device__ double combine_slice(const LzArgs& a, const double* Qsh, const double
                                 double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   double nn = 0.0;
+  if (a.cache_q && ne <= nwarp) {
+    // few owned entries: one warp per entry, lanes along i (an FP64 warp
+    // instruction costs the same with 7 lanes active as with 32)
+    if (warp < ne) {
+      const int e = warp;
+      double s0 = 0.0, s1 = 0.0;
+      int i = lane;
+      for (; i + 32 < nv; i += 64) {
+        s0 = fma(Qsh[(int64_t)i * a.E + e], coef[i], s0);
+        s1 = fma(Qsh[(int64_t)(i + 32) * a.E + e], coef[i + 32], s1);
+      }
+      if (i < nv) s0 = fma(Qsh[(int64_t)i * a.E + e], coef[i], s0);
+      const double t = warp_sum(s0 + s1);
+      if (lane == 0) {
+        const double v = base[e] - t;
+        out[e] = v;
+        out_g[n0 + e] = v;
+        red[e] = v * v;
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int e = lane; e < ne; e += 32) nn += red[e];
+    }
+    __syncthreads();
+    return nn;  // warp 0 lanes hold partial sums of squares
+  }
   for (int c0 = 0; c0 < ne; c0 += 32) {
     const int e = c0 + lane;
     double s0 = 0.0, s1 = 0.0;

@@ -565,12 +565,23 @@ __global__ void transpose_pad_kernel(const float* in, int64_t rows, int64_t cols
   }
 }
 
-__device__ __forceinline__ void split2_store(float2 v, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t at) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
-  const float2 hf = __bfloat1622float2(h);
-  const __nv_bfloat162 l = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
-  *reinterpret_cast<__nv_bfloat162*>(hi + at) = h;
-  *reinterpret_cast<__nv_bfloat162*>(lo + at) = l;
+
+// Eight consecutive values split into bf16 hi/lo planes, 16-byte stores.
+__device__ __forceinline__ void split8_store(const float (&v)[8], __nv_bfloat16* hi, __nv_bfloat16* lo,
+                                             int64_t at) {
+  uint4 h, l;
+  uint32_t* hp = &h.x;
+  uint32_t* lp = &l.x;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __nv_bfloat162 hh = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    const float2 hf = __bfloat1622float2(hh);
+    const __nv_bfloat162 ll = __floats2bfloat162_rn(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
+    hp[i] = *reinterpret_cast<const uint32_t*>(&hh);
+    lp[i] = *reinterpret_cast<const uint32_t*>(&ll);
+  }
+  *reinterpret_cast<uint4*>(hi + at) = h;
+  *reinterpret_cast<uint4*>(lo + at) = l;
 }
 
 // Row Tin of the mode-2 A operand: ones over the examples (zero padding
@@ -592,9 +603,8 @@ __global__ void ones_row_kernel(__nv_bfloat16* hi, __nv_bfloat16* lo, int64_t N,
 // rdT: [u][i][ld] and aT: [q][ld], example-fastest and zero-padded.
 __global__ void build_wrows_kernel(const float* rdT, const float* aT, int Tin, int Tout, int64_t R0,
                                    int64_t nrows, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ld) {
-  // one warp per row, lanes along the examples
+  // one warp per row, lanes along the examples (8 per lane per pass)
   const int lane = threadIdx.x & 31;
-  const int64_t half = ld / 2;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = w0; r < nrows; r += nw) {
@@ -602,12 +612,14 @@ __global__ void build_wrows_kernel(const float* rdT, const float* aT, int Tin, i
     const int64_t u = wrow_unit(g, Tin, Tout);
     const int64_t rr = g - rows_before(u, Tin, Tout);
     const int64_t i = u + rr / Tin, q = rr % Tin;
-    const float2* x = reinterpret_cast<const float2*>(rdT + (u * Tout + i) * ld);
-    const float2* y = reinterpret_cast<const float2*>(aT + q * ld);
+    const float4* x = reinterpret_cast<const float4*>(rdT + (u * Tout + i) * ld);
+    const float4* y = reinterpret_cast<const float4*>(aT + q * ld);
     const int64_t at = r * ld;
-    for (int64_t j = lane; j < half; j += 32) {
-      const float2 p = x[j], w = y[j];
-      split2_store(make_float2(p.x * w.x, p.y * w.y), hi, lo, at + 2 * j);
+    for (int64_t j = lane; j < ld / 8; j += 32) {
+      const float4 p0 = x[2 * j], p1 = x[2 * j + 1], w0 = y[2 * j], w1 = y[2 * j + 1];
+      const float v[8] = {p0.x * w0.x, p0.y * w0.y, p0.z * w0.z, p0.w * w0.w,
+                          p1.x * w1.x, p1.y * w1.y, p1.z * w1.z, p1.w * w1.w};
+      split8_store(v, hi, lo, at + 8 * j);
     }
   }
 }
@@ -638,10 +650,9 @@ struct FArgs {
 // (u - p0) * cols + c holds F[., u, c] over the examples (zero-padded to ld).
 __global__ void build_f_bf16_kernel(FArgs f, int p0, int np, __nv_bfloat16* hi, __nv_bfloat16* lo,
                                     int64_t ld) {
-  // one warp per row, lanes along the examples
+  // one warp per row, lanes along the examples (8 per lane per pass)
   const int lane = threadIdx.x & 31;
   const int64_t rows = (int64_t)np * f.cols;
-  const int64_t half = ld / 2;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t row = w0; row < rows; row += nw) {
@@ -651,30 +662,39 @@ __global__ void build_f_bf16_kernel(FArgs f, int p0, int np, __nv_bfloat16* hi, 
     while (s + 1 < f.nseg && f.seg[s + 1].c0 <= c) ++s;
     const FSeg& g = f.seg[s];
     const int64_t cl = c - g.c0;
-    const float2 *x1, *y1 = nullptr, *x2 = nullptr, *y2 = nullptr;
+    const float4 *x1, *y1 = nullptr, *x2 = nullptr, *y2 = nullptr;
     if (cl < g.nW) {
       const int i = (int)(cl / g.Tin), k = (int)(cl % g.Tin);
-      x1 = reinterpret_cast<const float2*>(g.rd + ((int64_t)u * g.Tout + i) * ld);
-      y1 = reinterpret_cast<const float2*>(g.a + (int64_t)k * ld);
+      x1 = reinterpret_cast<const float4*>(g.rd + ((int64_t)u * g.Tout + i) * ld);
+      y1 = reinterpret_cast<const float4*>(g.a + (int64_t)k * ld);
       if (g.ra) {
-        x2 = reinterpret_cast<const float2*>(g.dlt + (int64_t)i * ld);
-        y2 = reinterpret_cast<const float2*>(g.ra + ((int64_t)u * g.Tin + k) * ld);
+        x2 = reinterpret_cast<const float4*>(g.dlt + (int64_t)i * ld);
+        y2 = reinterpret_cast<const float4*>(g.ra + ((int64_t)u * g.Tin + k) * ld);
       }
     } else {
-      x1 = reinterpret_cast<const float2*>(g.rd + ((int64_t)u * g.Tout + (cl - g.nW)) * ld);
+      x1 = reinterpret_cast<const float4*>(g.rd + ((int64_t)u * g.Tout + (cl - g.nW)) * ld);
     }
     const int64_t at = row * ld;
-    for (int64_t j = lane; j < half; j += 32) {
-      float2 v = x1[j];
+    for (int64_t j = lane; j < ld / 8; j += 32) {
+      float v[8];
+      {
+        const float4 a0 = x1[2 * j], a1 = x1[2 * j + 1];
+        v[0] = a0.x; v[1] = a0.y; v[2] = a0.z; v[3] = a0.w;
+        v[4] = a1.x; v[5] = a1.y; v[6] = a1.z; v[7] = a1.w;
+      }
       if (y1) {
-        const float2 w = y1[j];
-        v = make_float2(v.x * w.x, v.y * w.y);
+        const float4 b0 = y1[2 * j], b1 = y1[2 * j + 1];
+        v[0] *= b0.x; v[1] *= b0.y; v[2] *= b0.z; v[3] *= b0.w;
+        v[4] *= b1.x; v[5] *= b1.y; v[6] *= b1.z; v[7] *= b1.w;
       }
       if (x2) {
-        const float2 d = x2[j], r = y2[j];
-        v = make_float2(fmaf(d.x, r.x, v.x), fmaf(d.y, r.y, v.y));
+        const float4 d0 = x2[2 * j], d1 = x2[2 * j + 1], r0 = y2[2 * j], r1 = y2[2 * j + 1];
+        v[0] = fmaf(d0.x, r0.x, v[0]); v[1] = fmaf(d0.y, r0.y, v[1]);
+        v[2] = fmaf(d0.z, r0.z, v[2]); v[3] = fmaf(d0.w, r0.w, v[3]);
+        v[4] = fmaf(d1.x, r1.x, v[4]); v[5] = fmaf(d1.y, r1.y, v[5]);
+        v[6] = fmaf(d1.z, r1.z, v[6]); v[7] = fmaf(d1.w, r1.w, v[7]);
       }
-      split2_store(v, hi, lo, at + 2 * j);
+      split8_store(v, hi, lo, at + 8 * j);
     }
   }
 }
