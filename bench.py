@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--batch", action="store_true",
                     help="the many-networks workload: OPG + exact Hessian of 256 networks in waves")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--autotune", action="store_true",
+                    help="tune the tensor-core tile widths during the warm-up steps")
     ap.add_argument("--batch-workspace-gb", type=float, default=64.0)
     ap.add_argument("--batch-out-gb", type=float, default=96.0)
     ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
@@ -386,8 +388,11 @@ def batch_bench(args):
                     worst = max(worst, check(i, o, h))
         return ms, launch_ms, flops, waves, chunked, worst
 
+    if args.autotune:
+        hm.autotune(True)
     for _ in range(args.warmup):
         one_pass(False)
+    hm.autotune(False)
     sampler = ClockSampler(gpu_index(0))
     sampler.start()
     l0 = lib.hess_launch_count()
@@ -410,6 +415,8 @@ def batch_bench(args):
         "config": {"workload": f"{args.batch_count} MLPs of the batching distribution (seed 3), "
                                "OPG + exact Hessian each, split-BF16",
                    "networks": args.batch_count, "groups": len(groups), "waves": waves,
+                   "tile_widths": (f"autotuned ({hm.autotune_entries()} shapes)" if args.autotune
+                                   else "cost model"),
                    "items_alone": chunked,
                    "workspace_gb": args.batch_workspace_gb, "output_pool_gb": args.batch_out_gb,
                    "l2": "outputs and operands far larger than L2"},
@@ -547,8 +554,11 @@ def main():
 
     def timed(prec, steps, warmup, sampler=None):
         io = make_io(prec)
+        if args.autotune:
+            hm.autotune(True)
         for _ in range(warmup):
             step(prec, io)
+        hm.autotune(False)
         torch.cuda.synchronize()
         for cls in hm._lib.KERNEL_CLASS:
             net.read_timing(cls)

@@ -236,6 +236,24 @@ HESS_API hess_status hess_server_wait(hess_server* s, int64_t ticket, double tim
 HESS_API hess_status hess_server_destroy(hess_server* s);
 
 /* ----------------------------------------------------------------------
+ * Tile-width autotuning of the tensor-core contractions (no counterpart in
+ * the paper).  By default each contraction's tile width comes from a cost
+ * model.  With tuning on, the first contraction of each shape (mode, output
+ * columns, K blocks, BF16 or split-BF16) that a call meets is run alone at
+ * every candidate width (64 .. 256) on its real operands -- its output is
+ * written each time, with the same values -- and the fastest width is kept
+ * for the rest of the process.  Tuning synchronises the calling stream and
+ * is skipped inside a CUDA-graph capture.  The table can be saved and loaded
+ * (text, one "mode columns kblocks products3 width" line per shape).
+ * -------------------------------------------------------------------- */
+HESS_API hess_status hess_autotune(int enable);
+HESS_API int hess_autotune_entries(void);
+HESS_API hess_status hess_autotune_save(const char* path);
+/* Errors: INVALID_ARG for an unreadable file or malformed lines (the valid
+ * lines are still loaded). */
+HESS_API hess_status hess_autotune_load(const char* path);
+
+/* ----------------------------------------------------------------------
  * Batched curvature matrices (no counterpart in the paper, which computes the
  * matrices of one network per call).  The OPG and/or exact Hessian of many
  * networks, each with its own data, in waves: a wave builds the operands of

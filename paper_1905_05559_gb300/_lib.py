@@ -35,6 +35,7 @@ EXPORTS = (
     "hess_launch_count", "per_example_grads_noalloc", "hess_server_create",
     "hess_server_add_network", "hess_server_submit", "hess_server_wait", "hess_server_destroy",
     "hess_mlp_set_operand_limit", "hess_batch_create", "hess_batch_run", "hess_batch_destroy",
+    "hess_autotune", "hess_autotune_entries", "hess_autotune_save", "hess_autotune_load",
 )
 
 REQUEST_KIND = {"hessian": 0, "opg": 1, "eig": 2}
@@ -134,6 +135,14 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.hess_batch_run.restype = st
     lib.hess_batch_destroy.argtypes = [vp]
     lib.hess_batch_destroy.restype = st
+    lib.hess_autotune.argtypes = [ctypes.c_int]
+    lib.hess_autotune.restype = st
+    lib.hess_autotune_entries.argtypes = []
+    lib.hess_autotune_entries.restype = ctypes.c_int
+    lib.hess_autotune_save.argtypes = [ctypes.c_char_p]
+    lib.hess_autotune_save.restype = st
+    lib.hess_autotune_load.argtypes = [ctypes.c_char_p]
+    lib.hess_autotune_load.restype = st
     lib.hess_launch_count.argtypes = []
     lib.hess_launch_count.restype = ctypes.c_int64
     lib.hess_last_error.argtypes = []

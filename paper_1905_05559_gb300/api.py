@@ -151,6 +151,23 @@ class HessMLP:
         return np.empty(shape, dtype=dt)
 
 
+def autotune(enable: bool = True):
+    """Turn tile-width autotuning of the tensor-core contractions on or off."""
+    _lib.check(_lib.load().hess_autotune(1 if enable else 0))
+
+
+def autotune_entries() -> int:
+    return int(_lib.load().hess_autotune_entries())
+
+
+def autotune_save(path: str):
+    _lib.check(_lib.load().hess_autotune_save(str(path).encode()))
+
+
+def autotune_load(path: str):
+    _lib.check(_lib.load().hess_autotune_load(str(path).encode()))
+
+
 class HessBatch:
     """Batched OPG / exact Hessian of many networks (hess_batch_*): marshalling only."""
 

@@ -170,7 +170,7 @@ hess_status hess_batch_run(hess_batch* b, const hess_batch_item* items, int coun
       Arena ar{b->ws, base};
       for (int q = i; q < j; ++q) {
         const hess_batch_item& it = items[q];
-        TcItem ti{it.X, it.Y, it.N, it.opg != nullptr, it.hessian != nullptr, it.opg, it.hessian};
+        TcItem ti{it.X, it.Y, it.N, it.opg != nullptr, it.hessian != nullptr, it.opg, it.hessian, x3};
         const size_t at = ar.off;
         HM_TRY(tc_prep(it.net, ti, ar, true, plan, s));
         ar.off = at + align_up(ar.off - at, 256);

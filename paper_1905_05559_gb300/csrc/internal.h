@@ -311,6 +311,7 @@ struct Job {
 struct TcPlan {
   std::vector<tc::Job> jobs;
   std::vector<int4> tiles;  // (job, row tile, column tile, 0)
+  int64_t tiles_cap = 0;    // tiles at the narrowest candidate width (table room)
   double syrk_flops = 0.0, hess_flops = 0.0;
 };
 
@@ -324,6 +325,7 @@ struct TcItem {
   bool want_opg = false, want_hess = false;
   float* opg = nullptr;
   float* hess = nullptr;
+  bool x3 = true;  // split-BF16 (three products) or BF16 (one)
 };
 
 hess_status tc_available(hess_mlp* h);

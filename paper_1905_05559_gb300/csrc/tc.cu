@@ -19,6 +19,9 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
+#include <functional>
+#include <map>
 #include <mutex>
 #include <type_traits>
 
@@ -851,6 +854,16 @@ double hcontract_flops(const Net& net, int64_t N, int jm, int jl, int64_t d0, in
 // Upper tiles of a P x P symmetric update with BM x BN tiles (the column
 // range reaches the diagonal), grouped by 8 tile rows so that concurrent tiles
 // share operand panels in L2.
+static int64_t syrk_tile_count(int64_t P, int BN) {
+  using namespace tc;
+  int64_t n = 0;
+  const int64_t mt = cdiv(P, BM), nt = cdiv(P, BN);
+  for (int64_t tn = 0; tn < nt; ++tn)
+    for (int64_t tm = 0; tm < mt; ++tm)
+      if (tn * BN + BN - 1 >= tm * BM) ++n;
+  return n;
+}
+
 static void syrk_tiles(int64_t P, int BN, int job, std::vector<int4>& tiles) {
   using namespace tc;
   const int64_t mt = cdiv(P, BM), nt = cdiv(P, BN);
@@ -985,12 +998,11 @@ static hess_status build_f(const tc::FArgs& fa, int p0, int np, int64_t ld, int 
 // Jobs of weight layer jm: W rows (u, i, q) for units [p0, p1) against the
 // W columns (mode 1); W and bias rows of units [q0, q0 + np) against the
 // columns after W (mode 2).
-static void wrow_job(const Net& net, int jm, int p0, int p1, int64_t R0, float* out, int64_t N, tc::Job& job,
-                     std::vector<int4>& tiles, int jid) {
+static void wrow_job(const Net& net, int jm, int p0, int p1, int64_t R0, float* out, int64_t N, int BN,
+                     tc::Job& job, std::vector<int4>& tiles, int jid) {
   using namespace tc;
   const int Tin = net.T[jm - 1], Tout = net.T[jm];
   const int64_t rows = rows_before(p1, Tin, Tout) - R0;
-  const int BN = pick_bn(Tin);
   job.BN = BN;
   job.M = rows;
   job.Nn = Tin;
@@ -1007,12 +1019,11 @@ static void wrow_job(const Net& net, int jm, int p0, int p1, int64_t R0, float* 
     for (int64_t tn = 0; tn < cdiv(Tin, BN); ++tn) tiles.push_back(make_int4(jid, (int)tm, (int)tn, 0));
 }
 
-static void f_job(const Net& net, int jm, int q0, int np, float* out, int64_t N, tc::Job& job,
+static void f_job(const Net& net, int jm, int q0, int np, float* out, int64_t N, int BN, tc::Job& job,
                   std::vector<int4>& tiles, int jid) {
   using namespace tc;
   const int Tin = net.T[jm - 1], Tout = net.T[jm];
   const int64_t boff = net.boff[jm - 1], rest = net.P - boff;
-  const int BN = pick_bn(rest);
   const int ntn = (int)cdiv(rest, BN);
   job.BN = BN;
   job.M = Tin + 1;
@@ -1041,6 +1052,117 @@ static double wrow_flops(int64_t Tin, int64_t Tout, int64_t p0, int64_t p1, int6
 }
 static double f_flops(int64_t Tin, int64_t rest, int64_t np, int64_t N) {
   return 2.0 * N * (double)np * (Tin + 1) * rest;
+}
+
+// ------------------------------------------------------------ autotuner --
+// Tile width of a contraction.  By default a cost model (pick_bn); with
+// tuning on, the first contraction of each shape (mode, columns, K blocks,
+// products) is timed alone at every candidate width on its real operands --
+// the output is written each time, with the same values -- and the fastest
+// width is kept for the process (and can be saved and loaded as a table).
+namespace {
+struct TuneKey {
+  int mode;
+  int64_t nn;
+  int nkb;
+  int x3;
+  bool operator<(const TuneKey& o) const {
+    if (mode != o.mode) return mode < o.mode;
+    if (nn != o.nn) return nn < o.nn;
+    if (nkb != o.nkb) return nkb < o.nkb;
+    return x3 < o.x3;
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned;
+std::atomic<int> g_tune_on{0};
+constexpr int kTuneCand[] = {64, 96, 128, 160, 192, 224, 256};
+struct TuneBuf {
+  tc::Job* jobs = nullptr;
+  int4* tiles = nullptr;
+  size_t cap = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+TuneBuf g_tune_buf;  // one per process (tuning is serialised by g_tune_mu)
+}  // namespace
+
+// The width for a contraction: tuned if known, else the cost model.
+// `*untuned` tells the caller that tuning is on and this shape has no entry.
+static int choose_bn(int mode, int64_t nn, int nkb, bool x3, bool* untuned) {
+  const TuneKey key{mode, nn, nkb, x3 ? 1 : 0};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      *untuned = false;
+      return it->second;
+    }
+  }
+  *untuned = g_tune_on.load() != 0;
+  return mode == 0 ? 256 : tc::pick_bn(nn);
+}
+
+// Builds the job and its tiles for a width (maps, fields, tile list).
+using JobBuilder = std::function<hess_status(int BN, tc::Job& job, std::vector<int4>& tiles)>;
+
+// Times the job alone at each candidate width and records the fastest.
+static hess_status tune_job(int sm_count, int mode, int64_t nn, int nkb, bool x3, const JobBuilder& build,
+                            PinnedStage& stage, int* err, cudaStream_t s, int* best_bn) {
+  const TuneKey key{mode, nn, nkb, x3 ? 1 : 0};
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto found = g_tuned.find(key);
+  if (found != g_tuned.end()) {
+    *best_bn = found->second;
+    return HESS_OK;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  HM_CUDA(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone) {  // no timing inside a graph capture
+    *best_bn = mode == 0 ? 256 : tc::pick_bn(nn);
+    return HESS_OK;
+  }
+  TuneBuf& b = g_tune_buf;
+  if (!b.e0) {
+    HM_CUDA(cudaEventCreate(&b.e0));
+    HM_CUDA(cudaEventCreate(&b.e1));
+  }
+  float best_ms = 1e30f;
+  int best = mode == 0 ? 256 : tc::pick_bn(nn);
+  for (int bn : kTuneCand) {
+    // a narrower candidate already covers every column in one tile
+    if (bn > kTuneCand[0] && bn - 32 >= (int64_t)align_up((size_t)nn, 16)) continue;
+    tc::Job job{};
+    std::vector<int4> tiles;
+    HM_TRY(build(bn, job, tiles));
+    for (int4& t : tiles) t.x = 0;  // the job runs alone: its table has one entry
+    const size_t need = tiles.size() + 1;
+    if (need > b.cap) {
+      HM_CUDA(cudaStreamSynchronize(s));
+      cudaFree(b.jobs);
+      cudaFree(b.tiles);
+      b.jobs = nullptr;
+      b.tiles = nullptr;
+      b.cap = 0;
+      HM_CUDA(cudaMalloc(&b.jobs, sizeof(tc::Job)));
+      HM_CUDA(cudaMalloc(&b.tiles, need * sizeof(int4)));
+      b.cap = need;
+    }
+    for (int rep = 0; rep < 2; ++rep) {  // the first run warms caches and tables
+      HM_CUDA(cudaEventRecord(b.e0, s));
+      HM_TRY(launch_jobs(sm_count, &job, 1, tiles.data(), (int)tiles.size(), b.jobs, b.tiles, x3, err, stage, s));
+      HM_CUDA(cudaEventRecord(b.e1, s));
+    }
+    HM_CUDA(cudaEventSynchronize(b.e1));
+    float ms = 0.f;
+    HM_CUDA(cudaEventElapsedTime(&ms, b.e0, b.e1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = bn;
+    }
+  }
+  g_tuned[key] = best;
+  *best_bn = best;
+  return HESS_OK;
 }
 
 hess_status tc_prep(hess_mlp* h, const TcItem& it, Arena& ar, bool live, TcPlan& plan, cudaStream_t s) {
@@ -1072,17 +1194,26 @@ hess_status tc_prep(hess_mlp* h, const TcItem& it, Arena& ar, bool live, TcPlan&
           G, N, P, P, hi, lo, ld);
       HM_LAUNCHED();
     }
+    const int jid = (int)plan.jobs.size();
+    JobBuilder build = [&](int BN, Job& job, std::vector<int4>& tl) -> hess_status {
+      if (live) HM_TRY(make_job(TcOperands{hi, lo, P, hi, lo, P, ld}, BN, &job));
+      job.BN = BN;
+      job.M = P;
+      job.Nn = P;
+      job.scale = 1.0f / (float)N;
+      job.out = it.opg;
+      job.ldo = P;
+      job.mode = 0;
+      syrk_tiles(P, BN, jid, tl);
+      return HESS_OK;
+    };
+    bool untuned = false;
+    int BN = choose_bn(0, P, (int)(ld / BK), it.x3, &untuned);
+    if (live && untuned) HM_TRY(tune_job(h->sm_count, 0, P, (int)(ld / BK), it.x3, build, h->stage, h->err_dev, s, &BN));
     Job job{};
-    if (live) HM_TRY(make_job(TcOperands{hi, lo, P, hi, lo, P, ld}, 256, &job));
-    job.BN = 256;
-    job.M = P;
-    job.Nn = P;
-    job.scale = 1.0f / (float)N;
-    job.out = it.opg;
-    job.ldo = P;
-    job.mode = 0;
-    syrk_tiles(P, 256, (int)plan.jobs.size(), plan.tiles);
+    HM_TRY(build(BN, job, plan.tiles));
     plan.jobs.push_back(job);
+    plan.tiles_cap += syrk_tile_count(P, kTuneCand[0]);
   }
   if (it.want_hess) {
     // exact Hessian (Sec. 3, Eq. for H_ij) from the R-operator over the bias
@@ -1121,15 +1252,37 @@ hess_status tc_prep(hess_mlp* h, const TcItem& it, Arena& ar, bool live, TcPlan&
         HM_TRY(build_wrows(net, tq, jm, Tout, 0, ld, h->sm_count, ahi, alo, s));
         HM_TRY(build_f(fa, 0, Tout, ld, h->sm_count, fhi, flo, s));
       }
-      Job jw{}, jf{};
-      if (live) {
-        HM_TRY(make_job(TcOperands{ahi, alo, rows, bhi, blo, Tin, ld}, pick_bn(Tin), &jw));
-        HM_TRY(make_job(TcOperands{bhi, blo, Tin + 1, fhi, flo, (int64_t)Tout * rest, ld}, pick_bn(rest), &jf));
+      const int nkb = (int)(ld / BK);
+      {
+        const int jid = (int)plan.jobs.size();
+        JobBuilder build = [&](int BN, Job& job, std::vector<int4>& tl) -> hess_status {
+          if (live) HM_TRY(make_job(TcOperands{ahi, alo, rows, bhi, blo, Tin, ld}, BN, &job));
+          wrow_job(net, jm, 0, Tout, 0, it.hess, N, BN, job, tl, jid);
+          return HESS_OK;
+        };
+        bool untuned = false;
+        int BN = choose_bn(1, Tin, nkb, it.x3, &untuned);
+        if (live && untuned) HM_TRY(tune_job(h->sm_count, 1, Tin, nkb, it.x3, build, h->stage, h->err_dev, s, &BN));
+        Job jw{};
+        HM_TRY(build(BN, jw, plan.tiles));
+        plan.jobs.push_back(jw);
+        plan.tiles_cap += cdiv(rows, BM) * cdiv(Tin, kTuneCand[0]);
       }
-      wrow_job(net, jm, 0, Tout, 0, it.hess, N, jw, plan.tiles, (int)plan.jobs.size());
-      plan.jobs.push_back(jw);
-      f_job(net, jm, 0, Tout, it.hess, N, jf, plan.tiles, (int)plan.jobs.size());
-      plan.jobs.push_back(jf);
+      {
+        const int jid = (int)plan.jobs.size();
+        JobBuilder build = [&](int BN, Job& job, std::vector<int4>& tl) -> hess_status {
+          if (live) HM_TRY(make_job(TcOperands{bhi, blo, Tin + 1, fhi, flo, (int64_t)Tout * rest, ld}, BN, &job));
+          f_job(net, jm, 0, Tout, it.hess, N, BN, job, tl, jid);
+          return HESS_OK;
+        };
+        bool untuned = false;
+        int BN = choose_bn(2, rest, nkb, it.x3, &untuned);
+        if (live && untuned) HM_TRY(tune_job(h->sm_count, 2, rest, nkb, it.x3, build, h->stage, h->err_dev, s, &BN));
+        Job jf{};
+        HM_TRY(build(BN, jf, plan.tiles));
+        plan.jobs.push_back(jf);
+        plan.tiles_cap += cdiv(Tin + 1, BM) * (int64_t)Tout * cdiv(rest, kTuneCand[0]);
+      }
     }
   }
   return HESS_OK;
@@ -1138,8 +1291,11 @@ hess_status tc_prep(hess_mlp* h, const TcItem& it, Arena& ar, bool live, TcPlan&
 hess_status tc_launch_plan(int sm_count, const TcPlan& plan, Arena& ar, bool live, bool x3, int* err,
                            PinnedStage& stage, cudaStream_t s) {
   using namespace tc;
+  // room for the tile list at any candidate width, so that a planning pass
+  // (before tuning) lays out enough
+  const size_t nt = plan.tiles.size() > (size_t)plan.tiles_cap ? plan.tiles.size() : (size_t)plan.tiles_cap;
   tc::Job* jd = ar.take<tc::Job>(plan.jobs.size() ? plan.jobs.size() : 1);
-  int4* td = ar.take<int4>(plan.tiles.size() ? plan.tiles.size() : 1);
+  int4* td = ar.take<int4>(nt ? nt : 1);
   if (!live || plan.tiles.empty()) return HESS_OK;
   // longest tiles first (K and tile width), so that a static round-robin over
   // the CTAs ends with short tiles; the stable order keeps each job's L2
@@ -1192,7 +1348,7 @@ static hess_status run_single(hess_mlp* h, const void* X, const void* Y, int64_t
     Staged d;
     HM_TRY(stage(h, ar, live, X, Y, out, N, st, d));
     split = ar.take<char>(kSplitBytes);
-    TcItem it{d.X, d.Y, N, kind == 0, kind == 1, kind == 0 ? d.out : nullptr, kind == 1 ? d.out : nullptr};
+    TcItem it{d.X, d.Y, N, kind == 0, kind == 1, kind == 0 ? d.out : nullptr, kind == 1 ? d.out : nullptr, x3};
     SplitGuard sg(split, kSplitBytes, h->sm_count);
     HM_TRY(tc_prep(h, it, ar, live, plan, s));
     Tick t(live ? h : nullptr, kind == 0 ? HESS_K_SYRK : HESS_K_HCONTRACT,
@@ -1323,10 +1479,11 @@ hess_status run_hessian_chunked(hess_mlp* h, const void* X, const void* Y, int64
       const int64_t R0 = rows_before(p0, Tin, Tout);
       HM_TRY(build_wrows(net, tq, jm, p1, R0, ld, h->sm_count, ahi, alo, s));
       Job job{};
-      HM_TRY(make_job(TcOperands{ahi, alo, rows_before(p1, Tin, Tout) - R0, bhi, blo, Tin, ld}, pick_bn(Tin),
-                      &job));
+      bool untuned = false;
+      const int BN = choose_bn(1, Tin, (int)(ld / BK), x3, &untuned);
+      HM_TRY(make_job(TcOperands{ahi, alo, rows_before(p1, Tin, Tout) - R0, bhi, blo, Tin, ld}, BN, &job));
       tiles.clear();
-      wrow_job(net, jm, p0, p1, R0, O, N, job, tiles, 0);
+      wrow_job(net, jm, p0, p1, R0, O, N, BN, job, tiles, 0);
       {
         Tick t(h, HESS_K_HCONTRACT, wrow_flops(Tin, Tout, p0, p1, N), 0.0);
         HM_TRY(launch_jobs(h->sm_count, &job, 1, tiles.data(), (int)tiles.size(), jd, tl, x3, h->err_dev, h->stage, s));
@@ -1340,9 +1497,11 @@ hess_status run_hessian_chunked(hess_mlp* h, const void* X, const void* Y, int64
       const int pc = Tout - q0 < pchunk ? Tout - q0 : pchunk;
       HM_TRY(build_f(fa, q0, pc, ld, h->sm_count, fhi, flo, s));
       Job job{};
-      HM_TRY(make_job(TcOperands{bhi, blo, Tin + 1, fhi, flo, (int64_t)pc * rest, ld}, pick_bn(rest), &job));
+      bool untuned = false;
+      const int BN = choose_bn(2, rest, (int)(ld / BK), x3, &untuned);
+      HM_TRY(make_job(TcOperands{bhi, blo, Tin + 1, fhi, flo, (int64_t)pc * rest, ld}, BN, &job));
       tiles.clear();
-      f_job(net, jm, q0, pc, O, N, job, tiles, 0);
+      f_job(net, jm, q0, pc, O, N, BN, job, tiles, 0);
       {
         Tick t(h, HESS_K_HCONTRACT, f_flops(Tin, rest, pc, N), 0.0);
         HM_TRY(launch_jobs(h->sm_count, &job, 1, tiles.data(), (int)tiles.size(), jd, tl, x3, h->err_dev, h->stage, s));
@@ -1373,3 +1532,55 @@ hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N,
 }
 
 }  // namespace hm
+
+extern "C" {
+
+hess_status hess_autotune(int enable) {
+  hm::clear_error();
+  hm::g_tune_on.store(enable ? 1 : 0);
+  return HESS_OK;
+}
+
+int hess_autotune_entries(void) {
+  std::lock_guard<std::mutex> lk(hm::g_tune_mu);
+  return (int)hm::g_tuned.size();
+}
+
+hess_status hess_autotune_save(const char* path) {
+  hm::clear_error();
+  if (!path) return hm::set_error(HESS_ERR_INVALID_ARG, "path is NULL");
+  std::lock_guard<std::mutex> lk(hm::g_tune_mu);
+  FILE* f = fopen(path, "w");
+  if (!f) return hm::set_error(HESS_ERR_INVALID_ARG, "cannot write %s", path);
+  fprintf(f, "# mode columns kblocks products3 width\n");
+  for (const auto& kv : hm::g_tuned)
+    fprintf(f, "%d %lld %d %d %d\n", kv.first.mode, (long long)kv.first.nn, kv.first.nkb, kv.first.x3, kv.second);
+  fclose(f);
+  return HESS_OK;
+}
+
+hess_status hess_autotune_load(const char* path) {
+  hm::clear_error();
+  if (!path) return hm::set_error(HESS_ERR_INVALID_ARG, "path is NULL");
+  FILE* f = fopen(path, "r");
+  if (!f) return hm::set_error(HESS_ERR_INVALID_ARG, "cannot read %s", path);
+  std::lock_guard<std::mutex> lk(hm::g_tune_mu);
+  char line[256];
+  int bad = 0;
+  while (fgets(line, sizeof line, f)) {
+    if (line[0] == '#' || line[0] == '\n') continue;
+    int mode, nkb, x3, bn;
+    long long nn;
+    if (sscanf(line, "%d %lld %d %d %d", &mode, &nn, &nkb, &x3, &bn) != 5 || mode < 0 || mode > 2 || bn < 16 ||
+        bn > 256 || bn % 16 || nn < 1 || nkb < 1) {
+      ++bad;
+      continue;
+    }
+    hm::g_tuned[hm::TuneKey{mode, (int64_t)nn, nkb, x3 ? 1 : 0}] = bn;
+  }
+  fclose(f);
+  if (bad) return hm::set_error(HESS_ERR_INVALID_ARG, "%d malformed lines in %s", bad, path);
+  return HESS_OK;
+}
+
+}  // extern "C"

@@ -89,3 +89,20 @@ def test_batch_entry_points_reject_bad_arguments_before_touching_cuda(lib):
     assert lib.hess_batch_run(None, None, 0, 3, ctypes.byref(info)) == _lib.HESS_ERR_INVALID_ARG
     assert lib.hess_batch_destroy(None) == _lib.HESS_OK
     assert lib.hess_mlp_set_operand_limit(None, 1 << 30) == _lib.HESS_ERR_INVALID_ARG
+
+
+def test_autotune_table_load_and_save_on_cpu(lib, tmp_path):
+    from paper_1905_05559_gb300 import _lib
+    good = tmp_path / "table.txt"
+    good.write_text("# mode columns kblocks products3 width\n0 12730 16 1 192\n2 186 16 1 96\n")
+    n0 = lib.hess_autotune_entries()
+    assert lib.hess_autotune_load(str(good).encode()) == _lib.HESS_OK
+    assert lib.hess_autotune_entries() == n0 + 2
+    out = tmp_path / "saved.txt"
+    assert lib.hess_autotune_save(str(out).encode()) == _lib.HESS_OK
+    lines = [ln for ln in out.read_text().splitlines() if not ln.startswith("#")]
+    assert "0 12730 16 1 192" in lines and "2 186 16 1 96" in lines
+    bad = tmp_path / "bad.txt"
+    bad.write_text("0 100 4 1 200\nnot a line\n")  # 200 is not a multiple of 16
+    assert lib.hess_autotune_load(str(bad).encode()) == _lib.HESS_ERR_INVALID_ARG
+    assert lib.hess_autotune_load(str(tmp_path / "missing.txt").encode()) == _lib.HESS_ERR_INVALID_ARG
