@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--batch", action="store_true",
                     help="the many-networks workload: OPG + exact Hessian of 256 networks in waves")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--batch-graphs", action="store_true",
+                    help="replay each group of the batch from a CUDA graph (use --warmup >= 2)")
     ap.add_argument("--autotune", action="store_true",
                     help="tune the tensor-core tile widths during the warm-up steps")
     ap.add_argument("--batch-workspace-gb", type=float, default=64.0)
@@ -336,6 +338,8 @@ def batch_bench(args):
         used += need
     groups.append(cur)
     batch = hm.HessBatch(int(args.batch_workspace_gb * (1 << 30)), stream=stream.cuda_stream)
+    if args.batch_graphs:
+        batch.set_graphs(True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     rng = np.random.default_rng(3)
 
@@ -368,7 +372,7 @@ def batch_bench(args):
 
     def one_pass(do_check):
         ms = launch_ms = flops = 0.0
-        waves = chunked = 0
+        waves = chunked = replayed = 0
         worst = 0.0
         for g in groups:
             outs = group_outputs(g)
@@ -383,10 +387,11 @@ def batch_bench(args):
             flops += info["flops"]
             waves += info["waves"]
             chunked += info["items_chunked"]
+            replayed += int(info["graph_replayed"])
             if do_check:
                 for i, (o, h) in zip(g, outs):
                     worst = max(worst, check(i, o, h))
-        return ms, launch_ms, flops, waves, chunked, worst
+        return ms, launch_ms, flops, waves, chunked, worst, replayed
 
     if args.autotune:
         hm.autotune(True)
@@ -417,6 +422,8 @@ def batch_bench(args):
                    "networks": args.batch_count, "groups": len(groups), "waves": waves,
                    "tile_widths": (f"autotuned ({hm.autotune_entries()} shapes)" if args.autotune
                                    else "cost model"),
+                   "cuda_graphs": (f"{runs[-1][6]} of {len(groups)} groups replayed" if args.batch_graphs
+                                   else "off"),
                    "items_alone": chunked,
                    "workspace_gb": args.batch_workspace_gb, "output_pool_gb": args.batch_out_gb,
                    "l2": "outputs and operands far larger than L2"},

@@ -280,6 +280,7 @@ typedef struct {
   int64_t tiles;      /* output tiles of the wave launches */
   double flops;       /* tensor-core flops of the wave launches (3 products for BF16X3) */
   double launch_ms;   /* summed device time of the wave launches (CUDA events) */
+  int graph_replayed; /* 1 when the run replayed a captured CUDA graph */
 } hess_batch_info;
 
 /* workspace_bytes: device memory the batch allocates now and reuses for every
@@ -296,6 +297,15 @@ HESS_API hess_status hess_batch_create(int64_t workspace_bytes, void* stream, he
  * TIMEOUT (a pipeline wait of the tensor-core kernel gave up). */
 HESS_API hess_status hess_batch_run(hess_batch* b, const hess_batch_item* items, int count,
                                     hess_precision prec, hess_batch_info* info);
+
+/* CUDA graphs for repeated runs (off by default).  With graphs on, the second
+ * run of an item list (the same handles, buffers, N and precision; buffer
+ * contents may change) captures all of its waves -- every forward/backward
+ * pass, operand builder and persistent launch -- into one CUDA graph, and
+ * later runs of that list replay it with a single launch.  The graphs of the
+ * 8 most recently used lists are kept.  Lists with an item too large for the
+ * workspace run directly.  Errors: INVALID_ARG, CUDA. */
+HESS_API hess_status hess_batch_set_graphs(hess_batch* b, int enable);
 
 /* Waits for the batch stream and releases the workspace.  NULL is ignored. */
 HESS_API hess_status hess_batch_destroy(hess_batch* b);

@@ -36,6 +36,7 @@ EXPORTS = (
     "hess_server_add_network", "hess_server_submit", "hess_server_wait", "hess_server_destroy",
     "hess_mlp_set_operand_limit", "hess_batch_create", "hess_batch_run", "hess_batch_destroy",
     "hess_autotune", "hess_autotune_entries", "hess_autotune_save", "hess_autotune_load",
+    "hess_batch_set_graphs",
 )
 
 REQUEST_KIND = {"hessian": 0, "opg": 1, "eig": 2}
@@ -55,7 +56,7 @@ class BatchItem(ctypes.Structure):
 class BatchInfo(ctypes.Structure):
     _fields_ = [("waves", ctypes.c_int), ("items_chunked", ctypes.c_int),
                 ("tiles", ctypes.c_int64), ("flops", ctypes.c_double),
-                ("launch_ms", ctypes.c_double)]
+                ("launch_ms", ctypes.c_double), ("graph_replayed", ctypes.c_int)]
 
 
 KERNEL_CLASS = {"syrk": 0, "hcontract": 1, "grads": 2, "rop": 3, "eig": 4, "hrest": 5}
@@ -133,6 +134,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.hess_batch_run.argtypes = [vp, ctypes.POINTER(BatchItem), ctypes.c_int, ctypes.c_int,
                                    ctypes.POINTER(BatchInfo)]
     lib.hess_batch_run.restype = st
+    lib.hess_batch_set_graphs.argtypes = [vp, ctypes.c_int]
+    lib.hess_batch_set_graphs.restype = st
     lib.hess_batch_destroy.argtypes = [vp]
     lib.hess_batch_destroy.restype = st
     lib.hess_autotune.argtypes = [ctypes.c_int]

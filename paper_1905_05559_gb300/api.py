@@ -188,7 +188,12 @@ class HessBatch:
         _lib.check(self._lib.hess_batch_run(self.b, arr, len(items), _lib.PRECISION[prec],
                                             ctypes.byref(info)))
         return {"waves": info.waves, "items_chunked": info.items_chunked, "tiles": info.tiles,
-                "flops": info.flops, "launch_ms": info.launch_ms}
+                "flops": info.flops, "launch_ms": info.launch_ms,
+                "graph_replayed": bool(info.graph_replayed)}
+
+    def set_graphs(self, enable: bool):
+        """Capture repeated runs of the same item list in a CUDA graph."""
+        _lib.check(self._lib.hess_batch_set_graphs(self.b, 1 if enable else 0))
 
     def close(self):
         if getattr(self, "b", None):

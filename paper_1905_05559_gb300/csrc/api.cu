@@ -49,7 +49,12 @@ hess_status set_error(hess_status s, const char* fmt, ...) {
   va_end(ap);
   return s;
 }
-void clear_error() { g_err[0] = 0; }
+// Every entry point starts here: a stale, non-sticky CUDA error left by
+// someone else's call on this thread must not be reported as this call's.
+void clear_error() {
+  g_err[0] = 0;
+  cudaGetLastError();
+}
 
 hess_status make_net(const hess_mlp_desc* desc, Net* out) {
   if (!desc) return set_error(HESS_ERR_INVALID_ARG, "desc is NULL");
@@ -133,7 +138,12 @@ hess_status stage_copy(PinnedStage& st, const void* const* src, const size_t* by
     HM_CUDA(cudaMemcpyAsync(dst[i], st.p + off, bytes[i], cudaMemcpyHostToDevice, s));
     off += align_up(bytes[i], 256);
   }
-  HM_CUDA(cudaEventRecord(st.ev, s));
+  // inside a graph capture the record becomes a node of the graph
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  HM_CUDA(cudaStreamIsCapturing(s, &cs));
+  HM_CUDA(cudaEventRecordWithFlags(st.ev, s,
+                                   cs == cudaStreamCaptureStatusNone ? cudaEventRecordDefault
+                                                                     : cudaEventRecordExternal));
   return HESS_OK;
 }
 
@@ -144,6 +154,7 @@ void stage_free(PinnedStage& st) {
   }
   if (st.p) cudaFreeHost(st.p);
   st = PinnedStage{};
+  cudaGetLastError();
 }
 
 hess_status ensure_ws(hess_mlp* h, size_t bytes) {

@@ -13,12 +13,28 @@
 //     handle's operand limit);
 //   * the per-tile arithmetic does not depend on the schedule, so every matrix
 //     is bit-identical to what the single-network call returns.
+#include <algorithm>
+
 #include "internal.h"
 
 struct hess_batch {
   int device = 0;
   int sm_count = 0;
   cudaStream_t stream = nullptr;
+  // CUDA-graph replay of repeated runs (same items and precision)
+  struct GraphEntry {
+    std::vector<hess_batch_item> items;
+    int prec = -1;
+    int seen = 0;                        // runs of this list so far
+    cudaGraphExec_t exec = nullptr;
+    std::vector<hm::PinnedStage> stages; // the graph's table copies read these
+    hess_batch_info info{};
+    int64_t kernels = 0;                 // kernels in the graph
+    bool capturable = true;
+  };
+  bool graphs = false;
+  cudaStream_t cap_stream = nullptr;     // capture stream (never the legacy one)
+  std::vector<GraphEntry> cache;         // most recently used last
   char* ws = nullptr;
   size_t ws_bytes = 0;
   int* err_host = nullptr;  // mapped pinned error flag of the tensor-core kernels
@@ -88,6 +104,183 @@ hess_status run_alone(hess_batch* b, const hess_batch_item& it, hess_precision p
   return st;
 }
 
+// Queues every wave of the run on stream s.  While capturing (stages given),
+// each wave copies its tables from its own pinned buffer, which the graph
+// keeps; an item too large for the workspace cannot be captured
+// (HESS_ERR_UNSUPPORTED, nothing else queued).
+hess_status enqueue_waves(hess_batch* b, const hess_batch_item* items, int count, hess_precision prec,
+                          cudaStream_t s, std::vector<PinnedStage>* stages, hess_batch_info* infp) {
+  hess_batch_info& inf = *infp;
+  const bool x3 = prec == HESS_BF16X3;
+    // fixed head of the workspace: split-K scratch
+    Arena head{b->ws, 0};
+    char* split = head.take<char>(kSplitBytes);
+    const size_t base = align_up(head.off, 256);
+    SplitGuard sg(split, kSplitBytes, b->sm_count);
+    int i = 0;
+    while (i < count) {
+      // gather the wave
+      size_t used = base, njobs = 0, ntiles = 0;
+      int j = i;
+      while (j < count) {
+        TcPlan one;
+        const size_t need = item_bytes(items[j], one);
+        const size_t nj = njobs + one.jobs.size(), nt = ntiles + one.tiles.size();
+        if (used + need + table_bytes(nj, nt) > b->ws_bytes) break;
+        used += need;
+        njobs = nj;
+        ntiles = nt;
+        ++j;
+      }
+      if (j == i) {
+        // too large for the workspace: alone, through the single-network calls
+        if (stages) return HESS_ERR_UNSUPPORTED;
+        HM_TRY(run_alone(b, items[i], prec));
+        ++inf.items_chunked;
+        ++i;
+        continue;
+      }
+      TcPlan plan;
+      Arena ar{b->ws, base};
+      for (int q = i; q < j; ++q) {
+        const hess_batch_item& it = items[q];
+        TcItem ti{it.X, it.Y, it.N, it.opg != nullptr, it.hessian != nullptr, it.opg, it.hessian, x3};
+        const size_t at = ar.off;
+        HM_TRY(tc_prep(it.net, ti, ar, true, plan, s));
+        ar.off = at + align_up(ar.off - at, 256);
+      }
+      const size_t e0 = 2 * (size_t)inf.waves;
+      while (b->events.size() < e0 + 2) {
+        cudaEvent_t e;
+        HM_CUDA(cudaEventCreate(&e));
+        b->events.push_back(e);
+      }
+      // inside a capture the records become graph nodes (external records)
+      const unsigned rec = stages ? cudaEventRecordExternal : cudaEventRecordDefault;
+      HM_CUDA(cudaEventRecordWithFlags(b->events[e0], s, rec));
+      PinnedStage* st = &b->stage;
+      if (stages) {
+        stages->emplace_back();
+        st = &stages->back();
+      }
+      HM_TRY(tc_launch_plan(b->sm_count, plan, ar, true, x3, b->err_dev, *st, s));
+      HM_CUDA(cudaEventRecordWithFlags(b->events[e0 + 1], s, rec));
+      inf.tiles += (int64_t)plan.tiles.size();
+      inf.flops += (plan.syrk_flops + plan.hess_flops) * (x3 ? 3.0 : 1.0);
+      ++inf.waves;
+      i = j;
+    }
+  return HESS_OK;
+}
+
+constexpr size_t kGraphCache = 8;  // item lists with a graph kept at once
+
+bool same_items(const hess_batch::GraphEntry& g, const hess_batch_item* items, int count, hess_precision prec) {
+  if ((int)g.items.size() != count || g.prec != (int)prec) return false;
+  for (int i = 0; i < count; ++i) {
+    const hess_batch_item& x = g.items[i];
+    const hess_batch_item& y = items[i];
+    if (x.net != y.net || x.X != y.X || x.Y != y.Y || x.N != y.N || x.opg != y.opg || x.hessian != y.hessian)
+      return false;
+  }
+  return true;
+}
+
+void drop_entry(hess_batch::GraphEntry& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  g.exec = nullptr;
+  for (auto& st : g.stages) stage_free(st);
+  g.stages.clear();
+}
+
+void drop_graphs(hess_batch* b) {
+  for (auto& g : b->cache) drop_entry(g);
+  b->cache.clear();
+}
+
+// Captures the run's waves into a graph (on the capture stream, ordered
+// after the user's stream).  HESS_ERR_UNSUPPORTED: the list cannot be
+// captured (an item runs alone); nothing was queued.
+hess_status capture(hess_batch* b, hess_batch::GraphEntry& g, const hess_batch_item* items, int count,
+                    hess_precision prec) {
+  cudaEvent_t dep;
+  HM_CUDA(cudaEventCreateWithFlags(&dep, cudaEventDisableTiming));
+  cudaEventRecord(dep, b->stream);
+  cudaStreamWaitEvent(b->cap_stream, dep, 0);
+  cudaEventDestroy(dep);
+  HM_CUDA(cudaStreamSynchronize(b->cap_stream));
+  std::vector<PinnedStage> stages;
+  hess_batch_info ci{};
+  const int64_t l0 = g_launches.load();
+  // relaxed: the waves allocate their pinned table buffers while capturing
+  HM_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeRelaxed));
+  hess_status st = enqueue_waves(b, items, count, prec, b->cap_stream, &stages, &ci);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(b->cap_stream, &graph);
+  // captured kernels run when the graph does: count them then
+  const int64_t kernels = g_launches.load() - l0;
+  g_launches -= kernels;
+  if (st != HESS_OK || ec != cudaSuccess || !graph) {
+    cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    for (auto& x : stages) stage_free(x);
+    if (st != HESS_OK) return st;
+    return set_error(HESS_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ec));
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    cudaGetLastError();
+    for (auto& x : stages) stage_free(x);
+    g.exec = nullptr;
+    return set_error(HESS_ERR_CUDA, "graph instantiation: %s", cudaGetErrorString(ei));
+  }
+  g.stages = std::move(stages);
+  g.info = ci;
+  g.kernels = kernels;
+  return HESS_OK;
+}
+
+// One run: directly, or (graphs on, a list seen before) through its graph,
+// captured on the second run of the list and replayed afterwards.
+hess_status run_batch(hess_batch* b, const hess_batch_item* items, int count, hess_precision prec,
+                      hess_batch_info* inf) {
+  if (!b->graphs) return enqueue_waves(b, items, count, prec, b->stream, nullptr, inf);
+  size_t at = b->cache.size();
+  for (size_t i = 0; i < b->cache.size(); ++i)
+    if (same_items(b->cache[i], items, count, prec)) at = i;
+  if (at == b->cache.size()) {
+    if (b->cache.size() >= kGraphCache) {
+      drop_entry(b->cache.front());
+      b->cache.erase(b->cache.begin());
+    }
+    hess_batch::GraphEntry g;
+    g.items.assign(items, items + count);
+    g.prec = (int)prec;
+    b->cache.push_back(std::move(g));
+    at = b->cache.size() - 1;
+  } else if (at + 1 != b->cache.size()) {
+    std::rotate(b->cache.begin() + at, b->cache.begin() + at + 1, b->cache.end());  // most recent last
+    at = b->cache.size() - 1;
+  }
+  hess_batch::GraphEntry& g = b->cache[at];
+  ++g.seen;
+  if (g.seen < 2 || !g.capturable) return enqueue_waves(b, items, count, prec, b->stream, nullptr, inf);
+  if (!g.exec) {
+    const hess_status st = capture(b, g, items, count, prec);
+    if (st == HESS_ERR_UNSUPPORTED) {
+      g.capturable = false;
+      return enqueue_waves(b, items, count, prec, b->stream, nullptr, inf);
+    }
+    HM_TRY(st);
+  }
+  HM_CUDA(cudaGraphLaunch(g.exec, b->stream));
+  g_launches += g.kernels;
+  *inf = g.info;
+  inf->graph_replayed = 1;
+  return HESS_OK;
+}
+
 }  // namespace
 }  // namespace hm
 
@@ -121,6 +314,10 @@ hess_status hess_batch_create(int64_t workspace_bytes, void* stream, hess_batch*
   }
   b->ws_bytes = (size_t)workspace_bytes;
   *b->err_host = 0;
+  if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    b->cap_stream = nullptr;  // graphs stay unavailable
+  }
   *out = b;
   return HESS_OK;
 }
@@ -137,59 +334,8 @@ hess_status hess_batch_run(hess_batch* b, const hess_batch_item* items, int coun
   hess_batch_info inf{};
   if (count > 0) {
     HM_TRY(tc_available(items[0].net));
-    const bool x3 = prec == HESS_BF16X3;
-    cudaStream_t s = b->stream;
-    // fixed head of the workspace: split-K scratch
-    Arena head{b->ws, 0};
-    char* split = head.take<char>(kSplitBytes);
-    const size_t base = align_up(head.off, 256);
-    SplitGuard sg(split, kSplitBytes, b->sm_count);
-    int i = 0;
-    while (i < count) {
-      // gather the wave
-      size_t used = base, njobs = 0, ntiles = 0;
-      int j = i;
-      while (j < count) {
-        TcPlan one;
-        const size_t need = item_bytes(items[j], one);
-        const size_t nj = njobs + one.jobs.size(), nt = ntiles + one.tiles.size();
-        if (used + need + table_bytes(nj, nt) > b->ws_bytes) break;
-        used += need;
-        njobs = nj;
-        ntiles = nt;
-        ++j;
-      }
-      if (j == i) {
-        // too large for the workspace: alone, through the single-network calls
-        HM_TRY(run_alone(b, items[i], prec));
-        ++inf.items_chunked;
-        ++i;
-        continue;
-      }
-      TcPlan plan;
-      Arena ar{b->ws, base};
-      for (int q = i; q < j; ++q) {
-        const hess_batch_item& it = items[q];
-        TcItem ti{it.X, it.Y, it.N, it.opg != nullptr, it.hessian != nullptr, it.opg, it.hessian, x3};
-        const size_t at = ar.off;
-        HM_TRY(tc_prep(it.net, ti, ar, true, plan, s));
-        ar.off = at + align_up(ar.off - at, 256);
-      }
-      const size_t e0 = 2 * (size_t)inf.waves;
-      while (b->events.size() < e0 + 2) {
-        cudaEvent_t e;
-        HM_CUDA(cudaEventCreate(&e));
-        b->events.push_back(e);
-      }
-      HM_CUDA(cudaEventRecord(b->events[e0], s));
-      HM_TRY(tc_launch_plan(b->sm_count, plan, ar, true, x3, b->err_dev, b->stage, s));
-      HM_CUDA(cudaEventRecord(b->events[e0 + 1], s));
-      inf.tiles += (int64_t)plan.tiles.size();
-      inf.flops += (plan.syrk_flops + plan.hess_flops) * (x3 ? 3.0 : 1.0);
-      ++inf.waves;
-      i = j;
-    }
-    HM_CUDA(cudaStreamSynchronize(s));
+    HM_TRY(run_batch(b, items, count, prec, &inf));
+    HM_CUDA(cudaStreamSynchronize(b->stream));
     if (*(volatile int*)b->err_host) {
       *(volatile int*)b->err_host = 0;
       return set_error(HESS_ERR_TIMEOUT, "a tensor-core pipeline wait gave up");
@@ -204,10 +350,22 @@ hess_status hess_batch_run(hess_batch* b, const hess_batch_item* items, int coun
   return HESS_OK;
 }
 
+hess_status hess_batch_set_graphs(hess_batch* b, int enable) {
+  clear_error();
+  if (!b) return set_error(HESS_ERR_INVALID_ARG, "batch is NULL");
+  if (enable && !b->cap_stream) return set_error(HESS_ERR_CUDA, "no capture stream");
+  Guard g(b->device);
+  if (!enable) drop_graphs(b);
+  b->graphs = enable != 0;
+  return HESS_OK;
+}
+
 hess_status hess_batch_destroy(hess_batch* b) {
   if (!b) return HESS_OK;
   Guard g(b->device);
   cudaStreamSynchronize(b->stream);
+  drop_graphs(b);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   for (cudaEvent_t e : b->events) cudaEventDestroy(e);
   cudaFree(b->ws);
   cudaFreeHost(b->err_host);

@@ -8,6 +8,8 @@
   single-network call.
 * The chunked Hessian schedule (a small operand limit) gives the same bits as
   the one-launch schedule.
+* CUDA-graph replay of a repeated item list gives the same bits as direct
+  runs and reads the buffers' current contents.
 """
 
 import numpy as np
@@ -129,3 +131,34 @@ def test_batch_rejects_bad_items(hm):
         b.run([(net, X, Y, o, None)], "fp32")
     with pytest.raises(hm.HessError, match="no output"):
         b.run([(net, X, Y, None, None)])
+
+
+def test_batch_graph_replay(hm):
+    pbs = [make_problem(w, a, n, s, "normal", "uniform") for (w, a, n, s) in SMALL[:4]]
+    nets = [hm.HessMLP(pb.widths, pb.acts, pb.omega) for pb in pbs]
+    Xs = [dev(pb.X) for pb in pbs]
+    Ys = [dev(pb.Y) for pb in pbs]
+    outs = [(torch.empty((pb.P, pb.P), device="cuda"), torch.empty((pb.P, pb.P), device="cuda"))
+            for pb in pbs]
+    items = [(n, x, y, o, h) for n, x, y, (o, h) in zip(nets, Xs, Ys, outs)]
+    direct = hm.HessBatch(256 << 20)
+    direct.run(items, "bf16x3")
+    ref = [(o.clone(), h.clone()) for o, h in outs]
+    b = hm.HessBatch(256 << 20)
+    b.set_graphs(True)
+    infos = []
+    for _ in range(3):  # direct, capture + launch, replay
+        for o, h in outs:
+            o.fill_(float("nan"))
+            h.fill_(float("nan"))
+        infos.append(b.run(items, "bf16x3"))
+        for (o, h), (ro, rh) in zip(outs, ref):
+            assert torch.equal(o, ro) and torch.equal(h, rh)
+    assert [i["graph_replayed"] for i in infos] == [False, True, True]
+    assert infos[2]["waves"] == infos[0]["waves"]
+    # the graph reads the buffers' current contents
+    Xs[0].mul_(0.5)
+    b.run(items, "bf16x3")
+    o2 = outs[0][0].clone()
+    direct.run(items, "bf16x3")
+    assert torch.equal(o2, outs[0][0]) and not torch.equal(o2, ref[0][0])
