@@ -220,10 +220,13 @@ __host__ __device__ __forceinline__ int64_t rows_before(int64_t p, int64_t Tin, 
 // are the directions W_(u,q) and the product column n is the n-th Hessian
 // column from the layer's bias on.
 // Unit u of concatenated W row r: rows_before(u) <= r < rows_before(u + 1)
-// (the root of the quadratic rows_before, then corrected by whole steps).
+// (the root of the quadratic rows_before as an FP32 estimate -- FP64 is slow
+// on this GPU and the estimate only needs to be near -- then corrected by
+// whole steps in integer arithmetic).
 __device__ __forceinline__ int64_t wrow_unit(int64_t r, int64_t Tin, int64_t Tout) {
-  const double b = 2.0 * Tout + 1.0;
-  int64_t u = (int64_t)floor((b - sqrt(fmax(b * b - 8.0 * (double)r / (double)Tin, 0.0))) * 0.5);
+  const float b = 2.0f * (float)Tout + 1.0f;
+  const float q = (float)(r / Tin);  // whole units of Tin rows
+  int64_t u = (int64_t)floorf((b - sqrtf(fmaxf(b * b - 8.0f * q, 0.0f))) * 0.5f);
   if (u < 0) u = 0;
   if (u > Tout - 1) u = Tout - 1;
   while (u > 0 && rows_before(u, Tin, Tout) > r) --u;
