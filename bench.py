@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--batch", action="store_true",
                     help="the many-networks workload: OPG + exact Hessian of 256 networks in waves")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--streams", type=int, default=2, choices=[1, 2],
+                    help="2: the eigenpairs on their own stream and handle, concurrent with OPG + H")
     ap.add_argument("--batch-graphs", action="store_true",
                     help="replay each group of the batch from a CUDA graph (use --warmup >= 2)")
     ap.add_argument("--autotune", action="store_true",
@@ -534,6 +536,18 @@ def main():
     stream = torch.cuda.current_stream()
     net = hm.HessMLP(pb.widths, pb.acts, pb.omega, stream=stream.cuda_stream)
     lib = hm.load()
+    # two streams: OPG + H on one handle, the eigenpairs on another (each
+    # handle owns its workspace); the FP64 Gram work overlaps the tensor-core
+    # contractions
+    two = args.streams == 2 and "eig" in calls and len(calls) > 1
+    if two:
+        s_mat, s_eig = torch.cuda.Stream(), torch.cuda.Stream()
+        net_m = hm.HessMLP(pb.widths, pb.acts, pb.omega, stream=s_mat.cuda_stream)
+        net_e = hm.HessMLP(pb.widths, pb.acts, pb.omega, stream=s_eig.cuda_stream)
+        handles = (net_m, net_e)
+    else:
+        net_m = net_e = net
+        handles = (net,)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def barrier():
@@ -552,12 +566,22 @@ def main():
 
     def step(prec, io):
         X, Y, H, OPG, ev, Q = io
+        if two:
+            start = torch.cuda.Event()
+            start.record(stream)
+            s_mat.wait_event(start)
+            s_eig.wait_event(start)
         if "opg" in calls:
-            net.opg(X, Y, prec, out=OPG)
+            net_m.opg(X, Y, prec, out=OPG)
         if "hessian" in calls:
-            net.exact_hessian(X, Y, prec, out=H)
+            net_m.exact_hessian(X, Y, prec, out=H)
         if "eig" in calls:
-            net.opg_topk_eig(X, Y, K_EIG_W, prec, evals=ev, evecs=Q)
+            net_e.opg_topk_eig(X, Y, K_EIG_W, prec, evals=ev, evecs=Q)
+        if two:
+            for st in (s_mat, s_eig):
+                done = torch.cuda.Event()
+                done.record(st)
+                stream.wait_event(done)
 
     def timed(prec, steps, warmup, sampler=None):
         io = make_io(prec)
@@ -567,9 +591,10 @@ def main():
             step(prec, io)
         hm.autotune(False)
         torch.cuda.synchronize()
-        for cls in hm._lib.KERNEL_CLASS:
-            net.read_timing(cls)
-        net.timing(True)
+        for hd in handles:
+            for cls in hm._lib.KERNEL_CLASS:
+                hd.read_timing(cls)
+            hd.timing(True)
         l0 = lib.hess_launch_count()
         if sampler:
             sampler.start()
@@ -590,8 +615,14 @@ def main():
         wall = time.perf_counter() - t0
         clocks = sampler.stop() if sampler else None
         launches = lib.hess_launch_count() - l0
-        net.timing(False)
-        kern = {cls: net.read_timing(cls) for cls in hm._lib.KERNEL_CLASS}
+        kern = {}
+        for hd in handles:
+            hd.timing(False)
+            for cls in hm._lib.KERNEL_CLASS:
+                r = hd.read_timing(cls)
+                acc = kern.setdefault(cls, {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0})
+                for kk in acc:
+                    acc[kk] += r[kk]
         per = [x.elapsed_time(y) for x, y in ms]
         t = max_over_ranks(sum(per) / len(per), dist if world > 1 else None, "cuda")
         del io
@@ -704,6 +735,7 @@ def main():
                        "precision": args.precision, "P": P, "N": N, "k": K_EIG_W,
                        "l2": "flushed between steps (256 MiB write outside the timed events)",
                        "parallelism": f"replicas x{world}",
+                       "streams": ("2 (OPG + H on one, the eigenpairs on the other)" if two else "1"),
                        **({"only": args.only} if args.only else {})},
             "roofline": roof,
             "rooflines": rooflines,
