@@ -655,13 +655,45 @@ def main():
         evh = pin((K_EIG_W,), torch.float64)
         Qh = pin((K_EIG_W, P), torch.float64)
 
-        def host_step():
+        if two:
+            # each call on its own handle, stream and host thread (the calls
+            # wait for their own copies; ctypes releases the GIL), so the
+            # output copies of one overlap the others' compute
+            import threading
+            s_o = torch.cuda.Stream()
+            net_o = hm.HessMLP(pb.widths, pb.acts, pb.omega, stream=s_o.cuda_stream)
+            jobs = []
             if "opg" in calls:
-                net.opg(Xh, Yh, args.precision, out=Oh)
+                jobs.append(lambda: net_o.opg(Xh, Yh, args.precision, out=Oh))
             if "hessian" in calls:
-                net.exact_hessian(Xh, Yh, args.precision, out=Hh)
+                jobs.append(lambda: net_m.exact_hessian(Xh, Yh, args.precision, out=Hh))
             if "eig" in calls:
-                net.opg_topk_eig(Xh, Yh, K_EIG_W, args.precision, evals=evh, evecs=Qh)
+                jobs.append(lambda: net_e.opg_topk_eig(Xh, Yh, K_EIG_W, args.precision, evals=evh,
+                                                       evecs=Qh))
+
+            def host_step():
+                errs = []
+
+                def run(f):
+                    try:
+                        f()
+                    except Exception as ex:  # re-raised below
+                        errs.append(ex)
+                ths = [threading.Thread(target=run, args=(f,)) for f in jobs]
+                for t in ths:
+                    t.start()
+                for t in ths:
+                    t.join()
+                if errs:
+                    raise errs[0]
+        else:
+            def host_step():
+                if "opg" in calls:
+                    net.opg(Xh, Yh, args.precision, out=Oh)
+                if "hessian" in calls:
+                    net.exact_hessian(Xh, Yh, args.precision, out=Hh)
+                if "eig" in calls:
+                    net.opg_topk_eig(Xh, Yh, K_EIG_W, args.precision, evals=evh, evecs=Qh)
 
         host_step()
         torch.cuda.synchronize()

@@ -1318,8 +1318,20 @@ struct Staged {
   const float* X;
   const float* Y;
   float* out;
-  int x_dev, y_dev, o_dev;
+  int x_dev, y_dev, o_dev;  // 1: device-accessible as given (device memory or mapped pinned host memory)
+  int o_host;               // the output is host memory written in place (no copy back)
 };
+
+// The device alias of pinned (page-locked, mapped) host memory, or null: the
+// kernels then read and write it in place over the host link.
+static void* host_alias(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
 
 static hess_status stage(hess_mlp* h, Arena& ar, bool live, const void* X, const void* Y, void* out, int64_t N,
                          const Staged& st, Staged& d) {
@@ -1340,10 +1352,19 @@ static hess_status stage(hess_mlp* h, Arena& ar, bool live, const void* X, const
 // One network through tc_prep + one persistent launch (kind 0: OPG, 1: H).
 static hess_status run_single(hess_mlp* h, const void* X, const void* Y, int64_t N, bool x3, void* out,
                               int kind) {
-  Staged st{(const float*)X, (const float*)Y, (float*)out, 0, 0, 0};
+  Staged st{(const float*)X, (const float*)Y, (float*)out, 0, 0, 0, 0};
   HM_TRY(classify_ptr(h, X, &st.x_dev));
   HM_TRY(classify_ptr(h, Y, &st.y_dev));
   HM_TRY(classify_ptr(h, out, &st.o_dev));
+  if (!st.o_dev) {
+    // pinned host output: written in place by the kernels (the transfer
+    // overlaps the contraction instead of following it)
+    if (void* a = host_alias(out)) {
+      st.out = static_cast<float*>(a);
+      st.o_dev = 1;
+      st.o_host = 1;
+    }
+  }
   cudaStream_t s = h->stream;
   char* split = nullptr;
   TcPlan plan;
@@ -1370,6 +1391,9 @@ static hess_status run_single(hess_mlp* h, const void* X, const void* Y, int64_t
     Arena a2{h->ws, 0};
     HM_TRY(stage(h, a2, false, X, Y, out, N, st, d));
     HM_CUDA(cudaMemcpyAsync(out, d.out, P * P * 4, cudaMemcpyDeviceToHost, s));
+  }
+  if (!st.o_dev || st.o_host || !st.x_dev || !st.y_dev) {
+    // host buffers involved: the call waits for its work
     HM_CUDA(cudaStreamSynchronize(s));
     return take_sticky_error(h);
   }
@@ -1511,8 +1535,9 @@ hess_status run_hessian_chunked(hess_mlp* h, const void* X, const void* Y, int64
       }
     }
   }
-  if (!st.o_dev) {
-    HM_CUDA(cudaMemcpyAsync(Hout, O, P * P * 4, cudaMemcpyDeviceToHost, s));
+  if (!st.o_dev) HM_CUDA(cudaMemcpyAsync(Hout, O, P * P * 4, cudaMemcpyDeviceToHost, s));
+  if (!st.o_dev || !st.x_dev || !st.y_dev) {
+    // host buffers involved: the call waits for its work
     HM_CUDA(cudaStreamSynchronize(s));
     return take_sticky_error(h);
   }

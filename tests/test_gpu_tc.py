@@ -129,3 +129,15 @@ def test_tc_host_buffers_match_device_buffers(hm, kind):
     assert isinstance(host, np.ndarray)
     devo = getattr(net, kind)(dev(pb.X), dev(pb.Y), "bf16x3").cpu().numpy()
     assert np.array_equal(host, devo)
+
+
+@pytest.mark.parametrize("kind", ["opg", "exact_hessian"])
+def test_tc_pinned_host_output_written_in_place(hm, kind):
+    # a pinned host output is written by the kernels over the host link
+    pb = make_problem([70, 33, 10], ["tanh"], 129, 7, "normal", "uniform")
+    net = hm.HessMLP(pb.widths, pb.acts, pb.omega)
+    X, Y = dev(pb.X), dev(pb.Y)
+    out = torch.full((pb.P, pb.P), float("nan"), dtype=torch.float32, pin_memory=True)
+    getattr(net, kind)(X, Y, "bf16x3", out=out)  # returns after its work (host buffer)
+    ref = getattr(net, kind)(X, Y, "bf16x3").cpu()
+    assert torch.equal(out, ref)
