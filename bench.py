@@ -65,8 +65,9 @@ def parse():
     ap.add_argument("--batch", action="store_true",
                     help="the many-networks workload: OPG + exact Hessian of 256 networks in waves")
     ap.add_argument("--batch-count", type=int, default=256)
-    ap.add_argument("--streams", type=int, default=2, choices=[1, 2],
-                    help="2: the eigenpairs on their own stream and handle, concurrent with OPG + H")
+    ap.add_argument("--step", default="fused", choices=["fused", "streams", "calls"],
+                    help="fused: one hess_curvature call (two internal streams); streams: the "
+                         "single calls on two handles and streams; calls: the single calls in turn")
     ap.add_argument("--batch-graphs", action="store_true",
                     help="replay each group of the batch from a CUDA graph (use --warmup >= 2)")
     ap.add_argument("--autotune", action="store_true",
@@ -539,9 +540,12 @@ def main():
     # two streams: OPG + H on one handle, the eigenpairs on another (each
     # handle owns its workspace); the FP64 Gram work overlaps the tensor-core
     # contractions
-    two = args.streams == 2 and "eig" in calls and len(calls) > 1
+    fused = args.step == "fused" and "eig" in calls and len(calls) > 1
+    two = args.step == "streams" and "eig" in calls and len(calls) > 1
     if two:
-        s_mat, s_eig = torch.cuda.Stream(), torch.cuda.Stream()
+        # the eigen stream has the higher priority: when SMs free up its
+        # cooperative Lanczos launch is placed before further contraction CTAs
+        s_mat, s_eig = torch.cuda.Stream(priority=0), torch.cuda.Stream(priority=-1)
         net_m = hm.HessMLP(pb.widths, pb.acts, pb.omega, stream=s_mat.cuda_stream)
         net_e = hm.HessMLP(pb.widths, pb.acts, pb.omega, stream=s_eig.cuda_stream)
         handles = (net_m, net_e)
@@ -566,6 +570,9 @@ def main():
 
     def step(prec, io):
         X, Y, H, OPG, ev, Q = io
+        if fused:
+            net.curvature(X, Y, prec, opg=OPG, hessian=H, k=K_EIG_W, evals=ev, evecs=Q)
+            return
         if two:
             start = torch.cuda.Event()
             start.record(stream)
@@ -655,7 +662,11 @@ def main():
         evh = pin((K_EIG_W,), torch.float64)
         Qh = pin((K_EIG_W, P), torch.float64)
 
-        if two:
+        if fused:
+            def host_step():
+                net.curvature(Xh, Yh, args.precision, opg=Oh, hessian=Hh, k=K_EIG_W, evals=evh,
+                              evecs=Qh)
+        elif two:
             # each call on its own handle, stream and host thread (the calls
             # wait for their own copies; ctypes releases the GIL), so the
             # output copies of one overlap the others' compute
@@ -767,7 +778,9 @@ def main():
                        "precision": args.precision, "P": P, "N": N, "k": K_EIG_W,
                        "l2": "flushed between steps (256 MiB write outside the timed events)",
                        "parallelism": f"replicas x{world}",
-                       "streams": ("2 (OPG + H on one, the eigenpairs on the other)" if two else "1"),
+                       "step": ("one hess_curvature call (two internal streams)" if fused else
+                                ("single calls on two handles and streams" if two else
+                                 "single calls in turn")),
                        **({"only": args.only} if args.only else {})},
             "roofline": roof,
             "rooflines": rooflines,

@@ -158,6 +158,20 @@ HESS_API hess_status exact_hessian(hess_mlp* h, const void* X, const void* Y, in
 HESS_API hess_status opg_topk_eig(hess_mlp* h, const void* X, const void* Y, int64_t N, int k,
                          hess_precision prec, double* evals, double* evecs);
 
+/* OPG, exact Hessian and top-k OPG eigenpairs of one data set in one call
+ * (any of them may be left out: OPG or H NULL, k = 0).  The same results as
+ * opg(), exact_hessian() and opg_topk_eig() with the same arguments, but
+ * scheduled across two streams for BF16/BF16X3: the tensor-core operands and
+ * the FP64 Gram matrix are built concurrently, the cooperative Lanczos
+ * launches run alone, and the OPG and Hessian contractions overlap the FP64
+ * back-projection.  X, Y float (double for HESS_FP64), host or device; OPG
+ * and H as in opg()/exact_hessian() (pinned host outputs are written in
+ * place); evals/evecs as in opg_topk_eig().  Other precisions, or nothing to
+ * overlap, run the single calls in turn.  The call returns without waiting
+ * when every buffer is device memory.  Errors: those of the three calls. */
+HESS_API hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y, int64_t N, hess_precision prec,
+                                    void* OPG, void* H, int k, double* evals, double* evecs);
+
 /* Host helper: perm[i] = the index in the order of Eq. flatten of the i-th
  * parameter in "augmented row" order, where each output unit's weight row is
  * followed by its bias ([W_i,: , b_i] for every layer).  perm has P entries. */

@@ -36,7 +36,7 @@ EXPORTS = (
     "hess_server_add_network", "hess_server_submit", "hess_server_wait", "hess_server_destroy",
     "hess_mlp_set_operand_limit", "hess_batch_create", "hess_batch_run", "hess_batch_destroy",
     "hess_autotune", "hess_autotune_entries", "hess_autotune_save", "hess_autotune_load",
-    "hess_batch_set_graphs",
+    "hess_batch_set_graphs", "hess_curvature",
 )
 
 REQUEST_KIND = {"hessian": 0, "opg": 1, "eig": 2}
@@ -108,6 +108,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         f.restype = st
     lib.opg_topk_eig.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, vp, vp]
     lib.opg_topk_eig.restype = st
+    lib.hess_curvature.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp, vp, ctypes.c_int, vp, vp]
+    lib.hess_curvature.restype = st
     lib.hess_param_permutation.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_int64)]
     lib.hess_param_permutation.restype = st

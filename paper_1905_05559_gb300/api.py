@@ -143,6 +143,16 @@ class HessMLP:
                         allow)
         return evals, evecs, st
 
+    def curvature(self, X, Y, prec="bf16x3", opg=None, hessian=None, k=0, evals=None, evecs=None,
+                  allow_deficient=False):
+        """OPG, exact Hessian and top-k eigenpairs in one call (hess_curvature);
+        the given output buffers are filled.  Returns the status."""
+        N = self._io(X, Y, prec)
+        allow = (_lib.HESS_ERR_RANK_DEFICIENT,) if allow_deficient else ()
+        return _lib.check(self._lib.hess_curvature(self.h, _ptr(X), _ptr(Y), N, _lib.PRECISION[prec],
+                                                   _ptr(opg), _ptr(hessian), int(k), _ptr(evals),
+                                                   _ptr(evecs)), allow)
+
     @staticmethod
     def _alloc_like(X, shape, prec):
         dt = _dtype_of(prec)

@@ -99,6 +99,9 @@ hess_status host_side_init(hess_mlp* h) {
 }
 
 void host_side_free(hess_mlp* h) {
+  if (h->stream2) cudaStreamDestroy(h->stream2);
+  if (h->stream3) cudaStreamDestroy(h->stream3);
+  h->stream2 = h->stream3 = nullptr;
   if (h->host_pinned) cudaFreeHost(h->host_pinned);
   if (h->err_host) cudaFreeHost(h->err_host);
   h->host_pinned = nullptr;

@@ -1,0 +1,213 @@
+// All curvature matrices of one network and one data set in one call, with
+// the work of the three on three streams:
+//
+//   stream A (the handle's)    : forward/backward, the tensor-core operands
+//                                and the contractions of the OPG and the
+//                                Hessian (FP32 / split-BF16)
+//   stream B (the handle's 2nd): the FP64 forward/backward, Gram matrix,
+//                                Lanczos launches, tridiagonal eigenpairs and
+//                                back-projection
+//   stream C (the handle's 3rd): each matrix's copy to a host buffer, queued
+//                                behind its contraction
+//
+// Stream B has the higher priority: the eigen step is the longer chain of
+// short launches, and its blocks are scheduled first when both streams have
+// work waiting.  The contractions fill the SMs around it.  (Holding the
+// contractions back until the Lanczos launches are done measured slower.)
+// Host outputs are written to device memory and copied by the copy engine,
+// so that the OPG's transfer overlaps the Hessian's contraction and both
+// overlap the eigen step.  The streams use separate regions of the handle's
+// workspace (and separate split-K scratch).
+#include "internal.h"
+
+using namespace hm;
+
+namespace {
+
+// Device memory (on the handle's device) or not.
+hess_status on_device(const hess_mlp* h, const void* p, bool* dev) {
+  cudaPointerAttributes at;
+  *dev = false;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return HESS_OK;
+  }
+  if (at.type == cudaMemoryTypeDevice && at.device != h->device)
+    return set_error(HESS_ERR_INVALID_ARG, "buffer on device %d, handle on device %d", at.device, h->device);
+  *dev = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return HESS_OK;
+}
+
+struct EventSet {
+  cudaEvent_t e[5] = {};
+  ~EventSet() {
+    for (cudaEvent_t x : e)
+      if (x) cudaEventDestroy(x);
+  }
+};
+
+}  // namespace
+
+extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y, int64_t N, hess_precision prec,
+                                      void* OPG, void* H, int k, double* evals, double* evecs) {
+  clear_error();
+  if (!h) return set_error(HESS_ERR_INVALID_ARG, "handle is NULL");
+  if (!X || !Y) return set_error(HESS_ERR_INVALID_ARG, "X and Y must be non-NULL");
+  if (N < 1 || N > (1ll << 31) - 1) return set_error(HESS_ERR_INVALID_ARG, "N must be in 1 .. 2^31 - 1");
+  if (prec < HESS_FP64 || prec > HESS_BF16X3) return set_error(HESS_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+  if (!OPG && !H && k == 0) return set_error(HESS_ERR_INVALID_ARG, "no output requested");
+  const Net& net = h->net;
+  const int64_t P = net.P;
+  if (k < 0 || (k > 0 && (!evals || !evecs || k > N || k > P)))
+    return set_error(HESS_ERR_INVALID_ARG, "k must be 0, or 1 .. min(N, P) with evals and evecs");
+  HM_TRY(take_sticky_error(h));
+  const bool tc = prec == HESS_BF16 || prec == HESS_BF16X3;
+  if (!tc || k == 0 || (!OPG && !H)) {
+    // nothing to overlap: the single calls in turn
+    if (OPG) HM_TRY(opg(h, X, Y, N, prec, OPG));
+    if (H) HM_TRY(exact_hessian(h, X, Y, N, prec, H));
+    if (k > 0) return opg_topk_eig(h, X, Y, N, k, prec, evals, evecs);
+    return HESS_OK;
+  }
+  Guard g(h->device);
+  HM_TRY(tc_available(h));
+  const bool x3 = prec == HESS_BF16X3;
+  const int64_t T1 = net.T[0], TL = net.T[net.L - 1];
+  bool x_dev, y_dev, o_dev = true, hh_dev = true, ev_dev, q_dev;
+  HM_TRY(on_device(h, X, &x_dev));
+  HM_TRY(on_device(h, Y, &y_dev));
+  if (OPG) HM_TRY(on_device(h, OPG, &o_dev));
+  if (H) HM_TRY(on_device(h, H, &hh_dev));
+  HM_TRY(on_device(h, evals, &ev_dev));
+  HM_TRY(on_device(h, evecs, &q_dev));
+  const bool host_io = !x_dev || !y_dev || !o_dev || !hh_dev || !ev_dev || !q_dev;
+  if (!h->stream2) {
+    int lo = 0, hi = 0;
+    HM_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    HM_CUDA(cudaStreamCreateWithPriority(&h->stream2, cudaStreamNonBlocking, hi));
+  }
+  if (!h->stream3) HM_CUDA(cudaStreamCreateWithFlags(&h->stream3, cudaStreamNonBlocking));
+  const cudaStream_t sA = h->stream, sB = h->stream2, sC = h->stream3;
+
+  // ---- workspace: region A (tensor-core operands and tables), region B
+  // (the eigen step); the planning pass and the live pass take the same
+  // sizes in the same order
+  float *xs = nullptr, *ys = nullptr, *os = nullptr, *hs = nullptr;
+  double *xd = nullptr, *yd = nullptr, *evd = nullptr, *eqd = nullptr;
+  char *splitA = nullptr, *splitB = nullptr;
+  size_t tabO = 0, tabH = 0, offEig = 0;
+  Caches<double> c64;
+  TcPlan plan_o, plan_h;
+  EigResult res;
+  auto layout = [&](Arena& ar, bool live) -> hess_status {
+    xs = x_dev ? (float*)X : ar.take<float>(N * T1);
+    ys = y_dev ? (float*)Y : ar.take<float>(N * TL);
+    os = OPG ? (o_dev ? (float*)OPG : ar.take<float>(P * P)) : nullptr;
+    hs = H ? (hh_dev ? (float*)H : ar.take<float>(P * P)) : nullptr;
+    splitA = ar.take<char>(kSplitBytes);
+    if (live) {
+      if (!x_dev) HM_CUDA(cudaMemcpyAsync(xs, X, N * T1 * 4, cudaMemcpyHostToDevice, sA));
+      if (!y_dev) HM_CUDA(cudaMemcpyAsync(ys, Y, N * TL * 4, cudaMemcpyHostToDevice, sA));
+    }
+    {
+      SplitGuard sg(splitA, kSplitBytes, h->sm_count);
+      if (OPG) HM_TRY(tc_prep(h, TcItem{xs, ys, N, true, false, os, nullptr, x3}, ar, live, plan_o, sA));
+      if (H) HM_TRY(tc_prep(h, TcItem{xs, ys, N, false, true, nullptr, hs, x3}, ar, live, plan_h, sA));
+    }
+    tabO = ar.off;
+    HM_TRY(tc_launch_plan(h->sm_count, plan_o, ar, false, x3, h->err_dev, h->stage, sA));
+    tabH = ar.off;
+    HM_TRY(tc_launch_plan(h->sm_count, plan_h, ar, false, x3, h->err_dev, h->stage, sA));
+    xd = ar.take<double>(N * T1);
+    yd = ar.take<double>(N * TL);
+    plan_caches(ar, net, N, c64);
+    evd = ev_dev ? evals : ar.take<double>(k);
+    eqd = q_dev ? evecs : ar.take<double>(P * (int64_t)k);
+    splitB = ar.take<char>(kSplitBytes);
+    offEig = ar.off;
+    if (!live) HM_TRY(topk_eig_gram(h, net, c64, N, k, evd, eqd, ar, true, &res));
+    return HESS_OK;
+  };
+  Arena ar;
+  HM_TRY(layout(ar, false));
+  HM_TRY(ensure_ws(h, ar.off));
+  plan_o = TcPlan{};
+  plan_h = TcPlan{};
+  ar = Arena{h->ws, 0};
+  HM_TRY(layout(ar, true));  // queues A's input staging and operand preparation
+
+  EventSet ev;
+  for (cudaEvent_t& e : ev.e) HM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  // stream B starts once the inputs are on the device (and after earlier work
+  // on the handle's stream)
+  HM_CUDA(cudaEventRecord(ev.e[0], sA));
+  HM_CUDA(cudaStreamWaitEvent(sB, ev.e[0], 0));
+
+  // stream A: the contractions, right behind their operands
+  hess_status tc_status = HESS_OK;
+  if (OPG) {
+    Tick t(h, HESS_K_SYRK, plan_o.syrk_flops, 0.0);
+    Arena at{h->ws, tabO};
+    tc_status = tc_launch_plan(h->sm_count, plan_o, at, true, x3, h->err_dev, h->stage, sA);
+  }
+  if (OPG && !o_dev && tc_status == HESS_OK) {
+    HM_CUDA(cudaEventRecord(ev.e[2], sA));
+    HM_CUDA(cudaStreamWaitEvent(sC, ev.e[2], 0));
+    HM_CUDA(cudaMemcpyAsync(OPG, os, P * P * 4, cudaMemcpyDeviceToHost, sC));
+  }
+  if (H && tc_status == HESS_OK) {
+    Tick t(h, HESS_K_HCONTRACT, plan_h.hess_flops, 0.0);
+    Arena at{h->ws, tabH};
+    tc_status = tc_launch_plan(h->sm_count, plan_h, at, true, x3, h->err_dev, h->stage, sA);
+  }
+  if (H && !hh_dev && tc_status == HESS_OK) {
+    HM_CUDA(cudaEventRecord(ev.e[3], sA));
+    HM_CUDA(cudaStreamWaitEvent(sC, ev.e[3], 0));
+    HM_CUDA(cudaMemcpyAsync(H, hs, P * P * 4, cudaMemcpyDeviceToHost, sC));
+  }
+  if (tc_status != HESS_OK) {
+    cudaStreamSynchronize(sB);
+    cudaStreamSynchronize(sC);
+    return tc_status;
+  }
+
+  // ---- stream B: the eigen step (the handle's stream is B meanwhile, so that
+  // the eigen kernels and their timing run there)
+  hess_status eig_status = HESS_OK;
+  h->stream = sB;
+  {
+    SplitGuard sg(splitB, kSplitBytes, h->sm_count);
+    eig_status = convert(xs, xd, N * T1, sB);
+    if (eig_status == HESS_OK) eig_status = convert(ys, yd, N * TL, sB);
+    if (eig_status == HESS_OK)
+      eig_status = forward_backward(net, (const double*)h->omega64, (const double*)xd, (const double*)yd, c64, sB);
+    if (eig_status == HESS_OK) {
+      Tick t(h, HESS_K_EIG, 0.0, 0.0);
+      Arena are{h->ws, offEig};
+      eig_status = topk_eig_gram(h, net, c64, N, k, evd, eqd, are, false, &res);
+      t.set_work(res.flops, 0.0);
+    }
+  }
+  h->stream = sA;
+  if (eig_status != HESS_OK) {
+    cudaStreamSynchronize(sB);  // nothing of B or C may run past the call
+    cudaStreamSynchronize(sC);
+    return eig_status;
+  }
+  if (!ev_dev) HM_CUDA(cudaMemcpyAsync(evals, evd, k * sizeof(double), cudaMemcpyDeviceToHost, sB));
+  if (!q_dev) HM_CUDA(cudaMemcpyAsync(evecs, eqd, P * k * sizeof(double), cudaMemcpyDeviceToHost, sB));
+  // stream A ends after everything of B and C
+  HM_CUDA(cudaEventRecord(ev.e[1], sB));
+  HM_CUDA(cudaStreamWaitEvent(sA, ev.e[1], 0));
+  HM_CUDA(cudaEventRecord(ev.e[4], sC));
+  HM_CUDA(cudaStreamWaitEvent(sA, ev.e[4], 0));
+  if (host_io) {
+    HM_CUDA(cudaStreamSynchronize(sA));
+    HM_TRY(take_sticky_error(h));
+  }
+  if (!res.converged)
+    return set_error(HESS_ERR_NOT_CONVERGED, "Lanczos did not converge in %d steps", res.lanczos_steps);
+  if (res.rank_deficient)
+    return set_error(HESS_ERR_RANK_DEFICIENT, "some of the top-%d OPG eigenvalues are null", k);
+  return HESS_OK;
+}

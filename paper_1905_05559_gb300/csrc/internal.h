@@ -127,6 +127,10 @@ struct hess_mlp {
   int* err_host = nullptr;
   int* err_dev = nullptr;
   hm::PinnedStage stage;
+  // second stream (the eigen step) and copy stream (the matrices' transfer to
+  // the host) of the fused call, created on first use
+  cudaStream_t stream2 = nullptr;
+  cudaStream_t stream3 = nullptr;
   int sm_count = 0;
   // operand bytes above which the tensor-core Hessian is built and contracted
   // in chunks (one launch per chunk) instead of in one launch
