@@ -16,7 +16,9 @@ Everything here is plain numpy in float64, written from the definitions in
 * OPG:             Sec. 3, Eq. hesseq2 / hesseq3 (J^T J / N with J the
   per-example gradient matrix, one row per example);
 * OPG eigenpairs:  Sec. 5.4, Eq. J (eigenvectors of J^T J are the right
-  singular vectors of J), reached through the N x N Gram matrix J J^T / N.
+  singular vectors of J), reached through the N x N Gram matrix J J^T / N;
+* Hessian eigenpairs: Sec. 5.3 (the algebraically largest eigenpairs of H),
+  from the full H and a dense symmetric eigensolver.
 
 Pins that tie this code to the mathematics (finite differences, the closed
 form of a single softmax layer, invariants, the paper's printed sizes) live in
@@ -280,6 +282,19 @@ def hessian(omega, widths, acts, X, Y) -> np.ndarray:
     products with unit vectors."""
     P = num_params(widths)
     return hessian_columns(omega, widths, acts, X, Y, range(P))
+
+
+def hessian_topk_eig(omega, widths, acts, X, Y, k):
+    """Top-k eigenpairs of the exact Hessian, eigenvalues algebraically
+    largest first (Sec. 5.3: the k largest-algebraic eigenpairs of the Hessian
+    operator; H is indefinite, so 'largest' is algebraic, not in magnitude).
+    Here H is formed in full (Sec. 3, Eq. hesseq1) and numpy.linalg.eigh
+    serves as the dense symmetric eigensolver step.  Returns (lam (k,),
+    Q (P, k) with unit columns of canonical sign)."""
+    H = hessian(omega, widths, acts, X, Y)
+    lam, U = np.linalg.eigh(H)
+    order = np.argsort(lam)[::-1][:k]
+    return lam[order], canonical_sign(U[:, order])
 
 
 # ----------------------------------------------------------------------------

@@ -233,6 +233,22 @@ def test_hessian_symmetry_and_hvp_reciprocity():
     assert np.allclose(Hv, H @ v, rtol=0, atol=1e-13 * np.linalg.norm(Hv))
 
 
+def test_hvp_matches_directional_difference_of_gradient():
+    """H v = d/dr grad C(omega + r v) at r = 0, by Richardson-extrapolated
+    central differences of the (separately pinned) gradient along v."""
+    pb = _tiny([5, 6, 4, 3], ["sigmoid", "tanh"], N=7, seed=21)
+    rng = np.random.default_rng(5)
+    v = rng.standard_normal(pb.P)
+
+    def d(h):
+        g1 = O.gradient(pb.omega + h * v, pb.widths, pb.acts, pb.X, pb.Y)
+        g2 = O.gradient(pb.omega - h * v, pb.widths, pb.acts, pb.X, pb.Y)
+        return (g1 - g2) / (2 * h)
+
+    fd = (4 * d(5e-4) - d(1e-3)) / 3
+    assert _relerr(O.hvp(pb.omega, pb.widths, pb.acts, pb.X, pb.Y, v), fd) < 1e-9
+
+
 def _shift_null_vectors(widths):
     """Softmax is invariant to adding a constant to all logits (Sec. 2), so the
     direction that adds 1 to every output bias and, for each input unit r of the
@@ -389,6 +405,102 @@ def test_pins_catch_unnormalised_softmax(monkeypatch):
     monkeypatch.setattr(O, "forward", broken_forward)
     H = O.hessian(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
     assert _relerr(H[np.ix_(perm, perm)], ref) > 1e-3
+
+
+# ------------------------------------------------- Hessian eigenpairs ----
+
+def test_hessian_topk_eig_closed_form_two_classes():
+    """One example, a single softmax layer with zero weights and two classes:
+    p = (1/2, 1/2), H = (diag p - p p^T) (x) xt xt^T (augmented-row order)
+    with diag p - p p^T = [[1, -1], [-1, 1]] / 4, so the only nonzero
+    eigenvalue is ||xt||^2 / 2 = (||x||^2 + 1) / 2, with eigenvector
+    (1, -1)/sqrt(2) (x) xt / ||xt||; every other eigenvalue is 0."""
+    widths = [4, 2]
+    x = np.array([[0.3, -1.2, 2.0, 0.5]])
+    y = np.array([[0.0, 1.0]])
+    omega = np.zeros(O.num_params(widths))
+    lam, Q = O.hessian_topk_eig(omega, widths, [], x, y, 3)
+    xt = np.append(x[0], 1.0)
+    assert abs(lam[0] - (xt @ xt) / 2) < 1e-14 * lam[0]
+    assert np.all(np.abs(lam[1:]) < 1e-14 * lam[0])
+    q_aug = np.kron(np.array([1.0, -1.0]) / np.sqrt(2), xt / np.linalg.norm(xt))
+    q = np.empty_like(q_aug)
+    q[O.param_permutation(widths)] = q_aug
+    assert abs(abs(q @ Q[:, 0]) - 1.0) < 1e-14
+
+
+def test_hessian_topk_eig_closed_form_three_classes_degenerate():
+    """Three classes at zero weights: diag p - p p^T = I/3 - 11^T/9 has the
+    double eigenvalue 1/3 on the complement of 1, so the top two Hessian
+    eigenvalues are both ||xt||^2 / 3 and their eigenvectors span
+    {u (x) xt : u . 1 = 0}."""
+    widths = [3, 3]
+    x = np.array([[1.0, -0.5, 0.25]])
+    y = np.array([[1.0, 0.0, 0.0]])
+    omega = np.zeros(O.num_params(widths))
+    lam, Q = O.hessian_topk_eig(omega, widths, [], x, y, 3)
+    xt = np.append(x[0], 1.0)
+    assert np.allclose(lam[:2], (xt @ xt) / 3, rtol=1e-14, atol=0)
+    assert abs(lam[2]) < 1e-14 * lam[0]
+    perm = O.param_permutation(widths)
+    basis = []
+    for u in (np.array([1.0, -1.0, 0.0]), np.array([1.0, 1.0, -2.0])):
+        b_aug = np.kron(u / np.linalg.norm(u), xt / np.linalg.norm(xt))
+        b = np.empty_like(b_aug)
+        b[perm] = b_aug
+        basis.append(b)
+    B = np.array(basis).T
+    # the two computed vectors lie in span(B) and are orthonormal
+    assert np.linalg.norm(Q[:, :2] - B @ (B.T @ Q[:, :2])) < 1e-13
+    assert np.allclose(Q[:, :2].T @ Q[:, :2], np.eye(2), atol=1e-14)
+
+
+def _check_top_eigenpairs(pb, lam, Q, H):
+    """Each pair satisfies H q = lam q with the directional-difference-pinned
+    products, the vectors are orthonormal, the values descend, and every
+    Rayleigh quotient on the orthogonal complement of the top-k space is at
+    most lam_k (the top-k invariant subspace maximises it)."""
+    k = len(lam)
+    assert np.all(np.diff(lam) <= 0)
+    for c in range(k):
+        Hq = O.hvp(pb.omega, pb.widths, pb.acts, pb.X, pb.Y, Q[:, c])
+        assert np.linalg.norm(Hq - lam[c] * Q[:, c]) < 1e-12 * abs(lam[0])
+    assert np.allclose(Q.T @ Q, np.eye(k), atol=1e-13)
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        v = rng.standard_normal(pb.P)
+        v -= Q @ (Q.T @ v)
+        rq = (v @ (H @ v)) / (v @ v)
+        assert rq <= lam[-1] + 1e-12 * abs(lam[0])
+
+
+def test_hessian_topk_eig_is_the_top_of_the_spectrum():
+    """An indefinite Hessian (tanh hidden layer): the pairs pass the checks
+    above, and with k = P the values sum to trace(H) and their squares to
+    ||H||_F^2."""
+    pb = _tiny([5, 6, 3], ["tanh"], N=8, seed=10)
+    H = O.hessian(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
+    full = np.linalg.eigvalsh(H)
+    assert full.min() < -1e-6 * full.max()  # indefinite: 'largest' must be algebraic
+    lam, Q = O.hessian_topk_eig(pb.omega, pb.widths, pb.acts, pb.X, pb.Y, 6)
+    _check_top_eigenpairs(pb, lam, Q, H)
+    lam_all, _ = O.hessian_topk_eig(pb.omega, pb.widths, pb.acts, pb.X, pb.Y, pb.P)
+    assert abs(lam_all.sum() - np.trace(H)) < 1e-12 * np.abs(lam_all).sum()
+    assert abs((lam_all ** 2).sum() - (H * H).sum()) < 1e-12 * (H * H).sum()
+
+
+def test_pins_catch_eigenpairs_ordered_by_magnitude():
+    """Planting the largest-magnitude eigenpairs (instead of the algebraically
+    largest) is caught by the spectrum checks on an indefinite Hessian whose
+    most negative eigenvalue outweighs the k-th largest."""
+    pb = _tiny([5, 6, 3], ["tanh"], N=8, seed=10)
+    H = O.hessian(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
+    lam, U = np.linalg.eigh(H)
+    k = 6
+    order = np.argsort(-np.abs(lam))[:k]
+    assert lam[order].min() < 0  # the planted mistake picks a negative one
+    with pytest.raises(AssertionError):
+        _check_top_eigenpairs(pb, lam[order], O.canonical_sign(U[:, order]), H)
 
 
 # ------------------------------------------------- memory-light routes ----
