@@ -29,7 +29,7 @@ def main():
         fh.write("# P = 12730, N = 1024, seeded inputs of synth.named_config('mlp_784_16_10');\n")
         fh.write("# written by tests/golden/make_hessian_top_eigs.py from the FP64 oracle\n")
         for v in lam:
-            fh.write(f"{v!r}\n")
+            fh.write(f"{float(v)!r}\n")
     print(path)
 
 
