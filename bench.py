@@ -68,6 +68,10 @@ def parse():
     ap.add_argument("--step", default="fused", choices=["fused", "streams", "calls"],
                     help="fused: one hess_curvature call (two internal streams); streams: the "
                          "single calls on two handles and streams; calls: the single calls in turn")
+    ap.add_argument("--row", default=None, choices=["hessian-eig"],
+                    help="hessian-eig: top-k Hessian eigenpairs by Lanczos on H v products "
+                         "(its own JSON line)")
+    ap.add_argument("--row-k", type=int, default=32)
     ap.add_argument("--batch-graphs", action="store_true",
                     help="replay each group of the batch from a CUDA graph (use --warmup >= 2)")
     ap.add_argument("--autotune", action="store_true",
@@ -442,6 +446,109 @@ def batch_bench(args):
 
 
 
+def heig_bench(args):
+    """Top-k eigenpairs of the exact Hessian by Lanczos on the operator
+    v -> H v (hessian_topk_eig), never forming H: the MLP workload (P = 12730,
+    N = 1024), k = 32, FP64 products and recurrence.  One step = one solve.
+    The CPU baseline is the oracle's route (all P Hessian columns from its
+    products, then a dense eigensolver), timed on a sample: 256 columns and
+    the eigensolver on a 3072 x 3072 symmetric matrix, scaled by P / 256 and
+    (P / 3072)^3."""
+    import numpy as np
+    import torch
+
+    import paper_1905_05559_gb300 as hm
+    from paper_1905_05559_gb300 import build
+    from synth import named_config
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import mlp as O
+        pb = named_config(args.workload)
+        t0 = time.perf_counter()
+        O.hessian_columns(pb.omega, pb.widths, pb.acts, pb.X, pb.Y, range(256))
+        t_cols = time.perf_counter() - t0
+        A = np.random.default_rng(0).standard_normal((3072, 3072))
+        A = A + A.T
+        t0 = time.perf_counter()
+        np.linalg.eigh(A)
+        t_eig = time.perf_counter() - t0
+        est = t_cols * pb.P / 256 + t_eig * (pb.P / 3072) ** 3
+        cpu = {"value": 1.0 / est, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"256 of {pb.P} Hessian columns ({t_cols:.1f} s) and eigh of 3072^2 "
+                         f"({t_eig:.1f} s), scaled to one solve ({est:.0f} s)"}
+
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    lib = hm.load()
+    pb = named_config(args.workload)
+    k = args.row_k
+    prec = "fp64" if args.precision not in ("fp32",) else "fp32"
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    net = hm.HessMLP(pb.widths, pb.acts, pb.omega, stream=stream.cuda_stream)
+    X = torch.as_tensor(pb.X, dtype=dt, device="cuda")
+    Y = torch.as_tensor(pb.Y, dtype=dt, device="cuda")
+    ev = torch.empty(k, dtype=torch.float64, device="cuda")
+    Q = torch.empty((k, pb.P), dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    steps = 0
+    for _ in range(args.warmup):
+        _, _, steps = net.hessian_topk_eig(X, Y, k, prec, evals=ev, evecs=Q)
+    torch.cuda.synchronize()
+    for cls in ("hvp", "hlanczos"):
+        net.read_timing(cls)
+    net.timing(True)
+    sampler = ClockSampler(gpu_index(0))
+    sampler.start()
+    l0 = lib.hess_launch_count()
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, _, steps = net.hessian_topk_eig(X, Y, k, prec, evals=ev, evecs=Q)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    launches = (lib.hess_launch_count() - l0) / args.steps
+    clocks = sampler.stop()
+    net.timing(False)
+    lz = net.read_timing("hlanczos")
+    t = statistics.median(ms)
+    peak = 1.25
+    achieved = lz["flops"] / (lz["ms"] * 1e-3) / 1e12 if lz["ms"] > 0 else None
+    # end to end: host inputs, host outputs
+    Xh = np.ascontiguousarray(pb.X, dtype=np.float64 if prec == "fp64" else np.float32)
+    Yh = np.ascontiguousarray(pb.Y, dtype=Xh.dtype)
+    evh = np.empty(k)
+    Qh = np.empty((k, pb.P))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        net.hessian_topk_eig(Xh, Yh, k, prec, evals=evh, evecs=Qh)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    line = {
+        "metric": f"Hessian top-{k} eigenpair solves/s", "impl": "ours", "value": 1000.0 / t,
+        "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == "fp64" else "f32 products, f64 recurrence", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: MLP {pb.widths} {'/'.join(pb.acts)}, P={pb.P}, "
+                               f"N={pb.N}; top-{k} Hessian eigenpairs, Lanczos on H v",
+                   "krylov_dim": steps, "l2": "flushed between solves (256 MiB write)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "kernel_class": "hlanczos (H v products + reorthogonalisation)",
+                     "peak_source": "FP64 1.25 TFLOP/s (152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz)",
+                     "ms_per_step": lz["ms"] / args.steps, "launches_per_step": lz["launches"] / args.steps},
+        "cpu_baseline": cpu,
+        "e2e": {"value": 1.0 / e2e_s, "unit": "solves/s",
+                "h2d_bytes_per_step": Xh.nbytes + Yh.nbytes, "d2h_bytes_per_step": evh.nbytes + Qh.nbytes},
+        "gpu_launches": launches, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # -------------------------------------------------------------- replicas ----
 def max_over_ranks(value: float, dist=None, device="cpu") -> float:
     """Replicas only: every rank runs the whole workload on its own GPU and
@@ -502,6 +609,9 @@ def main():
         return
     if args.batch:
         batch_bench(args)
+        return
+    if args.row == "hessian-eig":
+        heig_bench(args)
         return
 
     import numpy as np

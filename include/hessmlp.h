@@ -161,16 +161,45 @@ HESS_API hess_status opg_topk_eig(hess_mlp* h, const void* X, const void* Y, int
 /* OPG, exact Hessian and top-k OPG eigenpairs of one data set in one call
  * (any of them may be left out: OPG or H NULL, k = 0).  The same results as
  * opg(), exact_hessian() and opg_topk_eig() with the same arguments, but
- * scheduled across two streams for BF16/BF16X3: the tensor-core operands and
- * the FP64 Gram matrix are built concurrently, the cooperative Lanczos
- * launches run alone, and the OPG and Hessian contractions overlap the FP64
- * back-projection.  X, Y float (double for HESS_FP64), host or device; OPG
- * and H as in opg()/exact_hessian() (pinned host outputs are written in
- * place); evals/evecs as in opg_topk_eig().  Other precisions, or nothing to
- * overlap, run the single calls in turn.  The call returns without waiting
- * when every buffer is device memory.  Errors: those of the three calls. */
+ * scheduled across three streams for BF16/BF16X3: the tensor-core operands and
+ * contractions on the handle's stream, the FP64 eigen step (Gram matrix,
+ * Lanczos, back-projection) concurrently on a second, higher-priority stream,
+ * and the copies of host outputs on a third, each behind its contraction.
+ * X, Y float (double for HESS_FP64), host or device; OPG and H as in
+ * opg()/exact_hessian(); evals/evecs as in opg_topk_eig().  Other precisions,
+ * or nothing to overlap, run the single calls in turn.  The call returns
+ * without waiting when every buffer is device memory.  Errors: those of the
+ * three calls. */
 HESS_API hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y, int64_t N, hess_precision prec,
                                     void* OPG, void* H, int k, double* evals, double* evecs);
+
+/* Hessian-vector products H v_d for b directions (Sec. 5.1: the exact
+ * Hessian's columns are its products with the unit vectors; here any
+ * directions).  Each product applies the R-operator (Appendix A) to the
+ * forward pass and to the per-example back-propagation of every example and
+ * averages over the N examples, without forming H.  V and HV: b x P row-major
+ * (direction d is the P-vector V + d P, in the parameter order of Eq.
+ * flatten), host or device.  X, Y, V and HV are double for HESS_FP64, float
+ * for HESS_FP32 (the arithmetic's precision); BF16 precisions return
+ * HESS_ERR_UNSUPPORTED.  Directions are processed in blocks sized to the
+ * workspace.  Waits for its work when a buffer is host memory.  Errors:
+ * INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+HESS_API hess_status hessian_vector_products(hess_mlp* h, const void* X, const void* Y, int64_t N,
+                                             hess_precision prec, const void* V, int b, void* HV);
+
+/* The k algebraically largest eigenpairs of the exact Hessian (Sec. 5.3:
+ * Lanczos on the operator v -> H v, never forming H).  FP64 Lanczos with full
+ * reorthogonalisation, extended until every top-k Ritz pair's residual bound
+ * is below 1e-10 ||T_m||; the products H q run in FP64 (HESS_FP64: X, Y
+ * double) or FP32 (HESS_FP32: X, Y float).  evals: k doubles, descending;
+ * evecs: P x k column-major doubles (column c unit norm, largest-magnitude
+ * entry positive).  steps (may be NULL) receives the Krylov dimension used.
+ * Requires 1 <= k <= P.  Waits for its work.  Errors: INVALID_ARG,
+ * UNSUPPORTED (BF16 precisions), OOM, CUDA, NOT_CONVERGED (Krylov dimension
+ * cap min(P, 8k + 1024) reached; the outputs then hold the current Ritz
+ * pairs). */
+HESS_API hess_status hessian_topk_eig(hess_mlp* h, const void* X, const void* Y, int64_t N, int k,
+                                      hess_precision prec, double* evals, double* evecs, int* steps);
 
 /* Host helper: perm[i] = the index in the order of Eq. flatten of the i-th
  * parameter in "augmented row" order, where each output unit's weight row is
@@ -339,7 +368,10 @@ typedef enum {
   HESS_K_ROP = 3,       /* R-operator over a block of directions */
   HESS_K_EIG = 4,       /* Gram matrix, Lanczos and back-projection */
   HESS_K_HREST = 5,     /* Hessian columns outside the tensor-core blocks */
-  HESS_K_COUNT = 6
+  HESS_K_HVP = 6,       /* Hessian-vector products over a block of directions */
+  HESS_K_HLANCZOS = 7,  /* Lanczos steps on the Hessian operator (products,
+                           reorthogonalisation) and its Ritz vectors */
+  HESS_K_COUNT = 8
 } hess_kernel_class;
 
 typedef struct {

@@ -36,7 +36,7 @@ EXPORTS = (
     "hess_server_add_network", "hess_server_submit", "hess_server_wait", "hess_server_destroy",
     "hess_mlp_set_operand_limit", "hess_batch_create", "hess_batch_run", "hess_batch_destroy",
     "hess_autotune", "hess_autotune_entries", "hess_autotune_save", "hess_autotune_load",
-    "hess_batch_set_graphs", "hess_curvature",
+    "hess_batch_set_graphs", "hess_curvature", "hessian_vector_products", "hessian_topk_eig",
 )
 
 REQUEST_KIND = {"hessian": 0, "opg": 1, "eig": 2}
@@ -59,7 +59,8 @@ class BatchInfo(ctypes.Structure):
                 ("launch_ms", ctypes.c_double), ("graph_replayed", ctypes.c_int)]
 
 
-KERNEL_CLASS = {"syrk": 0, "hcontract": 1, "grads": 2, "rop": 3, "eig": 4, "hrest": 5}
+KERNEL_CLASS = {"syrk": 0, "hcontract": 1, "grads": 2, "rop": 3, "eig": 4, "hrest": 5, "hvp": 6,
+                "hlanczos": 7}
 
 
 class KernelStats(ctypes.Structure):
@@ -110,6 +111,11 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.opg_topk_eig.restype = st
     lib.hess_curvature.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp, vp, ctypes.c_int, vp, vp]
     lib.hess_curvature.restype = st
+    lib.hessian_vector_products.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp, ctypes.c_int, vp]
+    lib.hessian_vector_products.restype = st
+    lib.hessian_topk_eig.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, vp, vp,
+                                     ctypes.POINTER(ctypes.c_int)]
+    lib.hessian_topk_eig.restype = st
     lib.hess_param_permutation.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_int64)]
     lib.hess_param_permutation.restype = st

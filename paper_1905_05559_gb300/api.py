@@ -143,6 +143,33 @@ class HessMLP:
                         allow)
         return evals, evecs, st
 
+    def hvp(self, X, Y, V, prec="fp64", out=None):
+        """H v for the rows v of V (b x P, or one P-vector); returns the
+        products in the same shape (hessian_vector_products)."""
+        N = self._io(X, Y, prec)
+        _check_dtype(V, prec, "V")
+        b = 1 if len(V.shape) == 1 else int(V.shape[0])
+        if int(V.shape[-1]) != self.P:
+            raise ValueError(f"directions must have P = {self.P} entries")
+        out = self._alloc_like(X, tuple(V.shape), prec) if out is None else out
+        _lib.check(self._lib.hessian_vector_products(self.h, _ptr(X), _ptr(Y), N,
+                                                     _lib.PRECISION[prec], _ptr(V), b, _ptr(out)))
+        return out
+
+    def hessian_topk_eig(self, X, Y, k, prec="fp64", evals=None, evecs=None):
+        """Top-k eigenpairs of the exact Hessian by Lanczos on H v products.
+        Returns (evals (k,), evecs (k, P) whose row c is q_c, Krylov steps)."""
+        N = self._io(X, Y, prec)
+        if evals is None:
+            evals = self._alloc_like(X, (k,), "fp64")
+        if evecs is None:
+            evecs = self._alloc_like(X, (k, self.P), "fp64")
+        steps = ctypes.c_int(0)
+        _lib.check(self._lib.hessian_topk_eig(self.h, _ptr(X), _ptr(Y), N, int(k),
+                                              _lib.PRECISION[prec], _ptr(evals), _ptr(evecs),
+                                              ctypes.byref(steps)))
+        return evals, evecs, steps.value
+
     def curvature(self, X, Y, prec="bf16x3", opg=None, hessian=None, k=0, evals=None, evecs=None,
                   allow_deficient=False):
         """OPG, exact Hessian and top-k eigenpairs in one call (hess_curvature);

@@ -38,7 +38,7 @@ def build(verbose: bool = False, extra: list | None = None) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     srcs = sources()
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(HERE, "..", "include", "hessmlp.h"))
     newest_header = max(os.path.getmtime(h) for h in headers)
 

@@ -12,70 +12,12 @@
 #include <cfloat>
 #include <mutex>
 
+#include "devmath.cuh"
 #include "internal.h"
 
 namespace hm {
 
 namespace {
-
-__device__ __forceinline__ uint64_t mix64(uint64_t z) {
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-// SplitMix64 in counter mode: uniform in [-1, 1)
-__device__ __forceinline__ double rnd_sym(uint64_t key, uint64_t i) {
-  uint64_t z = mix64(key + (i + 1) * 0x9E3779B97F4A7C15ull);
-  return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// 1/x to about one ulp: the hardware reciprocal estimate refined by two
-// Newton-Raphson steps r <- r + r (1 - x r) (quadratic convergence from the
-// estimate's ~2^-23 relative error).  Used inside the long dependent chains of
-// the tridiagonal recurrences, where a full-precision division would dominate.
-__device__ __forceinline__ double rcp64(double x) {
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
-}
-
-// 1/sqrt(x) for x > 0: the hardware estimate refined by two Newton-Raphson
-// steps r <- r (3 - x r^2) / 2.  On this GPU an FP64 operation has a long
-// dependent latency, and this chain is shorter than a square root followed
-// by a division.
-__device__ __forceinline__ double rsqrt64(double x) {
-  double r;
-  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  const double hx = 0.5 * x;
-  r = r * fma(-hx * r, r, 1.5);
-  return r * fma(-hx * r, r, 1.5);
-}
-
-// sum over a block of up to 1024 threads
-__device__ double block_sum(double v, double* sh) {
-  v = warp_sum(v);
-  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) sh[w] = v;
-  __syncthreads();
-  int nw = (blockDim.x + 31) >> 5;
-  double t = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
-  if (w == 0) t = warp_sum(t);
-  if (threadIdx.x == 0) sh[0] = t;
-  __syncthreads();
-  double r = sh[0];
-  __syncthreads();
-  return r;
-}
 
 // ------------------------------------------------------------ Gram matrix
 __global__ void gram_acc_kernel(double* M, const double* DD, const double* AA, int64_t n2,
@@ -899,6 +841,35 @@ hess_status eig_kernel_attributes() {
   return HESS_OK;
 }
 
+int64_t tridiag_scratch_doubles(int64_t mcap, int k) {
+  const bool need = (size_t)6 * mcap * sizeof(double) > kEigSmemCap;
+  return need ? (int64_t)k * 6 * (mcap + 1) : 0;
+}
+
+hess_status tridiag_topk(const double* a, const double* b, int m, int k, double* theta, int* cstart, double* Y,
+                         int64_t ldy, const double* beta_last, double* res, double* mx, uint64_t key,
+                         double* scratch, cudaStream_t s) {
+  HM_TRY(eig_kernel_attributes());
+  const bool inv_g = (size_t)6 * m * sizeof(double) > kEigSmemCap;
+  const bool bis_g = (size_t)3 * m * sizeof(double) > kEigSmemCap;
+  if ((inv_g || bis_g) && !scratch) return set_error(HESS_ERR_INVALID_ARG, "tridiagonal scratch missing");
+  // one block per eigenvalue: the FP64 Sturm recurrences of different
+  // eigenvalues run on different SMs
+  bisect_kernel<<<(unsigned)k, 128, bis_g ? 0 : (size_t)3 * m * sizeof(double), s>>>(a, b, m, k, theta,
+                                                                                   bis_g ? scratch : nullptr);
+  HM_LAUNCHED();
+  // eigenvalues closer than 1e-6 of the largest share a cluster
+  clusters_kernel<<<1, 32, 0, s>>>(theta, k, 1e-6, cstart);
+  HM_LAUNCHED();
+  inviter_kernel<<<k, 256, inv_g ? 0 : (size_t)6 * m * sizeof(double), s>>>(a, b, m, k, theta, cstart, Y, ldy,
+                                                                           beta_last, res, key,
+                                                                           inv_g ? scratch : nullptr);
+  HM_LAUNCHED();
+  max_res_kernel<<<1, 32, 0, s>>>(res, k, theta, mx);
+  HM_LAUNCHED();
+  return HESS_OK;
+}
+
 hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, int64_t N, int k,
                           double* evals_d, double* evecs_d, Arena& ar, bool dry, EigResult* res) {
   const int64_t P = net.P;
@@ -930,9 +901,8 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   int* flag = ar.take<int>(2);
   int* stop = ar.take<int>(1);
   // global scratch of the tridiagonal kernels when shared memory is too small
-  double* tri_scratch = (size_t)3 * mcap * sizeof(double) > kEigSmemCap || (size_t)6 * mcap * sizeof(double) > kEigSmemCap
-                            ? ar.take<double>((int64_t)k * 6 * (mcap + 1))
-                            : nullptr;
+  const int64_t tri_n = tridiag_scratch_doubles(mcap, k);
+  double* tri_scratch = tri_n ? ar.take<double>(tri_n) : nullptr;
   if (dry) return HESS_OK;
   cudaStream_t s = h->stream;
 
@@ -997,10 +967,6 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   HM_TRY(eig_kernel_attributes());
   HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lanczos_coop_kernel, 512, dyn));
   if (per_sm < 1 || grid > per_sm * h->sm_count) return set_error(HESS_ERR_CUDA, "Lanczos kernel cannot be resident");
-  // shared memory of the tridiagonal kernels, or their global scratch
-  const bool inv_g = (size_t)6 * mcap * sizeof(double) > kEigSmemCap;
-  const bool bis_g = (size_t)3 * mcap * sizeof(double) > kEigSmemCap;
-  const size_t inv_smem = inv_g ? 0 : (size_t)6 * mcap * sizeof(double);
   init_start_kernel<<<1, 1024, 0, s>>>(w, npart, grid, N, key);
   HM_LAUNCHED();
   HM_CUDA(cudaMemsetAsync(bar, 0, 64 * sizeof(unsigned), s));
@@ -1048,19 +1014,7 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
     m = (int)target;
     last_beta_kernel<<<1, 32, 0, s>>>(npart, grid, h2);
     HM_LAUNCHED();
-    // one block per eigenvalue: the FP64 Sturm recurrences of different
-    // eigenvalues run on different SMs
-    bisect_kernel<<<(unsigned)k, 128, bis_g ? 0 : (size_t)3 * m * sizeof(double), s>>>(alpha, beta, m, k, theta,
-                                                                                 bis_g ? tri_scratch : nullptr);
-    HM_LAUNCHED();
-    // eigenvalues closer than 1e-6 of the largest share a cluster
-    clusters_kernel<<<1, 32, 0, s>>>(theta, k, 1e-6, cstart);
-    HM_LAUNCHED();
-    inviter_kernel<<<k, 256, inv_smem, s>>>(alpha, beta, m, k, theta, cstart, Y, mcap, h2, rr, key + 11,
-                                            inv_g ? tri_scratch : nullptr);
-    HM_LAUNCHED();
-    max_res_kernel<<<1, 32, 0, s>>>(rr, k, theta, mx);
-    HM_LAUNCHED();
+    HM_TRY(tridiag_topk(alpha, beta, m, k, theta, cstart, Y, mcap, h2, rr, mx, key + 11, tri_scratch, s));
     HM_CUDA(cudaMemcpyAsync(hp, mx, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaMemcpyAsync(reinterpret_cast<int*>(hp + 2), err, sizeof(int), cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaMemcpyAsync(reinterpret_cast<int*>(hp + 2) + 1, stop, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -262,6 +262,11 @@ void plan_rop(Arena& ar, const Net& net, int64_t N, int jm, int B, RopBufs<T>& r
 template <typename T>
 hess_status rop_block(const Net& net, const T* omega, const Caches<T>& c, int jm, int64_t d0, int B,
                       RopBufs<T>& r, cudaStream_t s);
+// H v_d for B general directions (v_d = V + d ldv, result HV + d ldh); r
+// planned with jm = 1.
+template <typename T>
+hess_status hvp_block(const Net& net, const T* omega, const Caches<T>& c, const T* V, int64_t ldv, int B,
+                      RopBufs<T>& r, T* HV, int64_t ldh, cudaStream_t s);
 // H[d][c] for the block's rows and the columns of weight layer jl (>= jm),
 // kept where c >= d and mirrored to H[c][d] where c > d.  tmp: B x P_l.
 template <typename T>
@@ -278,6 +283,16 @@ struct EigResult {
   int lanczos_steps = 0;
   double flops = 0.0;  // algorithmic FP64 flops of the Gram matrix, Lanczos and back-projection
 };
+// Top-k eigenpairs of the symmetric tridiagonal matrix with diagonal a[0..m-1]
+// and off-diagonal b[0..m-2]: theta[c] = c-th largest eigenvalue (Sturm
+// bisection), row c of Y (stride ldy) its unit eigenvector (inverse
+// iteration; clusters closer than 1e-6 |theta_0| orthogonalised), res[c] =
+// |beta_last y_c[m-1]| (the Lanczos residual bound), mx = {max res, |theta_0|}.
+// scratch: tridiag_scratch_doubles(m, k) doubles (null when that is 0).
+int64_t tridiag_scratch_doubles(int64_t mcap, int k);
+hess_status tridiag_topk(const double* a, const double* b, int m, int k, double* theta, int* cstart, double* Y,
+                         int64_t ldy, const double* beta_last, double* res, double* mx, uint64_t key,
+                         double* scratch, cudaStream_t s);
 hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, int64_t N, int k,
                           double* evals_d, double* evecs_d, Arena& ar, bool dry, EigResult* res);
 

@@ -820,4 +820,216 @@ template hess_status contract_layer<double>(const Net&, const Caches<double>&,
 template hess_status contract_layer<float>(const Net&, const Caches<float>&, const RopBufs<float>&,
                                            int, int, int64_t, float*, float*, cudaStream_t);
 
+// ============================================ Hessian-vector products
+// Direction-bias term and activation of the R-forward pass for general
+// directions: R{z}[n, d, t] += v_d(b)[t]; hidden positions also get
+// R{a} = sigma'(z) R{z}.  Layout [n][d][t].
+template <typename T>
+__global__ void hvp_bias_act_kernel(T* rz, const T* V, int64_t ldv, int64_t boff, int B, int64_t N, int Tn,
+                                    const T* s1, T* ra) {
+  const int64_t n_el = N * B * Tn;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n_el;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int t = (int)(idx % Tn);
+    const int64_t r = idx / Tn;
+    const int d = (int)(r % B);
+    const int64_t n = r / B;
+    const T v = rz[idx] + V[(int64_t)d * ldv + boff + t];
+    rz[idx] = v;
+    if (ra) ra[idx] = s1[n * Tn + t] * v;
+  }
+}
+
+// out_d[i] = alpha sum_n A[n, d, i] (layout [n][d][i]), written to
+// out + d ldo + i.  Block (32 x 32): threadIdx.x over 32 adjacent (d, i)
+// columns, threadIdx.y over slices of n.
+template <typename T>
+__global__ void dir_colsum_kernel(const T* A, int B, int Tn, int64_t N, T alpha, T* out, int64_t ldo) {
+  __shared__ T part[32][33];
+  const int64_t R = (int64_t)B * Tn;
+  const int64_t r = blockIdx.x * (int64_t)32 + threadIdx.x;
+  T acc = T(0);
+  if (r < R)
+    for (int64_t n = threadIdx.y; n < N; n += 32) acc += A[n * R + r];
+  part[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && r < R) {
+    T sum = T(0);
+    for (int y = 0; y < 32; ++y) sum += part[y][threadIdx.x];
+    out[(r / Tn) * ldo + (r % Tn)] = alpha * sum;
+  }
+}
+
+// H v_d for B general directions at once (Sec. 5.1; the R-operator of
+// Pearlmutter applied to the forward pass and the per-example
+// back-propagation, Appendix A):
+//   R{z^(j)}  = W^(j) R{a^(j-1)} + V^(j) a^(j-1) + v_b^(j)     (R{a^(0)} = 0)
+//   R{a^(j)}  = sigma'(z^(j)) R{z^(j)}
+//   R{delta^(L)}   = (diag p - p p^T) R{z^(L)} sum(y)
+//   R{delta^(j)}   = sigma''(z^(j)) R{z^(j)} e^(j)
+//                    + sigma'(z^(j)) (R{delta^(j+1)} W^(j+1) + delta^(j+1) V^(j+1))
+//   (H v)_W^(j) = (1/N) sum_n R{delta^(j)} a^(j-1)^T + delta^(j) R{a^(j-1)}^T
+//   (H v)_b^(j) = (1/N) sum_n R{delta^(j)}
+// with V^(j), v_b^(j) the direction's slices in the parameter order.  The
+// weight GEMMs shared by all directions run once over N B rows; the
+// direction-dependent ones are batched over d.
+template <typename T>
+hess_status hvp_block(const Net& net, const T* omega, const Caches<T>& c, const T* V, int64_t ldv, int B,
+                      RopBufs<T>& r, T* HV, int64_t ldh, cudaStream_t s) {
+  const int L = net.L;
+  const int64_t N = c.N;
+  const T invN = T(1) / T(N);
+  // forward
+  for (int j = 1; j <= L - 1; ++j) {
+    const int Tin = net.T[j - 1], Tout = net.T[j];
+    if (j > 1) {
+      Gemm<T> g;  // R{a}^(j-1) W^(j)^T, W^(j) is Tout x Tin
+      g.M = (int)(N * B);
+      g.N = Tout;
+      g.K = Tin;
+      g.A = r.ra[j - 1];
+      g.sam = Tin;
+      g.sak = 1;
+      g.B = omega + net.woff[j - 1];
+      g.sbk = 1;
+      g.sbn = Tin;
+      g.C = r.rz[j];
+      g.scm = Tout;
+      g.scn = 1;
+      HM_TRY(gemm(g, s));
+    }
+    {
+      Gemm<T> g;  // + a^(j-1) V_d^(j)^T, batched over d
+      g.M = (int)N;
+      g.N = Tout;
+      g.K = Tin;
+      g.beta = j > 1 ? T(1) : T(0);
+      g.A = c.a[j - 1];
+      g.sam = Tin;
+      g.sak = 1;
+      g.bsa = 0;
+      g.B = V + net.woff[j - 1];
+      g.sbk = 1;
+      g.sbn = Tin;
+      g.bsb = ldv;
+      g.C = r.rz[j];
+      g.scm = (int64_t)B * Tout;
+      g.scn = 1;
+      g.bsc = Tout;
+      g.batch = B;
+      HM_TRY(gemm(g, s));
+    }
+    const bool hidden = j <= L - 2;
+    hvp_bias_act_kernel<T><<<grid1d(N * B * Tout), 256, 0, s>>>(r.rz[j], V, ldv, net.boff[j - 1], B, N, Tout,
+                                                              hidden ? c.s1[j] : nullptr,
+                                                              hidden ? r.ra[j] : nullptr);
+    HM_LAUNCHED();
+  }
+  {
+    const int TL = net.T[L - 1];
+    rop_softmax_kernel<T><<<(unsigned)cdiv(N * B, 128), 128, 0, s>>>(r.rz[L - 1], c.p, c.ysum, r.rd[L - 1], B,
+                                                                      N, TL);
+    HM_LAUNCHED();
+  }
+  // backward
+  for (int j = L - 2; j >= 1; --j) {
+    const int Tj = net.T[j], Tn = net.T[j + 1];
+    {
+      Gemm<T> g;  // R{delta}^(j+1) W^(j+1)
+      g.M = (int)(N * B);
+      g.N = Tj;
+      g.K = Tn;
+      g.A = r.rd[j + 1];
+      g.sam = Tn;
+      g.sak = 1;
+      g.B = omega + net.woff[j];
+      g.sbk = Tj;
+      g.sbn = 1;
+      g.C = r.tmp;
+      g.scm = Tj;
+      g.scn = 1;
+      HM_TRY(gemm(g, s));
+    }
+    {
+      Gemm<T> g;  // + delta^(j+1) V_d^(j+1), batched over d
+      g.M = (int)N;
+      g.N = Tj;
+      g.K = Tn;
+      g.beta = T(1);
+      g.A = c.d[j + 1];
+      g.sam = Tn;
+      g.sak = 1;
+      g.bsa = 0;
+      g.B = V + net.woff[j];
+      g.sbk = Tj;
+      g.sbn = 1;
+      g.bsb = ldv;
+      g.C = r.tmp;
+      g.scm = (int64_t)B * Tj;
+      g.scn = 1;
+      g.bsc = Tj;
+      g.batch = B;
+      HM_TRY(gemm(g, s));
+    }
+    rop_back_kernel<T><<<grid1d(N * B * Tj), 256, 0, s>>>(r.rz[j], r.tmp, c.s1[j], c.s2[j], c.e[j], r.rd[j], B, N,
+                                                         Tj);
+    HM_LAUNCHED();
+  }
+  // contraction with the forward quantities
+  for (int j = 1; j <= L - 1; ++j) {
+    const int Tin = net.T[j - 1], Tout = net.T[j];
+    {
+      Gemm<T> g;  // (1/N) R{delta}_d^(j)^T a^(j-1), batched over d
+      g.M = Tout;
+      g.N = Tin;
+      g.K = (int)N;
+      g.alpha = invN;
+      g.A = r.rd[j];
+      g.sam = 1;
+      g.sak = (int64_t)B * Tout;
+      g.bsa = Tout;
+      g.B = c.a[j - 1];
+      g.sbk = Tin;
+      g.sbn = 1;
+      g.bsb = 0;
+      g.C = HV + net.woff[j - 1];
+      g.scm = Tin;
+      g.scn = 1;
+      g.bsc = ldh;
+      g.batch = B;
+      HM_TRY(gemm(g, s));
+    }
+    if (j > 1) {
+      Gemm<T> g;  // + (1/N) delta^(j)^T R{a}_d^(j-1), batched over d
+      g.M = Tout;
+      g.N = Tin;
+      g.K = (int)N;
+      g.alpha = invN;
+      g.beta = T(1);
+      g.A = c.d[j];
+      g.sam = 1;
+      g.sak = Tout;
+      g.bsa = 0;
+      g.B = r.ra[j - 1];
+      g.sbk = (int64_t)B * Tin;
+      g.sbn = 1;
+      g.bsb = Tin;
+      g.C = HV + net.woff[j - 1];
+      g.scm = Tin;
+      g.scn = 1;
+      g.bsc = ldh;
+      g.batch = B;
+      HM_TRY(gemm(g, s));
+    }
+    dir_colsum_kernel<T><<<(unsigned)cdiv((int64_t)B * Tout, 32), dim3(32, 32), 0, s>>>(
+        r.rd[j], B, Tout, N, invN, HV + net.boff[j - 1], ldh);
+    HM_LAUNCHED();
+  }
+  return HESS_OK;
+}
+template hess_status hvp_block<double>(const Net&, const double*, const Caches<double>&, const double*, int64_t,
+                                       int, RopBufs<double>&, double*, int64_t, cudaStream_t);
+template hess_status hvp_block<float>(const Net&, const float*, const Caches<float>&, const float*, int64_t, int,
+                                      RopBufs<float>&, float*, int64_t, cudaStream_t);
+
 }  // namespace hm
