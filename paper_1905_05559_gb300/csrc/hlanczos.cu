@@ -24,10 +24,14 @@ namespace hm {
 
 namespace {
 
-constexpr int kHlChunks = 16;  // slices of the vector length in the coefficient kernel
+constexpr int kHlChunks = 32;  // slices of the vector length in the coefficient kernel
 
-// q = a random unit vector (counter-based draws), one block.
-__global__ void hl_start_kernel(double* q, int64_t P, uint64_t key) {
+// The recurrence's step index j lives in device memory (jd), so that one
+// captured step replays for every j.  qcur holds q_j, the direction of the
+// next product.
+
+// q_0 = qcur = a random unit vector (counter-based draws), one block.
+__global__ void hl_start_kernel(double* q, double* qcur, int64_t P, uint64_t key) {
   __shared__ double sh[32];
   double s = 0.0;
   for (int64_t i = threadIdx.x; i < P; i += blockDim.x) {
@@ -37,87 +41,153 @@ __global__ void hl_start_kernel(double* q, int64_t P, uint64_t key) {
   }
   s = block_sum(s, sh);
   const double inv = 1.0 / sqrt(s);
-  for (int64_t i = threadIdx.x; i < P; i += blockDim.x) q[i] *= inv;
+  for (int64_t i = threadIdx.x; i < P; i += blockDim.x) {
+    q[i] *= inv;
+    qcur[i] = q[i];
+  }
 }
 
-// Partial coefficients part[ch][i] = sum over slice ch of q_i . w for
-// i < cnt, and (self) part[ch][cnt] = slice of w . w.  One warp per vector,
-// blockIdx.y = slice.  Does nothing once the recurrence has stopped.
-__global__ void hl_coef_kernel(const double* Q, const double* w, int64_t P, int cnt, int self, int64_t pc,
-                               double* part, int ldp, const int* stop) {
+__global__ void hl_setj_kernel(int* jd, int v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *jd = v;
+}
+
+// Coefficients c_i = q_i . w for i < cnt = *jd + 1 and (self) c_cnt = w . w.
+// One warp per vector and slice of the vector length (blockIdx.y = slice)
+// writes a partial; the last block to finish adds the partials in slice
+// order (the same order on every run) into c.  Does nothing once the
+// recurrence has stopped.
+__global__ void hl_coef_kernel(const double* Q, const double* w, int64_t P, const int* jd, int self, int64_t pc,
+                               double* part, int ldp, double* c, unsigned* counter, const int* stop) {
+  __shared__ int s_last;
   if (*stop >= 0) return;
+  const int cnt = *jd + 1;
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (i > cnt || (i == cnt && !self)) return;
-  const int64_t p0 = (int64_t)blockIdx.y * pc;
-  const int64_t p1 = p0 + pc < P ? p0 + pc : P;
-  const double* a = i < cnt ? Q + (int64_t)i * P : w;
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int64_t p = p0 + lane;
-  for (; p + 96 < p1; p += 128) {
-    s0 = fma(a[p], w[p], s0);
-    s1 = fma(a[p + 32], w[p + 32], s1);
-    s2 = fma(a[p + 64], w[p + 64], s2);
-    s3 = fma(a[p + 96], w[p + 96], s3);
-  }
-  for (; p < p1; p += 32) s0 = fma(a[p], w[p], s0);
-  const double s = warp_sum((s0 + s1) + (s2 + s3));
-  if (lane == 0) part[(int64_t)blockIdx.y * ldp + i] = s;
-}
-
-// w -= sum_{i<cnt} c_i q_i with c_i = sum of the slices' partials (every
-// block sums them into shared memory; block 0 also stores them, with the
-// self product at index cnt when present, in c).  One thread per entry.
-__global__ void hl_sub_kernel(const double* Q, const double* part, int ldp, int nch, int cnt, int self, int64_t P,
-                              double* w, double* c, const int* stop) {
-  extern __shared__ double cs[];
-  if (*stop >= 0) return;
   const int ctot = cnt + (self ? 1 : 0);
-  for (int i = threadIdx.x; i < ctot; i += blockDim.x) {
-    double v = 0.0;
-    for (int ch = 0; ch < nch; ++ch) v += part[(int64_t)ch * ldp + i];
-    cs[i] = v;
-    if (blockIdx.x == 0) c[i] = v;
+  if (i < ctot) {
+    const int64_t p0 = (int64_t)blockIdx.y * pc;
+    const int64_t p1 = p0 + pc < P ? p0 + pc : P;
+    const double* a = i < cnt ? Q + (int64_t)i * P : w;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int64_t p = p0 + lane;
+    for (; p + 96 < p1; p += 128) {
+      s0 = fma(a[p], w[p], s0);
+      s1 = fma(a[p + 32], w[p + 32], s1);
+      s2 = fma(a[p + 64], w[p + 64], s2);
+      s3 = fma(a[p + 96], w[p + 96], s3);
+    }
+    for (; p < p1; p += 32) s0 = fma(a[p], w[p], s0);
+    const double sum = warp_sum((s0 + s1) + (s2 + s3));
+    if (lane == 0) {
+      part[(int64_t)blockIdx.y * ldp + i] = sum;
+      __threadfence();
+    }
   }
   __syncthreads();
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int i = 0;
-    for (; i + 3 < cnt; i += 4) {
-      s0 = fma(cs[i], Q[(int64_t)i * P + p], s0);
-      s1 = fma(cs[i + 1], Q[(int64_t)(i + 1) * P + p], s1);
-      s2 = fma(cs[i + 2], Q[(int64_t)(i + 2) * P + p], s2);
-      s3 = fma(cs[i + 3], Q[(int64_t)(i + 3) * P + p], s3);
+  if (threadIdx.x == 0) {
+    const unsigned t = atomicAdd(counter, 1u);
+    s_last = t == gridDim.x * gridDim.y - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int nch = gridDim.y;
+  for (int ii = threadIdx.x; ii < ctot; ii += blockDim.x) {
+    double v0 = 0.0, v1 = 0.0;
+    int ch = 0;
+    for (; ch + 1 < nch; ch += 2) {
+      v0 += __ldcg(part + (int64_t)ch * ldp + ii);
+      v1 += __ldcg(part + (int64_t)(ch + 1) * ldp + ii);
     }
-    for (; i < cnt; ++i) s0 = fma(cs[i], Q[(int64_t)i * P + p], s0);
-    w[p] -= (s0 + s1) + (s2 + s3);
+    if (ch < nch) v0 += __ldcg(part + (int64_t)ch * ldp + ii);
+    c[ii] = v0 + v1;
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// w -= sum_{i<cnt} c_i q_i (cnt = *jd + 1).  A block of 8 warps owns 32
+// consecutive entries (one per lane; grid-stride over such chunks); its
+// warps take every 8th i and their sums meet in shared memory in warp order.
+// npart (may be null): per-block sums of the updated w_p^2.
+__global__ void __launch_bounds__(256) hl_sub_kernel(const double* Q, const double* c, const int* jd, int64_t P,
+                                                     double* w, double* npart, const int* stop) {
+  extern __shared__ double cs[];
+  __shared__ double red[8][33];
+  __shared__ double sh[32];
+  if (*stop >= 0) return;
+  const int cnt = *jd + 1;
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) cs[i] = c[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double nn = 0.0;
+  for (int64_t p0 = (int64_t)blockIdx.x * 32; p0 < P; p0 += (int64_t)gridDim.x * 32) {
+    const int64_t p = p0 + lane;
+    double s0 = 0.0, s1 = 0.0;
+    if (p < P) {
+      int i = warp;
+      for (; i + 8 < cnt; i += 16) {
+        s0 = fma(cs[i], Q[(int64_t)i * P + p], s0);
+        s1 = fma(cs[i + 8], Q[(int64_t)(i + 8) * P + p], s1);
+      }
+      if (i < cnt) s0 = fma(cs[i], Q[(int64_t)i * P + p], s0);
+    }
+    red[warp][lane] = s0 + s1;
+    __syncthreads();
+    if (warp == 0 && p < P) {
+      double t = 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) t += red[q][lane];
+      const double v = w[p] - t;
+      w[p] = v;
+      nn = fma(v, v, nn);
+    }
+    __syncthreads();
+  }
+  if (npart) {
+    nn = block_sum(nn, sh);
+    if (threadIdx.x == 0) npart[blockIdx.x] = nn;
   }
 }
 
-// End of step j: alpha_j = c1_j + c2_j (both passes' coefficient of q_j),
-// beta_j = ||w||, q_{j+1} = w / beta_j.  A breakdown (||w|| below 1e-8 of
-// ||H q_j||, or zero) sets beta_j = 0 and stop = j instead.  One block.
-__global__ void hl_next_kernel(const double* w, int64_t P, const double* c1, const double* c2, int j, double* alpha,
-                               double* beta, double* qnext, int* stop) {
-  __shared__ double sh[32];
+// End of step j = *jd: alpha_j = c1_j + c2_j (both passes' coefficient of
+// q_j), beta_j = ||w|| (from the nparts block sums of the second pass, added
+// in the same order by every block), q_{j+1} = qcur = w / beta_j.  A
+// breakdown (||w|| below 1e-8 of ||H q_j||, or zero) sets beta_j = 0 and
+// stop = j instead.
+__global__ void hl_next_kernel(const double* w, int64_t P, const double* npart, int nparts, const double* c1,
+                               const double* c2, const int* jd, double* alpha, double* beta, double* Q,
+                               double* qcur, int* stop) {
+  __shared__ double s_n2;
   if (*stop >= 0) return;
-  double s = 0.0;
-  for (int64_t p = threadIdx.x; p < P; p += blockDim.x) s = fma(w[p], w[p], s);
-  s = block_sum(s, sh);
-  const double nrm = sqrt(s);
+  const int j = *jd;
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nparts; b += 32) t += npart[b];
+    t = warp_sum(t);
+    if (threadIdx.x == 0) s_n2 = t;
+  }
+  __syncthreads();
+  const double nrm = sqrt(s_n2);
   const double nrm0 = sqrt(fmax(c1[j + 1], 0.0));
   const bool brk = !(nrm > 1e-8 * nrm0) || !(nrm > 0.0);
-  if (threadIdx.x == 0) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     alpha[j] = c1[j] + c2[j];
     beta[j] = brk ? 0.0 : nrm;
+    if (brk) *stop = j;
   }
-  if (brk) {
-    __syncthreads();
-    if (threadIdx.x == 0) *stop = j;
-    return;
-  }
+  if (brk) return;
   const double inv = 1.0 / nrm;
-  for (int64_t p = threadIdx.x; p < P; p += blockDim.x) qnext[p] = w[p] * inv;
+  double* qn = Q + (int64_t)(j + 1) * P;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+    const double v = w[p] * inv;
+    qn[p] = v;
+    qcur[p] = v;
+  }
+}
+
+// j <- j + 1 unless the recurrence has stopped.
+__global__ void hl_advance_kernel(int* jd, const int* stop) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && *stop < 0) *jd += 1;
 }
 
 // Restart after a breakdown at step j - 1: w = a fresh random vector (the
@@ -127,14 +197,18 @@ __global__ void hl_fill_kernel(double* w, int64_t P, uint64_t key, int j) {
     w[p] = rnd_sym(key, (uint64_t)j * 0x100000000ull + (uint64_t)p);
 }
 
-// q = w / ||w|| and clear the stop flag (one block).
-__global__ void hl_store_kernel(const double* w, int64_t P, double* q, int* stop) {
+// q = qcur = w / ||w|| and clear the stop flag (one block).
+__global__ void hl_store_kernel(const double* w, int64_t P, double* q, double* qcur, int* stop) {
   __shared__ double sh[32];
   double s = 0.0;
   for (int64_t p = threadIdx.x; p < P; p += blockDim.x) s = fma(w[p], w[p], s);
   s = block_sum(s, sh);
   const double inv = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
-  for (int64_t p = threadIdx.x; p < P; p += blockDim.x) q[p] = w[p] * inv;
+  for (int64_t p = threadIdx.x; p < P; p += blockDim.x) {
+    const double v = w[p] * inv;
+    q[p] = v;
+    qcur[p] = v;
+  }
   if (threadIdx.x == 0) *stop = -1;
 }
 
@@ -363,9 +437,10 @@ hess_status run_heig(hess_mlp* h, const void* X, const void* Y, int64_t N, bool 
   Inputs<T> in;
   Caches<T> c;
   RopBufs<T> r;
-  double *Q, *w, *part, *c1, *c2, *alpha, *beta, *theta, *Y_, *rr, *mx, *evd, *eqd, *tri;
+  double *Q, *w, *qcur, *part, *npart, *c1, *c2, *alpha, *beta, *theta, *Y_, *rr, *mx, *evd, *eqd, *tri;
   T *vt = nullptr, *ht = nullptr;  // FP32 products: the direction and result in T
-  int *stop, *cstart;
+  int *stop, *cstart, *jd;
+  unsigned* counter;
   char* split = nullptr;
   auto plan = [&](Arena& ar) {
     plan_inputs(ar, net, N, in_dbl, x_dev, y_dev, X, Y, in);
@@ -373,11 +448,13 @@ hess_status run_heig(hess_mlp* h, const void* X, const void* Y, int64_t N, bool 
     plan_rop(ar, net, N, 1, 1, r);
     Q = ar.take<double>((mcap + 1) * P);
     w = ar.take<double>(P);
+    qcur = ar.take<double>(P);
     if (!dbl) {
       vt = ar.take<T>(P);
       ht = ar.take<T>(P);
     }
     part = ar.take<double>((int64_t)kHlChunks * ldp);
+    npart = ar.take<double>(4096);
     c1 = ar.take<double>(ldp);
     c2 = ar.take<double>(ldp);
     alpha = ar.take<double>(mcap + 1);
@@ -388,6 +465,8 @@ hess_status run_heig(hess_mlp* h, const void* X, const void* Y, int64_t N, bool 
     mx = ar.take<double>(4);
     cstart = ar.take<int>(k);
     stop = ar.take<int>(1);
+    jd = ar.take<int>(1);
+    counter = ar.take<unsigned>(1);
     const int64_t tn = tridiag_scratch_doubles(mcap, k);
     tri = tn ? ar.take<double>(tn) : nullptr;
     evd = ev_dev ? evals : ar.take<double>(k);
@@ -411,9 +490,13 @@ hess_status run_heig(hess_mlp* h, const void* X, const void* Y, int64_t N, bool 
   HM_CUDA(cudaMemsetAsync(alpha, 0, (mcap + 1) * sizeof(double), s));
   HM_CUDA(cudaMemsetAsync(beta, 0, (mcap + 1) * sizeof(double), s));
   HM_CUDA(cudaMemsetAsync(stop, 0xff, sizeof(int), s));
-  hl_start_kernel<<<1, 1024, 0, s>>>(Q, P, key);
+  HM_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), s));
+  HM_TRY(fill(r.ones, N, T(1), s));
+  r.ones_ready = true;
+  hl_start_kernel<<<1, 1024, 0, s>>>(Q, qcur, P, key);
   HM_LAUNCHED();
-  const unsigned gsub = (unsigned)(cdiv(P, 256) < 4096 ? cdiv(P, 256) : 4096);
+  const unsigned gsub = (unsigned)(cdiv(P, 32) < 4096 ? cdiv(P, 32) : 4096);
+  const unsigned gnext = (unsigned)(cdiv(P, 256) < 4096 ? cdiv(P, 256) : 4096);
   const size_t sub_smem = (size_t)ldp * sizeof(double);
   if (sub_smem > (size_t)48 << 10) {
     static std::once_flag once;
@@ -423,13 +506,80 @@ hess_status run_heig(hess_mlp* h, const void* X, const void* Y, int64_t N, bool 
     });
     if (e != cudaSuccess) return set_error(HESS_ERR_CUDA, "Lanczos kernel attribute: %s", cudaGetErrorString(e));
   }
-  // two Gram-Schmidt passes of w against q_0 .. q_{cnt-1}; coefficients to co
-  auto cgs = [&](int cnt, int self, double* co) -> hess_status {
-    dim3 gc((unsigned)cdiv(cnt + 1, 8), kHlChunks);
-    hl_coef_kernel<<<gc, 256, 0, s>>>(Q, w, P, cnt, self, pc, part, ldp, stop);
+  // a Gram-Schmidt pass of w against q_0 .. q_{*jd}; coefficients to co;
+  // the coefficient grid has a warp for each of up to cnt_max vectors and
+  // for the self product
+  auto cgs = [&](int cnt_max, int self, double* co, double* np, cudaStream_t st) -> hess_status {
+    dim3 gc((unsigned)cdiv(cnt_max + 1, 8), kHlChunks);
+    hl_coef_kernel<<<gc, 256, 0, st>>>(Q, w, P, jd, self, pc, part, ldp, co, counter, stop);
     HM_LAUNCHED();
-    hl_sub_kernel<<<gsub, 256, sub_smem, s>>>(Q, part, ldp, kHlChunks, cnt, self, P, w, co, stop);
+    hl_sub_kernel<<<gsub, 256, sub_smem, st>>>(Q, co, jd, P, w, np, stop);
     HM_LAUNCHED();
+    return HESS_OK;
+  };
+  // one Lanczos step j = *jd (j <= jmax): w = H q_j, two passes, q_{j+1}
+  auto one_step = [&](int jmax, cudaStream_t st) -> hess_status {
+    if (dbl) {
+      HM_TRY(hvp_block(net, omega, c, (const T*)qcur, P, 1, r, (T*)w, P, st));
+    } else {
+      d2f_kernel<<<grid_for(P), 256, 0, st>>>(qcur, (float*)vt, P);
+      HM_LAUNCHED();
+      HM_TRY(hvp_block(net, omega, c, (const T*)vt, P, 1, r, ht, P, st));
+      f2d_kernel<<<grid_for(P), 256, 0, st>>>((const float*)ht, w, P);
+      HM_LAUNCHED();
+    }
+    HM_TRY(cgs(jmax + 1, 1, c1, nullptr, st));
+    HM_TRY(cgs(jmax + 1, 0, c2, npart, st));
+    hl_next_kernel<<<gnext, 256, 0, st>>>(w, P, npart, (int)gsub, c1, c2, jd, alpha, beta, Q, qcur, stop);
+    HM_LAUNCHED();
+    hl_advance_kernel<<<1, 32, 0, st>>>(jd, stop);
+    HM_LAUNCHED();
+    return HESS_OK;
+  };
+  // steps m .. target-1: one step captured as a CUDA graph on a private
+  // stream and replayed (launch-bound short kernels), or launched directly
+  // when the capture is not possible
+  cudaStream_t cs = nullptr;
+  HM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  struct StreamGuard {
+    cudaStream_t s;
+    ~StreamGuard() {
+      if (s) cudaStreamDestroy(s);
+    }
+  } csg{cs};
+  auto run_steps = [&](int m0, int m1) -> hess_status {
+    hl_setj_kernel<<<1, 32, 0, s>>>(jd, m0);
+    HM_LAUNCHED();
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const int64_t l0 = g_launches.load();
+    bool captured = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (captured) {
+      const hess_status st = one_step(m1 - 1, cs);
+      const bool ended = cudaStreamEndCapture(cs, &graph) == cudaSuccess;
+      captured = st == HESS_OK && ended && graph &&
+                 cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+      if (!captured) clear_error();
+    }
+    const int64_t nodes = g_launches.load() - l0;
+    g_launches -= nodes;
+    if (captured) {
+      for (int j = m0; j < m1; ++j) {
+        const cudaError_t e = cudaGraphLaunch(exec, s);
+        if (e != cudaSuccess) {
+          cudaGraphExecDestroy(exec);
+          cudaGraphDestroy(graph);
+          return set_error(HESS_ERR_CUDA, "Lanczos step graph: %s", cudaGetErrorString(e));
+        }
+        g_launches += nodes;
+      }
+      // launches already queued keep their resources until they finish
+      cudaGraphExecDestroy(exec);
+      cudaGraphDestroy(graph);
+      return HESS_OK;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    for (int j = m0; j < m1; ++j) HM_TRY(one_step(m1 - 1, s));
     return HESS_OK;
   };
   int m = 0;
@@ -440,25 +590,9 @@ hess_status run_heig(hess_mlp* h, const void* X, const void* Y, int64_t N, bool 
   while (true) {
     {
       Tick t(h, HESS_K_HLANCZOS, 0.0, 0.0);
+      HM_TRY(run_steps(m, (int)target));
       double f = 0.0;
-      for (int j = m; j < (int)target; ++j) {
-        // w = H q_j
-        const double* qj = Q + (int64_t)j * P;
-        if (dbl) {
-          HM_TRY(hvp_block(net, omega, c, (const T*)qj, P, 1, r, (T*)w, P, s));
-        } else {
-          d2f_kernel<<<grid_for(P), 256, 0, s>>>(qj, (float*)vt, P);
-          HM_LAUNCHED();
-          HM_TRY(hvp_block(net, omega, c, (const T*)vt, P, 1, r, ht, P, s));
-          f2d_kernel<<<grid_for(P), 256, 0, s>>>((const float*)ht, w, P);
-          HM_LAUNCHED();
-        }
-        HM_TRY(cgs(j + 1, 1, c1));
-        HM_TRY(cgs(j + 1, 0, c2));
-        hl_next_kernel<<<1, 1024, 0, s>>>(w, P, c1, c2, j, alpha, beta, Q + (int64_t)(j + 1) * P, stop);
-        HM_LAUNCHED();
-        f += hflops + 8.0 * (j + 1) * (double)P + 4.0 * P;
-      }
+      for (int j = m; j < (int)target; ++j) f += hflops + 8.0 * (j + 1) * (double)P + 4.0 * P;
       t.set_work(f, 0.0);
       flops += f;
     }
@@ -481,12 +615,14 @@ hess_status run_heig(hess_mlp* h, const void* X, const void* Y, int64_t N, bool 
       }
       if (m >= mcap) break;
       // continue from a random vector orthogonal to q_0 .. q_{m-1}
-      hl_fill_kernel<<<gsub, 256, 0, s>>>(w, P, key + 7, m);
+      hl_fill_kernel<<<gnext, 256, 0, s>>>(w, P, key + 7, m);
       HM_LAUNCHED();
       HM_CUDA(cudaMemsetAsync(stop, 0xff, sizeof(int), s));
-      HM_TRY(cgs(m, 0, c2));
-      HM_TRY(cgs(m, 0, c2));
-      hl_store_kernel<<<1, 1024, 0, s>>>(w, P, Q + (int64_t)m * P, stop);
+      hl_setj_kernel<<<1, 32, 0, s>>>(jd, m - 1);
+      HM_LAUNCHED();
+      HM_TRY(cgs(m, 0, c2, nullptr, s));
+      HM_TRY(cgs(m, 0, c2, nullptr, s));
+      hl_store_kernel<<<1, 1024, 0, s>>>(w, P, Q + (int64_t)m * P, qcur, stop);
       HM_LAUNCHED();
       target = m + step > (int64_t)k ? m + step : (int64_t)k;
       if (target > mcap) target = mcap;

@@ -256,6 +256,8 @@ struct RopBufs {
   std::vector<T*> ra;  // hidden positions j >= jm
   std::vector<T*> rd;  // positions j >= jm
   T* tmp = nullptr;    // B x N x max T
+  T* ones = nullptr;   // N ones (filled by the first hvp_block on these buffers)
+  bool ones_ready = false;
 };
 template <typename T>
 void plan_rop(Arena& ar, const Net& net, int64_t N, int jm, int B, RopBufs<T>& r);

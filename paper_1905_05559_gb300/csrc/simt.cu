@@ -2,6 +2,7 @@
 // backward passes of the MLP, the per-example gradient writer, the batched
 // R-operator over blocks of unit directions, and the symmetric scatter that
 // places Hessian row blocks and their mirror images.
+#include <cstdint>
 #include <type_traits>
 
 #include "internal.h"
@@ -22,6 +23,15 @@ struct GemmCfg<float> {
 // narrow outputs (<= 32 columns, e.g. the k eigenvector columns)
 struct GemmCfgNarrow64 {
   static constexpr int BM = 128, BN = 32, BK = 16, TM = 8, TN = 2;
+};
+// very narrow FP64 outputs (<= 16 columns): no idle half tile
+struct GemmCfgNarrow16 {
+  static constexpr int BM = 128, BN = 16, BK = 16, TM = 8, TN = 1;
+};
+// tiny outputs (at most 16 x 16, e.g. a contraction over the examples into a
+// small weight block): one entry per thread, K split across blocks
+struct GemmCfgTiny {
+  static constexpr int BM = 16, BN = 16, BK = 16, TM = 1, TN = 1;
 };
 
 // Row of the upper-triangular tile enumeration: row r holds nt - r tiles and
@@ -146,7 +156,30 @@ __global__ void __launch_bounds__(256) gemm_kernel(Gemm<T> g, int splits, T* par
   }
 }
 
-// Sum the split-K partials in slice order and apply alpha / beta.
+// Short K: one thread per output entry, the products accumulated in k order
+// (the order of the tiled kernel, so the two give the same bits).
+template <typename T>
+__global__ void gemm_smallk_kernel(Gemm<T> g) {
+  const int64_t mn = (int64_t)g.M * g.N;
+  const int64_t total = mn * g.batch;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t bz = idx / mn, r = idx % mn;
+    const int64_t m = r / g.N, n = r % g.N;
+    const T* A = g.A + bz * g.bsa + m * g.sam;
+    const T* B = g.B + bz * g.bsb + n * g.sbn;
+    T acc = T(0);
+    for (int k = 0; k < g.K; ++k) acc = fma(A[k * g.sak], B[k * g.sbk], acc);
+    T* c = g.C + bz * g.bsc + m * g.scm + n * g.scn;
+    T v = g.alpha * acc;
+    if (g.beta != T(0)) v += g.beta * (*c);
+    *c = v;
+  }
+}
+
+// Sum the split-K partials in slice order and apply alpha / beta: one thread
+// per output, or (few outputs) one warp per output with the lanes over the
+// slices and a fixed-order warp sum.
 template <typename T>
 __global__ void splitk_reduce_kernel(Gemm<T> g, int splits, const T* part) {
   const int64_t mn = (int64_t)g.M * g.N;
@@ -163,11 +196,42 @@ __global__ void splitk_reduce_kernel(Gemm<T> g, int splits, const T* part) {
     *c = v;
   }
 }
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T>
+__global__ void splitk_reduce_warp_kernel(Gemm<T> g, int splits, const T* part) {
+  const int64_t mn = (int64_t)g.M * g.N;
+  const int64_t total = mn * g.batch;
+  const int64_t idx = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (idx >= total) return;
+  const int64_t b = idx / mn, r = idx % mn;
+  const int64_t m = r / g.N, n = r % g.N;
+  T a0 = T(0), a1 = T(0);
+  int sl = lane;
+  for (; sl + 32 < splits; sl += 64) {
+    a0 += part[((int64_t)sl * g.batch + b) * mn + r];
+    a1 += part[((int64_t)(sl + 32) * g.batch + b) * mn + r];
+  }
+  if (sl < splits) a0 += part[((int64_t)sl * g.batch + b) * mn + r];
+  const T acc = warp_sum_t(a0 + a1);
+  if (lane == 0) {
+    T* c = g.C + b * g.bsc + m * g.scm + n * g.scn;
+    T v = g.alpha * acc;
+    if (g.beta != T(0)) v += g.beta * (*c);
+    *c = v;
+  }
+}
 
 thread_local SplitScratch g_split;
 
-// Block (32 x 32): threadIdx.x over 32 adjacent columns r (coalesced),
-// threadIdx.y over 32 slices of n; the slices meet in shared memory.
+// Column sums: block (32 x 32), threadIdx.x over 32 adjacent columns r
+// (coalesced), threadIdx.y over 32 slices of n; the slices meet in shared
+// memory.
 template <typename T>
 __global__ void colsum_kernel(const T* A, int64_t lda, int64_t R, int64_t K, T alpha, T* out,
                               int64_t ostride) {
@@ -225,16 +289,27 @@ static hess_status gemm_cfg(const Gemm<T>& g, cudaStream_t s) {
   // (FP64 runs at a small fraction of the FP32 rate, so FP64 products split
   // down to slices of 32)
   const int64_t kmin = std::is_same<T, double>::value ? 64 : 256;
-  const int64_t kslice = std::is_same<T, double>::value ? 32 : 128;
+  const int64_t kslice = std::is_same<T, double>::value ? 16 : 128;
   if (!g.upper && g_split.p && tiles * g.batch < 2 * sms && g.K >= kmin) {
-    int64_t want = cdiv(2 * sms, tiles * g.batch);
     int64_t maxs = g.K / kslice;
     int64_t cap = (int64_t)(g_split.bytes / ((size_t)g.M * g.N * g.batch * sizeof(T)));
-    int64_t sp = want < maxs ? want : maxs;
-    sp = sp < cap ? sp : cap;
-    if (sp > 64) sp = 64;
-    if ((int64_t)g.batch * sp > 65535) sp = 65535 / g.batch;
-    if (sp >= 2) splits = (int)sp;
+    if (maxs > cap) maxs = cap;
+    if (maxs > 64) maxs = 64;
+    if ((int64_t)g.batch * maxs > 65535) maxs = 65535 / g.batch;
+    // the split with the least work per SM: waves of blocks times the K
+    // range of a block (slices are whole BK steps, so some splits leave
+    // empty slices or an idle tail wave)
+    int64_t best = 1, best_cost = INT64_MAX;
+    for (int64_t sp = 1; sp <= maxs; ++sp) {
+      const int64_t kc = cdiv(cdiv(g.K, sp), Cfg::BK) * Cfg::BK;
+      const int64_t eff = cdiv(g.K, kc);
+      const int64_t cost = cdiv(tiles * g.batch * eff, sms) * kc;
+      if (cost < best_cost) {
+        best_cost = cost;
+        best = sp;
+      }
+    }
+    if (best >= 2) splits = (int)best;
   }
   if (splits > 1) {
     grid.z = g.batch * splits;
@@ -242,9 +317,13 @@ static hess_status gemm_cfg(const Gemm<T>& g, cudaStream_t s) {
     gemm_kernel<T, Cfg::BM, Cfg::BN, Cfg::BK, Cfg::TM, Cfg::TN><<<grid, 256, 0, s>>>(g, splits, part);
     HM_LAUNCHED();
     int64_t total = (int64_t)g.M * g.N * g.batch;
-    int64_t blocks = cdiv(total, 256);
-    if (blocks > 65536) blocks = 65536;
-    splitk_reduce_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(g, splits, part);
+    if (total <= 8 * sms * 8) {
+      splitk_reduce_warp_kernel<T><<<(unsigned)cdiv(total, 8), 256, 0, s>>>(g, splits, part);
+    } else {
+      int64_t blocks = cdiv(total, 256);
+      if (blocks > 65536) blocks = 65536;
+      splitk_reduce_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(g, splits, part);
+    }
     HM_LAUNCHED();
     return HESS_OK;
   }
@@ -252,9 +331,43 @@ static hess_status gemm_cfg(const Gemm<T>& g, cudaStream_t s) {
   HM_LAUNCHED();
   return HESS_OK;
 }
+// Shape dispatch.  Skinny problems waste most of a tile (and, in FP64, whose
+// rate per SM partition is small, the idle lanes cost as much as busy ones),
+// so:
+//   K <= 32 and a narrow output     -> one thread per entry
+//   M, N <= 16                      -> 16 x 16 tiles (split K)
+//   M < 32 <= 4 M <= N              -> the transposed problem C^T = B^T A^T
+//   FP64, N <= 16 / N <= 32         -> 256 x 16 / 128 x 32 tiles
 template <typename T>
 hess_status gemm(const Gemm<T>& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return HESS_OK;
+  if (g.batch > 65535) return set_error(HESS_ERR_INVALID_ARG, "gemm batch %d too large", g.batch);
+  const int64_t entries = (int64_t)g.M * g.N;
+  if (!g.upper && g.K <= 32 && (g.N <= 32 || entries <= 16384)) {
+    int64_t blocks = cdiv(entries * g.batch, 256);
+    if (blocks > 65536) blocks = 65536;
+    gemm_smallk_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(g);
+    HM_LAUNCHED();
+    return HESS_OK;
+  }
+  if (!g.upper && g.M <= 16 && g.N <= 16) return gemm_cfg<T, GemmCfgTiny>(g, s);
+  if (!g.upper && g.M < 32 && g.N >= 4 * g.M) {
+    Gemm<T> t = g;
+    t.M = g.N;
+    t.N = g.M;
+    t.A = g.B;
+    t.sam = g.sbn;
+    t.sak = g.sbk;
+    t.bsa = g.bsb;
+    t.B = g.A;
+    t.sbk = g.sak;
+    t.sbn = g.sam;
+    t.bsb = g.bsa;
+    t.scm = g.scn;
+    t.scn = g.scm;
+    return gemm(t, s);
+  }
+  if (std::is_same<T, double>::value && !g.upper && g.N <= 16) return gemm_cfg<T, GemmCfgNarrow16>(g, s);
   if (std::is_same<T, double>::value && !g.upper && g.N <= 32) return gemm_cfg<T, GemmCfgNarrow64>(g, s);
   return gemm_cfg<T, GemmCfg<T>>(g, s);
 }
@@ -677,6 +790,8 @@ void plan_rop(Arena& ar, const Net& net, int64_t N, int jm, int B, RopBufs<T>& r
     maxT = net.T[j] > maxT ? net.T[j] : maxT;
   }
   r.tmp = ar.take<T>(N * B * maxT);
+  r.ones = ar.take<T>(N);
+  r.ones_ready = false;
 }
 template void plan_rop<double>(Arena&, const Net&, int64_t, int, int, RopBufs<double>&);
 template void plan_rop<float>(Arena&, const Net&, int64_t, int, int, RopBufs<float>&);
@@ -840,26 +955,6 @@ __global__ void hvp_bias_act_kernel(T* rz, const T* V, int64_t ldv, int64_t boff
   }
 }
 
-// out_d[i] = alpha sum_n A[n, d, i] (layout [n][d][i]), written to
-// out + d ldo + i.  Block (32 x 32): threadIdx.x over 32 adjacent (d, i)
-// columns, threadIdx.y over slices of n.
-template <typename T>
-__global__ void dir_colsum_kernel(const T* A, int B, int Tn, int64_t N, T alpha, T* out, int64_t ldo) {
-  __shared__ T part[32][33];
-  const int64_t R = (int64_t)B * Tn;
-  const int64_t r = blockIdx.x * (int64_t)32 + threadIdx.x;
-  T acc = T(0);
-  if (r < R)
-    for (int64_t n = threadIdx.y; n < N; n += 32) acc += A[n * R + r];
-  part[threadIdx.y][threadIdx.x] = acc;
-  __syncthreads();
-  if (threadIdx.y == 0 && r < R) {
-    T sum = T(0);
-    for (int y = 0; y < 32; ++y) sum += part[y][threadIdx.x];
-    out[(r / Tn) * ldo + (r % Tn)] = alpha * sum;
-  }
-}
-
 // H v_d for B general directions at once (Sec. 5.1; the R-operator of
 // Pearlmutter applied to the forward pass and the per-example
 // back-propagation, Appendix A):
@@ -879,6 +974,10 @@ hess_status hvp_block(const Net& net, const T* omega, const Caches<T>& c, const 
   const int L = net.L;
   const int64_t N = c.N;
   const T invN = T(1) / T(N);
+  if (!r.ones_ready) {
+    HM_TRY(fill(r.ones, N, T(1), s));
+    r.ones_ready = true;
+  }
   // forward
   for (int j = 1; j <= L - 1; ++j) {
     const int Tin = net.T[j - 1], Tout = net.T[j];
@@ -1021,9 +1120,27 @@ hess_status hvp_block(const Net& net, const T* omega, const Caches<T>& c, const 
       g.batch = B;
       HM_TRY(gemm(g, s));
     }
-    dir_colsum_kernel<T><<<(unsigned)cdiv((int64_t)B * Tout, 32), dim3(32, 32), 0, s>>>(
-        r.rd[j], B, Tout, N, invN, HV + net.boff[j - 1], ldh);
-    HM_LAUNCHED();
+    {
+      Gemm<T> g;  // (1/N) sum_n R{delta}_d^(j), batched over d: a product with ones
+      g.M = Tout;
+      g.N = 1;
+      g.K = (int)N;
+      g.alpha = invN;
+      g.A = r.rd[j];
+      g.sam = 1;
+      g.sak = (int64_t)B * Tout;
+      g.bsa = Tout;
+      g.B = r.ones;
+      g.sbk = 1;
+      g.sbn = 0;
+      g.bsb = 0;
+      g.C = HV + net.boff[j - 1];
+      g.scm = 1;
+      g.scn = 0;
+      g.bsc = ldh;
+      g.batch = B;
+      HM_TRY(gemm(g, s));
+    }
   }
   return HESS_OK;
 }
