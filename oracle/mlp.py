@@ -18,7 +18,9 @@ Everything here is plain numpy in float64, written from the definitions in
 * OPG eigenpairs:  Sec. 5.4, Eq. J (eigenvectors of J^T J are the right
   singular vectors of J), reached through the N x N Gram matrix J J^T / N;
 * Hessian eigenpairs: Sec. 5.3 (the algebraically largest eigenpairs of H),
-  from the full H and a dense symmetric eigensolver.
+  from the full H and a dense symmetric eigensolver;
+* low-rank and full-rank approximations: Sec. 4.1, 4.2 and their implicit
+  application, Sec. 5.5, 5.6.
 
 Pins that tie this code to the mathematics (finite differences, the closed
 form of a single softmax layer, invariants, the paper's printed sizes) live in
@@ -295,6 +297,43 @@ def hessian_topk_eig(omega, widths, acts, X, Y, k):
     lam, U = np.linalg.eigh(H)
     order = np.argsort(lam)[::-1][:k]
     return lam[order], canonical_sign(U[:, order])
+
+
+# ----------------------------------------------------------------------------
+# Low-rank and full-rank approximations from K eigenpairs (Sec. 4.1, 4.2,
+# Sec. 5.5, 5.6, Appendix "Derivation of the Full-rank Approximation")
+# ----------------------------------------------------------------------------
+
+def lowrank_matrix(Q, lam) -> np.ndarray:
+    """H~ = Q diag(lam) Q^T (Sec. 4.1, Eq. lowrankapprox); Q is P x K with the
+    eigenvectors as columns."""
+    Q = np.asarray(Q, dtype=np.float64)
+    return Q @ np.diag(np.asarray(lam, dtype=np.float64)) @ Q.T
+
+
+def fullrank_matrix(Q, lam, lam_tilde) -> np.ndarray:
+    """H~~ = H~ + lam_tilde (I - Q Q^T) (Sec. 4.2): the remaining P - K
+    eigenvalues replaced by lam_tilde (the paper's choice is lam_K)."""
+    Q = np.asarray(Q, dtype=np.float64)
+    P = Q.shape[0]
+    return lowrank_matrix(Q, lam) + lam_tilde * (np.eye(P) - Q @ Q.T)
+
+
+def approx_apply(Q, lam, X, lam_tilde=None):
+    """For each row x of X (b x P): H~ x and x^T H~ x without forming a P x P
+    matrix (Sec. 5.5: (x^T Q) diag(lam) (Q^T x)); with lam_tilde given, the
+    full-rank operator (Sec. 5.6: + lam_tilde x^T x - lam_tilde (x^T Q)(Q^T x)).
+    Returns (HX (b x P), quad (b,))."""
+    Q = np.asarray(Q, dtype=np.float64)
+    lam = np.asarray(lam, dtype=np.float64)
+    X = np.atleast_2d(np.asarray(X, dtype=np.float64))
+    C = X @ Q  # b x K: the coordinates x^T Q
+    HX = (C * lam) @ Q.T
+    quad = (C * C) @ lam
+    if lam_tilde is not None:
+        HX = HX + lam_tilde * (X - C @ Q.T)
+        quad = quad + lam_tilde * ((X * X).sum(axis=1) - (C * C).sum(axis=1))
+    return HX, quad
 
 
 # ----------------------------------------------------------------------------

@@ -503,6 +503,58 @@ def test_pins_catch_eigenpairs_ordered_by_magnitude():
         _check_top_eigenpairs(pb, lam[order], O.canonical_sign(U[:, order]), H)
 
 
+# ------------------------------------ low-rank / full-rank approximations ----
+
+def test_lowrank_with_all_eigenpairs_is_the_hessian():
+    """K = P: Q diag(lam) Q^T rebuilds H (the spectral theorem), and the
+    full-rank term vanishes (Q Q^T = I)."""
+    pb = _tiny([5, 6, 3], ["tanh"], N=8, seed=10)
+    H = O.hessian(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
+    lam, Q = O.hessian_topk_eig(pb.omega, pb.widths, pb.acts, pb.X, pb.Y, pb.P)
+    assert _relerr(O.lowrank_matrix(Q, lam), H) < 1e-12
+    assert _relerr(O.fullrank_matrix(Q, lam, 0.7), H) < 1e-12
+
+
+def test_fullrank_spectrum_and_null_space():
+    """With K < P: H~ has eigenvalues lam_1..lam_K and P - K zeros; H~~ has
+    lam_1..lam_K and lam_tilde (P - K times), so it is positive definite when
+    lam_tilde > 0 (Appendix, full-rank derivation); H~ q_k = lam_k q_k and, for
+    v orthogonal to Q, H~ v = 0 and H~~ v = lam_tilde v."""
+    pb = _tiny([5, 6, 3], ["tanh"], N=8, seed=10)
+    K = 5
+    lam, Q = O.hessian_topk_eig(pb.omega, pb.widths, pb.acts, pb.X, pb.Y, K)
+    lt = lam[-1]
+    assert lt > 0
+    low = np.sort(np.linalg.eigvalsh(O.lowrank_matrix(Q, lam)))[::-1]
+    assert np.allclose(low[:K], lam, rtol=0, atol=1e-12 * lam[0])
+    assert np.all(np.abs(low[K:]) < 1e-12 * lam[0])
+    full = np.sort(np.linalg.eigvalsh(O.fullrank_matrix(Q, lam, lt)))[::-1]
+    assert np.allclose(full[:K], lam, rtol=0, atol=1e-12 * lam[0])
+    assert np.allclose(full[K:], lt, rtol=0, atol=1e-12 * lam[0])
+    v = np.random.default_rng(2).standard_normal(pb.P)
+    v -= Q @ (Q.T @ v)
+    HX, quad = O.approx_apply(Q, lam, np.vstack([Q[:, 1], v]))
+    assert np.linalg.norm(HX[0] - lam[1] * Q[:, 1]) < 1e-13 * lam[0]
+    assert np.linalg.norm(HX[1]) < 1e-13 * lam[0] * np.linalg.norm(v)
+    HX, quad = O.approx_apply(Q, lam, v[None, :], lam_tilde=lt)
+    assert np.linalg.norm(HX[0] - lt * v) < 1e-13 * lam[0] * np.linalg.norm(v)
+    assert abs(quad[0] - lt * (v @ v)) < 1e-12 * lam[0] * (v @ v)
+
+
+def test_implicit_application_matches_the_formed_matrices():
+    """The implicit products and quadratic forms of Sec. 5.5 / 5.6 equal the
+    explicit x^T H~ x with H~ formed (Sec. 4.1 / 4.2)."""
+    rng = np.random.default_rng(4)
+    P, K = 40, 6
+    Q, _ = np.linalg.qr(rng.standard_normal((P, K)))
+    lam = np.sort(rng.standard_normal(K))[::-1]
+    X = rng.standard_normal((3, P))
+    for lt, M in ((None, O.lowrank_matrix(Q, lam)), (0.3, O.fullrank_matrix(Q, lam, 0.3))):
+        HX, quad = O.approx_apply(Q, lam, X, lam_tilde=lt)
+        assert np.allclose(HX, X @ M, rtol=0, atol=1e-13)
+        assert np.allclose(quad, np.einsum("ip,pq,iq->i", X, M, X), rtol=0, atol=1e-12)
+
+
 # ------------------------------------------------- memory-light routes ----
 
 def test_memory_light_routes_match_full_matrices():
