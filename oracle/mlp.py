@@ -20,7 +20,8 @@ Everything here is plain numpy in float64, written from the definitions in
 * Hessian eigenpairs: Sec. 5.3 (the algebraically largest eigenpairs of H),
   from the full H and a dense symmetric eigensolver;
 * low-rank and full-rank approximations: Sec. 4.1, 4.2 and their implicit
-  application, Sec. 5.5, 5.6.
+  application, Sec. 5.5, 5.6;
+* mini-batch and per-example Hessians: Sec. 5.1.
 
 Pins that tie this code to the mathematics (finite differences, the closed
 form of a single softmax layer, invariants, the paper's printed sizes) live in
@@ -334,6 +335,17 @@ def approx_apply(Q, lam, X, lam_tilde=None):
         HX = HX + lam_tilde * (X - C @ Q.T)
         quad = quad + lam_tilde * ((X * X).sum(axis=1) - (C * C).sum(axis=1))
     return HX, quad
+
+
+def minibatch_hessians(omega, widths, acts, X, Y, bs):
+    """Hessians of consecutive mini-batches of bs examples (the last may be
+    shorter), each the average of its examples' Hessians (Sec. 5.1: the
+    Hessian operation fed one example, or a mini-batch); bs = 1 gives the
+    per-example Hessians.  Returns an array (ceil(N / bs), P, P)."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    N = X.shape[0]
+    return np.stack([hessian(omega, widths, acts, X[b:b + bs], Y[b:b + bs]) for b in range(0, N, bs)])
 
 
 # ----------------------------------------------------------------------------

@@ -555,6 +555,36 @@ def test_implicit_application_matches_the_formed_matrices():
         assert np.allclose(quad, np.einsum("ip,pq,iq->i", X, M, X), rtol=0, atol=1e-12)
 
 
+# --------------------------------------------------- mini-batch Hessians ----
+
+def test_minibatch_hessians_average_to_the_full_hessian():
+    """The mini-batch Hessians weighted by their sizes average to the full H
+    (Eq. hesseq1 is a mean over examples), with a ragged last batch."""
+    pb = _tiny([5, 6, 4, 3], ["sigmoid", "tanh"], N=11, seed=14)
+    Hs = O.minibatch_hessians(pb.omega, pb.widths, pb.acts, pb.X, pb.Y, 4)
+    assert Hs.shape == (3, pb.P, pb.P)
+    sizes = np.array([4, 4, 3])
+    H = O.hessian(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
+    assert _relerr((Hs * sizes[:, None, None]).sum(axis=0) / pb.N, H) < 1e-13
+
+
+def test_per_example_hessians_single_layer_closed_form():
+    """bs = 1 on a single softmax layer: each per-example Hessian is
+    (diag p_n - p_n p_n^T) (x) xt_n xt_n^T (augmented-row order), rank at most
+    T_L - 1."""
+    pb = _tiny([4, 3], [], N=5, seed=6)
+    Hs = O.minibatch_hessians(pb.omega, pb.widths, pb.acts, pb.X, pb.Y, 1)
+    f = O.forward(pb.omega, pb.widths, pb.acts, pb.X)
+    perm = O.param_permutation(pb.widths)
+    for n in range(pb.N):
+        p = f["p"][n]
+        xt = np.append(pb.X[n], 1.0)
+        ref = np.kron(np.diag(p) - np.outer(p, p), np.outer(xt, xt))
+        assert _relerr(Hs[n][np.ix_(perm, perm)], ref) < 1e-13
+        ev = np.linalg.eigvalsh(Hs[n])
+        assert int((np.abs(ev) > 1e-12 * np.abs(ev).max()).sum()) <= pb.widths[-1] - 1
+
+
 # ------------------------------------------------- memory-light routes ----
 
 def test_memory_light_routes_match_full_matrices():
