@@ -68,9 +68,9 @@ def parse():
     ap.add_argument("--step", default="fused", choices=["fused", "streams", "calls"],
                     help="fused: one hess_curvature call (two internal streams); streams: the "
                          "single calls on two handles and streams; calls: the single calls in turn")
-    ap.add_argument("--row", default=None, choices=["hessian-eig"],
-                    help="hessian-eig: top-k Hessian eigenpairs by Lanczos on H v products "
-                         "(its own JSON line)")
+    ap.add_argument("--row", default=None, choices=["hessian-eig", "approx", "minibatch"],
+                    help="hessian-eig: top-k Hessian eigenpairs by Lanczos on H v products; "
+                         "approx: low/full-rank approximations from them (own JSON lines)")
     ap.add_argument("--row-k", type=int, default=32)
     ap.add_argument("--batch-graphs", action="store_true",
                     help="replay each group of the batch from a CUDA graph (use --warmup >= 2)")
@@ -549,6 +549,151 @@ def heig_bench(args):
     print(json.dumps(line), flush=True)
 
 
+def approx_bench(args):
+    """Low-rank / full-rank approximations (Sec. 4.1, 4.2) from the top-k
+    Hessian eigenpairs of the MLP workload: forming the P x P full-rank
+    matrix (FP64 and FP32) and applying it implicitly to a block of 1024
+    directions (Sec. 5.5, 5.6).  One step = one form in FP32 + one form in
+    FP64 + one implicit application."""
+    import numpy as np
+    import torch
+
+    import paper_1905_05559_gb300 as hm
+    from paper_1905_05559_gb300 import build
+    from synth import named_config
+
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    lib = hm.load()
+    pb = named_config(args.workload)
+    k = args.row_k
+    P = pb.P
+    net = hm.HessMLP(pb.widths, pb.acts, pb.omega, stream=stream.cuda_stream)
+    X = torch.as_tensor(pb.X, dtype=torch.float64, device="cuda")
+    Y = torch.as_tensor(pb.Y, dtype=torch.float64, device="cuda")
+    lam, Q, _ = net.hessian_topk_eig(X, Y, k, "fp64")
+    b = 1024
+    V = torch.as_tensor(np.random.default_rng(0).standard_normal((b, P)), device="cuda")
+    out64 = torch.empty((P, P), dtype=torch.float64, device="cuda")
+    out32 = torch.empty((P, P), dtype=torch.float32, device="cuda")
+
+    def step():
+        net.approx_form(lam, Q, full=True, prec="fp32", out=out32)
+        net.approx_form(lam, Q, full=True, prec="fp64", out=out64)
+        net.approx_apply(lam, Q, V, full=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    parts = {}
+    for name, fn in (("form_fp32", lambda: net.approx_form(lam, Q, full=True, prec="fp32", out=out32)),
+                     ("form_fp64", lambda: net.approx_form(lam, Q, full=True, prec="fp64", out=out64)),
+                     ("apply_fp64", lambda: net.approx_apply(lam, Q, V, full=True))):
+        ts = []
+        for _ in range(args.steps):
+            a = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            e.record(stream)
+            e.synchronize()
+            ts.append(a.elapsed_time(e))
+        parts[name] = statistics.median(ts)
+    sampler = ClockSampler(gpu_index(0))
+    sampler.start()
+    l0 = lib.hess_launch_count()
+    ms = []
+    for _ in range(args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        e.record(stream)
+        e.synchronize()
+        ms.append(a.elapsed_time(e))
+    launches = (lib.hess_launch_count() - l0) / args.steps
+    clocks = sampler.stop()
+    t = statistics.median(ms)
+    peaks, src = measured_peaks()
+    f64 = P * (P + 1) * k / (parts["form_fp64"] * 1e-3) / 1e12
+    f32 = P * (P + 1) * k / (parts["form_fp32"] * 1e-3) / 1e12
+    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    app = 4.0 * P * k * b / (parts["apply_fp64"] * 1e-3) / 1e12
+    line = {
+        "metric": "full-rank approximation entries/s (formed, FP32 + FP64)", "impl": "ours",
+        "value": 2.0 * P * P / (t * 1e-3), "unit": "entries/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: P={P}, top-{k} Hessian eigenpairs; full-rank form "
+                               f"(lam_tilde = lam_K) in FP32 and FP64, implicit application to {b} "
+                               "directions", "l2": "outputs (1.9 GB) far larger than L2"},
+        "parts_ms": parts,
+        "roofline": {"bound": "alu", "achieved": f64, "peak": 1.25, "unit": "TFLOP/s", "frac": f64 / 1.25,
+                     "traffic": None, "kernel_class": "approx (FP64 form: upper tiles of Q^T diag(w) Q)",
+                     "peak_source": "FP64 1.25 TFLOP/s (152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz)"},
+        "rooflines": {
+            "form_fp32": {"bound": "alu", "achieved": f32, "peak": fp32_peak, "unit": "TFLOP/s",
+                          "frac": f32 / fp32_peak, "hbm_gbs": P * P * 4 / (parts["form_fp32"] * 1e-3) / 1e9,
+                          "hbm_peak": peaks["hbm_gbs"]},
+            "apply_fp64": {"bound": "alu", "achieved": app, "peak": 1.25, "unit": "TFLOP/s", "frac": app / 1.25}},
+        "gpu_launches": launches, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def minibatch_bench(args):
+    """Mini-batch Hessians (Sec. 5.1) of the MLP workload: the N = 1024
+    examples in 16 mini-batches of 64, one P x P split-BF16 Hessian each
+    (10.4 GB of output), through the handle's batch waves."""
+    import torch
+
+    import paper_1905_05559_gb300 as hm
+    from paper_1905_05559_gb300 import build
+    from synth import named_config
+
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    lib = hm.load()
+    pb = named_config(args.workload)
+    P, N, bs = pb.P, pb.N, 64
+    nb = -(-N // bs)
+    net = hm.HessMLP(pb.widths, pb.acts, pb.omega, stream=stream.cuda_stream)
+    X = torch.as_tensor(pb.X, dtype=torch.float32, device="cuda")
+    Y = torch.as_tensor(pb.Y, dtype=torch.float32, device="cuda")
+    out = torch.empty((nb, P, P), dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        net.hessian_minibatches(X, Y, bs, args.precision, out=out)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(gpu_index(0))
+    sampler.start()
+    l0 = lib.hess_launch_count()
+    ms = []
+    for _ in range(args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        net.hessian_minibatches(X, Y, bs, args.precision, out=out)
+        e.record(stream)
+        e.synchronize()
+        ms.append(a.elapsed_time(e))
+    launches = (lib.hess_launch_count() - l0) / args.steps
+    clocks = sampler.stop()
+    t = statistics.median(ms)
+    line = {
+        "metric": "mini-batch Hessian entries/s", "impl": "ours", "value": nb * P * P / (t * 1e-3),
+        "unit": "entries/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: P={P}, N={N} in {nb} mini-batches of {bs}, one exact "
+                               "Hessian each", "l2": "outputs (10.4 GB) far larger than L2"},
+        "hbm_write_gbs": nb * P * P * 4 / (t * 1e-3) / 1e9,
+        "gpu_launches": launches, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # -------------------------------------------------------------- replicas ----
 def max_over_ranks(value: float, dist=None, device="cpu") -> float:
     """Replicas only: every rank runs the whole workload on its own GPU and
@@ -612,6 +757,12 @@ def main():
         return
     if args.row == "hessian-eig":
         heig_bench(args)
+        return
+    if args.row == "approx":
+        approx_bench(args)
+        return
+    if args.row == "minibatch":
+        minibatch_bench(args)
         return
 
     import numpy as np

@@ -201,6 +201,43 @@ HESS_API hess_status hessian_vector_products(hess_mlp* h, const void* X, const v
 HESS_API hess_status hessian_topk_eig(hess_mlp* h, const void* X, const void* Y, int64_t N, int k,
                                       hess_precision prec, double* evals, double* evecs, int* steps);
 
+/* Mini-batch (bs > 1) or per-example (bs = 1) Hessians (Sec. 5.1: feeding a
+ * mini-batch, or one example, to the Hessian operation yields the average of
+ * the per-example Hessians over it): H_b = (1/n_b) sum over examples n of
+ * batch b of d^2 C_n / d omega d omega^T for the consecutive batches of bs
+ * examples (n_b = bs except the last).  H: ceil(N / bs) row-major P x P
+ * matrices back to back, dtype of the precision.  For BF16/BF16X3 with every
+ * buffer in device memory the batches run through a batch object the handle
+ * keeps (waves of one persistent tensor-core launch; each matrix
+ * bit-identical to exact_hessian on its slice); otherwise one exact_hessian
+ * call per batch.  Waits for its work.  Errors: those of exact_hessian. */
+HESS_API hess_status hessian_minibatches(hess_mlp* h, const void* X, const void* Y, int64_t N, int64_t bs,
+                                         hess_precision prec, void* H);
+
+/* Low-rank and full-rank approximations of a curvature matrix from K of its
+ * eigenpairs (Sec. 4.1: H~ = Q diag(lam) Q^T; Sec. 4.2: H~~ = H~ +
+ * lam_tilde (I - Q Q^T), the other P - K eigenvalues replaced by lam_tilde,
+ * positive definite when lam_tilde > 0).  evals: K doubles; evecs: P x K
+ * column-major doubles with orthonormal columns (the outputs of
+ * hessian_topk_eig or opg_topk_eig), host or device.  full = 0 for H~, 1 for
+ * H~~; lam_tilde = NaN takes lam_K (the paper's choice).  P is the handle's.
+ *
+ * hess_approx_form writes the P x P matrix (row-major, exactly symmetric):
+ * double for HESS_FP64, float for HESS_FP32 (computed in that precision);
+ * BF16 precisions return HESS_ERR_UNSUPPORTED.
+ *
+ * hess_approx_apply applies the operator without forming it (Sec. 5.5, 5.6):
+ * for each row x of X (b x P row-major doubles), HX row = H~ x (or H~~ x) and
+ * quad = x^T H~ x (or x^T H~~ x); HX or quad may be NULL.  FP64.
+ *
+ * Both wait for their work when a buffer is host memory.  Errors:
+ * INVALID_ARG (K outside 1 .. P, b < 1, NULL buffers), UNSUPPORTED, OOM,
+ * CUDA. */
+HESS_API hess_status hess_approx_form(hess_mlp* h, int K, const double* evals, const double* evecs, int full,
+                                      double lam_tilde, hess_precision prec, void* out);
+HESS_API hess_status hess_approx_apply(hess_mlp* h, int K, const double* evals, const double* evecs, int full,
+                                       double lam_tilde, const double* X, int b, double* HX, double* quad);
+
 /* Host helper: perm[i] = the index in the order of Eq. flatten of the i-th
  * parameter in "augmented row" order, where each output unit's weight row is
  * followed by its bias ([W_i,: , b_i] for every layer).  perm has P entries. */
@@ -371,7 +408,8 @@ typedef enum {
   HESS_K_HVP = 6,       /* Hessian-vector products over a block of directions */
   HESS_K_HLANCZOS = 7,  /* Lanczos steps on the Hessian operator (products,
                            reorthogonalisation) and its Ritz vectors */
-  HESS_K_COUNT = 8
+  HESS_K_APPROX = 8,    /* low-/full-rank approximations: forming, applying */
+  HESS_K_COUNT = 9
 } hess_kernel_class;
 
 typedef struct {

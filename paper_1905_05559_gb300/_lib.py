@@ -37,6 +37,7 @@ EXPORTS = (
     "hess_mlp_set_operand_limit", "hess_batch_create", "hess_batch_run", "hess_batch_destroy",
     "hess_autotune", "hess_autotune_entries", "hess_autotune_save", "hess_autotune_load",
     "hess_batch_set_graphs", "hess_curvature", "hessian_vector_products", "hessian_topk_eig",
+    "hess_approx_form", "hess_approx_apply", "hessian_minibatches",
 )
 
 REQUEST_KIND = {"hessian": 0, "opg": 1, "eig": 2}
@@ -60,7 +61,7 @@ class BatchInfo(ctypes.Structure):
 
 
 KERNEL_CLASS = {"syrk": 0, "hcontract": 1, "grads": 2, "rop": 3, "eig": 4, "hrest": 5, "hvp": 6,
-                "hlanczos": 7}
+                "hlanczos": 7, "approx": 8}
 
 
 class KernelStats(ctypes.Structure):
@@ -116,6 +117,14 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.hessian_topk_eig.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, vp, vp,
                                      ctypes.POINTER(ctypes.c_int)]
     lib.hessian_topk_eig.restype = st
+    lib.hessian_minibatches.argtypes = [vp, vp, vp, i64, i64, ctypes.c_int, vp]
+    lib.hessian_minibatches.restype = st
+    lib.hess_approx_form.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_int, vp]
+    lib.hess_approx_form.restype = st
+    lib.hess_approx_apply.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_double, vp,
+                                      ctypes.c_int, vp, vp]
+    lib.hess_approx_apply.restype = st
     lib.hess_param_permutation.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_int64)]
     lib.hess_param_permutation.restype = st

@@ -170,6 +170,39 @@ class HessMLP:
                                               ctypes.byref(steps)))
         return evals, evecs, steps.value
 
+    def hessian_minibatches(self, X, Y, bs, prec="fp64", out=None):
+        """Mini-batch Hessians of consecutive batches of bs examples (bs = 1:
+        per-example Hessians); returns an array (ceil(N / bs), P, P)."""
+        N = self._io(X, Y, prec)
+        nb = -(-N // max(int(bs), 1))
+        out = self._alloc_like(X, (nb, self.P, self.P), prec) if out is None else out
+        _lib.check(self._lib.hessian_minibatches(self.h, _ptr(X), _ptr(Y), N, int(bs),
+                                                 _lib.PRECISION[prec], _ptr(out)))
+        return out
+
+    def approx_form(self, evals, evecs, full=False, lam_tilde=float("nan"), prec="fp64", out=None):
+        """The low-rank (Sec. 4.1) or full-rank (Sec. 4.2) approximation from K
+        eigenpairs (evecs: K x P, row c = q_c), formed as a P x P matrix."""
+        K = int(evals.shape[0])
+        if tuple(evecs.shape) != (K, self.P):
+            raise ValueError(f"evecs must be {K} x {self.P}")
+        out = self._alloc_like(evecs, (self.P, self.P), prec) if out is None else out
+        _lib.check(self._lib.hess_approx_form(self.h, K, _ptr(evals), _ptr(evecs), 1 if full else 0,
+                                              float(lam_tilde), _lib.PRECISION[prec], _ptr(out)))
+        return out
+
+    def approx_apply(self, evals, evecs, X, full=False, lam_tilde=float("nan"), products=True):
+        """For each row x of X (b x P, float64): (H~ x rows or None, x^T H~ x)
+        without forming H~ (Sec. 5.5, 5.6)."""
+        K = int(evals.shape[0])
+        b = 1 if len(X.shape) == 1 else int(X.shape[0])
+        _check_dtype(X, "fp64", "X")
+        HX = self._alloc_like(X, tuple(X.shape), "fp64") if products else None
+        quad = self._alloc_like(X, (b,), "fp64")
+        _lib.check(self._lib.hess_approx_apply(self.h, K, _ptr(evals), _ptr(evecs), 1 if full else 0,
+                                               float(lam_tilde), _ptr(X), b, _ptr(HX), _ptr(quad)))
+        return HX, quad
+
     def curvature(self, X, Y, prec="bf16x3", opg=None, hessian=None, k=0, evals=None, evecs=None,
                   allow_deficient=False):
         """OPG, exact Hessian and top-k eigenpairs in one call (hess_curvature);

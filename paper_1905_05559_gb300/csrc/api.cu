@@ -99,6 +99,8 @@ hess_status host_side_init(hess_mlp* h) {
 }
 
 void host_side_free(hess_mlp* h) {
+  if (h->mb_batch) hess_batch_destroy(h->mb_batch);
+  h->mb_batch = nullptr;
   if (h->stream2) cudaStreamDestroy(h->stream2);
   if (h->stream3) cudaStreamDestroy(h->stream3);
   h->stream2 = h->stream3 = nullptr;
@@ -257,6 +259,10 @@ int pick_block(const Net& net, int64_t N, int jm, size_t elem) {
 }
 
 }  // namespace
+
+hess_status locate(const hess_mlp* h, const void* p, const char* name, int* on_dev) {
+  return classify(h, p, name, on_dev);
+}
 
 // Algorithmic flops of the Hessian row block d0..d0+B-1 against the columns
 // of weight layer jl that lie in the upper triangle (column >= row): 2 N per

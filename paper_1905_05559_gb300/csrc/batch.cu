@@ -350,6 +350,61 @@ hess_status hess_batch_run(hess_batch* b, const hess_batch_item* items, int coun
   return HESS_OK;
 }
 
+hess_status hessian_minibatches(hess_mlp* h, const void* X, const void* Y, int64_t N, int64_t bs,
+                                hess_precision prec, void* H) {
+  clear_error();
+  if (!h) return set_error(HESS_ERR_INVALID_ARG, "handle is NULL");
+  if (!X || !Y || !H) return set_error(HESS_ERR_INVALID_ARG, "X, Y and H must be non-NULL");
+  if (N < 1 || N > (1ll << 31) - 1) return set_error(HESS_ERR_INVALID_ARG, "N must be in 1 .. 2^31 - 1");
+  if (bs < 1) return set_error(HESS_ERR_INVALID_ARG, "the mini-batch size must be >= 1 (got %lld)", (long long)bs);
+  if (prec < HESS_FP64 || prec > HESS_BF16X3) return set_error(HESS_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+  HM_TRY(take_sticky_error(h));
+  const Net& net = h->net;
+  const int64_t P = net.P, T1 = net.T[0], TL = net.T[net.L - 1];
+  const int64_t nb = cdiv(N, bs);
+  const size_t es = prec == HESS_FP64 ? sizeof(double) : sizeof(float);
+  auto slice = [&](const void* base, int64_t b, int64_t per) {
+    return (const void*)((const char*)base + (size_t)(b * bs) * per * es);
+  };
+  const bool tc = prec == HESS_BF16 || prec == HESS_BF16X3;
+  int x_dev = 0, y_dev = 0, o_dev = 0;
+  HM_TRY(locate(h, X, "X", &x_dev));
+  HM_TRY(locate(h, Y, "Y", &y_dev));
+  HM_TRY(locate(h, H, "H", &o_dev));
+  if (!tc || !x_dev || !y_dev || !o_dev || nb == 1) {
+    // the single call per mini-batch
+    for (int64_t b = 0; b < nb; ++b) {
+      const int64_t n = N - b * bs < bs ? N - b * bs : bs;
+      void* Hb = (char*)H + (size_t)b * P * P * es;
+      HM_TRY(exact_hessian(h, slice(X, b, T1), slice(Y, b, TL), n, prec, Hb));
+    }
+    return HESS_OK;
+  }
+  Guard g(h->device);
+  if (!h->mb_batch) {
+    size_t fr = 0, tot = 0;
+    HM_CUDA(cudaMemGetInfo(&fr, &tot));
+    int64_t ws = (int64_t)4 << 30;
+    if ((int64_t)(fr / 4) < ws) ws = (int64_t)(fr / 4);
+    const int64_t floor_bytes = (int64_t)kSplitBytes + ((int64_t)256 << 20);
+    if (ws < floor_bytes) ws = floor_bytes;
+    HM_TRY(hess_batch_create(ws, h->stream, &h->mb_batch));
+  }
+  h->mb_batch->stream = h->stream;
+  std::vector<hess_batch_item> items((size_t)nb);
+  for (int64_t b = 0; b < nb; ++b) {
+    hess_batch_item& it = items[(size_t)b];
+    it.net = h;
+    it.X = static_cast<const float*>(slice(X, b, T1));
+    it.Y = static_cast<const float*>(slice(Y, b, TL));
+    it.N = N - b * bs < bs ? N - b * bs : bs;
+    it.opg = nullptr;
+    it.hessian = reinterpret_cast<float*>((char*)H + (size_t)b * P * P * es);
+  }
+  if (nb > 1 << 30) return set_error(HESS_ERR_INVALID_ARG, "too many mini-batches");
+  return hess_batch_run(h->mb_batch, items.data(), (int)nb, prec, nullptr);
+}
+
 hess_status hess_batch_set_graphs(hess_batch* b, int enable) {
   clear_error();
   if (!b) return set_error(HESS_ERR_INVALID_ARG, "batch is NULL");

@@ -131,6 +131,8 @@ struct hess_mlp {
   // the host) of the fused call, created on first use
   cudaStream_t stream2 = nullptr;
   cudaStream_t stream3 = nullptr;
+  // batch object of hessian_minibatches (created on first use)
+  hess_batch* mb_batch = nullptr;
   int sm_count = 0;
   // operand bytes above which the tensor-core Hessian is built and contracted
   // in chunks (one launch per chunk) instead of in one launch
@@ -147,6 +149,9 @@ void host_side_free(hess_mlp* h);
 // HESS_ERR_TIMEOUT (and clears the flag) if a kernel of an earlier call on
 // the handle gave up a pipeline wait.
 hess_status take_sticky_error(hess_mlp* h);
+// *on_dev = 1 for device (or managed) memory of the handle's device, 0 for
+// host memory; INVALID_ARG for another device's memory.
+hess_status locate(const hess_mlp* h, const void* p, const char* name, int* on_dev);
 // Copies n host tables through the pinned stage to device memory on s.
 hess_status stage_copy(PinnedStage& st, const void* const* src, const size_t* bytes, void* const* dst, int n,
                        cudaStream_t s);
