@@ -412,6 +412,24 @@ def opg_topk_eig(omega, widths, acts, X, Y, k, rank_tol=1e-13):
     return opg_topk_eig_from_grads(per_example_grads(omega, widths, acts, X, Y), k, rank_tol)
 
 
+def opg_topk_eig_direct(omega, widths, acts, X, Y, k, rank_tol=1e-13):
+    """The same eigenpairs from the P x P OPG itself (Sec. 4.1: the
+    eigendecomposition of the matrix; no Gram matrix, so N may be large).
+    numpy.linalg.eigh serves as the dense symmetric eigensolver step; null
+    directions as in opg_topk_eig_from_grads."""
+    M = opg(omega, widths, acts, X, Y)
+    lam, U = np.linalg.eigh(M)
+    order = np.argsort(lam)[::-1][:k]
+    lam = lam[order]
+    Q = U[:, order].copy()
+    deficient = False
+    for c in range(k):
+        if not (lam[c] > rank_tol * lam[0] and lam[c] > 0):
+            Q[:, c] = 0.0
+            deficient = True
+    return lam, canonical_sign(Q), deficient
+
+
 # ----------------------------------------------------------------------------
 # Memory-light routes for large P (same definitions, no N x P matrix)
 # ----------------------------------------------------------------------------

@@ -336,6 +336,17 @@ def test_opg_topk_eig_against_full_eigendecomposition():
     assert abs(mu_all.sum() - np.trace(OPG)) < 1e-12 * np.trace(OPG)
 
 
+def test_opg_eig_direct_route_matches_gram_route():
+    """The P x P route (eigendecomposition of the OPG itself) gives the Gram
+    route's eigenpairs (Eq. J): the same values and, for separated values,
+    the same vectors."""
+    pb = _tiny([7, 6, 4], ["sigmoid"], N=15, seed=12)
+    lg, Qg, _ = O.opg_topk_eig(pb.omega, pb.widths, pb.acts, pb.X, pb.Y, 6)
+    ld, Qd, _ = O.opg_topk_eig_direct(pb.omega, pb.widths, pb.acts, pb.X, pb.Y, 6)
+    assert np.allclose(ld, lg, rtol=0, atol=1e-12 * lg[0])
+    assert np.allclose(np.abs(np.sum(Qd * Qg, axis=0)), 1.0, atol=1e-9)
+
+
 def test_opg_topk_eig_rank_deficient():
     """Three examples of which two are identical: the Gram matrix has rank 2,
     so asking for 3 pairs flags the null space and returns a zero vector."""
