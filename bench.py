@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--step", default="fused", choices=["fused", "streams", "calls"],
                     help="fused: one hess_curvature call (two internal streams); streams: the "
                          "single calls on two handles and streams; calls: the single calls in turn")
-    ap.add_argument("--row", default=None, choices=["hessian-eig", "approx", "minibatch"],
+    ap.add_argument("--row", default=None, choices=["hessian-eig", "approx", "minibatch", "stream-eig"],
                     help="hessian-eig: top-k Hessian eigenpairs by Lanczos on H v products; "
                          "approx: low/full-rank approximations from them (own JSON lines)")
     ap.add_argument("--row-k", type=int, default=32)
@@ -694,6 +694,74 @@ def minibatch_bench(args):
     print(json.dumps(line), flush=True)
 
 
+def stream_eig_bench(args):
+    """Top-32 OPG eigenpairs of the 784-16-10 tanh network over N = 262144
+    seeded examples (the same distribution and seed as the MLP workload, 256x
+    the examples; beyond the Gram route's N limit), from chunks of 8192
+    examples: split-BF16 chunk OPGs summed into a P x P FP64 matrix, FP64
+    Lanczos on it.  metric: examples/s."""
+    import torch
+
+    import paper_1905_05559_gb300 as hm
+    from paper_1905_05559_gb300 import build
+    from synth import make_problem
+
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    lib = hm.load()
+    N, k, chunk = 262144, args.row_k, 8192
+    pb = make_problem([784, 16, 10], ["tanh"], N, 1, "uniform", "zero")
+    P = pb.P
+    net = hm.HessMLP(pb.widths, pb.acts, pb.omega, stream=stream.cuda_stream)
+    X = torch.as_tensor(pb.X, dtype=torch.float32, device="cuda")
+    Y = torch.as_tensor(pb.Y, dtype=torch.float32, device="cuda")
+    ev = torch.empty(k, dtype=torch.float64, device="cuda")
+    Q = torch.empty((k, P), dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        net.opg_topk_eig_streaming(X, Y, k, "bf16x3", chunk=chunk, evals=ev, evecs=Q)
+    torch.cuda.synchronize()
+    for cls in ("syrk", "eig"):
+        net.read_timing(cls)
+    net.timing(True)
+    sampler = ClockSampler(gpu_index(0))
+    sampler.start()
+    l0 = lib.hess_launch_count()
+    ms = []
+    for _ in range(args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        net.opg_topk_eig_streaming(X, Y, k, "bf16x3", chunk=chunk, evals=ev, evecs=Q)
+        e.record(stream)
+        e.synchronize()
+        ms.append(a.elapsed_time(e))
+    launches = (lib.hess_launch_count() - l0) / args.steps
+    clocks = sampler.stop()
+    net.timing(False)
+    syrk = net.read_timing("syrk")
+    eig = net.read_timing("eig")
+    t = statistics.median(ms)
+    peaks, src = measured_peaks()
+    achieved = 3.0 * syrk["flops"] / (syrk["ms"] * 1e-3) / 1e12 if syrk["ms"] > 0 else None
+    peak = peaks["bf16_tflops_sustained"]
+    line = {
+        "metric": f"examples/s (top-{k} OPG eigenpairs, streamed)", "impl": "ours", "value": N / (t * 1e-3),
+        "unit": "examples/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3 (OPG), f64 (eig)",
+        "data": "synthetic",
+        "config": {"workload": f"MLP [784, 16, 10] tanh, P={P}, N={N} (seed 1, x ~ U[0,1)), chunks of {chunk}; "
+                               f"top-{k} OPG eigenpairs", "l2": "inputs (822 MB) larger than L2"},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak if achieved else None, "traffic": None,
+                     "kernel_class": "syrk (chunk OPGs)", "peak_source": f"{src} bf16 sustained",
+                     "ms_per_step": syrk["ms"] / args.steps},
+        "eig_ms_per_step": eig["ms"] / args.steps,
+        "gpu_launches": launches, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # -------------------------------------------------------------- replicas ----
 def max_over_ranks(value: float, dist=None, device="cpu") -> float:
     """Replicas only: every rank runs the whole workload on its own GPU and
@@ -763,6 +831,9 @@ def main():
         return
     if args.row == "minibatch":
         minibatch_bench(args)
+        return
+    if args.row == "stream-eig":
+        stream_eig_bench(args)
         return
 
     import numpy as np

@@ -158,6 +158,21 @@ HESS_API hess_status exact_hessian(hess_mlp* h, const void* X, const void* Y, in
 HESS_API hess_status opg_topk_eig(hess_mlp* h, const void* X, const void* Y, int64_t N, int k,
                          hess_precision prec, double* evals, double* evecs);
 
+/* Top-k OPG eigenpairs for data sets whose N x P gradient matrix is not held
+ * at once (Sec. 5.4 works through mini-batches of examples; here uncentred,
+ * as Eq. J states).  The examples are taken in chunks of `chunk`; each
+ * chunk's OPG comes from opg() in precision prec (so at most one chunk's
+ * gradients exist at a time) and is added, weighted by its share of the
+ * examples, into a P x P FP64 sum, whose top-k eigenpairs come from the same
+ * FP64 Lanczos, tridiagonal eigensolver and checks as opg_topk_eig.  Needs
+ * P^2 doubles of device memory (a second workspace the handle keeps) but no
+ * N x N Gram matrix, so N may exceed what opg_topk_eig accepts.  X, Y in the
+ * precision's dtype, host or device (host chunks are staged one at a time);
+ * evals/evecs as in opg_topk_eig.  Requires 1 <= k <= min(N, P).  Waits for
+ * its work.  Errors: those of opg() and opg_topk_eig. */
+HESS_API hess_status opg_topk_eig_streaming(hess_mlp* h, const void* X, const void* Y, int64_t N, int k,
+                                            hess_precision prec, int64_t chunk, double* evals, double* evecs);
+
 /* OPG, exact Hessian and top-k OPG eigenpairs of one data set in one call
  * (any of them may be left out: OPG or H NULL, k = 0).  The same results as
  * opg(), exact_hessian() and opg_topk_eig() with the same arguments, but

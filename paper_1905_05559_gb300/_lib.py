@@ -37,7 +37,7 @@ EXPORTS = (
     "hess_mlp_set_operand_limit", "hess_batch_create", "hess_batch_run", "hess_batch_destroy",
     "hess_autotune", "hess_autotune_entries", "hess_autotune_save", "hess_autotune_load",
     "hess_batch_set_graphs", "hess_curvature", "hessian_vector_products", "hessian_topk_eig",
-    "hess_approx_form", "hess_approx_apply", "hessian_minibatches",
+    "hess_approx_form", "hess_approx_apply", "hessian_minibatches", "opg_topk_eig_streaming",
 )
 
 REQUEST_KIND = {"hessian": 0, "opg": 1, "eig": 2}
@@ -117,6 +117,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.hessian_topk_eig.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, vp, vp,
                                      ctypes.POINTER(ctypes.c_int)]
     lib.hessian_topk_eig.restype = st
+    lib.opg_topk_eig_streaming.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, i64, vp, vp]
+    lib.opg_topk_eig_streaming.restype = st
     lib.hessian_minibatches.argtypes = [vp, vp, vp, i64, i64, ctypes.c_int, vp]
     lib.hessian_minibatches.restype = st
     lib.hess_approx_form.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_double,

@@ -170,6 +170,21 @@ class HessMLP:
                                               ctypes.byref(steps)))
         return evals, evecs, steps.value
 
+    def opg_topk_eig_streaming(self, X, Y, k, prec="fp64", chunk=8192, evals=None, evecs=None,
+                               allow_deficient=False):
+        """Top-k OPG eigenpairs from chunks of examples (P x P FP64 sum, no
+        Gram matrix).  Returns (evals (k,), evecs (k, P), status)."""
+        N = self._io(X, Y, prec)
+        if evals is None:
+            evals = self._alloc_like(X, (k,), "fp64")
+        if evecs is None:
+            evecs = self._alloc_like(X, (k, self.P), "fp64")
+        allow = (_lib.HESS_ERR_RANK_DEFICIENT,) if allow_deficient else ()
+        st = _lib.check(self._lib.opg_topk_eig_streaming(self.h, _ptr(X), _ptr(Y), N, int(k),
+                                                         _lib.PRECISION[prec], int(chunk), _ptr(evals),
+                                                         _ptr(evecs)), allow)
+        return evals, evecs, st
+
     def hessian_minibatches(self, X, Y, bs, prec="fp64", out=None):
         """Mini-batch Hessians of consecutive batches of bs examples (bs = 1:
         per-example Hessians); returns an array (ceil(N / bs), P, P)."""

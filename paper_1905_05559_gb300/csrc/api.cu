@@ -162,6 +162,25 @@ void stage_free(PinnedStage& st) {
   cudaGetLastError();
 }
 
+hess_status ensure_ws2(hess_mlp* h, size_t bytes) {
+  if (bytes <= h->ws2_bytes) return HESS_OK;
+  if (h->ws2) {
+    HM_CUDA(cudaStreamSynchronize(h->stream));
+    HM_CUDA(cudaFree(h->ws2));
+    h->ws2 = nullptr;
+    h->ws2_bytes = 0;
+  }
+  const size_t nb = align_up(bytes, (size_t)1 << 20);
+  cudaError_t e = cudaMalloc(&h->ws2, nb);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    h->ws2 = nullptr;
+    return set_error(HESS_ERR_OOM, "second workspace of %zu bytes: %s", nb, cudaGetErrorString(e));
+  }
+  h->ws2_bytes = nb;
+  return HESS_OK;
+}
+
 hess_status ensure_ws(hess_mlp* h, size_t bytes) {
   if (g_dry_bytes) {
     *g_dry_bytes = bytes;
@@ -581,6 +600,7 @@ hess_status hess_mlp_destroy(hess_mlp* h) {
     cudaFree(h->omega32);
   }
   cudaFree(h->ws);
+  if (h->ws2) cudaFree(h->ws2);
   host_side_free(h);
   for (auto& r : h->pending) {
     cudaEventDestroy(r.a);

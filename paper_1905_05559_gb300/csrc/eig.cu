@@ -776,7 +776,7 @@ __global__ void finalize_kernel(double* evecs, int64_t P, const double* theta, i
     for (int64_t i = threadIdx.x; i < P; i += blockDim.x) q[i] = 0.0;
     return;
   }
-  double sc = 1.0 / sqrt(N * mu);
+  const double sc = N > 0.0 ? 1.0 / sqrt(N * mu) : 1.0;  // N = 0: the vectors are eigenvectors already
   double best = -1.0;
   int64_t bi = 0;
   for (int64_t i = threadIdx.x; i < P; i += blockDim.x) {
@@ -870,76 +870,57 @@ hess_status tridiag_topk(const double* a, const double* b, int m, int k, double*
   return HESS_OK;
 }
 
-hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, int64_t N, int k,
-                          double* evals_d, double* evecs_d, Arena& ar, bool dry, EigResult* res) {
-  const int64_t P = net.P;
-  const int L = net.L;
-  int64_t mcap = N < (int64_t)8 * k + 512 ? N : (int64_t)8 * k + 512;
-  double* M = ar.take<double>(N * N);
-  double* DD = ar.take<double>(N * N);
-  double* AA = ar.take<double>(N * N);
-  double* G = ar.take<double>(N * P);
-  double* Q = AA;   // reused once the Gram matrix is formed (mcap <= N)
-  double* MQ = DD;  // likewise
-  double* w = ar.take<double>(N);
-  double* wt = ar.take<double>(N);
-  double* dpart = ar.take<double>((mcap + 1) * 8);
-  double* npart = ar.take<double>(4096);
-  double* apart = ar.take<double>(4096);
-  double* h1 = ar.take<double>(mcap + 1);
-  double* h2 = ar.take<double>(mcap + 1);
-  double* alpha = ar.take<double>(mcap + 1);
-  double* beta = ar.take<double>(mcap + 1);
-  double* theta = ar.take<double>(k);
-  double* Y = ar.take<double>((int64_t)k * mcap);
-  double* U = ar.take<double>(N * k);
-  unsigned* bar = ar.take<unsigned>(64);
-  int* err = ar.take<int>(1);
-  int* cstart = ar.take<int>(k);
-  double* rr = ar.take<double>(k);
-  double* mx = ar.take<double>(2);
-  int* flag = ar.take<int>(2);
-  int* stop = ar.take<int>(1);
+// Lanczos buffers of an n x n symmetric problem (Q and MQ: mcap x n; given
+// by the caller to reuse its memory, or taken from the arena).
+struct LzBufs {
+  int64_t n = 0, mcap = 0;
+  double *Q = nullptr, *MQ = nullptr, *w = nullptr, *wt = nullptr, *dpart = nullptr, *npart = nullptr,
+         *apart = nullptr, *h1 = nullptr, *h2 = nullptr, *alpha = nullptr, *beta = nullptr, *theta = nullptr,
+         *Y = nullptr, *rr = nullptr, *mx = nullptr, *tri_scratch = nullptr;
+  unsigned* bar = nullptr;
+  int *err = nullptr, *cstart = nullptr, *stop = nullptr;
+};
+
+void plan_lz(Arena& ar, int64_t n, int k, LzBufs& b, double* Q, double* MQ) {
+  b.n = n;
+  b.mcap = n < (int64_t)8 * k + 512 ? n : (int64_t)8 * k + 512;
+  const int64_t mcap = b.mcap;
+  b.Q = Q ? Q : ar.take<double>(mcap * n);
+  b.MQ = MQ ? MQ : ar.take<double>(mcap * n);
+  b.w = ar.take<double>(n);
+  b.wt = ar.take<double>(n);
+  b.dpart = ar.take<double>((mcap + 1) * 8);
+  b.npart = ar.take<double>(4096);
+  b.apart = ar.take<double>(4096);
+  b.h1 = ar.take<double>(mcap + 1);
+  b.h2 = ar.take<double>(mcap + 1);
+  b.alpha = ar.take<double>(mcap + 1);
+  b.beta = ar.take<double>(mcap + 1);
+  b.theta = ar.take<double>(k);
+  b.Y = ar.take<double>((int64_t)k * mcap);
+  b.bar = ar.take<unsigned>(64);
+  b.err = ar.take<int>(1);
+  b.cstart = ar.take<int>(k);
+  b.rr = ar.take<double>(k);
+  b.mx = ar.take<double>(2);
+  b.stop = ar.take<int>(1);
   // global scratch of the tridiagonal kernels when shared memory is too small
   const int64_t tri_n = tridiag_scratch_doubles(mcap, k);
-  double* tri_scratch = tri_n ? ar.take<double>(tri_n) : nullptr;
-  if (dry) return HESS_OK;
+  b.tri_scratch = tri_n ? ar.take<double>(tri_n) : nullptr;
+}
+
+// Steps 2-3 on the resident n x n matrix M: Lanczos with full
+// reorthogonalisation, extended until the top-k residual bounds converge;
+// on return b.theta and b.Y hold the top-k Ritz values and the eigenvectors
+// of T_m (rows of Y, stride mcap), *m_out the Krylov dimension.
+hess_status run_lz(hess_mlp* h, const double* M, int k, LzBufs& b, int* m_out, bool* converged_out) {
+  const int64_t N = b.n, mcap = b.mcap;
+  double *Q = b.Q, *MQ = b.MQ, *w = b.w, *wt = b.wt, *dpart = b.dpart, *npart = b.npart, *apart = b.apart,
+         *h1 = b.h1, *h2 = b.h2, *alpha = b.alpha, *beta = b.beta, *theta = b.theta, *Y = b.Y, *rr = b.rr,
+         *mx = b.mx, *tri_scratch = b.tri_scratch;
+  unsigned* bar = b.bar;
+  int *err = b.err, *cstart = b.cstart, *stop = b.stop;
   cudaStream_t s = h->stream;
-
-  // 1. Gram matrix, factored by layer
-  HM_TRY(fill(M, N * N, 0.0, s));
-  for (int wl = 1; wl <= L - 1; ++wl) {
-    const int Tin = net.T[wl - 1], Tout = net.T[wl];
-    Gemm<double> g;
-    g.M = (int)N;
-    g.N = (int)N;
-    g.K = Tout;
-    g.A = c.d[wl];
-    g.sam = Tout;
-    g.sak = 1;
-    g.B = c.d[wl];
-    g.sbk = 1;
-    g.sbn = Tout;
-    g.C = DD;
-    g.scm = N;
-    g.scn = 1;
-    g.upper = 1;
-    HM_TRY(gemm(g, s));
-    g.K = Tin;
-    g.A = c.a[wl - 1];
-    g.sam = Tin;
-    g.B = c.a[wl - 1];
-    g.sbn = Tin;
-    g.C = AA;
-    HM_TRY(gemm(g, s));
-    gram_acc_kernel<<<(unsigned)(cdiv(N * N, 256) < 65536 ? cdiv(N * N, 256) : 65536), 256, 0, s>>>(
-        M, DD, AA, N * N, 1.0 / (double)N);
-    HM_LAUNCHED();
-  }
-  HM_TRY(mirror_upper(M, N, N, s));
-
-  // 2-3. Lanczos with full reorthogonalisation, extended until the top-k
-  // residual bounds converge
   const uint64_t key = 0x5DEECE66Dull;
   // ownership: E entries per block over at most one block per SM; shared
   // memory holds the coefficients and the owned slices, then, as far as they
@@ -1052,6 +1033,67 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
     if (target > mcap) target = mcap;
     if (target > N) target = N;
   }
+  *m_out = m;
+  *converged_out = converged;
+  return HESS_OK;
+}
+
+hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, int64_t N, int k,
+                          double* evals_d, double* evecs_d, Arena& ar, bool dry, EigResult* res) {
+  const int64_t P = net.P;
+  const int L = net.L;
+  double* M = ar.take<double>(N * N);
+  double* DD = ar.take<double>(N * N);
+  double* AA = ar.take<double>(N * N);
+  double* G = ar.take<double>(N * P);
+  LzBufs lb;
+  // the basis and M Q reuse AA and DD once the Gram matrix is formed
+  plan_lz(ar, N, k, lb, AA, DD);
+  const int64_t mcap = lb.mcap;
+  double* U = ar.take<double>(N * k);
+  int* flag = ar.take<int>(2);
+  double* theta = lb.theta;
+  double* Y = lb.Y;
+  double* Q = lb.Q;
+  double* hp = h->host_pinned;
+  if (dry) return HESS_OK;
+  cudaStream_t s = h->stream;
+
+  // 1. Gram matrix, factored by layer
+  HM_TRY(fill(M, N * N, 0.0, s));
+  for (int wl = 1; wl <= L - 1; ++wl) {
+    const int Tin = net.T[wl - 1], Tout = net.T[wl];
+    Gemm<double> g;
+    g.M = (int)N;
+    g.N = (int)N;
+    g.K = Tout;
+    g.A = c.d[wl];
+    g.sam = Tout;
+    g.sak = 1;
+    g.B = c.d[wl];
+    g.sbk = 1;
+    g.sbn = Tout;
+    g.C = DD;
+    g.scm = N;
+    g.scn = 1;
+    g.upper = 1;
+    HM_TRY(gemm(g, s));
+    g.K = Tin;
+    g.A = c.a[wl - 1];
+    g.sam = Tin;
+    g.B = c.a[wl - 1];
+    g.sbn = Tin;
+    g.C = AA;
+    HM_TRY(gemm(g, s));
+    gram_acc_kernel<<<(unsigned)(cdiv(N * N, 256) < 65536 ? cdiv(N * N, 256) : 65536), 256, 0, s>>>(
+        M, DD, AA, N * N, 1.0 / (double)N);
+    HM_LAUNCHED();
+  }
+  HM_TRY(mirror_upper(M, N, N, s));
+
+  int m = 0;
+  bool converged = false;
+  HM_TRY(run_lz(h, M, k, lb, &m, &converged));
   res->lanczos_steps = m;
   {
     double f = 0.0;
@@ -1100,6 +1142,49 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   finalize_kernel<<<k, 256, 0, s>>>(evecs_d, P, theta, k, (double)N, evals_d, flag + 1);
   HM_LAUNCHED();
   int* hi = reinterpret_cast<int*>(hp);
+  HM_CUDA(cudaMemcpyAsync(hi, flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HM_CUDA(cudaStreamSynchronize(s));
+  res->rank_deficient = hi[0];
+  return HESS_OK;
+}
+
+hess_status topk_eig_dense(hess_mlp* h, const double* M, int64_t n, int k, double* evals_d, double* evecs_d,
+                           Arena& ar, bool dry, EigResult* res) {
+  LzBufs lb;
+  plan_lz(ar, n, k, lb, nullptr, nullptr);
+  int* flag = ar.take<int>(2);
+  if (dry) return HESS_OK;
+  cudaStream_t s = h->stream;
+  int m = 0;
+  bool converged = false;
+  HM_TRY(run_lz(h, M, k, lb, &m, &converged));
+  res->lanczos_steps = m;
+  {
+    double f = 0.0;
+    for (int j = 0; j < m; ++j) f += 2.0 * n * n + 8.0 * n * (j + 1);
+    f += 2.0 * n * m * k;
+    res->flops = f;
+  }
+  res->converged = converged ? 1 : 0;
+  // Ritz vectors: row c of evecs = sum_j Y[c][j] q_j
+  Gemm<double> g;
+  g.M = (int)n;
+  g.N = k;
+  g.K = m;
+  g.A = lb.Q;
+  g.sam = 1;
+  g.sak = n;
+  g.B = lb.Y;
+  g.sbk = 1;
+  g.sbn = lb.mcap;
+  g.C = evecs_d;
+  g.scm = 1;
+  g.scn = n;
+  HM_TRY(gemm(g, s));
+  HM_CUDA(cudaMemsetAsync(flag + 1, 0, sizeof(int), s));
+  finalize_kernel<<<k, 256, 0, s>>>(evecs_d, n, lb.theta, k, 0.0, evals_d, flag + 1);
+  HM_LAUNCHED();
+  int* hi = reinterpret_cast<int*>(h->host_pinned);
   HM_CUDA(cudaMemcpyAsync(hi, flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
   HM_CUDA(cudaStreamSynchronize(s));
   res->rank_deficient = hi[0];

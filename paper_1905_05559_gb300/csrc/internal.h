@@ -133,6 +133,10 @@ struct hess_mlp {
   cudaStream_t stream3 = nullptr;
   // batch object of hessian_minibatches (created on first use)
   hess_batch* mb_batch = nullptr;
+  // second growable device buffer, for results that the single-call entry
+  // points (which plan from the start of ws) must not overwrite
+  char* ws2 = nullptr;
+  size_t ws2_bytes = 0;
   int sm_count = 0;
   // operand bytes above which the tensor-core Hessian is built and contracted
   // in chunks (one launch per chunk) instead of in one launch
@@ -142,6 +146,7 @@ struct hess_mlp {
 namespace hm {
 
 hess_status ensure_ws(hess_mlp* h, size_t bytes);
+hess_status ensure_ws2(hess_mlp* h, size_t bytes);
 
 // Host-side resources of a handle (pinned scratch, mapped error flag).
 hess_status host_side_init(hess_mlp* h);
@@ -302,6 +307,12 @@ hess_status tridiag_topk(const double* a, const double* b, int m, int k, double*
                          double* scratch, cudaStream_t s);
 hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, int64_t N, int k,
                           double* evals_d, double* evecs_d, Arena& ar, bool dry, EigResult* res);
+// Top-k eigenpairs of a resident symmetric n x n FP64 matrix M (row-major):
+// the same Lanczos, tridiagonal eigensolver and checks as the Gram route;
+// evecs_d row c = the unit eigenvector of evals_d[c] (sign canonicalised;
+// zero when evals_d[c] <= 1e-13 evals_d[0], flagged in res->rank_deficient).
+hess_status topk_eig_dense(hess_mlp* h, const double* M, int64_t n, int k, double* evals_d, double* evecs_d,
+                           Arena& ar, bool dry, EigResult* res);
 
 // ------------------------------------------------------ tensor cores ----
 namespace tc {
