@@ -1056,6 +1056,17 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   double* Y = lb.Y;
   double* Q = lb.Q;
   double* hp = h->host_pinned;
+  // wide layer inputs (A A^T over K = T_in >= 128) go to the tensor cores as
+  // exact-digit FP64 products
+  int64_t ktc = 0;
+  for (int wl = 1; wl <= L - 1; ++wl)
+    if (f64_syrk_tc_eligible(h, N, net.T[wl - 1]) && net.T[wl - 1] > ktc) ktc = net.T[wl - 1];
+  F64SyrkScratch fs;
+  if (ktc) plan_f64_syrk(ar, N, ktc, fs);
+  // and so does the back-projection G^T U (K = N)
+  const bool bp_tc = f64_gemm_nt_tc_eligible(h, P, k, N);
+  F64GemmScratch fb;
+  if (bp_tc) plan_f64_gemm_nt(ar, P, k, N, fb);
   if (dry) return HESS_OK;
   cudaStream_t s = h->stream;
 
@@ -1078,13 +1089,17 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
     g.scn = 1;
     g.upper = 1;
     HM_TRY(gemm(g, s));
-    g.K = Tin;
-    g.A = c.a[wl - 1];
-    g.sam = Tin;
-    g.B = c.a[wl - 1];
-    g.sbn = Tin;
-    g.C = AA;
-    HM_TRY(gemm(g, s));
+    if (ktc && Tin >= 128 && Tin <= ktc) {
+      HM_TRY(f64_syrk_tc(h, c.a[wl - 1], Tin, Tin, AA, N, fs, s));
+    } else {
+      g.K = Tin;
+      g.A = c.a[wl - 1];
+      g.sam = Tin;
+      g.B = c.a[wl - 1];
+      g.sbn = Tin;
+      g.C = AA;
+      HM_TRY(gemm(g, s));
+    }
     gram_acc_kernel<<<(unsigned)(cdiv(N * N, 256) < 65536 ? cdiv(N * N, 256) : 65536), 256, 0, s>>>(
         M, DD, AA, N * N, 1.0 / (double)N);
     HM_LAUNCHED();
@@ -1122,7 +1137,9 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
     HM_TRY(gemm(g, s));
   }
   HM_TRY(write_grads(net, c, G, P, s));
-  {
+  if (bp_tc) {
+    HM_TRY(f64_gemm_nt_tc(h, G, P, U, 1, k, N, evecs_d, 1, P, fb, s));
+  } else {
     Gemm<double> g;
     g.M = (int)P;
     g.N = k;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -332,6 +333,7 @@ struct Job {
                   // 1: Hessian rows of one weight layer, W columns
                   // 2: Hessian rows of one weight layer (W rows and, from the
                   //    ones row of A, bias rows), columns after W
+                  // 3: a general product (orow = m, ocol = n, no mirror)
   float scale;
   float* out;
   int64_t ldo;
@@ -343,6 +345,52 @@ struct Job {
   int64_t brow;   // mode 2: B rows per unit
 };
 }  // namespace tc
+
+// Scratch of an exact-digit FP64 product A A^T on the tensor cores (n rows,
+// K columns): digit planes, row exponents, the FP32 results of a group of
+// digit pairs, and the launch tables.
+struct F64SyrkScratch {
+  int64_t n = 0, ldk = 0;
+  __nv_bfloat16* D = nullptr;  // digits side by side along K, and reversed
+  __nv_bfloat16* R = nullptr;
+  int* ex = nullptr;
+  float* T = nullptr;
+  int group = 1;
+  tc::Job* jobs = nullptr;
+  int4* tiles = nullptr;
+};
+// Usable when the tensor-core path is (sm_103, tensor-map encoder),
+// 128 <= K <= 4096 (exact FP32 sums of the digit products) and
+// 128 <= n <= 16384.
+bool f64_syrk_tc_eligible(hess_mlp* h, int64_t n, int64_t K);
+void plan_f64_syrk(Arena& ar, int64_t n, int64_t K, F64SyrkScratch& fs);
+// Upper triangle (and diagonal) of C = A A^T for row-major FP64 A (n x K,
+// stride lda), accurate to FP64 rounding; C's lower triangle is not written.
+hess_status f64_syrk_tc(hess_mlp* h, const double* A, int64_t lda, int64_t K, double* C, int64_t ldc,
+                        const F64SyrkScratch& fs, cudaStream_t s);
+
+// Scratch of an exact-digit FP64 product C = G^T B^T on the tensor cores
+// (G: K x M row-major, B rows of length K): digits of the rows of G^T
+// (side by side along K) and of B (reversed), exponents, the FP32 results of
+// a group of contractions, and the launch tables.
+struct F64GemmScratch {
+  int64_t M = 0, Nn = 0, ldk = 0;
+  __nv_bfloat16* DA = nullptr;
+  __nv_bfloat16* RB = nullptr;
+  int *exA = nullptr, *exB = nullptr;
+  float* T = nullptr;
+  int group = 1;
+  tc::Job* jobs = nullptr;
+  int4* tiles = nullptr;
+};
+// Usable when the tensor-core path is, 128 <= K <= 4096, M >= 128 and
+// 1 <= Nn <= 256 (one tile column).
+bool f64_gemm_nt_tc_eligible(hess_mlp* h, int64_t M, int64_t Nn, int64_t K);
+void plan_f64_gemm_nt(Arena& ar, int64_t M, int64_t Nn, int64_t K, F64GemmScratch& fs);
+// C(m, c) = sum_k G[k][m] B(c, k), B(c, k) = B[c b_rs + k b_ks], written to
+// C[m scm + c scn], accurate to FP64 rounding.
+hess_status f64_gemm_nt_tc(hess_mlp* h, const double* G, int64_t ldg, const double* B, int64_t b_rs, int64_t b_ks,
+                           int64_t K, double* C, int64_t scm, int64_t scn, const F64GemmScratch& fs, cudaStream_t s);
 
 // Jobs and tiles gathered for one persistent launch.
 struct TcPlan {

@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <atomic>
 #include <functional>
 #include <map>
@@ -236,7 +237,7 @@ __device__ __forceinline__ int64_t wrow_unit(int64_t r, int64_t Tin, int64_t Tou
 
 __device__ __forceinline__ void row_map(const Job& p, int64_t m, int tile_y, int64_t& orow,
                                         int64_t& ocolb) {
-  if (p.mode == 0) {
+  if (p.mode == 0 || p.mode == 3) {
     orow = m;
     ocolb = 0;
     return;
@@ -431,6 +432,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int64_t pM = p.M, Nn = p.Nn, ldo = p.ldo;
       const float scale = p.scale;
       float* const out = p.out;
+      const bool sym = p.mode != 3;  // mode 3: a general product, every entry direct
       const int nchunk = (p.nkb + CHUNK_KB - 1) / CHUNK_KB;
       const int acc = tcount & 1;
       const bool got = mbar_wait(tfull(acc), fulls[acc] & 1u, L.err, abort_flag);
@@ -480,7 +482,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int64_t n = n0 + jj;
           const float val = v[jj] * scale;
           e[lane * EPI_LD + jj] = val;
-          if (rvalid && n < Nn) {
+          if (sym && rvalid && n < Nn) {
             const int64_t ocol = ocolb + n;
             if (ocol > orow) __stcs(out + ocol * ldo + orow, val);
           }
@@ -494,7 +496,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int64_t orow_i = srow[i];
           if (orow_i >= 0 && n < Nn) {
             const int64_t ocol = scol[i] + n;
-            if (ocol >= orow_i) __stcs(out + orow_i * ldo + ocol, e[i * EPI_LD + jj]);
+            if (!sym || ocol >= orow_i) __stcs(out + orow_i * ldo + ocol, e[i * EPI_LD + jj]);
           }
         }
         __syncwarp();
@@ -1557,6 +1559,340 @@ hess_status run_hessian_tc(hess_mlp* h, const void* X, const void* Y, int64_t N,
   HM_TRY(tc_available(h));
   if (hessian_plan_bytes(h, N) <= h->op_limit) return run_single(h, X, Y, N, x3, Hout, 1);
   return run_hessian_chunked(h, X, Y, N, x3, Hout);
+}
+
+// ============================================ exact-digit FP64 products
+// A FP64 product A A^T on the BF16 tensor cores (the splitting scheme of
+// Ozaki et al.): each row r of A is scaled by 2^-e_r (its largest magnitude
+// below 1) and written as eight signed integer digits,
+//   a = 2^e_r sum_d q_d 2^(-6 - 7d),   |q_d| <= 64,
+// exact to 2^-56 of the row's largest entry.  The digit products of equal
+// weight, sum over d + d' = w of Q_d Q_d'^T, are one contraction over the
+// digits laid side by side along K (Q_0 | Q_1 | ... against the reversed
+// order Q_7 | ... | Q_0); a contraction spans at most 4096 products per
+// entry, so with |q q'| <= 2^12 its FP32 sums stay below 2^24 and are exact.
+// The few integer matrices are combined in FP64 with their weights
+// 2^(e_r + e_c - 12 - 7w), smallest first.  Groups of contractions whose
+// FP32 results fit a bounded buffer run one persistent launch each.
+namespace {
+
+constexpr int kDigits = 8;
+constexpr size_t kPairBudget = (size_t)1 << 30;
+constexpr int64_t kExactK = 4096;  // products per entry with exact FP32 sums
+
+struct JobWeightsFwd {
+  double w[2 * kDigits * kDigits];  // 2^(-12 - 7w) of each contraction of the group
+  int count;
+};
+
+// Row digits: fwd[r][d ldk + k] = q_d and rev[r][(7 - d) ldk + k] = q_d.  The
+// row's value scaled into (-1, 1) becomes the integer m = v 2^62 (dropping
+// below 2^-62), whose digits come off by rounding shifts.
+__global__ void digits_rows_kernel(const double* A, int64_t rs, int64_t ks, int64_t n, int64_t K, int64_t ldk,
+                                   __nv_bfloat16* fwd, __nv_bfloat16* rev, int* ex) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= n) return;
+  const double* a = A + r * rs;  // element (r, k) = a[k * ks]
+  double mx = 0.0;
+  for (int64_t k = lane; k < K; k += 32) mx = fmax(mx, fabs(a[k * ks]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  int E = 0;
+  if (mx > 0.0 && mx <= DBL_MAX) frexp(mx, &E);  // mx = f 2^E, f in [0.5, 1)
+  if (lane == 0) ex[r] = E;
+  const int64_t L = (int64_t)kDigits * ldk;
+  __nv_bfloat16* fr = fwd ? fwd + r * L : nullptr;
+  __nv_bfloat16* rr = rev ? rev + r * L : nullptr;
+  for (int64_t k = lane; k < ldk; k += 32) {
+    long long m = k < K ? __double2ll_rn(ldexp(a[k * ks], 62 - E)) : 0ll;  // |m| < 2^62
+#pragma unroll
+    for (int d = 0; d < kDigits; ++d) {
+      const int sh = 56 - 7 * d;
+      const long long q = (m + (1ll << (sh - 1))) >> sh;  // round to nearest
+      m -= q << sh;
+      const __nv_bfloat16 v = __int2bfloat16_rn((int)q);  // |q| <= 64: exact
+      if (fr) fr[(int64_t)d * ldk + k] = v;
+      if (rr) rr[(int64_t)(kDigits - 1 - d) * ldk + k] = v;
+    }
+  }
+}
+
+// ex[c] for the columns of a row-major n x m FP64 array G (the rows of G^T):
+// the exponent E with max_r |G[r][c]| = f 2^E, f in [0.5, 1).  Block (32 x 8):
+// 32 adjacent columns, 8 slices of the rows.
+__global__ void colmax_exp_kernel(const double* G, int64_t ldg, int64_t n, int64_t m, int* ex) {
+  __shared__ double red[8][33];
+  const int64_t c = blockIdx.x * (int64_t)32 + threadIdx.x;
+  double mx = 0.0;
+  if (c < m) {
+    double m0 = 0.0, m1 = 0.0;
+    int64_t r = threadIdx.y;
+    for (; r + 8 < n; r += 16) {
+      m0 = fmax(m0, fabs(G[r * ldg + c]));
+      m1 = fmax(m1, fabs(G[(r + 8) * ldg + c]));
+    }
+    if (r < n) m0 = fmax(m0, fabs(G[r * ldg + c]));
+    mx = fmax(m0, m1);
+  }
+  red[threadIdx.y][threadIdx.x] = mx;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < m) {
+    for (int y = 1; y < 8; ++y) mx = fmax(mx, red[y][threadIdx.x]);
+    int E = 0;
+    if (mx > 0.0 && mx <= DBL_MAX) frexp(mx, &E);
+    ex[c] = E;
+  }
+}
+
+// Digits of the rows of G^T (G row-major n x m): fwd[c][d ldk + r] = q_d of
+// G[r][c] scaled by 2^-ex[c]; rows r in [n, ldk) are zero.  A 32 x 32 tile
+// is read along c and written along r through shared memory.
+__global__ void digits_cols_kernel(const double* G, int64_t ldg, int64_t n, int64_t m, const int* ex, int64_t ldk,
+                                   __nv_bfloat16* fwd) {
+  __shared__ double t[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const int64_t r = r0 + y, c = c0 + threadIdx.x;
+    t[y][threadIdx.x] = (r < n && c < m) ? G[r * ldg + c] : 0.0;
+  }
+  __syncthreads();
+  const int64_t L = (int64_t)kDigits * ldk;
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const int64_t c = c0 + y, r = r0 + threadIdx.x;
+    if (c >= m || r >= ldk) continue;
+    long long q_m = __double2ll_rn(ldexp(t[threadIdx.x][y], 62 - ex[c]));
+    __nv_bfloat16* fr = fwd + c * L;
+#pragma unroll
+    for (int d = 0; d < kDigits; ++d) {
+      const int sh = 56 - 7 * d;
+      const long long q = (q_m + (1ll << (sh - 1))) >> sh;
+      q_m -= q << sh;
+      fr[(int64_t)d * ldk + r] = __int2bfloat16_rn((int)q);
+    }
+  }
+}
+
+// C(r, c) = 2^(eA_r + eB_c) sum_j w_j T_j[r][c] (T_j: M x Nn), written to
+// C[r scm + c scn] (added when accumulate is set).
+__global__ void combine_general_kernel(const float* T, int64_t M, int64_t Nn, JobWeightsFwd jw, const int* exA,
+                                       const int* exB, double* C, int64_t scm, int64_t scn, int accumulate) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= M * Nn) return;
+  const int64_t r = idx / Nn, c = idx % Nn;
+  const size_t plane = (size_t)M * Nn;
+  double s = 0.0;
+  for (int j = 0; j < jw.count; ++j) s = fma((double)T[(size_t)j * plane + idx], jw.w[j], s);
+  s = ldexp(s, exA[r] + exB[c]);
+  double* o = C + r * scm + c * scn;
+  *o = accumulate ? *o + s : s;
+}
+
+using JobWeights = JobWeightsFwd;
+
+// Upper triangle (c >= r) of C = 2^(e_r + e_c) sum_j w_j T_j, added to C when
+// accumulate is set; contractions in the order given (smallest weights
+// first).
+__global__ void combine_upper_kernel(const float* T, int64_t n, JobWeights jw, const int* ex, double* C, int64_t ldc,
+                                     int accumulate) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t r = blockIdx.y;
+  if (c >= n || c < r) return;
+  const size_t plane = (size_t)n * n;
+  double s = 0.0;
+  for (int j = 0; j < jw.count; ++j) s = fma((double)T[(size_t)j * plane + (size_t)r * n + c], jw.w[j], s);
+  s = ldexp(s, ex[r] + ex[c]);
+  double* o = C + r * ldc + c;
+  *o = accumulate ? *o + s : s;
+}
+
+// A BF16 tensor map over a column block of a wider row-major array: inner
+// extent `inner` elements, rows `rows`, row stride `stride` elements.
+hess_status make_block_map(CUtensorMap* m, const void* ptr, int64_t inner, int64_t stride, int64_t rows,
+                           int box_rows) {
+  using namespace tc;
+  if ((reinterpret_cast<uintptr_t>(ptr) & 15) || (inner % BK) || (stride % 8))
+    return set_error(HESS_ERR_INVALID_ARG, "tensor map: misaligned operand block");
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)stride * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult res = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (res != CUDA_SUCCESS) return set_error(HESS_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)res);
+  return HESS_OK;
+}
+
+// The contractions: for each weight w = d + d' (0 .. 7), digits d in
+// segments of at most kExactK / ldk.
+struct Contraction {
+  int w, d0, d1;
+};
+std::vector<Contraction> contractions(int64_t ldk) {
+  const int seg = (int)std::max<int64_t>(1, kExactK / ldk);
+  std::vector<Contraction> out;
+  for (int w = kDigits - 1; w >= 0; --w)  // smallest weights first
+    for (int d0 = 0; d0 <= w; d0 += seg) out.push_back({w, d0, std::min(w + 1, d0 + seg)});
+  return out;
+}
+
+}  // namespace
+
+bool f64_syrk_tc_eligible(hess_mlp* h, int64_t n, int64_t K) {
+  if (K < 128 || K > kExactK || n < 128 || n > 16384) return false;
+  if (tc_available(h) != HESS_OK) {
+    clear_error();
+    return false;
+  }
+  return true;
+}
+
+void plan_f64_syrk(Arena& ar, int64_t n, int64_t K, F64SyrkScratch& fs) {
+  using namespace tc;
+  fs.n = n;
+  fs.ldk = (int64_t)align_up((size_t)K, BK);
+  fs.D = ar.take<__nv_bfloat16>((int64_t)kDigits * n * fs.ldk);
+  fs.R = ar.take<__nv_bfloat16>((int64_t)kDigits * n * fs.ldk);
+  fs.ex = ar.take<int>(n);
+  const int64_t njobs = (int64_t)contractions(fs.ldk).size();
+  int64_t g = (int64_t)(kPairBudget / ((size_t)n * n * sizeof(float)));
+  if (g < 1) g = 1;
+  if (g > njobs) g = njobs;
+  fs.group = (int)g;
+  fs.T = ar.take<float>(g * n * n);
+  fs.jobs = ar.take<tc::Job>(g);
+  fs.tiles = ar.take<int4>(g * syrk_tile_count(n, 256));
+}
+
+hess_status f64_syrk_tc(hess_mlp* h, const double* A, int64_t lda, int64_t K, double* C, int64_t ldc,
+                        const F64SyrkScratch& fs, cudaStream_t s) {
+  using namespace tc;
+  const int64_t n = fs.n, ldk = fs.ldk, L = (int64_t)kDigits * ldk;
+  if (K > ldk) return set_error(HESS_ERR_INVALID_ARG, "exact-digit product: K %lld beyond its plan", (long long)K);
+  digits_rows_kernel<<<(unsigned)cdiv(n, 8), 256, 0, s>>>(A, lda, 1, n, K, ldk, fs.D, fs.R, fs.ex);
+  HM_LAUNCHED();
+  const std::vector<Contraction> cs = contractions(ldk);
+  const int BN = 256;
+  bool first = true;
+  for (size_t j0 = 0; j0 < cs.size(); j0 += fs.group) {
+    const size_t j1 = std::min(cs.size(), j0 + (size_t)fs.group);
+    std::vector<Job> jobs;
+    std::vector<int4> tiles;
+    JobWeights jw{};
+    jw.count = (int)(j1 - j0);
+    for (size_t j = j0; j < j1; ++j) {
+      const Contraction& c = cs[j];
+      const int64_t inner = (int64_t)(c.d1 - c.d0) * ldk;
+      const __nv_bfloat16* Ablk = fs.D + (int64_t)c.d0 * ldk;                       // Q_d0 | ... | Q_{d1-1}
+      const __nv_bfloat16* Bblk = fs.R + (int64_t)(kDigits - 1 - c.w + c.d0) * ldk;  // Q_{w-d0} | ... | Q_{w-d1+1}
+      Job job{};
+      HM_TRY(make_block_map(&job.a_hi, Ablk, inner, L, n, BM));
+      job.a_lo = job.a_hi;
+      HM_TRY(make_block_map(&job.b_hi, Bblk, inner, L, n, BN));
+      job.b_lo = job.b_hi;
+      job.BN = BN;
+      job.nkb = (int)(inner / BK);
+      job.idesc = make_idesc(BN);
+      job.M = n;
+      job.Nn = n;
+      job.mode = 0;  // upper tiles; the mirrored writes land below the diagonal, unread
+      job.scale = 1.0f;
+      job.out = fs.T + (j - j0) * (size_t)n * n;
+      job.ldo = n;
+      syrk_tiles(n, BN, (int)jobs.size(), tiles);
+      jobs.push_back(job);
+      jw.w[j - j0] = ldexp(1.0, -12 - 7 * c.w);
+    }
+    HM_TRY(launch_jobs(h->sm_count, jobs.data(), (int)jobs.size(), tiles.data(), (int)tiles.size(), fs.jobs,
+                       fs.tiles, false, h->err_dev, h->stage, s));
+    combine_upper_kernel<<<dim3((unsigned)cdiv(n, 256), (unsigned)n), 256, 0, s>>>(fs.T, n, jw, fs.ex, C, ldc,
+                                                                                   first ? 0 : 1);
+    HM_LAUNCHED();
+    first = false;
+  }
+  return HESS_OK;
+}
+
+bool f64_gemm_nt_tc_eligible(hess_mlp* h, int64_t M, int64_t Nn, int64_t K) {
+  if (K < 128 || K > kExactK || M < 128 || Nn < 1 || Nn > 256) return false;
+  if (tc_available(h) != HESS_OK) {
+    clear_error();
+    return false;
+  }
+  return true;
+}
+
+void plan_f64_gemm_nt(Arena& ar, int64_t M, int64_t Nn, int64_t K, F64GemmScratch& fs) {
+  using namespace tc;
+  fs.M = M;
+  fs.Nn = Nn;
+  fs.ldk = (int64_t)align_up((size_t)K, BK);
+  fs.DA = ar.take<__nv_bfloat16>((int64_t)kDigits * M * fs.ldk);
+  fs.RB = ar.take<__nv_bfloat16>((int64_t)kDigits * Nn * fs.ldk);
+  fs.exA = ar.take<int>(M);
+  fs.exB = ar.take<int>(Nn);
+  const int64_t njobs = (int64_t)contractions(fs.ldk).size();
+  int64_t g = (int64_t)(kPairBudget / ((size_t)M * Nn * sizeof(float)));
+  if (g < 1) g = 1;
+  if (g > njobs) g = njobs;
+  fs.group = (int)g;
+  fs.T = ar.take<float>(g * M * Nn);
+  fs.jobs = ar.take<tc::Job>(g);
+  fs.tiles = ar.take<int4>(g * cdiv(M, BM) * cdiv(Nn, 16));
+}
+
+hess_status f64_gemm_nt_tc(hess_mlp* h, const double* G, int64_t ldg, const double* B, int64_t b_rs, int64_t b_ks,
+                           int64_t K, double* C, int64_t scm, int64_t scn, const F64GemmScratch& fs, cudaStream_t s) {
+  using namespace tc;
+  const int64_t M = fs.M, Nn = fs.Nn, ldk = fs.ldk, L = (int64_t)kDigits * ldk;
+  if (K > ldk) return set_error(HESS_ERR_INVALID_ARG, "exact-digit product: K %lld beyond its plan", (long long)K);
+  // A = G^T: rows are the columns of G
+  colmax_exp_kernel<<<(unsigned)cdiv(M, 32), dim3(32, 8), 0, s>>>(G, ldg, K, M, fs.exA);
+  HM_LAUNCHED();
+  digits_cols_kernel<<<dim3((unsigned)cdiv(ldk, 32), (unsigned)cdiv(M, 32)), dim3(32, 8), 0, s>>>(G, ldg, K, M, fs.exA,
+                                                                                              ldk, fs.DA);
+  HM_LAUNCHED();
+  digits_rows_kernel<<<(unsigned)cdiv(Nn, 8), 256, 0, s>>>(B, b_rs, b_ks, Nn, K, ldk, nullptr, fs.RB, fs.exB);
+  HM_LAUNCHED();
+  const std::vector<Contraction> cs = contractions(ldk);
+  const int BN = (int)align_up((size_t)Nn, 16);
+  bool first = true;
+  for (size_t j0 = 0; j0 < cs.size(); j0 += fs.group) {
+    const size_t j1 = std::min(cs.size(), j0 + (size_t)fs.group);
+    std::vector<Job> jobs;
+    std::vector<int4> tiles;
+    JobWeights jw{};
+    jw.count = (int)(j1 - j0);
+    for (size_t j = j0; j < j1; ++j) {
+      const Contraction& c = cs[j];
+      const int64_t inner = (int64_t)(c.d1 - c.d0) * ldk;
+      Job job{};
+      HM_TRY(make_block_map(&job.a_hi, fs.DA + (int64_t)c.d0 * ldk, inner, L, M, BM));
+      job.a_lo = job.a_hi;
+      HM_TRY(make_block_map(&job.b_hi, fs.RB + (int64_t)(kDigits - 1 - c.w + c.d0) * ldk, inner, L, Nn, BN));
+      job.b_lo = job.b_hi;
+      job.BN = BN;
+      job.nkb = (int)(inner / BK);
+      job.idesc = make_idesc(BN);
+      job.M = M;
+      job.Nn = Nn;
+      job.mode = 3;
+      job.scale = 1.0f;
+      job.out = fs.T + (j - j0) * (size_t)M * Nn;
+      job.ldo = Nn;
+      const int jid = (int)jobs.size();
+      for (int64_t tm = 0; tm < cdiv(M, BM); ++tm) tiles.push_back(make_int4(jid, (int)tm, 0, 0));
+      jobs.push_back(job);
+      jw.w[j - j0] = ldexp(1.0, -12 - 7 * c.w);
+    }
+    HM_TRY(launch_jobs(h->sm_count, jobs.data(), (int)jobs.size(), tiles.data(), (int)tiles.size(), fs.jobs,
+                       fs.tiles, false, h->err_dev, h->stage, s));
+    combine_general_kernel<<<(unsigned)cdiv(M * Nn, 256), 256, 0, s>>>(fs.T, M, Nn, jw, fs.exA, fs.exB, C, scm, scn,
+                                                                       first ? 0 : 1);
+    HM_LAUNCHED();
+    first = false;
+  }
+  return HESS_OK;
 }
 
 }  // namespace hm
