@@ -1580,6 +1580,36 @@ constexpr int kDigits = 8;
 constexpr size_t kPairBudget = (size_t)1 << 30;
 constexpr int64_t kExactK = 4096;  // products per entry with exact FP32 sums
 
+// round(x 2^(62 - E)) for |x| < 2^E, from the bits of x with integer
+// operations only (an FP64 operation costs many cycles per warp on this GPU):
+// x = mant 2^e, so the result is mant shifted by e + 62 - E (left by at most
+// 9, since mant >= 2^52; right shifts round half up, and values below 2^-63
+// of the scale vanish).
+__device__ __forceinline__ long long fixed62(double x, int E) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7ff);
+  unsigned long long mant = bits & 0xfffffffffffffull;
+  if (ex == 0 && mant == 0ull) return 0ll;
+  int e;
+  if (ex == 0) {
+    e = -1074;  // subnormal
+  } else {
+    mant |= 1ull << 52;
+    e = ex - 1075;
+  }
+  const int sh = e + 62 - E;
+  long long v;
+  if (sh >= 0) {
+    v = (long long)(mant << sh);
+  } else if (sh > -64) {
+    const int r = -sh;
+    v = (long long)((mant + (1ull << (r - 1))) >> r);
+  } else {
+    v = 0ll;
+  }
+  return (bits >> 63) ? -v : v;
+}
+
 struct JobWeightsFwd {
   double w[2 * kDigits * kDigits];  // 2^(-12 - 7w) of each contraction of the group
   int count;
@@ -1589,7 +1619,7 @@ struct JobWeightsFwd {
 // row's value scaled into (-1, 1) becomes the integer m = v 2^62 (dropping
 // below 2^-62), whose digits come off by rounding shifts.
 __global__ void digits_rows_kernel(const double* A, int64_t rs, int64_t ks, int64_t n, int64_t K, int64_t ldk,
-                                   __nv_bfloat16* fwd, __nv_bfloat16* rev, int* ex) {
+                                   __nv_bfloat16* fwd, __nv_bfloat16* rev, __nv_bfloat16* pm, int* ex) {
   const int lane = threadIdx.x & 31;
   const int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
   if (r >= n) return;
@@ -1604,7 +1634,7 @@ __global__ void digits_rows_kernel(const double* A, int64_t rs, int64_t ks, int6
   __nv_bfloat16* fr = fwd ? fwd + r * L : nullptr;
   __nv_bfloat16* rr = rev ? rev + r * L : nullptr;
   for (int64_t k = lane; k < ldk; k += 32) {
-    long long m = k < K ? __double2ll_rn(ldexp(a[k * ks], 62 - E)) : 0ll;  // |m| < 2^62
+    long long m = k < K ? fixed62(a[k * ks], E) : 0ll;  // |m| <= 2^62
 #pragma unroll
     for (int d = 0; d < kDigits; ++d) {
       const int sh = 56 - 7 * d;
@@ -1613,6 +1643,7 @@ __global__ void digits_rows_kernel(const double* A, int64_t rs, int64_t ks, int6
       const __nv_bfloat16 v = __int2bfloat16_rn((int)q);  // |q| <= 64: exact
       if (fr) fr[(int64_t)d * ldk + k] = v;
       if (rr) rr[(int64_t)(kDigits - 1 - d) * ldk + k] = v;
+      if (pm) pm[((int64_t)d * n + r) * ldk + k] = v;  // plane-major: rows (d, r)
     }
   }
 }
@@ -1645,43 +1676,66 @@ __global__ void colmax_exp_kernel(const double* G, int64_t ldg, int64_t n, int64
 }
 
 // Digits of the rows of G^T (G row-major n x m): fwd[c][d ldk + r] = q_d of
-// G[r][c] scaled by 2^-ex[c]; rows r in [n, ldk) are zero.  A 32 x 32 tile
-// is read along c and written along r through shared memory.
+// G[r][c] scaled by 2^-ex[c]; rows r in [n, ldk) are zero.  A 128 x 32 tile
+// (128 rows r, 32 columns c) is read along c and written along r through
+// shared memory, four consecutive r per thread (8-byte stores).
 __global__ void digits_cols_kernel(const double* G, int64_t ldg, int64_t n, int64_t m, const int* ex, int64_t ldk,
                                    __nv_bfloat16* fwd) {
-  __shared__ double t[32][33];
-  const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
-  for (int y = threadIdx.y; y < 32; y += 8) {
+  __shared__ double t[128][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 128, c0 = (int64_t)blockIdx.y * 32;
+  for (int y = threadIdx.y; y < 128; y += 8) {
     const int64_t r = r0 + y, c = c0 + threadIdx.x;
     t[y][threadIdx.x] = (r < n && c < m) ? G[r * ldg + c] : 0.0;
   }
   __syncthreads();
   const int64_t L = (int64_t)kDigits * ldk;
   for (int y = threadIdx.y; y < 32; y += 8) {
-    const int64_t c = c0 + y, r = r0 + threadIdx.x;
-    if (c >= m || r >= ldk) continue;
-    long long q_m = __double2ll_rn(ldexp(t[threadIdx.x][y], 62 - ex[c]));
-    __nv_bfloat16* fr = fwd + c * L;
+    const int64_t c = c0 + y, r = r0 + 4 * threadIdx.x;
+    if (c >= m || r >= ldk) continue;  // ldk is a multiple of 64: r..r+3 all in range
+    const int e = ex[c];
+    long long mm[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) mm[u] = fixed62(t[4 * threadIdx.x + u][y], e);
+    __nv_bfloat16* fr = fwd + c * L + r;
 #pragma unroll
     for (int d = 0; d < kDigits; ++d) {
       const int sh = 56 - 7 * d;
-      const long long q = (q_m + (1ll << (sh - 1))) >> sh;
-      q_m -= q << sh;
-      fr[(int64_t)d * ldk + r] = __int2bfloat16_rn((int)q);
+      __align__(8) __nv_bfloat16 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long q = (mm[u] + (1ll << (sh - 1))) >> sh;
+        mm[u] -= q << sh;
+        v[u] = __int2bfloat16_rn((int)q);
+      }
+      *reinterpret_cast<uint2*>(fr + (int64_t)d * ldk) = *reinterpret_cast<const uint2*>(v);
     }
   }
 }
 
-// C(r, c) = 2^(eA_r + eB_c) sum_j w_j T_j[r][c] (T_j: M x Nn), written to
-// C[r scm + c scn] (added when accumulate is set).
-__global__ void combine_general_kernel(const float* T, int64_t M, int64_t Nn, JobWeightsFwd jw, const int* exA,
+// Digit-major contractions of a general product: job j holds, for digit d_j
+// of A, the products with digits e in [e0_j, e1_j) of B side by side
+// (T_j: M x (e1_j - e0_j) Nn).  C(r, c) = 2^(eA_r + eB_c) sum over jobs and
+// their e with d + e <= 7 of 2^(-12 - 7(d + e)) T_j[r][(e - e0) Nn + c],
+// written to C[r scm + c scn] (added when accumulate is set).
+struct DigitJobs {
+  int d[2 * kDigits * kDigits], e0[2 * kDigits * kDigits], e1[2 * kDigits * kDigits];
+  int64_t off[2 * kDigits * kDigits];  // float offset of T_j
+  double wt[2 * kDigits];              // 2^(-12 - 7w) by w = d + e
+  int count;
+};
+__global__ void combine_general_kernel(const float* T, int64_t M, int64_t Nn, DigitJobs dj, const int* exA,
                                        const int* exB, double* C, int64_t scm, int64_t scn, int accumulate) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= M * Nn) return;
   const int64_t r = idx / Nn, c = idx % Nn;
-  const size_t plane = (size_t)M * Nn;
   double s = 0.0;
-  for (int j = 0; j < jw.count; ++j) s = fma((double)T[(size_t)j * plane + idx], jw.w[j], s);
+  for (int j = dj.count - 1; j >= 0; --j) {  // the later digits of A (smaller weights) first
+    const int d = dj.d[j], e1 = min(dj.e1[j], kDigits - d);
+    const int64_t wd = (int64_t)(dj.e1[j] - dj.e0[j]) * Nn;
+    const float* row = T + dj.off[j] + r * wd + c;
+    for (int e = e1 - 1; e >= dj.e0[j]; --e)
+      s = fma((double)row[(int64_t)(e - dj.e0[j]) * Nn], dj.wt[d + e], s);
+  }
   s = ldexp(s, exA[r] + exB[c]);
   double* o = C + r * scm + c * scn;
   *o = accumulate ? *o + s : s;
@@ -1769,7 +1823,7 @@ hess_status f64_syrk_tc(hess_mlp* h, const double* A, int64_t lda, int64_t K, do
   using namespace tc;
   const int64_t n = fs.n, ldk = fs.ldk, L = (int64_t)kDigits * ldk;
   if (K > ldk) return set_error(HESS_ERR_INVALID_ARG, "exact-digit product: K %lld beyond its plan", (long long)K);
-  digits_rows_kernel<<<(unsigned)cdiv(n, 8), 256, 0, s>>>(A, lda, 1, n, K, ldk, fs.D, fs.R, fs.ex);
+  digits_rows_kernel<<<(unsigned)cdiv(n, 8), 256, 0, s>>>(A, lda, 1, n, K, ldk, fs.D, fs.R, nullptr, fs.ex);
   HM_LAUNCHED();
   const std::vector<Contraction> cs = contractions(ldk);
   const int BN = 256;
@@ -1822,6 +1876,21 @@ bool f64_gemm_nt_tc_eligible(hess_mlp* h, int64_t M, int64_t Nn, int64_t K) {
   return true;
 }
 
+namespace {
+// Digit-major jobs of a general product: for each digit d of A, the digits e
+// < kDigits - d of B in groups of at most 256 / Nn (one tile column each).
+struct DigitJob {
+  int d, e0, e1;
+};
+std::vector<DigitJob> digit_jobs(int64_t Nn) {
+  const int per = (int)std::max<int64_t>(1, 256 / Nn);
+  std::vector<DigitJob> out;
+  for (int d = 0; d < kDigits; ++d)
+    for (int e0 = 0; e0 < kDigits - d; e0 += per) out.push_back({d, e0, std::min(kDigits - d, e0 + per)});
+  return out;
+}
+}  // namespace
+
 void plan_f64_gemm_nt(Arena& ar, int64_t M, int64_t Nn, int64_t K, F64GemmScratch& fs) {
   using namespace tc;
   fs.M = M;
@@ -1831,14 +1900,13 @@ void plan_f64_gemm_nt(Arena& ar, int64_t M, int64_t Nn, int64_t K, F64GemmScratc
   fs.RB = ar.take<__nv_bfloat16>((int64_t)kDigits * Nn * fs.ldk);
   fs.exA = ar.take<int>(M);
   fs.exB = ar.take<int>(Nn);
-  const int64_t njobs = (int64_t)contractions(fs.ldk).size();
-  int64_t g = (int64_t)(kPairBudget / ((size_t)M * Nn * sizeof(float)));
-  if (g < 1) g = 1;
-  if (g > njobs) g = njobs;
-  fs.group = (int)g;
-  fs.T = ar.take<float>(g * M * Nn);
-  fs.jobs = ar.take<tc::Job>(g);
-  fs.tiles = ar.take<int4>(g * cdiv(M, BM) * cdiv(Nn, 16));
+  const std::vector<DigitJob> js = digit_jobs(Nn);
+  int64_t cols = 0;
+  for (const DigitJob& j : js) cols += (int64_t)(j.e1 - j.e0) * Nn;
+  fs.group = (int)js.size();
+  fs.T = ar.take<float>(M * cols);
+  fs.jobs = ar.take<tc::Job>((int64_t)js.size());
+  fs.tiles = ar.take<int4>((int64_t)js.size() * cdiv(M, BM));
 }
 
 hess_status f64_gemm_nt_tc(hess_mlp* h, const double* G, int64_t ldg, const double* B, int64_t b_rs, int64_t b_ks,
@@ -1846,52 +1914,51 @@ hess_status f64_gemm_nt_tc(hess_mlp* h, const double* G, int64_t ldg, const doub
   using namespace tc;
   const int64_t M = fs.M, Nn = fs.Nn, ldk = fs.ldk, L = (int64_t)kDigits * ldk;
   if (K > ldk) return set_error(HESS_ERR_INVALID_ARG, "exact-digit product: K %lld beyond its plan", (long long)K);
-  // A = G^T: rows are the columns of G
+  // A = G^T: rows are the columns of G; B: plane-major digits, rows (e, c)
   colmax_exp_kernel<<<(unsigned)cdiv(M, 32), dim3(32, 8), 0, s>>>(G, ldg, K, M, fs.exA);
   HM_LAUNCHED();
-  digits_cols_kernel<<<dim3((unsigned)cdiv(ldk, 32), (unsigned)cdiv(M, 32)), dim3(32, 8), 0, s>>>(G, ldg, K, M, fs.exA,
-                                                                                              ldk, fs.DA);
+  digits_cols_kernel<<<dim3((unsigned)cdiv(ldk, 128), (unsigned)cdiv(M, 32)), dim3(32, 8), 0, s>>>(
+      G, ldg, K, M, fs.exA, ldk, fs.DA);
   HM_LAUNCHED();
-  digits_rows_kernel<<<(unsigned)cdiv(Nn, 8), 256, 0, s>>>(B, b_rs, b_ks, Nn, K, ldk, nullptr, fs.RB, fs.exB);
+  digits_rows_kernel<<<(unsigned)cdiv(Nn, 8), 256, 0, s>>>(B, b_rs, b_ks, Nn, K, ldk, nullptr, nullptr, fs.RB, fs.exB);
   HM_LAUNCHED();
-  const std::vector<Contraction> cs = contractions(ldk);
-  const int BN = (int)align_up((size_t)Nn, 16);
-  bool first = true;
-  for (size_t j0 = 0; j0 < cs.size(); j0 += fs.group) {
-    const size_t j1 = std::min(cs.size(), j0 + (size_t)fs.group);
-    std::vector<Job> jobs;
-    std::vector<int4> tiles;
-    JobWeights jw{};
-    jw.count = (int)(j1 - j0);
-    for (size_t j = j0; j < j1; ++j) {
-      const Contraction& c = cs[j];
-      const int64_t inner = (int64_t)(c.d1 - c.d0) * ldk;
-      Job job{};
-      HM_TRY(make_block_map(&job.a_hi, fs.DA + (int64_t)c.d0 * ldk, inner, L, M, BM));
-      job.a_lo = job.a_hi;
-      HM_TRY(make_block_map(&job.b_hi, fs.RB + (int64_t)(kDigits - 1 - c.w + c.d0) * ldk, inner, L, Nn, BN));
-      job.b_lo = job.b_hi;
-      job.BN = BN;
-      job.nkb = (int)(inner / BK);
-      job.idesc = make_idesc(BN);
-      job.M = M;
-      job.Nn = Nn;
-      job.mode = 3;
-      job.scale = 1.0f;
-      job.out = fs.T + (j - j0) * (size_t)M * Nn;
-      job.ldo = Nn;
-      const int jid = (int)jobs.size();
-      for (int64_t tm = 0; tm < cdiv(M, BM); ++tm) tiles.push_back(make_int4(jid, (int)tm, 0, 0));
-      jobs.push_back(job);
-      jw.w[j - j0] = ldexp(1.0, -12 - 7 * c.w);
-    }
-    HM_TRY(launch_jobs(h->sm_count, jobs.data(), (int)jobs.size(), tiles.data(), (int)tiles.size(), fs.jobs,
-                       fs.tiles, false, h->err_dev, h->stage, s));
-    combine_general_kernel<<<(unsigned)cdiv(M * Nn, 256), 256, 0, s>>>(fs.T, M, Nn, jw, fs.exA, fs.exB, C, scm, scn,
-                                                                       first ? 0 : 1);
-    HM_LAUNCHED();
-    first = false;
+  const std::vector<DigitJob> js = digit_jobs(Nn);
+  std::vector<Job> jobs;
+  std::vector<int4> tiles;
+  DigitJobs dj{};
+  dj.count = (int)js.size();
+  for (int w = 0; w < 2 * kDigits; ++w) dj.wt[w] = ldexp(1.0, -12 - 7 * w);
+  int64_t off = 0;
+  for (size_t j = 0; j < js.size(); ++j) {
+    const DigitJob& g = js[j];
+    const int64_t cols = (int64_t)(g.e1 - g.e0) * Nn;
+    const int BN = (int)align_up((size_t)cols, 16);
+    Job job{};
+    HM_TRY(make_block_map(&job.a_hi, fs.DA + (int64_t)g.d * ldk, ldk, L, M, BM));
+    job.a_lo = job.a_hi;
+    HM_TRY(make_block_map(&job.b_hi, fs.RB + (int64_t)g.e0 * Nn * ldk, ldk, ldk, cols, BN));
+    job.b_lo = job.b_hi;
+    job.BN = BN;
+    job.nkb = (int)(ldk / BK);
+    job.idesc = make_idesc(BN);
+    job.M = M;
+    job.Nn = cols;
+    job.mode = 3;
+    job.scale = 1.0f;
+    job.out = fs.T + off;
+    job.ldo = cols;
+    for (int64_t tm = 0; tm < cdiv(M, BM); ++tm) tiles.push_back(make_int4((int)j, (int)tm, 0, 0));
+    jobs.push_back(job);
+    dj.d[j] = g.d;
+    dj.e0[j] = g.e0;
+    dj.e1[j] = g.e1;
+    dj.off[j] = off;
+    off += M * cols;
   }
+  HM_TRY(launch_jobs(h->sm_count, jobs.data(), (int)jobs.size(), tiles.data(), (int)tiles.size(), fs.jobs, fs.tiles,
+                     false, h->err_dev, h->stage, s));
+  combine_general_kernel<<<(unsigned)cdiv(M * Nn, 256), 256, 0, s>>>(fs.T, M, Nn, dj, fs.exA, fs.exB, C, scm, scn, 0);
+  HM_LAUNCHED();
   return HESS_OK;
 }
 
