@@ -793,10 +793,13 @@ def measured_peaks():
                 "sm_max_mhz": 2070.0}, "fallback"
 
 
-def profiled_traffic(cls):
+def profiled_traffic(cls, workload=WORKLOAD):
     """Per-launch DRAM traffic from the committed ncu summary of this kernel
-    class, if the kernel source has not changed since the capture."""
+    class on the MLP workload, if the kernel source has not changed since the
+    capture (None for other workloads)."""
     import hashlib
+    if workload != WORKLOAD:
+        return None
     name = {"syrk": "umma_gemm_opg_mlp_784_16_10.md",
             "hcontract": "umma_gemm_hessian_mlp_784_16_10.md"}.get(cls)
     if not name:
@@ -1074,7 +1077,7 @@ def main():
             r = {"bound": "tensor", "achieved": mult * k["flops"] / sec / 1e12,
                  "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
                  "peak_source": f"{peak_src} bf16 sustained",
-                 "traffic": profiled_traffic(cls)}
+                 "traffic": profiled_traffic(cls, args.workload)}
         elif k["flops"] > 0:
             fp64 = cls == "eig" or args.precision == "fp64"
             r = {"bound": "alu", "achieved": k["flops"] / sec / 1e12,
@@ -1082,6 +1085,11 @@ def main():
                  "peak_source": ("FP64 1.25 TFLOP/s (152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz)"
                                  if fp64 else "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"),
                  "traffic": None}
+            if cls == "eig":
+                r["note"] = ("algorithmic FP64 flops of the Gram matrix, Lanczos and back-projection "
+                             "over the class time; the Gram matrix's wide layer and the "
+                             "back-projection run as exact-digit FP64 products on the BF16 tensor "
+                             "cores, so the rate can exceed the SIMT FP64 rate")
         else:
             r = {"bound": "hbm", "achieved": k["bytes"] / sec / 1e9, "peak": peaks["hbm_gbs"],
                  "unit": "GB/s", "peak_source": f"{peak_src} copy bandwidth", "traffic": None}

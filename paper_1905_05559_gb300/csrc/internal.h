@@ -383,8 +383,9 @@ struct F64GemmScratch {
   tc::Job* jobs = nullptr;
   int4* tiles = nullptr;
 };
-// Usable when the tensor-core path is, 128 <= K <= 4096, M >= 128 and
-// 1 <= Nn <= 256 (one tile column).
+// Usable when the tensor-core path is, K >= 128 (in segments of at most
+// 4096, each with exact FP32 sums), M >= 128 and 1 <= Nn <= 256 (one tile
+// column), and the digit jobs and their FP32 results fit their bounds.
 bool f64_gemm_nt_tc_eligible(hess_mlp* h, int64_t M, int64_t Nn, int64_t K);
 void plan_f64_gemm_nt(Arena& ar, int64_t M, int64_t Nn, int64_t K, F64GemmScratch& fs);
 // C(m, c) = sum_k G[k][m] B(c, k), B(c, k) = B[c b_rs + k b_ks], written to

@@ -1719,7 +1719,7 @@ __global__ void digits_cols_kernel(const double* G, int64_t ldg, int64_t n, int6
 // written to C[r scm + c scn] (added when accumulate is set).
 struct DigitJobs {
   int d[2 * kDigits * kDigits], e0[2 * kDigits * kDigits], e1[2 * kDigits * kDigits];
-  int64_t off[2 * kDigits * kDigits];  // float offset of T_j
+  int64_t off[2 * kDigits * kDigits];  // float offset of T_j (one per digit job and K segment)
   double wt[2 * kDigits];              // 2^(-12 - 7w) by w = d + e
   int count;
 };
@@ -1867,8 +1867,26 @@ hess_status f64_syrk_tc(hess_mlp* h, const double* A, int64_t lda, int64_t K, do
   return HESS_OK;
 }
 
+namespace {
+constexpr int kMaxDigitJobs = 2 * kDigits * kDigits;
+int64_t k_segments(int64_t ldk) { return cdiv(ldk, kExactK); }
+}  // namespace
+
 bool f64_gemm_nt_tc_eligible(hess_mlp* h, int64_t M, int64_t Nn, int64_t K) {
-  if (K < 128 || K > kExactK || M < 128 || Nn < 1 || Nn > 256) return false;
+  if (K < 128 || M < 128 || Nn < 1 || Nn > 256) return false;
+  // K in segments of at most kExactK products (exact FP32 sums each); every
+  // digit job of every segment needs its own output
+  const int64_t ldk = (int64_t)align_up((size_t)K, tc::BK);
+  const int per = (int)std::max<int64_t>(1, 256 / Nn);
+  int64_t jobs = 0, cols = 0;
+  for (int d = 0; d < kDigits; ++d)
+    for (int e0 = 0; e0 < kDigits - d; e0 += per) {
+      ++jobs;
+      cols += (int64_t)(std::min(kDigits - d, e0 + per) - e0) * Nn;
+    }
+  const int64_t nseg = k_segments(ldk);
+  if (jobs * nseg > kMaxDigitJobs) return false;
+  if ((double)M * cols * nseg * 4.0 > 8.0 * (1 << 30)) return false;  // FP32 results within 8 GB
   if (tc_available(h) != HESS_OK) {
     clear_error();
     return false;
@@ -1901,12 +1919,13 @@ void plan_f64_gemm_nt(Arena& ar, int64_t M, int64_t Nn, int64_t K, F64GemmScratc
   fs.exA = ar.take<int>(M);
   fs.exB = ar.take<int>(Nn);
   const std::vector<DigitJob> js = digit_jobs(Nn);
+  const int64_t nseg = k_segments(fs.ldk);
   int64_t cols = 0;
   for (const DigitJob& j : js) cols += (int64_t)(j.e1 - j.e0) * Nn;
-  fs.group = (int)js.size();
-  fs.T = ar.take<float>(M * cols);
-  fs.jobs = ar.take<tc::Job>((int64_t)js.size());
-  fs.tiles = ar.take<int4>((int64_t)js.size() * cdiv(M, BM));
+  fs.group = (int)(js.size() * nseg);
+  fs.T = ar.take<float>(M * cols * nseg);
+  fs.jobs = ar.take<tc::Job>((int64_t)js.size() * nseg);
+  fs.tiles = ar.take<int4>((int64_t)js.size() * nseg * cdiv(M, BM));
 }
 
 hess_status f64_gemm_nt_tc(hess_mlp* h, const double* G, int64_t ldg, const double* B, int64_t b_rs, int64_t b_ks,
@@ -1923,37 +1942,45 @@ hess_status f64_gemm_nt_tc(hess_mlp* h, const double* G, int64_t ldg, const doub
   digits_rows_kernel<<<(unsigned)cdiv(Nn, 8), 256, 0, s>>>(B, b_rs, b_ks, Nn, K, ldk, nullptr, nullptr, fs.RB, fs.exB);
   HM_LAUNCHED();
   const std::vector<DigitJob> js = digit_jobs(Nn);
+  const int64_t nseg = k_segments(ldk);
+  if ((int64_t)js.size() * nseg > kMaxDigitJobs)
+    return set_error(HESS_ERR_INVALID_ARG, "exact-digit product: too many digit jobs");
   std::vector<Job> jobs;
   std::vector<int4> tiles;
   DigitJobs dj{};
-  dj.count = (int)js.size();
+  dj.count = (int)(js.size() * nseg);
   for (int w = 0; w < 2 * kDigits; ++w) dj.wt[w] = ldexp(1.0, -12 - 7 * w);
   int64_t off = 0;
-  for (size_t j = 0; j < js.size(); ++j) {
-    const DigitJob& g = js[j];
-    const int64_t cols = (int64_t)(g.e1 - g.e0) * Nn;
-    const int BN = (int)align_up((size_t)cols, 16);
-    Job job{};
-    HM_TRY(make_block_map(&job.a_hi, fs.DA + (int64_t)g.d * ldk, ldk, L, M, BM));
-    job.a_lo = job.a_hi;
-    HM_TRY(make_block_map(&job.b_hi, fs.RB + (int64_t)g.e0 * Nn * ldk, ldk, ldk, cols, BN));
-    job.b_lo = job.b_hi;
-    job.BN = BN;
-    job.nkb = (int)(ldk / BK);
-    job.idesc = make_idesc(BN);
-    job.M = M;
-    job.Nn = cols;
-    job.mode = 3;
-    job.scale = 1.0f;
-    job.out = fs.T + off;
-    job.ldo = cols;
-    for (int64_t tm = 0; tm < cdiv(M, BM); ++tm) tiles.push_back(make_int4((int)j, (int)tm, 0, 0));
-    jobs.push_back(job);
-    dj.d[j] = g.d;
-    dj.e0[j] = g.e0;
-    dj.e1[j] = g.e1;
-    dj.off[j] = off;
-    off += M * cols;
+  for (int64_t sg = 0; sg < nseg; ++sg) {
+    const int64_t k0 = sg * kExactK;
+    const int64_t inner = std::min<int64_t>(kExactK, ldk - k0);  // a multiple of 64
+    for (size_t jj = 0; jj < js.size(); ++jj) {
+      const DigitJob& g = js[jj];
+      const int j = (int)jobs.size();
+      const int64_t cols = (int64_t)(g.e1 - g.e0) * Nn;
+      const int BN = (int)align_up((size_t)cols, 16);
+      Job job{};
+      HM_TRY(make_block_map(&job.a_hi, fs.DA + (int64_t)g.d * ldk + k0, inner, L, M, BM));
+      job.a_lo = job.a_hi;
+      HM_TRY(make_block_map(&job.b_hi, fs.RB + (int64_t)g.e0 * Nn * ldk + k0, inner, ldk, cols, BN));
+      job.b_lo = job.b_hi;
+      job.BN = BN;
+      job.nkb = (int)(inner / BK);
+      job.idesc = make_idesc(BN);
+      job.M = M;
+      job.Nn = cols;
+      job.mode = 3;
+      job.scale = 1.0f;
+      job.out = fs.T + off;
+      job.ldo = cols;
+      for (int64_t tm = 0; tm < cdiv(M, BM); ++tm) tiles.push_back(make_int4(j, (int)tm, 0, 0));
+      jobs.push_back(job);
+      dj.d[j] = g.d;
+      dj.e0[j] = g.e0;
+      dj.e1[j] = g.e1;
+      dj.off[j] = off;
+      off += M * cols;
+    }
   }
   HM_TRY(launch_jobs(h->sm_count, jobs.data(), (int)jobs.size(), tiles.data(), (int)tiles.size(), fs.jobs, fs.tiles,
                      false, h->err_dev, h->stage, s));
