@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cfloat>
 #include <atomic>
 #include <functional>
@@ -418,8 +419,11 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else {
     const int q = warp & 3;  // TMEM lane quadrant of this warp
     float* e = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(epi) + (warp - 2) * EPI_WARP_BYTES);
-    int64_t* srow = reinterpret_cast<int64_t*>(e + 32 * EPI_LD);  // [32] output row (-1: invalid)
-    int64_t* scol = srow + 32;                                     // [32] output column base
+    // per row of the warp's 32: where column n of the tile goes directly
+    // (sptr[i] + n, null for rows past M) and the first column stored
+    // directly (the diagonal for symmetric outputs)
+    float** sptr = reinterpret_cast<float**>(e + 32 * EPI_LD);    // [32]
+    int64_t* sdm = reinterpret_cast<int64_t*>(sptr + 32);         // [32]
     int tcount = 0;
     unsigned fulls[2] = {0u, 0u};  // chunk results consumed from each TMEM buffer
     const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
@@ -468,35 +472,49 @@ __global__ void __launch_bounds__(THREADS, 1)
       int64_t orow = 0, ocolb = 0;
       if (rvalid) row_map(p, m, tile.z, orow, ocolb);
       const int64_t nbase = p.mode == 2 ? (int64_t)(tile.z % p.ntn) * BN : (int64_t)tile.z * BN;
-      srow[lane] = rvalid ? orow : -1;
-      scol[lane] = ocolb;
+      // column n of this lane's row: direct at out + orow ldo + ocolb + n when
+      // n >= dmin (symmetric outputs: on or above the diagonal), mirrored at
+      // out + (ocolb + n) ldo + orow when n > dmin
+      const int64_t dmin = sym ? orow - ocolb : INT64_MIN / 2;
+      const bool mir = sym && rvalid;
+      sptr[lane] = rvalid ? out + orow * ldo + ocolb : nullptr;
+      sdm[lane] = dmin;
       __syncwarp();
       const uint32_t tbase = tmem_base + acc * MAXBN + (static_cast<uint32_t>(q * 32) << 16);
       // 16 columns of the tile: the mirror image (for a fixed column the
       // warp's 32 rows are adjacent), then the direct entries transposed
-      // through shared memory so that each half warp writes 16 adjacent
-      // columns of one row
+      // through shared memory: 4 rows x 8 column pairs per warp store,
+      // 8-byte stores where the address allows
       auto emit16 = [&](const float* v, int64_t n0) {
+        float* mp = mir ? out + (ocolb + n0) * ldo + orow : nullptr;
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) {
           const int64_t n = n0 + jj;
           const float val = v[jj] * scale;
           e[lane * EPI_LD + jj] = val;
-          if (sym && rvalid && n < Nn) {
-            const int64_t ocol = ocolb + n;
-            if (ocol > orow) __stcs(out + ocol * ldo + orow, val);
+          if (mir) {
+            if (n < Nn && n > dmin) __stcs(mp, val);
+            mp += ldo;
           }
         }
         __syncwarp();
-        const int jj = lane & 15;
-        const int64_t n = n0 + jj;
-#pragma unroll 4
-        for (int r = 0; r < 16; ++r) {
-          const int i = (lane >> 4) + 2 * r;
-          const int64_t orow_i = srow[i];
-          if (orow_i >= 0 && n < Nn) {
-            const int64_t ocol = scol[i] + n;
-            if (!sym || ocol >= orow_i) __stcs(out + orow_i * ldo + ocol, e[i * EPI_LD + jj]);
+        const int cp = lane & 7, rg = lane >> 3;
+        const int64_t n = n0 + 2 * cp;
+#pragma unroll 2
+        for (int r = 0; r < 8; ++r) {
+          const int i = rg + 4 * r;
+          float* const rp = sptr[i];
+          if (rp != nullptr) {
+            const int64_t dm = sdm[i];
+            const float a0 = e[i * EPI_LD + 2 * cp], a1 = e[i * EPI_LD + 2 * cp + 1];
+            const bool ok0 = n < Nn && n >= dm;
+            const bool ok1 = n + 1 < Nn && n + 1 >= dm;
+            if (ok0 && ok1 && ((reinterpret_cast<uintptr_t>(rp + n) & 7u) == 0u)) {
+              __stcs(reinterpret_cast<float2*>(rp + n), make_float2(a0, a1));
+            } else {
+              if (ok0) __stcs(rp + n, a0);
+              if (ok1) __stcs(rp + n + 1, a1);
+            }
           }
         }
         __syncwarp();
