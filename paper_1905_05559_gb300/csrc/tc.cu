@@ -3,7 +3,8 @@
 // memory, one persistent CTA per SM with warp-specialised roles:
 //   warp 0      TMA producer (one elected thread)
 //   warp 1      TMEM allocator and MMA issuer (one elected thread)
-//   warps 2-5   epilogue: TMEM -> registers -> global, 32 TMEM lanes each
+//   warps 2-9   epilogue: TMEM -> registers -> global, 32 TMEM lanes and
+//               every other 32-column group of the tile each
 // The accumulator is double-buffered in TMEM (2 x 256 fp32 columns) so the
 // epilogue of one tile overlaps the main loop of the next.
 //
@@ -46,10 +47,11 @@ constexpr int EPI_LD = 17;  // 16 columns + 1 pad
 // per epilogue warp: a 32 x 16 transpose tile, then the 32 rows' output row
 // and column base (int64 each)
 constexpr int EPI_WARP_BYTES = 32 * EPI_LD * 4 + 32 * 16;
-constexpr int EPI_BYTES = 4 * EPI_WARP_BYTES;
+constexpr int EPI_WARPS = 8;  // two per TMEM lane quadrant, splitting the columns
+constexpr int EPI_BYTES = EPI_WARPS * EPI_WARP_BYTES;
 constexpr int BAR_BYTES = 256;
 constexpr int SMEM_BYTES = 1024 + RING_BYTES + EPI_BYTES + BAR_BYTES;
-constexpr int THREADS = 192;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr long long TIMEOUT_CYCLES = 4000000000ll;  // ~2 s at 2 GHz
 // K is accumulated in chunks of CHUNK_KB k-blocks (1024 products): each chunk
@@ -288,7 +290,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(tfull(a), 1);
-      mbar_init(tempty(a), 128);
+      mbar_init(tempty(a), 32 * EPI_WARPS);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -417,7 +419,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     __syncwarp();
   } else {
-    const int q = warp & 3;  // TMEM lane quadrant of this warp
+    const int q = warp & 3;               // TMEM lane quadrant of this warp
+    const int half = (warp - 2) >> 2;     // which 32-column groups of the tile it handles
     float* e = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(epi) + (warp - 2) * EPI_WARP_BYTES);
     // per row of the warp's 32: where column n of the tile goes directly
     // (sptr[i] + n, null for rows past M) and the first column stored
@@ -456,6 +459,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const uint32_t pm = tmem_base + acc * MAXBN + lane_off;
         const uint32_t pp = tmem_base + part * MAXBN + lane_off;
         for (int c = 0; c < BN / 16; ++c) {
+          if (((c >> 1) & 1) != half) continue;
           float vm[16], vp[16];
           tmem_ld16(pp + c * 16, vp);
           tmem_ld16(pm + c * 16, vm);
@@ -521,12 +525,13 @@ __global__ void __launch_bounds__(THREADS, 1)
       };
       int c = 0;
       for (; c + 2 <= BN / 16; c += 2) {
+        if (((c >> 1) & 1) != half) continue;
         float v[32];
         tmem_ld32(tbase + c * 16, v);
         emit16(v, nbase + c * 16);
         emit16(v + 16, nbase + c * 16 + 16);
       }
-      if (c < BN / 16) {
+      if (c < BN / 16 && ((c >> 1) & 1) == half) {
         float v[16];
         tmem_ld16(tbase + c * 16, v);
         emit16(v, nbase + c * 16);
