@@ -9,6 +9,8 @@
 //      eigenvectors by inverse iteration (orthogonalised against the earlier
 //      ones), residual bound |beta_m y_m| for convergence
 //   4. Ritz vectors U = Q_m Y, back-projection q = G^T u / sqrt(N mu)
+#include <cooperative_groups.h>
+
 #include <cfloat>
 #include <mutex>
 
@@ -623,6 +625,109 @@ __global__ void bisect_kernel(const double* a, const double* b, int m, int k, do
   if (tid == 0) theta[c] = 0.5 * (lo + hi) / sc;
 }
 
+// The same multisection with a cluster of kBisCta CTAs per eigenvalue: each
+// CTA evaluates 128 of the kBisCta * 128 points of a sweep (the bracket
+// shrinks (kBisCta * 128 + 1)-fold), the CTAs exchange their first crossing
+// through distributed shared memory, and all of them take the same new
+// bracket, so they make the same number of cluster barriers.  FP64 Sturm
+// counts are bound by the SM's FP64 rate, so the sweeps of one eigenvalue
+// spread over kBisCta SMs.
+constexpr int kBisCta = 4;
+__global__ void bisect_cluster_kernel(const double* a, const double* b, int m, int k, double* theta) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ double tsh_c[];
+  double* sa = tsh_c;
+  double* sb2 = tsh_c + m;
+  float* fa = reinterpret_cast<float*>(tsh_c + 2 * m);
+  float* fb2 = fa + m;
+  __shared__ double s_lo, s_hi, s_sc;
+  __shared__ int s4[32];
+  __shared__ int s_first;  // this CTA's first crossing in the current sweep (128: none)
+  const int c = blockIdx.x / kBisCta;
+  const int rank = (int)cluster.block_rank();
+  const int tid = threadIdx.x, nt = blockDim.x;  // nt = 128
+  // c is the same for the whole cluster, so a cluster leaves together
+  if (c >= k) return;
+  if (tid < 32) {
+    double lo = DBL_MAX, hi = -DBL_MAX;
+    for (int i = tid; i < m; i += 32) {
+      const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < m - 1 ? fabs(b[i]) : 0.0);
+      lo = fmin(lo, a[i] - r);
+      hi = fmax(hi, a[i] + r);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (tid == 0) {
+      const double tnorm = fmax(fabs(lo), fabs(hi));
+      int E = 0;
+      if (tnorm > 0.0) frexp(tnorm, &E);
+      const double sc = ldexp(1.0, -E);
+      s_sc = sc;
+      s_lo = lo * sc - (2.0 * DBL_EPSILON + 4.0 * DBL_MIN);
+      s_hi = hi * sc + (2.0 * DBL_EPSILON + 4.0 * DBL_MIN);
+    }
+  }
+  __syncthreads();
+  const double sc = s_sc;
+  for (int i = tid; i < m; i += nt) {
+    const double ai = a[i] * sc;
+    const double bi = i < m - 1 ? b[i] * sc : 0.0;
+    sa[i] = ai;
+    sb2[i] = bi * bi;
+    fa[i] = (float)ai;
+    fb2[i] = (float)(bi * bi);
+  }
+  __syncthreads();
+  const int t = m - 1 - c;  // index from the smallest
+  const int np = kBisCta * nt;  // points per sweep
+  const double inv_n = 1.0 / (double)(np + 1);
+  const int g = rank * nt + tid;  // this thread's point
+  double lo = s_lo, hi = s_hi;
+  const double lo0 = lo, hi0 = hi;
+  // the cluster's first crossing of a sweep, from every CTA's own
+  auto cluster_first = [&](bool pred) -> int {
+    const int f = block_first(pred, s4);
+    if (tid == 0) s_first = f;
+    cluster.sync();
+    int F = np;
+    for (int r = 0; r < kBisCta; ++r) {
+      const int fr = *cluster.map_shared_rank(&s_first, r);
+      if (fr < nt) {
+        F = r * nt + fr;
+        break;
+      }
+    }
+    cluster.sync();  // every CTA has read s_first before the next sweep writes it
+    return F;
+  };
+  // coarse FP32 sweeps
+  for (int it = 0; it < 2; ++it) {
+    const float xf = (float)(lo + (hi - lo) * (double)(g + 1) * inv_n);
+    const int F = cluster_first(sturm_count_f32(fa, fb2, m, xf) > t);
+    const double nhi = F < np ? lo + (hi - lo) * (double)(F + 1) * inv_n : hi;
+    const double nlo = F > 0 ? lo + (hi - lo) * (double)F * inv_n : lo;
+    lo = nlo;
+    hi = nhi;
+  }
+  lo = fmax(lo0, lo - 4e-6);
+  hi = fmin(hi0, hi + 4e-6);
+  const double tiny = 4.0 * DBL_MIN;
+  for (int it = 0; it < 64; ++it) {
+    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + tiny) break;
+    const double x = lo + (hi - lo) * (double)(g + 1) * inv_n;
+    const int F = cluster_first(sturm_count(sa, sb2, m, x) > t);
+    const double nhi = F < np ? lo + (hi - lo) * (double)(F + 1) * inv_n : hi;
+    const double nlo = F > 0 ? lo + (hi - lo) * (double)F * inv_n : lo;
+    if (!(nlo < nhi)) break;
+    lo = nlo;
+    hi = nhi;
+  }
+  if (rank == 0 && tid == 0) theta[c] = 0.5 * (lo + hi) / sc;
+}
+
 // Eigenvectors of T_m for theta[0..k-1] by inverse iteration with a
 // partially pivoted tridiagonal LU of (T - theta I).  One block per cluster
 // (block c works only if c starts a cluster); inside a cluster the vectors
@@ -835,6 +940,9 @@ hess_status eig_kernel_attributes() {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEigSmemCap);
     if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(bisect_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kEigSmemCap);
+    if (e == cudaSuccess)
       e = cudaFuncSetAttribute(inviter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEigSmemCap);
   });
   if (e != cudaSuccess) return set_error(HESS_ERR_CUDA, "eigen kernel attributes: %s", cudaGetErrorString(e));
@@ -853,10 +961,26 @@ hess_status tridiag_topk(const double* a, const double* b, int m, int k, double*
   const bool inv_g = (size_t)6 * m * sizeof(double) > kEigSmemCap;
   const bool bis_g = (size_t)3 * m * sizeof(double) > kEigSmemCap;
   if ((inv_g || bis_g) && !scratch) return set_error(HESS_ERR_INVALID_ARG, "tridiagonal scratch missing");
-  // one block per eigenvalue: the FP64 Sturm recurrences of different
-  // eigenvalues run on different SMs
-  bisect_kernel<<<(unsigned)k, 128, bis_g ? 0 : (size_t)3 * m * sizeof(double), s>>>(a, b, m, k, theta,
-                                                                                   bis_g ? scratch : nullptr);
+  // a cluster of CTAs per eigenvalue (T in each CTA's shared memory), or,
+  // when T does not fit shared memory, one block per eigenvalue over global
+  // scratch
+  if (!bis_g) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(kBisCta * k));
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = (size_t)3 * m * sizeof(double);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kBisCta;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    HM_CUDA(cudaLaunchKernelEx(&cfg, bisect_cluster_kernel, a, b, m, k, theta));
+  } else {
+    bisect_kernel<<<(unsigned)k, 128, 0, s>>>(a, b, m, k, theta, scratch);
+  }
   HM_LAUNCHED();
   // eigenvalues closer than 1e-6 of the largest share a cluster
   clusters_kernel<<<1, 32, 0, s>>>(theta, k, 1e-6, cstart);
