@@ -110,9 +110,13 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
       if (!y_dev) HM_CUDA(cudaMemcpyAsync(ys, Y, N * TL * 4, cudaMemcpyHostToDevice, sA));
     }
     {
+      // one preparation (one forward/backward pass) for both matrices, then
+      // the OPG's job and the Hessian's jobs as two launches, so that the
+      // OPG's copy can start while the Hessian is contracted
       SplitGuard sg(splitA, kSplitBytes, h->sm_count);
-      if (OPG) HM_TRY(tc_prep(h, TcItem{xs, ys, N, true, false, os, nullptr, x3}, ar, live, plan_o, sA));
-      if (H) HM_TRY(tc_prep(h, TcItem{xs, ys, N, false, true, nullptr, hs, x3}, ar, live, plan_h, sA));
+      TcPlan both;
+      HM_TRY(tc_prep(h, TcItem{xs, ys, N, OPG != nullptr, H != nullptr, os, hs, x3}, ar, live, both, sA));
+      tc_split_plan(both, OPG ? 1 : 0, plan_o, plan_h);
     }
     tabO = ar.off;
     HM_TRY(tc_launch_plan(h->sm_count, plan_o, ar, false, x3, h->err_dev, h->stage, sA));

@@ -396,10 +396,14 @@ hess_status f64_gemm_nt_tc(hess_mlp* h, const double* G, int64_t ldg, const doub
 // Jobs and tiles gathered for one persistent launch.
 struct TcPlan {
   std::vector<tc::Job> jobs;
-  std::vector<int4> tiles;  // (job, row tile, column tile, 0)
-  int64_t tiles_cap = 0;    // tiles at the narrowest candidate width (table room)
+  std::vector<int64_t> caps;  // per job: its tiles at the narrowest candidate width
+  std::vector<int4> tiles;    // (job, row tile, column tile, 0)
+  int64_t tiles_cap = 0;      // tiles at the narrowest candidate width (table room)
   double syrk_flops = 0.0, hess_flops = 0.0;
 };
+// The first `nfirst` jobs of `both` (with their tiles and the SYRK flops) and
+// the others (re-indexed, with the Hessian flops), for separate launches.
+void tc_split_plan(const TcPlan& both, int nfirst, TcPlan& first, TcPlan& rest);
 
 // One network's request: device X (N x T_1), Y (N x T_L) and the P x P
 // device outputs of the requested matrices (the pointers are not consulted to

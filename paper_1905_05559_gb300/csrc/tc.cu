@@ -1241,7 +1241,8 @@ hess_status tc_prep(hess_mlp* h, const TcItem& it, Arena& ar, bool live, TcPlan&
     Job job{};
     HM_TRY(build(BN, job, plan.tiles));
     plan.jobs.push_back(job);
-    plan.tiles_cap += syrk_tile_count(P, kTuneCand[0]);
+    plan.caps.push_back(syrk_tile_count(P, kTuneCand[0]));
+    plan.tiles_cap += plan.caps.back();
   }
   if (it.want_hess) {
     // exact Hessian (Sec. 3, Eq. for H_ij) from the R-operator over the bias
@@ -1294,7 +1295,8 @@ hess_status tc_prep(hess_mlp* h, const TcItem& it, Arena& ar, bool live, TcPlan&
         Job jw{};
         HM_TRY(build(BN, jw, plan.tiles));
         plan.jobs.push_back(jw);
-        plan.tiles_cap += cdiv(rows, BM) * cdiv(Tin, kTuneCand[0]);
+        plan.caps.push_back(cdiv(rows, BM) * cdiv(Tin, kTuneCand[0]));
+        plan.tiles_cap += plan.caps.back();
       }
       {
         const int jid = (int)plan.jobs.size();
@@ -1309,11 +1311,32 @@ hess_status tc_prep(hess_mlp* h, const TcItem& it, Arena& ar, bool live, TcPlan&
         Job jf{};
         HM_TRY(build(BN, jf, plan.tiles));
         plan.jobs.push_back(jf);
-        plan.tiles_cap += cdiv(Tin + 1, BM) * (int64_t)Tout * cdiv(rest, kTuneCand[0]);
+        plan.caps.push_back(cdiv(Tin + 1, BM) * (int64_t)Tout * cdiv(rest, kTuneCand[0]));
+        plan.tiles_cap += plan.caps.back();
       }
     }
   }
   return HESS_OK;
+}
+
+void tc_split_plan(const TcPlan& both, int nfirst, TcPlan& first, TcPlan& rest) {
+  first = TcPlan{};
+  rest = TcPlan{};
+  for (int j = 0; j < (int)both.jobs.size(); ++j) {
+    TcPlan& dst = j < nfirst ? first : rest;
+    dst.jobs.push_back(both.jobs[j]);
+    const int64_t cap = j < (int)both.caps.size() ? both.caps[j] : 0;
+    dst.caps.push_back(cap);
+    dst.tiles_cap += cap;
+  }
+  for (const int4& t : both.tiles) {
+    if (t.x < nfirst)
+      first.tiles.push_back(t);
+    else
+      rest.tiles.push_back(make_int4(t.x - nfirst, t.y, t.z, t.w));
+  }
+  first.syrk_flops = both.syrk_flops;
+  rest.hess_flops = both.hess_flops;
 }
 
 hess_status tc_launch_plan(int sm_count, const TcPlan& plan, Arena& ar, bool live, bool x3, int* err,
