@@ -732,7 +732,9 @@ __global__ void bisect_cluster_kernel(const double* a, const double* b, int m, i
 // partially pivoted tridiagonal LU of (T - theta I).  One block per cluster
 // (block c works only if c starts a cluster); inside a cluster the vectors
 // are found in order, each orthogonalised against the earlier ones at every
-// iteration.  Thread 0 runs the O(m) recurrences.  Y: k rows of length ldy.
+// iteration.  Thread 0 runs the O(m) recurrences (elimination and solves);
+// the fill, the reciprocal pivots and the norms are spread over the block.
+// Y: k rows of length ldy.
 // res[c] = |beta_m y_c[m-1]| bounds the residual of Ritz pair c.
 __global__ void inviter_kernel(const double* a, const double* b, int m, int k, const double* theta,
                                const int* cstart, double* Y, int64_t ldy, const double* beta_last,
@@ -768,15 +770,17 @@ __global__ void inviter_kernel(const double* a, const double* b, int m, int k, c
   for (int c = c0; c < k && cstart[c] == c0; ++c) {
     const double th = theta[c];
     double* y = ys;
-    if (threadIdx.x == 0) {
-      for (int i = 0; i < m; ++i) {
-        d[i] = a[i] - th;
-        if (i < m - 1) {
-          du[i] = b[i];
-          dl[i] = b[i];
-        }
-        du2[i] = 0.0;
+    // T - theta I by all threads; the elimination below is sequential
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      d[i] = a[i] - th;
+      if (i < m - 1) {
+        du[i] = b[i];
+        dl[i] = b[i];
       }
+      du2[i] = 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
       for (int i = 0; i < m - 1; ++i) {
         if (fabs(d[i]) >= fabs(dl[i])) {
           piv[i] = 0;
@@ -799,28 +803,35 @@ __global__ void inviter_kernel(const double* a, const double* b, int m, int k, c
         }
       }
       if (fabs(d[m - 1]) < tiny) d[m - 1] = d[m - 1] < 0 ? -tiny : tiny;
-      for (int i = 0; i < m; ++i) d[i] = rcp64(d[i]);  // the solves multiply
     }
+    __syncthreads();
+    // the solves multiply by the reciprocal pivots
+    for (int i = threadIdx.x; i < m; i += blockDim.x) d[i] = rcp64(d[i]);
     for (int i = threadIdx.x; i < m; i += blockDim.x) y[i] = 1.0 + 0.25 * rnd_sym(key + c, i);
     __syncthreads();
     // two solves: with a shift accurate to a few ulps the first leaves an
     // error of about eps ||T|| / gap, the second removes it
     for (int it = 0; it < 2; ++it) {
-      if (threadIdx.x == 0) {
-        for (int i = 0; i < m - 1; ++i) {
-          if (piv[i]) {
-            const double t = y[i];
-            y[i] = y[i + 1];
-            y[i + 1] = t;
+      if (warp == 0) {
+        if (lane == 0) {
+          for (int i = 0; i < m - 1; ++i) {
+            if (piv[i]) {
+              const double t = y[i];
+              y[i] = y[i + 1];
+              y[i + 1] = t;
+            }
+            y[i + 1] -= dl[i] * y[i];
           }
-          y[i + 1] -= dl[i] * y[i];
+          y[m - 1] *= d[m - 1];
+          if (m >= 2) y[m - 2] = (y[m - 2] - du[m - 2] * y[m - 1]) * d[m - 2];
+          for (int i = m - 3; i >= 0; --i) y[i] = (y[i] - du[i] * y[i + 1] - du2[i] * y[i + 2]) * d[i];
         }
-        y[m - 1] *= d[m - 1];
-        if (m >= 2) y[m - 2] = (y[m - 2] - du[m - 2] * y[m - 1]) * d[m - 2];
-        for (int i = m - 3; i >= 0; --i) y[i] = (y[i] - du[i] * y[i + 1] - du2[i] * y[i + 2]) * d[i];
+        __syncwarp();
+        // max |y_i| over the warp (exact in any order)
         double mx = 0.0;
-        for (int i = 0; i < m; ++i) mx = fmax(mx, fabs(y[i]));
-        sh[0] = mx > 0.0 ? 1.0 / mx : 1.0;
+        for (int i = lane; i < m; i += 32) mx = fmax(mx, fabs(y[i]));
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) sh[0] = mx > 0.0 ? 1.0 / mx : 1.0;
       }
       __syncthreads();
       const double inv = sh[0];

@@ -20,11 +20,12 @@ template <>
 struct GemmCfg<float> {
   static constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8;
 };
-// narrow outputs (<= 32 columns, e.g. the k eigenvector columns)
+// narrow outputs (<= 32 columns, e.g. the k eigenvector columns, or a layer
+// of at most 32 units)
 struct GemmCfgNarrow64 {
   static constexpr int BM = 128, BN = 32, BK = 16, TM = 8, TN = 2;
 };
-// very narrow FP64 outputs (<= 16 columns): no idle half tile
+// very narrow outputs (<= 16 columns): no idle half tile
 struct GemmCfgNarrow16 {
   static constexpr int BM = 128, BN = 16, BK = 16, TM = 8, TN = 1;
 };
@@ -287,9 +288,11 @@ static hess_status gemm_cfg(const Gemm<T>& g, cudaStream_t s) {
   int splits = 1;
   const int sms = g_split.sms > 0 ? g_split.sms : 148;
   // (FP64 runs at a small fraction of the FP32 rate, so FP64 products split
-  // down to slices of 32)
-  const int64_t kmin = std::is_same<T, double>::value ? 64 : 256;
-  const int64_t kslice = std::is_same<T, double>::value ? 16 : 128;
+  // down to slices of 16; FP32 products on the narrow 128-row tiles, whose
+  // blocks carry little work per K step, down to slices of 32)
+  constexpr bool narrow = Cfg::BM == 128 && Cfg::BN <= 32;
+  const int64_t kmin = std::is_same<T, double>::value ? 64 : (narrow ? 64 : 256);
+  const int64_t kslice = std::is_same<T, double>::value ? 16 : (narrow ? 32 : 128);
   if (!g.upper && g_split.p && tiles * g.batch < 2 * sms && g.K >= kmin) {
     int64_t maxs = g.K / kslice;
     int64_t cap = (int64_t)(g_split.bytes / ((size_t)g.M * g.N * g.batch * sizeof(T)));
@@ -337,7 +340,7 @@ static hess_status gemm_cfg(const Gemm<T>& g, cudaStream_t s) {
 //   K <= 32 and a narrow output     -> one thread per entry
 //   M, N <= 16                      -> 16 x 16 tiles (split K)
 //   M < 32 <= 4 M <= N              -> the transposed problem C^T = B^T A^T
-//   FP64, N <= 16 / N <= 32         -> 256 x 16 / 128 x 32 tiles
+//   N <= 16 / N <= 32               -> 128 x 16 / 128 x 32 tiles
 template <typename T>
 hess_status gemm(const Gemm<T>& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return HESS_OK;
@@ -367,8 +370,8 @@ hess_status gemm(const Gemm<T>& g, cudaStream_t s) {
     t.scn = g.scm;
     return gemm(t, s);
   }
-  if (std::is_same<T, double>::value && !g.upper && g.N <= 16) return gemm_cfg<T, GemmCfgNarrow16>(g, s);
-  if (std::is_same<T, double>::value && !g.upper && g.N <= 32) return gemm_cfg<T, GemmCfgNarrow64>(g, s);
+  if (!g.upper && g.N <= 16) return gemm_cfg<T, GemmCfgNarrow16>(g, s);
+  if (!g.upper && g.N <= 32) return gemm_cfg<T, GemmCfgNarrow64>(g, s);
   return gemm_cfg<T, GemmCfg<T>>(g, s);
 }
 template hess_status gemm<double>(const Gemm<double>&, cudaStream_t);
@@ -464,27 +467,37 @@ __global__ void bias_act_kernel(const T* Z, const T* b, int64_t N, int Tn, int a
 }
 
 // Softmax output with the log-sum-exp in FP64; delta^(L) = p * sum(y) - y.
+// One warp per example, the lanes over the classes; the xor-butterfly sums
+// leave the same bits in every lane (IEEE addition commutes).
 template <typename T>
 __global__ void softmax_kernel(const T* Z, const T* b, const T* Y, int64_t N, int TL, T* Pout,
                                T* D, T* ysum) {
-  int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (n >= N) return;
+  const int64_t n = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (n >= N) return;  // whole warps
   const T* z = Z + n * TL;
   const T* y = Y + n * TL;
   double m = -INFINITY;
-  for (int i = 0; i < TL; ++i) m = fmax(m, (double)z[i] + (double)b[i]);
+  for (int i = lane; i < TL; i += 32) m = fmax(m, (double)z[i] + (double)b[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   double s = 0.0, ys = 0.0;
-  for (int i = 0; i < TL; ++i) {
+  for (int i = lane; i < TL; i += 32) {
     s += exp((double)z[i] + (double)b[i] - m);
     ys += (double)y[i];
   }
-  double lse = m + log(s);
-  for (int i = 0; i < TL; ++i) {
-    double p = exp((double)z[i] + (double)b[i] - lse);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    ys += __shfl_xor_sync(0xffffffffu, ys, o);
+  }
+  const double lse = m + log(s);
+  for (int i = lane; i < TL; i += 32) {
+    const double p = exp((double)z[i] + (double)b[i] - lse);
     Pout[n * TL + i] = (T)p;
     D[n * TL + i] = (T)(p * ys - (double)y[i]);
   }
-  ysum[n] = (T)ys;
+  if (lane == 0) ysum[n] = (T)ys;
 }
 
 template <typename T>
@@ -551,7 +564,7 @@ hess_status forward_backward(const Net& net, const T* omega, const T* X, const T
                                                           const_cast<T*>(c.a[w]), c.s1[w], c.s2[w]);
       HM_LAUNCHED();
     } else {
-      softmax_kernel<T><<<(unsigned)cdiv(N, 128), 128, 0, s>>>(c.z, b, Y, N, Tout, c.p, c.d[w],
+      softmax_kernel<T><<<(unsigned)cdiv(N, 8), 256, 0, s>>>(c.z, b, Y, N, Tout, c.p, c.d[w],
                                                                 c.ysum);
       HM_LAUNCHED();
     }

@@ -1694,29 +1694,39 @@ __global__ void digits_rows_kernel(const double* A, int64_t rs, int64_t ks, int6
   }
 }
 
+// max(m, |x|) on the bit patterns of doubles (integer order is the order of
+// non-negative doubles); NaN is skipped, as fmax skips it
+__device__ __forceinline__ unsigned long long max_abs_bits(unsigned long long m, double x) {
+  const unsigned long long a = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  return (a <= 0x7ff0000000000000ull && a > m) ? a : m;
+}
+
 // ex[c] for the columns of a row-major n x m FP64 array G (the rows of G^T):
 // the exponent E with max_r |G[r][c]| = f 2^E, f in [0.5, 1).  Block (32 x 8):
-// 32 adjacent columns, 8 slices of the rows.
+// 32 adjacent columns, 8 slices of the rows, eight loads in flight per
+// thread; the maxima are taken on the integer pipe.
 __global__ void colmax_exp_kernel(const double* G, int64_t ldg, int64_t n, int64_t m, int* ex) {
-  __shared__ double red[8][33];
+  __shared__ unsigned long long red[8][33];
   const int64_t c = blockIdx.x * (int64_t)32 + threadIdx.x;
-  double mx = 0.0;
+  unsigned long long mx = 0ull;
   if (c < m) {
-    double m0 = 0.0, m1 = 0.0;
     int64_t r = threadIdx.y;
-    for (; r + 8 < n; r += 16) {
-      m0 = fmax(m0, fabs(G[r * ldg + c]));
-      m1 = fmax(m1, fabs(G[(r + 8) * ldg + c]));
+    for (; r + 56 < n; r += 64) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = G[(r + 8 * u) * ldg + c];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) mx = max_abs_bits(mx, v[u]);
     }
-    if (r < n) m0 = fmax(m0, fabs(G[r * ldg + c]));
-    mx = fmax(m0, m1);
+    for (; r < n; r += 8) mx = max_abs_bits(mx, G[r * ldg + c]);
   }
   red[threadIdx.y][threadIdx.x] = mx;
   __syncthreads();
   if (threadIdx.y == 0 && c < m) {
-    for (int y = 1; y < 8; ++y) mx = fmax(mx, red[y][threadIdx.x]);
+    for (int y = 1; y < 8; ++y) mx = red[y][threadIdx.x] > mx ? red[y][threadIdx.x] : mx;
+    const double v = __longlong_as_double((long long)mx);
     int E = 0;
-    if (mx > 0.0 && mx <= DBL_MAX) frexp(mx, &E);
+    if (v > 0.0 && v <= DBL_MAX) frexp(v, &E);
     ex[c] = E;
   }
 }
@@ -1774,13 +1784,20 @@ __global__ void combine_general_kernel(const float* T, int64_t M, int64_t Nn, Di
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= M * Nn) return;
   const int64_t r = idx / Nn, c = idx % Nn;
+  // The contraction results are integers below 2^24 in magnitude (at most
+  // 4096 products of digits in [-64, 64]), so the terms of one weight
+  // w = d + e are summed exactly as integers, and only the eight weighted
+  // sums, smallest weight first, are FP64 operations.
   double s = 0.0;
-  for (int j = dj.count - 1; j >= 0; --j) {  // the later digits of A (smaller weights) first
-    const int d = dj.d[j], e1 = min(dj.e1[j], kDigits - d);
-    const int64_t wd = (int64_t)(dj.e1[j] - dj.e0[j]) * Nn;
-    const float* row = T + dj.off[j] + r * wd + c;
-    for (int e = e1 - 1; e >= dj.e0[j]; --e)
-      s = fma((double)row[(int64_t)(e - dj.e0[j]) * Nn], dj.wt[d + e], s);
+  for (int w = kDigits - 1; w >= 0; --w) {
+    long long a = 0;
+    for (int j = 0; j < dj.count; ++j) {
+      const int e = w - dj.d[j];  // d + e = w <= 7
+      if (e < dj.e0[j] || e >= dj.e1[j]) continue;
+      const int64_t wd = (int64_t)(dj.e1[j] - dj.e0[j]) * Nn;
+      a += __float2int_rn(T[dj.off[j] + r * wd + (int64_t)(e - dj.e0[j]) * Nn + c]);
+    }
+    s = fma((double)a, dj.wt[w], s);
   }
   s = ldexp(s, exA[r] + exB[c]);
   double* o = C + r * scm + c * scn;
