@@ -75,11 +75,24 @@ struct LzArgs {
 
 constexpr long long BAR_TIMEOUT = 4000000000ll;
 
+__device__ __forceinline__ unsigned atom_add_release_gpu(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // Grid barrier: thread 0 of every block adds to one counter, block 0 adding
 // 2^31 - (gridDim.x - 1) and the others 1, so that the counter's top bit
 // flips exactly when the last block arrives; each block waits (bounded) for
-// the flip from the value it saw on arrival.  Fences on both sides publish
-// the block's writes and make the other blocks' writes visible.
+// the flip from the value it saw on arrival.  The add is a release at GPU
+// scope (after the block barrier, it publishes every thread's writes) and the
+// polling load an acquire (the block barrier after it passes the other
+// blocks' writes on to every thread).
 __device__ bool grid_barrier(const LzArgs& a, unsigned& epoch) {
   __shared__ int ok;
   __syncthreads();
@@ -87,17 +100,15 @@ __device__ bool grid_barrier(const LzArgs& a, unsigned& epoch) {
     ok = 1;
     ++epoch;
     const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
-    __threadfence();
-    const unsigned old = atomicAdd(a.bar, add);
+    const unsigned old = atom_add_release_gpu(a.bar, add);
     const long long t0 = clock64();
-    while (((old ^ *(volatile unsigned*)a.bar) & 0x80000000u) == 0u) {
+    while (((old ^ ld_acquire_gpu(a.bar)) & 0x80000000u) == 0u) {
       if (clock64() - t0 > BAR_TIMEOUT || *(volatile int*)a.err) {
         atomicExch(a.err, 1);
         ok = 0;
         break;
       }
     }
-    __threadfence();
   }
   __syncthreads();
   return ok != 0;
@@ -875,7 +886,8 @@ __global__ void inviter_kernel(const double* a, const double* b, int m, int k, c
 }
 
 // Final per-column pass: evals, zero null columns, scale 1/sqrt(N mu),
-// sign so that the largest-magnitude entry is positive.
+// sign so that the largest-magnitude entry is positive.  One block of 1024
+// threads per column (up to 32 warps).
 __global__ void finalize_kernel(double* evecs, int64_t P, const double* theta, int k, double N,
                                 double* evals, int* deficient) {
   __shared__ double shv[32];
@@ -895,6 +907,7 @@ __global__ void finalize_kernel(double* evecs, int64_t P, const double* theta, i
   const double sc = N > 0.0 ? 1.0 / sqrt(N * mu) : 1.0;  // N = 0: the vectors are eigenvectors already
   double best = -1.0;
   int64_t bi = 0;
+#pragma unroll 4
   for (int64_t i = threadIdx.x; i < P; i += blockDim.x) {
     double v = q[i] * sc;
     q[i] = v;
@@ -1291,7 +1304,7 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
     HM_TRY(gemm(g, s));
   }
   HM_CUDA(cudaMemsetAsync(flag + 1, 0, sizeof(int), s));
-  finalize_kernel<<<k, 256, 0, s>>>(evecs_d, P, theta, k, (double)N, evals_d, flag + 1);
+  finalize_kernel<<<k, 1024, 0, s>>>(evecs_d, P, theta, k, (double)N, evals_d, flag + 1);
   HM_LAUNCHED();
   int* hi = reinterpret_cast<int*>(hp);
   HM_CUDA(cudaMemcpyAsync(hi, flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1334,7 +1347,7 @@ hess_status topk_eig_dense(hess_mlp* h, const double* M, int64_t n, int k, doubl
   g.scn = n;
   HM_TRY(gemm(g, s));
   HM_CUDA(cudaMemsetAsync(flag + 1, 0, sizeof(int), s));
-  finalize_kernel<<<k, 256, 0, s>>>(evecs_d, n, lb.theta, k, 0.0, evals_d, flag + 1);
+  finalize_kernel<<<k, 1024, 0, s>>>(evecs_d, n, lb.theta, k, 0.0, evals_d, flag + 1);
   HM_LAUNCHED();
   int* hi = reinterpret_cast<int*>(h->host_pinned);
   HM_CUDA(cudaMemcpyAsync(hi, flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
