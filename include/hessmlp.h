@@ -176,10 +176,11 @@ HESS_API hess_status opg_topk_eig_streaming(hess_mlp* h, const void* X, const vo
 /* OPG, exact Hessian and top-k OPG eigenpairs of one data set in one call
  * (any of them may be left out: OPG or H NULL, k = 0).  The same results as
  * opg(), exact_hessian() and opg_topk_eig() with the same arguments, but
- * scheduled across three streams for BF16/BF16X3: the tensor-core operands and
+ * scheduled across four streams for BF16/BF16X3: the tensor-core operands and
  * contractions on the handle's stream, the FP64 eigen step (Gram matrix,
  * Lanczos, back-projection) concurrently on a second, higher-priority stream,
- * and the copies of host outputs on a third, each behind its contraction.
+ * and the copies of host outputs behind their contractions, each matrix in two
+ * halves on a third and a fourth stream.
  * X, Y float (double for HESS_FP64), host or device; OPG and H as in
  * opg()/exact_hessian(); evals/evecs as in opg_topk_eig().  Other precisions,
  * or nothing to overlap, run the single calls in turn.  The call returns

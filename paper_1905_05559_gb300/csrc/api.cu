@@ -103,7 +103,8 @@ void host_side_free(hess_mlp* h) {
   h->mb_batch = nullptr;
   if (h->stream2) cudaStreamDestroy(h->stream2);
   if (h->stream3) cudaStreamDestroy(h->stream3);
-  h->stream2 = h->stream3 = nullptr;
+  if (h->stream4) cudaStreamDestroy(h->stream4);
+  h->stream2 = h->stream3 = h->stream4 = nullptr;
   if (h->host_pinned) cudaFreeHost(h->host_pinned);
   if (h->err_host) cudaFreeHost(h->err_host);
   h->host_pinned = nullptr;

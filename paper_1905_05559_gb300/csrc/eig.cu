@@ -622,9 +622,13 @@ __global__ void bisect_kernel(const double* a, const double* b, int m, int k, do
   }
   lo = fmax(lo0, lo - 4e-6);
   hi = fmin(hi0, hi + 4e-6);
+  // down to a few ulps of the eigenvalue, or to 4 eps ||T|| (the accuracy of
+  // any backward-stable symmetric eigensolver) for eigenvalues much smaller
+  // than ||T||
   const double tiny = 4.0 * DBL_MIN;
+  const double tol_abs = 4.0 * DBL_EPSILON * fmax(fabs(lo0), fabs(hi0));
   for (int it = 0; it < 64; ++it) {
-    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + tiny) break;
+    if (hi - lo <= fmax(2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)), tol_abs) + tiny) break;
     const double x = lo + (hi - lo) * (double)(tid + 1) * inv_n;
     const int f = block_first(sturm_count(sa, sb2, m, x) > t, s4);
     const double nhi = f < nt ? lo + (hi - lo) * (double)(f + 1) * inv_n : hi;
@@ -725,9 +729,13 @@ __global__ void bisect_cluster_kernel(const double* a, const double* b, int m, i
   }
   lo = fmax(lo0, lo - 4e-6);
   hi = fmin(hi0, hi + 4e-6);
+  // down to a few ulps of the eigenvalue, or to 4 eps ||T|| (the accuracy of
+  // any backward-stable symmetric eigensolver) for eigenvalues much smaller
+  // than ||T||
   const double tiny = 4.0 * DBL_MIN;
+  const double tol_abs = 4.0 * DBL_EPSILON * fmax(fabs(lo0), fabs(hi0));
   for (int it = 0; it < 64; ++it) {
-    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + tiny) break;
+    if (hi - lo <= fmax(2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)), tol_abs) + tiny) break;
     const double x = lo + (hi - lo) * (double)(g + 1) * inv_n;
     const int F = cluster_first(sturm_count(sa, sb2, m, x) > t);
     const double nhi = F < np ? lo + (hi - lo) * (double)(F + 1) * inv_n : hi;

@@ -1,5 +1,5 @@
 // All curvature matrices of one network and one data set in one call, with
-// the work of the three on three streams:
+// the work of the three on four streams:
 //
 //   stream A (the handle's)    : forward/backward, the tensor-core operands
 //                                and the contractions of the OPG and the
@@ -7,14 +7,16 @@
 //   stream B (the handle's 2nd): the FP64 forward/backward, Gram matrix,
 //                                Lanczos launches, tridiagonal eigenpairs and
 //                                back-projection
-//   stream C (the handle's 3rd): each matrix's copy to a host buffer, queued
-//                                behind its contraction
+//   streams C and D (3rd, 4th): each matrix's copy to a host buffer, queued
+//                                behind its contraction, in two halves (one
+//                                per stream, so that two copy engines share
+//                                each transfer)
 //
 // Stream B has the higher priority: the eigen step is the longer chain of
 // short launches, and its blocks are scheduled first when both streams have
 // work waiting.  The contractions fill the SMs around it.  (Holding the
 // contractions back until the Lanczos launches are done measured slower.)
-// Host outputs are written to device memory and copied by the copy engine,
+// Host outputs are written to device memory and copied by the copy engines,
 // so that the OPG's transfer overlaps the Hessian's contraction and both
 // overlap the eigen step.  The streams use separate regions of the handle's
 // workspace (and separate split-K scratch).
@@ -39,7 +41,7 @@ hess_status on_device(const hess_mlp* h, const void* p, bool* dev) {
 }
 
 struct EventSet {
-  cudaEvent_t e[5] = {};
+  cudaEvent_t e[6] = {};
   ~EventSet() {
     for (cudaEvent_t x : e)
       if (x) cudaEventDestroy(x);
@@ -87,7 +89,24 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
     HM_CUDA(cudaStreamCreateWithPriority(&h->stream2, cudaStreamNonBlocking, hi));
   }
   if (!h->stream3) HM_CUDA(cudaStreamCreateWithFlags(&h->stream3, cudaStreamNonBlocking));
-  const cudaStream_t sA = h->stream, sB = h->stream2, sC = h->stream3;
+  if (!h->stream4) HM_CUDA(cudaStreamCreateWithFlags(&h->stream4, cudaStreamNonBlocking));
+  const cudaStream_t sA = h->stream, sB = h->stream2, sC = h->stream3, sD = h->stream4;
+  // a device matrix to the host in two halves, one per copy stream, both
+  // behind event e of stream A
+  auto to_host = [&](void* dstv, const float* src, cudaEvent_t e) -> hess_status {
+    float* dst = static_cast<float*>(dstv);
+    const int64_t n = P * P, half = n / 2;
+    HM_CUDA(cudaEventRecord(e, sA));
+    HM_CUDA(cudaStreamWaitEvent(sC, e, 0));
+    HM_CUDA(cudaStreamWaitEvent(sD, e, 0));
+    HM_CUDA(cudaMemcpyAsync(dst, src, half * 4, cudaMemcpyDeviceToHost, sC));
+    HM_CUDA(cudaMemcpyAsync(dst + half, src + half, (n - half) * 4, cudaMemcpyDeviceToHost, sD));
+    return HESS_OK;
+  };
+  auto drain_copies = [&]() {
+    cudaStreamSynchronize(sC);
+    cudaStreamSynchronize(sD);
+  };
 
   // ---- workspace: region A (tensor-core operands and tables), region B
   // (the eigen step); the planning pass and the live pass take the same
@@ -154,24 +173,16 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
     Arena at{h->ws, tabO};
     tc_status = tc_launch_plan(h->sm_count, plan_o, at, true, x3, h->err_dev, h->stage, sA);
   }
-  if (OPG && !o_dev && tc_status == HESS_OK) {
-    HM_CUDA(cudaEventRecord(ev.e[2], sA));
-    HM_CUDA(cudaStreamWaitEvent(sC, ev.e[2], 0));
-    HM_CUDA(cudaMemcpyAsync(OPG, os, P * P * 4, cudaMemcpyDeviceToHost, sC));
-  }
+  if (OPG && !o_dev && tc_status == HESS_OK) HM_TRY(to_host(OPG, os, ev.e[2]));
   if (H && tc_status == HESS_OK) {
     Tick t(h, HESS_K_HCONTRACT, plan_h.hess_flops, 0.0);
     Arena at{h->ws, tabH};
     tc_status = tc_launch_plan(h->sm_count, plan_h, at, true, x3, h->err_dev, h->stage, sA);
   }
-  if (H && !hh_dev && tc_status == HESS_OK) {
-    HM_CUDA(cudaEventRecord(ev.e[3], sA));
-    HM_CUDA(cudaStreamWaitEvent(sC, ev.e[3], 0));
-    HM_CUDA(cudaMemcpyAsync(H, hs, P * P * 4, cudaMemcpyDeviceToHost, sC));
-  }
+  if (H && !hh_dev && tc_status == HESS_OK) HM_TRY(to_host(H, hs, ev.e[3]));
   if (tc_status != HESS_OK) {
     cudaStreamSynchronize(sB);
-    cudaStreamSynchronize(sC);
+    drain_copies();
     return tc_status;
   }
 
@@ -194,8 +205,8 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
   }
   h->stream = sA;
   if (eig_status != HESS_OK) {
-    cudaStreamSynchronize(sB);  // nothing of B or C may run past the call
-    cudaStreamSynchronize(sC);
+    cudaStreamSynchronize(sB);  // nothing of B or the copies may run past the call
+    drain_copies();
     return eig_status;
   }
   if (!ev_dev) HM_CUDA(cudaMemcpyAsync(evals, evd, k * sizeof(double), cudaMemcpyDeviceToHost, sB));
@@ -205,6 +216,8 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
   HM_CUDA(cudaStreamWaitEvent(sA, ev.e[1], 0));
   HM_CUDA(cudaEventRecord(ev.e[4], sC));
   HM_CUDA(cudaStreamWaitEvent(sA, ev.e[4], 0));
+  HM_CUDA(cudaEventRecord(ev.e[5], sD));
+  HM_CUDA(cudaStreamWaitEvent(sA, ev.e[5], 0));
   if (host_io) {
     HM_CUDA(cudaStreamSynchronize(sA));
     HM_TRY(take_sticky_error(h));

@@ -128,10 +128,12 @@ struct hess_mlp {
   int* err_host = nullptr;
   int* err_dev = nullptr;
   hm::PinnedStage stage;
-  // second stream (the eigen step) and copy stream (the matrices' transfer to
-  // the host) of the fused call, created on first use
+  // second stream (the eigen step) and two copy streams (the matrices'
+  // transfer to the host, each matrix in two halves, one per copy stream, so
+  // that two copy engines share it) of the fused call, created on first use
   cudaStream_t stream2 = nullptr;
   cudaStream_t stream3 = nullptr;
+  cudaStream_t stream4 = nullptr;
   // batch object of hessian_minibatches (created on first use)
   hess_batch* mb_batch = nullptr;
   // second growable device buffer, for results that the single-call entry
