@@ -597,40 +597,39 @@ template hess_status forward_backward<float>(const Net&, const float*, const flo
 
 // ================================================== per-example gradients
 // G[n, woff + i*Tin + k] = delta[n,i] a[n,k];  G[n, boff + i] = delta[n,i].
-// One block row per example; consecutive threads write consecutive columns.
+// Block (n, y) writes rows i in [16 y, 16 y + 16) of example n's outer
+// product: consecutive threads take consecutive k (coalesced stores, no
+// index division), a[n,k] is loaded once per k and delta[n,i] is a broadcast.
+constexpr int kGradRows = 16;
 template <typename T>
 __global__ void write_grads_kernel(const T* D, const T* A, int Tin, int Tout, T* G, int64_t ldg,
                                    int64_t woff, int64_t boff) {
   const int64_t n = blockIdx.x;
-  const int64_t nW = (int64_t)Tin * Tout;
+  const int i0 = blockIdx.y * kGradRows;
+  const int i1 = min(Tout, i0 + kGradRows);
   const T* d = D + n * Tout;
   const T* a = A + n * Tin;
   T* g = G + n * ldg;
-  const int64_t per_block = 2048;
-  int64_t c0 = (int64_t)blockIdx.y * per_block;
+  for (int k = threadIdx.x; k < Tin; k += blockDim.x) {
+    const T ak = a[k];
+    T* gk = g + woff + (int64_t)i0 * Tin + k;
 #pragma unroll 4
-  for (int it = 0; it < per_block / 256; ++it) {
-    int64_t c = c0 + threadIdx.x + it * 256;
-    if (c < nW) {
-      int i = (int)(c / Tin);
-      int k = (int)(c - (int64_t)i * Tin);
-      g[woff + c] = d[i] * a[k];
-    } else if (c < nW + Tout) {
-      g[boff + (c - nW)] = d[c - nW];
-    }
+    for (int i = i0; i < i1; ++i, gk += Tin) *gk = d[i] * ak;
   }
+  for (int i = i0 + (int)threadIdx.x; i < i1; i += blockDim.x) g[boff + i] = d[i];
 }
 
 template <typename T>
 hess_status write_grads(const Net& net, const Caches<T>& c, T* G, int64_t ldg, cudaStream_t s) {
   for (int w = 1; w <= net.L - 1; ++w) {
     const int Tin = net.T[w - 1], Tout = net.T[w];
-    int64_t cols = (int64_t)Tin * Tout + Tout;
-    int64_t gy = cdiv(cols, 2048);
+    const int64_t gy = cdiv(Tout, kGradRows);
+    if (gy > 65535) return set_error(HESS_ERR_INVALID_ARG, "layer of %d units too wide for the gradient writer", Tout);
+    const int threads = Tin >= 256 ? 256 : (Tin >= 128 ? 128 : (Tin >= 64 ? 64 : 32));
     int64_t n0 = 0;
     while (n0 < c.N) {
       int64_t nb = c.N - n0 < 2147483647 ? c.N - n0 : 2147483647;
-      write_grads_kernel<T><<<dim3((unsigned)nb, (unsigned)gy), 256, 0, s>>>(
+      write_grads_kernel<T><<<dim3((unsigned)nb, (unsigned)gy), threads, 0, s>>>(
           c.d[w] + n0 * Tout, c.a[w - 1] + n0 * Tin, Tin, Tout, G + n0 * ldg, ldg, net.woff[w - 1],
           net.boff[w - 1]);
       HM_LAUNCHED();
