@@ -118,6 +118,16 @@ def run_cpu_baseline(sample_cols: int) -> dict:
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def workload_desc(name):
+    """The workload string of the bench line (shared by both arms)."""
+    from synth import named_config
+    pb = named_config(name)
+    calls, k = WORKLOADS[name]
+    what = " + ".join({"opg": "OPG", "hessian": "exact Hessian", "eig": f"top-{k} OPG eig"}[c] for c in calls)
+    return (f"{name}: MLP {pb.widths} {'/'.join(pb.acts)}, P={pb.P}, N={pb.N}; {what} per step",
+            pb.P, pb.N, k)
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -136,7 +146,9 @@ def reference_arm(args):
         "ms_per_step": 1e3 * statistics.mean(secs) if secs else None,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD} tanh N=1024 (bounded sample per step)"},
+        "config": dict(zip(("workload", "P", "N", "k"), workload_desc(WORKLOAD)),
+                       step="FP64 oracle on the host cores, a bounded sample of the step's "
+                            "Hessian and OPG columns per step"),
         "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle",
                          "cores": res[0].get("cores") if res else None,
                          "sample": res[0].get("sample") if res else None},
@@ -1122,7 +1134,7 @@ def main():
                        "precision": args.precision, "P": P, "N": N, "k": K_EIG_W,
                        "l2": "flushed between steps (256 MiB write outside the timed events)",
                        "parallelism": f"replicas x{world}",
-                       "step": ("one hess_curvature call (two internal streams)" if fused else
+                       "step": ("one hess_curvature call (two compute and two copy streams)" if fused else
                                 ("single calls on two handles and streams" if two else
                                  "single calls in turn")),
                        **({"only": args.only} if args.only else {})},
