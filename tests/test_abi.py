@@ -106,3 +106,15 @@ def test_autotune_table_load_and_save_on_cpu(lib, tmp_path):
     bad.write_text("0 100 4 1 200\nnot a line\n")  # 200 is not a multiple of 16
     assert lib.hess_autotune_load(str(bad).encode()) == _lib.HESS_ERR_INVALID_ARG
     assert lib.hess_autotune_load(str(tmp_path / "missing.txt").encode()) == _lib.HESS_ERR_INVALID_ARG
+
+
+def test_package_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No CPU fallback: with the shared library absent, the handle classes
+    raise instead of computing anything."""
+    from paper_1905_05559_gb300 import _lib, api
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "libhessmlp.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        api.HessMLP([4, 5, 3], ["sigmoid"], np.zeros(43))
+    with pytest.raises(RuntimeError, match="missing"):
+        _lib.load()
