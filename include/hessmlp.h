@@ -173,8 +173,9 @@ HESS_API hess_status opg_topk_eig(hess_mlp* h, const void* X, const void* Y, int
 HESS_API hess_status opg_topk_eig_streaming(hess_mlp* h, const void* X, const void* Y, int64_t N, int k,
                                             hess_precision prec, int64_t chunk, double* evals, double* evecs);
 
-/* OPG, exact Hessian and top-k OPG eigenpairs of one data set in one call
- * (any of them may be left out: OPG or H NULL, k = 0).  The same results as
+/* OPG (Eq. hesseq2, hesseq3), exact Hessian (Eq. hesseq1) and top-k OPG
+ * eigenpairs (Sec. 5.4, Eq. J) of one data set in one call (any of them may
+ * be left out: OPG or H NULL, k = 0).  The same results as
  * opg(), exact_hessian() and opg_topk_eig() with the same arguments, but
  * scheduled across four streams for BF16/BF16X3: the tensor-core operands and
  * contractions on the handle's stream, the FP64 eigen step (Gram matrix,

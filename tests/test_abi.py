@@ -118,3 +118,21 @@ def test_package_fails_loudly_without_the_library(monkeypatch, tmp_path):
         api.HessMLP([4, 5, 3], ["sigmoid"], np.zeros(43))
     with pytest.raises(RuntimeError, match="missing"):
         _lib.load()
+
+
+def test_compute_entry_points_cite_the_paper():
+    """Every compute entry point of the header carries a doc comment that
+    cites the passage defining its operation."""
+    txt = open(HEADER).read()
+    compute = {"per_example_grads", "opg", "exact_hessian", "opg_topk_eig", "opg_topk_eig_streaming",
+               "hess_curvature", "hessian_vector_products", "hessian_topk_eig", "hessian_minibatches",
+               "hess_approx_form"}
+    prev_end, seen = 0, set()
+    for m in re.finditer(r"HESS_API\s+[\w\s\*]+?\b(\w+)\s*\(", txt):
+        comments = re.findall(r"/\*.*?\*/", txt[prev_end:m.start()], re.S)
+        if m.group(1) in compute:
+            assert comments, m.group(1)
+            assert re.search(r"Sec\. \d|Eq\. \w|Appendix", comments[-1]), m.group(1)
+            seen.add(m.group(1))
+        prev_end = txt.index(";", m.end()) + 1
+    assert seen == compute
