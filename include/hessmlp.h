@@ -72,7 +72,7 @@ typedef enum {
   HESS_ERR_NOT_CONVERGED = 5,  /* opg_topk_eig: iteration limit reached */
   HESS_ERR_TIMEOUT = 6,        /* a bounded device wait gave up */
   HESS_ERR_ADMISSION = 7,      /* request exceeds the memory budget */
-  HESS_ERR_UNSUPPORTED = 8     /* valid request this build cannot serve */
+  HESS_ERR_UNSUPPORTED = 8     /* valid request the library cannot serve (e.g. a precision the call lacks) */
 } hess_status;
 
 typedef enum { HESS_ACT_SIGMOID = 0, HESS_ACT_TANH = 1, HESS_ACT_RELU = 2 } hess_act;
