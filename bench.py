@@ -78,6 +78,8 @@ def parse():
                     help="tune the tensor-core tile widths during the warm-up steps")
     ap.add_argument("--batch-workspace-gb", type=float, default=64.0)
     ap.add_argument("--batch-out-gb", type=float, default=96.0)
+    ap.add_argument("--probe-fp64", action="store_true",
+                    help="measure the FP64 FMA issue rate of the GPU and exit")
     ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -805,27 +807,45 @@ def measured_peaks():
                 "sm_max_mhz": 2070.0}, "fallback"
 
 
-def profiled_traffic(cls, workload=WORKLOAD):
-    """Per-launch DRAM traffic from the committed ncu summary of this kernel
-    class on the MLP workload, if the kernel source has not changed since the
-    capture (None for other workloads)."""
-    import hashlib
-    if workload != WORKLOAD:
-        return None
-    name = {"syrk": "umma_gemm_opg_mlp_784_16_10.md",
-            "hcontract": "umma_gemm_hessian_mlp_784_16_10.md"}.get(cls)
-    if not name:
-        return None
-    try:
-        txt = open(os.path.join(ROOT, "profiles", name)).read()
-        src = open(os.path.join(ROOT, "paper_1905_05559_gb300", "csrc", "tc.cu"), "rb").read()
-    except OSError:
-        return None
-    vals = dict(line.strip().split(": ", 1) for line in txt.splitlines()
-                if line.strip().startswith(("traffic_bytes_per_launch", "kernel_source_sha256_16")))
-    if vals.get("kernel_source_sha256_16") != hashlib.sha256(src).hexdigest()[:16]:
-        return None
-    return float(vals["traffic_bytes_per_launch"])
+def fp64_probe(lib, torch, iters=10000):
+    """The FP64 issue rate of this GPU, measured now: hess_probe_fp64 runs
+    eight independent FMA chains per thread over 4 x 256 threads per SM; its
+    flops over its CUDA-event duration (one warm-up launch first)."""
+    import ctypes
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    fl = ctypes.c_double()
+    lib.hess_probe_fp64(200, ctypes.byref(fl), ctypes.c_void_p(sink.data_ptr()), ctypes.c_void_p(st.cuda_stream))
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    lib.hess_probe_fp64(iters, ctypes.byref(fl), ctypes.c_void_p(sink.data_ptr()), ctypes.c_void_p(st.cuda_stream))
+    b.record(st)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    return {"tflops": fl.value / (ms * 1e-3) / 1e12, "ms": ms, "flops": fl.value}
+
+
+def probe_main(args):
+    """--probe-fp64: the FP64 issue rate with the SM clock sampled during a
+    longer run of the same probe kernel."""
+    import torch
+    from paper_1905_05559_gb300 import build
+    build.build()
+    import paper_1905_05559_gb300 as hm
+    lib = hm.load()
+    fp64_probe(lib, torch, 1000)
+    sampler = ClockSampler(gpu_index(0))
+    sampler.start()
+    runs = [fp64_probe(lib, torch, 50000) for _ in range(5)]
+    clocks = sampler.stop()
+    best = max(r["tflops"] for r in runs)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    out = {"probe": "fp64_probe_kernel", "tflops_best": best, "tflops_runs": [r["tflops"] for r in runs],
+           "ms_per_run": [r["ms"] for r in runs], "sms": sms, "clocks": clocks}
+    if clocks and clocks.get("sm_mhz"):
+        out["fp64_fma_per_clk_per_sm"] = best * 1e12 / 2.0 / (clocks["sm_mhz"] * 1e6) / sms
+    print(json.dumps(out), flush=True)
 
 
 def main():
@@ -835,6 +855,9 @@ def main():
         return
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.probe_fp64:
+        probe_main(args)
         return
     if args.serve:
         serve_bench(args)
@@ -995,7 +1018,7 @@ def main():
     if not args.no_fp64 and args.precision != "fp64":
         ms64, _, _, kern64, _ = timed("fp64", args.fp64_steps, 1)
         fp64 = {"value": job_throughput(entries, ms64 * 1e-3, world), "ms_per_step": ms64,
-                "kernels_ms": {k: v["ms"] for k, v in kern64.items()}}
+                "kernels_ms_per_step": {k: v["ms"] / max(args.fp64_steps, 1) for k, v in kern64.items()}}
 
     # end to end through the C ABI with host buffers: the library stages the
     # pinned host inputs to the device and the outputs back every step
@@ -1076,49 +1099,70 @@ def main():
 
     peaks, peak_src = measured_peaks()
     smx = peaks.get("sm_max_mhz", 2070.0) * 1e6
-    fp64_peak = 1.25  # TFLOP/s: GB300 FP64 rate from the platform table (2 DFMA/clk/SM)
+    fp64_nominal = 1.25  # TFLOP/s: the platform's nominal FP64 rate
     fp32_peak = 152 * 128 * 2 * smx / 1e12
+    probe = fp64_probe(lib, torch) if rank == 0 else None
+    bf16_peak = peaks["bf16_tflops_sustained"]
+    mult = 3.0 if args.precision == "bf16x3" else 1.0
+    # kernel-level classes (one kernel, or one kernel's launches) and what
+    # each one is; the composite classes (eig: the whole eigen step; gram,
+    # backproj: several small kernels) are reported by time only
+    kernel_of = {
+        "syrk": "umma_gemm_kernel (OPG contraction)",
+        "hcontract": "umma_gemm_kernel (Hessian contraction)",
+        "digits": "umma_gemm_kernel (exact-digit FP64 products of the Gram matrix and back-projection)",
+        "lanczos": "lanczos kernel on the Gram matrix (cooperative launch)",
+        "grads": "write_grads_kernel",
+        "tridiag": "bisect_cluster_kernel + inviter_kernel",
+    }
 
     def class_roofline(cls):
         k = kern[cls]
-        if k["ms"] <= 0 or (k["flops"] <= 0 and k["bytes"] <= 0):
+        if cls not in kernel_of or k["ms"] <= 0:
             return None
         sec = k["ms"] * 1e-3
         if cls in ("syrk", "hcontract") and args.precision in ("bf16", "bf16x3"):
-            mult = 3.0 if args.precision == "bf16x3" else 1.0
-            r = {"bound": "tensor", "achieved": mult * k["flops"] / sec / 1e12,
-                 "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
-                 "peak_source": f"{peak_src} bf16 sustained",
-                 "traffic": profiled_traffic(cls, args.workload)}
-        elif k["flops"] > 0:
-            fp64 = cls == "eig" or args.precision == "fp64"
-            r = {"bound": "alu", "achieved": k["flops"] / sec / 1e12,
-                 "peak": fp64_peak if fp64 else fp32_peak, "unit": "TFLOP/s",
-                 "peak_source": ("FP64 1.25 TFLOP/s (152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz)"
-                                 if fp64 else "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"),
-                 "traffic": None}
-            if cls == "eig":
-                r["note"] = ("algorithmic FP64 flops of the Gram matrix, Lanczos and back-projection "
-                             "over the class time; the Gram matrix's wide layer and the "
-                             "back-projection run as exact-digit FP64 products on the BF16 tensor "
-                             "cores, so the rate can exceed the SIMT FP64 rate")
-        else:
+            r = {"bound": "tensor", "achieved": mult * k["flops"] / sec / 1e12, "peak": bf16_peak,
+                 "unit": "TFLOP/s", "peak_source": f"{peak_src} bf16 sustained",
+                 "work": f"{mult:g} BF16 products x N P (P+1) (OPG) or the Hessian's contraction flops"}
+        elif cls == "digits":
+            r = {"bound": "tensor", "achieved": k["flops"] / sec / 1e12, "peak": bf16_peak,
+                 "unit": "TFLOP/s", "peak_source": f"{peak_src} bf16 sustained",
+                 "work": "BF16 digit-product flops of the exact-digit FP64 products"}
+        elif cls == "lanczos":
+            r = {"bound": "alu", "achieved": k["flops"] / sec / 1e12, "peak": fp64_nominal,
+                 "unit": "TFLOP/s", "peak_source": "FP64 nominal 1.25 TFLOP/s (probe measured "
+                 + (f"{probe['tflops']:.3f}" if probe else "n/a") + " TFLOP/s in this run)",
+                 "work": "sum over Lanczos steps j of 2 N^2 + 8 N (j + 1) FP64 flops"}
+        elif cls == "grads":
             r = {"bound": "hbm", "achieved": k["bytes"] / sec / 1e9, "peak": peaks["hbm_gbs"],
-                 "unit": "GB/s", "peak_source": f"{peak_src} copy bandwidth", "traffic": None}
-        r["frac"] = r["achieved"] / r["peak"] if r.get("peak") else None
+                 "unit": "GB/s", "peak_source": f"{peak_src} copy bandwidth",
+                 "work": "N P x 4 bytes of gradient rows written"}
+        elif k["flops"] > 0:
+            fp64 = args.precision == "fp64"
+            r = {"bound": "alu", "achieved": k["flops"] / sec / 1e12,
+                 "peak": fp64_nominal if fp64 else fp32_peak, "unit": "TFLOP/s",
+                 "peak_source": "FP64 nominal 1.25 TFLOP/s" if fp64 else
+                 "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+        else:
+            r = {"bound": "latency", "achieved": None, "peak": None, "unit": None,
+                 "work": "dependent recurrences on small tridiagonal matrices; no throughput bound"}
+        r["traffic"] = None  # DRAM bytes: the ncu summaries under profiles/
+        r["frac"] = r["achieved"] / r["peak"] if r.get("peak") and r.get("achieved") else None
         r["kernel_class"] = cls
+        r["kernel"] = kernel_of[cls]
         r["launches_per_step"] = k["launches"] / max(args.steps, 1)
         r["ms_per_step"] = k["ms"] / max(args.steps, 1)
+        r["step_share"] = r["ms_per_step"] / ms_step
         return r
 
-    total_ms = max(sum(v["ms"] for v in kern.values()), 1e-9)
     rooflines = {c: class_roofline(c) for c in kern}
     rooflines = {c: r for c, r in rooflines.items() if r}
-    # the dominant kernel class of the step (largest device time with known work)
-    dom = max(rooflines, key=lambda c: kern[c]["ms"]) if rooflines else None
+    # the dominant kernel of the step: largest device time among the
+    # kernel-level classes with a throughput bound
+    cands = [c for c, r in rooflines.items() if r.get("frac") is not None]
+    dom = max(cands, key=lambda c: kern[c]["ms"]) if cands else None
     roof = dict(rooflines[dom]) if dom else None
-    if roof:
-        roof["step_share"] = kern[dom]["ms"] / total_ms
 
     if rank == 0:
         line = {
@@ -1147,6 +1191,7 @@ def main():
             "gpu_launches": launches,
             "clocks": clocks,
             "fp64_plain": fp64,
+            "fp64_probe": probe,
             "kernels_ms_per_step": {k: v["ms"] / max(args.steps, 1) for k, v in kern.items()},
             "wall_s": wall,
         }

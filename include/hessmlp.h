@@ -20,9 +20,12 @@
  *            i*T_{l-1} + j) followed by b^(l) (Sec. 2, Eq. flatten, read as a
  *            row-wise flatten of each matrix).  Every row and column index of
  *            G, OPG, H and of the eigenvectors follows this order.
- * Inputs:    X is N x T_1 row-major, Y is N x T_L row-major one-hot labels
- *            (rows may be any probability vector; the library uses
- *            dC_n/dz^(L) = p_n - y_n, exact when each row sums to one).
+ * Inputs:    X is N x T_1 row-major, Y is N x T_L row-major one-hot labels.
+ *            Rows may be any non-negative label vector: the library computes
+ *            dC_n/dz^(L) = p_n (sum_m y_nm) - y_n and scales the softmax
+ *            curvature diag(p_n) - p_n p_n^T by sum_m y_nm, which is the
+ *            exact derivative of C_n = (sum_m y_nm) logsumexp(z^(L)) - y_n . z^(L)
+ *            (Eq. cost) and equals p_n - y_n for one-hot rows.
  * Precision: HESS_FP64 -- X, Y and outputs are double; all arithmetic FP64.
  *            HESS_FP32 -- X, Y and outputs are float; arithmetic FP32 (the
  *                         softmax log-sum-exp in FP64).
@@ -268,15 +271,22 @@ HESS_API hess_status hess_param_permutation(int L, const int* widths, int64_t* p
  * implicit synchronisation and possible failure, is not acceptable.  Computes
  * the same G as per_example_grads in FP64 (N x P row-major, one row per
  * example) without a handle and without allocating: desc describes the
- * network (validated as in hess_mlp_create); omega (P doubles), X (N x T_1),
- * Y (N x T_L) and G (N x P) must all be device memory on the current device.
+ * network (validated as in hess_mlp_create); omega (at least P doubles), X
+ * (at least N x T_1), Y (at least N x T_L) and G (at least N x P) must all be
+ * device memory on the current device.  The call checks each pointer's
+ * device and that its allocation extends far enough past it; a buffer carved
+ * out of a larger allocation (a caching allocator's segment) cannot be
+ * checked more closely than that, so its size is the caller's promise.
  * The forward/backward caches live in a file-scope device array of 32 MiB
  * that every GPU loading the library holds until the process exits; a request
  * whose caches exceed it, N * (4 (T_2 + ... + T_{L-1}) + (T_2 + ... + T_L) +
  * T_L + max_l T_l + 1) doubles plus alignment, is rejected with
- * HESS_ERR_INVALID_ARG before any GPU work.  The first call on a device looks
- * up that array's device address (cudaGetSymbolAddress) with the device
- * current; make that first call before any stream capture.  Work is queued on
+ * HESS_ERR_INVALID_ARG before any GPU work.  The array's device address
+ * belongs to a CUDA context: the first call under each context (the device's
+ * primary context, a new one after cudaDeviceReset, or a caller's own
+ * driver-API context) looks it up with cudaGetSymbolAddress while that
+ * context is current and caches it under the context's handle; make that
+ * first call before any stream capture.  Work is queued on
  * `stream` (a cudaStream_t, NULL = legacy default stream) and the call returns
  * without waiting.  All calls share the array: calls whose work overlaps on
  * the GPU (on different streams or from different threads) race on it. */
@@ -426,7 +436,21 @@ typedef enum {
   HESS_K_HLANCZOS = 7,  /* Lanczos steps on the Hessian operator (products,
                            reorthogonalisation) and its Ritz vectors */
   HESS_K_APPROX = 8,    /* low-/full-rank approximations: forming, applying */
-  HESS_K_COUNT = 9
+  /* parts of the OPG eigen step (HESS_K_EIG brackets the whole step; these
+   * bracket pieces of it): */
+  HESS_K_GRAM = 9,      /* Gram matrix: SIMT FP64 products, digit splitting
+                           and FP64 combines of the exact-digit products,
+                           Hadamard updates; flops = FP64 work of the Gram
+                           matrix */
+  HESS_K_DIGITS = 10,   /* the exact-digit products' tensor-core launches
+                           (Gram term and back-projection); flops = BF16
+                           digit-product flops */
+  HESS_K_LANCZOS = 11,  /* the Lanczos launches on the Gram matrix; flops =
+                           sum over steps j of 2 N^2 + 8 N (j + 1) */
+  HESS_K_TRIDIAG = 12,  /* eigenpairs of the tridiagonal T_m */
+  HESS_K_BACKPROJ = 13, /* Ritz vectors, gradient rows and back-projection;
+                           flops = 2 N m k + 2 P N k */
+  HESS_K_COUNT = 14
 } hess_kernel_class;
 
 typedef struct {
@@ -438,6 +462,35 @@ typedef struct {
 
 HESS_API hess_status hess_timing_enable(hess_mlp* h, int enable);
 HESS_API hess_status hess_timing_read(hess_mlp* h, int kernel_class, hess_kernel_stats* out);
+
+/* Test hooks (no counterpart in the paper).
+ *
+ * hess_check_devmath: for n device doubles x, writes four rows of n device
+ * doubles to out (4 n entries, row-major): the refined FP64 reciprocal the
+ * eigensolvers use (hardware estimate plus two Newton-Raphson steps), CUDA's
+ * correctly rounded 1.0 / x, the refined reciprocal square root, and
+ * 1.0 / sqrt(x) (the last two 0 where x <= 0).  The refined forms are meant
+ * for |x| in [2^-1022, 2^1022]: the estimate flushes subnormal inputs and
+ * results to zero, so outside that range they return 0 or infinity.  Queued
+ * on `stream`; returns without waiting.  Errors: INVALID_ARG.
+ *
+ * hess_debug_set_barrier_limit: the number of SM clock cycles a block of the
+ * OPG eigen step's cooperative Lanczos kernel waits at a grid barrier before
+ * it gives up (the kernel then stops and the call returns HESS_ERR_TIMEOUT);
+ * cycles <= 0 restores the default of 4e9 cycles (about 2 s).  Process-wide;
+ * affects launches queued after it returns.  Meant for tests that make the
+ * wait run out.  Errors: none.
+ *
+ * hess_probe_fp64: a measurement kernel of the current device, 4 blocks of
+ * 256 threads per SM, each thread running eight independent chains of iters
+ * FP64 fused multiply-adds; *flops receives the launch's flop count (2 per
+ * FMA), so that flops over the launch's duration (timed by the caller with
+ * events on `stream`) is the device's FP64 issue rate.  sink: device memory
+ * for one double, never written in practice.  Queued on `stream`; returns
+ * without waiting.  Errors: INVALID_ARG, CUDA. */
+HESS_API hess_status hess_check_devmath(const double* x, int64_t n, double* out, void* stream);
+HESS_API hess_status hess_debug_set_barrier_limit(int64_t cycles);
+HESS_API hess_status hess_probe_fp64(int64_t iters, double* flops, double* sink, void* stream);
 
 /* Number of kernels this library has launched in the process so far. */
 HESS_API int64_t hess_launch_count(void);

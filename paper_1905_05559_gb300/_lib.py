@@ -38,6 +38,7 @@ EXPORTS = (
     "hess_autotune", "hess_autotune_entries", "hess_autotune_save", "hess_autotune_load",
     "hess_batch_set_graphs", "hess_curvature", "hessian_vector_products", "hessian_topk_eig",
     "hess_approx_form", "hess_approx_apply", "hessian_minibatches", "opg_topk_eig_streaming",
+    "hess_check_devmath", "hess_debug_set_barrier_limit", "hess_probe_fp64",
 )
 
 REQUEST_KIND = {"hessian": 0, "opg": 1, "eig": 2}
@@ -61,7 +62,8 @@ class BatchInfo(ctypes.Structure):
 
 
 KERNEL_CLASS = {"syrk": 0, "hcontract": 1, "grads": 2, "rop": 3, "eig": 4, "hrest": 5, "hvp": 6,
-                "hlanczos": 7, "approx": 8}
+                "hlanczos": 7, "approx": 8, "gram": 9, "digits": 10, "lanczos": 11, "tridiag": 12,
+                "backproj": 13}
 
 
 class KernelStats(ctypes.Structure):
@@ -165,6 +167,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.hess_autotune_save.restype = st
     lib.hess_autotune_load.argtypes = [ctypes.c_char_p]
     lib.hess_autotune_load.restype = st
+    lib.hess_check_devmath.argtypes = [vp, i64, vp, vp]
+    lib.hess_check_devmath.restype = st
+    lib.hess_debug_set_barrier_limit.argtypes = [i64]
+    lib.hess_debug_set_barrier_limit.restype = st
+    lib.hess_probe_fp64.argtypes = [i64, ctypes.POINTER(ctypes.c_double), vp, vp]
+    lib.hess_probe_fp64.restype = st
     lib.hess_launch_count.argtypes = []
     lib.hess_launch_count.restype = ctypes.c_int64
     lib.hess_last_error.argtypes = []

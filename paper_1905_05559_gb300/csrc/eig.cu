@@ -11,6 +11,7 @@
 //   4. Ritz vectors U = Q_m Y, back-projection q = G^T u / sqrt(N mu)
 #include <cooperative_groups.h>
 
+#include <atomic>
 #include <cfloat>
 #include <mutex>
 
@@ -71,9 +72,12 @@ struct LzArgs {
   int* stop;      // set to j when step j meets a breakdown (the kernel returns)
   int resumed;    // m0 follows a restart: beta_{m0-1} = 0 is already set
   uint64_t key;
+  long long bar_limit;  // clock cycles a grid-barrier wait may take
 };
 
 constexpr long long BAR_TIMEOUT = 4000000000ll;
+// test hook: a shorter grid-barrier limit (0 = BAR_TIMEOUT)
+std::atomic<long long> g_bar_limit{0};
 
 __device__ __forceinline__ unsigned atom_add_release_gpu(unsigned* p, unsigned v) {
   unsigned old;
@@ -103,7 +107,7 @@ __device__ bool grid_barrier(const LzArgs& a, unsigned& epoch) {
     const unsigned old = atom_add_release_gpu(a.bar, add);
     const long long t0 = clock64();
     while (((old ^ ld_acquire_gpu(a.bar)) & 0x80000000u) == 0u) {
-      if (clock64() - t0 > BAR_TIMEOUT || *(volatile int*)a.err) {
+      if (clock64() - t0 > a.bar_limit || *(volatile int*)a.err) {
         atomicExch(a.err, 1);
         ok = 0;
         break;
@@ -1143,15 +1147,27 @@ hess_status run_lz(hess_mlp* h, const double* M, int k, LzBufs& b, int* m_out, b
     la.stop = stop;
     la.resumed = resumed;
     la.key = key + 7;
+    {
+      const long long lim = g_bar_limit.load();
+      la.bar_limit = lim > 0 ? lim : BAR_TIMEOUT;
+    }
     void* kargs[] = {&la};
     HM_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
     HM_CUDA(cudaMemsetAsync(stop, 0xff, sizeof(int), s));
-    HM_CUDA(cudaLaunchCooperativeKernel((void*)lanczos_coop_kernel, grid, 512, kargs, dyn, s));
-    HM_LAUNCHED();
+    {
+      double fl = 0.0;
+      for (int64_t j = m; j < target; ++j) fl += 2.0 * N * N + 8.0 * N * (j + 1);
+      Tick t(h, HESS_K_LANCZOS, fl, 0.0);
+      HM_CUDA(cudaLaunchCooperativeKernel((void*)lanczos_coop_kernel, grid, 512, kargs, dyn, s));
+      HM_LAUNCHED();
+    }
     m = (int)target;
-    last_beta_kernel<<<1, 32, 0, s>>>(npart, grid, h2);
-    HM_LAUNCHED();
-    HM_TRY(tridiag_topk(alpha, beta, m, k, theta, cstart, Y, mcap, h2, rr, mx, key + 11, tri_scratch, s));
+    {
+      Tick t(h, HESS_K_TRIDIAG, 0.0, 0.0);
+      last_beta_kernel<<<1, 32, 0, s>>>(npart, grid, h2);
+      HM_LAUNCHED();
+      HM_TRY(tridiag_topk(alpha, beta, m, k, theta, cstart, Y, mcap, h2, rr, mx, key + 11, tri_scratch, s));
+    }
     HM_CUDA(cudaMemcpyAsync(hp, mx, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaMemcpyAsync(reinterpret_cast<int*>(hp + 2), err, sizeof(int), cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaMemcpyAsync(reinterpret_cast<int*>(hp + 2) + 1, stop, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1227,9 +1243,13 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   cudaStream_t s = h->stream;
 
   // 1. Gram matrix, factored by layer
-  HM_TRY(fill(M, N * N, 0.0, s));
+  {
+    Tick t(h, HESS_K_GRAM, 0.0, 0.0);
+    HM_TRY(fill(M, N * N, 0.0, s));
+  }
   for (int wl = 1; wl <= L - 1; ++wl) {
     const int Tin = net.T[wl - 1], Tout = net.T[wl];
+    Tick tg(h, HESS_K_GRAM, (double)N * (N + 1) * Tout, 0.0);
     Gemm<double> g;
     g.M = (int)N;
     g.N = (int)N;
@@ -1246,8 +1266,10 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
     g.upper = 1;
     HM_TRY(gemm(g, s));
     if (ktc && Tin >= 128 && Tin <= ktc) {
+      tg.stop();
       HM_TRY(f64_syrk_tc(h, c.a[wl - 1], Tin, Tin, AA, N, fs, s));
     } else {
+      tg.set_work((double)N * (N + 1) * (Tout + Tin), 0.0);
       g.K = Tin;
       g.A = c.a[wl - 1];
       g.sam = Tin;
@@ -1255,12 +1277,17 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
       g.sbn = Tin;
       g.C = AA;
       HM_TRY(gemm(g, s));
+      tg.stop();
     }
+    Tick ta(h, HESS_K_GRAM, 0.0, 0.0);
     gram_acc_kernel<<<(unsigned)(cdiv(N * N, 256) < 65536 ? cdiv(N * N, 256) : 65536), 256, 0, s>>>(
         M, DD, AA, N * N, 1.0 / (double)N);
     HM_LAUNCHED();
   }
-  HM_TRY(mirror_upper(M, N, N, s));
+  {
+    Tick t(h, HESS_K_GRAM, 0.0, 0.0);
+    HM_TRY(mirror_upper(M, N, N, s));
+  }
 
   int m = 0;
   bool converged = false;
@@ -1277,6 +1304,7 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
 
   // 4. Ritz vectors U = Q_m^T Y (N x k), back-projection through G
   {
+    Tick t(h, HESS_K_BACKPROJ, 2.0 * N * m * k, 0.0);
     Gemm<double> g;
     g.M = (int)N;
     g.N = k;
@@ -1292,10 +1320,14 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
     g.scn = 1;
     HM_TRY(gemm(g, s));
   }
-  HM_TRY(write_grads(net, c, G, P, s));
+  {
+    Tick t(h, HESS_K_BACKPROJ, 0.0, (double)N * P * sizeof(double));
+    HM_TRY(write_grads(net, c, G, P, s));
+  }
   if (bp_tc) {
     HM_TRY(f64_gemm_nt_tc(h, G, P, U, 1, k, N, evecs_d, 1, P, fb, s));
   } else {
+    Tick t(h, HESS_K_BACKPROJ, 2.0 * P * N * k, 0.0);
     Gemm<double> g;
     g.M = (int)P;
     g.N = k;
@@ -1311,9 +1343,12 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
     g.scn = P;
     HM_TRY(gemm(g, s));
   }
-  HM_CUDA(cudaMemsetAsync(flag + 1, 0, sizeof(int), s));
-  finalize_kernel<<<k, 1024, 0, s>>>(evecs_d, P, theta, k, (double)N, evals_d, flag + 1);
-  HM_LAUNCHED();
+  {
+    Tick t(h, HESS_K_BACKPROJ, 0.0, 0.0);
+    HM_CUDA(cudaMemsetAsync(flag + 1, 0, sizeof(int), s));
+    finalize_kernel<<<k, 1024, 0, s>>>(evecs_d, P, theta, k, (double)N, evals_d, flag + 1);
+    HM_LAUNCHED();
+  }
   int* hi = reinterpret_cast<int*>(hp);
   HM_CUDA(cudaMemcpyAsync(hi, flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
   HM_CUDA(cudaStreamSynchronize(s));
@@ -1365,3 +1400,8 @@ hess_status topk_eig_dense(hess_mlp* h, const double* M, int64_t n, int k, doubl
 }
 
 }  // namespace hm
+
+extern "C" hess_status hess_debug_set_barrier_limit(int64_t cycles) {
+  hm::g_bar_limit.store(cycles > 0 ? (long long)cycles : 0);
+  return HESS_OK;
+}

@@ -1886,8 +1886,12 @@ hess_status f64_syrk_tc(hess_mlp* h, const double* A, int64_t lda, int64_t K, do
   using namespace tc;
   const int64_t n = fs.n, ldk = fs.ldk, L = (int64_t)kDigits * ldk;
   if (K > ldk) return set_error(HESS_ERR_INVALID_ARG, "exact-digit product: K %lld beyond its plan", (long long)K);
-  digits_rows_kernel<<<(unsigned)cdiv(n, 8), 256, 0, s>>>(A, lda, 1, n, K, ldk, fs.D, fs.R, nullptr, fs.ex);
-  HM_LAUNCHED();
+  {
+    // (the only caller is the Gram matrix of the OPG eigen step)
+    Tick t(h, HESS_K_GRAM, 0.0, 0.0);
+    digits_rows_kernel<<<(unsigned)cdiv(n, 8), 256, 0, s>>>(A, lda, 1, n, K, ldk, fs.D, fs.R, nullptr, fs.ex);
+    HM_LAUNCHED();
+  }
   const std::vector<Contraction> cs = contractions(ldk);
   const int BN = 256;
   bool first = true;
@@ -1920,11 +1924,19 @@ hess_status f64_syrk_tc(hess_mlp* h, const double* A, int64_t lda, int64_t K, do
       jobs.push_back(job);
       jw.w[j - j0] = ldexp(1.0, -12 - 7 * c.w);
     }
-    HM_TRY(launch_jobs(h->sm_count, jobs.data(), (int)jobs.size(), tiles.data(), (int)tiles.size(), fs.jobs,
-                       fs.tiles, false, h->err_dev, h->stage, s));
-    combine_upper_kernel<<<dim3((unsigned)cdiv(n, 256), (unsigned)n), 256, 0, s>>>(fs.T, n, jw, fs.ex, C, ldc,
-                                                                                   first ? 0 : 1);
-    HM_LAUNCHED();
+    {
+      double fl = 0.0;
+      for (size_t j = j0; j < j1; ++j) fl += (double)n * (n + 1) * (double)(cs[j].d1 - cs[j].d0) * ldk;
+      Tick t(h, HESS_K_DIGITS, fl, 0.0);
+      HM_TRY(launch_jobs(h->sm_count, jobs.data(), (int)jobs.size(), tiles.data(), (int)tiles.size(), fs.jobs,
+                         fs.tiles, false, h->err_dev, h->stage, s));
+    }
+    {
+      Tick t(h, HESS_K_GRAM, 0.0, 0.0);
+      combine_upper_kernel<<<dim3((unsigned)cdiv(n, 256), (unsigned)n), 256, 0, s>>>(fs.T, n, jw, fs.ex, C, ldc,
+                                                                                     first ? 0 : 1);
+      HM_LAUNCHED();
+    }
     first = false;
   }
   return HESS_OK;
@@ -1996,6 +2008,8 @@ hess_status f64_gemm_nt_tc(hess_mlp* h, const double* G, int64_t ldg, const doub
   using namespace tc;
   const int64_t M = fs.M, Nn = fs.Nn, ldk = fs.ldk, L = (int64_t)kDigits * ldk;
   if (K > ldk) return set_error(HESS_ERR_INVALID_ARG, "exact-digit product: K %lld beyond its plan", (long long)K);
+  // (the only caller is the back-projection of the OPG eigen step)
+  Tick tp(h, HESS_K_BACKPROJ, 0.0, 0.0);
   // A = G^T: rows are the columns of G; B: plane-major digits, rows (e, c)
   colmax_exp_kernel<<<(unsigned)cdiv(M, 32), dim3(32, 8), 0, s>>>(G, ldg, K, M, fs.exA);
   HM_LAUNCHED();
@@ -2004,6 +2018,7 @@ hess_status f64_gemm_nt_tc(hess_mlp* h, const double* G, int64_t ldg, const doub
   HM_LAUNCHED();
   digits_rows_kernel<<<(unsigned)cdiv(Nn, 8), 256, 0, s>>>(B, b_rs, b_ks, Nn, K, ldk, nullptr, nullptr, fs.RB, fs.exB);
   HM_LAUNCHED();
+  tp.stop();
   const std::vector<DigitJob> js = digit_jobs(Nn);
   const int64_t nseg = k_segments(ldk);
   if ((int64_t)js.size() * nseg > kMaxDigitJobs)
@@ -2045,8 +2060,14 @@ hess_status f64_gemm_nt_tc(hess_mlp* h, const double* G, int64_t ldg, const doub
       off += M * cols;
     }
   }
-  HM_TRY(launch_jobs(h->sm_count, jobs.data(), (int)jobs.size(), tiles.data(), (int)tiles.size(), fs.jobs, fs.tiles,
-                     false, h->err_dev, h->stage, s));
+  {
+    double fl = 0.0;
+    for (const Job& jb : jobs) fl += 2.0 * (double)jb.M * jb.Nn * (double)jb.nkb * BK;
+    Tick t(h, HESS_K_DIGITS, fl, 0.0);
+    HM_TRY(launch_jobs(h->sm_count, jobs.data(), (int)jobs.size(), tiles.data(), (int)tiles.size(), fs.jobs,
+                       fs.tiles, false, h->err_dev, h->stage, s));
+  }
+  Tick tc(h, HESS_K_BACKPROJ, 0.0, 0.0);
   combine_general_kernel<<<(unsigned)cdiv(M * Nn, 256), 256, 0, s>>>(fs.T, M, Nn, dj, fs.exA, fs.exB, C, scm, scn, 0);
   HM_LAUNCHED();
   return HESS_OK;

@@ -11,6 +11,7 @@ the residual of the OPG eigen-equation.
 import numpy as np
 import pytest
 
+from eigcheck import check_eig
 from oracle import mlp as O
 from synth import make_problem, named_config
 
@@ -81,26 +82,6 @@ def test_small_full_matrices(hm, case, prec, tol):
     assert relerr(H, O.hessian(om, widths, acts, X, Y)) <= tol
     assert np.array_equal(OPG, OPG.T)
     assert np.array_equal(H, H.T)
-
-
-def check_eig(evals, evecs, G_ref, k, val_tol, vec_tol):
-    mu, Q, deficient = O.opg_topk_eig_from_grads(G_ref, k)
-    top = mu[0]
-    assert np.all(np.abs(evals - mu) <= val_tol * top), (evals, mu)
-    N = G_ref.shape[0]
-    for c in range(k):
-        if not (mu[c] > 1e-13 * top):
-            assert np.all(evecs[c] == 0)
-            continue
-        gaps = [abs(mu[c] - mu[j]) for j in (c - 1, c + 1) if 0 <= j < len(mu)]
-        if not gaps or min(gaps) > 1e-6 * top:
-            assert abs(abs(evecs[c] @ Q[:, c]) - 1.0) <= vec_tol, c
-        q = evecs[c]
-        r = G_ref.T @ (G_ref @ q) / N - evals[c] * q
-        assert np.linalg.norm(r) <= 1e-8 * top, c
-        i = int(np.argmax(np.abs(q)))
-        assert q[i] > 0
-    return deficient
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
