@@ -78,6 +78,12 @@ def parse():
                     help="tune the tensor-core tile widths during the warm-up steps")
     ap.add_argument("--batch-workspace-gb", type=float, default=64.0)
     ap.add_argument("--batch-out-gb", type=float, default=96.0)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg of the default line")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the precision workload's OPG leg of the default line")
+    ap.add_argument("--serve-leg-seconds", type=float, default=3.0)
+    ap.add_argument("--eig-blocks", type=int, default=0,
+                    help="most blocks of the eigen step's Lanczos kernel (0: one per SM)")
     ap.add_argument("--probe-fp64", action="store_true",
                     help="measure the FP64 FMA issue rate of the GPU and exit")
     ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
@@ -221,33 +227,34 @@ def gpu_index(local_rank):
 
 
 # --------------------------------------------------------------- serving ----
-def serve_bench(args):
+def serve_leg(seconds, rate, slots, torch=None):
     """Poisson arrivals (seed 4) of exact-Hessian, OPG and top-32 eigenpair
     requests, uniform over the three kinds and over 16 networks of the
     batching distribution, through the continuous-batching request server
-    with a 100 GB workspace budget.  Latency = submit to completion."""
+    with a 100 GB workspace budget.  Latency = submit to completion (host
+    clock); each request's device interval comes from the server's events on
+    its slot stream, and the fraction of device-busy time during which two or
+    more requests were on the GPU shows the overlap."""
     import threading
 
     import numpy as np
-    import torch
+    if torch is None:
+        import torch
 
     import paper_1905_05559_gb300 as hm
-    from paper_1905_05559_gb300 import build
     from synth import SplitMix64Stream, make_problem, make_random_mlp
 
-    build.build()
-    torch.cuda.set_device(0)
     nets = []
     for i in range(16):
         widths, acts, N = make_random_mlp(4, i)
         pb = make_problem(widths, acts, N, 400 + i, "normal", "zero")
         nets.append((pb, torch.as_tensor(pb.X, dtype=torch.float32, device="cuda"),
                      torch.as_tensor(pb.Y, dtype=torch.float32, device="cuda")))
-    srv = hm.HessServer(slots=args.serve_slots, budget_bytes=100 * (1 << 30))
+    srv = hm.HessServer(slots=slots, budget_bytes=100 * (1 << 30))
     ids = [srv.add_network(pb.widths, pb.acts, pb.omega) for pb, _, _ in nets]
     rs = SplitMix64Stream(4, 1)
-    n_req = int(args.serve_rate * args.serve_seconds)
-    gaps = -np.log(1.0 - rs.uniform(n_req)) / args.serve_rate
+    n_req = int(rate * seconds)
+    gaps = -np.log(1.0 - rs.uniform(n_req)) / rate
     arrivals = np.cumsum(gaps)
     kinds = rs.integers(n_req, 0, 2)
     which = rs.integers(n_req, 0, len(nets) - 1)
@@ -263,6 +270,7 @@ def serve_bench(args):
                 srv.wait(srv.submit(kind, ids[i], X, Y, "bf16x3", out))
     torch.cuda.synchronize()
     lat = [None] * n_req
+    dev = [None] * n_req
     entries = [0.0] * n_req
     sem = threading.Semaphore(64)  # the client keeps at most 64 requests in flight
     lock = threading.Lock()
@@ -271,11 +279,12 @@ def serve_bench(args):
     failures = {}
 
     def waiter(j, ticket, t_submit, keep):
-        st = srv.wait(ticket)
+        st, g0, g1 = srv.wait_timed(ticket)
         t_done = time.perf_counter()
         msg = hm.last_error() if st not in (0, 4) else ""
         with lock:
             lat[j] = (t_done - t_submit, st)
+            dev[j] = (g0, g1)
             if msg:
                 failures.setdefault(f"{st}: {msg[:120]}", 0)
                 failures[f"{st}: {msg[:120]}"] += 1
@@ -311,20 +320,87 @@ def serve_bench(args):
     srv.close()
     ok = [l for l, st in lat if st in (0, 4)]
     ls = np.sort(np.asarray(ok)) * 1e3
+    # device concurrency: sweep over the requests' device intervals
+    ev = []
+    for d in dev:
+        if d and d[0] >= 0 and d[1] >= d[0]:
+            ev.append((d[0], 1))
+            ev.append((d[1], -1))
+    ev.sort()
+    busy = over = 0.0
+    act = 0
+    for (t, dlt), (t2, _) in zip(ev, ev[1:] + [(ev[-1][0] if ev else 0.0, 0)]):
+        act += dlt
+        if act >= 1:
+            busy += t2 - t
+        if act >= 2:
+            over += t2 - t
+    spans = sum(d[1] - d[0] for d in dev if d and d[0] >= 0 and d[1] >= d[0])
+    return {
+        "p50_ms": float(np.percentile(ls, 50)), "p99_ms": float(np.percentile(ls, 99)),
+        "entries_per_s": float(sum(entries) / wall), "submitted": n_req, "completed": len(ok),
+        "failures": failures, "wall_s": wall, "offered_rate": rate, "achieved_rate": n_req / wall,
+        "device_busy_s": busy * 1e-3, "overlap_frac": (over / busy) if busy > 0 else None,
+        "mean_concurrency": (spans / busy) if busy > 0 else None, "slots": slots, "seconds": seconds,
+        "workload": "Poisson request stream (seed 4): exact Hessian (split-BF16), OPG (split-BF16), "
+                    "top-32 OPG eig (FP64 Gram), 16 networks of the batching distribution, "
+                    "100 GB workspace budget",
+    }
+
+
+def serve_bench(args):
+    import torch
+    from paper_1905_05559_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    r = serve_leg(args.serve_seconds, args.serve_rate, args.serve_slots, torch)
     line = {
         "metric": "served p50/p99 latency (ms) and delivered entries/s", "impl": "ours",
-        "value": float(np.percentile(ls, 50)), "unit": "ms (p50)",
-        "p50_ms": float(np.percentile(ls, 50)), "p99_ms": float(np.percentile(ls, 99)),
-        "entries_per_s": float(sum(entries) / wall), "requests": n_req,
-        "completed": len(ok), "failures": failures, "wall_s": wall, "offered_rate": args.serve_rate,
-        "achieved_rate": n_req / wall, "higher_is_better": False, "n_gpus": 1,
-        "config": {"workload": "Poisson request stream (seed 4): exact Hessian (split-BF16), OPG "
-                               "(split-BF16), top-32 OPG eig (FP64 Gram), 16 networks of the "
-                               "batching distribution, 100 GB workspace budget",
-                   "slots": args.serve_slots, "seconds": args.serve_seconds},
+        "value": r["p50_ms"], "unit": "ms (p50)", "higher_is_better": False, "n_gpus": 1,
+        **{k: v for k, v in r.items() if k != "workload"},
+        "config": {"workload": r["workload"], "slots": args.serve_slots, "seconds": args.serve_seconds},
         "data": "synthetic",
     }
     print(json.dumps(line), flush=True)
+
+
+def precision_leg(hm, torch, peaks):
+    """The precision workload's OPG: MLP [1024, 64, 64, 10] ReLU, P = 70410,
+    N = 8192, split-BF16 and BF16 on the tensor cores (one warm call, then one
+    timed call each); the SYRK's flops over its own CUDA-event time."""
+    from synth import named_config
+    pb = named_config("mlp_1024_64_64_10")
+    P, N = pb.P, pb.N
+    net = hm.HessMLP(pb.widths, pb.acts, pb.omega)
+    X = torch.as_tensor(pb.X, dtype=torch.float32, device="cuda")
+    Y = torch.as_tensor(pb.Y, dtype=torch.float32, device="cuda")
+    OPG = torch.empty((P, P), dtype=torch.float32, device="cuda")
+    out = {"workload": f"mlp_1024_64_64_10: MLP {pb.widths} relu, P={P}, N={N}; one OPG call",
+           "P": P, "N": N}
+    st = torch.cuda.current_stream()
+    for prec, mult in (("bf16x3", 3.0), ("bf16", 1.0)):
+        net.opg(X, Y, prec, out=OPG)
+        torch.cuda.synchronize()
+        net.read_timing("syrk")
+        net.timing(True)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        net.opg(X, Y, prec, out=OPG)
+        b.record(st)
+        torch.cuda.synchronize()
+        net.timing(False)
+        k = net.read_timing("syrk")
+        call_ms = a.elapsed_time(b)
+        tf = mult * k["flops"] / (k["ms"] * 1e-3) / 1e12 if k["ms"] > 0 else None
+        out[prec] = {"call_ms": call_ms, "opg_entries_per_s": float(P) * P / (call_ms * 1e-3),
+                     "syrk_ms": k["ms"], "syrk_tflops": tf,
+                     "syrk_frac": tf / peaks["bf16_tflops_sustained"] if tf else None,
+                     "peak": peaks["bf16_tflops_sustained"], "peak_source": "measured bf16 sustained"}
+    del OPG
+    net.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def batch_bench(args):
@@ -910,6 +986,8 @@ def main():
     P, N = pb.P, pb.N
     stream = torch.cuda.current_stream()
     net = hm.HessMLP(pb.widths, pb.acts, pb.omega, stream=stream.cuda_stream)
+    if args.eig_blocks:
+        net.set_eig_blocks(args.eig_blocks)
     lib = hm.load()
     # two streams: OPG + H on one handle, the eigenpairs on another (each
     # handle owns its workspace); the FP64 Gram work overlaps the tensor-core
@@ -1130,10 +1208,12 @@ def main():
                  "unit": "TFLOP/s", "peak_source": f"{peak_src} bf16 sustained",
                  "work": "BF16 digit-product flops of the exact-digit FP64 products"}
         elif cls == "lanczos":
-            r = {"bound": "alu", "achieved": k["flops"] / sec / 1e12, "peak": fp64_nominal,
-                 "unit": "TFLOP/s", "peak_source": "FP64 nominal 1.25 TFLOP/s (probe measured "
-                 + (f"{probe['tflops']:.3f}" if probe else "n/a") + " TFLOP/s in this run)",
-                 "work": "sum over Lanczos steps j of 2 N^2 + 8 N (j + 1) FP64 flops"}
+            pk = probe["tflops"] if probe else fp64_nominal
+            r = {"bound": "alu", "achieved": k["flops"] / sec / 1e12, "peak": pk,
+                 "unit": "TFLOP/s",
+                 "peak_source": ("measured in this run: FP64 FMA issue rate of hess_probe_fp64"
+                                 if probe else "FP64 nominal 1.25 TFLOP/s") + " (nominal 1.25)",
+                 "work": "sum over Lanczos steps j of 2 N^2 + 8 N (j + 1) FP64-class flops"}
         elif cls == "grads":
             r = {"bound": "hbm", "achieved": k["bytes"] / sec / 1e9, "peak": peaks["hbm_gbs"],
                  "unit": "GB/s", "peak_source": f"{peak_src} copy bandwidth",
@@ -1164,6 +1244,13 @@ def main():
     dom = max(cands, key=lambda c: kern[c]["ms"]) if cands else None
     roof = dict(rooflines[dom]) if dom else None
 
+    serve = precision = None
+    if rank == 0 and world == 1 and args.workload == WORKLOAD:
+        if not args.no_precision:
+            precision = precision_leg(hm, torch, peaks)
+        if not args.no_serve:
+            serve = serve_leg(args.serve_leg_seconds, args.serve_rate, args.serve_slots, torch)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -1192,6 +1279,8 @@ def main():
             "clocks": clocks,
             "fp64_plain": fp64,
             "fp64_probe": probe,
+            "serve": serve,
+            "precision_opg": precision,
             "kernels_ms_per_step": {k: v["ms"] / max(args.steps, 1) for k, v in kern.items()},
             "wall_s": wall,
         }

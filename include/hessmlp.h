@@ -121,6 +121,13 @@ HESS_API hess_status hess_mlp_set_stream(hess_mlp* h, void* stream);
  * Results do not depend on it. */
 HESS_API hess_status hess_mlp_set_operand_limit(hess_mlp* h, int64_t bytes);
 
+/* Most blocks (one per SM) the Lanczos kernel of the OPG eigen step may use
+ * (0, the default: every SM).  The kernel is bound by the latency of its
+ * grid barriers rather than by arithmetic, so a smaller grid leaves SMs to
+ * work that overlaps it (the contractions of hess_curvature) at little cost.
+ * Results do not depend on it beyond rounding. */
+HESS_API hess_status hess_mlp_set_eig_blocks(hess_mlp* h, int blocks);
+
 /* Per-example gradient matrix (Sec. 3.1 and Sec. 5.2 "get_J_op"; the matrix J
  * of Eq. hesseq3 read with one example per ROW): G is N x P row-major,
  * G[n, :] = dC_n/domega^T with C_n the per-example cross-entropy of Eq. cost.
@@ -339,6 +346,14 @@ HESS_API hess_status hess_server_submit(hess_server* s, const hess_request* req,
 HESS_API hess_status hess_server_wait(hess_server* s, int64_t ticket, double timeout_seconds,
                                       hess_status* result);
 
+/* hess_server_wait, and the request's device times: *gpu_start_ms and
+ * *gpu_end_ms (either may be NULL) receive the times, in ms since the server
+ * was created, of CUDA events recorded on the request's slot stream just
+ * before and just after its work was queued (so the interval spans the
+ * request's kernels on the device); -1 if they could not be read. */
+HESS_API hess_status hess_server_wait_timed(hess_server* s, int64_t ticket, double timeout_seconds,
+                                            hess_status* result, double* gpu_start_ms, double* gpu_end_ms);
+
 /* Finish the running requests, fail the queued ones, release everything. */
 HESS_API hess_status hess_server_destroy(hess_server* s);
 
@@ -467,12 +482,14 @@ HESS_API hess_status hess_timing_read(hess_mlp* h, int kernel_class, hess_kernel
  *
  * hess_check_devmath: for n device doubles x, writes four rows of n device
  * doubles to out (4 n entries, row-major): the refined FP64 reciprocal the
- * eigensolvers use (hardware estimate plus two Newton-Raphson steps), CUDA's
- * correctly rounded 1.0 / x, the refined reciprocal square root, and
- * 1.0 / sqrt(x) (the last two 0 where x <= 0).  The refined forms are meant
- * for |x| in [2^-1022, 2^1022]: the estimate flushes subnormal inputs and
- * results to zero, so outside that range they return 0 or infinity.  Queued
- * on `stream`; returns without waiting.  Errors: INVALID_ARG.
+ * eigensolvers use (hardware estimate plus two Newton-Raphson steps; within
+ * one ulp of 1/x), CUDA's correctly rounded 1.0 / x, the refined reciprocal
+ * square root (within two ulps), and 1.0 / sqrt(x) (the last two 0 where
+ * x <= 0).  The refined forms are meant for |x| in [2^-1022, 2^1022]: the
+ * estimate flushes subnormal inputs and results to zero, so outside that
+ * range they return 0 (|x| > 2^1022) or a value that is not finite
+ * (subnormal x).  Queued on `stream`; returns without waiting.  Errors:
+ * INVALID_ARG.
  *
  * hess_debug_set_barrier_limit: the number of SM clock cycles a block of the
  * OPG eigen step's cooperative Lanczos kernel waits at a grid barrier before

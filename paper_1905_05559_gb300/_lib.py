@@ -38,7 +38,8 @@ EXPORTS = (
     "hess_autotune", "hess_autotune_entries", "hess_autotune_save", "hess_autotune_load",
     "hess_batch_set_graphs", "hess_curvature", "hessian_vector_products", "hessian_topk_eig",
     "hess_approx_form", "hess_approx_apply", "hessian_minibatches", "opg_topk_eig_streaming",
-    "hess_check_devmath", "hess_debug_set_barrier_limit", "hess_probe_fp64",
+    "hess_check_devmath", "hess_debug_set_barrier_limit", "hess_probe_fp64", "hess_mlp_set_eig_blocks",
+    "hess_server_wait_timed",
 )
 
 REQUEST_KIND = {"hessian": 0, "opg": 1, "eig": 2}
@@ -146,10 +147,15 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.hess_server_submit.restype = st
     lib.hess_server_wait.argtypes = [vp, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]
     lib.hess_server_wait.restype = st
+    lib.hess_server_wait_timed.argtypes = [vp, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.hess_server_wait_timed.restype = st
     lib.hess_server_destroy.argtypes = [vp]
     lib.hess_server_destroy.restype = st
     lib.hess_mlp_set_operand_limit.argtypes = [vp, i64]
     lib.hess_mlp_set_operand_limit.restype = st
+    lib.hess_mlp_set_eig_blocks.argtypes = [vp, ctypes.c_int]
+    lib.hess_mlp_set_eig_blocks.restype = st
     lib.hess_batch_create.argtypes = [i64, vp, ctypes.POINTER(vp)]
     lib.hess_batch_create.restype = st
     lib.hess_batch_run.argtypes = [vp, ctypes.POINTER(BatchItem), ctypes.c_int, ctypes.c_int,

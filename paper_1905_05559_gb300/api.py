@@ -95,6 +95,9 @@ class HessMLP:
     def set_operand_limit(self, nbytes: int):
         _lib.check(self._lib.hess_mlp_set_operand_limit(self.h, int(nbytes)))
 
+    def set_eig_blocks(self, blocks: int):
+        _lib.check(self._lib.hess_mlp_set_eig_blocks(self.h, int(blocks)))
+
     def timing(self, enable: bool):
         _lib.check(self._lib.hess_timing_enable(self.h, 1 if enable else 0))
 
@@ -329,6 +332,16 @@ class HessServer:
         _lib.check(self._lib.hess_server_wait(self.s, int(ticket), float(timeout), ctypes.byref(res)))
         self._keep.pop(ticket, None)
         return res.value
+
+    def wait_timed(self, ticket, timeout=-1.0):
+        """Returns (status, gpu_start_ms, gpu_end_ms): the request's device
+        interval in ms since the server was created."""
+        res = ctypes.c_int()
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _lib.check(self._lib.hess_server_wait_timed(self.s, int(ticket), float(timeout), ctypes.byref(res),
+                                                    ctypes.byref(a), ctypes.byref(b)))
+        self._keep.pop(ticket, None)
+        return res.value, a.value, b.value
 
     def close(self):
         if getattr(self, "s", None):

@@ -643,6 +643,14 @@ hess_status hess_mlp_set_operand_limit(hess_mlp* h, int64_t bytes) {
   return HESS_OK;
 }
 
+hess_status hess_mlp_set_eig_blocks(hess_mlp* h, int blocks) {
+  clear_error();
+  if (!h) return set_error(HESS_ERR_INVALID_ARG, "handle is NULL");
+  if (blocks < 0) return set_error(HESS_ERR_INVALID_ARG, "blocks must be >= 0");
+  h->lz_blocks = blocks;
+  return HESS_OK;
+}
+
 hess_status per_example_grads(hess_mlp* h, const void* X, const void* Y, int64_t N,
                               hess_precision prec, void* G) {
   clear_error();

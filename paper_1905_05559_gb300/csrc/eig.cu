@@ -97,18 +97,17 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
 // scope (after the block barrier, it publishes every thread's writes) and the
 // polling load an acquire (the block barrier after it passes the other
 // blocks' writes on to every thread).
-__device__ bool grid_barrier(const LzArgs& a, unsigned& epoch) {
+__device__ bool grid_barrier_at(unsigned* bar, int* err, long long limit) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
-    ++epoch;
     const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
-    const unsigned old = atom_add_release_gpu(a.bar, add);
+    const unsigned old = atom_add_release_gpu(bar, add);
     const long long t0 = clock64();
-    while (((old ^ ld_acquire_gpu(a.bar)) & 0x80000000u) == 0u) {
-      if (clock64() - t0 > a.bar_limit || *(volatile int*)a.err) {
-        atomicExch(a.err, 1);
+    while (((old ^ ld_acquire_gpu(bar)) & 0x80000000u) == 0u) {
+      if (clock64() - t0 > limit || *(volatile int*)err) {
+        atomicExch(err, 1);
         ok = 0;
         break;
       }
@@ -116,6 +115,10 @@ __device__ bool grid_barrier(const LzArgs& a, unsigned& epoch) {
   }
   __syncthreads();
   return ok != 0;
+}
+__device__ bool grid_barrier(const LzArgs& a, unsigned& epoch) {
+  ++epoch;
+  return grid_barrier_at(a.bar, a.err, a.bar_limit);
 }
 
 // sum_c x[c] y[c] over one warp for c in [n0, n1); x in global memory, y in
@@ -442,6 +445,385 @@ __global__ void last_beta_kernel(const double* npart, int nparts, double* out) {
     double s = 0.0;
     for (int b = 0; b < nparts; ++b) s += npart[b];
     *out = sqrt(s);
+  }
+}
+
+// ------------------------------------------ double-float Lanczos kernel ----
+// The same Lanczos process with full reorthogonalisation, for Gram matrices
+// whose rows fit the blocks' shared memory, in double-float arithmetic
+// (devmath.cuh: about 48 significant bits, all on the FP32 pipe) and with
+// three grid barriers per step j:
+//   1  gather q_j; u = M q_j on the owned rows (kept as row j of MQ); the
+//      first-pass coefficients h_i = (M q_i) . q_j for i < j (M symmetric:
+//      one warp each, over full rows of MQ); block partials of h_j = q_j . u
+//   2  h_j from its partials; w' = u - sum_{i<=j} h_i q_i on the owned slice;
+//      block partials of d_i = q_i . w' (i <= j) and of ||w'||^2
+//   3  d_i and ||w'||^2 from the partials (every block sums them in the same
+//      order, so every block gets the same bits); alpha_j = h_j + d_j;
+//      w = w' - sum_{i<=j} d_i q_i; beta_j^2 = ||w'||^2 - ||d||^2, since
+//      Q^T w' = d makes w' - Q d orthogonal to Q d (when ||d||^2 exceeds a
+//      quarter of ||w'||^2 the subtraction would lose digits, and the norm of
+//      w is summed directly, one barrier more); q_{j+1} = w / beta_j.
+// (classical Gram-Schmidt twice against every earlier vector, as in the FP64
+// kernel).  M arrives scaled by 2^-e (e from the largest diagonal entry,
+// which bounds every entry of a positive semidefinite matrix) as hi/lo
+// pairs; alpha and beta are stored unscaled in FP64.  A breakdown (beta_j <=
+// 1e-12 of the largest alpha or beta so far) stores beta_j = 0, records
+// stop = j + 1 and ends the kernel; the host restarts from a new direction.
+struct DfArgs {
+  const float2* M;    // N x N, scaled, hi/lo pairs
+  int64_t N;
+  float2* Q;          // Lanczos vectors, rows of length N (mcap rows)
+  float2* MQ;         // M q_i, rows of length N
+  float2* h;          // first-pass coefficient chunks ([mcap][nch])
+  float2* part;       // [gridDim][pst] block partials
+  float2* apart;      // [gridDim] block partials of q_j . u
+  double* alpha;
+  double* beta;
+  const int* escale;  // M was scaled by 2^-escale
+  unsigned* bar;
+  int* err;
+  int* stop;
+  int m0, m1, mcap, E, pst, qcap;
+  int nch;  // first-pass chunks per coefficient
+  long long bar_limit;
+};
+
+constexpr int kDfThreads = 512;
+constexpr int kDfMaxGrid = 256;
+constexpr int kDfChunk = 256;     // entries per first-pass dot-product task
+constexpr int kDfMaxChunks = 8;   // so N <= 2048
+constexpr int kDfWarps = kDfThreads / 32;
+constexpr int kDfRed = 1024;  // float2 scratch entries per block
+
+// out[e] = base[e] - sum_{i < nv} coef[i] Qs[e][i] for the owned entries:
+// a warp per entry (warps w0 .. w0 + nw - 1 of the block), lanes over i
+__device__ __forceinline__ void df_combine(const float2* Qs, int qcap, const float2* coef, int nv,
+                                           const float2* base, float2* out, int ne, int w0 = 0,
+                                           int nw = kDfWarps) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int e = warp - w0; e < ne; e += nw) {
+    const float2* q = Qs + (int64_t)e * qcap;
+    float s = 0.0f, c = 0.0f;
+    for (int i = lane; i < nv; i += 32) df_mac(coef[i], q[i], s, c);
+    const float2 t = df_warp_sum(s, c);
+    if (lane == 0) out[e] = df_sub(base[e], t);
+  }
+}
+
+__global__ void __launch_bounds__(kDfThreads, 1) lanczos_df_kernel(DfArgs a) {
+  extern __shared__ float2 dfsh[];
+  const int64_t N = a.N;
+  const int E = a.E, qcap = a.qcap;
+  float2* Msh = dfsh;                      // owned rows of M, E x N
+  float2* qf = Msh + (int64_t)E * N;       // q_j, N
+  float2* Qs = qf + N;                     // owned slices of q_i, entry-major, E x qcap
+  float2* us = Qs + (int64_t)E * qcap;     // owned slice of u, E
+  float2* ws = us + E;                     // owned slice of w' (then w), E
+  float2* cf = ws + E;                     // coefficients, mcap + 2
+  float2* red = cf + (a.mcap + 2);         // scratch, kDfRed
+  const int64_t n0 = (int64_t)blockIdx.x * E;
+  const int ne = (int)(N - n0 < E ? (N - n0 > 0 ? N - n0 : 0) : E);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int G = (int)gridDim.x;
+  __shared__ float2 s_h, s_dd, s_beta2, s_rb;
+  __shared__ int s_brk;
+  __shared__ float s_scale;  // largest |alpha|, beta so far (scaled units)
+  const double unscale = ldexp(1.0, *a.escale);
+  for (int e = 0; e < ne; ++e)
+    for (int64_t n = tid; n < N; n += kDfThreads) Msh[(int64_t)e * N + n] = a.M[(n0 + e) * N + n];
+  for (int e = warp; e < ne; e += kDfWarps)
+    for (int i = lane; i <= a.m0 && i < qcap; i += 32) Qs[(int64_t)e * qcap + i] = a.Q[(int64_t)i * N + n0 + e];
+  if (tid == 0) {
+    float sc = 0.0f;
+    for (int i = 0; i < a.m0; ++i)
+      sc = fmaxf(sc, fmaxf(fabsf((float)(a.alpha[i] / unscale)), (float)(a.beta[i] / unscale)));
+    s_scale = sc;
+  }
+  // wpr warps share one owned row of the product
+  int wpr = 1;
+  while (wpr < 8 && 2 * wpr * (ne > 0 ? ne : 1) <= kDfWarps) wpr *= 2;
+  const int rows_per_pass = kDfWarps / wpr;
+  __syncthreads();
+  for (int j = a.m0; j < a.m1; ++j) {
+    // ---- 1: u = M q_j (owned rows), first-pass coefficients.  The
+    // first-pass tasks are a warp per coefficient and chunk of kDfChunk
+    // entries (the chunks are summed after the barrier); each warp's first
+    // task has its loads issued with those of q_j, before the product.
+    const int task0 = (kDfWarps - 1 - warp) * G + (int)blockIdx.x;
+    float2 pv[kDfChunk / 32];
+    if (task0 < j * a.nch) {
+      const int i = task0 / a.nch, ch = task0 - i * a.nch;
+      const float2* mq = a.MQ + (int64_t)i * N + (int64_t)ch * kDfChunk + lane;
+      const int64_t rem = N - (int64_t)ch * kDfChunk - lane;
+#pragma unroll
+      for (int u = 0; u < kDfChunk / 32; ++u) pv[u] = u * 32 < rem ? mq[u * 32] : make_float2(0.0f, 0.0f);
+    }
+    for (int64_t n = tid; n < N; n += kDfThreads) qf[n] = a.Q[(int64_t)j * N + n];
+    __syncthreads();
+    for (int r = warp / wpr; r < ne; r += rows_per_pass) {
+      const float2* row = Msh + (int64_t)r * N;
+      // two independent running sums per lane
+      float s0 = 0.0f, c0 = 0.0f, s1 = 0.0f, c1 = 0.0f;
+      const int st = wpr * 32;
+      int64_t n = (warp % wpr) * 32 + lane;
+#pragma unroll 2
+      for (; n + st < N; n += 2 * st) {
+        df_mac(row[n], qf[n], s0, c0);
+        df_mac(row[n + st], qf[n + st], s1, c1);
+      }
+      if (n < N) df_mac(row[n], qf[n], s0, c0);
+      float sx, ex;
+      two_sum(s0, s1, sx, ex);
+      const float2 t = df_warp_sum(sx, (c0 + c1) + ex);
+      if (lane == 0) red[r * wpr + warp % wpr] = t;
+    }
+    for (int t = task0; t < j * a.nch; t += kDfWarps * G) {
+      const int i = t / a.nch, ch = t - i * a.nch;
+      const int64_t c0 = (int64_t)ch * kDfChunk + lane;
+      const float2* mq = a.MQ + (int64_t)i * N;
+      float2 v[kDfChunk / 32];
+      if (t == task0) {
+#pragma unroll
+        for (int u = 0; u < kDfChunk / 32; ++u) v[u] = pv[u];
+      } else {
+#pragma unroll
+        for (int u = 0; u < kDfChunk / 32; ++u) {
+          const int64_t n = c0 + u * 32;
+          v[u] = n < N ? mq[n] : make_float2(0.0f, 0.0f);
+        }
+      }
+      float s = 0.0f, c = 0.0f;
+#pragma unroll
+      for (int u = 0; u < kDfChunk / 32; ++u) {
+        const int64_t n = c0 + u * 32;
+        if (n < N) df_mac(v[u], qf[n], s, c);
+      }
+      const float2 r2 = df_warp_sum(s, c);
+      if (lane == 0) a.h[(int64_t)i * a.nch + ch] = r2;
+    }
+    __syncthreads();
+    if (tid < ne) {
+      float s = 0.0f, c = 0.0f;
+      for (int p = 0; p < wpr; ++p) df_acc(red[tid * wpr + p], s, c);
+      const float2 u = df_norm(s, c);
+      us[tid] = u;
+      a.MQ[(int64_t)j * N + n0 + tid] = u;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      float s = 0.0f, c = 0.0f;
+      for (int e = lane; e < ne; e += 32) df_mac(Qs[(int64_t)e * qcap + j], us[e], s, c);
+      const float2 t = df_warp_sum(s, c);
+      if (lane == 0) a.apart[blockIdx.x] = t;
+    }
+    if (!grid_barrier_at(a.bar, a.err, a.bar_limit)) return;
+    // ---- 2: w' on the owned slice, partials of the second pass
+    const float2 ap = tid < G ? a.apart[tid] : make_float2(0.0f, 0.0f);
+    for (int i = tid; i < j; i += kDfThreads) {
+      float2 v[kDfMaxChunks];
+#pragma unroll
+      for (int ch = 0; ch < kDfMaxChunks; ++ch)
+        v[ch] = ch < a.nch ? a.h[(int64_t)i * a.nch + ch] : make_float2(0.0f, 0.0f);
+      float s = 0.0f, c = 0.0f;
+#pragma unroll
+      for (int ch = 0; ch < kDfMaxChunks; ++ch) df_acc(v[ch], s, c);
+      cf[i] = df_norm(s, c);
+    }
+    if (tid < G) red[tid] = ap;
+    __syncthreads();
+    if (warp == 0) {
+      float s = 0.0f, c = 0.0f;
+      for (int b = lane; b < G; b += 32) df_acc(red[b], s, c);
+      const float2 t = df_warp_sum(s, c);
+      if (lane == 0) {
+        cf[j] = t;
+        s_h = t;
+      }
+    }
+    __syncthreads();
+    df_combine(Qs, qcap, cf, j + 1, us, ws, ne);
+    __syncthreads();
+    for (int i = tid; i <= j + 1; i += kDfThreads) {
+      float s = 0.0f, c = 0.0f;
+      if (i <= j) {
+        for (int e = 0; e < ne; ++e) df_mac(Qs[(int64_t)e * qcap + i], ws[e], s, c);
+      } else {
+        for (int e = 0; e < ne; ++e) df_mac(ws[e], ws[e], s, c);
+      }
+      a.part[(int64_t)blockIdx.x * a.pst + i] = df_norm(s, c);
+    }
+    if (!grid_barrier_at(a.bar, a.err, a.bar_limit)) return;
+    // ---- 3: d and ||w'||^2 from the partials (R threads per coefficient
+    // over interleaved blocks, then in order of r)
+    {
+      const int C = j + 2;
+      int R = 1;
+      while (R < 32 && 2 * R * C <= kDfThreads && 2 * R <= G) R *= 2;
+      for (int i0 = 0; i0 < C; i0 += kDfRed / R) {
+        const int cn = min(C - i0, kDfRed / R);
+        for (int t = tid; t < R * cn; t += kDfThreads) {
+          const int r = t / cn, i = i0 + t % cn;
+          float s = 0.0f, c = 0.0f;
+          // sixteen loads in flight per batch
+          for (int b0 = r; b0 < G; b0 += 16 * R) {
+            float2 v[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+              const int b = b0 + u * R;
+              v[u] = b < G ? a.part[(int64_t)b * a.pst + i] : make_float2(0.0f, 0.0f);
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u) df_acc(v[u], s, c);
+          }
+          red[r * cn + (i - i0)] = df_norm(s, c);
+        }
+        __syncthreads();
+        for (int i = tid; i < cn; i += kDfThreads) {
+          float s = 0.0f, c = 0.0f;
+          for (int r = 0; r < R; ++r) df_acc(red[r * cn + i], s, c);
+          cf[i0 + i] = df_norm(s, c);
+        }
+        __syncthreads();
+      }
+    }
+    // the last warp sums ||d||^2 while the others form w on the slice
+    if (warp == kDfWarps - 1) {
+      float s = 0.0f, c = 0.0f;
+      for (int i = lane; i <= j; i += 32) df_mac(cf[i], cf[i], s, c);
+      const float2 t = df_warp_sum(s, c);
+      if (lane == 0) s_dd = t;
+    } else {
+      df_combine(Qs, qcap, cf, j + 1, ws, ws, ne, 0, kDfWarps - 1);
+    }
+    __syncthreads();
+    const float2 nw2 = cf[j + 1];
+    const bool direct = s_dd.x > 0.25f * nw2.x;  // the same decision in every block
+    if (direct) {
+      __syncthreads();
+      if (warp == 0) {
+        float s = 0.0f, c = 0.0f;
+        for (int e = lane; e < ne; e += 32) df_mac(ws[e], ws[e], s, c);
+        const float2 t = df_warp_sum(s, c);
+        // (apart is free: every block read it before the second barrier)
+        if (lane == 0) a.apart[blockIdx.x] = t;
+      }
+      if (!grid_barrier_at(a.bar, a.err, a.bar_limit)) return;
+      if (warp == 0) {
+        float s = 0.0f, c = 0.0f;
+        for (int b = lane; b < G; b += 32) df_acc(a.apart[b], s, c);
+        const float2 t = df_warp_sum(s, c);
+        if (lane == 0) s_beta2 = t;
+      }
+    } else if (tid == 0) {
+      s_beta2 = df_sub(nw2, s_dd);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const float2 al = df_add(s_h, cf[j]);
+      const float2 be = df_sqrt(s_beta2);
+      const float sc = fmaxf(s_scale, fmaxf(fabsf(al.x), be.x));
+      s_scale = sc;
+      const int brk = !(be.x > 1e-12f * sc) || sc == 0.0f;
+      s_brk = brk;
+      s_rb = brk ? make_float2(0.0f, 0.0f) : df_rcp(be);
+      if (blockIdx.x == 0) {
+        a.alpha[j] = df_val(al) * unscale;
+        a.beta[j] = brk ? 0.0 : df_val(be) * unscale;
+        if (brk) *a.stop = j + 1;
+      }
+    }
+    __syncthreads();
+    if (s_brk) return;  // the same decision in every block
+    const float2 rb = s_rb;
+    for (int e = tid; e < ne; e += kDfThreads) {
+      const float2 q = df_mul(ws[e], rb);
+      if (j + 1 < qcap) Qs[(int64_t)e * qcap + j + 1] = q;
+      if (j + 1 < a.mcap) a.Q[(int64_t)(j + 1) * N + n0 + e] = q;
+    }
+    if (!grid_barrier_at(a.bar, a.err, a.bar_limit)) return;
+  }
+}
+
+// 2^e >= the largest diagonal entry of the n x n matrix M (one block)
+__global__ void df_scale_kernel(const double* M, int64_t n, int* escale) {
+  __shared__ double sh[32];
+  double mx = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, fabs(M[i * n + i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, sh[w]);
+    mx = fmax(mx, sh[0]);
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);  // mx < 2^e
+    *escale = e;
+  }
+}
+
+// M (FP64) -> 2^-e M as hi/lo pairs, in place (the same 8 bytes per entry)
+__global__ void df_split_kernel(double* M, int64_t n2, const int* escale) {
+  const double sc = ldexp(1.0, -*escale);
+  float2* out = reinterpret_cast<float2*>(M);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = df_split(M[i] * sc);
+}
+
+// q_0: a counter-based random unit vector (hi/lo pairs)
+__global__ void df_start_kernel(float2* q, int64_t N, uint64_t key) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int64_t n = threadIdx.x; n < N; n += blockDim.x) {
+    const double v = rnd_sym(key, n);
+    s = fma(v, v, s);
+  }
+  s = block_sum(s, sh);
+  const double inv = 1.0 / sqrt(s);
+  for (int64_t n = threadIdx.x; n < N; n += blockDim.x) q[n] = df_split(rnd_sym(key, n) * inv);
+}
+
+// Restart after a breakdown that ended step m - 1: q_m = a counter-based
+// random vector orthogonalised twice against q_0 .. q_{m-1}, normalised (one
+// block, FP64, w in shared memory; a rare path)
+__global__ void df_restart_kernel(float2* Q, int64_t N, int m, uint64_t key) {
+  extern __shared__ double rsh[];
+  double* w = rsh;      // N
+  double* c = rsh + N;  // m
+  __shared__ double sh[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int64_t n = threadIdx.x; n < N; n += blockDim.x) w[n] = rnd_sym(key + (uint64_t)m * 0x9E3779B97F4A7C15ull, n);
+  __syncthreads();
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int i = warp; i < m; i += nwarp) {
+      const float2* q = Q + (int64_t)i * N;
+      double s = 0.0;
+      for (int64_t n = lane; n < N; n += 32) s = fma(df_val(q[n]), w[n], s);
+      s = warp_sum(s);
+      if (lane == 0) c[i] = s;
+    }
+    __syncthreads();
+    for (int64_t n = threadIdx.x; n < N; n += blockDim.x) {
+      double v = w[n];
+      for (int i = 0; i < m; ++i) v = fma(-c[i], df_val(Q[(int64_t)i * N + n]), v);
+      w[n] = v;
+    }
+    __syncthreads();
+  }
+  double s = 0.0;
+  for (int64_t n = threadIdx.x; n < N; n += blockDim.x) s = fma(w[n], w[n], s);
+  s = block_sum(s, sh);
+  const double inv = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+  for (int64_t n = threadIdx.x; n < N; n += blockDim.x) Q[(int64_t)m * N + n] = df_split(w[n] * inv);
+}
+
+// rows of hi/lo pairs -> FP64 in place
+__global__ void df_to_f64_kernel(double* Q, int64_t n) {
+  const float2* in = reinterpret_cast<const float2*>(Q);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = df_val(in[i]);
+    Q[i] = v;
   }
 }
 
@@ -980,6 +1362,8 @@ hess_status eig_kernel_attributes() {
                                (int)kEigSmemCap);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(inviter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEigSmemCap);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(lanczos_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEigSmemCap);
   });
   if (e != cudaSuccess) return set_error(HESS_ERR_CUDA, "eigen kernel attributes: %s", cudaGetErrorString(e));
   return HESS_OK;
@@ -1039,6 +1423,9 @@ struct LzBufs {
          *Y = nullptr, *rr = nullptr, *mx = nullptr, *tri_scratch = nullptr;
   unsigned* bar = nullptr;
   int *err = nullptr, *cstart = nullptr, *stop = nullptr;
+  // double-float kernel: block partials and the scale exponent of M
+  float2 *dfpart = nullptr, *dfapart = nullptr, *dfh = nullptr;
+  int* escale = nullptr;
 };
 
 void plan_lz(Arena& ar, int64_t n, int k, LzBufs& b, double* Q, double* MQ) {
@@ -1067,6 +1454,157 @@ void plan_lz(Arena& ar, int64_t n, int k, LzBufs& b, double* Q, double* MQ) {
   // global scratch of the tridiagonal kernels when shared memory is too small
   const int64_t tri_n = tridiag_scratch_doubles(mcap, k);
   b.tri_scratch = tri_n ? ar.take<double>(tri_n) : nullptr;
+  b.dfpart = ar.take<float2>((int64_t)kDfMaxGrid * (mcap + 2));
+  b.dfapart = ar.take<float2>(kDfMaxGrid);
+  b.dfh = ar.take<float2>((mcap + 2) * kDfMaxChunks);
+  b.escale = ar.take<int>(1);
+}
+
+// Shared memory of the double-float kernel for grid g on an n x n matrix with
+// slices of q_0 .. q_{m1} (0 when the owned rows do not fit).
+size_t df_smem(int64_t n, int64_t g, int64_t mcap, int64_t m1) {
+  const int64_t E = cdiv(n, g);
+  const int64_t f2 = E * n + n + E * (m1 + 1) + 2 * E + (mcap + 2) + kDfRed;
+  return (size_t)f2 * sizeof(float2);
+}
+
+// Grid of the double-float kernel for an n x n matrix: one block per SM, or
+// the handle's lz_blocks when set; 0 when the kernel does not apply (n above
+// its chunk table, or the owned rows and slices exceed shared memory even
+// with a block on every SM).
+int df_grid(hess_mlp* h, int64_t n, int64_t mcap) {
+  const int gmax = h->sm_count < kDfMaxGrid ? h->sm_count : kDfMaxGrid;
+  if (gmax < 1 || n > (int64_t)kDfChunk * kDfMaxChunks || df_smem(n, gmax, mcap, mcap) > kEigSmemCap) return 0;
+  int g = gmax;
+  if (h->lz_blocks > 0 && h->lz_blocks < g) g = h->lz_blocks;
+  if (n < g) g = (int)n;
+  return g;
+}
+
+// The Lanczos process of run_lz with the double-float kernel; M (FP64, n x n)
+// is overwritten by its scaled hi/lo pairs.  On return b.Q holds q_0 ..
+// q_{m-1} in FP64 (rows of n), as run_lz leaves them.
+hess_status run_lz_df(hess_mlp* h, double* M, int k, LzBufs& b, int grid, int* m_out, bool* converged_out) {
+  const int64_t N = b.n, mcap = b.mcap;
+  cudaStream_t s = h->stream;
+  const uint64_t key = 0x5DEECE66Dull;
+  float2* Q = reinterpret_cast<float2*>(b.Q);
+  float2* MQ = reinterpret_cast<float2*>(b.MQ);
+  const int max_grid = h->sm_count < kDfMaxGrid ? h->sm_count : kDfMaxGrid;
+  HM_TRY(eig_kernel_attributes());
+  {
+    Tick t(h, HESS_K_LANCZOS, 0.0, 0.0);
+    df_scale_kernel<<<1, 1024, 0, s>>>(M, N, b.escale);
+    HM_LAUNCHED();
+    const int64_t n2 = N * N;
+    df_split_kernel<<<(unsigned)(cdiv(n2, 256) < 4096 ? cdiv(n2, 256) : 4096), 256, 0, s>>>(M, n2, b.escale);
+    HM_LAUNCHED();
+    df_start_kernel<<<1, 1024, 0, s>>>(Q, N, key);
+    HM_LAUNCHED();
+  }
+  HM_CUDA(cudaMemsetAsync(b.err, 0, sizeof(int), s));
+  int m = 0;
+  int64_t target = N < (int64_t)3 * k + 32 ? N : (int64_t)3 * k + 32;
+  if (target < k) target = k;
+  if (target > mcap) target = mcap;
+  bool converged = false;
+  double* hp = h->host_pinned;
+  const long long lim = g_bar_limit.load();
+  while (true) {
+    DfArgs a;
+    a.M = reinterpret_cast<const float2*>(M);
+    a.N = N;
+    a.Q = Q;
+    a.MQ = MQ;
+    a.h = b.dfh;
+    a.part = b.dfpart;
+    a.apart = b.dfapart;
+    a.alpha = b.alpha;
+    a.beta = b.beta;
+    a.escale = b.escale;
+    a.bar = b.bar;
+    a.err = b.err;
+    a.stop = b.stop;
+    a.m0 = m;
+    a.m1 = (int)target;
+    a.mcap = (int)mcap;
+    a.pst = (int)(mcap + 2);
+    a.qcap = (int)target + 1;
+    a.nch = (int)cdiv(N, kDfChunk);
+    a.bar_limit = lim > 0 ? lim : BAR_TIMEOUT;
+    // this launch's grid: the requested one, or more blocks when the slices
+    // of q_0 .. q_target do not fit shared memory (the eligibility check
+    // guarantees that the most blocks fit)
+    int gl = grid;
+    while (gl < max_grid && df_smem(N, gl, mcap, target) > kEigSmemCap) ++gl;
+    gl = (int)cdiv(N, cdiv(N, gl));
+    a.E = (int)cdiv(N, gl);
+    const size_t dyn = df_smem(N, gl, mcap, target);
+    void* kargs[] = {&a};
+    HM_CUDA(cudaMemsetAsync(b.bar, 0, 2 * sizeof(unsigned), s));
+    HM_CUDA(cudaMemsetAsync(b.stop, 0xff, sizeof(int), s));
+    {
+      double fl = 0.0;
+      for (int64_t j = m; j < target; ++j) fl += 2.0 * N * N + 8.0 * N * (j + 1);
+      Tick t(h, HESS_K_LANCZOS, fl, 0.0);
+      HM_CUDA(cudaLaunchCooperativeKernel((void*)lanczos_df_kernel, gl, kDfThreads, kargs, dyn, s));
+      HM_LAUNCHED();
+    }
+    HM_CUDA(cudaMemcpyAsync(reinterpret_cast<int*>(hp + 2), b.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaMemcpyAsync(reinterpret_cast<int*>(hp + 2) + 1, b.stop, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaStreamSynchronize(s));
+    if (*reinterpret_cast<int*>(hp + 2)) return set_error(HESS_ERR_TIMEOUT, "Lanczos grid barrier gave up");
+    const int stopped = reinterpret_cast<int*>(hp + 2)[1];
+    if (stopped >= 0) {
+      // breakdown: beta_{stopped-1} = 0 is stored and T_stopped is complete;
+      // a new direction orthogonal to the basis continues it (none exists
+      // once the basis spans the whole space)
+      m = stopped;
+      if (m >= N) {
+        converged = true;
+        break;
+      }
+      if (m < mcap) {
+        Tick t(h, HESS_K_LANCZOS, 0.0, 0.0);
+        df_restart_kernel<<<1, 1024, (size_t)(N + m) * sizeof(double), s>>>(Q, N, m, key + 7);
+        HM_LAUNCHED();
+        continue;
+      }
+    } else {
+      m = (int)target;
+    }
+    {
+      Tick t(h, HESS_K_TRIDIAG, 0.0, 0.0);
+      HM_TRY(tridiag_topk(b.alpha, b.beta, m, k, b.theta, b.cstart, b.Y, mcap, b.beta + (m - 1), b.rr, b.mx,
+                          key + 11, b.tri_scratch, s));
+    }
+    HM_CUDA(cudaMemcpyAsync(hp, b.mx, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaStreamSynchronize(s));
+    if (hp[0] <= 1e-10 * hp[1] || m >= N) {
+      converged = true;
+      break;
+    }
+    if (m >= mcap) break;
+    int64_t step = k > 32 ? k : 32;
+    target = m + step;
+    if (target > mcap) target = mcap;
+    if (target > N) target = N;
+  }
+  if (converged && m >= N) {
+    // the tridiagonal eigenpairs of the complete T (after a final breakdown)
+    Tick t(h, HESS_K_TRIDIAG, 0.0, 0.0);
+    HM_TRY(tridiag_topk(b.alpha, b.beta, m, k, b.theta, b.cstart, b.Y, mcap, b.beta + (m - 1), b.rr, b.mx,
+                        key + 11, b.tri_scratch, s));
+  }
+  {
+    Tick t(h, HESS_K_LANCZOS, 0.0, 0.0);
+    const int64_t nq = (int64_t)m * N;
+    df_to_f64_kernel<<<(unsigned)(cdiv(nq, 256) < 4096 ? cdiv(nq, 256) : 4096), 256, 0, s>>>(b.Q, nq);
+    HM_LAUNCHED();
+  }
+  *m_out = m;
+  *converged_out = converged;
+  return HESS_OK;
 }
 
 // Steps 2-3 on the resident n x n matrix M: Lanczos with full
@@ -1291,7 +1829,12 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
 
   int m = 0;
   bool converged = false;
-  HM_TRY(run_lz(h, M, k, lb, &m, &converged));
+  const int dfg = df_grid(h, N, mcap);
+  if (dfg > 0) {
+    HM_TRY(run_lz_df(h, M, k, lb, dfg, &m, &converged));
+  } else {
+    HM_TRY(run_lz(h, M, k, lb, &m, &converged));
+  }
   res->lanczos_steps = m;
   {
     double f = 0.0;

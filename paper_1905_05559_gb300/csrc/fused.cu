@@ -91,6 +91,10 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
   if (!h->stream3) HM_CUDA(cudaStreamCreateWithFlags(&h->stream3, cudaStreamNonBlocking));
   if (!h->stream4) HM_CUDA(cudaStreamCreateWithFlags(&h->stream4, cudaStreamNonBlocking));
   const cudaStream_t sA = h->stream, sB = h->stream2, sC = h->stream3, sD = h->stream4;
+  // with the eigen step's Lanczos kernel held to lz_blocks SMs, the
+  // persistent contractions take the other SMs, so that the two overlap
+  const int sm_tc =
+      (h->lz_blocks > 0 && h->lz_blocks < h->sm_count) ? h->sm_count - h->lz_blocks : h->sm_count;
   // a device matrix to the host in two halves, one per copy stream, both
   // behind event e of stream A
   auto to_host = [&](void* dstv, const float* src, cudaEvent_t e) -> hess_status {
@@ -138,9 +142,9 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
       tc_split_plan(both, OPG ? 1 : 0, plan_o, plan_h);
     }
     tabO = ar.off;
-    HM_TRY(tc_launch_plan(h->sm_count, plan_o, ar, false, x3, h->err_dev, h->stage, sA));
+    HM_TRY(tc_launch_plan(sm_tc, plan_o, ar, false, x3, h->err_dev, h->stage, sA));
     tabH = ar.off;
-    HM_TRY(tc_launch_plan(h->sm_count, plan_h, ar, false, x3, h->err_dev, h->stage, sA));
+    HM_TRY(tc_launch_plan(sm_tc, plan_h, ar, false, x3, h->err_dev, h->stage, sA));
     xd = ar.take<double>(N * T1);
     yd = ar.take<double>(N * TL);
     plan_caches(ar, net, N, c64);
@@ -171,13 +175,13 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
   if (OPG) {
     Tick t(h, HESS_K_SYRK, plan_o.syrk_flops, 0.0);
     Arena at{h->ws, tabO};
-    tc_status = tc_launch_plan(h->sm_count, plan_o, at, true, x3, h->err_dev, h->stage, sA);
+    tc_status = tc_launch_plan(sm_tc, plan_o, at, true, x3, h->err_dev, h->stage, sA);
   }
   if (OPG && !o_dev && tc_status == HESS_OK) HM_TRY(to_host(OPG, os, ev.e[2]));
   if (H && tc_status == HESS_OK) {
     Tick t(h, HESS_K_HCONTRACT, plan_h.hess_flops, 0.0);
     Arena at{h->ws, tabH};
-    tc_status = tc_launch_plan(h->sm_count, plan_h, at, true, x3, h->err_dev, h->stage, sA);
+    tc_status = tc_launch_plan(sm_tc, plan_h, at, true, x3, h->err_dev, h->stage, sA);
   }
   if (H && !hh_dev && tc_status == HESS_OK) HM_TRY(to_host(H, hs, ev.e[3]));
   if (tc_status != HESS_OK) {

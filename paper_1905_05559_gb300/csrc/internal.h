@@ -144,6 +144,8 @@ struct hess_mlp {
   // operand bytes above which the tensor-core Hessian is built and contracted
   // in chunks (one launch per chunk) instead of in one launch
   size_t op_limit = (size_t)4 << 30;
+  // blocks of the OPG eigen step's Lanczos kernel (0: one per SM)
+  int lz_blocks = 0;
 };
 
 namespace hm {

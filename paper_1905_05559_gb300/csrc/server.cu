@@ -30,6 +30,13 @@ struct Ticket {
   bool done = false;
   hess_status status = HESS_OK;
   char message[256] = {0};
+  // device timestamps: recorded on the slot's stream before and after the
+  // request's work (timing events; destroyed when the ticket is released)
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  ~Ticket() {
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+  }
 };
 
 struct Slot {
@@ -59,6 +66,7 @@ struct hess_server {
   int64_t next_ticket = 1;
   bool stopping = false;
   std::thread scheduler;
+  cudaEvent_t ref = nullptr;  // completed at creation: the origin of request times
 };
 
 namespace hm {
@@ -94,7 +102,10 @@ void worker_loop(hess_server* sv, Slot* sl) {
     h->ws = sl->ws;
     h->ws_bytes = sl->cap;
     lk.unlock();
+    if (!t->ev0 && cudaEventCreate(&t->ev0) == cudaSuccess) cudaEventRecord(t->ev0, sl->stream);
     hess_status st = run_request(h, t->req);
+    if (!t->ev1 && cudaEventCreate(&t->ev1) == cudaSuccess) cudaEventRecord(t->ev1, sl->stream);
+    cudaGetLastError();
     if (st == HESS_OK || st == HESS_ERR_RANK_DEFICIENT) {
       cudaError_t e = cudaStreamSynchronize(sl->stream);
       if (e != cudaSuccess) st = set_error(HESS_ERR_CUDA, "request stream: %s", cudaGetErrorString(e));
@@ -217,6 +228,13 @@ hess_status hess_server_create(int slots, int64_t budget_bytes, hess_server** ou
     }
     sv->slots.push_back(std::move(sl));
   }
+  if (cudaEventCreate(&sv->ref) != cudaSuccess || cudaEventRecord(sv->ref, sv->slots[0]->stream) != cudaSuccess ||
+      cudaEventSynchronize(sv->ref) != cudaSuccess) {
+    cudaGetLastError();
+    sv->stopping = true;
+    hess_server_destroy(sv);
+    return set_error(HESS_ERR_CUDA, "cannot record the server's reference event");
+  }
   for (auto& sl : sv->slots) sl->worker = std::thread(worker_loop, sv, sl.get());
   sv->scheduler = std::thread(scheduler_loop, sv);
   *out = sv;
@@ -282,6 +300,11 @@ hess_status hess_server_submit(hess_server* sv, const hess_request* req, int64_t
 
 hess_status hess_server_wait(hess_server* sv, int64_t ticket, double timeout_seconds,
                              hess_status* result) {
+  return hess_server_wait_timed(sv, ticket, timeout_seconds, result, nullptr, nullptr);
+}
+
+hess_status hess_server_wait_timed(hess_server* sv, int64_t ticket, double timeout_seconds,
+                                   hess_status* result, double* gpu_start_ms, double* gpu_end_ms) {
   clear_error();
   if (!sv || !result) return set_error(HESS_ERR_INVALID_ARG, "server and result must be non-NULL");
   std::unique_lock<std::mutex> lk(sv->mu);
@@ -294,6 +317,17 @@ hess_status hess_server_wait(hess_server* sv, int64_t ticket, double timeout_sec
   if (!sv->cv.wait_until(lk, deadline, [&] { return t->done; }))
     return set_error(HESS_ERR_TIMEOUT, "ticket %lld not finished", (long long)ticket);
   *result = t->status;
+  if (gpu_start_ms || gpu_end_ms) {
+    float a = -1.0f, b = -1.0f;
+    if (!t->ev0 || !t->ev1 || cudaEventSynchronize(t->ev1) != cudaSuccess ||
+        cudaEventElapsedTime(&a, sv->ref, t->ev0) != cudaSuccess ||
+        cudaEventElapsedTime(&b, sv->ref, t->ev1) != cudaSuccess) {
+      cudaGetLastError();
+      a = b = -1.0f;
+    }
+    if (gpu_start_ms) *gpu_start_ms = a;
+    if (gpu_end_ms) *gpu_end_ms = b;
+  }
   if (t->status != HESS_OK) set_error(t->status, "%s", t->message);
   sv->tickets.erase(it);
   return HESS_OK;
@@ -331,6 +365,8 @@ hess_status hess_server_destroy(hess_server* sv) {
     if (sl->ws) cudaFree(sl->ws);
     if (sl->stream) cudaStreamDestroy(sl->stream);
   }
+  sv->tickets.clear();
+  if (sv->ref) cudaEventDestroy(sv->ref);
   for (auto* n : sv->nets) hess_mlp_destroy(n);
   cudaGetLastError();
   delete sv;
