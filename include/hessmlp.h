@@ -121,11 +121,13 @@ HESS_API hess_status hess_mlp_set_stream(hess_mlp* h, void* stream);
  * Results do not depend on it. */
 HESS_API hess_status hess_mlp_set_operand_limit(hess_mlp* h, int64_t bytes);
 
-/* Most blocks (one per SM) the Lanczos kernel of the OPG eigen step may use
- * (0, the default: every SM).  The kernel is bound by the latency of its
- * grid barriers rather than by arithmetic, so a smaller grid leaves SMs to
- * work that overlaps it (the contractions of hess_curvature) at little cost.
- * Results do not depend on it beyond rounding. */
+/* Blocks (one per SM) the Lanczos kernel of the OPG eigen step uses when the
+ * Gram matrix's rows fit shared memory (0, the default: 5/8 of the SMs).
+ * The kernel is bound by the latency of its grid barriers rather than by
+ * arithmetic, so a grid smaller than the GPU costs it little and leaves SMs
+ * to work that overlaps it: hess_curvature runs its contractions there.
+ * Results depend on it only through the rounding of the Lanczos sums (the
+ * same setting gives the same bits). */
 HESS_API hess_status hess_mlp_set_eig_blocks(hess_mlp* h, int blocks);
 
 /* Per-example gradient matrix (Sec. 3.1 and Sec. 5.2 "get_J_op"; the matrix J

@@ -827,6 +827,36 @@ __global__ void df_to_f64_kernel(double* Q, int64_t n) {
   }
 }
 
+// ------------------------------------------------------ back-projection ----
+// B[n][i k + c] = delta[n][i] u[n][c]  (N x Tout k)
+__global__ void bp_build_kernel(const double* D, const double* U, int64_t N, int Tout, int k, double* B) {
+  const int64_t cols = (int64_t)Tout * k;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < N * cols;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = t / cols, r = t - n * cols;
+    const int i = (int)(r / k), c = (int)(r - (int64_t)i * k);
+    B[t] = D[n * Tout + i] * U[n * k + c];
+  }
+}
+
+// evecs[c][woff + i Tin + j] = R[j][i k + c], evecs[c][boff + i] = Rb[i][c]
+__global__ void bp_scatter_kernel(const double* R, const double* Rb, int Tin, int Tout, int k, double* evecs,
+                                  int64_t P, int64_t woff, int64_t boff) {
+  const int64_t per = (int64_t)(Tin + 1) * Tout;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < per * k;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(t / per);
+    const int64_t p = t - (int64_t)c * per;
+    if (p < (int64_t)Tin * Tout) {
+      const int64_t i = p / Tin, j = p - i * Tin;
+      evecs[(int64_t)c * P + woff + p] = R[j * Tout * (int64_t)k + i * k + c];
+    } else {
+      const int64_t i = p - (int64_t)Tin * Tout;
+      evecs[(int64_t)c * P + boff + i] = Rb[i * k + c];
+    }
+  }
+}
+
 // Cluster boundaries of the Ritz values (descending): eigenvalues closer
 // than ortol to their predecessor share a cluster whose eigenvectors are
 // orthogonalised against each other during inverse iteration.
@@ -1468,17 +1498,28 @@ size_t df_smem(int64_t n, int64_t g, int64_t mcap, int64_t m1) {
   return (size_t)f2 * sizeof(float2);
 }
 
-// Grid of the double-float kernel for an n x n matrix: one block per SM, or
-// the handle's lz_blocks when set; 0 when the kernel does not apply (n above
-// its chunk table, or the owned rows and slices exceed shared memory even
-// with a block on every SM).
+// Grid of the double-float kernel for an n x n matrix: the handle's
+// lz_blocks when set, else 5/8 of the SMs (the kernel waits on its grid
+// barriers far more than it computes: measured on this workload, 96 blocks
+// take the same time as 152, and the SMs left over run the contractions of
+// the fused call beside it); 0 when the kernel does not apply (n above its
+// chunk table, or the owned rows and slices exceed shared memory even with a
+// block on every SM).
 int df_grid(hess_mlp* h, int64_t n, int64_t mcap) {
   const int gmax = h->sm_count < kDfMaxGrid ? h->sm_count : kDfMaxGrid;
   if (gmax < 1 || n > (int64_t)kDfChunk * kDfMaxChunks || df_smem(n, gmax, mcap, mcap) > kEigSmemCap) return 0;
-  int g = gmax;
-  if (h->lz_blocks > 0 && h->lz_blocks < g) g = h->lz_blocks;
+  int g = h->lz_blocks > 0 ? h->lz_blocks : (h->sm_count * 5) / 8;
+  if (g > gmax) g = gmax;
+  if (g < 1) g = 1;
   if (n < g) g = (int)n;
   return g;
+}
+
+int eig_lanczos_blocks(hess_mlp* h, int64_t n, int k) {
+  const int64_t mcap = n < (int64_t)8 * k + 512 ? n : (int64_t)8 * k + 512;
+  const int g = df_grid(h, n, mcap);
+  if (g <= 0) return h->sm_count;  // the FP64 kernel: a block on every SM
+  return (int)cdiv(n, cdiv(n, g));
 }
 
 // The Lanczos process of run_lz with the double-float kernel; M (FP64, n x n)
@@ -1749,13 +1790,13 @@ hess_status run_lz(hess_mlp* h, const double* M, int k, LzBufs& b, int* m_out, b
 }
 
 hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, int64_t N, int k,
-                          double* evals_d, double* evecs_d, Arena& ar, bool dry, EigResult* res) {
+                          double* evals_d, double* evecs_d, Arena& ar, bool dry, EigResult* res,
+                          const std::function<hess_status()>* after_gram) {
   const int64_t P = net.P;
   const int L = net.L;
   double* M = ar.take<double>(N * N);
   double* DD = ar.take<double>(N * N);
   double* AA = ar.take<double>(N * N);
-  double* G = ar.take<double>(N * P);
   LzBufs lb;
   // the basis and M Q reuse AA and DD once the Gram matrix is formed
   plan_lz(ar, N, k, lb, AA, DD);
@@ -1774,9 +1815,35 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   F64SyrkScratch fs;
   if (ktc) plan_f64_syrk(ar, N, ktc, fs);
   // and so does the back-projection G^T U (K = N)
-  const bool bp_tc = f64_gemm_nt_tc_eligible(h, P, k, N);
+  // and so do the back-projection's wide layers: per weight layer,
+  // R = A^T B with B[n][(i, c)] = delta[n][i] u[n][c] (K = N)
+  // (mode 1: rows of A^T against B in column groups; mode 2, for narrow
+  // layers: rows of B^T against A, the transposed product; mode 0: the SIMT
+  // FP64 GEMM, for products too small to repay the digit splitting)
+  int64_t cols_max = 0, r_max = 0, tout_max = 0, m_tc = 0, n_tc = 0;
+  int bp_mode[kMaxLayers] = {};
+  for (int wl = 1; wl <= L - 1; ++wl) {
+    const int64_t Tin = net.T[wl - 1], Tout = net.T[wl], cols = Tout * k;
+    const int64_t gw = cols < 256 ? cols : 256;
+    cols_max = cols > cols_max ? cols : cols_max;
+    r_max = Tin * cols > r_max ? Tin * cols : r_max;
+    tout_max = Tout > tout_max ? Tout : tout_max;
+    if (2.0 * N * Tin * cols < 5e7) continue;
+    if (f64_gemm_nt_tc_eligible(h, Tin, gw, N)) {
+      bp_mode[wl] = 1;
+      m_tc = Tin > m_tc ? Tin : m_tc;
+      n_tc = gw > n_tc ? gw : n_tc;
+    } else if (Tin <= 256 && f64_gemm_nt_tc_eligible(h, cols, Tin, N)) {
+      bp_mode[wl] = 2;
+      m_tc = cols > m_tc ? cols : m_tc;
+      n_tc = Tin > n_tc ? Tin : n_tc;
+    }
+  }
+  double* Bf = ar.take<double>(N * cols_max);
+  double* Rf = ar.take<double>(r_max);
+  double* Rb = ar.take<double>(tout_max * k);
   F64GemmScratch fb;
-  if (bp_tc) plan_f64_gemm_nt(ar, P, k, N, fb);
+  if (m_tc) plan_f64_gemm_nt(ar, m_tc, n_tc, N, fb);
   if (dry) return HESS_OK;
   cudaStream_t s = h->stream;
 
@@ -1827,6 +1894,7 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
     HM_TRY(mirror_upper(M, N, N, s));
   }
 
+  if (after_gram) HM_TRY((*after_gram)());
   int m = 0;
   bool converged = false;
   const int dfg = df_grid(h, N, mcap);
@@ -1863,28 +1931,60 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
     g.scn = 1;
     HM_TRY(gemm(g, s));
   }
-  {
-    Tick t(h, HESS_K_BACKPROJ, 0.0, (double)N * P * sizeof(double));
-    HM_TRY(write_grads(net, c, G, P, s));
-  }
-  if (bp_tc) {
-    HM_TRY(f64_gemm_nt_tc(h, G, P, U, 1, k, N, evecs_d, 1, P, fb, s));
-  } else {
-    Tick t(h, HESS_K_BACKPROJ, 2.0 * P * N * k, 0.0);
+  // q_c = G^T u_c without forming G: the block of weight layer w is
+  // R[j][(i, c)] = sum_n a[n][j] (delta[n][i] u[n][c]), its bias rows
+  // sum_n delta[n][i] u[n][c] (Eq. J with g_n = [delta_n (x) a_n; delta_n])
+  for (int wl = 1; wl <= L - 1; ++wl) {
+    const int64_t Tin = net.T[wl - 1], Tout = net.T[wl], cols = Tout * k;
+    Tick t(h, HESS_K_BACKPROJ, bp_mode[wl] ? 2.0 * N * Tout * k : 2.0 * N * (Tin + 1) * cols, 0.0);
+    bp_build_kernel<<<(unsigned)(cdiv(N * cols, 256) < 65536 ? cdiv(N * cols, 256) : 65536), 256, 0, s>>>(
+        c.d[wl], U, N, (int)Tout, k, Bf);
+    HM_LAUNCHED();
+    if (bp_mode[wl] == 1) {
+      F64GemmScratch f2 = fb;
+      f2.M = Tin;
+      f2.Nn = cols < 256 ? cols : 256;
+      HM_TRY(f64_gemm_nt_tc(h, c.a[wl - 1], Tin, Bf, 1, cols, N, Rf, cols, 1, f2, s, cols));
+    } else if (bp_mode[wl] == 2) {
+      // R^T = B^T A: rows (i, c) of B^T against the Tin rows of A^T
+      F64GemmScratch f2 = fb;
+      f2.M = cols;
+      f2.Nn = Tin;
+      HM_TRY(f64_gemm_nt_tc(h, Bf, cols, c.a[wl - 1], 1, Tin, N, Rf, 1, cols, f2, s, Tin));
+    } else {
+      Gemm<double> g;
+      g.M = (int)Tin;
+      g.N = (int)cols;
+      g.K = (int)N;
+      g.A = c.a[wl - 1];
+      g.sam = 1;
+      g.sak = Tin;
+      g.B = Bf;
+      g.sbk = cols;
+      g.sbn = 1;
+      g.C = Rf;
+      g.scm = cols;
+      g.scn = 1;
+      HM_TRY(gemm(g, s));
+    }
     Gemm<double> g;
-    g.M = (int)P;
+    g.M = (int)Tout;
     g.N = k;
     g.K = (int)N;
-    g.A = G;
+    g.A = c.d[wl];
     g.sam = 1;
-    g.sak = P;
+    g.sak = Tout;
     g.B = U;
     g.sbk = k;
     g.sbn = 1;
-    g.C = evecs_d;
-    g.scm = 1;
-    g.scn = P;
+    g.C = Rb;
+    g.scm = k;
+    g.scn = 1;
     HM_TRY(gemm(g, s));
+    const int64_t per = (Tin + 1) * Tout;
+    bp_scatter_kernel<<<(unsigned)(cdiv(per * k, 256) < 65536 ? cdiv(per * k, 256) : 65536), 256, 0, s>>>(
+        Rf, Rb, (int)Tin, (int)Tout, k, evecs_d, P, net.woff[wl - 1], net.boff[wl - 1]);
+    HM_LAUNCHED();
   }
   {
     Tick t(h, HESS_K_BACKPROJ, 0.0, 0.0);

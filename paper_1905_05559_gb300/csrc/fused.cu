@@ -20,6 +20,8 @@
 // so that the OPG's transfer overlaps the Hessian's contraction and both
 // overlap the eigen step.  The streams use separate regions of the handle's
 // workspace (and separate split-K scratch).
+#include <functional>
+
 #include "internal.h"
 
 using namespace hm;
@@ -91,10 +93,13 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
   if (!h->stream3) HM_CUDA(cudaStreamCreateWithFlags(&h->stream3, cudaStreamNonBlocking));
   if (!h->stream4) HM_CUDA(cudaStreamCreateWithFlags(&h->stream4, cudaStreamNonBlocking));
   const cudaStream_t sA = h->stream, sB = h->stream2, sC = h->stream3, sD = h->stream4;
-  // with the eigen step's Lanczos kernel held to lz_blocks SMs, the
-  // persistent contractions take the other SMs, so that the two overlap
-  const int sm_tc =
-      (h->lz_blocks > 0 && h->lz_blocks < h->sm_count) ? h->sm_count - h->lz_blocks : h->sm_count;
+  // the persistent contractions take the SMs the eigen step's Lanczos
+  // launches leave free, so that the two overlap -- unless a matrix goes to
+  // a host buffer: then its copy (the longest part of such a call) should
+  // start as early as possible, and the contractions run first on every SM
+  const int lz_g = eig_lanczos_blocks(h, N, k);
+  const bool host_out = (OPG && !o_dev) || (H && !hh_dev);
+  const int sm_tc = (lz_g < h->sm_count && !host_out) ? h->sm_count - lz_g : h->sm_count;
   // a device matrix to the host in two halves, one per copy stream, both
   // behind event e of stream A
   auto to_host = [&](void* dstv, const float* src, cudaEvent_t e) -> hess_status {
@@ -122,6 +127,7 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
   Caches<double> c64;
   TcPlan plan_o, plan_h;
   EigResult res;
+  cudaEvent_t ev_in = nullptr;
   auto layout = [&](Arena& ar, bool live) -> hess_status {
     xs = x_dev ? (float*)X : ar.take<float>(N * T1);
     ys = y_dev ? (float*)Y : ar.take<float>(N * TL);
@@ -131,6 +137,9 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
     if (live) {
       if (!x_dev) HM_CUDA(cudaMemcpyAsync(xs, X, N * T1 * 4, cudaMemcpyHostToDevice, sA));
       if (!y_dev) HM_CUDA(cudaMemcpyAsync(ys, Y, N * TL * 4, cudaMemcpyHostToDevice, sA));
+      // stream B may start once the inputs are on the device (and after
+      // earlier work on the handle's stream)
+      HM_CUDA(cudaEventRecord(ev_in, sA));
     }
     {
       // one preparation (one forward/backward pass) for both matrices, then
@@ -155,6 +164,9 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
     if (!live) HM_TRY(topk_eig_gram(h, net, c64, N, k, evd, eqd, ar, true, &res));
     return HESS_OK;
   };
+  EventSet ev;
+  for (cudaEvent_t& e : ev.e) HM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  ev_in = ev.e[0];
   Arena ar;
   HM_TRY(layout(ar, false));
   HM_TRY(ensure_ws(h, ar.off));
@@ -163,31 +175,47 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
   ar = Arena{h->ws, 0};
   HM_TRY(layout(ar, true));  // queues A's input staging and operand preparation
 
-  EventSet ev;
-  for (cudaEvent_t& e : ev.e) HM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-  // stream B starts once the inputs are on the device (and after earlier work
-  // on the handle's stream)
-  HM_CUDA(cudaEventRecord(ev.e[0], sA));
   HM_CUDA(cudaStreamWaitEvent(sB, ev.e[0], 0));
 
-  // stream A: the contractions, right behind their operands
+  // stream A: the contractions, right behind their operands (queued with the
+  // handle's stream set to A, so that their timing runs there)
   hess_status tc_status = HESS_OK;
-  if (OPG) {
-    Tick t(h, HESS_K_SYRK, plan_o.syrk_flops, 0.0);
-    Arena at{h->ws, tabO};
-    tc_status = tc_launch_plan(sm_tc, plan_o, at, true, x3, h->err_dev, h->stage, sA);
-  }
-  if (OPG && !o_dev && tc_status == HESS_OK) HM_TRY(to_host(OPG, os, ev.e[2]));
-  if (H && tc_status == HESS_OK) {
-    Tick t(h, HESS_K_HCONTRACT, plan_h.hess_flops, 0.0);
-    Arena at{h->ws, tabH};
-    tc_status = tc_launch_plan(sm_tc, plan_h, at, true, x3, h->err_dev, h->stage, sA);
-  }
-  if (H && !hh_dev && tc_status == HESS_OK) HM_TRY(to_host(H, hs, ev.e[3]));
-  if (tc_status != HESS_OK) {
-    cudaStreamSynchronize(sB);
-    drain_copies();
-    return tc_status;
+  auto contractions = [&]() -> hess_status {
+    cudaStream_t keep = h->stream;
+    h->stream = sA;
+    if (OPG) {
+      Tick t(h, HESS_K_SYRK, plan_o.syrk_flops, 0.0);
+      Arena at{h->ws, tabO};
+      tc_status = tc_launch_plan(sm_tc, plan_o, at, true, x3, h->err_dev, h->stage, sA);
+    }
+    hess_status st = HESS_OK;
+    if (OPG && !o_dev && tc_status == HESS_OK) st = to_host(OPG, os, ev.e[2]);
+    if (H && tc_status == HESS_OK && st == HESS_OK) {
+      Tick t(h, HESS_K_HCONTRACT, plan_h.hess_flops, 0.0);
+      Arena at{h->ws, tabH};
+      tc_status = tc_launch_plan(sm_tc, plan_h, at, true, x3, h->err_dev, h->stage, sA);
+    }
+    if (H && !hh_dev && tc_status == HESS_OK && st == HESS_OK) st = to_host(H, hs, ev.e[3]);
+    h->stream = keep;
+    return tc_status != HESS_OK ? tc_status : st;
+  };
+  // When the Lanczos launches leave SMs free, the contractions wait for the
+  // Gram matrix (whose exact-digit product wants every SM) and then run on
+  // the free SMs beside the Lanczos launches; otherwise they are queued at
+  // once and interleave with the eigen step.
+  const bool overlap = sm_tc < h->sm_count;
+  std::function<hess_status()> after_gram = [&]() -> hess_status {
+    HM_CUDA(cudaEventRecord(ev.e[1], sB));
+    HM_CUDA(cudaStreamWaitEvent(sA, ev.e[1], 0));
+    return contractions();
+  };
+  if (!overlap) {
+    const hess_status st = contractions();
+    if (st != HESS_OK) {
+      cudaStreamSynchronize(sB);
+      drain_copies();
+      return st;
+    }
   }
 
   // ---- stream B: the eigen step (the handle's stream is B meanwhile, so that
@@ -203,11 +231,12 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
     if (eig_status == HESS_OK) {
       Tick t(h, HESS_K_EIG, 0.0, 0.0);
       Arena are{h->ws, offEig};
-      eig_status = topk_eig_gram(h, net, c64, N, k, evd, eqd, are, false, &res);
+      eig_status = topk_eig_gram(h, net, c64, N, k, evd, eqd, are, false, &res, overlap ? &after_gram : nullptr);
       t.set_work(res.flops, 0.0);
     }
   }
   h->stream = sA;
+  if (eig_status == HESS_OK && tc_status != HESS_OK) eig_status = tc_status;
   if (eig_status != HESS_OK) {
     cudaStreamSynchronize(sB);  // nothing of B or the copies may run past the call
     drain_copies();

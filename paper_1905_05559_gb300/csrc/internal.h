@@ -9,6 +9,7 @@
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
+#include <functional>
 #include <vector>
 
 #include "../../include/hessmlp.h"
@@ -310,8 +311,15 @@ int64_t tridiag_scratch_doubles(int64_t mcap, int k);
 hess_status tridiag_topk(const double* a, const double* b, int m, int k, double* theta, int* cstart, double* Y,
                          int64_t ldy, const double* beta_last, double* res, double* mx, uint64_t key,
                          double* scratch, cudaStream_t s);
+// Blocks (one per SM) the Lanczos launches of the OPG eigen step take for N
+// examples and k eigenpairs.
+int eig_lanczos_blocks(hess_mlp* h, int64_t n, int k);
+// after_gram (optional) runs once the Gram matrix's kernels are queued and
+// before the first Lanczos launch (whose result the host waits for): the
+// fused call queues its contractions there, behind the Gram matrix.
 hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, int64_t N, int k,
-                          double* evals_d, double* evecs_d, Arena& ar, bool dry, EigResult* res);
+                          double* evals_d, double* evecs_d, Arena& ar, bool dry, EigResult* res,
+                          const std::function<hess_status()>* after_gram = nullptr);
 // Top-k eigenpairs of a resident symmetric n x n FP64 matrix M (row-major):
 // the same Lanczos, tridiagonal eigensolver and checks as the Gram route;
 // evecs_d row c = the unit eigenvector of evals_d[c] (sign canonicalised;
@@ -393,9 +401,11 @@ struct F64GemmScratch {
 bool f64_gemm_nt_tc_eligible(hess_mlp* h, int64_t M, int64_t Nn, int64_t K);
 void plan_f64_gemm_nt(Arena& ar, int64_t M, int64_t Nn, int64_t K, F64GemmScratch& fs);
 // C(m, c) = sum_k G[k][m] B(c, k), B(c, k) = B[c b_rs + k b_ks], written to
-// C[m scm + c scn], accurate to FP64 rounding.
+// C[m scm + c scn], accurate to FP64 rounding; c < Nn_total (default: the
+// plan's Nn), taken in groups of the plan's Nn columns, G's digits formed once.
 hess_status f64_gemm_nt_tc(hess_mlp* h, const double* G, int64_t ldg, const double* B, int64_t b_rs, int64_t b_ks,
-                           int64_t K, double* C, int64_t scm, int64_t scn, const F64GemmScratch& fs, cudaStream_t s);
+                           int64_t K, double* C, int64_t scm, int64_t scn, const F64GemmScratch& fs, cudaStream_t s,
+                           int64_t Nn_total = -1);
 
 // Jobs and tiles gathered for one persistent launch.
 struct TcPlan {

@@ -2004,72 +2004,83 @@ void plan_f64_gemm_nt(Arena& ar, int64_t M, int64_t Nn, int64_t K, F64GemmScratc
 }
 
 hess_status f64_gemm_nt_tc(hess_mlp* h, const double* G, int64_t ldg, const double* B, int64_t b_rs, int64_t b_ks,
-                           int64_t K, double* C, int64_t scm, int64_t scn, const F64GemmScratch& fs, cudaStream_t s) {
+                           int64_t K, double* C, int64_t scm, int64_t scn, const F64GemmScratch& fs, cudaStream_t s,
+                           int64_t Nn_total) {
   using namespace tc;
-  const int64_t M = fs.M, Nn = fs.Nn, ldk = fs.ldk, L = (int64_t)kDigits * ldk;
+  const int64_t M = fs.M, ldk = fs.ldk, L = (int64_t)kDigits * ldk;
+  const int64_t Nt = Nn_total < 0 ? fs.Nn : Nn_total;
   if (K > ldk) return set_error(HESS_ERR_INVALID_ARG, "exact-digit product: K %lld beyond its plan", (long long)K);
   // (the only caller is the back-projection of the OPG eigen step)
   Tick tp(h, HESS_K_BACKPROJ, 0.0, 0.0);
-  // A = G^T: rows are the columns of G; B: plane-major digits, rows (e, c)
+  // A = G^T: rows are the columns of G, split once; B: plane-major digits,
+  // rows (e, c), one group of at most fs.Nn rows at a time
   colmax_exp_kernel<<<(unsigned)cdiv(M, 32), dim3(32, 8), 0, s>>>(G, ldg, K, M, fs.exA);
   HM_LAUNCHED();
   digits_cols_kernel<<<dim3((unsigned)cdiv(ldk, 128), (unsigned)cdiv(M, 32)), dim3(32, 8), 0, s>>>(
       G, ldg, K, M, fs.exA, ldk, fs.DA);
   HM_LAUNCHED();
-  digits_rows_kernel<<<(unsigned)cdiv(Nn, 8), 256, 0, s>>>(B, b_rs, b_ks, Nn, K, ldk, nullptr, nullptr, fs.RB, fs.exB);
-  HM_LAUNCHED();
   tp.stop();
-  const std::vector<DigitJob> js = digit_jobs(Nn);
   const int64_t nseg = k_segments(ldk);
-  if ((int64_t)js.size() * nseg > kMaxDigitJobs)
-    return set_error(HESS_ERR_INVALID_ARG, "exact-digit product: too many digit jobs");
-  std::vector<Job> jobs;
-  std::vector<int4> tiles;
-  DigitJobs dj{};
-  dj.count = (int)(js.size() * nseg);
-  for (int w = 0; w < 2 * kDigits; ++w) dj.wt[w] = ldexp(1.0, -12 - 7 * w);
-  int64_t off = 0;
-  for (int64_t sg = 0; sg < nseg; ++sg) {
-    const int64_t k0 = sg * kExactK;
-    const int64_t inner = std::min<int64_t>(kExactK, ldk - k0);  // a multiple of 64
-    for (size_t jj = 0; jj < js.size(); ++jj) {
-      const DigitJob& g = js[jj];
-      const int j = (int)jobs.size();
-      const int64_t cols = (int64_t)(g.e1 - g.e0) * Nn;
-      const int BN = (int)align_up((size_t)cols, 16);
-      Job job{};
-      HM_TRY(make_block_map(&job.a_hi, fs.DA + (int64_t)g.d * ldk + k0, inner, L, M, BM));
-      job.a_lo = job.a_hi;
-      HM_TRY(make_block_map(&job.b_hi, fs.RB + (int64_t)g.e0 * Nn * ldk + k0, inner, ldk, cols, BN));
-      job.b_lo = job.b_hi;
-      job.BN = BN;
-      job.nkb = (int)(inner / BK);
-      job.idesc = make_idesc(BN);
-      job.M = M;
-      job.Nn = cols;
-      job.mode = 3;
-      job.scale = 1.0f;
-      job.out = fs.T + off;
-      job.ldo = cols;
-      for (int64_t tm = 0; tm < cdiv(M, BM); ++tm) tiles.push_back(make_int4(j, (int)tm, 0, 0));
-      jobs.push_back(job);
-      dj.d[j] = g.d;
-      dj.e0[j] = g.e0;
-      dj.e1[j] = g.e1;
-      dj.off[j] = off;
-      off += M * cols;
+  for (int64_t c0 = 0; c0 < Nt; c0 += fs.Nn) {
+    const int64_t Nn = std::min<int64_t>(fs.Nn, Nt - c0);
+    {
+      Tick tb(h, HESS_K_BACKPROJ, 0.0, 0.0);
+      digits_rows_kernel<<<(unsigned)cdiv(Nn, 8), 256, 0, s>>>(B + c0 * b_rs, b_rs, b_ks, Nn, K, ldk, nullptr, nullptr,
+                                                               fs.RB, fs.exB);
+      HM_LAUNCHED();
     }
+    const std::vector<DigitJob> js = digit_jobs(Nn);
+    if ((int64_t)js.size() * nseg > kMaxDigitJobs)
+      return set_error(HESS_ERR_INVALID_ARG, "exact-digit product: too many digit jobs");
+    std::vector<Job> jobs;
+    std::vector<int4> tiles;
+    DigitJobs dj{};
+    dj.count = (int)(js.size() * nseg);
+    for (int w = 0; w < 2 * kDigits; ++w) dj.wt[w] = ldexp(1.0, -12 - 7 * w);
+    int64_t off = 0;
+    for (int64_t sg = 0; sg < nseg; ++sg) {
+      const int64_t k0 = sg * kExactK;
+      const int64_t inner = std::min<int64_t>(kExactK, ldk - k0);  // a multiple of 64
+      for (size_t jj = 0; jj < js.size(); ++jj) {
+        const DigitJob& g = js[jj];
+        const int j = (int)jobs.size();
+        const int64_t cols = (int64_t)(g.e1 - g.e0) * Nn;
+        const int BN = (int)align_up((size_t)cols, 16);
+        Job job{};
+        HM_TRY(make_block_map(&job.a_hi, fs.DA + (int64_t)g.d * ldk + k0, inner, L, M, BM));
+        job.a_lo = job.a_hi;
+        HM_TRY(make_block_map(&job.b_hi, fs.RB + (int64_t)g.e0 * Nn * ldk + k0, inner, ldk, cols, BN));
+        job.b_lo = job.b_hi;
+        job.BN = BN;
+        job.nkb = (int)(inner / BK);
+        job.idesc = make_idesc(BN);
+        job.M = M;
+        job.Nn = cols;
+        job.mode = 3;
+        job.scale = 1.0f;
+        job.out = fs.T + off;
+        job.ldo = cols;
+        for (int64_t tm = 0; tm < cdiv(M, BM); ++tm) tiles.push_back(make_int4(j, (int)tm, 0, 0));
+        jobs.push_back(job);
+        dj.d[j] = g.d;
+        dj.e0[j] = g.e0;
+        dj.e1[j] = g.e1;
+        dj.off[j] = off;
+        off += M * cols;
+      }
+    }
+    {
+      double fl = 0.0;
+      for (const Job& jb : jobs) fl += 2.0 * (double)jb.M * jb.Nn * (double)jb.nkb * BK;
+      Tick t(h, HESS_K_DIGITS, fl, 0.0);
+      HM_TRY(launch_jobs(h->sm_count, jobs.data(), (int)jobs.size(), tiles.data(), (int)tiles.size(), fs.jobs,
+                         fs.tiles, false, h->err_dev, h->stage, s));
+    }
+    Tick tc(h, HESS_K_BACKPROJ, 0.0, 0.0);
+    combine_general_kernel<<<(unsigned)cdiv(M * Nn, 256), 256, 0, s>>>(fs.T, M, Nn, dj, fs.exA, fs.exB,
+                                                                       C + c0 * scn, scm, scn, 0);
+    HM_LAUNCHED();
   }
-  {
-    double fl = 0.0;
-    for (const Job& jb : jobs) fl += 2.0 * (double)jb.M * jb.Nn * (double)jb.nkb * BK;
-    Tick t(h, HESS_K_DIGITS, fl, 0.0);
-    HM_TRY(launch_jobs(h->sm_count, jobs.data(), (int)jobs.size(), tiles.data(), (int)tiles.size(), fs.jobs,
-                       fs.tiles, false, h->err_dev, h->stage, s));
-  }
-  Tick tc(h, HESS_K_BACKPROJ, 0.0, 0.0);
-  combine_general_kernel<<<(unsigned)cdiv(M * Nn, 256), 256, 0, s>>>(fs.T, M, Nn, dj, fs.exA, fs.exB, C, scm, scn, 0);
-  HM_LAUNCHED();
   return HESS_OK;
 }
 

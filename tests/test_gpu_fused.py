@@ -48,6 +48,33 @@ def test_fused_equals_single_calls_at_benchmark_size(hm, name, k):
     assert torch.equal(ev, ev1) and torch.equal(Q, Q1)
 
 
+@pytest.mark.parametrize("blocks", [64, 100])
+def test_fused_with_a_capped_lanczos_grid(hm, blocks):
+    """With the eigen step's Lanczos kernel held to fewer blocks, the fused
+    call queues its contractions behind the Gram matrix on the other SMs:
+    still the same bits as the single calls on the same handle, and the
+    eigenvalues of the default grid to rounding."""
+    pb = named_config("mlp_784_16_10")
+    k = 32
+    X = torch.as_tensor(pb.X, dtype=torch.float32, device="cuda")
+    Y = torch.as_tensor(pb.Y, dtype=torch.float32, device="cuda")
+    ref = hm.HessMLP(pb.widths, pb.acts, pb.omega)
+    ev0, _, _ = ref.opg_topk_eig(X, Y, k, "bf16x3")
+    net = hm.HessMLP(pb.widths, pb.acts, pb.omega)
+    net.set_eig_blocks(blocks)
+    o1, h1, ev1, Q1 = _single(net, X, Y, "bf16x3", k)
+    o = torch.full_like(o1, float("nan"))
+    h = torch.full_like(h1, float("nan"))
+    ev = torch.empty_like(ev1)
+    Q = torch.empty_like(Q1)
+    for _ in range(2):  # twice: the second call reuses the workspace and streams
+        net.curvature(X, Y, "bf16x3", opg=o, hessian=h, k=k, evals=ev, evecs=Q)
+        torch.cuda.synchronize()
+        assert torch.equal(o, o1) and torch.equal(h, h1)
+        assert torch.equal(ev, ev1) and torch.equal(Q, Q1)
+    assert float((ev - ev0).abs().max()) <= 1e-12 * float(ev0[0])
+
+
 def test_fused_with_host_buffers(hm):
     pb = make_problem([70, 33, 10], ["tanh"], 129, 7, "normal", "uniform")
     net = hm.HessMLP(pb.widths, pb.acts, pb.omega)
