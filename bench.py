@@ -68,10 +68,13 @@ def parse():
     ap.add_argument("--step", default="fused", choices=["fused", "streams", "calls"],
                     help="fused: one hess_curvature call (two internal streams); streams: the "
                          "single calls on two handles and streams; calls: the single calls in turn")
-    ap.add_argument("--row", default=None, choices=["hessian-eig", "approx", "minibatch", "stream-eig"],
+    ap.add_argument("--row", default=None, choices=["hessian-eig", "approx", "minibatch", "stream-eig", "lowmem-eig"],
                     help="hessian-eig: top-k Hessian eigenpairs by Lanczos on H v products; "
                          "approx: low/full-rank approximations from them (own JSON lines)")
     ap.add_argument("--row-k", type=int, default=32)
+    ap.add_argument("--lowmem-n", type=int, default=262144)
+    ap.add_argument("--lowmem-k", type=int, default=100)
+    ap.add_argument("--lowmem-block", type=int, default=0)
     ap.add_argument("--batch-graphs", action="store_true",
                     help="replay each group of the batch from a CUDA graph (use --warmup >= 2)")
     ap.add_argument("--autotune", action="store_true",
@@ -856,6 +859,95 @@ def stream_eig_bench(args):
     print(json.dumps(line), flush=True)
 
 
+def lowmem_eig_bench(args):
+    """Top-k OPG eigenpairs in O(k P) memory (opg_topk_eig_lowmem): the
+    precision workload's network (MLP [1024, 64, 64, 10] ReLU, P = 70410)
+    over N = 262144 seeded examples (x ~ N(0,1), seed 2), chunks of 8192, FP32
+    products, FP64 basis; neither G, nor the Gram matrix, nor the 8 P^2-byte
+    OPG is formed.  metric: examples/s; the device memory the call holds is
+    reported beside the P x P route's."""
+    import ctypes
+
+    import torch
+
+    import paper_1905_05559_gb300 as hm
+    from paper_1905_05559_gb300 import _lib, build
+    from synth import named_config
+
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    lib = hm.load()
+    N, k, chunk = args.lowmem_n, args.lowmem_k, 8192
+    pb = named_config("mlp_1024_64_64_10", N=N)
+    P = pb.P
+    free0, total = torch.cuda.mem_get_info()
+    net = hm.HessMLP(pb.widths, pb.acts, pb.omega, stream=stream.cuda_stream)
+    X = torch.as_tensor(pb.X, dtype=torch.float32, device="cuda")
+    Y = torch.as_tensor(pb.Y, dtype=torch.float32, device="cuda")
+    ev = torch.empty(k, dtype=torch.float64, device="cuda")
+    Q = torch.empty((k, P), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    free_in, _ = torch.cuda.mem_get_info()
+    passes = ctypes.c_int()
+
+    def call():
+        st = lib.opg_topk_eig_lowmem(net.h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()), N, k,
+                                     _lib.PRECISION["fp32"], chunk, args.lowmem_block,
+                                     ctypes.c_void_p(ev.data_ptr()), ctypes.c_void_p(Q.data_ptr()),
+                                     ctypes.byref(passes))
+        _lib.check(st, allow=(_lib.HESS_ERR_RANK_DEFICIENT,))
+
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    free_ws, _ = torch.cuda.mem_get_info()
+    for c in ("lowmem", "lanczos", "tridiag", "gram", "backproj", "eig"):
+        net.read_timing(c)
+    net.timing(True)
+    sampler = ClockSampler(gpu_index(0))
+    sampler.start()
+    l0 = lib.hess_launch_count()
+    ms = []
+    for _ in range(args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        call()
+        e.record(stream)
+        e.synchronize()
+        ms.append(a.elapsed_time(e))
+    launches = (lib.hess_launch_count() - l0) / args.steps
+    clocks = sampler.stop()
+    net.timing(False)
+    lm = net.read_timing("lowmem")
+    other = {c: net.read_timing(c)["ms"] / args.steps for c in ("lanczos", "tridiag", "gram", "backproj", "eig")}
+    t = statistics.median(ms)
+    smx = measured_peaks()[0].get("sm_max_mhz", 2070.0) * 1e6
+    fp32_peak = 152 * 128 * 2 * smx / 1e12
+    achieved = lm["flops"] / (lm["ms"] * 1e-3) / 1e12 if lm["ms"] > 0 else None
+    line = {
+        "metric": f"examples/s (top-{k} OPG eigenpairs, O(kP) memory)", "impl": "ours", "value": N / (t * 1e-3),
+        "unit": "examples/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (products), f64 (basis)",
+        "data": "synthetic",
+        "config": {"workload": f"MLP {pb.widths} relu, P={P}, N={N} (seed 2, x ~ N(0,1)), chunks of {chunk}; "
+                               f"top-{k} OPG eigenpairs", "l2": f"inputs ({X.numel() * 4 / 1e9:.2f} GB) larger than L2"},
+        "passes": passes.value,
+        "device_bytes": {"inputs": free0 - free_in, "workspace": free_in - free_ws,
+                         "pxp_route_opg_alone": 8 * P * P},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak if achieved else None, "traffic": None,
+                     "kernel_class": "lowmem (passes over the data: 4 N P b flops each, and the basis updates)",
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock",
+                     "ms_per_step": lm["ms"] / args.steps},
+        "evals_head": [float(v) for v in ev[:4].cpu()],
+        "projected_eig_ms_per_step": other,
+        "gpu_launches": launches, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # -------------------------------------------------------------- replicas ----
 def max_over_ranks(value: float, dist=None, device="cpu") -> float:
     """Replicas only: every rank runs the whole workload on its own GPU and
@@ -952,6 +1044,9 @@ def main():
         return
     if args.row == "stream-eig":
         stream_eig_bench(args)
+        return
+    if args.row == "lowmem-eig":
+        lowmem_eig_bench(args)
         return
 
     import numpy as np

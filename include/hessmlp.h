@@ -185,6 +185,31 @@ HESS_API hess_status opg_topk_eig(hess_mlp* h, const void* X, const void* Y, int
 HESS_API hess_status opg_topk_eig_streaming(hess_mlp* h, const void* X, const void* Y, int64_t N, int k,
                                             hess_precision prec, int64_t chunk, double* evals, double* evecs);
 
+/* Top-k OPG eigenpairs in O(k P) device memory (Sec. 5.4 and Sec. 6: the
+ * OPG eigenpairs from passes over mini-batches of examples with memory
+ * O(K P); here uncentred, as Eq. J states, and converged rather than
+ * truncated).  Neither G (N x P), nor the Gram matrix (N x N), nor the OPG
+ * (P x P) is formed: each pass over the examples, in chunks of `chunk`,
+ * applies OPG = (1/N) sum G_c^T G_c to a block of `block` vectors (0: the
+ * default, min(max(k, 16), 128)) through per-layer GEMMs with the chunk's
+ * forward/backward quantities; a block Krylov method with Rayleigh-Ritz
+ * extraction and thick restarts keeps at most max(6 block, k + 3 block)
+ * basis vectors and stops when every one of the top k Ritz residuals
+ * ||OPG q - mu q|| is at most tol mu_1 (tol = 1e-10 for HESS_FP64, 1e-5 for
+ * HESS_FP32, the precision of the products; the basis and the projected
+ * eigenproblem are FP64 in both).  Device memory: about 2 (6 block + k) P
+ * doubles plus one chunk's caches and two chunk x (T_out block) arrays.
+ * X, Y in the precision's dtype, host or device (host data is staged chunk
+ * by chunk, every pass); evals/evecs as in opg_topk_eig; *passes (may be
+ * NULL) receives the number of passes over the data.  Requires 1 <= k <=
+ * min(N, P).  Waits for its work.  Errors: INVALID_ARG (also for BF16
+ * precisions), OOM, CUDA, NOT_CONVERGED (after 300 passes),
+ * RANK_DEFICIENT (as opg_topk_eig), TIMEOUT. */
+HESS_API hess_status opg_topk_eig_lowmem(hess_mlp* h, const void* X, const void* Y, int64_t N, int k,
+                                         hess_precision prec, int64_t chunk, int block, double* evals,
+                                         double* evecs, int* passes);
+
+
 /* OPG (Eq. hesseq2, hesseq3), exact Hessian (Eq. hesseq1) and top-k OPG
  * eigenpairs (Sec. 5.4, Eq. J) of one data set in one call (any of them may
  * be left out: OPG or H NULL, k = 0).  The same results as
@@ -465,9 +490,12 @@ typedef enum {
   HESS_K_LANCZOS = 11,  /* the Lanczos launches on the Gram matrix; flops =
                            sum over steps j of 2 N^2 + 8 N (j + 1) */
   HESS_K_TRIDIAG = 12,  /* eigenpairs of the tridiagonal T_m */
-  HESS_K_BACKPROJ = 13, /* Ritz vectors, gradient rows and back-projection;
-                           flops = 2 N m k + 2 P N k */
-  HESS_K_COUNT = 14
+  HESS_K_BACKPROJ = 13, /* Ritz vectors and back-projection; flops =
+                           2 N m k + 2 P N k */
+  HESS_K_LOWMEM = 14,   /* opg_topk_eig_lowmem: the passes over the data
+                           (flops 4 N P b per pass); its basis updates and
+                           projected eigenproblems count as HESS_K_EIG */
+  HESS_K_COUNT = 15
 } hess_kernel_class;
 
 typedef struct {

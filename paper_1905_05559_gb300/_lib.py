@@ -39,7 +39,7 @@ EXPORTS = (
     "hess_batch_set_graphs", "hess_curvature", "hessian_vector_products", "hessian_topk_eig",
     "hess_approx_form", "hess_approx_apply", "hessian_minibatches", "opg_topk_eig_streaming",
     "hess_check_devmath", "hess_debug_set_barrier_limit", "hess_probe_fp64", "hess_mlp_set_eig_blocks",
-    "hess_server_wait_timed",
+    "hess_server_wait_timed", "opg_topk_eig_lowmem",
 )
 
 REQUEST_KIND = {"hessian": 0, "opg": 1, "eig": 2}
@@ -64,7 +64,7 @@ class BatchInfo(ctypes.Structure):
 
 KERNEL_CLASS = {"syrk": 0, "hcontract": 1, "grads": 2, "rop": 3, "eig": 4, "hrest": 5, "hvp": 6,
                 "hlanczos": 7, "approx": 8, "gram": 9, "digits": 10, "lanczos": 11, "tridiag": 12,
-                "backproj": 13}
+                "backproj": 13, "lowmem": 14}
 
 
 class KernelStats(ctypes.Structure):
@@ -122,6 +122,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.hessian_topk_eig.restype = st
     lib.opg_topk_eig_streaming.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, i64, vp, vp]
     lib.opg_topk_eig_streaming.restype = st
+    lib.opg_topk_eig_lowmem.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, i64, ctypes.c_int, vp, vp,
+                                        ctypes.POINTER(ctypes.c_int)]
+    lib.opg_topk_eig_lowmem.restype = st
     lib.hessian_minibatches.argtypes = [vp, vp, vp, i64, i64, ctypes.c_int, vp]
     lib.hessian_minibatches.restype = st
     lib.hess_approx_form.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_double,

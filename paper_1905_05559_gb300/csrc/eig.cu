@@ -1534,7 +1534,8 @@ hess_status run_lz_df(hess_mlp* h, double* M, int k, LzBufs& b, int grid, int* m
   const int max_grid = h->sm_count < kDfMaxGrid ? h->sm_count : kDfMaxGrid;
   HM_TRY(eig_kernel_attributes());
   {
-    Tick t(h, HESS_K_LANCZOS, 0.0, 0.0);
+    // (preparation of M and the start vector: counted with the Gram matrix)
+    Tick t(h, HESS_K_GRAM, 0.0, 0.0);
     df_scale_kernel<<<1, 1024, 0, s>>>(M, N, b.escale);
     HM_LAUNCHED();
     const int64_t n2 = N * N;
@@ -1606,7 +1607,7 @@ hess_status run_lz_df(hess_mlp* h, double* M, int k, LzBufs& b, int grid, int* m
         break;
       }
       if (m < mcap) {
-        Tick t(h, HESS_K_LANCZOS, 0.0, 0.0);
+        Tick t(h, HESS_K_TRIDIAG, 0.0, 0.0);
         df_restart_kernel<<<1, 1024, (size_t)(N + m) * sizeof(double), s>>>(Q, N, m, key + 7);
         HM_LAUNCHED();
         continue;
@@ -1638,7 +1639,8 @@ hess_status run_lz_df(hess_mlp* h, double* M, int k, LzBufs& b, int grid, int* m
                         key + 11, b.tri_scratch, s));
   }
   {
-    Tick t(h, HESS_K_LANCZOS, 0.0, 0.0);
+    // (the basis in FP64 for the Ritz vectors: counted with them)
+    Tick t(h, HESS_K_BACKPROJ, 0.0, 0.0);
     const int64_t nq = (int64_t)m * N;
     df_to_f64_kernel<<<(unsigned)(cdiv(nq, 256) < 4096 ? cdiv(nq, 256) : 4096), 256, 0, s>>>(b.Q, nq);
     HM_LAUNCHED();

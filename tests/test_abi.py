@@ -126,7 +126,7 @@ def test_compute_entry_points_cite_the_paper():
     txt = open(HEADER).read()
     compute = {"per_example_grads", "opg", "exact_hessian", "opg_topk_eig", "opg_topk_eig_streaming",
                "hess_curvature", "hessian_vector_products", "hessian_topk_eig", "hessian_minibatches",
-               "hess_approx_form"}
+               "hess_approx_form", "opg_topk_eig_lowmem"}
     prev_end, seen = 0, set()
     for m in re.finditer(r"HESS_API\s+[\w\s\*]+?\b(\w+)\s*\(", txt):
         comments = re.findall(r"/\*.*?\*/", txt[prev_end:m.start()], re.S)
