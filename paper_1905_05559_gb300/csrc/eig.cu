@@ -957,6 +957,46 @@ __device__ int sturm_count_f32(const float* a, const float* b2, int m, float x) 
   return cnt;
 }
 
+// The same count in double-float (devmath.cuh), rescaled every 4 steps: on
+// the FP32 pipe, resolving eigenvalues to about 1e-13 ||T|| between the FP32
+// sweeps and the FP64 ones.
+__device__ int sturm_count_df(const float2* a, const float2* b2, int m, float2 x) {
+  float2 pm1 = make_float2(1.0f, 0.0f);
+  float2 p = df_sub(a[0], x);
+  int cnt = 0;
+  unsigned sprev = 0u;
+  auto step_sign = [&](float2& v) {
+    unsigned bits = __float_as_uint(v.x);
+    if ((bits & 0x7fffffffu) == 0u) {
+      bits = 0x00800000u | ((sprev ^ 1u) << 31);  // +-FLT_MIN
+      v = make_float2(__uint_as_float(bits), 0.0f);
+    }
+    const unsigned sb = bits >> 31;
+    cnt += (int)(sb ^ sprev);
+    sprev = sb;
+  };
+  step_sign(p);
+#pragma unroll 4
+  for (int i = 1; i < m; ++i) {
+    const float2 t = df_mul(b2[i - 1], pm1);
+    float2 pn = df_sub(df_mul(df_sub(a[i], x), p), t);
+    step_sign(pn);
+    pm1 = p;
+    p = pn;
+    if ((i & 3) == 0) {
+      const int ep = (int)((__float_as_uint(p.x) >> 23) & 0xff);
+      const int eq = (int)((__float_as_uint(pm1.x) >> 23) & 0xff);
+      const int e = ep > eq ? ep : eq;
+      if (e > 127 + 40 || e < 127 - 40) {
+        const float sc = __uint_as_float((unsigned)(254 - e) << 23);  // 2^(127 - e)
+        p = make_float2(p.x * sc, p.y * sc);
+        pm1 = make_float2(pm1.x * sc, pm1.y * sc);
+      }
+    }
+  }
+  return cnt;
+}
+
 // Smallest thread index of the block whose predicate holds (blockDim.x if
 // none); every thread gets the answer.
 __device__ int block_first(bool pred, int* s4) {
@@ -1072,6 +1112,8 @@ __global__ void bisect_cluster_kernel(const double* a, const double* b, int m, i
   double* sb2 = tsh_c + m;
   float* fa = reinterpret_cast<float*>(tsh_c + 2 * m);
   float* fb2 = fa + m;
+  float2* da = reinterpret_cast<float2*>(tsh_c + 3 * m);
+  float2* db2 = da + m;
   __shared__ double s_lo, s_hi, s_sc;
   __shared__ int s4[32];
   __shared__ int s_first;  // this CTA's first crossing in the current sweep (128: none)
@@ -1110,6 +1152,8 @@ __global__ void bisect_cluster_kernel(const double* a, const double* b, int m, i
     sb2[i] = bi * bi;
     fa[i] = (float)ai;
     fb2[i] = (float)(bi * bi);
+    da[i] = df_split(ai);
+    db2[i] = df_split(bi * bi);
   }
   __syncthreads();
   const int t = m - 1 - c;  // index from the smallest
@@ -1145,6 +1189,21 @@ __global__ void bisect_cluster_kernel(const double* a, const double* b, int m, i
   }
   lo = fmax(lo0, lo - 4e-6);
   hi = fmin(hi0, hi + 4e-6);
+  // double-float sweeps down to 2^-40 of ||T|| (<= 1 here), the bracket then
+  // widened by that much (far above the double-float count's error), so that
+  // the FP64 sweeps below start within a few multisections of the end
+  for (int it = 0; it < 8; ++it) {
+    if (hi - lo <= 9.1e-13) break;
+    const double x = lo + (hi - lo) * (double)(g + 1) * inv_n;
+    const int F = cluster_first(sturm_count_df(da, db2, m, df_split(x)) > t);
+    const double nhi = F < np ? lo + (hi - lo) * (double)(F + 1) * inv_n : hi;
+    const double nlo = F > 0 ? lo + (hi - lo) * (double)F * inv_n : lo;
+    if (!(nlo < nhi)) break;
+    lo = nlo;
+    hi = nhi;
+  }
+  lo = fmax(lo0, lo - 9.1e-13);
+  hi = fmin(hi0, hi + 9.1e-13);
   // down to a few ulps of the eigenvalue, or to 4 eps ||T|| (the accuracy of
   // any backward-stable symmetric eigensolver) for eigenvalues much smaller
   // than ||T||
@@ -1309,6 +1368,155 @@ __global__ void inviter_kernel(const double* a, const double* b, int m, int k, c
   }
 }
 
+// The same inverse iteration with the O(m) recurrences (elimination and the
+// two solves, one thread's dependent chains) in double-float on T scaled by
+// a power of two (||T|| < 1; the eigenvector does not change): a dependent
+// step costs a few FP32 latencies instead of several FP64 ones.  The
+// normalisation and the orthogonalisation within a cluster stay FP64, on an
+// FP64 copy of the vector.  Needs 7 m doubles of shared memory.
+__global__ void inviter_df_kernel(const double* a, const double* b, int m, int k, const double* theta,
+                                  const int* cstart, double* Y, int64_t ldy, const double* beta_last, double* res,
+                                  uint64_t key) {
+  const int c0 = blockIdx.x;
+  if (cstart[c0] != c0) return;
+  __shared__ double sh[32];
+  __shared__ double sdot[1024];
+  extern __shared__ double idf_s[];
+  float2* d = reinterpret_cast<float2*>(idf_s);
+  float2* du = d + m;
+  float2* dl = du + m;
+  float2* du2 = dl + m;
+  float2* y = du2 + m;
+  double* y64 = idf_s + 5 * m;
+  int* piv = reinterpret_cast<int*>(idf_s + 6 * m);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  __shared__ double s_sc, s_inv;
+  __shared__ float s_tiny;
+  if (warp == 0) {
+    double tn = 0.0;
+    for (int i = lane; i < m; i += 32)
+      tn = fmax(tn, fabs(a[i]) + (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < m - 1 ? fabs(b[i]) : 0.0));
+    for (int o = 16; o > 0; o >>= 1) tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
+    if (lane == 0) {
+      int E = 0;
+      if (tn > 0.0) frexp(tn, &E);
+      const double sc = ldexp(1.0, -E);  // exact
+      s_sc = sc;
+      s_tiny = (float)(DBL_EPSILON * fmax(tn * sc, DBL_MIN));
+    }
+  }
+  __syncthreads();
+  const double sc = s_sc;
+  const float tiny = s_tiny;
+  const double beta_m = *beta_last;
+  for (int c = c0; c < k && cstart[c] == c0; ++c) {
+    const double th = theta[c] * sc;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      d[i] = df_split(a[i] * sc - th);
+      if (i < m - 1) {
+        du[i] = df_split(b[i] * sc);
+        dl[i] = du[i];
+      }
+      du2[i] = make_float2(0.0f, 0.0f);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int i = 0; i < m - 1; ++i) {
+        if (fabsf(d[i].x) >= fabsf(dl[i].x)) {
+          piv[i] = 0;
+          if (fabsf(d[i].x) < tiny) d[i] = make_float2(d[i].x < 0.0f ? -tiny : tiny, 0.0f);
+          const float2 f = df_mul(dl[i], df_rcp(d[i]));
+          dl[i] = f;
+          d[i + 1] = df_sub(d[i + 1], df_mul(f, du[i]));
+        } else {
+          piv[i] = 1;
+          const float2 f = df_mul(d[i], df_rcp(dl[i]));
+          d[i] = dl[i];
+          dl[i] = f;
+          const float2 tmp = du[i];
+          du[i] = d[i + 1];
+          d[i + 1] = df_sub(tmp, df_mul(f, d[i + 1]));
+          if (i < m - 2) {
+            du2[i] = du[i + 1];
+            du[i + 1] = df_mul(make_float2(-f.x, -f.y), du[i + 1]);
+          }
+        }
+      }
+      if (fabsf(d[m - 1].x) < tiny) d[m - 1] = make_float2(d[m - 1].x < 0.0f ? -tiny : tiny, 0.0f);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) d[i] = df_rcp(d[i]);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) y[i] = df_split(1.0 + 0.25 * rnd_sym(key + c, i));
+    __syncthreads();
+    for (int it = 0; it < 2; ++it) {
+      if (threadIdx.x == 0) {
+        for (int i = 0; i < m - 1; ++i) {
+          if (piv[i]) {
+            const float2 t = y[i];
+            y[i] = y[i + 1];
+            y[i + 1] = t;
+          }
+          y[i + 1] = df_sub(y[i + 1], df_mul(dl[i], y[i]));
+        }
+        y[m - 1] = df_mul(y[m - 1], d[m - 1]);
+        if (m >= 2) y[m - 2] = df_mul(df_sub(y[m - 2], df_mul(du[m - 2], y[m - 1])), d[m - 2]);
+        for (int i = m - 3; i >= 0; --i)
+          y[i] = df_mul(df_sub(df_sub(y[i], df_mul(du[i], y[i + 1])), df_mul(du2[i], y[i + 2])), d[i]);
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < m; i += blockDim.x) y64[i] = df_val(y[i]);
+      __syncthreads();
+      if (warp == 0) {
+        double mx = 0.0;
+        for (int i = lane; i < m; i += 32) mx = fmax(mx, fabs(y64[i]));
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) sh[0] = mx > 0.0 ? 1.0 / mx : 1.0;
+      }
+      __syncthreads();
+      const double inv = sh[0];
+      __syncthreads();
+      for (int i = threadIdx.x; i < m; i += blockDim.x) y64[i] *= inv;
+      __syncthreads();
+      // orthogonalise against the cluster's earlier vectors (twice)
+      const int nprev = c - c0;
+      for (int pass = 0; pass < 2 && nprev > 0; ++pass) {
+        for (int pb = 0; pb < nprev; pb += 1024) {
+          const int cnt = nprev - pb < 1024 ? nprev - pb : 1024;
+          for (int pi = warp; pi < cnt; pi += nwarp) {
+            const double* yp = Y + (int64_t)(c0 + pb + pi) * ldy;
+            double dot = 0.0;
+            for (int i = lane; i < m; i += 32) dot = fma(yp[i], y64[i], dot);
+            dot = warp_sum(dot);
+            if (lane == 0) sdot[pi] = dot;
+          }
+          __syncthreads();
+          for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            double sacc = 0.0;
+            for (int pi = 0; pi < cnt; ++pi) sacc = fma(sdot[pi], Y[(int64_t)(c0 + pb + pi) * ldy + i], sacc);
+            y64[i] -= sacc;
+          }
+          __syncthreads();
+        }
+      }
+      double nn = 0.0;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) nn = fma(y64[i], y64[i], nn);
+      nn = block_sum(nn, sh);
+      if (threadIdx.x == 0) s_inv = nn > 0.0 ? rsqrt64(nn) : 0.0;
+      __syncthreads();
+      const double inv2 = s_inv;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        y64[i] *= inv2;
+        y[i] = df_split(y64[i]);
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) res[c] = fabs(beta_m * y64[m - 1]);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) Y[(int64_t)c * ldy + i] = y64[i];
+    __syncthreads();
+  }
+}
+
+
 // Final per-column pass: evals, zero null columns, scale 1/sqrt(N mu),
 // sign so that the largest-magnitude entry is positive.  One block of 1024
 // threads per column (up to 32 warps).
@@ -1394,6 +1602,8 @@ hess_status eig_kernel_attributes() {
       e = cudaFuncSetAttribute(inviter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEigSmemCap);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(lanczos_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEigSmemCap);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(inviter_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEigSmemCap);
   });
   if (e != cudaSuccess) return set_error(HESS_ERR_CUDA, "eigen kernel attributes: %s", cudaGetErrorString(e));
   return HESS_OK;
@@ -1409,7 +1619,7 @@ hess_status tridiag_topk(const double* a, const double* b, int m, int k, double*
                          double* scratch, cudaStream_t s) {
   HM_TRY(eig_kernel_attributes());
   const bool inv_g = (size_t)6 * m * sizeof(double) > kEigSmemCap;
-  const bool bis_g = (size_t)3 * m * sizeof(double) > kEigSmemCap;
+  const bool bis_g = (size_t)5 * m * sizeof(double) > kEigSmemCap;
   if ((inv_g || bis_g) && !scratch) return set_error(HESS_ERR_INVALID_ARG, "tridiagonal scratch missing");
   // a cluster of CTAs per eigenvalue (T in each CTA's shared memory), or,
   // when T does not fit shared memory, one block per eigenvalue over global
@@ -1418,7 +1628,7 @@ hess_status tridiag_topk(const double* a, const double* b, int m, int k, double*
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(kBisCta * k));
     cfg.blockDim = dim3(128);
-    cfg.dynamicSmemBytes = (size_t)3 * m * sizeof(double);
+    cfg.dynamicSmemBytes = (size_t)5 * m * sizeof(double);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1435,6 +1645,14 @@ hess_status tridiag_topk(const double* a, const double* b, int m, int k, double*
   // eigenvalues closer than 1e-6 of the largest share a cluster
   clusters_kernel<<<1, 32, 0, s>>>(theta, k, 1e-6, cstart);
   HM_LAUNCHED();
+  if ((size_t)7 * m * sizeof(double) <= kEigSmemCap) {
+    inviter_df_kernel<<<k, 256, (size_t)7 * m * sizeof(double), s>>>(a, b, m, k, theta, cstart, Y, ldy, beta_last,
+                                                                     res, key);
+    HM_LAUNCHED();
+    max_res_kernel<<<1, 32, 0, s>>>(res, k, theta, mx);
+    HM_LAUNCHED();
+    return HESS_OK;
+  }
   inviter_kernel<<<k, 256, inv_g ? 0 : (size_t)6 * m * sizeof(double), s>>>(a, b, m, k, theta, cstart, Y, ldy,
                                                                            beta_last, res, key,
                                                                            inv_g ? scratch : nullptr);
@@ -1592,6 +1810,15 @@ hess_status run_lz_df(hess_mlp* h, double* M, int k, LzBufs& b, int grid, int* m
       HM_CUDA(cudaLaunchCooperativeKernel((void*)lanczos_df_kernel, gl, kDfThreads, kargs, dyn, s));
       HM_LAUNCHED();
     }
+    // the tridiagonal eigenpairs of T_target are queued at once and read
+    // with the kernel's flags (one host round trip); after a breakdown or a
+    // failed barrier they are discarded
+    {
+      Tick t(h, HESS_K_TRIDIAG, 0.0, 0.0);
+      HM_TRY(tridiag_topk(b.alpha, b.beta, target, k, b.theta, b.cstart, b.Y, mcap, b.beta + (target - 1), b.rr,
+                          b.mx, key + 11, b.tri_scratch, s));
+    }
+    HM_CUDA(cudaMemcpyAsync(hp, b.mx, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaMemcpyAsync(reinterpret_cast<int*>(hp + 2), b.err, sizeof(int), cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaMemcpyAsync(reinterpret_cast<int*>(hp + 2) + 1, b.stop, sizeof(int), cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaStreamSynchronize(s));
@@ -1615,13 +1842,15 @@ hess_status run_lz_df(hess_mlp* h, double* M, int k, LzBufs& b, int grid, int* m
     } else {
       m = (int)target;
     }
-    {
+    if (stopped >= 0) {
+      // (reached only when the basis cannot grow: m == mcap) the eigenpairs
+      // of the complete T_m
       Tick t(h, HESS_K_TRIDIAG, 0.0, 0.0);
       HM_TRY(tridiag_topk(b.alpha, b.beta, m, k, b.theta, b.cstart, b.Y, mcap, b.beta + (m - 1), b.rr, b.mx,
                           key + 11, b.tri_scratch, s));
+      HM_CUDA(cudaMemcpyAsync(hp, b.mx, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      HM_CUDA(cudaStreamSynchronize(s));
     }
-    HM_CUDA(cudaMemcpyAsync(hp, b.mx, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    HM_CUDA(cudaStreamSynchronize(s));
     if (hp[0] <= 1e-10 * hp[1] || m >= N) {
       converged = true;
       break;
