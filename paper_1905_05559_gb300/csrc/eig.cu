@@ -493,6 +493,7 @@ constexpr int kDfThreads = 512;
 constexpr int kDfMaxGrid = 256;
 constexpr int kDfChunk = 256;     // entries per first-pass dot-product task
 constexpr int kDfMaxChunks = 8;   // so N <= 2048
+constexpr int kDfBatch = 16;      // partials loaded at once per thread
 constexpr int kDfWarps = kDfThreads / 32;
 constexpr int kDfRed = 1024;  // float2 scratch entries per block
 
@@ -665,16 +666,16 @@ __global__ void __launch_bounds__(kDfThreads, 1) lanczos_df_kernel(DfArgs a) {
         for (int t = tid; t < R * cn; t += kDfThreads) {
           const int r = t / cn, i = i0 + t % cn;
           float s = 0.0f, c = 0.0f;
-          // sixteen loads in flight per batch
-          for (int b0 = r; b0 < G; b0 += 16 * R) {
-            float2 v[16];
+          // kDfBatch loads in flight per batch
+          for (int b0 = r; b0 < G; b0 += kDfBatch * R) {
+            float2 v[kDfBatch];
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
+            for (int u = 0; u < kDfBatch; ++u) {
               const int b = b0 + u * R;
               v[u] = b < G ? a.part[(int64_t)b * a.pst + i] : make_float2(0.0f, 0.0f);
             }
 #pragma unroll
-            for (int u = 0; u < 16; ++u) df_acc(v[u], s, c);
+            for (int u = 0; u < kDfBatch; ++u) df_acc(v[u], s, c);
           }
           red[r * cn + (i - i0)] = df_norm(s, c);
         }
@@ -828,12 +829,20 @@ __global__ void df_to_f64_kernel(double* Q, int64_t n) {
 }
 
 // ------------------------------------------------------ back-projection ----
-// B[n][i k + c] = delta[n][i] u[n][c]  (N x Tout k)
-__global__ void bp_build_kernel(const double* D, const double* U, int64_t N, int Tout, int k, double* B) {
+// B[n][i k + c] = delta[n][i] u[n][c]  (N x Tout k), or its transpose
+// B[i k + c][n] (trans: the rows that the digit split reads along n)
+__global__ void bp_build_kernel(const double* D, const double* U, int64_t N, int Tout, int k, double* B, int trans) {
   const int64_t cols = (int64_t)Tout * k;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < N * cols;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t n = t / cols, r = t - n * cols;
+    int64_t n, r;
+    if (trans) {
+      r = t / N;
+      n = t - r * N;
+    } else {
+      n = t / cols;
+      r = t - n * cols;
+    }
     const int i = (int)(r / k), c = (int)(r - (int64_t)i * k);
     B[t] = D[n * Tout + i] * U[n * k + c];
   }
@@ -2169,13 +2178,14 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
     const int64_t Tin = net.T[wl - 1], Tout = net.T[wl], cols = Tout * k;
     Tick t(h, HESS_K_BACKPROJ, bp_mode[wl] ? 2.0 * N * Tout * k : 2.0 * N * (Tin + 1) * cols, 0.0);
     bp_build_kernel<<<(unsigned)(cdiv(N * cols, 256) < 65536 ? cdiv(N * cols, 256) : 65536), 256, 0, s>>>(
-        c.d[wl], U, N, (int)Tout, k, Bf);
+        c.d[wl], U, N, (int)Tout, k, Bf, bp_mode[wl] == 1 ? 1 : 0);
     HM_LAUNCHED();
     if (bp_mode[wl] == 1) {
+      // (B transposed: the digit split reads its rows along n, coalesced)
       F64GemmScratch f2 = fb;
       f2.M = Tin;
       f2.Nn = cols < 256 ? cols : 256;
-      HM_TRY(f64_gemm_nt_tc(h, c.a[wl - 1], Tin, Bf, 1, cols, N, Rf, cols, 1, f2, s, cols));
+      HM_TRY(f64_gemm_nt_tc(h, c.a[wl - 1], Tin, Bf, N, 1, N, Rf, cols, 1, f2, s, cols));
     } else if (bp_mode[wl] == 2) {
       // R^T = B^T A: rows (i, c) of B^T against the Tin rows of A^T
       F64GemmScratch f2 = fb;
