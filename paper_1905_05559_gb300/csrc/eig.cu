@@ -23,11 +23,117 @@ namespace hm {
 namespace {
 
 // ------------------------------------------------------------ Gram matrix
-__global__ void gram_acc_kernel(double* M, const double* DD, const double* AA, int64_t n2,
-                                double invN) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2;
-       i += (int64_t)gridDim.x * blockDim.x)
-    M[i] += DD[i] * (AA[i] + 1.0) * invN;
+// One launch forms the layers' terms of M = G G^T / N (Eq. J with g_n =
+// [delta_n (x) a_n; delta_n] per weight layer),
+//   M[n][m] (+)= (1/N) sum_l (delta_{l,n} . delta_{l,m}) (a_{l,n} . a_{l,m} + 1),
+// in FP64.  A layer's activation product a_n . a_m is either summed from its
+// FP64 rows here (narrow layers) or, for at most one wide layer per launch,
+// taken from the exact-digit planes of its tensor-core product.  Each block
+// computes one kGt x kGt tile on or above the diagonal and writes it at
+// (n, m) and, through shared memory, at (m, n).
+struct GramLayer {
+  const double* D;  // delta rows, N x Tout
+  const double* A;  // activation rows, N x Tin; nullptr: the planes
+  int Tout, Tin;
+};
+struct GramArgs {
+  GramLayer l[kMaxLayers];
+  int nl;
+  F64SyrkPlanes pl;  // the wide layer's a . a (pl.T set)
+  int64_t N;
+  double invN;
+  int accumulate;
+};
+constexpr int kGt = 32;
+
+// out[i] = X_{n0 + ty + 8 i} . X_{m0 + tx} over the K columns of row-major X
+// (rows past N count as zero); sr and sc stage 32-column chunks, sc
+// transposed so that the lanes read consecutive words
+__device__ __forceinline__ void gram_tile_dot(const double* X, int K, int64_t N, int64_t n0, int64_t m0,
+                                              double (*sr)[kGt + 1], double (*sc)[kGt + 1], double out[4]) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) out[i] = 0.0;
+  for (int k0 = 0; k0 < K; k0 += kGt) {
+    for (int e = threadIdx.x; e < kGt * kGt; e += blockDim.x) {
+      const int r = e >> 5, kk = e & 31;
+      const int64_t kg = k0 + kk;
+      sr[r][kk] = (n0 + r < N && kg < K) ? X[(n0 + r) * K + kg] : 0.0;
+      sc[kk][r] = (m0 + r < N && kg < K) ? X[(m0 + r) * K + kg] : 0.0;
+    }
+    __syncthreads();
+    const int kc = K - k0 < kGt ? K - k0 : kGt;
+    for (int kk = 0; kk < kc; ++kk) {
+      const double b = sc[kk][tx];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) out[i] = fma(sr[ty + 8 * i][kk], b, out[i]);
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) gram_fused_kernel(const __grid_constant__ GramArgs g, double* M) {
+  __shared__ double sr[kGt][kGt + 1];
+  __shared__ double sc[kGt][kGt + 1];
+  const int64_t bi = blockIdx.y, bj = blockIdx.x;
+  if (bi > bj) return;
+  const int64_t N = g.N, n0 = bi * kGt, m0 = bj * kGt;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t m = m0 + tx;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int l = 0; l < g.nl; ++l) {
+    double dd[4], aa[4];
+    gram_tile_dot(g.l[l].D, g.l[l].Tout, N, n0, m0, sr, sc, dd);
+    if (g.l[l].A) {
+      gram_tile_dot(g.l[l].A, g.l[l].Tin, N, n0, m0, sr, sc, aa);
+    } else {
+      // the planes hold entries (r, c >= r); a diagonal tile reads its lower
+      // half transposed
+#pragma unroll 1
+      for (int i = 0; i < 4; ++i) {
+        const int64_t n = n0 + ty + 8 * i;
+        aa[i] = 0.0;
+        if (n >= N || m >= N) continue;
+        const int64_t r = n <= m ? n : m, c = n <= m ? m : n;
+        const size_t at = (size_t)r * N + c, plane = (size_t)N * N;
+        float v[kMaxSyrkPlanes];
+#pragma unroll
+        for (int j = 0; j < kMaxSyrkPlanes; ++j) v[j] = j < g.pl.count ? g.pl.T[j * plane + at] : 0.0f;
+        double sv = 0.0;
+#pragma unroll
+        for (int j = 0; j < kMaxSyrkPlanes; ++j)
+          if (j < g.pl.count) sv = fma((double)v[j], g.pl.w[j], sv);
+        sv = ldexp(sv, g.pl.ex[r] + g.pl.ex[c]);
+        aa[i] = g.pl.part ? g.pl.part[r * g.pl.ldp + c] + sv : sv;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i] = fma(dd[i], aa[i] + 1.0, acc[i]);
+  }
+  // sr holds the tile for the mirrored store
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = ty + 8 * i;
+    const int64_t n = n0 + r;
+    const double v = acc[i] * g.invN;
+    sr[r][tx] = v;
+    if (n < N && m < N) {
+      double* o = M + n * N + m;
+      *o = g.accumulate ? *o + v : v;
+    }
+  }
+  if (bi == bj) return;
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = ty + 8 * i;  // row m0 + r of M, column n0 + tx
+    const int64_t mm = m0 + r, nn = n0 + tx;
+    if (mm < N && nn < N) {
+      double* o = M + mm * N + nn;
+      const double v = sr[tx][r];
+      *o = g.accumulate ? *o + v : v;
+    }
+  }
 }
 
 
@@ -2060,78 +2166,66 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   // (mode 1: rows of A^T against B in column groups; mode 2, for narrow
   // layers: rows of B^T against A, the transposed product; mode 0: the SIMT
   // FP64 GEMM, for products too small to repay the digit splitting)
-  int64_t cols_max = 0, r_max = 0, tout_max = 0, m_tc = 0, n_tc = 0;
+  int64_t cols_max = 0, r_max = 0, tout_max = 0;
+  F64GemmNeed need;
   int bp_mode[kMaxLayers] = {};
   for (int wl = 1; wl <= L - 1; ++wl) {
     const int64_t Tin = net.T[wl - 1], Tout = net.T[wl], cols = Tout * k;
     const int64_t gw = cols < 256 ? cols : 256;
     cols_max = cols > cols_max ? cols : cols_max;
-    r_max = Tin * cols > r_max ? Tin * cols : r_max;
+    r_max = (Tin + 1) * cols > r_max ? (Tin + 1) * cols : r_max;
     tout_max = Tout > tout_max ? Tout : tout_max;
     if (2.0 * N * Tin * cols < 5e7) continue;
-    if (f64_gemm_nt_tc_eligible(h, Tin, gw, N)) {
+    if (f64_gemm_nt_tc_eligible(h, Tin + 1, gw, N, cols)) {
       bp_mode[wl] = 1;
-      m_tc = Tin > m_tc ? Tin : m_tc;
-      n_tc = gw > n_tc ? gw : n_tc;
+      f64_gemm_nt_need(Tin + 1, gw, N, cols, need);
     } else if (Tin <= 256 && f64_gemm_nt_tc_eligible(h, cols, Tin, N)) {
       bp_mode[wl] = 2;
-      m_tc = cols > m_tc ? cols : m_tc;
-      n_tc = Tin > n_tc ? Tin : n_tc;
+      f64_gemm_nt_need(cols, Tin, N, Tin, need);
     }
   }
   double* Bf = ar.take<double>(N * cols_max);
   double* Rf = ar.take<double>(r_max);
   double* Rb = ar.take<double>(tout_max * k);
   F64GemmScratch fb;
-  if (m_tc) plan_f64_gemm_nt(ar, m_tc, n_tc, N, fb);
+  if (need.M) plan_f64_gemm_nt(ar, need, fb);
   if (dry) return HESS_OK;
   cudaStream_t s = h->stream;
 
-  // 1. Gram matrix, factored by layer
+  // 1. Gram matrix, factored by layer: the wide layers' activation products
+  // as exact-digit tensor-core planes, every other term (and the planes'
+  // combine) in fused FP64 launches, one per wide layer
   {
-    Tick t(h, HESS_K_GRAM, 0.0, 0.0);
-    HM_TRY(fill(M, N * N, 0.0, s));
-  }
-  for (int wl = 1; wl <= L - 1; ++wl) {
-    const int Tin = net.T[wl - 1], Tout = net.T[wl];
-    Tick tg(h, HESS_K_GRAM, (double)N * (N + 1) * Tout, 0.0);
-    Gemm<double> g;
-    g.M = (int)N;
-    g.N = (int)N;
-    g.K = Tout;
-    g.A = c.d[wl];
-    g.sam = Tout;
-    g.sak = 1;
-    g.B = c.d[wl];
-    g.sbk = 1;
-    g.sbn = Tout;
-    g.C = DD;
-    g.scm = N;
-    g.scn = 1;
-    g.upper = 1;
-    HM_TRY(gemm(g, s));
-    if (ktc && Tin >= 128 && Tin <= ktc) {
-      tg.stop();
-      HM_TRY(f64_syrk_tc(h, c.a[wl - 1], Tin, Tin, AA, N, fs, s));
-    } else {
-      tg.set_work((double)N * (N + 1) * (Tout + Tin), 0.0);
-      g.K = Tin;
-      g.A = c.a[wl - 1];
-      g.sam = Tin;
-      g.B = c.a[wl - 1];
-      g.sbn = Tin;
-      g.C = AA;
-      HM_TRY(gemm(g, s));
-      tg.stop();
+    GramArgs ga{};
+    ga.N = N;
+    ga.invN = 1.0 / (double)N;
+    double fl = 0.0;
+    int launches = 0;
+    auto flush = [&]() -> hess_status {
+      Tick t(h, HESS_K_GRAM, fl, 0.0);
+      ga.accumulate = launches > 0 ? 1 : 0;
+      const unsigned nb = (unsigned)cdiv(N, kGt);
+      gram_fused_kernel<<<dim3(nb, nb), 256, 0, s>>>(ga, M);
+      HM_LAUNCHED();
+      ++launches;
+      ga.nl = 0;
+      ga.pl = F64SyrkPlanes{};
+      fl = 0.0;
+      return HESS_OK;
+    };
+    for (int wl = 1; wl <= L - 1; ++wl) {
+      const int Tin = net.T[wl - 1], Tout = net.T[wl];
+      const bool wide = ktc && Tin >= 128 && Tin <= ktc;
+      GramLayer gl{c.d[wl], wide ? nullptr : c.a[wl - 1], Tout, Tin};
+      fl += (double)N * (N + 1) * (Tout + (wide ? 0 : Tin));
+      if (wide) {
+        if (ga.pl.T) HM_TRY(flush());
+        HM_TRY(f64_syrk_tc(h, c.a[wl - 1], Tin, Tin, AA, N, fs, s, &ga.pl));
+        if (!ga.pl.T) return set_error(HESS_ERR_UNSUPPORTED, "exact-digit Gram term: no planes left to combine");
+      }
+      ga.l[ga.nl++] = gl;
     }
-    Tick ta(h, HESS_K_GRAM, 0.0, 0.0);
-    gram_acc_kernel<<<(unsigned)(cdiv(N * N, 256) < 65536 ? cdiv(N * N, 256) : 65536), 256, 0, s>>>(
-        M, DD, AA, N * N, 1.0 / (double)N);
-    HM_LAUNCHED();
-  }
-  {
-    Tick t(h, HESS_K_GRAM, 0.0, 0.0);
-    HM_TRY(mirror_upper(M, N, N, s));
+    HM_TRY(flush());
   }
 
   if (after_gram) HM_TRY((*after_gram)());
@@ -2180,12 +2274,16 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
     bp_build_kernel<<<(unsigned)(cdiv(N * cols, 256) < 65536 ? cdiv(N * cols, 256) : 65536), 256, 0, s>>>(
         c.d[wl], U, N, (int)Tout, k, Bf, bp_mode[wl] == 1 ? 1 : 0);
     HM_LAUNCHED();
+    // the bias rows: row Tin of R (a row of ones appended to A^T), or their
+    // own product
+    const double* Rbl = Rb;
     if (bp_mode[wl] == 1) {
       // (B transposed: the digit split reads its rows along n, coalesced)
       F64GemmScratch f2 = fb;
-      f2.M = Tin;
+      f2.M = Tin + 1;
       f2.Nn = cols < 256 ? cols : 256;
-      HM_TRY(f64_gemm_nt_tc(h, c.a[wl - 1], Tin, Bf, N, 1, N, Rf, cols, 1, f2, s, cols));
+      HM_TRY(f64_gemm_nt_tc(h, c.a[wl - 1], Tin, Bf, N, 1, N, Rf, cols, 1, f2, s, cols, Tin));
+      Rbl = Rf + Tin * cols;
     } else if (bp_mode[wl] == 2) {
       // R^T = B^T A: rows (i, c) of B^T against the Tin rows of A^T
       F64GemmScratch f2 = fb;
@@ -2208,23 +2306,25 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
       g.scn = 1;
       HM_TRY(gemm(g, s));
     }
-    Gemm<double> g;
-    g.M = (int)Tout;
-    g.N = k;
-    g.K = (int)N;
-    g.A = c.d[wl];
-    g.sam = 1;
-    g.sak = Tout;
-    g.B = U;
-    g.sbk = k;
-    g.sbn = 1;
-    g.C = Rb;
-    g.scm = k;
-    g.scn = 1;
-    HM_TRY(gemm(g, s));
+    if (bp_mode[wl] != 1) {
+      Gemm<double> g;
+      g.M = (int)Tout;
+      g.N = k;
+      g.K = (int)N;
+      g.A = c.d[wl];
+      g.sam = 1;
+      g.sak = Tout;
+      g.B = U;
+      g.sbk = k;
+      g.sbn = 1;
+      g.C = Rb;
+      g.scm = k;
+      g.scn = 1;
+      HM_TRY(gemm(g, s));
+    }
     const int64_t per = (Tin + 1) * Tout;
     bp_scatter_kernel<<<(unsigned)(cdiv(per * k, 256) < 65536 ? cdiv(per * k, 256) : 65536), 256, 0, s>>>(
-        Rf, Rb, (int)Tin, (int)Tout, k, evecs_d, P, net.woff[wl - 1], net.boff[wl - 1]);
+        Rf, Rbl, (int)Tin, (int)Tout, k, evecs_d, P, net.woff[wl - 1], net.boff[wl - 1]);
     HM_LAUNCHED();
   }
   {

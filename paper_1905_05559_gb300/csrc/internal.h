@@ -376,36 +376,67 @@ struct F64SyrkScratch {
 // 128 <= n <= 16384.
 bool f64_syrk_tc_eligible(hess_mlp* h, int64_t n, int64_t K);
 void plan_f64_syrk(Arena& ar, int64_t n, int64_t K, F64SyrkScratch& fs);
+// The digit planes of the last group of an exact-digit A A^T, left for the
+// caller to combine: entry (r, c), c >= r, of the product is
+//   part[r ldp + c] (when part is set) + 2^(ex[r] + ex[c]) s,
+//   s = fma(T_j, w_j, s) over j = 0 .. count - 1 in turn from s = 0,
+// T_j = T[j n^2 + r n + c] (exact FP32 integers).
+constexpr int kMaxSyrkPlanes = 36;  // digit pairs with d + d' <= 7
+struct F64SyrkPlanes {
+  const float* T = nullptr;
+  int count = 0;
+  double w[kMaxSyrkPlanes] = {};
+  const int* ex = nullptr;
+  const double* part = nullptr;  // the earlier groups, combined (C)
+  int64_t ldp = 0;
+};
 // Upper triangle (and diagonal) of C = A A^T for row-major FP64 A (n x K,
 // stride lda), accurate to FP64 rounding; C's lower triangle is not written.
+// With defer set, the last group of digit planes is not combined: its planes
+// are described there instead (C then holds the earlier groups only, and
+// defer->part points to it when there were any).
 hess_status f64_syrk_tc(hess_mlp* h, const double* A, int64_t lda, int64_t K, double* C, int64_t ldc,
-                        const F64SyrkScratch& fs, cudaStream_t s);
+                        const F64SyrkScratch& fs, cudaStream_t s, F64SyrkPlanes* defer = nullptr);
 
 // Scratch of an exact-digit FP64 product C = G^T B^T on the tensor cores
 // (G: K x M row-major, B rows of length K): digits of the rows of G^T
 // (side by side along K) and of B (reversed), exponents, the FP32 results of
 // a group of contractions, and the launch tables.
 struct F64GemmScratch {
-  int64_t M = 0, Nn = 0, ldk = 0;
+  int64_t M = 0, Nn = 0, Nt = 0, ldk = 0;
   __nv_bfloat16* DA = nullptr;
   __nv_bfloat16* RB = nullptr;
   int *exA = nullptr, *exB = nullptr;
+  unsigned long long* mxA = nullptr;  // column maxima of G (bits)
   float* T = nullptr;
-  int group = 1;
+  int64_t Mcap = 0;   // rows of A the plan has room for
+  int64_t tsize = 0;  // floats of T
+  int group = 1;      // room for digit jobs
+  int64_t ntiles = 0; // room for tiles
   tc::Job* jobs = nullptr;
   int4* tiles = nullptr;
 };
+// The scratch several products need (the largest of each part): add each
+// product with f64_gemm_nt_need, then take it with plan_f64_gemm_nt.  A
+// product run on the plan sets the scratch's M and Nn to its own.
+struct F64GemmNeed {
+  int64_t M = 0, Nt = 0, ldk = 0, t = 0, jobs = 0, tiles = 0;
+};
 // Usable when the tensor-core path is, K >= 128 (in segments of at most
 // 4096, each with exact FP32 sums), M >= 128 and 1 <= Nn <= 256 (one tile
-// column), and the digit jobs and their FP32 results fit their bounds.
-bool f64_gemm_nt_tc_eligible(hess_mlp* h, int64_t M, int64_t Nn, int64_t K);
-void plan_f64_gemm_nt(Arena& ar, int64_t M, int64_t Nn, int64_t K, F64GemmScratch& fs);
+// column per group of columns), and the FP32 results of the Nt columns
+// (default Nn) fit their bound.
+bool f64_gemm_nt_tc_eligible(hess_mlp* h, int64_t M, int64_t Nn, int64_t K, int64_t Nt = -1);
+void f64_gemm_nt_need(int64_t M, int64_t Nn, int64_t K, int64_t Nt, F64GemmNeed& nd);
+void plan_f64_gemm_nt(Arena& ar, const F64GemmNeed& nd, F64GemmScratch& fs);
 // C(m, c) = sum_k G[k][m] B(c, k), B(c, k) = B[c b_rs + k b_ks], written to
 // C[m scm + c scn], accurate to FP64 rounding; c < Nn_total (default: the
-// plan's Nn), taken in groups of the plan's Nn columns, G's digits formed once.
+// plan's Nn; at most its Nt), in groups of the plan's Nn columns, all in one
+// tensor-core launch.  With Mg < M, G has Mg columns and the rows m >= Mg of
+// G^T are all ones (C's row m then sums B's row over k).
 hess_status f64_gemm_nt_tc(hess_mlp* h, const double* G, int64_t ldg, const double* B, int64_t b_rs, int64_t b_ks,
                            int64_t K, double* C, int64_t scm, int64_t scn, const F64GemmScratch& fs, cudaStream_t s,
-                           int64_t Nn_total = -1);
+                           int64_t Nn_total = -1, int64_t Mg = -1);
 
 // Jobs and tiles gathered for one persistent launch.
 struct TcPlan {

@@ -1664,8 +1664,11 @@ struct JobWeightsFwd {
 // Row digits: fwd[r][d ldk + k] = q_d and rev[r][(7 - d) ldk + k] = q_d.  The
 // row's value scaled into (-1, 1) becomes the integer m = v 2^62 (dropping
 // below 2^-62), whose digits come off by rounding shifts.
+// pm: plane-major digits of groups of gn rows: row r of group g = r / gn
+// (ng = min(gn, n - g gn) rows) has digit d at pm + (g 8 gn + d ng + r - g gn) ldk.
 __global__ void digits_rows_kernel(const double* A, int64_t rs, int64_t ks, int64_t n, int64_t K, int64_t ldk,
-                                   __nv_bfloat16* fwd, __nv_bfloat16* rev, __nv_bfloat16* pm, int* ex) {
+                                   __nv_bfloat16* fwd, __nv_bfloat16* rev, __nv_bfloat16* pm, int* ex,
+                                   int64_t gn) {
   const int lane = threadIdx.x & 31;
   const int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
   if (r >= n) return;
@@ -1679,6 +1682,8 @@ __global__ void digits_rows_kernel(const double* A, int64_t rs, int64_t ks, int6
   const int64_t L = (int64_t)kDigits * ldk;
   __nv_bfloat16* fr = fwd ? fwd + r * L : nullptr;
   __nv_bfloat16* rr = rev ? rev + r * L : nullptr;
+  const int64_t grp = r / gn, rg = r - grp * gn, ng = n - grp * gn < gn ? n - grp * gn : gn;
+  __nv_bfloat16* pr = pm ? pm + (grp * kDigits * gn + rg) * ldk : nullptr;
   for (int64_t k = lane; k < ldk; k += 32) {
     long long m = k < K ? fixed62(a[k * ks], E) : 0ll;  // |m| <= 2^62
 #pragma unroll
@@ -1689,7 +1694,7 @@ __global__ void digits_rows_kernel(const double* A, int64_t rs, int64_t ks, int6
       const __nv_bfloat16 v = __int2bfloat16_rn((int)q);  // |q| <= 64: exact
       if (fr) fr[(int64_t)d * ldk + k] = v;
       if (rr) rr[(int64_t)(kDigits - 1 - d) * ldk + k] = v;
-      if (pm) pm[((int64_t)d * n + r) * ldk + k] = v;  // plane-major: rows (d, r)
+      if (pr) pr[(int64_t)d * ng * ldk + k] = v;  // plane-major: rows (d, r) of the group
     }
   }
 }
@@ -1701,54 +1706,67 @@ __device__ __forceinline__ unsigned long long max_abs_bits(unsigned long long m,
   return (a <= 0x7ff0000000000000ull && a > m) ? a : m;
 }
 
-// ex[c] for the columns of a row-major n x m FP64 array G (the rows of G^T):
-// the exponent E with max_r |G[r][c]| = f 2^E, f in [0.5, 1).  Block (32 x 8):
-// 32 adjacent columns, 8 slices of the rows, eight loads in flight per
-// thread; the maxima are taken on the integer pipe.
-__global__ void colmax_exp_kernel(const double* G, int64_t ldg, int64_t n, int64_t m, int* ex) {
+// mx[c] = max_r |G[r][c]| as FP64 bits (non-negative doubles order as their
+// bit patterns) for the columns of a row-major n x mg FP64 array G (the rows
+// of G^T); mx is zeroed beforehand.  Block (32 x 8): 32 adjacent columns, 8
+// slices of its share of the rows (gridDim.y shares), maxima on the integer
+// pipe, one atomic per column and block.
+__global__ void colmax_bits_kernel(const double* G, int64_t ldg, int64_t n, int64_t mg, unsigned long long* mx) {
   __shared__ unsigned long long red[8][33];
   const int64_t c = blockIdx.x * (int64_t)32 + threadIdx.x;
-  unsigned long long mx = 0ull;
-  if (c < m) {
-    int64_t r = threadIdx.y;
-    for (; r + 56 < n; r += 64) {
-      double v[8];
+  unsigned long long v = 0ull;
+  if (c < mg) {
+    const int64_t step = (int64_t)gridDim.y * 8;
+    int64_t r = (int64_t)blockIdx.y * 8 + threadIdx.y;
+    for (; r + 3 * step < n; r += 4 * step) {
+      double x[4];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = G[(r + 8 * u) * ldg + c];
+      for (int u = 0; u < 4; ++u) x[u] = G[(r + u * step) * ldg + c];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) mx = max_abs_bits(mx, v[u]);
+      for (int u = 0; u < 4; ++u) v = max_abs_bits(v, x[u]);
     }
-    for (; r < n; r += 8) mx = max_abs_bits(mx, G[r * ldg + c]);
+    for (; r < n; r += step) v = max_abs_bits(v, G[r * ldg + c]);
   }
-  red[threadIdx.y][threadIdx.x] = mx;
+  red[threadIdx.y][threadIdx.x] = v;
   __syncthreads();
-  if (threadIdx.y == 0 && c < m) {
-    for (int y = 1; y < 8; ++y) mx = red[y][threadIdx.x] > mx ? red[y][threadIdx.x] : mx;
-    const double v = __longlong_as_double((long long)mx);
-    int E = 0;
-    if (v > 0.0 && v <= DBL_MAX) frexp(v, &E);
-    ex[c] = E;
+  if (threadIdx.y == 0 && c < mg) {
+    for (int y = 1; y < 8; ++y) v = red[y][threadIdx.x] > v ? red[y][threadIdx.x] : v;
+    if (v) atomicMax(mx + c, v);
   }
 }
 
-// Digits of the rows of G^T (G row-major n x m): fwd[c][d ldk + r] = q_d of
-// G[r][c] scaled by 2^-ex[c]; rows r in [n, ldk) are zero.  A 128 x 32 tile
-// (128 rows r, 32 columns c) is read along c and written along r through
-// shared memory, four consecutive r per thread (8-byte stores).
-__global__ void digits_cols_kernel(const double* G, int64_t ldg, int64_t n, int64_t m, const int* ex, int64_t ldk,
-                                   __nv_bfloat16* fwd) {
+// The exponent E with max_r |G[r][c]| = f 2^E, f in [0.5, 1) (0 for a zero or
+// non-finite maximum); the all-ones columns c >= mg have E = 1.
+__device__ __forceinline__ int col_exp(const unsigned long long* mx, int64_t c, int64_t mg) {
+  if (c >= mg) return 1;
+  const double v = __longlong_as_double((long long)mx[c]);
+  int E = 0;
+  if (v > 0.0 && v <= DBL_MAX) frexp(v, &E);
+  return E;
+}
+
+// Digits of the rows of G^T (G row-major n x mg, then m - mg all-ones
+// columns): fwd[c][d ldk + r] = q_d of G[r][c] scaled by 2^-ex[c], with ex[c]
+// from the column maxima mx (written to ex by the blocks of the first row
+// tile); rows r in [n, ldk) are zero.  A 128 x 32 tile (128 rows r, 32
+// columns c) is read along c and written along r through shared memory, four
+// consecutive r per thread (8-byte stores).
+__global__ void digits_cols_kernel(const double* G, int64_t ldg, int64_t n, int64_t mg, int64_t m,
+                                   const unsigned long long* mx, int* ex, int64_t ldk, __nv_bfloat16* fwd) {
   __shared__ double t[128][33];
   const int64_t r0 = (int64_t)blockIdx.x * 128, c0 = (int64_t)blockIdx.y * 32;
   for (int y = threadIdx.y; y < 128; y += 8) {
     const int64_t r = r0 + y, c = c0 + threadIdx.x;
-    t[y][threadIdx.x] = (r < n && c < m) ? G[r * ldg + c] : 0.0;
+    t[y][threadIdx.x] = (r < n && c < m) ? (c < mg ? G[r * ldg + c] : 1.0) : 0.0;
   }
+  if (blockIdx.x == 0 && threadIdx.y == 0 && c0 + threadIdx.x < m)
+    ex[c0 + threadIdx.x] = col_exp(mx, c0 + threadIdx.x, mg);
   __syncthreads();
   const int64_t L = (int64_t)kDigits * ldk;
   for (int y = threadIdx.y; y < 32; y += 8) {
     const int64_t c = c0 + y, r = r0 + 4 * threadIdx.x;
     if (c >= m || r >= ldk) continue;  // ldk is a multiple of 64: r..r+3 all in range
-    const int e = ex[c];
+    const int e = col_exp(mx, c, mg);
     long long mm[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) mm[u] = fixed62(t[4 * threadIdx.x + u][y], e);
@@ -1768,40 +1786,44 @@ __global__ void digits_cols_kernel(const double* G, int64_t ldg, int64_t n, int6
   }
 }
 
-// Digit-major contractions of a general product: job j holds, for digit d_j
-// of A, the products with digits e in [e0_j, e1_j) of B side by side
-// (T_j: M x (e1_j - e0_j) Nn).  C(r, c) = 2^(eA_r + eB_c) sum over jobs and
-// their e with d + e <= 7 of 2^(-12 - 7(d + e)) T_j[r][(e - e0) Nn + c],
-// written to C[r scm + c scn] (added when accumulate is set).
-struct DigitJobs {
-  int d[2 * kDigits * kDigits], e0[2 * kDigits * kDigits], e1[2 * kDigits * kDigits];
-  int64_t off[2 * kDigits * kDigits];  // float offset of T_j (one per digit job and K segment)
-  double wt[2 * kDigits];              // 2^(-12 - 7w) by w = d + e
-  int count;
-};
-__global__ void combine_general_kernel(const float* T, int64_t M, int64_t Nn, DigitJobs dj, const int* exA,
-                                       const int* exB, double* C, int64_t scm, int64_t scn, int accumulate) {
+// Terms of a general digit product: the pairs (d, e), d + e <= 7, of a digit
+// of A and one of B, numbered d-major with e ascending, kTerms per K segment.
+constexpr int kTerms = kDigits * (kDigits + 1) / 2;
+__host__ __device__ constexpr int term_of(int d, int e) { return kDigits * d - d * (d - 1) / 2 + e; }
+__device__ __forceinline__ double pow2i(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+
+// C = the combined terms of a general digit product whose Nt columns come in
+// groups of Nn: group g (columns g Nn + c', c' < ng = min(Nn, Nt - g Nn)) keeps
+// row r's terms side by side at T + g M nt Nn + r nt ng + (s kTerms + t) ng + c'
+// (nt = nseg kTerms; s the K segment, t = term_of(d, e)).  The terms are
+// integers below 2^24 in magnitude (at most 4096 products of digits in
+// [-64, 64]), so those of one weight w = d + e are summed exactly as
+// integers, and only the eight weighted sums, smallest weight first, are FP64
+// operations: C(r, c) = 2^(exA_r + exB_c) sum_w 2^(-12 - 7 w) a_w, written to
+// C[r scm + c scn].
+__global__ void combine_terms_kernel(const float* T, int64_t M, int64_t Nn, int64_t Nt, int nseg, const int* exA,
+                                     const int* exB, double* C, int64_t scm, int64_t scn) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= M * Nn) return;
-  const int64_t r = idx / Nn, c = idx % Nn;
-  // The contraction results are integers below 2^24 in magnitude (at most
-  // 4096 products of digits in [-64, 64]), so the terms of one weight
-  // w = d + e are summed exactly as integers, and only the eight weighted
-  // sums, smallest weight first, are FP64 operations.
-  double s = 0.0;
-  for (int w = kDigits - 1; w >= 0; --w) {
-    long long a = 0;
-    for (int j = 0; j < dj.count; ++j) {
-      const int e = w - dj.d[j];  // d + e = w <= 7
-      if (e < dj.e0[j] || e >= dj.e1[j]) continue;
-      const int64_t wd = (int64_t)(dj.e1[j] - dj.e0[j]) * Nn;
-      a += __float2int_rn(T[dj.off[j] + r * wd + (int64_t)(e - dj.e0[j]) * Nn + c]);
-    }
-    s = fma((double)a, dj.wt[w], s);
+  if (idx >= M * Nt) return;
+  const int64_t r = idx / Nt, c = idx - r * Nt;
+  const int64_t g = c / Nn, cc = c - g * Nn;
+  const int64_t ng = Nt - g * Nn < Nn ? Nt - g * Nn : Nn;
+  const int64_t nt = (int64_t)nseg * kTerms;
+  const float* p = T + g * M * nt * Nn + r * nt * ng + cc;
+  long long a[kDigits] = {};
+  for (int sg = 0; sg < nseg; ++sg) {
+    float v[kTerms];
+#pragma unroll
+    for (int t = 0; t < kTerms; ++t) v[t] = p[(int64_t)(sg * kTerms + t) * ng];
+#pragma unroll
+    for (int d = 0; d < kDigits; ++d)
+#pragma unroll
+      for (int e = 0; e < kDigits - d; ++e) a[d + e] += __float2int_rn(v[term_of(d, e)]);
   }
-  s = ldexp(s, exA[r] + exB[c]);
-  double* o = C + r * scm + c * scn;
-  *o = accumulate ? *o + s : s;
+  double sum = 0.0;
+#pragma unroll
+  for (int w = kDigits - 1; w >= 0; --w) sum = fma((double)a[w], pow2i(-12 - 7 * w), sum);
+  C[r * scm + c * scn] = ldexp(sum, exA[r] + exB[c]);
 }
 
 using JobWeights = JobWeightsFwd;
@@ -1882,14 +1904,14 @@ void plan_f64_syrk(Arena& ar, int64_t n, int64_t K, F64SyrkScratch& fs) {
 }
 
 hess_status f64_syrk_tc(hess_mlp* h, const double* A, int64_t lda, int64_t K, double* C, int64_t ldc,
-                        const F64SyrkScratch& fs, cudaStream_t s) {
+                        const F64SyrkScratch& fs, cudaStream_t s, F64SyrkPlanes* defer) {
   using namespace tc;
   const int64_t n = fs.n, ldk = fs.ldk, L = (int64_t)kDigits * ldk;
   if (K > ldk) return set_error(HESS_ERR_INVALID_ARG, "exact-digit product: K %lld beyond its plan", (long long)K);
   {
     // (the only caller is the Gram matrix of the OPG eigen step)
     Tick t(h, HESS_K_GRAM, 0.0, 0.0);
-    digits_rows_kernel<<<(unsigned)cdiv(n, 8), 256, 0, s>>>(A, lda, 1, n, K, ldk, fs.D, fs.R, nullptr, fs.ex);
+    digits_rows_kernel<<<(unsigned)cdiv(n, 8), 256, 0, s>>>(A, lda, 1, n, K, ldk, fs.D, fs.R, nullptr, fs.ex, n);
     HM_LAUNCHED();
   }
   const std::vector<Contraction> cs = contractions(ldk);
@@ -1931,6 +1953,15 @@ hess_status f64_syrk_tc(hess_mlp* h, const double* A, int64_t lda, int64_t K, do
       HM_TRY(launch_jobs(h->sm_count, jobs.data(), (int)jobs.size(), tiles.data(), (int)tiles.size(), fs.jobs,
                          fs.tiles, false, h->err_dev, h->stage, s));
     }
+    if (defer && j1 == cs.size() && jw.count <= kMaxSyrkPlanes) {
+      defer->T = fs.T;
+      defer->count = jw.count;
+      for (int j = 0; j < jw.count; ++j) defer->w[j] = jw.w[j];
+      defer->ex = fs.ex;
+      defer->part = first ? nullptr : C;
+      defer->ldp = ldc;
+      break;
+    }
     {
       Tick t(h, HESS_K_GRAM, 0.0, 0.0);
       combine_upper_kernel<<<dim3((unsigned)cdiv(n, 256), (unsigned)n), 256, 0, s>>>(fs.T, n, jw, fs.ex, C, ldc,
@@ -1943,25 +1974,37 @@ hess_status f64_syrk_tc(hess_mlp* h, const double* A, int64_t lda, int64_t K, do
 }
 
 namespace {
-constexpr int kMaxDigitJobs = 2 * kDigits * kDigits;
 int64_t k_segments(int64_t ldk) { return cdiv(ldk, kExactK); }
+// Digit-major jobs of a general product with a group of ng columns: for each
+// digit d of A, the digits e < kDigits - d of B in runs of at most 256 / ng
+// (one tile column each); a run's terms are adjacent (term_of).
+struct DigitJob {
+  int d, e0, e1;
+};
+std::vector<DigitJob> digit_jobs(int64_t ng) {
+  const int per = (int)std::max<int64_t>(1, 256 / ng);
+  std::vector<DigitJob> out;
+  for (int d = 0; d < kDigits; ++d)
+    for (int e0 = 0; e0 < kDigits - d; e0 += per) out.push_back({d, e0, std::min(kDigits - d, e0 + per)});
+  return out;
+}
+int64_t gemm_groups(int64_t Nn, int64_t Nt) { return cdiv(Nt, Nn); }
+// jobs of all groups (each group's job count depends on its width)
+int64_t gemm_job_count(int64_t Nn, int64_t Nt, int64_t nseg) {
+  int64_t n = 0;
+  for (int64_t c0 = 0; c0 < Nt; c0 += Nn) n += (int64_t)digit_jobs(std::min(Nn, Nt - c0)).size() * nseg;
+  return n;
+}
 }  // namespace
 
-bool f64_gemm_nt_tc_eligible(hess_mlp* h, int64_t M, int64_t Nn, int64_t K) {
-  if (K < 128 || M < 128 || Nn < 1 || Nn > 256) return false;
+bool f64_gemm_nt_tc_eligible(hess_mlp* h, int64_t M, int64_t Nn, int64_t K, int64_t Nt) {
+  if (Nt < 0) Nt = Nn;
+  if (K < 128 || M < 128 || Nn < 1 || Nn > 256 || Nt < 1) return false;
   // K in segments of at most kExactK products (exact FP32 sums each); every
-  // digit job of every segment needs its own output
+  // term of every segment has its own FP32 result
   const int64_t ldk = (int64_t)align_up((size_t)K, tc::BK);
-  const int per = (int)std::max<int64_t>(1, 256 / Nn);
-  int64_t jobs = 0, cols = 0;
-  for (int d = 0; d < kDigits; ++d)
-    for (int e0 = 0; e0 < kDigits - d; e0 += per) {
-      ++jobs;
-      cols += (int64_t)(std::min(kDigits - d, e0 + per) - e0) * Nn;
-    }
-  const int64_t nseg = k_segments(ldk);
-  if (jobs * nseg > kMaxDigitJobs) return false;
-  if ((double)M * cols * nseg * 4.0 > 8.0 * (1 << 30)) return false;  // FP32 results within 8 GB
+  const int64_t nt = k_segments(ldk) * kTerms;
+  if ((double)M * nt * Nt * 4.0 > 8.0 * (1 << 30)) return false;  // FP32 results within 8 GB
   if (tc_available(h) != HESS_OK) {
     clear_error();
     return false;
@@ -1969,87 +2012,86 @@ bool f64_gemm_nt_tc_eligible(hess_mlp* h, int64_t M, int64_t Nn, int64_t K) {
   return true;
 }
 
-namespace {
-// Digit-major jobs of a general product: for each digit d of A, the digits e
-// < kDigits - d of B in groups of at most 256 / Nn (one tile column each).
-struct DigitJob {
-  int d, e0, e1;
-};
-std::vector<DigitJob> digit_jobs(int64_t Nn) {
-  const int per = (int)std::max<int64_t>(1, 256 / Nn);
-  std::vector<DigitJob> out;
-  for (int d = 0; d < kDigits; ++d)
-    for (int e0 = 0; e0 < kDigits - d; e0 += per) out.push_back({d, e0, std::min(kDigits - d, e0 + per)});
-  return out;
-}
-}  // namespace
-
-void plan_f64_gemm_nt(Arena& ar, int64_t M, int64_t Nn, int64_t K, F64GemmScratch& fs) {
+void f64_gemm_nt_need(int64_t M, int64_t Nn, int64_t K, int64_t Nt, F64GemmNeed& nd) {
   using namespace tc;
-  fs.M = M;
-  fs.Nn = Nn;
-  fs.ldk = (int64_t)align_up((size_t)K, BK);
-  fs.DA = ar.take<__nv_bfloat16>((int64_t)kDigits * M * fs.ldk);
-  fs.RB = ar.take<__nv_bfloat16>((int64_t)kDigits * Nn * fs.ldk);
-  fs.exA = ar.take<int>(M);
-  fs.exB = ar.take<int>(Nn);
-  const std::vector<DigitJob> js = digit_jobs(Nn);
-  const int64_t nseg = k_segments(fs.ldk);
-  int64_t cols = 0;
-  for (const DigitJob& j : js) cols += (int64_t)(j.e1 - j.e0) * Nn;
-  fs.group = (int)(js.size() * nseg);
-  fs.T = ar.take<float>(M * cols * nseg);
-  fs.jobs = ar.take<tc::Job>((int64_t)js.size() * nseg);
-  fs.tiles = ar.take<int4>((int64_t)js.size() * nseg * cdiv(M, BM));
+  if (Nt < 0) Nt = Nn;
+  const int64_t ldk = (int64_t)align_up((size_t)K, BK), nseg = k_segments(ldk);
+  const int64_t nj = gemm_job_count(Nn, Nt, nseg);
+  nd.M = std::max(nd.M, M);
+  nd.Nt = std::max(nd.Nt, Nt);
+  nd.ldk = std::max(nd.ldk, ldk);
+  nd.t = std::max(nd.t, M * nseg * kTerms * Nt);
+  nd.jobs = std::max(nd.jobs, nj);
+  nd.tiles = std::max(nd.tiles, nj * cdiv(M, BM));
+}
+
+void plan_f64_gemm_nt(Arena& ar, const F64GemmNeed& nd, F64GemmScratch& fs) {
+  fs.M = nd.M;
+  fs.Mcap = nd.M;
+  fs.Nt = nd.Nt;
+  fs.ldk = nd.ldk;
+  fs.DA = ar.take<__nv_bfloat16>((int64_t)kDigits * nd.M * nd.ldk);
+  fs.RB = ar.take<__nv_bfloat16>((int64_t)kDigits * nd.Nt * nd.ldk);
+  fs.exA = ar.take<int>(nd.M);
+  fs.mxA = ar.take<unsigned long long>(nd.M);
+  fs.exB = ar.take<int>(nd.Nt);
+  fs.T = ar.take<float>(nd.t);
+  fs.tsize = nd.t;
+  fs.group = (int)nd.jobs;
+  fs.ntiles = nd.tiles;
+  fs.jobs = ar.take<tc::Job>(nd.jobs);
+  fs.tiles = ar.take<int4>(nd.tiles);
 }
 
 hess_status f64_gemm_nt_tc(hess_mlp* h, const double* G, int64_t ldg, const double* B, int64_t b_rs, int64_t b_ks,
                            int64_t K, double* C, int64_t scm, int64_t scn, const F64GemmScratch& fs, cudaStream_t s,
-                           int64_t Nn_total) {
+                           int64_t Nn_total, int64_t Mg) {
   using namespace tc;
-  const int64_t M = fs.M, ldk = fs.ldk, L = (int64_t)kDigits * ldk;
-  const int64_t Nt = Nn_total < 0 ? fs.Nn : Nn_total;
-  if (K > ldk) return set_error(HESS_ERR_INVALID_ARG, "exact-digit product: K %lld beyond its plan", (long long)K);
-  // (the only caller is the back-projection of the OPG eigen step)
-  Tick tp(h, HESS_K_BACKPROJ, 0.0, 0.0);
-  // A = G^T: rows are the columns of G, split once; B: plane-major digits,
-  // rows (e, c), one group of at most fs.Nn rows at a time
-  colmax_exp_kernel<<<(unsigned)cdiv(M, 32), dim3(32, 8), 0, s>>>(G, ldg, K, M, fs.exA);
-  HM_LAUNCHED();
-  digits_cols_kernel<<<dim3((unsigned)cdiv(ldk, 128), (unsigned)cdiv(M, 32)), dim3(32, 8), 0, s>>>(
-      G, ldg, K, M, fs.exA, ldk, fs.DA);
-  HM_LAUNCHED();
-  tp.stop();
-  const int64_t nseg = k_segments(ldk);
-  for (int64_t c0 = 0; c0 < Nt; c0 += fs.Nn) {
-    const int64_t Nn = std::min<int64_t>(fs.Nn, Nt - c0);
-    {
-      Tick tb(h, HESS_K_BACKPROJ, 0.0, 0.0);
-      digits_rows_kernel<<<(unsigned)cdiv(Nn, 8), 256, 0, s>>>(B + c0 * b_rs, b_rs, b_ks, Nn, K, ldk, nullptr, nullptr,
-                                                               fs.RB, fs.exB);
-      HM_LAUNCHED();
-    }
-    const std::vector<DigitJob> js = digit_jobs(Nn);
-    if ((int64_t)js.size() * nseg > kMaxDigitJobs)
-      return set_error(HESS_ERR_INVALID_ARG, "exact-digit product: too many digit jobs");
-    std::vector<Job> jobs;
-    std::vector<int4> tiles;
-    DigitJobs dj{};
-    dj.count = (int)(js.size() * nseg);
-    for (int w = 0; w < 2 * kDigits; ++w) dj.wt[w] = ldexp(1.0, -12 - 7 * w);
-    int64_t off = 0;
+  const int64_t M = fs.M, Nn = fs.Nn;
+  const int64_t Nt = Nn_total < 0 ? Nn : Nn_total;
+  const int64_t mg = Mg < 0 ? M : Mg;  // columns of G; rows [mg, M) of A are ones
+  if (mg < 1 || mg > M) return set_error(HESS_ERR_INVALID_ARG, "exact-digit product: bad column count of G");
+  // this product's digit rows have its own length (the plan's is the longest)
+  const int64_t ldk = (int64_t)align_up((size_t)K, BK), L = (int64_t)kDigits * ldk;
+  const int64_t nseg = k_segments(ldk), nt = nseg * kTerms;
+  const int64_t nj = gemm_job_count(Nn, Nt, nseg);
+  if (M > fs.Mcap || ldk > fs.ldk || Nt > fs.Nt || M * nt * Nt > fs.tsize || nj > fs.group || nj * cdiv(M, BM) > fs.ntiles)
+    return set_error(HESS_ERR_INVALID_ARG, "exact-digit product: %lld x %lld x %lld beyond its plan", (long long)M,
+                     (long long)Nt, (long long)K);
+  {
+    // (the only caller is the back-projection of the OPG eigen step)
+    Tick tp(h, HESS_K_BACKPROJ, 0.0, 0.0);
+    // A = G^T: rows are the columns of G; B: rows (e, c') of each group of Nn
+    // columns, plane-major; both split once
+    HM_CUDA(cudaMemsetAsync(fs.mxA, 0, (size_t)M * sizeof(unsigned long long), s));
+    const unsigned ry = (unsigned)std::max<int64_t>(1, std::min<int64_t>(16, cdiv(K, 64)));
+    colmax_bits_kernel<<<dim3((unsigned)cdiv(mg, 32), ry), dim3(32, 8), 0, s>>>(G, ldg, K, mg, fs.mxA);
+    HM_LAUNCHED();
+    digits_cols_kernel<<<dim3((unsigned)cdiv(ldk, 128), (unsigned)cdiv(M, 32)), dim3(32, 8), 0, s>>>(
+        G, ldg, K, mg, M, fs.mxA, fs.exA, ldk, fs.DA);
+    HM_LAUNCHED();
+    digits_rows_kernel<<<(unsigned)cdiv(Nt, 8), 256, 0, s>>>(B, b_rs, b_ks, Nt, K, ldk, nullptr, nullptr, fs.RB,
+                                                             fs.exB, Nn);
+    HM_LAUNCHED();
+  }
+  std::vector<Job> jobs;
+  std::vector<int4> tiles;
+  for (int64_t c0 = 0, g = 0; c0 < Nt; c0 += Nn, ++g) {
+    const int64_t ng = std::min(Nn, Nt - c0);
+    float* Tg = fs.T + g * M * nt * Nn;
+    const __nv_bfloat16* RBg = fs.RB + g * kDigits * Nn * ldk;
+    const std::vector<DigitJob> js = digit_jobs(ng);
     for (int64_t sg = 0; sg < nseg; ++sg) {
       const int64_t k0 = sg * kExactK;
       const int64_t inner = std::min<int64_t>(kExactK, ldk - k0);  // a multiple of 64
-      for (size_t jj = 0; jj < js.size(); ++jj) {
-        const DigitJob& g = js[jj];
+      for (const DigitJob& dj : js) {
         const int j = (int)jobs.size();
-        const int64_t cols = (int64_t)(g.e1 - g.e0) * Nn;
+        const int64_t cols = (int64_t)(dj.e1 - dj.e0) * ng;
         const int BN = (int)align_up((size_t)cols, 16);
         Job job{};
-        HM_TRY(make_block_map(&job.a_hi, fs.DA + (int64_t)g.d * ldk + k0, inner, L, M, BM));
+        HM_TRY(make_block_map(&job.a_hi, fs.DA + (int64_t)dj.d * ldk + k0, inner, L, M, BM));
         job.a_lo = job.a_hi;
-        HM_TRY(make_block_map(&job.b_hi, fs.RB + (int64_t)g.e0 * Nn * ldk + k0, inner, ldk, cols, BN));
+        HM_TRY(make_block_map(&job.b_hi, RBg + (int64_t)dj.e0 * ng * ldk + k0, inner, ldk, cols, BN));
         job.b_lo = job.b_hi;
         job.BN = BN;
         job.nkb = (int)(inner / BK);
@@ -2058,29 +2100,24 @@ hess_status f64_gemm_nt_tc(hess_mlp* h, const double* G, int64_t ldg, const doub
         job.Nn = cols;
         job.mode = 3;
         job.scale = 1.0f;
-        job.out = fs.T + off;
-        job.ldo = cols;
+        job.out = Tg + (sg * kTerms + term_of(dj.d, dj.e0)) * ng;
+        job.ldo = nt * ng;
         for (int64_t tm = 0; tm < cdiv(M, BM); ++tm) tiles.push_back(make_int4(j, (int)tm, 0, 0));
         jobs.push_back(job);
-        dj.d[j] = g.d;
-        dj.e0[j] = g.e0;
-        dj.e1[j] = g.e1;
-        dj.off[j] = off;
-        off += M * cols;
       }
     }
-    {
-      double fl = 0.0;
-      for (const Job& jb : jobs) fl += 2.0 * (double)jb.M * jb.Nn * (double)jb.nkb * BK;
-      Tick t(h, HESS_K_DIGITS, fl, 0.0);
-      HM_TRY(launch_jobs(h->sm_count, jobs.data(), (int)jobs.size(), tiles.data(), (int)tiles.size(), fs.jobs,
-                         fs.tiles, false, h->err_dev, h->stage, s));
-    }
-    Tick tc(h, HESS_K_BACKPROJ, 0.0, 0.0);
-    combine_general_kernel<<<(unsigned)cdiv(M * Nn, 256), 256, 0, s>>>(fs.T, M, Nn, dj, fs.exA, fs.exB,
-                                                                       C + c0 * scn, scm, scn, 0);
-    HM_LAUNCHED();
   }
+  {
+    double fl = 0.0;
+    for (const Job& jb : jobs) fl += 2.0 * (double)jb.M * jb.Nn * (double)jb.nkb * BK;
+    Tick t(h, HESS_K_DIGITS, fl, 0.0);
+    HM_TRY(launch_jobs(h->sm_count, jobs.data(), (int)jobs.size(), tiles.data(), (int)tiles.size(), fs.jobs,
+                       fs.tiles, false, h->err_dev, h->stage, s));
+  }
+  Tick tc(h, HESS_K_BACKPROJ, 0.0, 0.0);
+  combine_terms_kernel<<<(unsigned)cdiv(M * Nt, 256), 256, 0, s>>>(fs.T, M, Nn, Nt, (int)nseg, fs.exA, fs.exB, C,
+                                                                   scm, scn);
+  HM_LAUNCHED();
   return HESS_OK;
 }
 

@@ -50,3 +50,20 @@ def test_opg_eig_through_exact_digit_products(hm, spread):
         if gaps[c] > 1e-4 * lam_ref[0]:
             assert abs(abs(Q[c] @ Q_ref[:, c]) - 1.0) <= 1e-10
         assert np.linalg.norm(M @ Q[c] - lam[c] * Q[c]) <= 1e-9 * lam_ref[0]
+
+
+@pytest.mark.parametrize("widths,N,seed", [([200, 30, 10], 600, 22), ([64, 40, 10], 1024, 23)],
+                         ids=["groups-ragged-ones-row", "transposed-narrow"])
+def test_back_projection_digit_routes(hm, widths, N, seed):
+    """The back-projection's exact-digit products: [200, 30, 10] at N = 600
+    takes the first layer's R = A^T B (B of 30 x 12 = 360 columns: a group of
+    256 and a ragged group of 104) with a row of ones appended to A^T for the
+    bias rows; [64, 40, 10] at N = 1024 takes the transposed product of a
+    narrow layer (480 rows against 64 columns)."""
+    from eigcheck import check_eig
+    pb = make_problem(widths, ["tanh"], N, seed, "normal", "uniform")
+    net = hm.HessMLP(pb.widths, pb.acts, pb.omega)
+    k = 12
+    lam, Q, _ = net.opg_topk_eig(dev(pb.X), dev(pb.Y), k, "fp64")
+    Gr = O.per_example_grads(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
+    check_eig(lam.cpu().numpy(), Q.cpu().numpy(), Gr, k, 1e-12, 1e-10)
