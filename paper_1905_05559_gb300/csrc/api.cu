@@ -121,8 +121,10 @@ hess_status take_sticky_error(hess_mlp* h) {
   return HESS_OK;
 }
 
-hess_status stage_copy(PinnedStage& st, const void* const* src, const size_t* bytes, void* const* dst, int n,
+hess_status stage_copy(PinnedStage& ring, const void* const* src, const size_t* bytes, void* const* dst, int n,
                        cudaStream_t s) {
+  PinnedSlot& st = ring.slot[ring.next];
+  ring.next = (ring.next + 1) % kStageSlots;
   size_t total = 0;
   for (int i = 0; i < n; ++i) total += align_up(bytes[i], 256);
   if (st.ev) {
@@ -153,13 +155,15 @@ hess_status stage_copy(PinnedStage& st, const void* const* src, const size_t* by
   return HESS_OK;
 }
 
-void stage_free(PinnedStage& st) {
-  if (st.ev) {
-    cudaEventSynchronize(st.ev);
-    cudaEventDestroy(st.ev);
+void stage_free(PinnedStage& ring) {
+  for (PinnedSlot& st : ring.slot) {
+    if (st.ev) {
+      cudaEventSynchronize(st.ev);
+      cudaEventDestroy(st.ev);
+    }
+    if (st.p) cudaFreeHost(st.p);
   }
-  if (st.p) cudaFreeHost(st.p);
-  st = PinnedStage{};
+  ring = PinnedStage{};
   cudaGetLastError();
 }
 

@@ -13,6 +13,7 @@
 
 #include <atomic>
 #include <cfloat>
+#include <climits>
 #include <mutex>
 
 #include "devmath.cuh"
@@ -23,119 +24,292 @@ namespace hm {
 namespace {
 
 // ------------------------------------------------------------ Gram matrix
-// One launch forms the layers' terms of M = G G^T / N (Eq. J with g_n =
-// [delta_n (x) a_n; delta_n] per weight layer),
-//   M[n][m] (+)= (1/N) sum_l (delta_{l,n} . delta_{l,m}) (a_{l,n} . a_{l,m} + 1),
-// in FP64.  A layer's activation product a_n . a_m is either summed from its
-// FP64 rows here (narrow layers) or, for at most one wide layer per launch,
-// taken from the exact-digit planes of its tensor-core product.  Each block
-// computes one kGt x kGt tile on or above the diagonal and writes it at
-// (n, m) and, through shared memory, at (m, n).
-struct GramLayer {
+// M = G G^T / N in factored form (Eq. J, with g_n = [delta_n (x) a_n; delta_n]
+// for each weight layer):
+//   M[n][m] = (1/N) sum_l (delta_{l,n} . delta_{l,m}) (a_{l,n} . a_{l,m} + 1).
+// The dot products are formed in double-float arithmetic (devmath.cuh; FP64
+// issues at 1/64 of the FP32 rate on this part) from rows scaled by powers of
+// two, a wide layer's a . a from the exact-digit planes of its tensor-core
+// product.  With e_D, e_A the exponents of a row's largest delta and
+// activation, u_l = e_D + max(e_A, 0) and r_n = max_l u_{l,n}, every layer's
+// term of entry (n, m) is 2^(r_n + r_m) times a double-float number of modest
+// size: the scaled dots times 2^(p_{A,n} + p_{A,m}) and 2^(p_{D,n} + p_{D,m}),
+// p_A = e_D + e_A - r <= 0, p_D = e_D - r <= 0.  (Below 2^-126 a factor counts
+// as zero: such a term is under 2^-126 of the larger diagonal entries.)
+
+// The exponent E of max |x| = f 2^E, f in [0.5, 1); 0 for a zero or non-finite
+// maximum (the digit split's rule, so that both agree on a wide layer).
+__device__ __forceinline__ int row_exp(double mx) {
+  int E = 0;
+  if (mx > 0.0 && mx <= DBL_MAX) frexp(mx, &E);
+  return E;
+}
+// x 2^e for |e| <= 2100 (two exact power-of-two factors, each in range)
+__device__ __forceinline__ double scale2(double x, int e) {
+  const int e1 = e / 2, e2 = e - e1;
+  return x * __longlong_as_double((long long)(1023 + e1) << 52) * __longlong_as_double((long long)(1023 + e2) << 52);
+}
+// 2^x as FP32 for x <= 127; 0 below 2^-126
+__device__ __forceinline__ float pow2f(int x) { return x < -126 ? 0.0f : __int_as_float((x + 127) << 23); }
+
+struct GramPrepLayer {
   const double* D;  // delta rows, N x Tout
-  const double* A;  // activation rows, N x Tin; nullptr: the planes
+  const double* A;  // activation rows, N x Tin
+  int Tout, Tin;
+  float2* XD;       // delta rows times 2^-e_D, double-float, N x Tout
+  float2* XA;       // activation rows times 2^-e_A, N x Tin (nullptr: a wide layer, not split)
+  int *pD, *pA, *eA;  // per row: e_D - r, e_D + e_A - r, e_A
+};
+struct GramPrepArgs {
+  GramPrepLayer l[kMaxLayers];
+  int nl;
+  int64_t N;
+  double invN;
+  int* r;
+  unsigned long long* maxdiag;  // FP64 bits of max_n M[n][n] (zeroed beforehand)
+};
+
+// One warp per example row n: exponents, r_n, the FP64 diagonal entry (for the
+// scale of the double-float output), and the split rows.
+__global__ void gram_prep_kernel(const __grid_constant__ GramPrepArgs g) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (n >= g.N) return;
+  int r = INT_MIN;
+  double diag = 0.0;
+  for (int l = 0; l < g.nl; ++l) {
+    const GramPrepLayer& L = g.l[l];
+    const double* d = L.D + n * L.Tout;
+    const double* a = L.A + n * L.Tin;
+    double md = 0.0, ma = 0.0, sd = 0.0, sa = 0.0;
+    for (int k = lane; k < L.Tout; k += 32) {
+      const double v = d[k];
+      md = fmax(md, fabs(v));
+      sd = fma(v, v, sd);
+    }
+    for (int k = lane; k < L.Tin; k += 32) {
+      const double v = a[k];
+      ma = fmax(ma, fabs(v));
+      sa = fma(v, v, sa);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
+      ma = fmax(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+    }
+    sd = warp_sum(sd);
+    sa = warp_sum(sa);
+    const int eD = row_exp(md), eA = row_exp(ma);
+    const int u = eD + (eA > 0 ? eA : 0);
+    r = u > r ? u : r;
+    diag = fma(sd, sa + 1.0, diag);
+    if (lane == 0) {
+      L.pD[n] = eD;  // (relative to r below)
+      L.eA[n] = eA;
+    }
+  }
+  if (lane == 0) {
+    g.r[n] = r;
+    const double v = diag * g.invN;
+    if (v > 0.0) atomicMax(g.maxdiag, (unsigned long long)__double_as_longlong(v));
+  }
+  __syncwarp();
+  for (int l = 0; l < g.nl; ++l) {
+    const GramPrepLayer& L = g.l[l];
+    const int eD = L.pD[n], eA = L.eA[n];
+    __syncwarp();
+    if (lane == 0) {
+      L.pD[n] = eD - r;
+      L.pA[n] = eD + eA - r;
+    }
+    const double* d = L.D + n * L.Tout;
+    for (int k = lane; k < L.Tout; k += 32) L.XD[n * L.Tout + k] = df_split(scale2(d[k], -eD));
+    if (L.XA) {
+      const double* a = L.A + n * L.Tin;
+      for (int k = lane; k < L.Tin; k += 32) L.XA[n * L.Tin + k] = df_split(scale2(a[k], -eA));
+    }
+  }
+}
+
+struct GramLayer {
+  const float2* D;  // split delta rows (N x Tout)
+  const float2* A;  // split activation rows (N x Tin); nullptr: the planes
+  const int *pD, *pA, *eA;
   int Tout, Tin;
 };
 struct GramArgs {
   GramLayer l[kMaxLayers];
   int nl;
   F64SyrkPlanes pl;  // the wide layer's a . a (pl.T set)
+  const int* r;
+  const unsigned long long* maxdiag;
   int64_t N;
   double invN;
   int accumulate;
+  int df_out;   // 1: write 2^-E M as double-float pairs, E = the exponent of max M[n][n]; 0: FP64 M
+  int* escale;  // receives E (df_out)
 };
 constexpr int kGt = 32;
 
-// out[i] = X_{n0 + ty + 8 i} . X_{m0 + tx} over the K columns of row-major X
-// (rows past N count as zero); sr and sc stage 32-column chunks, sc
-// transposed so that the lanes read consecutive words
-__device__ __forceinline__ void gram_tile_dot(const double* X, int K, int64_t N, int64_t n0, int64_t m0,
-                                              double (*sr)[kGt + 1], double (*sc)[kGt + 1], double out[4]) {
+// (s[i], c[i]) = X_{n0 + ty + 8 i} . X_{m0 + tx} over the K columns of the
+// split rows X (rows past N count as zero); sr and sc stage 32-column chunks,
+// sc transposed so that the lanes read consecutive words.
+__device__ __forceinline__ void gram_tile_dot(const float2* X, int K, int64_t N, int64_t n0, int64_t m0,
+                                              float2 (*sr)[kGt + 1], float2 (*sc)[kGt + 1], float s[4], float c[4]) {
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) out[i] = 0.0;
+  for (int i = 0; i < 4; ++i) s[i] = c[i] = 0.0f;
   for (int k0 = 0; k0 < K; k0 += kGt) {
     for (int e = threadIdx.x; e < kGt * kGt; e += blockDim.x) {
-      const int r = e >> 5, kk = e & 31;
+      const int rr = e >> 5, kk = e & 31;
       const int64_t kg = k0 + kk;
-      sr[r][kk] = (n0 + r < N && kg < K) ? X[(n0 + r) * K + kg] : 0.0;
-      sc[kk][r] = (m0 + r < N && kg < K) ? X[(m0 + r) * K + kg] : 0.0;
+      sr[rr][kk] = (n0 + rr < N && kg < K) ? X[(n0 + rr) * K + kg] : make_float2(0.0f, 0.0f);
+      sc[kk][rr] = (m0 + rr < N && kg < K) ? X[(m0 + rr) * K + kg] : make_float2(0.0f, 0.0f);
     }
     __syncthreads();
     const int kc = K - k0 < kGt ? K - k0 : kGt;
     for (int kk = 0; kk < kc; ++kk) {
-      const double b = sc[kk][tx];
+      const float2 b = sc[kk][tx];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) out[i] = fma(sr[ty + 8 * i][kk], b, out[i]);
+      for (int i = 0; i < 4; ++i) df_mac(sr[ty + 8 * i][kk], b, s[i], c[i]);
     }
     __syncthreads();
   }
 }
 
-__global__ void __launch_bounds__(256) gram_fused_kernel(const __grid_constant__ GramArgs g, double* M) {
-  __shared__ double sr[kGt][kGt + 1];
-  __shared__ double sc[kGt][kGt + 1];
+// One block per kGt x kGt tile on or above the diagonal, written at (n, m)
+// and, through shared memory, at (m, n); a diagonal tile writes its upper
+// half and mirrors it, so M is exactly symmetric.
+__global__ void __launch_bounds__(256, 3) gram_fused_kernel(const __grid_constant__ GramArgs g, void* Mout) {
+  __shared__ float2 sr[kGt][kGt + 1];
+  __shared__ float2 sc[kGt][kGt + 1];
   const int64_t bi = blockIdx.y, bj = blockIdx.x;
   if (bi > bj) return;
   const int64_t N = g.N, n0 = bi * kGt, m0 = bj * kGt;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int64_t m = m0 + tx;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const bool diag_tile = bi == bj;
+  float2 acc[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc[i] = make_float2(0.0f, 0.0f);
   for (int l = 0; l < g.nl; ++l) {
-    double dd[4], aa[4];
-    gram_tile_dot(g.l[l].D, g.l[l].Tout, N, n0, m0, sr, sc, dd);
-    if (g.l[l].A) {
-      gram_tile_dot(g.l[l].A, g.l[l].Tin, N, n0, m0, sr, sc, aa);
+    const GramLayer& L = g.l[l];
+    float ds[4], dc[4], as[4], ac[4];
+    gram_tile_dot(L.D, L.Tout, N, n0, m0, sr, sc, ds, dc);
+    if (L.A) {
+      gram_tile_dot(L.A, L.Tin, N, n0, m0, sr, sc, as, ac);
     } else {
-      // the planes hold entries (r, c >= r); a diagonal tile reads its lower
-      // half transposed
+      // the planes hold the entries (n, m >= n) of the scaled product
 #pragma unroll 1
       for (int i = 0; i < 4; ++i) {
         const int64_t n = n0 + ty + 8 * i;
-        aa[i] = 0.0;
-        if (n >= N || m >= N) continue;
-        const int64_t r = n <= m ? n : m, c = n <= m ? m : n;
-        const size_t at = (size_t)r * N + c, plane = (size_t)N * N;
-        float v[kMaxSyrkPlanes];
+        float S = 0.0f, C = 0.0f;
+        if (n < N && m < N && (!diag_tile || n <= m)) {
+          const size_t at = (size_t)n * N + m, plane = (size_t)N * N;
+          // the planes of one weight 2^(-12 - 7 w) are summed exactly as
+          // integers (each below 2^24), then added as a double-float pair;
+          // loads in batches of 12
+          constexpr int kB = 12;
+          int a = 0;
 #pragma unroll
-        for (int j = 0; j < kMaxSyrkPlanes; ++j) v[j] = j < g.pl.count ? g.pl.T[j * plane + at] : 0.0f;
-        double sv = 0.0;
+          for (int j0 = 0; j0 < kMaxSyrkPlanes; j0 += kB) {
+            if (j0 >= g.pl.count) break;
+            float v[kB];
 #pragma unroll
-        for (int j = 0; j < kMaxSyrkPlanes; ++j)
-          if (j < g.pl.count) sv = fma((double)v[j], g.pl.w[j], sv);
-        sv = ldexp(sv, g.pl.ex[r] + g.pl.ex[c]);
-        aa[i] = g.pl.part ? g.pl.part[r * g.pl.ldp + c] + sv : sv;
+            for (int j = 0; j < kB; ++j) v[j] = j0 + j < g.pl.count ? g.pl.T[(j0 + j) * plane + at] : 0.0f;
+#pragma unroll
+            for (int j = 0; j < kB; ++j) {
+              const int jj = j0 + j;
+              if (jj >= g.pl.count) break;
+              a += __float2int_rn(v[j]);
+              const int wn = jj + 1 < kMaxSyrkPlanes ? g.pl.wexp[jj + 1] : -1;
+              if (jj + 1 == g.pl.count || wn != g.pl.wexp[jj]) {
+                const float hi = __int2float_rn(a);
+                const float lo = __int2float_rn(a - __float2int_rz(hi));
+                const float pw = pow2f(-12 - 7 * g.pl.wexp[jj]);
+                float t, e;
+                two_sum(S, hi * pw, t, e);
+                S = t;
+                C += e + lo * pw;
+                a = 0;
+              }
+            }
+          }
+          if (g.pl.part) {
+            // earlier groups of planes, combined in FP64
+            const float2 p = df_split(scale2(g.pl.part[n * g.pl.ldp + m], -(L.eA[n] + L.eA[m])));
+            float t, e;
+            two_sum(S, p.x, t, e);
+            S = t;
+            C += e + p.y;
+          }
+        }
+        as[i] = S;
+        ac[i] = C;
       }
     }
+    const int pDm = L.pD[m < N ? m : 0], pAm = L.pA[m < N ? m : 0];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) acc[i] = fma(dd[i], aa[i] + 1.0, acc[i]);
-  }
-  // sr holds the tile for the mirrored store
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int r = ty + 8 * i;
-    const int64_t n = n0 + r;
-    const double v = acc[i] * g.invN;
-    sr[r][tx] = v;
-    if (n < N && m < N) {
-      double* o = M + n * N + m;
-      *o = g.accumulate ? *o + v : v;
+    for (int i = 0; i < 4; ++i) {
+      const int64_t n = n0 + ty + 8 * i;
+      const int pDn = L.pD[n < N ? n : 0], pAn = L.pA[n < N ? n : 0];
+      const float pa = pow2f(pAn + pAm), pd = pow2f(pDn + pDm);
+      const float2 aa = df_norm(as[i], ac[i]);
+      const float2 t = df_add(make_float2(aa.x * pa, aa.y * pa), make_float2(pd, 0.0f));
+      acc[i] = df_add(acc[i], df_mul(df_norm(ds[i], dc[i]), t));
     }
   }
-  if (bi == bj) return;
+  // the tile in shared memory (8-byte entries: a double-float pair or an FP64
+  // value), then the direct and the mirrored stores
+  unsigned long long(*so)[kGt + 1] = reinterpret_cast<unsigned long long(*)[kGt + 1]>(sr);
+  const float2 invN = df_split(g.invN);
+  int E = 0;
+  if (g.df_out) {
+    E = row_exp(__longlong_as_double((long long)*g.maxdiag));
+    if (bi == 0 && bj == 0 && threadIdx.x == 0) *g.escale = E;
+  }
+  const int rm = g.r[m < N ? m : 0];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int rr = ty + 8 * i;
+    const int64_t n = n0 + rr;
+    const int rn = g.r[n < N ? n : 0];
+    const float2 v = df_mul(acc[i], invN);
+    unsigned long long bits;
+    if (g.df_out) {
+      // |2^-E M[n][m]| < 1: a large exponent comes with a tiny v
+      int x = rn + rm - E;
+      x = x < -250 ? -250 : (x > 250 ? 250 : x);
+      const float p1 = pow2f(x / 2), p2 = pow2f(x - x / 2);
+      const float2 o = make_float2(v.x * p1 * p2, v.y * p1 * p2);
+      bits = (unsigned long long)__double_as_longlong(*reinterpret_cast<const double*>(&o));
+    } else {
+      bits = (unsigned long long)__double_as_longlong(scale2(df_val(v), rn + rm));
+    }
+    so[rr][tx] = bits;
+  }
   __syncthreads();
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int r = ty + 8 * i;  // row m0 + r of M, column n0 + tx
-    const int64_t mm = m0 + r, nn = n0 + tx;
-    if (mm < N && nn < N) {
-      double* o = M + mm * N + nn;
-      const double v = sr[tx][r];
+  auto store = [&](int64_t row, int64_t col, unsigned long long bits) {
+    if (g.df_out) {
+      float2* o = reinterpret_cast<float2*>(Mout) + row * N + col;
+      const float2 v = *reinterpret_cast<const float2*>(&bits);
+      *o = g.accumulate ? df_add(*o, v) : v;
+    } else {
+      double* o = reinterpret_cast<double*>(Mout) + row * N + col;
+      const double v = __longlong_as_double((long long)bits);
       *o = g.accumulate ? *o + v : v;
     }
+  };
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int rr = ty + 8 * i;
+    const int64_t n = n0 + rr;
+    if (n < N && m < N && (!diag_tile || rr <= tx)) store(n, m, so[rr][tx]);
+    // mirrored: row m0 + rr, column n0 + tx holds entry (n0 + tx, m0 + rr)
+    const int64_t mm = m0 + rr, nn = n0 + tx;
+    if (mm < N && nn < N && (!diag_tile || tx < rr)) store(mm, nn, so[tx][rr]);
   }
 }
-
 
 // ------------------------------------------------ cooperative Lanczos
 // All Lanczos steps of one extension run in a single cooperative launch (all
@@ -1858,7 +2032,8 @@ int eig_lanczos_blocks(hess_mlp* h, int64_t n, int k) {
 // The Lanczos process of run_lz with the double-float kernel; M (FP64, n x n)
 // is overwritten by its scaled hi/lo pairs.  On return b.Q holds q_0 ..
 // q_{m-1} in FP64 (rows of n), as run_lz leaves them.
-hess_status run_lz_df(hess_mlp* h, double* M, int k, LzBufs& b, int grid, int* m_out, bool* converged_out) {
+hess_status run_lz_df(hess_mlp* h, double* M, int k, LzBufs& b, int grid, int* m_out, bool* converged_out,
+                      bool m_split) {
   const int64_t N = b.n, mcap = b.mcap;
   cudaStream_t s = h->stream;
   const uint64_t key = 0x5DEECE66Dull;
@@ -1869,11 +2044,13 @@ hess_status run_lz_df(hess_mlp* h, double* M, int k, LzBufs& b, int grid, int* m
   {
     // (preparation of M and the start vector: counted with the Gram matrix)
     Tick t(h, HESS_K_GRAM, 0.0, 0.0);
-    df_scale_kernel<<<1, 1024, 0, s>>>(M, N, b.escale);
-    HM_LAUNCHED();
-    const int64_t n2 = N * N;
-    df_split_kernel<<<(unsigned)(cdiv(n2, 256) < 4096 ? cdiv(n2, 256) : 4096), 256, 0, s>>>(M, n2, b.escale);
-    HM_LAUNCHED();
+    if (!m_split) {
+      df_scale_kernel<<<1, 1024, 0, s>>>(M, N, b.escale);
+      HM_LAUNCHED();
+      const int64_t n2 = N * N;
+      df_split_kernel<<<(unsigned)(cdiv(n2, 256) < 4096 ? cdiv(n2, 256) : 4096), 256, 0, s>>>(M, n2, b.escale);
+      HM_LAUNCHED();
+    }
     df_start_kernel<<<1, 1024, 0, s>>>(Q, N, key);
     HM_LAUNCHED();
   }
@@ -2160,6 +2337,27 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
     if (f64_syrk_tc_eligible(h, N, net.T[wl - 1]) && net.T[wl - 1] > ktc) ktc = net.T[wl - 1];
   F64SyrkScratch fs;
   if (ktc) plan_f64_syrk(ar, N, ktc, fs);
+  // the Gram kernels' split rows and per-row exponents
+  GramPrepArgs gp{};
+  gp.nl = L - 1;
+  gp.N = N;
+  gp.invN = 1.0 / (double)N;
+  for (int wl = 1; wl <= L - 1; ++wl) {
+    const int Tin = net.T[wl - 1], Tout = net.T[wl];
+    const bool wide = ktc && Tin >= 128 && Tin <= ktc;
+    GramPrepLayer& pl = gp.l[wl - 1];
+    pl.D = c.d[wl];
+    pl.A = c.a[wl - 1];
+    pl.Tout = Tout;
+    pl.Tin = Tin;
+    pl.XD = ar.take<float2>(N * Tout);
+    pl.XA = wide ? nullptr : ar.take<float2>(N * Tin);
+    pl.pD = ar.take<int>(N);
+    pl.pA = ar.take<int>(N);
+    pl.eA = ar.take<int>(N);
+  }
+  gp.r = ar.take<int>(N);
+  gp.maxdiag = ar.take<unsigned long long>(1);
   // and so does the back-projection G^T U (K = N)
   // and so do the back-projection's wide layers: per weight layer,
   // R = A^T B with B[n][(i, c)] = delta[n][i] u[n][c] (K = N)
@@ -2193,12 +2391,24 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   cudaStream_t s = h->stream;
 
   // 1. Gram matrix, factored by layer: the wide layers' activation products
-  // as exact-digit tensor-core planes, every other term (and the planes'
-  // combine) in fused FP64 launches, one per wide layer
+  // as exact-digit tensor-core planes, everything else in double-float in
+  // fused launches (one per wide layer), written as the Lanczos kernel's
+  // double-float input when that kernel runs
+  const int dfg = df_grid(h, N, mcap);
+  {
+    Tick t(h, HESS_K_GRAM, 0.0, 0.0);
+    HM_CUDA(cudaMemsetAsync(gp.maxdiag, 0, sizeof(unsigned long long), s));
+    gram_prep_kernel<<<(unsigned)cdiv(N, 8), 256, 0, s>>>(gp);
+    HM_LAUNCHED();
+  }
   {
     GramArgs ga{};
     ga.N = N;
     ga.invN = 1.0 / (double)N;
+    ga.r = gp.r;
+    ga.maxdiag = gp.maxdiag;
+    ga.df_out = dfg > 0 ? 1 : 0;
+    ga.escale = lb.escale;
     double fl = 0.0;
     int launches = 0;
     auto flush = [&]() -> hess_status {
@@ -2214,13 +2424,13 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
       return HESS_OK;
     };
     for (int wl = 1; wl <= L - 1; ++wl) {
-      const int Tin = net.T[wl - 1], Tout = net.T[wl];
-      const bool wide = ktc && Tin >= 128 && Tin <= ktc;
-      GramLayer gl{c.d[wl], wide ? nullptr : c.a[wl - 1], Tout, Tin};
-      fl += (double)N * (N + 1) * (Tout + (wide ? 0 : Tin));
+      const GramPrepLayer& pl = gp.l[wl - 1];
+      const bool wide = pl.XA == nullptr;
+      GramLayer gl{pl.XD, pl.XA, pl.pD, pl.pA, pl.eA, pl.Tout, pl.Tin};
+      fl += (double)N * (N + 1) * (pl.Tout + (wide ? 0 : pl.Tin));
       if (wide) {
         if (ga.pl.T) HM_TRY(flush());
-        HM_TRY(f64_syrk_tc(h, c.a[wl - 1], Tin, Tin, AA, N, fs, s, &ga.pl));
+        HM_TRY(f64_syrk_tc(h, c.a[wl - 1], pl.Tin, pl.Tin, AA, N, fs, s, &ga.pl));
         if (!ga.pl.T) return set_error(HESS_ERR_UNSUPPORTED, "exact-digit Gram term: no planes left to combine");
       }
       ga.l[ga.nl++] = gl;
@@ -2231,9 +2441,8 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   if (after_gram) HM_TRY((*after_gram)());
   int m = 0;
   bool converged = false;
-  const int dfg = df_grid(h, N, mcap);
   if (dfg > 0) {
-    HM_TRY(run_lz_df(h, M, k, lb, dfg, &m, &converged));
+    HM_TRY(run_lz_df(h, M, k, lb, dfg, &m, &converged, true));
   } else {
     HM_TRY(run_lz(h, M, k, lb, &m, &converged));
   }

@@ -101,12 +101,20 @@ struct TimingRec {
 
 namespace hm {
 // Pinned host staging for the small tables a launch reads (jobs, tiles), so
-// that their copies are asynchronous.  The buffer is reused once its previous
-// copy has completed (event).
-struct PinnedStage {
+// that their copies are asynchronous.  A slot's buffer is reused once its
+// previous copy has completed (event).
+struct PinnedSlot {
   char* p = nullptr;
   size_t cap = 0;
   cudaEvent_t ev = nullptr;
+};
+// A ring of slots, so that a copy waits only for the one kStageSlots copies
+// before it (not for the last): launches queued behind other work do not
+// hold up the host.
+constexpr int kStageSlots = 4;
+struct PinnedStage {
+  PinnedSlot slot[kStageSlots];
+  int next = 0;
 };
 }  // namespace hm
 
@@ -386,6 +394,7 @@ struct F64SyrkPlanes {
   const float* T = nullptr;
   int count = 0;
   double w[kMaxSyrkPlanes] = {};
+  int wexp[kMaxSyrkPlanes] = {};  // w[j] = 2^(-12 - 7 wexp[j]); equal wexp adjacent
   const int* ex = nullptr;
   const double* part = nullptr;  // the earlier groups, combined (C)
   int64_t ldp = 0;

@@ -1956,7 +1956,10 @@ hess_status f64_syrk_tc(hess_mlp* h, const double* A, int64_t lda, int64_t K, do
     if (defer && j1 == cs.size() && jw.count <= kMaxSyrkPlanes) {
       defer->T = fs.T;
       defer->count = jw.count;
-      for (int j = 0; j < jw.count; ++j) defer->w[j] = jw.w[j];
+      for (int j = 0; j < jw.count; ++j) {
+        defer->w[j] = jw.w[j];
+        defer->wexp[j] = cs[j0 + j].w;
+      }
       defer->ex = fs.ex;
       defer->part = first ? nullptr : C;
       defer->ldp = ldc;

@@ -67,3 +67,16 @@ def test_back_projection_digit_routes(hm, widths, N, seed):
     lam, Q, _ = net.opg_topk_eig(dev(pb.X), dev(pb.Y), k, "fp64")
     Gr = O.per_example_grads(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
     check_eig(lam.cpu().numpy(), Q.cpu().numpy(), Gr, k, 1e-12, 1e-10)
+
+
+def test_gram_with_two_wide_layers(hm):
+    """Two layers wide enough for the exact-digit Gram term ([160, 130, 10]):
+    the second layer's planes are combined by a second fused launch that adds
+    to the first one's double-float output."""
+    from eigcheck import check_eig
+    pb = make_problem([160, 130, 10], ["sigmoid"], 300, 24, "normal", "uniform")
+    net = hm.HessMLP(pb.widths, pb.acts, pb.omega)
+    k = 10
+    lam, Q, _ = net.opg_topk_eig(dev(pb.X), dev(pb.Y), k, "fp64")
+    Gr = O.per_example_grads(pb.omega, pb.widths, pb.acts, pb.X, pb.Y)
+    check_eig(lam.cpu().numpy(), Q.cpu().numpy(), Gr, k, 1e-12, 1e-10)
