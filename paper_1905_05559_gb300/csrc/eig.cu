@@ -87,6 +87,7 @@ __global__ void gram_prep_kernel(const __grid_constant__ GramPrepArgs g) {
       md = fmax(md, fabs(v));
       sd = fma(v, v, sd);
     }
+#pragma unroll 8
     for (int k = lane; k < L.Tin; k += 32) {
       const double v = a[k];
       ma = fmax(ma, fabs(v));
@@ -1806,60 +1807,211 @@ __global__ void inviter_df_kernel(const double* a, const double* b, int m, int k
 }
 
 
-// Final per-column pass: evals, zero null columns, scale 1/sqrt(N mu),
-// sign so that the largest-magnitude entry is positive.  One block of 1024
-// threads per column (up to 32 warps).
-__global__ void finalize_kernel(double* evecs, int64_t P, const double* theta, int k, double N,
-                                double* evals, int* deficient) {
-  __shared__ double shv[32];
+// U[n][c] = sum_j q_j[n] Y[c][j]: the Ritz vectors in the example space from
+// the double-float Lanczos basis (rows q_j), in double-float, written in
+// FP64.  Block (32, 4): 32 adjacent examples, the steps j in 4 interleaved
+// slices (summed through shared memory at the end), 8 columns c; Y's 8 rows
+// split into shared memory (8 m pairs).
+constexpr int kRitzC = 8;
+__global__ void ritz_df_kernel(const float2* Q, int64_t N, int m, const double* Y, int64_t ldy, int k, double* U) {
+  extern __shared__ float2 ys[];  // kRitzC x m, then the slice sums
+  const int c0 = blockIdx.y * kRitzC;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  for (int e = tid; e < kRitzC * m; e += 128) {
+    const int cc = e / m, j = e - cc * m;
+    ys[e] = c0 + cc < k ? df_split(Y[(int64_t)(c0 + cc) * ldy + j]) : make_float2(0.0f, 0.0f);
+  }
+  __syncthreads();
+  const int64_t n = blockIdx.x * (int64_t)32 + threadIdx.x;
+  float s[kRitzC], c[kRitzC];
+#pragma unroll
+  for (int cc = 0; cc < kRitzC; ++cc) s[cc] = c[cc] = 0.0f;
+  if (n < N) {
+    // eight basis rows in flight per batch
+    for (int j0 = threadIdx.y; j0 < m; j0 += 32) {
+      float2 q[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = j0 + 4 * u;
+        q[u] = j < m ? Q[(int64_t)j * N + n] : make_float2(0.0f, 0.0f);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = j0 + 4 * u;
+        if (j < m)
+#pragma unroll
+          for (int cc = 0; cc < kRitzC; ++cc) df_mac(q[u], ys[cc * m + j], s[cc], c[cc]);
+      }
+    }
+  }
+  float2* red = ys + kRitzC * m;  // 4 x kRitzC x 32
+#pragma unroll
+  for (int cc = 0; cc < kRitzC; ++cc) red[(threadIdx.y * kRitzC + cc) * 32 + threadIdx.x] = make_float2(s[cc], c[cc]);
+  __syncthreads();
+  if (threadIdx.y != 0 || n >= N) return;
+#pragma unroll
+  for (int cc = 0; cc < kRitzC; ++cc) {
+    float2 v = df_norm(red[cc * 32 + threadIdx.x].x, red[cc * 32 + threadIdx.x].y);
+    for (int y = 1; y < 4; ++y) {
+      const float2 w = red[(y * kRitzC + cc) * 32 + threadIdx.x];
+      v = df_add(v, df_norm(w.x, w.y));
+    }
+    if (c0 + cc < k) U[n * k + c0 + cc] = df_val(v);
+  }
+}
+
+// A narrow weight layer's block of G^T U and its bias rows without forming G
+// or B: R[j][i k + c] = sum_n a1[n][j] delta[n][i] u[n][c] with a1 = [a | 1]
+// (j = Tin: the bias rows), in double-float.  Block (32, 8) for 32 columns
+// (i, c) and up to kBpRows rows j, over the examples of its slice
+// (blockIdx.z) in batches of 32 staged in shared memory; the slices' partial
+// sums go to part[slice][j][col] for bp_small_reduce_kernel.
+constexpr int kBpRows = 32;
+__global__ void bp_small_kernel(const double* A, int Tin, const double* D, int Tout, const double* U, int k,
+                                int64_t N, int64_t nper, float2* part) {
+  __shared__ float2 sa[32][kBpRows + 1];
+  __shared__ float2 sb[32][33];
+  const int cols = Tout * k;
+  const int col = blockIdx.x * 32 + threadIdx.x;
+  const int j0 = blockIdx.y * kBpRows;
+  const int64_t nb = (int64_t)blockIdx.z * nper, ne = nb + nper < N ? nb + nper : N;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  float s[kBpRows / 8], c[kBpRows / 8];
+#pragma unroll
+  for (int t = 0; t < kBpRows / 8; ++t) s[t] = c[t] = 0.0f;
+  for (int64_t b0 = nb; b0 < ne; b0 += 32) {
+    for (int e = tid; e < 32 * kBpRows; e += 256) {
+      const int nn = e / kBpRows, jj = e - nn * kBpRows;
+      const int64_t n = b0 + nn;
+      const int j = j0 + jj;
+      double v = 0.0;
+      if (n < ne && j <= Tin) v = j < Tin ? A[n * Tin + j] : 1.0;
+      sa[nn][jj] = df_split(v);
+    }
+    for (int e = tid; e < 32 * 32; e += 256) {
+      const int nn = e >> 5, cc = e & 31;
+      const int64_t n = b0 + nn;
+      const int cl = blockIdx.x * 32 + cc;
+      double v = 0.0;
+      if (n < ne && cl < cols) {
+        const int i = cl / k, ci = cl - i * k;
+        v = D[n * Tout + i] * U[n * k + ci];
+      }
+      sb[nn][cc] = df_split(v);
+    }
+    __syncthreads();
+    const int nc = ne - b0 < 32 ? (int)(ne - b0) : 32;
+    for (int nn = 0; nn < nc; ++nn) {
+      const float2 b = sb[nn][threadIdx.x];
+#pragma unroll
+      for (int t = 0; t < kBpRows / 8; ++t) df_mac(sa[nn][threadIdx.y + 8 * t], b, s[t], c[t]);
+    }
+    __syncthreads();
+  }
+  if (col >= cols) return;
+#pragma unroll
+  for (int t = 0; t < kBpRows / 8; ++t) {
+    const int j = j0 + threadIdx.y + 8 * t;
+    if (j <= Tin) part[((int64_t)blockIdx.z * (Tin + 1) + j) * cols + col] = make_float2(s[t], c[t]);
+  }
+}
+
+// R[j][col] (FP64) = the sum over the slices of part
+__global__ void bp_small_reduce_kernel(const float2* part, int slices, int64_t rows_cols, double* R) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= rows_cols) return;
+  float2 v = make_float2(0.0f, 0.0f);
+#pragma unroll 8
+  for (int z = 0; z < slices; ++z) {
+    const float2 w = part[(int64_t)z * rows_cols + t];
+    v = df_add(v, df_norm(w.x, w.y));
+  }
+  R[t] = df_val(v);
+}
+
+// The output pass over the k eigenvectors (P entries each), in slices of
+// blockIdx.y: evals; null directions (mu <= 1e-13 mu_1) zeroed and flagged;
+// the others scaled by 1/sqrt(N mu) (N = 0: left as they are); each slice
+// reports its entry of largest magnitude (FP64 bits of |v|; 2 index + 1 if
+// v < 0; ties to the smaller index) for the sign pass.
+__global__ void finalize_scale_kernel(double* evecs, int64_t P, const double* theta, int k, double N,
+                                      double* evals, int* deficient, unsigned long long* best) {
+  __shared__ unsigned long long shv[32];
   __shared__ int64_t shi[32];
-  int c = blockIdx.x;
-  double mu = theta[c], mu0 = theta[0];
+  const int c = blockIdx.x, S = gridDim.y, sl = blockIdx.y;
+  const int64_t chunk = (P + S - 1) / S, i0 = sl * chunk, i1 = i0 + chunk < P ? i0 + chunk : P;
+  const double mu = theta[c], mu0 = theta[0];
   double* q = evecs + (int64_t)c * P;
-  bool null_dir = !(mu > 1e-13 * mu0) || !(mu > 0.0);
-  if (threadIdx.x == 0) {
+  const bool null_dir = !(mu > 1e-13 * mu0) || !(mu > 0.0);
+  if (sl == 0 && threadIdx.x == 0) {
     evals[c] = mu;
     if (null_dir) atomicExch(deficient, 1);
   }
+  unsigned long long bv = 0ull;
+  int64_t bi = i0;
+  bool neg = false;
   if (null_dir) {
-    for (int64_t i = threadIdx.x; i < P; i += blockDim.x) q[i] = 0.0;
-    return;
-  }
-  const double sc = N > 0.0 ? 1.0 / sqrt(N * mu) : 1.0;  // N = 0: the vectors are eigenvectors already
-  double best = -1.0;
-  int64_t bi = 0;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) q[i] = 0.0;
+  } else {
+    const double sc = N > 0.0 ? 1.0 / sqrt(N * mu) : 1.0;
 #pragma unroll 4
-  for (int64_t i = threadIdx.x; i < P; i += blockDim.x) {
-    double v = q[i] * sc;
-    q[i] = v;
-    if (fabs(v) > best) {
-      best = fabs(v);
-      bi = i;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const double v = q[i] * sc;
+      q[i] = v;
+      const unsigned long long a = (unsigned long long)__double_as_longlong(fabs(v));
+      if (a > bv) {
+        bv = a;
+        bi = i;
+        neg = v < 0.0;
+      }
     }
   }
+  int64_t bx = 2 * bi + (neg ? 1 : 0);  // index and sign
   for (int o = 16; o > 0; o >>= 1) {
-    double ov = __shfl_xor_sync(0xffffffffu, best, o);
-    int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
-    if (ov > best || (ov == best && oi < bi)) {
-      best = ov;
-      bi = oi;
+    const unsigned long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
+    const int64_t ox = __shfl_xor_sync(0xffffffffu, bx, o);
+    if (ov > bv || (ov == bv && (ox >> 1) < (bx >> 1))) {
+      bv = ov;
+      bx = ox;
     }
   }
   if ((threadIdx.x & 31) == 0) {
-    shv[threadIdx.x >> 5] = best;
-    shi[threadIdx.x >> 5] = bi;
+    shv[threadIdx.x >> 5] = bv;
+    shi[threadIdx.x >> 5] = bx;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int i = 1; i < (int)(blockDim.x >> 5); ++i)
-      if (shv[i] > shv[0] || (shv[i] == shv[0] && shi[i] < shi[0])) {
-        shv[0] = shv[i];
-        shi[0] = shi[i];
+    bv = shv[0];
+    bx = shi[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (shv[w] > bv || (shv[w] == bv && (shi[w] >> 1) < (bx >> 1))) {
+        bv = shv[w];
+        bx = shi[w];
       }
+    best[((int64_t)c * S + sl) * 2] = bv;
+    best[((int64_t)c * S + sl) * 2 + 1] = (unsigned long long)bx;
   }
-  __syncthreads();
-  if (q[shi[0]] < 0.0)
-    for (int64_t i = threadIdx.x; i < P; i += blockDim.x) q[i] = -q[i];
+}
+
+// The sign pass: each slice finds its vector's entry of largest magnitude
+// from the slices' reports (not from the vector, which other slices may be
+// negating) and negates its own entries when that entry is negative.
+__global__ void finalize_sign_kernel(double* evecs, int64_t P, const unsigned long long* best) {
+  const int c = blockIdx.x, S = gridDim.y, sl = blockIdx.y;
+  const int64_t chunk = (P + S - 1) / S, i0 = sl * chunk, i1 = i0 + chunk < P ? i0 + chunk : P;
+  unsigned long long bv = 0ull;
+  int64_t bx = 2 * P;
+  for (int z = 0; z < S; ++z) {
+    const unsigned long long v = best[((int64_t)c * S + z) * 2];
+    const int64_t x = (int64_t)best[((int64_t)c * S + z) * 2 + 1];
+    if (v > bv || (v == bv && (x >> 1) < (bx >> 1))) {
+      bv = v;
+      bx = x;
+    }
+  }
+  if (!(bx & 1)) return;
+  double* q = evecs + (int64_t)c * P;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) q[i] = -q[i];
 }
 
 __global__ void max_res_kernel(const double* res, int k, const double* theta, double* out) {
@@ -1893,8 +2045,26 @@ hess_status eig_kernel_attributes() {
       e = cudaFuncSetAttribute(lanczos_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEigSmemCap);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(inviter_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEigSmemCap);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ritz_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEigSmemCap);
   });
   if (e != cudaSuccess) return set_error(HESS_ERR_CUDA, "eigen kernel attributes: %s", cudaGetErrorString(e));
+  return HESS_OK;
+}
+
+// The output pass (finalize_scale_kernel, then finalize_sign_kernel) over
+// slices of about 2048 entries; best holds 2 k finalize_slices(P) words.
+int finalize_slices(int64_t P) {
+  const int64_t S = cdiv(P, 2048);
+  return (int)(S < 1 ? 1 : (S > 64 ? 64 : S));
+}
+hess_status finalize_vectors(double* evecs, int64_t P, const double* theta, int k, double N, double* evals,
+                             int* deficient, unsigned long long* best, cudaStream_t s) {
+  const dim3 grid((unsigned)k, (unsigned)finalize_slices(P));
+  finalize_scale_kernel<<<grid, 256, 0, s>>>(evecs, P, theta, k, N, evals, deficient, best);
+  HM_LAUNCHED();
+  finalize_sign_kernel<<<grid, 256, 0, s>>>(evecs, P, best);
+  HM_LAUNCHED();
   return HESS_OK;
 }
 
@@ -2159,13 +2329,6 @@ hess_status run_lz_df(hess_mlp* h, double* M, int k, LzBufs& b, int grid, int* m
     HM_TRY(tridiag_topk(b.alpha, b.beta, m, k, b.theta, b.cstart, b.Y, mcap, b.beta + (m - 1), b.rr, b.mx,
                         key + 11, b.tri_scratch, s));
   }
-  {
-    // (the basis in FP64 for the Ritz vectors: counted with them)
-    Tick t(h, HESS_K_BACKPROJ, 0.0, 0.0);
-    const int64_t nq = (int64_t)m * N;
-    df_to_f64_kernel<<<(unsigned)(cdiv(nq, 256) < 4096 ? cdiv(nq, 256) : 4096), 256, 0, s>>>(b.Q, nq);
-    HM_LAUNCHED();
-  }
   *m_out = m;
   *converged_out = converged;
   return HESS_OK;
@@ -2385,6 +2548,13 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   double* Bf = ar.take<double>(N * cols_max);
   double* Rf = ar.take<double>(r_max);
   double* Rb = ar.take<double>(tout_max * k);
+  // the narrow layers' slices of examples (bp_small_kernel)
+  const int64_t bp_nper = 64, bp_slices = cdiv(N, bp_nper);
+  int64_t part_max = 0;
+  for (int wl = 1; wl <= L - 1; ++wl)
+    if (!bp_mode[wl]) part_max = std::max<int64_t>(part_max, (int64_t)(net.T[wl - 1] + 1) * net.T[wl] * k);
+  float2* bp_part = ar.take<float2>(bp_slices * part_max);
+  unsigned long long* best = ar.take<unsigned long long>((int64_t)2 * k * finalize_slices(P));
   F64GemmScratch fb;
   if (need.M) plan_f64_gemm_nt(ar, need, fb);
   if (dry) return HESS_OK;
@@ -2457,7 +2627,13 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   res->converged = converged ? 1 : 0;
 
   // 4. Ritz vectors U = Q_m^T Y (N x k), back-projection through G
-  {
+  if (dfg > 0) {
+    Tick t(h, HESS_K_BACKPROJ, 2.0 * N * m * k, 0.0);
+    const size_t sm = (size_t)kRitzC * m * sizeof(float2) + (size_t)4 * kRitzC * 32 * sizeof(float2);
+    ritz_df_kernel<<<dim3((unsigned)cdiv(N, 32), (unsigned)cdiv(k, kRitzC)), dim3(32, 4), sm, s>>>(
+        reinterpret_cast<const float2*>(Q), N, m, Y, mcap, k, U);
+    HM_LAUNCHED();
+  } else {
     Tick t(h, HESS_K_BACKPROJ, 2.0 * N * m * k, 0.0);
     Gemm<double> g;
     g.M = (int)N;
@@ -2480,9 +2656,11 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   for (int wl = 1; wl <= L - 1; ++wl) {
     const int64_t Tin = net.T[wl - 1], Tout = net.T[wl], cols = Tout * k;
     Tick t(h, HESS_K_BACKPROJ, bp_mode[wl] ? 2.0 * N * Tout * k : 2.0 * N * (Tin + 1) * cols, 0.0);
-    bp_build_kernel<<<(unsigned)(cdiv(N * cols, 256) < 65536 ? cdiv(N * cols, 256) : 65536), 256, 0, s>>>(
-        c.d[wl], U, N, (int)Tout, k, Bf, bp_mode[wl] == 1 ? 1 : 0);
-    HM_LAUNCHED();
+    if (bp_mode[wl]) {
+      bp_build_kernel<<<(unsigned)(cdiv(N * cols, 256) < 65536 ? cdiv(N * cols, 256) : 65536), 256, 0, s>>>(
+          c.d[wl], U, N, (int)Tout, k, Bf, bp_mode[wl] == 1 ? 1 : 0);
+      HM_LAUNCHED();
+    }
     // the bias rows: row Tin of R (a row of ones appended to A^T), or their
     // own product
     const double* Rbl = Rb;
@@ -2500,22 +2678,17 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
       f2.Nn = Tin;
       HM_TRY(f64_gemm_nt_tc(h, Bf, cols, c.a[wl - 1], 1, Tin, N, Rf, 1, cols, f2, s, Tin));
     } else {
-      Gemm<double> g;
-      g.M = (int)Tin;
-      g.N = (int)cols;
-      g.K = (int)N;
-      g.A = c.a[wl - 1];
-      g.sam = 1;
-      g.sak = Tin;
-      g.B = Bf;
-      g.sbk = cols;
-      g.sbn = 1;
-      g.C = Rf;
-      g.scm = cols;
-      g.scn = 1;
-      HM_TRY(gemm(g, s));
+      // R and its bias row Tin in one pass, without forming B
+      const dim3 grid((unsigned)cdiv(cols, 32), (unsigned)cdiv(Tin + 1, kBpRows), (unsigned)bp_slices);
+      bp_small_kernel<<<grid, dim3(32, 8), 0, s>>>(c.a[wl - 1], (int)Tin, c.d[wl], (int)Tout, U, k, N, bp_nper,
+                                                   bp_part);
+      HM_LAUNCHED();
+      const int64_t rc = (Tin + 1) * cols;
+      bp_small_reduce_kernel<<<(unsigned)cdiv(rc, 256), 256, 0, s>>>(bp_part, (int)bp_slices, rc, Rf);
+      HM_LAUNCHED();
+      Rbl = Rf + Tin * cols;
     }
-    if (bp_mode[wl] != 1) {
+    if (bp_mode[wl] == 2) {
       Gemm<double> g;
       g.M = (int)Tout;
       g.N = k;
@@ -2539,8 +2712,7 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   {
     Tick t(h, HESS_K_BACKPROJ, 0.0, 0.0);
     HM_CUDA(cudaMemsetAsync(flag + 1, 0, sizeof(int), s));
-    finalize_kernel<<<k, 1024, 0, s>>>(evecs_d, P, theta, k, (double)N, evals_d, flag + 1);
-    HM_LAUNCHED();
+    HM_TRY(finalize_vectors(evecs_d, P, theta, k, (double)N, evals_d, flag + 1, best, s));
   }
   int* hi = reinterpret_cast<int*>(hp);
   HM_CUDA(cudaMemcpyAsync(hi, flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -2554,6 +2726,7 @@ hess_status topk_eig_dense(hess_mlp* h, const double* M, int64_t n, int k, doubl
   LzBufs lb;
   plan_lz(ar, n, k, lb, nullptr, nullptr);
   int* flag = ar.take<int>(2);
+  unsigned long long* best = ar.take<unsigned long long>((int64_t)2 * k * finalize_slices(n));
   if (dry) return HESS_OK;
   cudaStream_t s = h->stream;
   int m = 0;
@@ -2583,8 +2756,7 @@ hess_status topk_eig_dense(hess_mlp* h, const double* M, int64_t n, int k, doubl
   g.scn = n;
   HM_TRY(gemm(g, s));
   HM_CUDA(cudaMemsetAsync(flag + 1, 0, sizeof(int), s));
-  finalize_kernel<<<k, 1024, 0, s>>>(evecs_d, n, lb.theta, k, 0.0, evals_d, flag + 1);
-  HM_LAUNCHED();
+  HM_TRY(finalize_vectors(evecs_d, n, lb.theta, k, 0.0, evals_d, flag + 1, best, s));
   int* hi = reinterpret_cast<int*>(h->host_pinned);
   HM_CUDA(cudaMemcpyAsync(hi, flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
   HM_CUDA(cudaStreamSynchronize(s));

@@ -363,6 +363,8 @@ struct Job {
   int64_t R0;     // mode 1: first concatenated row of unit p0
   int ntn;        // mode 2: column tiles per unit
   int64_t brow;   // mode 2: B rows per unit
+  int chunk_kb;   // k-blocks per TMEM accumulation chunk (0: CHUNK_KB; exact
+                  // integer products take the whole K in one chunk)
 };
 }  // namespace tc
 

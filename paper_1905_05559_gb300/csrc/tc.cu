@@ -375,7 +375,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         const Job& jb = L.jobs[L.tiles[t].x];
         const int nvk = jb.nkb;
         const uint32_t idesc = jb.idesc;
-        const int nchunk = (nvk + CHUNK_KB - 1) / CHUNK_KB;
+        const int ckb = jb.chunk_kb > 0 ? jb.chunk_kb : CHUNK_KB;
+        const int nchunk = (nvk + ckb - 1) / ckb;
         // the first chunk goes to the tile's main buffer, the others to the
         // second buffer, which the epilogue merges into the main one
         const int mainb = tcount & 1;
@@ -388,7 +389,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           ++uses[buf];
           tc_fence_after();
           const uint32_t d_tmem = tmem_base + buf * MAXBN;
-          const int j0 = ch * CHUNK_KB, j1 = min(nvk, j0 + CHUNK_KB);
+          const int j0 = ch * ckb, j1 = min(nvk, j0 + ckb);
           for (int j = j0; j < j1; ++j, ++it) {
             const int s = it % STAGES;
             const uint32_t ph = (it / STAGES) & 1;
@@ -440,7 +441,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       const float scale = p.scale;
       float* const out = p.out;
       const bool sym = p.mode != 3;  // mode 3: a general product, every entry direct
-      const int nchunk = (p.nkb + CHUNK_KB - 1) / CHUNK_KB;
+      const int ckb = p.chunk_kb > 0 ? p.chunk_kb : CHUNK_KB;
+      const int nchunk = (p.nkb + ckb - 1) / ckb;
       const int acc = tcount & 1;
       const bool got = mbar_wait(tfull(acc), fulls[acc] & 1u, L.err, abort_flag);
       if (__any_sync(0xffffffffu, !got)) break;
@@ -1674,6 +1676,7 @@ __global__ void digits_rows_kernel(const double* A, int64_t rs, int64_t ks, int6
   if (r >= n) return;
   const double* a = A + r * rs;  // element (r, k) = a[k * ks]
   double mx = 0.0;
+#pragma unroll 8
   for (int64_t k = lane; k < K; k += 32) mx = fmax(mx, fabs(a[k * ks]));
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   int E = 0;
@@ -1684,6 +1687,7 @@ __global__ void digits_rows_kernel(const double* A, int64_t rs, int64_t ks, int6
   __nv_bfloat16* rr = rev ? rev + r * L : nullptr;
   const int64_t grp = r / gn, rg = r - grp * gn, ng = n - grp * gn < gn ? n - grp * gn : gn;
   __nv_bfloat16* pr = pm ? pm + (grp * kDigits * gn + rg) * ldk : nullptr;
+#pragma unroll 4
   for (int64_t k = lane; k < ldk; k += 32) {
     long long m = k < K ? fixed62(a[k * ks], E) : 0ll;  // |m| <= 2^62
 #pragma unroll
@@ -1940,6 +1944,7 @@ hess_status f64_syrk_tc(hess_mlp* h, const double* A, int64_t lda, int64_t K, do
       job.Nn = n;
       job.mode = 0;  // upper tiles; the mirrored writes land below the diagonal, unread
       job.scale = 1.0f;
+      job.chunk_kb = job.nkb;  // exact integer sums: no chunked accumulation
       job.out = fs.T + (j - j0) * (size_t)n * n;
       job.ldo = n;
       syrk_tiles(n, BN, (int)jobs.size(), tiles);
@@ -2103,6 +2108,7 @@ hess_status f64_gemm_nt_tc(hess_mlp* h, const double* G, int64_t ldg, const doub
         job.Nn = cols;
         job.mode = 3;
         job.scale = 1.0f;
+        job.chunk_kb = job.nkb;  // exact integer sums: no chunked accumulation
         job.out = Tg + (sg * kTerms + term_of(dj.d, dj.e0)) * ng;
         job.ldo = nt * ng;
         for (int64_t tm = 0; tm < cdiv(M, BM); ++tm) tiles.push_back(make_int4(j, (int)tm, 0, 0));
