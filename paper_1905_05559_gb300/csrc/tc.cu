@@ -264,8 +264,10 @@ __device__ __forceinline__ void row_map(const Job& p, int64_t m, int tile_y, int
 __global__ void __launch_bounds__(THREADS, 1)
     umma_gemm_kernel(const Launch L) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  // the ring's 1024-byte alignment as an offset from the array, so that the
+  // compiler still knows every pointer below addresses shared memory (an
+  // integer round trip would make the epilogue's accesses generic ones)
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   float* epi = reinterpret_cast<float*>(smem + RING_BYTES);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + RING_BYTES + EPI_BYTES);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * MAXSTAGES + 4);
@@ -486,11 +488,21 @@ __global__ void __launch_bounds__(THREADS, 1)
       sptr[lane] = rvalid ? out + orow * ldo + ocolb : nullptr;
       sdm[lane] = dmin;
       __syncwarp();
+      // this lane's share of the direct stores: rows rg + 8 r (r < 4) of the
+      // warp's 32, columns 4 cq .. 4 cq + 3 of each group of 16
+      const int cq = lane & 3, rg = lane >> 2;
+      float* rps[4];
+      int64_t dms[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        rps[r] = sptr[rg + 8 * r];
+        dms[r] = sdm[rg + 8 * r];
+      }
       const uint32_t tbase = tmem_base + acc * MAXBN + (static_cast<uint32_t>(q * 32) << 16);
       // 16 columns of the tile: the mirror image (for a fixed column the
       // warp's 32 rows are adjacent), then the direct entries transposed
-      // through shared memory: 4 rows x 8 column pairs per warp store,
-      // 8-byte stores where the address allows
+      // through shared memory: 8 rows x 4 column quads per warp store,
+      // 16-byte stores where the address allows
       auto emit16 = [&](const float* v, int64_t n0) {
         float* mp = mir ? out + (ocolb + n0) * ldo + orow : nullptr;
 #pragma unroll
@@ -504,22 +516,26 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
         }
         __syncwarp();
-        const int cp = lane & 7, rg = lane >> 3;
-        const int64_t n = n0 + 2 * cp;
-#pragma unroll 2
-        for (int r = 0; r < 8; ++r) {
-          const int i = rg + 4 * r;
-          float* const rp = sptr[i];
+        const int64_t n = n0 + 4 * cq;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          float* const rp = rps[r];
           if (rp != nullptr) {
-            const int64_t dm = sdm[i];
-            const float a0 = e[i * EPI_LD + 2 * cp], a1 = e[i * EPI_LD + 2 * cp + 1];
-            const bool ok0 = n < Nn && n >= dm;
-            const bool ok1 = n + 1 < Nn && n + 1 >= dm;
-            if (ok0 && ok1 && ((reinterpret_cast<uintptr_t>(rp + n) & 7u) == 0u)) {
-              __stcs(reinterpret_cast<float2*>(rp + n), make_float2(a0, a1));
+            const int i = rg + 8 * r;
+            const int64_t dm = dms[r];
+            float a[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = e[i * EPI_LD + 4 * cq + u];
+            const uintptr_t ad = reinterpret_cast<uintptr_t>(rp + n);
+            if (n >= dm && n + 3 < Nn && (ad & 15u) == 0u) {
+              __stcs(reinterpret_cast<float4*>(rp + n), make_float4(a[0], a[1], a[2], a[3]));
+            } else if (n >= dm && n + 3 < Nn && (ad & 7u) == 0u) {
+              __stcs(reinterpret_cast<float2*>(rp + n), make_float2(a[0], a[1]));
+              __stcs(reinterpret_cast<float2*>(rp + n + 2), make_float2(a[2], a[3]));
             } else {
-              if (ok0) __stcs(rp + n, a0);
-              if (ok1) __stcs(rp + n + 1, a1);
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (n + u < Nn && n + u >= dm) __stcs(rp + n + u, a[u]);
             }
           }
         }
