@@ -1174,7 +1174,7 @@ def main():
             hd.timing(False)
             for cls in hm._lib.KERNEL_CLASS:
                 r = hd.read_timing(cls)
-                acc = kern.setdefault(cls, {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0})
+                acc = kern.setdefault(cls, {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0, "sm_ms": 0.0})
                 for kk in acc:
                     acc[kk] += r[kk]
         per = [x.elapsed_time(y) for x, y in ms]
@@ -1274,6 +1274,7 @@ def main():
     smx = peaks.get("sm_max_mhz", 2070.0) * 1e6
     fp64_nominal = 1.25  # TFLOP/s: the platform's nominal FP64 rate
     fp32_peak = 152 * 128 * 2 * smx / 1e12
+    n_sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     probe = fp64_probe(lib, torch) if rank == 0 else None
     bf16_peak = peaks["bf16_tflops_sustained"]
     mult = 3.0 if args.precision == "bf16x3" else 1.0
@@ -1324,6 +1325,13 @@ def main():
                  "work": "dependent recurrences on small tridiagonal matrices; no throughput bound"}
         r["traffic"] = None  # DRAM bytes: the ncu summaries under profiles/
         r["frac"] = r["achieved"] / r["peak"] if r.get("peak") and r.get("achieved") else None
+        # a persistent grid confined to part of the GPU (the contractions
+        # beside the Lanczos kernel): the SMs it had and its fraction of
+        # their share of the peak
+        sms = k.get("sm_ms", 0.0) / k["ms"] if k["ms"] > 0 else 0.0
+        if r["frac"] is not None and 0 < sms < n_sms - 0.5:
+            r["sms"] = round(sms, 1)
+            r["frac_of_sms"] = r["frac"] * n_sms / sms
         r["kernel_class"] = cls
         r["kernel"] = kernel_of[cls]
         r["launches_per_step"] = k["launches"] / max(args.steps, 1)

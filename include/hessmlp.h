@@ -503,6 +503,8 @@ typedef struct {
   double ms;    /* summed device time of the bracketed launches */
   double flops; /* summed algorithmic flops */
   double bytes; /* summed algorithmic HBM bytes */
+  double sm_ms; /* summed device time x SMs the launches were given (the
+                   whole GPU unless a launch was confined to fewer) */
 } hess_kernel_stats;
 
 HESS_API hess_status hess_timing_enable(hess_mlp* h, int enable);

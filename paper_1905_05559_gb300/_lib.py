@@ -69,7 +69,7 @@ KERNEL_CLASS = {"syrk": 0, "hcontract": 1, "grads": 2, "rop": 3, "eig": 4, "hres
 
 class KernelStats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double),
-                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double), ("sm_ms", ctypes.c_double)]
 
 
 class HessDesc(ctypes.Structure):

@@ -105,7 +105,7 @@ class HessMLP:
         st = _lib.KernelStats()
         _lib.check(self._lib.hess_timing_read(self.h, _lib.KERNEL_CLASS[kernel_class],
                                               ctypes.byref(st)))
-        return {"launches": st.launches, "ms": st.ms, "flops": st.flops, "bytes": st.bytes}
+        return {"launches": st.launches, "ms": st.ms, "flops": st.flops, "bytes": st.bytes, "sm_ms": st.sm_ms}
 
     # ------------------------------------------------------------ calls
     def _io(self, X, Y, prec):

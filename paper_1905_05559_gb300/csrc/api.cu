@@ -749,6 +749,7 @@ hess_status hess_timing_read(hess_mlp* h, int cls, hess_kernel_stats* out) {
     a.ms += ms;
     a.flops += r.flops;
     a.bytes += r.bytes;
+    a.sm_ms += (double)ms * (r.sms > 0 && r.sms < h->sm_count ? r.sms : h->sm_count);
     h->event_pool.push_back(r.a);
     h->event_pool.push_back(r.b);
   }

@@ -20,6 +20,7 @@
 // so that the OPG's transfer overlaps the Hessian's contraction and both
 // overlap the eigen step.  The streams use separate regions of the handle's
 // workspace (and separate split-K scratch).
+#include <algorithm>
 #include <functional>
 
 #include "internal.h"
@@ -43,7 +44,7 @@ hess_status on_device(const hess_mlp* h, const void* p, bool* dev) {
 }
 
 struct EventSet {
-  cudaEvent_t e[6] = {};
+  cudaEvent_t e[7] = {};
   ~EventSet() {
     for (cudaEvent_t x : e)
       if (x) cudaEventDestroy(x);
@@ -127,20 +128,42 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
   Caches<double> c64;
   TcPlan plan_o, plan_h;
   EigResult res;
-  cudaEvent_t ev_in = nullptr;
-  auto layout = [&](Arena& ar, bool live) -> hess_status {
+  cudaEvent_t ev_in = nullptr, ev_fb = nullptr;
+  // ---- workspace, in the order taken: the inputs' and eigen step's buffers
+  // (head), the contraction operands and tables (prep), the eigen step's own
+  // scratch; the planning pass and the live pass take the same sizes
+  auto head = [&](Arena& ar, bool live) -> hess_status {
     xs = x_dev ? (float*)X : ar.take<float>(N * T1);
     ys = y_dev ? (float*)Y : ar.take<float>(N * TL);
     os = OPG ? (o_dev ? (float*)OPG : ar.take<float>(P * P)) : nullptr;
     hs = H ? (hh_dev ? (float*)H : ar.take<float>(P * P)) : nullptr;
     splitA = ar.take<char>(kSplitBytes);
+    xd = ar.take<double>(N * T1);
+    yd = ar.take<double>(N * TL);
+    plan_caches(ar, net, N, c64);
+    evd = ev_dev ? evals : ar.take<double>(k);
+    eqd = q_dev ? evecs : ar.take<double>(P * (int64_t)k);
+    splitB = ar.take<char>(kSplitBytes);
     if (live) {
       if (!x_dev) HM_CUDA(cudaMemcpyAsync(xs, X, N * T1 * 4, cudaMemcpyHostToDevice, sA));
       if (!y_dev) HM_CUDA(cudaMemcpyAsync(ys, Y, N * TL * 4, cudaMemcpyHostToDevice, sA));
       // stream B may start once the inputs are on the device (and after
-      // earlier work on the handle's stream)
+      // earlier work on the handle's stream): its FP64 forward/backward pass
+      // (the head of the eigen step, the call's longest chain) goes first,
+      // and stream A's preparation of the contraction operands waits for
+      // it instead of sharing the SMs with it
       HM_CUDA(cudaEventRecord(ev_in, sA));
+      HM_CUDA(cudaStreamWaitEvent(sB, ev_in, 0));
+      SplitGuard sg(splitB, kSplitBytes, h->sm_count);
+      HM_TRY(convert(xs, xd, N * T1, sB));
+      HM_TRY(convert(ys, yd, N * TL, sB));
+      HM_TRY(forward_backward(net, (const double*)h->omega64, (const double*)xd, (const double*)yd, c64, sB));
+      HM_CUDA(cudaEventRecord(ev_fb, sB));
+      HM_CUDA(cudaStreamWaitEvent(sA, ev_fb, 0));
     }
+    return HESS_OK;
+  };
+  auto prep = [&](Arena& ar, bool live) -> hess_status {
     {
       // one preparation (one forward/backward pass) for both matrices, then
       // the OPG's job and the Hessian's jobs as two launches, so that the
@@ -154,28 +177,50 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
     HM_TRY(tc_launch_plan(sm_tc, plan_o, ar, false, x3, h->err_dev, h->stage, sA));
     tabH = ar.off;
     HM_TRY(tc_launch_plan(sm_tc, plan_h, ar, false, x3, h->err_dev, h->stage, sA));
-    xd = ar.take<double>(N * T1);
-    yd = ar.take<double>(N * TL);
-    plan_caches(ar, net, N, c64);
-    evd = ev_dev ? evals : ar.take<double>(k);
-    eqd = q_dev ? evecs : ar.take<double>(P * (int64_t)k);
-    splitB = ar.take<char>(kSplitBytes);
-    offEig = ar.off;
-    if (!live) HM_TRY(topk_eig_gram(h, net, c64, N, k, evd, eqd, ar, true, &res));
     return HESS_OK;
   };
   EventSet ev;
   for (cudaEvent_t& e : ev.e) HM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   ev_in = ev.e[0];
-  Arena ar;
-  HM_TRY(layout(ar, false));
-  HM_TRY(ensure_ws(h, ar.off));
+  ev_fb = ev.e[6];
+  // the planning pass, or its result for a call of the same shape
+  const int64_t key[16] = {N, (int64_t)prec, k, OPG ? 1 : 0, H ? 1 : 0, x_dev, y_dev, o_dev, hh_dev, ev_dev,
+                           q_dev, sm_tc, (int64_t)h->op_limit, h->lz_blocks, P, 0};
+  size_t offPrep = 0;
+  if (h->fplan.valid && std::equal(key, key + 16, h->fplan.key)) {
+    offPrep = h->fplan.off_prep;
+    offEig = h->fplan.off_eig;
+    HM_TRY(ensure_ws(h, h->fplan.ws));
+  } else {
+    h->fplan.valid = false;
+    Arena ar;
+    HM_TRY(head(ar, false));
+    offPrep = ar.off;
+    HM_TRY(prep(ar, false));
+    offEig = ar.off;
+    HM_TRY(topk_eig_gram(h, net, c64, N, k, evd, eqd, ar, true, &res));
+    HM_TRY(ensure_ws(h, ar.off));
+    std::copy(key, key + 16, h->fplan.key);
+    h->fplan.ws = ar.off;
+    h->fplan.off_prep = offPrep;
+    h->fplan.off_eig = offEig;
+    h->fplan.valid = true;
+  }
   plan_o = TcPlan{};
   plan_h = TcPlan{};
-  ar = Arena{h->ws, 0};
-  HM_TRY(layout(ar, true));  // queues A's input staging and operand preparation
-
-  HM_CUDA(cudaStreamWaitEvent(sB, ev.e[0], 0));
+  {
+    Arena ar{h->ws, 0};
+    HM_TRY(head(ar, true));  // queues A's input staging and B's forward/backward
+  }
+  // A's operand preparation (queued on A, with A's timing)
+  auto prep_live = [&]() -> hess_status {
+    cudaStream_t keep = h->stream;
+    h->stream = sA;
+    Arena ar{h->ws, offPrep};
+    const hess_status st = prep(ar, true);
+    h->stream = keep;
+    return st;
+  };
 
   // stream A: the contractions, right behind their operands (queued with the
   // handle's stream set to A, so that their timing runs there)
@@ -185,6 +230,7 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
     h->stream = sA;
     if (OPG) {
       Tick t(h, HESS_K_SYRK, plan_o.syrk_flops, 0.0);
+      t.set_sms(sm_tc);
       Arena at{h->ws, tabO};
       tc_status = tc_launch_plan(sm_tc, plan_o, at, true, x3, h->err_dev, h->stage, sA);
     }
@@ -192,6 +238,7 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
     if (OPG && !o_dev && tc_status == HESS_OK) st = to_host(OPG, os, ev.e[2]);
     if (H && tc_status == HESS_OK && st == HESS_OK) {
       Tick t(h, HESS_K_HCONTRACT, plan_h.hess_flops, 0.0);
+      t.set_sms(sm_tc);
       Arena at{h->ws, tabH};
       tc_status = tc_launch_plan(sm_tc, plan_h, at, true, x3, h->err_dev, h->stage, sA);
     }
@@ -204,13 +251,17 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
   // the free SMs beside the Lanczos launches; otherwise they are queued at
   // once and interleave with the eigen step.
   const bool overlap = sm_tc < h->sm_count;
+  // (the host builds A's operand preparation there, while the GPU runs B's
+  // forward/backward pass and Gram matrix, instead of before queueing them)
   std::function<hess_status()> after_gram = [&]() -> hess_status {
+    HM_TRY(prep_live());
     HM_CUDA(cudaEventRecord(ev.e[1], sB));
     HM_CUDA(cudaStreamWaitEvent(sA, ev.e[1], 0));
     return contractions();
   };
   if (!overlap) {
-    const hess_status st = contractions();
+    hess_status st = prep_live();
+    if (st == HESS_OK) st = contractions();
     if (st != HESS_OK) {
       cudaStreamSynchronize(sB);
       drain_copies();
@@ -223,12 +274,9 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
   hess_status eig_status = HESS_OK;
   h->stream = sB;
   {
+    // (the caches of the eigen step were formed on stream B at the start)
     SplitGuard sg(splitB, kSplitBytes, h->sm_count);
-    eig_status = convert(xs, xd, N * T1, sB);
-    if (eig_status == HESS_OK) eig_status = convert(ys, yd, N * TL, sB);
-    if (eig_status == HESS_OK)
-      eig_status = forward_backward(net, (const double*)h->omega64, (const double*)xd, (const double*)yd, c64, sB);
-    if (eig_status == HESS_OK) {
+    {
       Tick t(h, HESS_K_EIG, 0.0, 0.0);
       Arena are{h->ws, offEig};
       eig_status = topk_eig_gram(h, net, c64, N, k, evd, eqd, are, false, &res, overlap ? &after_gram : nullptr);

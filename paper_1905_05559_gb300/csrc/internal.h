@@ -96,6 +96,7 @@ struct TimingRec {
   cudaEvent_t a, b;
   int cls;
   double flops, bytes;
+  int sms;  // SMs the bracketed launches were given (0: all)
 };
 }  // namespace hm
 
@@ -115,6 +116,16 @@ constexpr int kStageSlots = 4;
 struct PinnedStage {
   PinnedSlot slot[kStageSlots];
   int next = 0;
+};
+}  // namespace hm
+
+namespace hm {
+// The planning pass of a fused call (workspace size and region offsets), kept
+// for the next call of the same shape so that the host queues work at once.
+struct FusedPlanCache {
+  bool valid = false;
+  int64_t key[16] = {};
+  size_t ws = 0, off_prep = 0, off_eig = 0;
 };
 }  // namespace hm
 
@@ -155,6 +166,7 @@ struct hess_mlp {
   size_t op_limit = (size_t)4 << 30;
   // blocks of the OPG eigen step's Lanczos kernel (0: one per SM)
   int lz_blocks = 0;
+  hm::FusedPlanCache fplan;
 };
 
 namespace hm {
@@ -191,6 +203,9 @@ class Tick {
     rec_.flops = flops;
     rec_.bytes = bytes;
   }
+  // the bracketed launches run on sms SMs (persistent grids confined to part
+  // of the GPU)
+  void set_sms(int sms) { rec_.sms = sms; }
   void stop();
   ~Tick() { stop(); }
 
