@@ -1341,11 +1341,41 @@ def main():
 
     rooflines = {c: class_roofline(c) for c in kern}
     rooflines = {c: r for c, r in rooflines.items() if r}
-    # the dominant kernel of the step: largest device time among the
-    # kernel-level classes with a throughput bound
-    cands = [c for c, r in rooflines.items() if r.get("frac") is not None]
-    dom = max(cands, key=lambda c: kern[c]["ms"]) if cands else None
-    roof = dict(rooflines[dom]) if dom else None
+    # the dominant kernel of the step: the kernel function with the largest
+    # device time, its classes' launches together (the OPG, Hessian and
+    # exact-digit launches are one persistent tensor-core kernel)
+    groups = {"umma_gemm_kernel": [c for c in ("syrk", "hcontract", "digits")
+                                   if c in rooflines and rooflines[c]["bound"] == "tensor"]}
+    for c, r in rooflines.items():
+        if r.get("frac") is not None and not any(c in g for g in groups.values()):
+            groups[c] = [c]
+    groups = {g: cs for g, cs in groups.items() if cs}
+
+    def group_roofline(cs):
+        if len(cs) == 1:
+            return dict(rooflines[cs[0]])
+        ms = sum(kern[c]["ms"] for c in cs)
+        sec = ms * 1e-3
+        fl = sum(rooflines[c]["achieved"] * 1e12 * kern[c]["ms"] * 1e-3 for c in cs)  # the classes' flops
+        sm_ms = sum(kern[c].get("sm_ms", 0.0) for c in cs)
+        r = {"bound": "tensor", "achieved": fl / sec / 1e12, "peak": bf16_peak, "unit": "TFLOP/s",
+             "peak_source": f"{peak_src} bf16 sustained",
+             "work": "the classes' tensor flops: " + ", ".join(f"{c} ({rooflines[c]['work']})" for c in cs),
+             "traffic": None}
+        r["frac"] = r["achieved"] / r["peak"]
+        sms = sm_ms / ms if ms > 0 else 0.0
+        if 0 < sms < n_sms - 0.5:
+            r["sms"] = round(sms, 1)
+            r["frac_of_sms"] = r["frac"] * n_sms / sms
+        r["kernel_class"] = "+".join(cs)
+        r["kernel"] = "umma_gemm_kernel (" + ", ".join(cs) + " launches)"
+        r["launches_per_step"] = sum(kern[c]["launches"] for c in cs) / max(args.steps, 1)
+        r["ms_per_step"] = ms / max(args.steps, 1)
+        r["step_share"] = r["ms_per_step"] / ms_step
+        return r
+
+    dom = max(groups, key=lambda g: sum(kern[c]["ms"] for c in groups[g])) if groups else None
+    roof = group_roofline(groups[dom]) if dom else None
 
     serve = precision = None
     if rank == 0 and world == 1 and args.workload == WORKLOAD:

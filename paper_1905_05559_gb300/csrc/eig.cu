@@ -67,11 +67,27 @@ struct GramPrepArgs {
   double invN;
   int* r;
   unsigned long long* maxdiag;  // FP64 bits of max_n M[n][n] (zeroed beforehand)
+  float2* q0;                   // when set, the last block writes the Lanczos start vector there
+  uint64_t key;
 };
 
 // One warp per example row n: exponents, r_n, the FP64 diagonal entry (for the
 // scale of the double-float output), and the split rows.
 __global__ void gram_prep_kernel(const __grid_constant__ GramPrepArgs g) {
+  if (g.q0 && blockIdx.x == gridDim.x - 1) {
+    // the Lanczos start vector q_0: a counter-based random unit vector
+    // (hi/lo pairs), formed here off the eigen step's critical path
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int64_t n = threadIdx.x; n < g.N; n += blockDim.x) {
+      const double v = rnd_sym(g.key, n);
+      s = fma(v, v, s);
+    }
+    s = block_sum(s, sh);
+    const double inv = 1.0 / sqrt(s);
+    for (int64_t n = threadIdx.x; n < g.N; n += blockDim.x) g.q0[n] = df_split(rnd_sym(g.key, n) * inv);
+    return;
+  }
   const int lane = threadIdx.x & 31;
   const int64_t n = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
   if (n >= g.N) return;
@@ -2202,11 +2218,13 @@ int eig_lanczos_blocks(hess_mlp* h, int64_t n, int k) {
 // The Lanczos process of run_lz with the double-float kernel; M (FP64, n x n)
 // is overwritten by its scaled hi/lo pairs.  On return b.Q holds q_0 ..
 // q_{m-1} in FP64 (rows of n), as run_lz leaves them.
+constexpr uint64_t kLzKey = 0x5DEECE66Dull;  // the start vector's counter-based draw
+
 hess_status run_lz_df(hess_mlp* h, double* M, int k, LzBufs& b, int grid, int* m_out, bool* converged_out,
-                      bool m_split) {
+                      bool m_split, bool q0_ready) {
   const int64_t N = b.n, mcap = b.mcap;
   cudaStream_t s = h->stream;
-  const uint64_t key = 0x5DEECE66Dull;
+  const uint64_t key = kLzKey;
   float2* Q = reinterpret_cast<float2*>(b.Q);
   float2* MQ = reinterpret_cast<float2*>(b.MQ);
   const int max_grid = h->sm_count < kDfMaxGrid ? h->sm_count : kDfMaxGrid;
@@ -2221,8 +2239,10 @@ hess_status run_lz_df(hess_mlp* h, double* M, int k, LzBufs& b, int grid, int* m
       df_split_kernel<<<(unsigned)(cdiv(n2, 256) < 4096 ? cdiv(n2, 256) : 4096), 256, 0, s>>>(M, n2, b.escale);
       HM_LAUNCHED();
     }
-    df_start_kernel<<<1, 1024, 0, s>>>(Q, N, key);
-    HM_LAUNCHED();
+    if (!q0_ready) {
+      df_start_kernel<<<1, 1024, 0, s>>>(Q, N, key);
+      HM_LAUNCHED();
+    }
   }
   HM_CUDA(cudaMemsetAsync(b.err, 0, sizeof(int), s));
   int m = 0;
@@ -2484,8 +2504,12 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   double* DD = ar.take<double>(N * N);
   double* AA = ar.take<double>(N * N);
   LzBufs lb;
-  // the basis and M Q reuse AA and DD once the Gram matrix is formed
-  plan_lz(ar, N, k, lb, AA, DD);
+  // M Q reuses DD once the Gram matrix is formed, and so does the basis AA
+  // unless the double-float kernel runs (its start vector is formed with
+  // the Gram matrix, while AA may still hold a partial product)
+  const int64_t mcap0 = N < (int64_t)8 * k + 512 ? N : (int64_t)8 * k + 512;
+  const int dfg = df_grid(h, N, mcap0);
+  plan_lz(ar, N, k, lb, dfg > 0 ? nullptr : AA, DD);
   const int64_t mcap = lb.mcap;
   double* U = ar.take<double>(N * k);
   int* flag = ar.take<int>(2);
@@ -2521,6 +2545,8 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   }
   gp.r = ar.take<int>(N);
   gp.maxdiag = ar.take<unsigned long long>(1);
+  gp.q0 = dfg > 0 ? reinterpret_cast<float2*>(lb.Q) : nullptr;
+  gp.key = kLzKey;
   // and so does the back-projection G^T U (K = N)
   // and so do the back-projection's wide layers: per weight layer,
   // R = A^T B with B[n][(i, c)] = delta[n][i] u[n][c] (K = N)
@@ -2564,11 +2590,10 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   // as exact-digit tensor-core planes, everything else in double-float in
   // fused launches (one per wide layer), written as the Lanczos kernel's
   // double-float input when that kernel runs
-  const int dfg = df_grid(h, N, mcap);
   {
     Tick t(h, HESS_K_GRAM, 0.0, 0.0);
     HM_CUDA(cudaMemsetAsync(gp.maxdiag, 0, sizeof(unsigned long long), s));
-    gram_prep_kernel<<<(unsigned)cdiv(N, 8), 256, 0, s>>>(gp);
+    gram_prep_kernel<<<(unsigned)(cdiv(N, 8) + (gp.q0 ? 1 : 0)), 256, 0, s>>>(gp);
     HM_LAUNCHED();
   }
   {
@@ -2612,7 +2637,7 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   int m = 0;
   bool converged = false;
   if (dfg > 0) {
-    HM_TRY(run_lz_df(h, M, k, lb, dfg, &m, &converged, true));
+    HM_TRY(run_lz_df(h, M, k, lb, dfg, &m, &converged, true, true));
   } else {
     HM_TRY(run_lz(h, M, k, lb, &m, &converged));
   }

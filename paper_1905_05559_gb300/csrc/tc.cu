@@ -1684,37 +1684,53 @@ struct JobWeightsFwd {
 // below 2^-62), whose digits come off by rounding shifts.
 // pm: plane-major digits of groups of gn rows: row r of group g = r / gn
 // (ng = min(gn, n - g gn) rows) has digit d at pm + (g 8 gn + d ng + r - g gn) ldk.
-__global__ void digits_rows_kernel(const double* A, int64_t rs, int64_t ks, int64_t n, int64_t K, int64_t ldk,
-                                   __nv_bfloat16* fwd, __nv_bfloat16* rev, __nv_bfloat16* pm, int* ex,
-                                   int64_t gn) {
-  const int lane = threadIdx.x & 31;
-  const int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (r >= n) return;
-  const double* a = A + r * rs;  // element (r, k) = a[k * ks]
+// A block of 256 threads splits two rows, 128 threads per row, each thread
+// two adjacent k at a time (4-byte stores of BF16 pairs).
+constexpr int kDrRow = 128;
+__global__ void __launch_bounds__(256) digits_rows_kernel(const double* A, int64_t rs, int64_t ks, int64_t n,
+                                                          int64_t K, int64_t ldk, __nv_bfloat16* fwd,
+                                                          __nv_bfloat16* rev, __nv_bfloat16* pm, int* ex,
+                                                          int64_t gn) {
+  __shared__ double smx[2][kDrRow / 32];
+  const int rl = threadIdx.x / kDrRow, t = threadIdx.x % kDrRow, lane = threadIdx.x & 31;
+  const int64_t r = (int64_t)blockIdx.x * 2 + rl;
+  const bool live = r < n;
+  const double* a = A + (live ? r : 0) * rs;  // element (r, k) = a[k * ks]
   double mx = 0.0;
-#pragma unroll 8
-  for (int64_t k = lane; k < K; k += 32) mx = fmax(mx, fabs(a[k * ks]));
+  if (live) {
+#pragma unroll 4
+    for (int64_t k = t; k < K; k += kDrRow) mx = fmax(mx, fabs(a[k * ks]));
+  }
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) smx[rl][t >> 5] = mx;
+  __syncthreads();
+  if (!live) return;
+  mx = fmax(fmax(smx[rl][0], smx[rl][1]), fmax(smx[rl][2], smx[rl][3]));
   int E = 0;
   if (mx > 0.0 && mx <= DBL_MAX) frexp(mx, &E);  // mx = f 2^E, f in [0.5, 1)
-  if (lane == 0) ex[r] = E;
+  if (t == 0) ex[r] = E;
   const int64_t L = (int64_t)kDigits * ldk;
   __nv_bfloat16* fr = fwd ? fwd + r * L : nullptr;
   __nv_bfloat16* rr = rev ? rev + r * L : nullptr;
   const int64_t grp = r / gn, rg = r - grp * gn, ng = n - grp * gn < gn ? n - grp * gn : gn;
   __nv_bfloat16* pr = pm ? pm + (grp * kDigits * gn + rg) * ldk : nullptr;
-#pragma unroll 4
-  for (int64_t k = lane; k < ldk; k += 32) {
-    long long m = k < K ? fixed62(a[k * ks], E) : 0ll;  // |m| <= 2^62
+#pragma unroll 2
+  for (int64_t k = 2 * t; k < ldk; k += 2 * kDrRow) {  // ldk is even: k + 1 < ldk
+    long long m0 = k < K ? fixed62(a[k * ks], E) : 0ll;  // |m| <= 2^62
+    long long m1 = k + 1 < K ? fixed62(a[(k + 1) * ks], E) : 0ll;
 #pragma unroll
     for (int d = 0; d < kDigits; ++d) {
       const int sh = 56 - 7 * d;
-      const long long q = (m + (1ll << (sh - 1))) >> sh;  // round to nearest
-      m -= q << sh;
-      const __nv_bfloat16 v = __int2bfloat16_rn((int)q);  // |q| <= 64: exact
-      if (fr) fr[(int64_t)d * ldk + k] = v;
-      if (rr) rr[(int64_t)(kDigits - 1 - d) * ldk + k] = v;
-      if (pr) pr[(int64_t)d * ng * ldk + k] = v;  // plane-major: rows (d, r) of the group
+      const long long q0 = (m0 + (1ll << (sh - 1))) >> sh;  // round to nearest
+      const long long q1 = (m1 + (1ll << (sh - 1))) >> sh;
+      m0 -= q0 << sh;
+      m1 -= q1 << sh;
+      __nv_bfloat162 v;
+      v.x = __int2bfloat16_rn((int)q0);  // |q| <= 64: exact
+      v.y = __int2bfloat16_rn((int)q1);
+      if (fr) *reinterpret_cast<__nv_bfloat162*>(fr + (int64_t)d * ldk + k) = v;
+      if (rr) *reinterpret_cast<__nv_bfloat162*>(rr + (int64_t)(kDigits - 1 - d) * ldk + k) = v;
+      if (pr) *reinterpret_cast<__nv_bfloat162*>(pr + (int64_t)d * ng * ldk + k) = v;  // rows (d, r) of the group
     }
   }
 }
@@ -1931,7 +1947,7 @@ hess_status f64_syrk_tc(hess_mlp* h, const double* A, int64_t lda, int64_t K, do
   {
     // (the only caller is the Gram matrix of the OPG eigen step)
     Tick t(h, HESS_K_GRAM, 0.0, 0.0);
-    digits_rows_kernel<<<(unsigned)cdiv(n, 8), 256, 0, s>>>(A, lda, 1, n, K, ldk, fs.D, fs.R, nullptr, fs.ex, n);
+    digits_rows_kernel<<<(unsigned)cdiv(n, 2), 256, 0, s>>>(A, lda, 1, n, K, ldk, fs.D, fs.R, nullptr, fs.ex, n);
     HM_LAUNCHED();
   }
   const std::vector<Contraction> cs = contractions(ldk);
@@ -2094,7 +2110,7 @@ hess_status f64_gemm_nt_tc(hess_mlp* h, const double* G, int64_t ldg, const doub
     digits_cols_kernel<<<dim3((unsigned)cdiv(ldk, 128), (unsigned)cdiv(M, 32)), dim3(32, 8), 0, s>>>(
         G, ldg, K, mg, M, fs.mxA, fs.exA, ldk, fs.DA);
     HM_LAUNCHED();
-    digits_rows_kernel<<<(unsigned)cdiv(Nt, 8), 256, 0, s>>>(B, b_rs, b_ks, Nt, K, ldk, nullptr, nullptr, fs.RB,
+    digits_rows_kernel<<<(unsigned)cdiv(Nt, 2), 256, 0, s>>>(B, b_rs, b_ks, Nt, K, ldk, nullptr, nullptr, fs.RB,
                                                              fs.exB, Nn);
     HM_LAUNCHED();
   }
