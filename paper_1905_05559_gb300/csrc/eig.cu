@@ -748,49 +748,59 @@ __global__ void last_beta_kernel(const double* npart, int nparts, double* out) {
 // ------------------------------------------ double-float Lanczos kernel ----
 // The same Lanczos process with full reorthogonalisation, for Gram matrices
 // whose rows fit the blocks' shared memory, in double-float arithmetic
-// (devmath.cuh: about 48 significant bits, all on the FP32 pipe) and with
-// three grid barriers per step j:
-//   1  gather q_j; u = M q_j on the owned rows (kept as row j of MQ); the
-//      first-pass coefficients h_i = (M q_i) . q_j for i < j (M symmetric:
-//      one warp each, over full rows of MQ); block partials of h_j = q_j . u
-//   2  h_j from its partials; w' = u - sum_{i<=j} h_i q_i on the owned slice;
-//      block partials of d_i = q_i . w' (i <= j) and of ||w'||^2
-//   3  d_i and ||w'||^2 from the partials (every block sums them in the same
-//      order, so every block gets the same bits); alpha_j = h_j + d_j;
-//      w = w' - sum_{i<=j} d_i q_i; beta_j^2 = ||w'||^2 - ||d||^2, since
-//      Q^T w' = d makes w' - Q d orthogonal to Q d (when ||d||^2 exceeds a
-//      quarter of ||w'||^2 the subtraction would lose digits, and the norm of
-//      w is summed directly, one barrier more); q_{j+1} = w / beta_j.
-// (classical Gram-Schmidt twice against every earlier vector, as in the FP64
-// kernel).  M arrives scaled by 2^-e (e from the largest diagonal entry,
-// which bounds every entry of a positive semidefinite matrix) as hi/lo
-// pairs; alpha and beta are stored unscaled in FP64.  A breakdown (beta_j <=
-// 1e-12 of the largest alpha or beta so far) stores beta_j = 0, records
-// stop = j + 1 and ends the kernel; the host restarts from a new direction.
+// (devmath.cuh: about 48 significant bits, all on the FP32 pipe), with one
+// grid-wide reduction and two grid barriers per step j.  The second
+// Gram-Schmidt pass of each vector is taken one step late, in the next
+// step's reduction (classical Gram-Schmidt twice, the second pass lagged):
+// the vector handed from step j-1 to step j is w = q~_j, orthogonalised once
+// and not normalised.
+//   1  gather q~_j; u~ = M q~_j on the owned rows; chunk partials of
+//      c_i = q_i . q~_j and g_i = (M q_i) . q~_j for i < j (a warp per
+//      coefficient and chunk of kDfChunk entries, over the stored rows q_i and
+//      M q_i); block partials of nu = ||q~_j||^2 and a~ = q~_j . u~; barrier
+//   2  c, g, nu and a~ from the partials (every block sums them in the same
+//      order, so every block gets the same bits);
+//      r^2 = nu - ||c||^2 (Pythagoras: q~_j - Q c is orthogonal to Q c; when
+//      ||c||^2 exceeds a quarter of nu the subtraction would lose digits, and
+//      ||q~_j - Q c||^2 is summed directly, one barrier more); r = beta_{j-1};
+//      q_j = (q~_j - Q c) / r and u = M q_j = (u~ - (MQ) c) / r on the owned
+//      slice, kept as column j of the slices of Q and MQ and as rows j of Q
+//      and MQ; with Q^T M Q = T_j (the tridiagonal matrix so far):
+//      alpha_j = q_j . u = (a~ - 2 c.g + c.T_j c) / r^2 and the first pass
+//      h = Q^T u = (g - T_j c) / r; w = u - Q h - alpha_j q_j on the owned
+//      slice, written as row j+1 of Q (q~_{j+1}); barrier.
+// A launch over steps m0 .. m1-1 ends with a half step m1 (1 without the
+// product, then r) that gives beta_{m1-1} and leaves q~_{m1} in row m1 of Q,
+// where the next launch resumes.  M arrives scaled by 2^-e (e from the
+// largest diagonal entry, which bounds every entry of a positive
+// semidefinite matrix) as hi/lo pairs; alpha and beta are stored unscaled in
+// FP64.  A breakdown (beta_{j-1} <= 1e-12 of the largest alpha or beta so
+// far) stores beta_{j-1} = 0, records stop = j and ends the kernel; the host
+// restarts from a new direction (row j of Q), and the first step of a launch
+// leaves beta_{m0-1} as stored.
 struct DfArgs {
   const float2* M;    // N x N, scaled, hi/lo pairs
   int64_t N;
-  float2* Q;          // Lanczos vectors, rows of length N (mcap rows)
-  float2* MQ;         // M q_i, rows of length N
-  float2* h;          // first-pass coefficient chunks ([mcap][nch])
-  float2* part;       // [gridDim][pst] block partials
-  float2* apart;      // [gridDim] block partials of q_j . u
+  float2* Q;          // rows q_i (mcap + 1 rows; row j holds q~_j until step j)
+  float2* MQ;         // rows M q_i
+  float2* hc;         // chunk partials of c ([mcap + 2][nch])
+  float2* hg;         // chunk partials of g
+  float2* apart;      // [gridDim][4] block partials: nu, a~, ||q~ - Q c||^2
   double* alpha;
   double* beta;
   const int* escale;  // M was scaled by 2^-escale
   unsigned* bar;
   int* err;
   int* stop;
-  int m0, m1, mcap, E, pst, qcap;
-  int nch;  // first-pass chunks per coefficient
+  int m0, m1, mcap, E, qcap;
+  int nch;  // chunks per coefficient
   long long bar_limit;
 };
 
 constexpr int kDfThreads = 512;
 constexpr int kDfMaxGrid = 256;
-constexpr int kDfChunk = 256;     // entries per first-pass dot-product task
+constexpr int kDfChunk = 256;     // entries per coefficient task
 constexpr int kDfMaxChunks = 8;   // so N <= 2048
-constexpr int kDfBatch = 16;      // partials loaded at once per thread
 constexpr int kDfWarps = kDfThreads / 32;
 constexpr int kDfRed = 1024;  // float2 scratch entries per block
 
@@ -809,33 +819,56 @@ __device__ __forceinline__ void df_combine(const float2* Qs, int qcap, const flo
   }
 }
 
+// sum over the blocks' partials part[b * 4 + f] in block order, by one warp
+// (the same bits in every block)
+__device__ __forceinline__ float2 df_block_sum(const float2* part, int f, int G) {
+  const int lane = threadIdx.x & 31;
+  float s = 0.0f, c = 0.0f;
+  for (int b = lane; b < G; b += 32) df_acc(part[(int64_t)b * 4 + f], s, c);
+  return df_warp_sum(s, c);
+}
+
 __global__ void __launch_bounds__(kDfThreads, 1) lanczos_df_kernel(DfArgs a) {
   extern __shared__ float2 dfsh[];
   const int64_t N = a.N;
   const int E = a.E, qcap = a.qcap;
   float2* Msh = dfsh;                      // owned rows of M, E x N
-  float2* qf = Msh + (int64_t)E * N;       // q_j, N
+  float2* qf = Msh + (int64_t)E * N;       // q~_j, N
   float2* Qs = qf + N;                     // owned slices of q_i, entry-major, E x qcap
-  float2* us = Qs + (int64_t)E * qcap;     // owned slice of u, E
-  float2* ws = us + E;                     // owned slice of w' (then w), E
-  float2* cf = ws + E;                     // coefficients, mcap + 2
-  float2* red = cf + (a.mcap + 2);         // scratch, kDfRed
+  float2* MQs = Qs + (int64_t)E * qcap;    // owned slices of M q_i, E x qcap
+  float2* us = MQs + (int64_t)E * qcap;    // owned slice of u~ (then u), E
+  float2* qn = us + E;                     // owned slice of q~ - Q c (then q_j), E
+  float2* ws = qn + E;                     // owned slice of w, E
+  float2* cc = ws + E;                     // c, qcap + 1
+  float2* cg = cc + (qcap + 1);            // g, qcap + 1
+  float2* ch = cg + (qcap + 1);            // T_j c, then h and alpha_j, qcap + 1
+  float2* Ta = ch + (qcap + 1);            // alpha_i (scaled), qcap + 1
+  float2* Tb = Ta + (qcap + 1);            // beta_i (scaled), qcap + 1
+  float2* red = Tb + (qcap + 1);           // scratch, kDfRed
   const int64_t n0 = (int64_t)blockIdx.x * E;
   const int ne = (int)(N - n0 < E ? (N - n0 > 0 ? N - n0 : 0) : E);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = (int)gridDim.x;
-  __shared__ float2 s_h, s_dd, s_beta2, s_rb;
-  __shared__ int s_brk;
+  __shared__ float2 s_nu, s_at, s_cc, s_cgd, s_ctc, s_r2, s_rinv;
+  __shared__ int s_brk, s_direct;
   __shared__ float s_scale;  // largest |alpha|, beta so far (scaled units)
   const double unscale = ldexp(1.0, *a.escale);
+  const double rescale = 1.0 / unscale;
   for (int e = 0; e < ne; ++e)
     for (int64_t n = tid; n < N; n += kDfThreads) Msh[(int64_t)e * N + n] = a.M[(n0 + e) * N + n];
   for (int e = warp; e < ne; e += kDfWarps)
-    for (int i = lane; i <= a.m0 && i < qcap; i += 32) Qs[(int64_t)e * qcap + i] = a.Q[(int64_t)i * N + n0 + e];
+    for (int i = lane; i < a.m0 && i < qcap; i += 32) {
+      Qs[(int64_t)e * qcap + i] = a.Q[(int64_t)i * N + n0 + e];
+      MQs[(int64_t)e * qcap + i] = a.MQ[(int64_t)i * N + n0 + e];
+    }
+  for (int i = tid; i < a.m0 && i <= qcap; i += kDfThreads) {
+    Ta[i] = df_split(a.alpha[i] * rescale);
+    Tb[i] = df_split(a.beta[i] * rescale);
+  }
   if (tid == 0) {
     float sc = 0.0f;
     for (int i = 0; i < a.m0; ++i)
-      sc = fmaxf(sc, fmaxf(fabsf((float)(a.alpha[i] / unscale)), (float)(a.beta[i] / unscale)));
+      sc = fmaxf(sc, fmaxf(fabsf((float)(a.alpha[i] * rescale)), (float)(a.beta[i] * rescale)));
     s_scale = sc;
   }
   // wpr warps share one owned row of the product
@@ -843,43 +876,51 @@ __global__ void __launch_bounds__(kDfThreads, 1) lanczos_df_kernel(DfArgs a) {
   while (wpr < 8 && 2 * wpr * (ne > 0 ? ne : 1) <= kDfWarps) wpr *= 2;
   const int rows_per_pass = kDfWarps / wpr;
   __syncthreads();
-  for (int j = a.m0; j < a.m1; ++j) {
-    // ---- 1: u = M q_j (owned rows), first-pass coefficients.  The
-    // first-pass tasks are a warp per coefficient and chunk of kDfChunk
-    // entries (the chunks are summed after the barrier); each warp's first
-    // task has its loads issued with those of q_j, before the product.
+  for (int j = a.m0; j <= a.m1; ++j) {
+    const bool full = j < a.m1;  // the last pass is the half step
+    // ---- 1: u~ = M q~_j (owned rows); chunk partials of c and g.  The
+    // tasks are a warp per coefficient and chunk (the chunks are summed
+    // after the barrier); each warp's first task has its loads issued with
+    // those of q~_j, before the product.
+    const int ntc = j * a.nch, ntask = full ? 2 * ntc : ntc;
     const int task0 = (kDfWarps - 1 - warp) * G + (int)blockIdx.x;
     float2 pv[kDfChunk / 32];
-    if (task0 < j * a.nch) {
-      const int i = task0 / a.nch, ch = task0 - i * a.nch;
-      const float2* mq = a.MQ + (int64_t)i * N + (int64_t)ch * kDfChunk + lane;
-      const int64_t rem = N - (int64_t)ch * kDfChunk - lane;
+    if (task0 < ntask) {
+      const bool isg = task0 >= ntc;
+      const int tt = isg ? task0 - ntc : task0;
+      const int i = tt / a.nch, chn = tt - i * a.nch;
+      const float2* src = (isg ? a.MQ : a.Q) + (int64_t)i * N + (int64_t)chn * kDfChunk + lane;
+      const int64_t rem = N - (int64_t)chn * kDfChunk - lane;
 #pragma unroll
-      for (int u = 0; u < kDfChunk / 32; ++u) pv[u] = u * 32 < rem ? mq[u * 32] : make_float2(0.0f, 0.0f);
+      for (int u = 0; u < kDfChunk / 32; ++u) pv[u] = u * 32 < rem ? src[u * 32] : make_float2(0.0f, 0.0f);
     }
     for (int64_t n = tid; n < N; n += kDfThreads) qf[n] = a.Q[(int64_t)j * N + n];
     __syncthreads();
-    for (int r = warp / wpr; r < ne; r += rows_per_pass) {
-      const float2* row = Msh + (int64_t)r * N;
-      // two independent running sums per lane
-      float s0 = 0.0f, c0 = 0.0f, s1 = 0.0f, c1 = 0.0f;
-      const int st = wpr * 32;
-      int64_t n = (warp % wpr) * 32 + lane;
+    if (full) {
+      for (int r = warp / wpr; r < ne; r += rows_per_pass) {
+        const float2* row = Msh + (int64_t)r * N;
+        // two independent running sums per lane
+        float s0 = 0.0f, c0 = 0.0f, s1 = 0.0f, c1 = 0.0f;
+        const int st = wpr * 32;
+        int64_t n = (warp % wpr) * 32 + lane;
 #pragma unroll 2
-      for (; n + st < N; n += 2 * st) {
-        df_mac(row[n], qf[n], s0, c0);
-        df_mac(row[n + st], qf[n + st], s1, c1);
+        for (; n + st < N; n += 2 * st) {
+          df_mac(row[n], qf[n], s0, c0);
+          df_mac(row[n + st], qf[n + st], s1, c1);
+        }
+        if (n < N) df_mac(row[n], qf[n], s0, c0);
+        float sx, ex;
+        two_sum(s0, s1, sx, ex);
+        const float2 t = df_warp_sum(sx, (c0 + c1) + ex);
+        if (lane == 0) red[r * wpr + warp % wpr] = t;
       }
-      if (n < N) df_mac(row[n], qf[n], s0, c0);
-      float sx, ex;
-      two_sum(s0, s1, sx, ex);
-      const float2 t = df_warp_sum(sx, (c0 + c1) + ex);
-      if (lane == 0) red[r * wpr + warp % wpr] = t;
     }
-    for (int t = task0; t < j * a.nch; t += kDfWarps * G) {
-      const int i = t / a.nch, ch = t - i * a.nch;
-      const int64_t c0 = (int64_t)ch * kDfChunk + lane;
-      const float2* mq = a.MQ + (int64_t)i * N;
+    for (int t = task0; t < ntask; t += kDfWarps * G) {
+      const bool isg = t >= ntc;
+      const int tt = isg ? t - ntc : t;
+      const int i = tt / a.nch, chn = tt - i * a.nch;
+      const int64_t c0 = (int64_t)chn * kDfChunk + lane;
+      const float2* src = (isg ? a.MQ : a.Q) + (int64_t)i * N;
       float2 v[kDfChunk / 32];
       if (t == task0) {
 #pragma unroll
@@ -888,7 +929,7 @@ __global__ void __launch_bounds__(kDfThreads, 1) lanczos_df_kernel(DfArgs a) {
 #pragma unroll
         for (int u = 0; u < kDfChunk / 32; ++u) {
           const int64_t n = c0 + u * 32;
-          v[u] = n < N ? mq[n] : make_float2(0.0f, 0.0f);
+          v[u] = n < N ? src[n] : make_float2(0.0f, 0.0f);
         }
       }
       float s = 0.0f, c = 0.0f;
@@ -898,147 +939,154 @@ __global__ void __launch_bounds__(kDfThreads, 1) lanczos_df_kernel(DfArgs a) {
         if (n < N) df_mac(v[u], qf[n], s, c);
       }
       const float2 r2 = df_warp_sum(s, c);
-      if (lane == 0) a.h[(int64_t)i * a.nch + ch] = r2;
+      if (lane == 0) (isg ? a.hg : a.hc)[(int64_t)i * a.nch + chn] = r2;
     }
     __syncthreads();
-    if (tid < ne) {
+    if (full && tid < ne) {
       float s = 0.0f, c = 0.0f;
       for (int p = 0; p < wpr; ++p) df_acc(red[tid * wpr + p], s, c);
-      const float2 u = df_norm(s, c);
-      us[tid] = u;
-      a.MQ[(int64_t)j * N + n0 + tid] = u;
+      us[tid] = df_norm(s, c);
     }
     __syncthreads();
     if (warp == 0) {
       float s = 0.0f, c = 0.0f;
-      for (int e = lane; e < ne; e += 32) df_mac(Qs[(int64_t)e * qcap + j], us[e], s, c);
+      for (int e = lane; e < ne; e += 32) df_mac(qf[n0 + e], qf[n0 + e], s, c);
       const float2 t = df_warp_sum(s, c);
-      if (lane == 0) a.apart[blockIdx.x] = t;
+      if (lane == 0) a.apart[(int64_t)blockIdx.x * 4 + 0] = t;
+    } else if (warp == 1 && full) {
+      float s = 0.0f, c = 0.0f;
+      for (int e = lane; e < ne; e += 32) df_mac(qf[n0 + e], us[e], s, c);
+      const float2 t = df_warp_sum(s, c);
+      if (lane == 0) a.apart[(int64_t)blockIdx.x * 4 + 1] = t;
     }
     if (!grid_barrier_at(a.bar, a.err, a.bar_limit)) return;
-    // ---- 2: w' on the owned slice, partials of the second pass
-    const float2 ap = tid < G ? a.apart[tid] : make_float2(0.0f, 0.0f);
+    // ---- 2: the coefficients and norms; q_j, u, alpha_j, h and w
     for (int i = tid; i < j; i += kDfThreads) {
-      float2 v[kDfMaxChunks];
+      float2 vc[kDfMaxChunks], vg[kDfMaxChunks];
 #pragma unroll
-      for (int ch = 0; ch < kDfMaxChunks; ++ch)
-        v[ch] = ch < a.nch ? a.h[(int64_t)i * a.nch + ch] : make_float2(0.0f, 0.0f);
-      float s = 0.0f, c = 0.0f;
+      for (int chn = 0; chn < kDfMaxChunks; ++chn) {
+        vc[chn] = chn < a.nch ? a.hc[(int64_t)i * a.nch + chn] : make_float2(0.0f, 0.0f);
+        vg[chn] = full && chn < a.nch ? a.hg[(int64_t)i * a.nch + chn] : make_float2(0.0f, 0.0f);
+      }
+      float s = 0.0f, c = 0.0f, s2 = 0.0f, c2 = 0.0f;
 #pragma unroll
-      for (int ch = 0; ch < kDfMaxChunks; ++ch) df_acc(v[ch], s, c);
-      cf[i] = df_norm(s, c);
+      for (int chn = 0; chn < kDfMaxChunks; ++chn) {
+        df_acc(vc[chn], s, c);
+        df_acc(vg[chn], s2, c2);
+      }
+      cc[i] = df_norm(s, c);
+      cg[i] = df_norm(s2, c2);
     }
-    if (tid < G) red[tid] = ap;
+    if (warp == kDfWarps - 1) {
+      const float2 t = df_block_sum(a.apart, 0, G);
+      if (lane == 0) s_nu = t;
+    } else if (warp == kDfWarps - 2 && full) {
+      const float2 t = df_block_sum(a.apart, 1, G);
+      if (lane == 0) s_at = t;
+    }
     __syncthreads();
-    if (warp == 0) {
+    // q~_j - Q c and u~ - (MQ) c on the owned slice (the first warps), T_j c
+    // and the sums ||c||^2, c.g, c.T_j c (the last three)
+    if (warp < kDfWarps - 3) {
+      df_combine(Qs, qcap, cc, j, qf + n0, qn, ne, 0, kDfWarps - 3);
+      if (full) df_combine(MQs, qcap, cc, j, us, us, ne, 0, kDfWarps - 3);
+    } else {
+      const int w3 = warp - (kDfWarps - 3);
       float s = 0.0f, c = 0.0f;
-      for (int b = lane; b < G; b += 32) df_acc(red[b], s, c);
+      for (int i = lane; i < j; i += 32) {
+        const float2 ci = cc[i];
+        if (w3 == 0) {
+          df_mac(ci, ci, s, c);
+        } else if (w3 == 1) {
+          df_mac(ci, cg[i], s, c);
+        } else {
+          // (T_j c)_i over the entries of T_j (indices below j)
+          float ts = 0.0f, tcr = 0.0f;
+          df_mac(Ta[i], ci, ts, tcr);
+          if (i > 0) df_mac(Tb[i - 1], cc[i - 1], ts, tcr);
+          if (i + 1 < j) df_mac(Tb[i], cc[i + 1], ts, tcr);
+          const float2 tci = df_norm(ts, tcr);
+          ch[i] = tci;
+          df_mac(ci, tci, s, c);
+        }
+      }
       const float2 t = df_warp_sum(s, c);
       if (lane == 0) {
-        cf[j] = t;
-        s_h = t;
+        if (w3 == 0) s_cc = t;
+        else if (w3 == 1) s_cgd = t;
+        else s_ctc = t;
       }
-    }
-    __syncthreads();
-    df_combine(Qs, qcap, cf, j + 1, us, ws, ne);
-    __syncthreads();
-    for (int i = tid; i <= j + 1; i += kDfThreads) {
-      float s = 0.0f, c = 0.0f;
-      if (i <= j) {
-        for (int e = 0; e < ne; ++e) df_mac(Qs[(int64_t)e * qcap + i], ws[e], s, c);
-      } else {
-        for (int e = 0; e < ne; ++e) df_mac(ws[e], ws[e], s, c);
-      }
-      a.part[(int64_t)blockIdx.x * a.pst + i] = df_norm(s, c);
-    }
-    if (!grid_barrier_at(a.bar, a.err, a.bar_limit)) return;
-    // ---- 3: d and ||w'||^2 from the partials (R threads per coefficient
-    // over interleaved blocks, then in order of r)
-    {
-      const int C = j + 2;
-      int R = 1;
-      while (R < 32 && 2 * R * C <= kDfThreads && 2 * R <= G) R *= 2;
-      for (int i0 = 0; i0 < C; i0 += kDfRed / R) {
-        const int cn = min(C - i0, kDfRed / R);
-        for (int t = tid; t < R * cn; t += kDfThreads) {
-          const int r = t / cn, i = i0 + t % cn;
-          float s = 0.0f, c = 0.0f;
-          // kDfBatch loads in flight per batch
-          for (int b0 = r; b0 < G; b0 += kDfBatch * R) {
-            float2 v[kDfBatch];
-#pragma unroll
-            for (int u = 0; u < kDfBatch; ++u) {
-              const int b = b0 + u * R;
-              v[u] = b < G ? a.part[(int64_t)b * a.pst + i] : make_float2(0.0f, 0.0f);
-            }
-#pragma unroll
-            for (int u = 0; u < kDfBatch; ++u) df_acc(v[u], s, c);
-          }
-          red[r * cn + (i - i0)] = df_norm(s, c);
-        }
-        __syncthreads();
-        for (int i = tid; i < cn; i += kDfThreads) {
-          float s = 0.0f, c = 0.0f;
-          for (int r = 0; r < R; ++r) df_acc(red[r * cn + i], s, c);
-          cf[i0 + i] = df_norm(s, c);
-        }
-        __syncthreads();
-      }
-    }
-    // the last warp sums ||d||^2 while the others form w on the slice
-    if (warp == kDfWarps - 1) {
-      float s = 0.0f, c = 0.0f;
-      for (int i = lane; i <= j; i += 32) df_mac(cf[i], cf[i], s, c);
-      const float2 t = df_warp_sum(s, c);
-      if (lane == 0) s_dd = t;
-    } else {
-      df_combine(Qs, qcap, cf, j + 1, ws, ws, ne, 0, kDfWarps - 1);
-    }
-    __syncthreads();
-    const float2 nw2 = cf[j + 1];
-    const bool direct = s_dd.x > 0.25f * nw2.x;  // the same decision in every block
-    if (direct) {
-      __syncthreads();
-      if (warp == 0) {
-        float s = 0.0f, c = 0.0f;
-        for (int e = lane; e < ne; e += 32) df_mac(ws[e], ws[e], s, c);
-        const float2 t = df_warp_sum(s, c);
-        // (apart is free: every block read it before the second barrier)
-        if (lane == 0) a.apart[blockIdx.x] = t;
-      }
-      if (!grid_barrier_at(a.bar, a.err, a.bar_limit)) return;
-      if (warp == 0) {
-        float s = 0.0f, c = 0.0f;
-        for (int b = lane; b < G; b += 32) df_acc(a.apart[b], s, c);
-        const float2 t = df_warp_sum(s, c);
-        if (lane == 0) s_beta2 = t;
-      }
-    } else if (tid == 0) {
-      s_beta2 = df_sub(nw2, s_dd);
     }
     __syncthreads();
     if (tid == 0) {
-      const float2 al = df_add(s_h, cf[j]);
-      const float2 be = df_sqrt(s_beta2);
-      const float sc = fmaxf(s_scale, fmaxf(fabsf(al.x), be.x));
-      s_scale = sc;
-      const int brk = !(be.x > 1e-12f * sc) || sc == 0.0f;
-      s_brk = brk;
-      s_rb = brk ? make_float2(0.0f, 0.0f) : df_rcp(be);
-      if (blockIdx.x == 0) {
-        a.alpha[j] = df_val(al) * unscale;
-        a.beta[j] = brk ? 0.0 : df_val(be) * unscale;
-        if (brk) *a.stop = j + 1;
-      }
+      const float2 nu = s_nu, c2 = s_cc;
+      s_direct = c2.x > 0.25f * nu.x;  // the same decision in every block
+      s_r2 = df_sub(nu, c2);
     }
     __syncthreads();
-    if (s_brk) return;  // the same decision in every block
-    const float2 rb = s_rb;
-    for (int e = tid; e < ne; e += kDfThreads) {
-      const float2 q = df_mul(ws[e], rb);
-      if (j + 1 < qcap) Qs[(int64_t)e * qcap + j + 1] = q;
-      if (j + 1 < a.mcap) a.Q[(int64_t)(j + 1) * N + n0 + e] = q;
+    if (s_direct) {
+      if (warp == 0) {
+        float s = 0.0f, c = 0.0f;
+        for (int e = lane; e < ne; e += 32) df_mac(qn[e], qn[e], s, c);
+        const float2 t = df_warp_sum(s, c);
+        if (lane == 0) a.apart[(int64_t)blockIdx.x * 4 + 2] = t;
+      }
+      if (!grid_barrier_at(a.bar, a.err, a.bar_limit)) return;
+      if (warp == 0) {
+        const float2 t = df_block_sum(a.apart, 2, G);
+        if (lane == 0) s_r2 = t;
+      }
+      __syncthreads();
     }
+    if (tid == 0) {
+      const float2 r = df_sqrt(s_r2);
+      float sc = s_scale;
+      int brk = 0;
+      if (j > a.m0) {
+        // r = beta_{j-1}
+        brk = !(r.x > 1e-12f * sc) || sc == 0.0f;
+        if (!brk) {
+          sc = fmaxf(sc, r.x);
+          Tb[j - 1] = r;
+        }
+        if (blockIdx.x == 0) {
+          a.beta[j - 1] = brk ? 0.0 : df_val(r) * unscale;
+          if (brk) *a.stop = j;
+        }
+      }
+      s_brk = brk;
+      s_rinv = r.x > 0.0f ? df_rcp(r) : make_float2(0.0f, 0.0f);
+      if (full && !brk) {
+        // alpha_j = (a~ - 2 c.g + c.T_j c) / r^2
+        const float2 ri = s_rinv;
+        const float2 num = df_add(df_sub(s_at, df_add(s_cgd, s_cgd)), s_ctc);
+        const float2 al = df_mul(df_mul(num, ri), ri);
+        sc = fmaxf(sc, fabsf(al.x));
+        Ta[j] = al;
+        ch[j] = al;
+        if (blockIdx.x == 0) a.alpha[j] = df_val(al) * unscale;
+      }
+      s_scale = sc;
+    }
+    __syncthreads();
+    if (s_brk || !full) return;  // the same decision in every block
+    const float2 rinv = s_rinv;
+    // h_i = (g_i - (T_j c)_i) / r; q_j, u on the slice
+    for (int i = tid; i < j; i += kDfThreads) ch[i] = df_mul(df_sub(cg[i], ch[i]), rinv);
+    for (int e = tid; e < ne; e += kDfThreads) {
+      const float2 q = df_mul(qn[e], rinv), u = df_mul(us[e], rinv);
+      qn[e] = q;
+      us[e] = u;
+      Qs[(int64_t)e * qcap + j] = q;
+      MQs[(int64_t)e * qcap + j] = u;
+      a.Q[(int64_t)j * N + n0 + e] = q;
+      a.MQ[(int64_t)j * N + n0 + e] = u;
+    }
+    __syncthreads();
+    // w = u - sum_{i<j} h_i q_i - alpha_j q_j, handed on as q~_{j+1}
+    df_combine(Qs, qcap, ch, j + 1, us, ws, ne);
+    __syncthreads();
+    for (int e = tid; e < ne; e += kDfThreads) a.Q[(int64_t)(j + 1) * N + n0 + e] = ws[e];
     if (!grid_barrier_at(a.bar, a.err, a.bar_limit)) return;
   }
 }
@@ -1114,15 +1162,6 @@ __global__ void df_restart_kernel(float2* Q, int64_t N, int m, uint64_t key) {
   s = block_sum(s, sh);
   const double inv = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
   for (int64_t n = threadIdx.x; n < N; n += blockDim.x) Q[(int64_t)m * N + n] = df_split(w[n] * inv);
-}
-
-// rows of hi/lo pairs -> FP64 in place
-__global__ void df_to_f64_kernel(double* Q, int64_t n) {
-  const float2* in = reinterpret_cast<const float2*>(Q);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = df_val(in[i]);
-    Q[i] = v;
-  }
 }
 
 // ------------------------------------------------------ back-projection ----
@@ -2147,7 +2186,7 @@ struct LzBufs {
   unsigned* bar = nullptr;
   int *err = nullptr, *cstart = nullptr, *stop = nullptr;
   // double-float kernel: block partials and the scale exponent of M
-  float2 *dfpart = nullptr, *dfapart = nullptr, *dfh = nullptr;
+  float2 *dfapart = nullptr, *dfh = nullptr, *dfg = nullptr;
   int* escale = nullptr;
 };
 
@@ -2155,7 +2194,7 @@ void plan_lz(Arena& ar, int64_t n, int k, LzBufs& b, double* Q, double* MQ) {
   b.n = n;
   b.mcap = n < (int64_t)8 * k + 512 ? n : (int64_t)8 * k + 512;
   const int64_t mcap = b.mcap;
-  b.Q = Q ? Q : ar.take<double>(mcap * n);
+  b.Q = Q ? Q : ar.take<double>((mcap + 1) * n);  // (the double-float kernel's q~ row)
   b.MQ = MQ ? MQ : ar.take<double>(mcap * n);
   b.w = ar.take<double>(n);
   b.wt = ar.take<double>(n);
@@ -2177,17 +2216,18 @@ void plan_lz(Arena& ar, int64_t n, int k, LzBufs& b, double* Q, double* MQ) {
   // global scratch of the tridiagonal kernels when shared memory is too small
   const int64_t tri_n = tridiag_scratch_doubles(mcap, k);
   b.tri_scratch = tri_n ? ar.take<double>(tri_n) : nullptr;
-  b.dfpart = ar.take<float2>((int64_t)kDfMaxGrid * (mcap + 2));
-  b.dfapart = ar.take<float2>(kDfMaxGrid);
+  b.dfapart = ar.take<float2>((int64_t)kDfMaxGrid * 4);
   b.dfh = ar.take<float2>((mcap + 2) * kDfMaxChunks);
+  b.dfg = ar.take<float2>((mcap + 2) * kDfMaxChunks);
   b.escale = ar.take<int>(1);
 }
 
 // Shared memory of the double-float kernel for grid g on an n x n matrix with
-// slices of q_0 .. q_{m1} (0 when the owned rows do not fit).
+// slices of q_0 .. q_{m1} and M q_0 .. M q_{m1}.
 size_t df_smem(int64_t n, int64_t g, int64_t mcap, int64_t m1) {
-  const int64_t E = cdiv(n, g);
-  const int64_t f2 = E * n + n + E * (m1 + 1) + 2 * E + (mcap + 2) + kDfRed;
+  (void)mcap;
+  const int64_t E = cdiv(n, g), qcap = m1 + 1;
+  const int64_t f2 = E * n + n + 2 * E * qcap + 3 * E + 5 * (qcap + 1) + kDfRed;
   return (size_t)f2 * sizeof(float2);
 }
 
@@ -2258,8 +2298,8 @@ hess_status run_lz_df(hess_mlp* h, double* M, int k, LzBufs& b, int grid, int* m
     a.N = N;
     a.Q = Q;
     a.MQ = MQ;
-    a.h = b.dfh;
-    a.part = b.dfpart;
+    a.hc = b.dfh;
+    a.hg = b.dfg;
     a.apart = b.dfapart;
     a.alpha = b.alpha;
     a.beta = b.beta;
@@ -2270,7 +2310,6 @@ hess_status run_lz_df(hess_mlp* h, double* M, int k, LzBufs& b, int grid, int* m
     a.m0 = m;
     a.m1 = (int)target;
     a.mcap = (int)mcap;
-    a.pst = (int)(mcap + 2);
     a.qcap = (int)target + 1;
     a.nch = (int)cdiv(N, kDfChunk);
     a.bar_limit = lim > 0 ? lim : BAR_TIMEOUT;
