@@ -104,7 +104,8 @@ void host_side_free(hess_mlp* h) {
   if (h->stream2) cudaStreamDestroy(h->stream2);
   if (h->stream3) cudaStreamDestroy(h->stream3);
   if (h->stream4) cudaStreamDestroy(h->stream4);
-  h->stream2 = h->stream3 = h->stream4 = nullptr;
+  if (h->stream5) cudaStreamDestroy(h->stream5);
+  h->stream2 = h->stream3 = h->stream4 = h->stream5 = nullptr;
   if (h->host_pinned) cudaFreeHost(h->host_pinned);
   if (h->err_host) cudaFreeHost(h->err_host);
   h->host_pinned = nullptr;

@@ -1,5 +1,5 @@
 // All curvature matrices of one network and one data set in one call, with
-// the work of the three on four streams:
+// the work of the three on five streams:
 //
 //   stream A (the handle's)    : forward/backward, the tensor-core operands
 //                                and the contractions of the OPG and the
@@ -11,6 +11,10 @@
 //                                behind its contraction, in two halves (one
 //                                per stream, so that two copy engines share
 //                                each transfer)
+//   stream E (5th)             : the Hessian's tensor-core operands (R-operator
+//                                blocks, W rows, F planes), behind A's
+//                                forward/backward pass; the Hessian's
+//                                contraction waits for them, the OPG's does not
 //
 // Stream B has the higher priority: the eigen step is the longer chain of
 // short launches, and its blocks are scheduled first when both streams have
@@ -44,7 +48,7 @@ hess_status on_device(const hess_mlp* h, const void* p, bool* dev) {
 }
 
 struct EventSet {
-  cudaEvent_t e[7] = {};
+  cudaEvent_t e[9] = {};
   ~EventSet() {
     for (cudaEvent_t x : e)
       if (x) cudaEventDestroy(x);
@@ -93,7 +97,8 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
   }
   if (!h->stream3) HM_CUDA(cudaStreamCreateWithFlags(&h->stream3, cudaStreamNonBlocking));
   if (!h->stream4) HM_CUDA(cudaStreamCreateWithFlags(&h->stream4, cudaStreamNonBlocking));
-  const cudaStream_t sA = h->stream, sB = h->stream2, sC = h->stream3, sD = h->stream4;
+  if (!h->stream5) HM_CUDA(cudaStreamCreateWithFlags(&h->stream5, cudaStreamNonBlocking));
+  const cudaStream_t sA = h->stream, sB = h->stream2, sC = h->stream3, sD = h->stream4, sE = h->stream5;
   // the persistent contractions take the SMs the eigen step's Lanczos
   // launches leave free, so that the two overlap -- unless a matrix goes to
   // a host buffer: then its copy (the longest part of such a call) should
@@ -116,6 +121,7 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
   auto drain_copies = [&]() {
     cudaStreamSynchronize(sC);
     cudaStreamSynchronize(sD);
+    cudaStreamSynchronize(sE);
   };
 
   // ---- workspace: region A (tensor-core operands and tables), region B
@@ -163,6 +169,11 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
     }
     return HESS_OK;
   };
+  // the Hessian's operands are prepared on stream E (behind the FP32
+  // forward/backward pass on A), so that the OPG's contraction starts as
+  // soon as its own operands and the Gram matrix are ready
+  TcFork fork;
+  fork.s = sE;
   auto prep = [&](Arena& ar, bool live) -> hess_status {
     {
       // one preparation (one forward/backward pass) for both matrices, then
@@ -170,7 +181,8 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
       // OPG's copy can start while the Hessian is contracted
       SplitGuard sg(splitA, kSplitBytes, h->sm_count);
       TcPlan both;
-      HM_TRY(tc_prep(h, TcItem{xs, ys, N, OPG != nullptr, H != nullptr, os, hs, x3}, ar, live, both, sA));
+      HM_TRY(tc_prep(h, TcItem{xs, ys, N, OPG != nullptr, H != nullptr, os, hs, x3}, ar, live, both, sA,
+                     live && H ? &fork : nullptr));
       tc_split_plan(both, OPG ? 1 : 0, plan_o, plan_h);
     }
     tabO = ar.off;
@@ -183,6 +195,8 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
   for (cudaEvent_t& e : ev.e) HM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   ev_in = ev.e[0];
   ev_fb = ev.e[6];
+  fork.after_fb = ev.e[7];
+  fork.done = ev.e[8];
   // the planning pass, or its result for a call of the same shape
   const int64_t key[16] = {N, (int64_t)prec, k, OPG ? 1 : 0, H ? 1 : 0, x_dev, y_dev, o_dev, hh_dev, ev_dev,
                            q_dev, sm_tc, (int64_t)h->op_limit, h->lz_blocks, P, 0};
@@ -237,6 +251,7 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
     hess_status st = HESS_OK;
     if (OPG && !o_dev && tc_status == HESS_OK) st = to_host(OPG, os, ev.e[2]);
     if (H && tc_status == HESS_OK && st == HESS_OK) {
+      HM_CUDA(cudaStreamWaitEvent(sA, fork.done, 0));  // its operands (stream E)
       Tick t(h, HESS_K_HCONTRACT, plan_h.hess_flops, 0.0);
       t.set_sms(sm_tc);
       Arena at{h->ws, tabH};

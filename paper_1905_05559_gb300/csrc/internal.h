@@ -154,6 +154,8 @@ struct hess_mlp {
   cudaStream_t stream2 = nullptr;
   cudaStream_t stream3 = nullptr;
   cudaStream_t stream4 = nullptr;
+  // the fused call's stream for the Hessian's operand preparation
+  cudaStream_t stream5 = nullptr;
   // batch object of hessian_minibatches (created on first use)
   hess_batch* mb_batch = nullptr;
   // second growable device buffer, for results that the single-call entry
@@ -494,7 +496,16 @@ hess_status tc_available(hess_mlp* h);
 // item's contractions read: forward/backward caches, split-BF16 operands, and
 // the Hessian entries outside the tensor-core blocks; appends the item's
 // jobs to the plan.  The caller provides the split-K scratch (SplitGuard).
-hess_status tc_prep(hess_mlp* h, const TcItem& it, Arena& ar, bool live, TcPlan& plan, cudaStream_t s);
+// With a fork (live calls), the Hessian's part runs on fork->s: it waits
+// for the forward/backward pass on s (event after_fb), and 'done' is recorded
+// behind it, so that the OPG's contraction need not wait for it.
+struct TcFork {
+  cudaStream_t s = nullptr;
+  cudaEvent_t after_fb = nullptr;
+  cudaEvent_t done = nullptr;
+};
+hess_status tc_prep(hess_mlp* h, const TcItem& it, Arena& ar, bool live, TcPlan& plan, cudaStream_t s,
+                    const TcFork* fork = nullptr);
 // Takes arena memory for the plan's job and tile tables; when live, copies
 // them there and starts one persistent launch over all tiles (longest first).
 hess_status tc_launch_plan(int sm_count, const TcPlan& plan, Arena& ar, bool live, bool x3, int* err,

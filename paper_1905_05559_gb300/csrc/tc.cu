@@ -1211,7 +1211,22 @@ static hess_status tune_job(int sm_count, int mode, int64_t nn, int nkb, bool x3
   return HESS_OK;
 }
 
-hess_status tc_prep(hess_mlp* h, const TcItem& it, Arena& ar, bool live, TcPlan& plan, cudaStream_t s) {
+namespace {
+// the handle's stream set to s for a scope (h may be null: nothing)
+struct StreamScope {
+  StreamScope(hess_mlp* h, cudaStream_t s) : h_(h), keep_(h ? h->stream : nullptr) {
+    if (h_) h_->stream = s;
+  }
+  ~StreamScope() {
+    if (h_) h_->stream = keep_;
+  }
+  hess_mlp* h_;
+  cudaStream_t keep_;
+};
+}  // namespace
+
+hess_status tc_prep(hess_mlp* h, const TcItem& it, Arena& ar, bool live, TcPlan& plan, cudaStream_t s,
+                    const TcFork* fork) {
   using namespace tc;
   using bf = __nv_bfloat16;
   const Net& net = h->net;
@@ -1223,6 +1238,11 @@ hess_status tc_prep(hess_mlp* h, const TcItem& it, Arena& ar, bool live, TcPlan&
   Caches<float> c;
   plan_caches(ar, net, N, c);
   if (live) HM_TRY(forward_backward(net, omega, it.X, it.Y, c, s));
+  const bool forked = live && fork && it.want_hess;
+  if (forked) {
+    HM_CUDA(cudaEventRecord(fork->after_fb, s));
+    HM_CUDA(cudaStreamWaitEvent(fork->s, fork->after_fb, 0));
+  }
   if (it.want_opg) {
     // OPG = G^T G / N (Sec. 3, the outer-product approximation): G is written
     // once in FP32, then split into K-major bf16 planes
@@ -1266,13 +1286,16 @@ hess_status tc_prep(hess_mlp* h, const TcItem& it, Arena& ar, bool live, TcPlan&
     // exact Hessian (Sec. 3, Eq. for H_ij) from the R-operator over the bias
     // directions of each weight layer: the W x W block (mode 1) and the W and
     // bias rows against the columns after W (mode 2), all on the tensor cores
+    // (on the fork's stream, with the per-class timing there too)
+    const cudaStream_t sh = forked ? fork->s : s;
+    StreamScope scope(th && forked ? h : nullptr, sh);
     int Tmax = 0;
     for (int jm = 1; jm < L; ++jm) Tmax = net.T[jm] > Tmax ? net.T[jm] : Tmax;
     RopBufs<float> r;
     plan_rop(ar, net, N, 1, Tmax, r);
     TQ tq;
     plan_tq(ar, net, ld, Tmax, tq);
-    if (live) HM_TRY(transpose_caches(net, c, N, ld, tq, s));
+    if (live) HM_TRY(transpose_caches(net, c, N, ld, tq, sh));
     for (int jm = 1; jm < L; ++jm) {
       const int Tin = net.T[jm - 1], Tout = net.T[jm];
       const int64_t boff = net.boff[jm - 1];
@@ -1292,12 +1315,12 @@ hess_status tc_prep(hess_mlp* h, const TcItem& it, Arena& ar, bool live, TcPlan&
         rb.B = Tout;
         {
           Tick t(th, HESS_K_ROP, 0.0, 0.0);
-          HM_TRY(rop_block(net, omega, c, jm, boff, Tout, rb, s));
+          HM_TRY(rop_block(net, omega, c, jm, boff, Tout, rb, sh));
         }
-        HM_TRY(transpose_rop(net, rb, jm, N, ld, tq, s));
-        HM_TRY(build_layer_b(net, c, jm, N, ld, bhi, blo, s));
-        HM_TRY(build_wrows(net, tq, jm, Tout, 0, ld, h->sm_count, ahi, alo, s));
-        HM_TRY(build_f(fa, 0, Tout, ld, h->sm_count, fhi, flo, s));
+        HM_TRY(transpose_rop(net, rb, jm, N, ld, tq, sh));
+        HM_TRY(build_layer_b(net, c, jm, N, ld, bhi, blo, sh));
+        HM_TRY(build_wrows(net, tq, jm, Tout, 0, ld, h->sm_count, ahi, alo, sh));
+        HM_TRY(build_f(fa, 0, Tout, ld, h->sm_count, fhi, flo, sh));
       }
       const int nkb = (int)(ld / BK);
       {
@@ -1309,7 +1332,7 @@ hess_status tc_prep(hess_mlp* h, const TcItem& it, Arena& ar, bool live, TcPlan&
         };
         bool untuned = false;
         int BN = choose_bn(1, Tin, nkb, it.x3, &untuned);
-        if (live && untuned) HM_TRY(tune_job(h->sm_count, 1, Tin, nkb, it.x3, build, h->stage, h->err_dev, s, &BN));
+        if (live && untuned) HM_TRY(tune_job(h->sm_count, 1, Tin, nkb, it.x3, build, h->stage, h->err_dev, sh, &BN));
         Job jw{};
         HM_TRY(build(BN, jw, plan.tiles));
         plan.jobs.push_back(jw);
@@ -1325,7 +1348,7 @@ hess_status tc_prep(hess_mlp* h, const TcItem& it, Arena& ar, bool live, TcPlan&
         };
         bool untuned = false;
         int BN = choose_bn(2, rest, nkb, it.x3, &untuned);
-        if (live && untuned) HM_TRY(tune_job(h->sm_count, 2, rest, nkb, it.x3, build, h->stage, h->err_dev, s, &BN));
+        if (live && untuned) HM_TRY(tune_job(h->sm_count, 2, rest, nkb, it.x3, build, h->stage, h->err_dev, sh, &BN));
         Job jf{};
         HM_TRY(build(BN, jf, plan.tiles));
         plan.jobs.push_back(jf);
@@ -1333,6 +1356,7 @@ hess_status tc_prep(hess_mlp* h, const TcItem& it, Arena& ar, bool live, TcPlan&
         plan.tiles_cap += plan.caps.back();
       }
     }
+    if (forked) HM_CUDA(cudaEventRecord(fork->done, sh));
   }
   return HESS_OK;
 }
