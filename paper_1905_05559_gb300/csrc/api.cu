@@ -106,6 +106,10 @@ void host_side_free(hess_mlp* h) {
   if (h->stream4) cudaStreamDestroy(h->stream4);
   if (h->stream5) cudaStreamDestroy(h->stream5);
   h->stream2 = h->stream3 = h->stream4 = h->stream5 = nullptr;
+  for (cudaEvent_t& e : h->fused_ev) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
   if (h->host_pinned) cudaFreeHost(h->host_pinned);
   if (h->err_host) cudaFreeHost(h->err_host);
   h->host_pinned = nullptr;
@@ -541,7 +545,7 @@ static hess_status run_eig(hess_mlp* h, const void* X, const void* Y, int64_t N,
     HM_TRY(convert((const float*)xsrc, xd, N * T1, s));
     HM_TRY(convert((const float*)ysrc, yd, N * TL, s));
   }
-  HM_TRY(forward_backward(net, (const double*)h->omega64, (const double*)xd, (const double*)yd, c, s));
+  HM_TRY(forward_backward(net, (const double*)h->omega64, (const double*)xd, (const double*)yd, c, s, true));
   {
     Tick t(h, HESS_K_EIG, 0.0, 0.0);
     HM_TRY(topk_eig_gram(h, net, c, N, k, evd, eqd, ar, false, &res));

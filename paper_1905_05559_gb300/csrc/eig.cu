@@ -2261,7 +2261,8 @@ int eig_lanczos_blocks(hess_mlp* h, int64_t n, int k) {
 constexpr uint64_t kLzKey = 0x5DEECE66Dull;  // the start vector's counter-based draw
 
 hess_status run_lz_df(hess_mlp* h, double* M, int k, LzBufs& b, int grid, int* m_out, bool* converged_out,
-                      bool m_split, bool q0_ready) {
+                      bool m_split, bool q0_ready, const std::function<hess_status(int)>* spec, int* spec_m) {
+  if (spec_m) *spec_m = -1;
   const int64_t N = b.n, mcap = b.mcap;
   cudaStream_t s = h->stream;
   const uint64_t key = kLzKey;
@@ -2339,6 +2340,12 @@ hess_status run_lz_df(hess_mlp* h, double* M, int k, LzBufs& b, int grid, int* m
       HM_TRY(tridiag_topk(b.alpha, b.beta, target, k, b.theta, b.cstart, b.Y, mcap, b.beta + (target - 1), b.rr,
                           b.mx, key + 11, b.tri_scratch, s));
     }
+    // the caller's work on the eigenpairs of T_target, queued before the
+    // flags are read (kept if they show convergence at target)
+    if (spec) {
+      HM_TRY((*spec)((int)target));
+      *spec_m = (int)target;
+    }
     HM_CUDA(cudaMemcpyAsync(hp, b.mx, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaMemcpyAsync(reinterpret_cast<int*>(hp + 2), b.err, sizeof(int), cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaMemcpyAsync(reinterpret_cast<int*>(hp + 2) + 1, b.stop, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -2366,6 +2373,7 @@ hess_status run_lz_df(hess_mlp* h, double* M, int k, LzBufs& b, int grid, int* m
     if (stopped >= 0) {
       // (reached only when the basis cannot grow: m == mcap) the eigenpairs
       // of the complete T_m
+      if (spec_m) *spec_m = -1;
       Tick t(h, HESS_K_TRIDIAG, 0.0, 0.0);
       HM_TRY(tridiag_topk(b.alpha, b.beta, m, k, b.theta, b.cstart, b.Y, mcap, b.beta + (m - 1), b.rr, b.mx,
                           key + 11, b.tri_scratch, s));
@@ -2384,6 +2392,7 @@ hess_status run_lz_df(hess_mlp* h, double* M, int k, LzBufs& b, int grid, int* m
   }
   if (converged && m >= N) {
     // the tridiagonal eigenpairs of the complete T (after a final breakdown)
+    if (spec_m) *spec_m = -1;
     Tick t(h, HESS_K_TRIDIAG, 0.0, 0.0);
     HM_TRY(tridiag_topk(b.alpha, b.beta, m, k, b.theta, b.cstart, b.Y, mcap, b.beta + (m - 1), b.rr, b.mx,
                         key + 11, b.tri_scratch, s));
@@ -2536,7 +2545,7 @@ hess_status run_lz(hess_mlp* h, const double* M, int k, LzBufs& b, int* m_out, b
 
 hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, int64_t N, int k,
                           double* evals_d, double* evecs_d, Arena& ar, bool dry, EigResult* res,
-                          const std::function<hess_status()>* after_gram) {
+                          const std::function<hess_status()>* after_gram, const EigSide* side) {
   const int64_t P = net.P;
   const int L = net.L;
   double* M = ar.take<double>(N * N);
@@ -2622,8 +2631,26 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   unsigned long long* best = ar.take<unsigned long long>((int64_t)2 * k * finalize_slices(P));
   F64GemmScratch fb;
   if (need.M) plan_f64_gemm_nt(ar, need, fb);
+  // the narrow layers' R when they run on the side stream
+  int64_t rs_max = 1;
+  for (int wl = 1; wl <= L - 1; ++wl)
+    if (!bp_mode[wl]) rs_max = std::max<int64_t>(rs_max, (int64_t)(net.T[wl - 1] + 1) * net.T[wl] * k);
+  double* Rs = ar.take<double>(rs_max);
   if (dry) return HESS_OK;
   cudaStream_t s = h->stream;
+  // the activations' digit split of the back-projection ahead of time, on
+  // the side stream, when exactly one layer's product uses the digit scratch
+  int a_pre = 0;
+  if (side && side->s) {
+    int users = 0;
+    for (int wl = 1; wl <= L - 1; ++wl)
+      if (bp_mode[wl]) {
+        ++users;
+        if (bp_mode[wl] == 1) a_pre = wl;
+      }
+    if (users != 1) a_pre = 0;
+    HM_CUDA(cudaEventRecord(side->ev[0], s));  // (the forward pass is done)
+  }
 
   // 1. Gram matrix, factored by layer: the wide layers' activation products
   // as exact-digit tensor-core planes, everything else in double-float in
@@ -2673,10 +2700,130 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   }
 
   if (after_gram) HM_TRY((*after_gram)());
-  int m = 0;
+  if (a_pre) {
+    // (on the side stream, behind its earlier work)
+    const int64_t Tin = net.T[a_pre - 1], cols = net.T[a_pre] * (int64_t)k;
+    F64GemmScratch f2 = fb;
+    f2.M = Tin + 1;
+    f2.Nn = cols < 256 ? cols : 256;
+    HM_CUDA(cudaStreamWaitEvent(side->s, side->ev[0], 0));
+    HM_TRY(f64_gemm_nt_split_a(c.a[a_pre - 1], Tin, N, f2, side->s, Tin));
+    HM_CUDA(cudaEventRecord(side->ev[3], side->s));
+  }
+
+  // 4. from the eigenpairs of T_m: Ritz vectors U = Q_m^T Y (N x k), the
+  // back-projection through G, the scaling and signs (queued by the
+  // double-float route as soon as the tridiagonal eigenpairs are, before
+  // their convergence is known, and again if they are replaced)
+  const bool narrow_side = side && side->s;
+  auto tail = [&](int m) -> hess_status {
+    if (dfg > 0) {
+      Tick t(h, HESS_K_BACKPROJ, 2.0 * N * m * k, 0.0);
+      const size_t sm = (size_t)kRitzC * m * sizeof(float2) + (size_t)4 * kRitzC * 32 * sizeof(float2);
+      ritz_df_kernel<<<dim3((unsigned)cdiv(N, 32), (unsigned)cdiv(k, kRitzC)), dim3(32, 4), sm, s>>>(
+          reinterpret_cast<const float2*>(Q), N, m, Y, mcap, k, U);
+      HM_LAUNCHED();
+    } else {
+      Tick t(h, HESS_K_BACKPROJ, 2.0 * N * m * k, 0.0);
+      Gemm<double> g;
+      g.M = (int)N;
+      g.N = k;
+      g.K = m;
+      g.A = Q;
+      g.sam = 1;
+      g.sak = N;
+      g.B = Y;
+      g.sbk = 1;
+      g.sbn = mcap;
+      g.C = U;
+      g.scm = k;
+      g.scn = 1;
+      HM_TRY(gemm(g, s));
+    }
+    if (narrow_side) {
+      HM_CUDA(cudaEventRecord(side->ev[1], s));
+      HM_CUDA(cudaStreamWaitEvent(side->s, side->ev[1], 0));
+    }
+    // q_c = G^T u_c without forming G: the block of weight layer w is
+    // R[j][(i, c)] = sum_n a[n][j] (delta[n][i] u[n][c]), its bias rows
+    // sum_n delta[n][i] u[n][c] (Eq. J with g_n = [delta_n (x) a_n; delta_n])
+    for (int wl = 1; wl <= L - 1; ++wl) {
+      const int64_t Tin = net.T[wl - 1], Tout = net.T[wl], cols = Tout * k;
+      if (!bp_mode[wl]) {
+        // R and its bias row Tin in one pass, without forming B (on the
+        // side stream, into its own R, beside the wide layers)
+        Tick t(narrow_side ? nullptr : h, HESS_K_BACKPROJ, 2.0 * N * (Tin + 1) * cols, 0.0);
+        const cudaStream_t sl = narrow_side ? side->s : s;
+        double* R = narrow_side ? Rs : Rf;
+        const dim3 grid((unsigned)cdiv(cols, 32), (unsigned)cdiv(Tin + 1, kBpRows), (unsigned)bp_slices);
+        bp_small_kernel<<<grid, dim3(32, 8), 0, sl>>>(c.a[wl - 1], (int)Tin, c.d[wl], (int)Tout, U, k, N, bp_nper,
+                                                      bp_part);
+        HM_LAUNCHED();
+        const int64_t rc = (Tin + 1) * cols;
+        bp_small_reduce_kernel<<<(unsigned)cdiv(rc, 256), 256, 0, sl>>>(bp_part, (int)bp_slices, rc, R);
+        HM_LAUNCHED();
+        const int64_t per = (Tin + 1) * Tout;
+        bp_scatter_kernel<<<(unsigned)(cdiv(per * k, 256) < 65536 ? cdiv(per * k, 256) : 65536), 256, 0, sl>>>(
+            R, R + Tin * cols, (int)Tin, (int)Tout, k, evecs_d, P, net.woff[wl - 1], net.boff[wl - 1]);
+        HM_LAUNCHED();
+        continue;
+      }
+      Tick t(h, HESS_K_BACKPROJ, 2.0 * N * Tout * k, 0.0);
+      bp_build_kernel<<<(unsigned)(cdiv(N * cols, 256) < 65536 ? cdiv(N * cols, 256) : 65536), 256, 0, s>>>(
+          c.d[wl], U, N, (int)Tout, k, Bf, bp_mode[wl] == 1 ? 1 : 0);
+      HM_LAUNCHED();
+      // the bias rows: row Tin of R (a row of ones appended to A^T), or their
+      // own product
+      const double* Rbl = Rb;
+      if (bp_mode[wl] == 1) {
+        // (B transposed: the digit split reads its rows along n, coalesced)
+        F64GemmScratch f2 = fb;
+        f2.M = Tin + 1;
+        f2.Nn = cols < 256 ? cols : 256;
+        if (wl == a_pre) HM_CUDA(cudaStreamWaitEvent(s, side->ev[3], 0));
+        HM_TRY(f64_gemm_nt_tc(h, c.a[wl - 1], Tin, Bf, N, 1, N, Rf, cols, 1, f2, s, cols, Tin, wl == a_pre));
+        Rbl = Rf + Tin * cols;
+      } else {
+        // R^T = B^T A: rows (i, c) of B^T against the Tin rows of A^T
+        F64GemmScratch f2 = fb;
+        f2.M = cols;
+        f2.Nn = Tin;
+        HM_TRY(f64_gemm_nt_tc(h, Bf, cols, c.a[wl - 1], 1, Tin, N, Rf, 1, cols, f2, s, Tin));
+        Gemm<double> g;
+        g.M = (int)Tout;
+        g.N = k;
+        g.K = (int)N;
+        g.A = c.d[wl];
+        g.sam = 1;
+        g.sak = Tout;
+        g.B = U;
+        g.sbk = k;
+        g.sbn = 1;
+        g.C = Rb;
+        g.scm = k;
+        g.scn = 1;
+        HM_TRY(gemm(g, s));
+      }
+      const int64_t per = (Tin + 1) * Tout;
+      bp_scatter_kernel<<<(unsigned)(cdiv(per * k, 256) < 65536 ? cdiv(per * k, 256) : 65536), 256, 0, s>>>(
+          Rf, Rbl, (int)Tin, (int)Tout, k, evecs_d, P, net.woff[wl - 1], net.boff[wl - 1]);
+      HM_LAUNCHED();
+    }
+    if (narrow_side) {
+      HM_CUDA(cudaEventRecord(side->ev[2], side->s));
+      HM_CUDA(cudaStreamWaitEvent(s, side->ev[2], 0));
+    }
+    Tick t(h, HESS_K_BACKPROJ, 0.0, 0.0);
+    HM_CUDA(cudaMemsetAsync(flag + 1, 0, sizeof(int), s));
+    HM_TRY(finalize_vectors(evecs_d, P, theta, k, (double)N, evals_d, flag + 1, best, s));
+    return HESS_OK;
+  };
+
+  int m = 0, spec_m = -1;
   bool converged = false;
   if (dfg > 0) {
-    HM_TRY(run_lz_df(h, M, k, lb, dfg, &m, &converged, true, true));
+    const std::function<hess_status(int)> spec = tail;
+    HM_TRY(run_lz_df(h, M, k, lb, dfg, &m, &converged, true, true, &spec, &spec_m));
   } else {
     HM_TRY(run_lz(h, M, k, lb, &m, &converged));
   }
@@ -2689,98 +2836,11 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
     res->flops = f;
   }
   res->converged = converged ? 1 : 0;
-
-  // 4. Ritz vectors U = Q_m^T Y (N x k), back-projection through G
-  if (dfg > 0) {
-    Tick t(h, HESS_K_BACKPROJ, 2.0 * N * m * k, 0.0);
-    const size_t sm = (size_t)kRitzC * m * sizeof(float2) + (size_t)4 * kRitzC * 32 * sizeof(float2);
-    ritz_df_kernel<<<dim3((unsigned)cdiv(N, 32), (unsigned)cdiv(k, kRitzC)), dim3(32, 4), sm, s>>>(
-        reinterpret_cast<const float2*>(Q), N, m, Y, mcap, k, U);
-    HM_LAUNCHED();
-  } else {
-    Tick t(h, HESS_K_BACKPROJ, 2.0 * N * m * k, 0.0);
-    Gemm<double> g;
-    g.M = (int)N;
-    g.N = k;
-    g.K = m;
-    g.A = Q;
-    g.sam = 1;
-    g.sak = N;
-    g.B = Y;
-    g.sbk = 1;
-    g.sbn = mcap;
-    g.C = U;
-    g.scm = k;
-    g.scn = 1;
-    HM_TRY(gemm(g, s));
-  }
-  // q_c = G^T u_c without forming G: the block of weight layer w is
-  // R[j][(i, c)] = sum_n a[n][j] (delta[n][i] u[n][c]), its bias rows
-  // sum_n delta[n][i] u[n][c] (Eq. J with g_n = [delta_n (x) a_n; delta_n])
-  for (int wl = 1; wl <= L - 1; ++wl) {
-    const int64_t Tin = net.T[wl - 1], Tout = net.T[wl], cols = Tout * k;
-    Tick t(h, HESS_K_BACKPROJ, bp_mode[wl] ? 2.0 * N * Tout * k : 2.0 * N * (Tin + 1) * cols, 0.0);
-    if (bp_mode[wl]) {
-      bp_build_kernel<<<(unsigned)(cdiv(N * cols, 256) < 65536 ? cdiv(N * cols, 256) : 65536), 256, 0, s>>>(
-          c.d[wl], U, N, (int)Tout, k, Bf, bp_mode[wl] == 1 ? 1 : 0);
-      HM_LAUNCHED();
-    }
-    // the bias rows: row Tin of R (a row of ones appended to A^T), or their
-    // own product
-    const double* Rbl = Rb;
-    if (bp_mode[wl] == 1) {
-      // (B transposed: the digit split reads its rows along n, coalesced)
-      F64GemmScratch f2 = fb;
-      f2.M = Tin + 1;
-      f2.Nn = cols < 256 ? cols : 256;
-      HM_TRY(f64_gemm_nt_tc(h, c.a[wl - 1], Tin, Bf, N, 1, N, Rf, cols, 1, f2, s, cols, Tin));
-      Rbl = Rf + Tin * cols;
-    } else if (bp_mode[wl] == 2) {
-      // R^T = B^T A: rows (i, c) of B^T against the Tin rows of A^T
-      F64GemmScratch f2 = fb;
-      f2.M = cols;
-      f2.Nn = Tin;
-      HM_TRY(f64_gemm_nt_tc(h, Bf, cols, c.a[wl - 1], 1, Tin, N, Rf, 1, cols, f2, s, Tin));
-    } else {
-      // R and its bias row Tin in one pass, without forming B
-      const dim3 grid((unsigned)cdiv(cols, 32), (unsigned)cdiv(Tin + 1, kBpRows), (unsigned)bp_slices);
-      bp_small_kernel<<<grid, dim3(32, 8), 0, s>>>(c.a[wl - 1], (int)Tin, c.d[wl], (int)Tout, U, k, N, bp_nper,
-                                                   bp_part);
-      HM_LAUNCHED();
-      const int64_t rc = (Tin + 1) * cols;
-      bp_small_reduce_kernel<<<(unsigned)cdiv(rc, 256), 256, 0, s>>>(bp_part, (int)bp_slices, rc, Rf);
-      HM_LAUNCHED();
-      Rbl = Rf + Tin * cols;
-    }
-    if (bp_mode[wl] == 2) {
-      Gemm<double> g;
-      g.M = (int)Tout;
-      g.N = k;
-      g.K = (int)N;
-      g.A = c.d[wl];
-      g.sam = 1;
-      g.sak = Tout;
-      g.B = U;
-      g.sbk = k;
-      g.sbn = 1;
-      g.C = Rb;
-      g.scm = k;
-      g.scn = 1;
-      HM_TRY(gemm(g, s));
-    }
-    const int64_t per = (Tin + 1) * Tout;
-    bp_scatter_kernel<<<(unsigned)(cdiv(per * k, 256) < 65536 ? cdiv(per * k, 256) : 65536), 256, 0, s>>>(
-        Rf, Rbl, (int)Tin, (int)Tout, k, evecs_d, P, net.woff[wl - 1], net.boff[wl - 1]);
-    HM_LAUNCHED();
-  }
-  {
-    Tick t(h, HESS_K_BACKPROJ, 0.0, 0.0);
-    HM_CUDA(cudaMemsetAsync(flag + 1, 0, sizeof(int), s));
-    HM_TRY(finalize_vectors(evecs_d, P, theta, k, (double)N, evals_d, flag + 1, best, s));
-  }
+  if (spec_m != m) HM_TRY(tail(m));
   int* hi = reinterpret_cast<int*>(hp);
   HM_CUDA(cudaMemcpyAsync(hi, flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
   HM_CUDA(cudaStreamSynchronize(s));
+  if (narrow_side) HM_CUDA(cudaStreamSynchronize(side->s));
   res->rank_deficient = hi[0];
   return HESS_OK;
 }

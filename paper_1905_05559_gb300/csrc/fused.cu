@@ -13,8 +13,11 @@
 //                                each transfer)
 //   stream E (5th)             : the Hessian's tensor-core operands (R-operator
 //                                blocks, W rows, F planes), behind A's
-//                                forward/backward pass; the Hessian's
-//                                contraction waits for them, the OPG's does not
+//                                forward/backward pass (the Hessian's
+//                                contraction waits for them, the OPG's does
+//                                not); then the eigen step's side work (the
+//                                back-projection's digit split of the
+//                                activations, its narrow layers)
 //
 // Stream B has the higher priority: the eigen step is the longer chain of
 // short launches, and its blocks are scheduled first when both streams have
@@ -46,14 +49,6 @@ hess_status on_device(const hess_mlp* h, const void* p, bool* dev) {
   *dev = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
   return HESS_OK;
 }
-
-struct EventSet {
-  cudaEvent_t e[9] = {};
-  ~EventSet() {
-    for (cudaEvent_t x : e)
-      if (x) cudaEventDestroy(x);
-  }
-};
 
 }  // namespace
 
@@ -163,7 +158,7 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
       SplitGuard sg(splitB, kSplitBytes, h->sm_count);
       HM_TRY(convert(xs, xd, N * T1, sB));
       HM_TRY(convert(ys, yd, N * TL, sB));
-      HM_TRY(forward_backward(net, (const double*)h->omega64, (const double*)xd, (const double*)yd, c64, sB));
+      HM_TRY(forward_backward(net, (const double*)h->omega64, (const double*)xd, (const double*)yd, c64, sB, true));
       HM_CUDA(cudaEventRecord(ev_fb, sB));
       HM_CUDA(cudaStreamWaitEvent(sA, ev_fb, 0));
     }
@@ -191,12 +186,18 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
     HM_TRY(tc_launch_plan(sm_tc, plan_h, ar, false, x3, h->err_dev, h->stage, sA));
     return HESS_OK;
   };
-  EventSet ev;
-  for (cudaEvent_t& e : ev.e) HM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-  ev_in = ev.e[0];
-  ev_fb = ev.e[6];
-  fork.after_fb = ev.e[7];
-  fork.done = ev.e[8];
+  for (cudaEvent_t& e : h->fused_ev)
+    if (!e) HM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaEvent_t* const ev = h->fused_ev;
+  ev_in = ev[0];
+  ev_fb = ev[6];
+  fork.after_fb = ev[7];
+  fork.done = ev[8];
+  // the eigen step's side work goes to stream E too, behind the Hessian's
+  // operands
+  EigSide eside;
+  eside.s = sE;
+  for (int i = 0; i < 4; ++i) eside.ev[i] = ev[9 + i];
   // the planning pass, or its result for a call of the same shape
   const int64_t key[16] = {N, (int64_t)prec, k, OPG ? 1 : 0, H ? 1 : 0, x_dev, y_dev, o_dev, hh_dev, ev_dev,
                            q_dev, sm_tc, (int64_t)h->op_limit, h->lz_blocks, P, 0};
@@ -249,7 +250,7 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
       tc_status = tc_launch_plan(sm_tc, plan_o, at, true, x3, h->err_dev, h->stage, sA);
     }
     hess_status st = HESS_OK;
-    if (OPG && !o_dev && tc_status == HESS_OK) st = to_host(OPG, os, ev.e[2]);
+    if (OPG && !o_dev && tc_status == HESS_OK) st = to_host(OPG, os, ev[2]);
     if (H && tc_status == HESS_OK && st == HESS_OK) {
       HM_CUDA(cudaStreamWaitEvent(sA, fork.done, 0));  // its operands (stream E)
       Tick t(h, HESS_K_HCONTRACT, plan_h.hess_flops, 0.0);
@@ -257,7 +258,7 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
       Arena at{h->ws, tabH};
       tc_status = tc_launch_plan(sm_tc, plan_h, at, true, x3, h->err_dev, h->stage, sA);
     }
-    if (H && !hh_dev && tc_status == HESS_OK && st == HESS_OK) st = to_host(H, hs, ev.e[3]);
+    if (H && !hh_dev && tc_status == HESS_OK && st == HESS_OK) st = to_host(H, hs, ev[3]);
     h->stream = keep;
     return tc_status != HESS_OK ? tc_status : st;
   };
@@ -270,8 +271,8 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
   // forward/backward pass and Gram matrix, instead of before queueing them)
   std::function<hess_status()> after_gram = [&]() -> hess_status {
     HM_TRY(prep_live());
-    HM_CUDA(cudaEventRecord(ev.e[1], sB));
-    HM_CUDA(cudaStreamWaitEvent(sA, ev.e[1], 0));
+    HM_CUDA(cudaEventRecord(ev[1], sB));
+    HM_CUDA(cudaStreamWaitEvent(sA, ev[1], 0));
     return contractions();
   };
   if (!overlap) {
@@ -294,7 +295,8 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
     {
       Tick t(h, HESS_K_EIG, 0.0, 0.0);
       Arena are{h->ws, offEig};
-      eig_status = topk_eig_gram(h, net, c64, N, k, evd, eqd, are, false, &res, overlap ? &after_gram : nullptr);
+      eig_status = topk_eig_gram(h, net, c64, N, k, evd, eqd, are, false, &res, overlap ? &after_gram : nullptr,
+                                 &eside);
       t.set_work(res.flops, 0.0);
     }
   }
@@ -308,12 +310,12 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
   if (!ev_dev) HM_CUDA(cudaMemcpyAsync(evals, evd, k * sizeof(double), cudaMemcpyDeviceToHost, sB));
   if (!q_dev) HM_CUDA(cudaMemcpyAsync(evecs, eqd, P * k * sizeof(double), cudaMemcpyDeviceToHost, sB));
   // stream A ends after everything of B and C
-  HM_CUDA(cudaEventRecord(ev.e[1], sB));
-  HM_CUDA(cudaStreamWaitEvent(sA, ev.e[1], 0));
-  HM_CUDA(cudaEventRecord(ev.e[4], sC));
-  HM_CUDA(cudaStreamWaitEvent(sA, ev.e[4], 0));
-  HM_CUDA(cudaEventRecord(ev.e[5], sD));
-  HM_CUDA(cudaStreamWaitEvent(sA, ev.e[5], 0));
+  HM_CUDA(cudaEventRecord(ev[1], sB));
+  HM_CUDA(cudaStreamWaitEvent(sA, ev[1], 0));
+  HM_CUDA(cudaEventRecord(ev[4], sC));
+  HM_CUDA(cudaStreamWaitEvent(sA, ev[4], 0));
+  HM_CUDA(cudaEventRecord(ev[5], sD));
+  HM_CUDA(cudaStreamWaitEvent(sA, ev[5], 0));
   if (host_io) {
     HM_CUDA(cudaStreamSynchronize(sA));
     HM_TRY(take_sticky_error(h));

@@ -156,6 +156,10 @@ struct hess_mlp {
   cudaStream_t stream4 = nullptr;
   // the fused call's stream for the Hessian's operand preparation
   cudaStream_t stream5 = nullptr;
+  // the fused call's ordering events (created on first use, re-recorded by
+  // every call)
+  static constexpr int kFusedEvents = 13;
+  cudaEvent_t fused_ev[kFusedEvents] = {};
   // batch object of hessian_minibatches (created on first use)
   hess_batch* mb_batch = nullptr;
   // second growable device buffer, for results that the single-call entry
@@ -276,9 +280,12 @@ struct Caches {
 };
 template <typename T>
 void plan_caches(Arena& ar, const Net& net, int64_t N, Caches<T>& c);
+// df_wide (FP64 only): the products of layers with 128 or more inputs in
+// double-float arithmetic (the eigen step's pass, whose later arithmetic is
+// double-float too).
 template <typename T>
 hess_status forward_backward(const Net& net, const T* omega, const T* X, const T* Y, Caches<T>& c,
-                             cudaStream_t s);
+                             cudaStream_t s, bool df_wide = false);
 template <typename T>
 hess_status write_grads(const Net& net, const Caches<T>& c, T* G, int64_t ldg, cudaStream_t s);
 template <typename T>
@@ -342,9 +349,18 @@ int eig_lanczos_blocks(hess_mlp* h, int64_t n, int k);
 // after_gram (optional) runs once the Gram matrix's kernels are queued and
 // before the first Lanczos launch (whose result the host waits for): the
 // fused call queues its contractions there, behind the Gram matrix.
+// side (optional): a second stream with four events, for the parts of the
+// eigen step that need not wait in line on the handle's stream (the
+// back-projection's split of the activations into digits, which needs
+// nothing but the forward pass, and the narrow layers' back-projection
+// beside the wide layers').
+struct EigSide {
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev[4] = {};
+};
 hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, int64_t N, int k,
                           double* evals_d, double* evecs_d, Arena& ar, bool dry, EigResult* res,
-                          const std::function<hess_status()>* after_gram = nullptr);
+                          const std::function<hess_status()>* after_gram = nullptr, const EigSide* side = nullptr);
 // Top-k eigenpairs of a resident symmetric n x n FP64 matrix M (row-major):
 // the same Lanczos, tridiagonal eigensolver and checks as the Gram route;
 // evecs_d row c = the unit eigenvector of evals_d[c] (sign canonicalised;
@@ -462,9 +478,14 @@ void plan_f64_gemm_nt(Arena& ar, const F64GemmNeed& nd, F64GemmScratch& fs);
 // plan's Nn; at most its Nt), in groups of the plan's Nn columns, all in one
 // tensor-core launch.  With Mg < M, G has Mg columns and the rows m >= Mg of
 // G^T are all ones (C's row m then sums B's row over k).
+// a_split: A's digits were formed by f64_gemm_nt_split_a (same G, K, fs, Mg)
+// earlier in stream order.
 hess_status f64_gemm_nt_tc(hess_mlp* h, const double* G, int64_t ldg, const double* B, int64_t b_rs, int64_t b_ks,
                            int64_t K, double* C, int64_t scm, int64_t scn, const F64GemmScratch& fs, cudaStream_t s,
-                           int64_t Nn_total = -1, int64_t Mg = -1);
+                           int64_t Nn_total = -1, int64_t Mg = -1, bool a_split = false);
+// The digit split of A = G^T alone (fs.DA, fs.exA), on stream s.
+hess_status f64_gemm_nt_split_a(const double* G, int64_t ldg, int64_t K, const F64GemmScratch& fs, cudaStream_t s,
+                                int64_t Mg = -1);
 
 // Jobs and tiles gathered for one persistent launch.
 struct TcPlan {

@@ -1,10 +1,12 @@
 // SIMT kernels of the plain FP64 / FP32 path: strided GEMM, the forward and
 // backward passes of the MLP, the per-example gradient writer, the batched
 // R-operator over blocks of unit directions, and the symmetric scatter that
-// places Hessian row blocks and their mirror images.
+// places Hessian row blocks and their mirror images; and the double-float
+// product of the eigen step's forward pass through a wide layer.
 #include <cstdint>
 #include <type_traits>
 
+#include "devmath.cuh"
 #include "internal.h"
 
 namespace hm {
@@ -536,14 +538,72 @@ template void plan_caches<float>(Arena&, const Net&, int64_t, Caches<float>&);
 
 // Forward pass (Sec. 2, Eq. modelfunc) and per-example back-propagation of
 // dC_n/dz^(l) (the per-example errors delta^(l)).
+// Z[n][o] = sum_i A[n][i] W[o][i] (A: N x K, W: T x K, Z: N x T, all FP64
+// row-major) in double-float arithmetic (devmath.cuh, about 48 significant
+// bits, on the FP32 pipe, where this GPU's FP64 rate would make the product
+// of a wide layer the longest launch of the pass).  Block (16, 8, 2): 16
+// outputs o (x) of 8 examples n (y), the two halves of each 64-wide slice of
+// K (z) summed at the end; the slices staged through shared memory as hi/lo
+// pairs.
+constexpr int kDfgK = 64;
+__global__ void __launch_bounds__(256) gemm_nt_df_kernel(const double* A, int64_t N, int K, const double* W, int T,
+                                                         double* Z) {
+  __shared__ float2 as[8][kDfgK + 1];
+  __shared__ float2 ws[16][kDfgK + 1];
+  __shared__ float2 half[8][16];
+  const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+  const int tid = tx + 16 * ty + 128 * tz;
+  const int64_t n = (int64_t)blockIdx.x * 8 + ty;
+  const int o = blockIdx.y * 16 + tx;
+  float s = 0.0f, c = 0.0f;
+  for (int k0 = 0; k0 < K; k0 += kDfgK) {
+    for (int e = tid; e < 8 * kDfgK; e += 256) {
+      const int r = e / kDfgK, k = e - r * kDfgK;
+      const int64_t nr = (int64_t)blockIdx.x * 8 + r;
+      as[r][k] = nr < N && k0 + k < K ? df_split(A[nr * K + k0 + k]) : make_float2(0.0f, 0.0f);
+    }
+    for (int e = tid; e < 16 * kDfgK; e += 256) {
+      const int r = e / kDfgK, k = e - r * kDfgK;
+      const int orow = blockIdx.y * 16 + r;
+      ws[r][k] = orow < T && k0 + k < K ? df_split(W[(int64_t)orow * K + k0 + k]) : make_float2(0.0f, 0.0f);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < kDfgK / 2; ++kk) df_mac(as[ty][tz * (kDfgK / 2) + kk], ws[tx][tz * (kDfgK / 2) + kk], s, c);
+    __syncthreads();
+  }
+  if (tz == 1) half[ty][tx] = df_norm(s, c);
+  __syncthreads();
+  if (tz == 0 && n < N && o < T) {
+    const float2 t = df_add(df_norm(s, c), half[ty][tx]);
+    Z[n * T + o] = df_val(t);
+  }
+}
+
 template <typename T>
 hess_status forward_backward(const Net& net, const T* omega, const T* X, const T* Y, Caches<T>& c,
-                             cudaStream_t s) {
+                             cudaStream_t s, bool df_wide) {
   const int L = net.L;
   const int64_t N = c.N;
   c.a[0] = X;
   for (int w = 1; w <= L - 1; ++w) {
     const int Tin = net.T[w - 1], Tout = net.T[w];
+    if constexpr (std::is_same<T, double>::value) {
+      if (df_wide && Tin >= 128) {
+        const dim3 grid((unsigned)cdiv(N, 8), (unsigned)cdiv(Tout, 16));
+        gemm_nt_df_kernel<<<grid, dim3(16, 8, 2), 0, s>>>(c.a[w - 1], N, Tin, omega + net.woff[w - 1], Tout, c.z);
+        HM_LAUNCHED();
+        const T* b = omega + net.boff[w - 1];
+        if (w < L - 1) {
+          bias_act_kernel<T><<<grid1d(N * Tout), 256, 0, s>>>(c.z, b, N, Tout, net.act[w - 1],
+                                                              const_cast<T*>(c.a[w]), c.s1[w], c.s2[w]);
+        } else {
+          softmax_kernel<T><<<(unsigned)cdiv(N, 8), 256, 0, s>>>(c.z, b, Y, N, Tout, c.p, c.d[w], c.ysum);
+        }
+        HM_LAUNCHED();
+        continue;
+      }
+    }
     Gemm<T> g;
     g.M = (int)N;
     g.N = Tout;
@@ -591,9 +651,9 @@ hess_status forward_backward(const Net& net, const T* omega, const T* X, const T
   return HESS_OK;
 }
 template hess_status forward_backward<double>(const Net&, const double*, const double*,
-                                              const double*, Caches<double>&, cudaStream_t);
+                                              const double*, Caches<double>&, cudaStream_t, bool);
 template hess_status forward_backward<float>(const Net&, const float*, const float*, const float*,
-                                             Caches<float>&, cudaStream_t);
+                                             Caches<float>&, cudaStream_t, bool);
 
 // ================================================== per-example gradients
 // G[n, woff + i*Tin + k] = delta[n,i] a[n,k];  G[n, boff + i] = delta[n,i].

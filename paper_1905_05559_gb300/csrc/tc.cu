@@ -2107,9 +2107,29 @@ void plan_f64_gemm_nt(Arena& ar, const F64GemmNeed& nd, F64GemmScratch& fs) {
   fs.tiles = ar.take<int4>(nd.tiles);
 }
 
+hess_status f64_gemm_nt_split_a(const double* G, int64_t ldg, int64_t K, const F64GemmScratch& fs, cudaStream_t s,
+                                int64_t Mg) {
+  using namespace tc;
+  const int64_t M = fs.M;
+  const int64_t mg = Mg < 0 ? M : Mg;
+  const int64_t ldk = (int64_t)align_up((size_t)K, BK);
+  if (mg < 1 || mg > M || M > fs.Mcap || ldk > fs.ldk)
+    return set_error(HESS_ERR_INVALID_ARG, "exact-digit product: bad operand of %lld x %lld", (long long)M,
+                     (long long)K);
+  // A = G^T: rows are the columns of G (rows [mg, M) all ones), split once
+  HM_CUDA(cudaMemsetAsync(fs.mxA, 0, (size_t)M * sizeof(unsigned long long), s));
+  const unsigned ry = (unsigned)std::max<int64_t>(1, std::min<int64_t>(16, cdiv(K, 64)));
+  colmax_bits_kernel<<<dim3((unsigned)cdiv(mg, 32), ry), dim3(32, 8), 0, s>>>(G, ldg, K, mg, fs.mxA);
+  HM_LAUNCHED();
+  digits_cols_kernel<<<dim3((unsigned)cdiv(ldk, 128), (unsigned)cdiv(M, 32)), dim3(32, 8), 0, s>>>(
+      G, ldg, K, mg, M, fs.mxA, fs.exA, ldk, fs.DA);
+  HM_LAUNCHED();
+  return HESS_OK;
+}
+
 hess_status f64_gemm_nt_tc(hess_mlp* h, const double* G, int64_t ldg, const double* B, int64_t b_rs, int64_t b_ks,
                            int64_t K, double* C, int64_t scm, int64_t scn, const F64GemmScratch& fs, cudaStream_t s,
-                           int64_t Nn_total, int64_t Mg) {
+                           int64_t Nn_total, int64_t Mg, bool a_split) {
   using namespace tc;
   const int64_t M = fs.M, Nn = fs.Nn;
   const int64_t Nt = Nn_total < 0 ? Nn : Nn_total;
@@ -2125,15 +2145,9 @@ hess_status f64_gemm_nt_tc(hess_mlp* h, const double* G, int64_t ldg, const doub
   {
     // (the only caller is the back-projection of the OPG eigen step)
     Tick tp(h, HESS_K_BACKPROJ, 0.0, 0.0);
-    // A = G^T: rows are the columns of G; B: rows (e, c') of each group of Nn
-    // columns, plane-major; both split once
-    HM_CUDA(cudaMemsetAsync(fs.mxA, 0, (size_t)M * sizeof(unsigned long long), s));
-    const unsigned ry = (unsigned)std::max<int64_t>(1, std::min<int64_t>(16, cdiv(K, 64)));
-    colmax_bits_kernel<<<dim3((unsigned)cdiv(mg, 32), ry), dim3(32, 8), 0, s>>>(G, ldg, K, mg, fs.mxA);
-    HM_LAUNCHED();
-    digits_cols_kernel<<<dim3((unsigned)cdiv(ldk, 128), (unsigned)cdiv(M, 32)), dim3(32, 8), 0, s>>>(
-        G, ldg, K, mg, M, fs.mxA, fs.exA, ldk, fs.DA);
-    HM_LAUNCHED();
+    // A = G^T (unless split beforehand) and B: rows (e, c') of each group of
+    // Nn columns, plane-major; both split once
+    if (!a_split) HM_TRY(f64_gemm_nt_split_a(G, ldg, K, fs, s, mg));
     digits_rows_kernel<<<(unsigned)cdiv(Nt, 2), 256, 0, s>>>(B, b_rs, b_ks, Nt, K, ldk, nullptr, nullptr, fs.RB,
                                                              fs.exB, Nn);
     HM_LAUNCHED();
