@@ -1445,19 +1445,19 @@ __global__ void bisect_kernel(const double* a, const double* b, int m, int k, do
 // CTA evaluates 128 of the kBisCta * 128 points of a sweep (the bracket
 // shrinks (kBisCta * 128 + 1)-fold), the CTAs exchange their first crossing
 // through distributed shared memory, and all of them take the same new
-// bracket, so they make the same number of cluster barriers.  FP64 Sturm
-// counts are bound by the SM's FP64 rate, so the sweeps of one eigenvalue
-// spread over kBisCta SMs.
+// bracket, so they make the same number of cluster barriers.  Two FP32
+// sweeps, then double-float sweeps down to 2^-40 ||T||: the eigenvalue to
+// about 1e-12 ||T||, which the inverse iteration's Rayleigh quotient takes to
+// FP64 rounding (FP64 Sturm counts, bound by this GPU's FP64 rate, are left
+// out).
 constexpr int kBisCta = 4;
 __global__ void bisect_cluster_kernel(const double* a, const double* b, int m, int k, double* theta) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ double tsh_c[];
-  double* sa = tsh_c;
-  double* sb2 = tsh_c + m;
-  float* fa = reinterpret_cast<float*>(tsh_c + 2 * m);
+  float* fa = reinterpret_cast<float*>(tsh_c);
   float* fb2 = fa + m;
-  float2* da = reinterpret_cast<float2*>(tsh_c + 3 * m);
+  float2* da = reinterpret_cast<float2*>(tsh_c + m);
   float2* db2 = da + m;
   __shared__ double s_lo, s_hi, s_sc;
   __shared__ int s4[32];
@@ -1493,8 +1493,6 @@ __global__ void bisect_cluster_kernel(const double* a, const double* b, int m, i
   for (int i = tid; i < m; i += nt) {
     const double ai = a[i] * sc;
     const double bi = i < m - 1 ? b[i] * sc : 0.0;
-    sa[i] = ai;
-    sb2[i] = bi * bi;
     fa[i] = (float)ai;
     fb2[i] = (float)(bi * bi);
     da[i] = df_split(ai);
@@ -1547,23 +1545,8 @@ __global__ void bisect_cluster_kernel(const double* a, const double* b, int m, i
     lo = nlo;
     hi = nhi;
   }
-  lo = fmax(lo0, lo - 9.1e-13);
-  hi = fmin(hi0, hi + 9.1e-13);
-  // down to a few ulps of the eigenvalue, or to 4 eps ||T|| (the accuracy of
-  // any backward-stable symmetric eigensolver) for eigenvalues much smaller
-  // than ||T||
-  const double tiny = 4.0 * DBL_MIN;
-  const double tol_abs = 4.0 * DBL_EPSILON * fmax(fabs(lo0), fabs(hi0));
-  for (int it = 0; it < 64; ++it) {
-    if (hi - lo <= fmax(2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)), tol_abs) + tiny) break;
-    const double x = lo + (hi - lo) * (double)(g + 1) * inv_n;
-    const int F = cluster_first(sturm_count(sa, sb2, m, x) > t);
-    const double nhi = F < np ? lo + (hi - lo) * (double)(F + 1) * inv_n : hi;
-    const double nlo = F > 0 ? lo + (hi - lo) * (double)F * inv_n : lo;
-    if (!(nlo < nhi)) break;
-    lo = nlo;
-    hi = nhi;
-  }
+  // (the inverse iteration refines the eigenvalue to FP64 rounding by the
+  // Rayleigh quotient of its vector)
   if (rank == 0 && tid == 0) theta[c] = 0.5 * (lo + hi) / sc;
 }
 
@@ -1575,7 +1558,7 @@ __global__ void bisect_cluster_kernel(const double* a, const double* b, int m, i
 // the fill, the reciprocal pivots and the norms are spread over the block.
 // Y: k rows of length ldy.
 // res[c] = |beta_m y_c[m-1]| bounds the residual of Ritz pair c.
-__global__ void inviter_kernel(const double* a, const double* b, int m, int k, const double* theta,
+__global__ void inviter_kernel(const double* a, const double* b, int m, int k, double* theta,
                                const int* cstart, double* Y, int64_t ldy, const double* beta_last,
                                double* res, uint64_t key, double* gscratch) {
   const int c0 = blockIdx.x;
@@ -1709,6 +1692,13 @@ __global__ void inviter_kernel(const double* a, const double* b, int m, int k, c
     }
     if (threadIdx.x == 0) res[c] = fabs(beta_m * y[m - 1]);
     for (int i = threadIdx.x; i < m; i += blockDim.x) Y[(int64_t)c * ldy + i] = y[i];
+    // theta_c = y^T T y (unit y): the eigenvalue to FP64 rounding (its error
+    // is quadratic in the vector's)
+    double rq = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x)
+      rq = fma(y[i], fma(a[i], y[i], i + 1 < m ? 2.0 * b[i] * y[i + 1] : 0.0), rq);
+    rq = block_sum(rq, sh);
+    if (threadIdx.x == 0) theta[c] = rq;
     __syncthreads();
   }
 }
@@ -1719,7 +1709,7 @@ __global__ void inviter_kernel(const double* a, const double* b, int m, int k, c
 // step costs a few FP32 latencies instead of several FP64 ones.  The
 // normalisation and the orthogonalisation within a cluster stay FP64, on an
 // FP64 copy of the vector.  Needs 7 m doubles of shared memory.
-__global__ void inviter_df_kernel(const double* a, const double* b, int m, int k, const double* theta,
+__global__ void inviter_df_kernel(const double* a, const double* b, int m, int k, double* theta,
                                   const int* cstart, double* Y, int64_t ldy, const double* beta_last, double* res,
                                   uint64_t key) {
   const int c0 = blockIdx.x;
@@ -1857,6 +1847,13 @@ __global__ void inviter_df_kernel(const double* a, const double* b, int m, int k
     }
     if (threadIdx.x == 0) res[c] = fabs(beta_m * y64[m - 1]);
     for (int i = threadIdx.x; i < m; i += blockDim.x) Y[(int64_t)c * ldy + i] = y64[i];
+    // theta_c = y^T T y (unit y, T unscaled): the eigenvalue to FP64
+    // rounding (its error is quadratic in the vector's)
+    double rq = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x)
+      rq = fma(y64[i], fma(a[i], y64[i], i + 1 < m ? 2.0 * b[i] * y64[i + 1] : 0.0), rq);
+    rq = block_sum(rq, sh);
+    if (threadIdx.x == 0) theta[c] = rq;
     __syncthreads();
   }
 }
@@ -2133,7 +2130,7 @@ hess_status tridiag_topk(const double* a, const double* b, int m, int k, double*
                          double* scratch, cudaStream_t s) {
   HM_TRY(eig_kernel_attributes());
   const bool inv_g = (size_t)6 * m * sizeof(double) > kEigSmemCap;
-  const bool bis_g = (size_t)5 * m * sizeof(double) > kEigSmemCap;
+  const bool bis_g = (size_t)3 * m * sizeof(double) > kEigSmemCap;
   if ((inv_g || bis_g) && !scratch) return set_error(HESS_ERR_INVALID_ARG, "tridiagonal scratch missing");
   // a cluster of CTAs per eigenvalue (T in each CTA's shared memory), or,
   // when T does not fit shared memory, one block per eigenvalue over global
@@ -2142,7 +2139,7 @@ hess_status tridiag_topk(const double* a, const double* b, int m, int k, double*
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(kBisCta * k));
     cfg.blockDim = dim3(128);
-    cfg.dynamicSmemBytes = (size_t)5 * m * sizeof(double);
+    cfg.dynamicSmemBytes = (size_t)3 * m * sizeof(double);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
