@@ -62,6 +62,26 @@ __device__ __forceinline__ float2 df_split(double v) {
   const float h = __double2float_rn(v);
   return make_float2(h, __double2float_rn(v - (double)h));
 }
+// The same pair from the bits of v with integer and FP32 operations only (no
+// FP64 conversion or arithmetic, which this GPU issues at a small fraction of
+// its FP32 rate): hi = v with its significand cut to 24 bits, lo = the other
+// 29 bits rounded to 24 (|lo| < ulp(hi)), so hi + lo = v to 2^-48 relative.
+// |v| below 2^-126 gives (0, 0); |v| of 2^128 and up, infinities and NaN take
+// the conversions of df_split.
+__device__ __forceinline__ float2 df_split_bits(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;  // unbiased exponent
+  if (e < -126) return make_float2(0.0f, 0.0f);
+  if (e > 127) return df_split(v);
+  const unsigned long long m = b & 0x000fffffffffffffull;
+  const float hi = __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | (unsigned)(m >> 29));
+  // lo = (the low 29 bits of the significand) 2^(e - 52)
+  const int el = e - 52;
+  float lo = __uint2float_rn((unsigned)(m & 0x1fffffffull));
+  lo = el >= -126 ? lo * __uint_as_float((unsigned)(el + 127) << 23) : ldexpf(lo, el);
+  return make_float2(hi, __uint_as_float(__float_as_uint(lo) | sgn));
+}
 __device__ __forceinline__ double df_val(float2 a) { return (double)a.x + (double)a.y; }
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;

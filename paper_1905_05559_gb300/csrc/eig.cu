@@ -1755,95 +1755,183 @@ __global__ void inviter_df_kernel(const double* a, const double* b, int m, int k
       du2[i] = make_float2(0.0f, 0.0f);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int i = 0; i < m - 1; ++i) {
-        if (fabsf(d[i].x) >= fabsf(dl[i].x)) {
-          piv[i] = 0;
-          if (fabsf(d[i].x) < tiny) d[i] = make_float2(d[i].x < 0.0f ? -tiny : tiny, 0.0f);
-          const float2 f = df_mul(dl[i], df_rcp(d[i]));
-          dl[i] = f;
-          d[i + 1] = df_sub(d[i + 1], df_mul(f, du[i]));
-        } else {
-          piv[i] = 1;
-          const float2 f = df_mul(d[i], df_rcp(dl[i]));
-          d[i] = dl[i];
-          dl[i] = f;
-          const float2 tmp = du[i];
-          du[i] = d[i + 1];
-          d[i + 1] = df_sub(tmp, df_mul(f, d[i + 1]));
-          if (i < m - 2) {
-            du2[i] = du[i + 1];
-            du[i + 1] = df_mul(make_float2(-f.x, -f.y), du[i + 1]);
-          }
-        }
-      }
-      if (fabsf(d[m - 1].x) < tiny) d[m - 1] = make_float2(d[m - 1].x < 0.0f ? -tiny : tiny, 0.0f);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < m; i += blockDim.x) d[i] = df_rcp(d[i]);
-    for (int i = threadIdx.x; i < m; i += blockDim.x) y[i] = df_split(1.0 + 0.25 * rnd_sym(key + c, i));
-    __syncthreads();
-    for (int it = 0; it < 2; ++it) {
+    if (c == c0 && (c + 1 >= k || cstart[c + 1] != c0)) {
+      // a cluster of one: the eigenvector from a twisted factorization of
+      // T - theta I (the pivots d+ from the top and d- from the bottom, one
+      // thread each; the twist r where gamma_r = d+_r + d-_r - (a_r - theta)
+      // is smallest in magnitude; then z_r = 1 and the products outward,
+      // z_i = -(b_i / d+_i) z_{i+1} above r, z_i = -(b_{i-1} / d-_i) z_{i-1}
+      // below), with no iteration
+      float2* dp = du2;
+      float2* dm = y;
       if (threadIdx.x == 0) {
-        for (int i = 0; i < m - 1; ++i) {
-          if (piv[i]) {
-            const float2 t = y[i];
-            y[i] = y[i + 1];
-            y[i + 1] = t;
-          }
-          y[i + 1] = df_sub(y[i + 1], df_mul(dl[i], y[i]));
+        float2 p = d[0];
+        if (fabsf(p.x) < tiny) p = make_float2(p.x < 0.0f ? -tiny : tiny, 0.0f);
+        dp[0] = p;
+        for (int i = 1; i < m; ++i) {
+          p = df_sub(d[i], df_mul(df_mul(du[i - 1], du[i - 1]), df_rcp(p)));
+          if (fabsf(p.x) < tiny) p = make_float2(p.x < 0.0f ? -tiny : tiny, 0.0f);
+          dp[i] = p;
         }
-        y[m - 1] = df_mul(y[m - 1], d[m - 1]);
-        if (m >= 2) y[m - 2] = df_mul(df_sub(y[m - 2], df_mul(du[m - 2], y[m - 1])), d[m - 2]);
-        for (int i = m - 3; i >= 0; --i)
-          y[i] = df_mul(df_sub(df_sub(y[i], df_mul(du[i], y[i + 1])), df_mul(du2[i], y[i + 2])), d[i]);
-      }
-      __syncthreads();
-      for (int i = threadIdx.x; i < m; i += blockDim.x) y64[i] = df_val(y[i]);
-      __syncthreads();
-      if (warp == 0) {
-        double mx = 0.0;
-        for (int i = lane; i < m; i += 32) mx = fmax(mx, fabs(y64[i]));
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) sh[0] = mx > 0.0 ? 1.0 / mx : 1.0;
-      }
-      __syncthreads();
-      const double inv = sh[0];
-      __syncthreads();
-      for (int i = threadIdx.x; i < m; i += blockDim.x) y64[i] *= inv;
-      __syncthreads();
-      // orthogonalise against the cluster's earlier vectors (twice)
-      const int nprev = c - c0;
-      for (int pass = 0; pass < 2 && nprev > 0; ++pass) {
-        for (int pb = 0; pb < nprev; pb += 1024) {
-          const int cnt = nprev - pb < 1024 ? nprev - pb : 1024;
-          for (int pi = warp; pi < cnt; pi += nwarp) {
-            const double* yp = Y + (int64_t)(c0 + pb + pi) * ldy;
-            double dot = 0.0;
-            for (int i = lane; i < m; i += 32) dot = fma(yp[i], y64[i], dot);
-            dot = warp_sum(dot);
-            if (lane == 0) sdot[pi] = dot;
-          }
-          __syncthreads();
-          for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            double sacc = 0.0;
-            for (int pi = 0; pi < cnt; ++pi) sacc = fma(sdot[pi], Y[(int64_t)(c0 + pb + pi) * ldy + i], sacc);
-            y64[i] -= sacc;
-          }
-          __syncthreads();
+      } else if (threadIdx.x == 32) {
+        float2 q = d[m - 1];
+        if (fabsf(q.x) < tiny) q = make_float2(q.x < 0.0f ? -tiny : tiny, 0.0f);
+        dm[m - 1] = q;
+        for (int i = m - 2; i >= 0; --i) {
+          q = df_sub(d[i], df_mul(df_mul(du[i], du[i]), df_rcp(q)));
+          if (fabsf(q.x) < tiny) q = make_float2(q.x < 0.0f ? -tiny : tiny, 0.0f);
+          dm[i] = q;
         }
       }
+      __syncthreads();
+      float gmin = FLT_MAX;
+      int gidx = m;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const float g = fabsf(df_sub(df_add(dp[i], dm[i]), d[i]).x);
+        if (g < gmin) {
+          gmin = g;
+          gidx = i;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float g2 = __shfl_xor_sync(0xffffffffu, gmin, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, gidx, o);
+        if (g2 < gmin || (g2 == gmin && i2 < gidx)) {
+          gmin = g2;
+          gidx = i2;
+        }
+      }
+      if (lane == 0) {
+        sdot[2 * warp] = (double)gmin;
+        sdot[2 * warp + 1] = (double)gidx;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double bg = sdot[0];
+        int bi = (int)sdot[1];
+        for (int w = 1; w < nwarp; ++w)
+          if (sdot[2 * w] < bg) {
+            bg = sdot[2 * w];
+            bi = (int)sdot[2 * w + 1];
+          }
+        piv[0] = bi;
+      }
+      __syncthreads();
+      const int r = piv[0];
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        if (i < r)
+          y64[i] = -df_val(df_mul(du[i], df_rcp(dp[i])));
+        else if (i > r)
+          y64[i] = -df_val(df_mul(du[i - 1], df_rcp(dm[i])));
+        else
+          y64[i] = 1.0;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        for (int i = r - 1; i >= 0; --i) y64[i] *= y64[i + 1];
+      } else if (threadIdx.x == 32) {
+        for (int i = r + 1; i < m; ++i) y64[i] *= y64[i - 1];
+      }
+      __syncthreads();
       double nn = 0.0;
       for (int i = threadIdx.x; i < m; i += blockDim.x) nn = fma(y64[i], y64[i], nn);
       nn = block_sum(nn, sh);
       if (threadIdx.x == 0) s_inv = nn > 0.0 ? rsqrt64(nn) : 0.0;
       __syncthreads();
       const double inv2 = s_inv;
-      for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        y64[i] *= inv2;
-        y[i] = df_split(y64[i]);
+      for (int i = threadIdx.x; i < m; i += blockDim.x) y64[i] *= inv2;
+      __syncthreads();
+    } else {
+      if (threadIdx.x == 0) {
+        for (int i = 0; i < m - 1; ++i) {
+          if (fabsf(d[i].x) >= fabsf(dl[i].x)) {
+            piv[i] = 0;
+            if (fabsf(d[i].x) < tiny) d[i] = make_float2(d[i].x < 0.0f ? -tiny : tiny, 0.0f);
+            const float2 f = df_mul(dl[i], df_rcp(d[i]));
+            dl[i] = f;
+            d[i + 1] = df_sub(d[i + 1], df_mul(f, du[i]));
+          } else {
+            piv[i] = 1;
+            const float2 f = df_mul(d[i], df_rcp(dl[i]));
+            d[i] = dl[i];
+            dl[i] = f;
+            const float2 tmp = du[i];
+            du[i] = d[i + 1];
+            d[i + 1] = df_sub(tmp, df_mul(f, d[i + 1]));
+            if (i < m - 2) {
+              du2[i] = du[i + 1];
+              du[i + 1] = df_mul(make_float2(-f.x, -f.y), du[i + 1]);
+            }
+          }
+        }
+        if (fabsf(d[m - 1].x) < tiny) d[m - 1] = make_float2(d[m - 1].x < 0.0f ? -tiny : tiny, 0.0f);
       }
       __syncthreads();
+      for (int i = threadIdx.x; i < m; i += blockDim.x) d[i] = df_rcp(d[i]);
+      for (int i = threadIdx.x; i < m; i += blockDim.x) y[i] = df_split(1.0 + 0.25 * rnd_sym(key + c, i));
+      __syncthreads();
+      for (int it = 0; it < 2; ++it) {
+        if (threadIdx.x == 0) {
+          for (int i = 0; i < m - 1; ++i) {
+            if (piv[i]) {
+              const float2 t = y[i];
+              y[i] = y[i + 1];
+              y[i + 1] = t;
+            }
+            y[i + 1] = df_sub(y[i + 1], df_mul(dl[i], y[i]));
+          }
+          y[m - 1] = df_mul(y[m - 1], d[m - 1]);
+          if (m >= 2) y[m - 2] = df_mul(df_sub(y[m - 2], df_mul(du[m - 2], y[m - 1])), d[m - 2]);
+          for (int i = m - 3; i >= 0; --i)
+            y[i] = df_mul(df_sub(df_sub(y[i], df_mul(du[i], y[i + 1])), df_mul(du2[i], y[i + 2])), d[i]);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < m; i += blockDim.x) y64[i] = df_val(y[i]);
+        __syncthreads();
+        if (warp == 0) {
+          double mx = 0.0;
+          for (int i = lane; i < m; i += 32) mx = fmax(mx, fabs(y64[i]));
+          for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+          if (lane == 0) sh[0] = mx > 0.0 ? 1.0 / mx : 1.0;
+        }
+        __syncthreads();
+        const double inv = sh[0];
+        __syncthreads();
+        for (int i = threadIdx.x; i < m; i += blockDim.x) y64[i] *= inv;
+        __syncthreads();
+        // orthogonalise against the cluster's earlier vectors (twice)
+        const int nprev = c - c0;
+        for (int pass = 0; pass < 2 && nprev > 0; ++pass) {
+          for (int pb = 0; pb < nprev; pb += 1024) {
+            const int cnt = nprev - pb < 1024 ? nprev - pb : 1024;
+            for (int pi = warp; pi < cnt; pi += nwarp) {
+              const double* yp = Y + (int64_t)(c0 + pb + pi) * ldy;
+              double dot = 0.0;
+              for (int i = lane; i < m; i += 32) dot = fma(yp[i], y64[i], dot);
+              dot = warp_sum(dot);
+              if (lane == 0) sdot[pi] = dot;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < m; i += blockDim.x) {
+              double sacc = 0.0;
+              for (int pi = 0; pi < cnt; ++pi) sacc = fma(sdot[pi], Y[(int64_t)(c0 + pb + pi) * ldy + i], sacc);
+              y64[i] -= sacc;
+            }
+            __syncthreads();
+          }
+        }
+        double nn = 0.0;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) nn = fma(y64[i], y64[i], nn);
+        nn = block_sum(nn, sh);
+        if (threadIdx.x == 0) s_inv = nn > 0.0 ? rsqrt64(nn) : 0.0;
+        __syncthreads();
+        const double inv2 = s_inv;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+          y64[i] *= inv2;
+          y[i] = df_split(y64[i]);
+        }
+        __syncthreads();
+      }
     }
     if (threadIdx.x == 0) res[c] = fabs(beta_m * y64[m - 1]);
     for (int i = threadIdx.x; i < m; i += blockDim.x) Y[(int64_t)c * ldy + i] = y64[i];
@@ -2258,7 +2346,8 @@ int eig_lanczos_blocks(hess_mlp* h, int64_t n, int k) {
 constexpr uint64_t kLzKey = 0x5DEECE66Dull;  // the start vector's counter-based draw
 
 hess_status run_lz_df(hess_mlp* h, double* M, int k, LzBufs& b, int grid, int* m_out, bool* converged_out,
-                      bool m_split, bool q0_ready, const std::function<hess_status(int)>* spec, int* spec_m) {
+                      bool m_split, bool q0_ready, const std::function<hess_status(int)>* spec, int* spec_m,
+                      const std::function<hess_status()>* after_launch) {
   if (spec_m) *spec_m = -1;
   const int64_t N = b.n, mcap = b.mcap;
   cudaStream_t s = h->stream;
@@ -2328,6 +2417,11 @@ hess_status run_lz_df(hess_mlp* h, double* M, int k, LzBufs& b, int grid, int* m
       Tick t(h, HESS_K_LANCZOS, fl, 0.0);
       HM_CUDA(cudaLaunchCooperativeKernel((void*)lanczos_df_kernel, gl, kDfThreads, kargs, dyn, s));
       HM_LAUNCHED();
+    }
+    // the caller's host work that may overlap the first launch
+    if (after_launch) {
+      HM_TRY((*after_launch)());
+      after_launch = nullptr;
     }
     // the tridiagonal eigenpairs of T_target are queued at once and read
     // with the kernel's flags (one host round trip); after a breakdown or a
@@ -2695,18 +2789,23 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
     }
     HM_TRY(flush());
   }
-
-  if (after_gram) HM_TRY((*after_gram)());
-  if (a_pre) {
-    // (on the side stream, behind its earlier work)
-    const int64_t Tin = net.T[a_pre - 1], cols = net.T[a_pre] * (int64_t)k;
-    F64GemmScratch f2 = fb;
-    f2.M = Tin + 1;
-    f2.Nn = cols < 256 ? cols : 256;
-    HM_CUDA(cudaStreamWaitEvent(side->s, side->ev[0], 0));
-    HM_TRY(f64_gemm_nt_split_a(c.a[a_pre - 1], Tin, N, f2, side->s, Tin));
-    HM_CUDA(cudaEventRecord(side->ev[3], side->s));
-  }
+  if (side && side->gram_done) HM_CUDA(cudaEventRecord(side->gram_done, s));
+  // the caller's hook and the side stream's digit split, once the first
+  // Lanczos launch is queued
+  const std::function<hess_status()> post_launch = [&]() -> hess_status {
+    if (after_gram) HM_TRY((*after_gram)());
+    if (a_pre) {
+      // (on the side stream, behind its earlier work)
+      const int64_t Tin = net.T[a_pre - 1], cols = net.T[a_pre] * (int64_t)k;
+      F64GemmScratch f2 = fb;
+      f2.M = Tin + 1;
+      f2.Nn = cols < 256 ? cols : 256;
+      HM_CUDA(cudaStreamWaitEvent(side->s, side->ev[0], 0));
+      HM_TRY(f64_gemm_nt_split_a(c.a[a_pre - 1], Tin, N, f2, side->s, Tin));
+      HM_CUDA(cudaEventRecord(side->ev[3], side->s));
+    }
+    return HESS_OK;
+  };
 
   // 4. from the eigenpairs of T_m: Ritz vectors U = Q_m^T Y (N x k), the
   // back-projection through G, the scaling and signs (queued by the
@@ -2820,8 +2919,9 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
   bool converged = false;
   if (dfg > 0) {
     const std::function<hess_status(int)> spec = tail;
-    HM_TRY(run_lz_df(h, M, k, lb, dfg, &m, &converged, true, true, &spec, &spec_m));
+    HM_TRY(run_lz_df(h, M, k, lb, dfg, &m, &converged, true, true, &spec, &spec_m, &post_launch));
   } else {
+    HM_TRY(post_launch());
     HM_TRY(run_lz(h, M, k, lb, &m, &converged));
   }
   res->lanczos_steps = m;

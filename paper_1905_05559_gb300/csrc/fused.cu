@@ -198,6 +198,7 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
   EigSide eside;
   eside.s = sE;
   for (int i = 0; i < 4; ++i) eside.ev[i] = ev[9 + i];
+  eside.gram_done = ev[1];
   // the planning pass, or its result for a call of the same shape
   const int64_t key[16] = {N, (int64_t)prec, k, OPG ? 1 : 0, H ? 1 : 0, x_dev, y_dev, o_dev, hh_dev, ev_dev,
                            q_dev, sm_tc, (int64_t)h->op_limit, h->lz_blocks, P, 0};
@@ -267,11 +268,11 @@ extern "C" hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y,
   // the free SMs beside the Lanczos launches; otherwise they are queued at
   // once and interleave with the eigen step.
   const bool overlap = sm_tc < h->sm_count;
-  // (the host builds A's operand preparation there, while the GPU runs B's
-  // forward/backward pass and Gram matrix, instead of before queueing them)
+  // (the host builds A's operand preparation there, once the GPU has B's
+  // forward/backward pass, Gram matrix and first Lanczos launch queued; the
+  // contractions wait for the Gram matrix, ev[1] on B)
   std::function<hess_status()> after_gram = [&]() -> hess_status {
     HM_TRY(prep_live());
-    HM_CUDA(cudaEventRecord(ev[1], sB));
     HM_CUDA(cudaStreamWaitEvent(sA, ev[1], 0));
     return contractions();
   };

@@ -346,17 +346,19 @@ hess_status tridiag_topk(const double* a, const double* b, int m, int k, double*
 // Blocks (one per SM) the Lanczos launches of the OPG eigen step take for N
 // examples and k eigenpairs.
 int eig_lanczos_blocks(hess_mlp* h, int64_t n, int k);
-// after_gram (optional) runs once the Gram matrix's kernels are queued and
-// before the first Lanczos launch (whose result the host waits for): the
-// fused call queues its contractions there, behind the Gram matrix.
+// after_gram (optional) runs once the Gram matrix's kernels and the first
+// Lanczos launch are queued, before the host waits for that launch's result:
+// the fused call queues its contractions there, behind side->gram_done.
 // side (optional): a second stream with four events, for the parts of the
 // eigen step that need not wait in line on the handle's stream (the
 // back-projection's split of the activations into digits, which needs
 // nothing but the forward pass, and the narrow layers' back-projection
-// beside the wide layers').
+// beside the wide layers'); gram_done (optional) is recorded on the
+// handle's stream behind the Gram matrix.
 struct EigSide {
   cudaStream_t s = nullptr;
   cudaEvent_t ev[4] = {};
+  cudaEvent_t gram_done = nullptr;
 };
 hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, int64_t N, int k,
                           double* evals_d, double* evecs_d, Arena& ar, bool dry, EigResult* res,

@@ -4,6 +4,7 @@
 // places Hessian row blocks and their mirror images; and the double-float
 // product of the eigen step's forward pass through a wide layer.
 #include <cstdint>
+#include <mutex>
 #include <type_traits>
 
 #include "devmath.cuh"
@@ -541,43 +542,86 @@ template void plan_caches<float>(Arena&, const Net&, int64_t, Caches<float>&);
 // Z[n][o] = sum_i A[n][i] W[o][i] (A: N x K, W: T x K, Z: N x T, all FP64
 // row-major) in double-float arithmetic (devmath.cuh, about 48 significant
 // bits, on the FP32 pipe, where this GPU's FP64 rate would make the product
-// of a wide layer the longest launch of the pass).  Block (16, 8, 2): 16
-// outputs o (x) of 8 examples n (y), the two halves of each 64-wide slice of
-// K (z) summed at the end; the slices staged through shared memory as hi/lo
-// pairs.
-constexpr int kDfgK = 64;
-__global__ void __launch_bounds__(256) gemm_nt_df_kernel(const double* A, int64_t N, int K, const double* W, int T,
-                                                         double* Z) {
-  __shared__ float2 as[8][kDfgK + 1];
-  __shared__ float2 ws[16][kDfgK + 1];
-  __shared__ float2 half[8][16];
+// of a wide layer the longest launch of the pass).  Block (16, 8, 8): 16
+// outputs o (x) of 8 examples n (y), the entries of K dealt to z by residue
+// mod 8 and the 8 partial sums added at the end in order of z; the 8 rows of
+// A and 16 rows of W staged in shared
+// memory as hi/lo pairs, kDfgK entries of K at a time (all of K, for the
+// layer widths of the workloads), with every load of a stage in flight at
+// once.
+constexpr int kDfgK = 1024;
+size_t gemm_nt_df_smem(int K) {
+  const int kc = K < kDfgK ? K : kDfgK;
+  return (size_t)24 * (kc + 1) * sizeof(float2);
+}
+constexpr int kDfgZ = 8;
+__global__ void __launch_bounds__(16 * 8 * kDfgZ) gemm_nt_df_kernel(const double* A, int64_t N, int K,
+                                                                     const double* W, int T, double* Z) {
+  extern __shared__ float2 gsh[];
+  __shared__ float2 part[kDfgZ][8][16];
+  const int kc = K < kDfgK ? K : kDfgK, ld = kc + 1;  // (odd row stride: no bank conflicts)
+  float2* as = gsh;             // 8 x ld
+  float2* ws = gsh + 8 * ld;    // 16 x ld
   const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
-  const int tid = tx + 16 * ty + 128 * tz;
+  const int tid = tx + 16 * ty + 128 * tz, nthr = 16 * 8 * kDfgZ;
   const int64_t n = (int64_t)blockIdx.x * 8 + ty;
   const int o = blockIdx.y * 16 + tx;
   float s = 0.0f, c = 0.0f;
-  for (int k0 = 0; k0 < K; k0 += kDfgK) {
-    for (int e = tid; e < 8 * kDfgK; e += 256) {
-      const int r = e / kDfgK, k = e - r * kDfgK;
-      const int64_t nr = (int64_t)blockIdx.x * 8 + r;
-      as[r][k] = nr < N && k0 + k < K ? df_split(A[nr * K + k0 + k]) : make_float2(0.0f, 0.0f);
-    }
-    for (int e = tid; e < 16 * kDfgK; e += 256) {
-      const int r = e / kDfgK, k = e - r * kDfgK;
-      const int orow = blockIdx.y * 16 + r;
-      ws[r][k] = orow < T && k0 + k < K ? df_split(W[(int64_t)orow * K + k0 + k]) : make_float2(0.0f, 0.0f);
+  for (int k0 = 0; k0 < K; k0 += kc) {
+    const int kn = K - k0 < kc ? K - k0 : kc;
+    // the 24 rows' entries k0 .. k0 + kn: eight loads in flight per thread
+    const int total = 24 * kn;
+    for (int e0 = tid; e0 < total; e0 += nthr * 8) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * nthr;
+        const int r = e / kn, k = e - r * kn;
+        v[u] = 0.0;
+        if (e < total) {
+          if (r < 8) {
+            const int64_t nr = (int64_t)blockIdx.x * 8 + r;
+            if (nr < N) v[u] = A[nr * K + k0 + k];
+          } else {
+            const int orow = blockIdx.y * 16 + (r - 8);
+            if (orow < T) v[u] = W[(int64_t)orow * K + k0 + k];
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * nthr;
+        if (e < total) {
+          const int r = e / kn, k = e - r * kn;
+          gsh[r * ld + k] = df_split_bits(v[u]);  // (as, then ws: rows 8 .. 23)
+        }
+      }
     }
     __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < kDfgK / 2; ++kk) df_mac(as[ty][tz * (kDfgK / 2) + kk], ws[tx][tz * (kDfgK / 2) + kk], s, c);
+    const float2* ar = as + ty * ld;
+    const float2* wr = ws + tx * ld;
+#pragma unroll 4
+    for (int k = tz; k < kn; k += kDfgZ) df_mac(ar[k], wr[k], s, c);
     __syncthreads();
   }
-  if (tz == 1) half[ty][tx] = df_norm(s, c);
+  part[tz][ty][tx] = df_norm(s, c);
   __syncthreads();
   if (tz == 0 && n < N && o < T) {
-    const float2 t = df_add(df_norm(s, c), half[ty][tx]);
-    Z[n * T + o] = df_val(t);
+    float ss = 0.0f, cs = 0.0f;
+    for (int z = 0; z < kDfgZ; ++z) df_acc(part[z][ty][tx], ss, cs);
+    Z[n * T + o] = df_val(df_norm(ss, cs));
   }
+}
+
+hess_status gemm_nt_df_attributes() {
+  static std::once_flag once;
+  static cudaError_t e = cudaSuccess;
+  std::call_once(once, [] {
+    e = cudaFuncSetAttribute(gemm_nt_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)gemm_nt_df_smem(kDfgK));
+  });
+  if (e != cudaSuccess) return set_error(HESS_ERR_CUDA, "double-float product attributes: %s", cudaGetErrorString(e));
+  return HESS_OK;
 }
 
 template <typename T>
@@ -590,8 +634,10 @@ hess_status forward_backward(const Net& net, const T* omega, const T* X, const T
     const int Tin = net.T[w - 1], Tout = net.T[w];
     if constexpr (std::is_same<T, double>::value) {
       if (df_wide && Tin >= 128) {
+        HM_TRY(gemm_nt_df_attributes());
         const dim3 grid((unsigned)cdiv(N, 8), (unsigned)cdiv(Tout, 16));
-        gemm_nt_df_kernel<<<grid, dim3(16, 8, 2), 0, s>>>(c.a[w - 1], N, Tin, omega + net.woff[w - 1], Tout, c.z);
+        gemm_nt_df_kernel<<<grid, dim3(16, 8, kDfgZ), gemm_nt_df_smem(Tin), s>>>(c.a[w - 1], N, Tin,
+                                                                             omega + net.woff[w - 1], Tout, c.z);
         HM_LAUNCHED();
         const T* b = omega + net.boff[w - 1];
         if (w < L - 1) {
