@@ -122,7 +122,7 @@ HESS_API hess_status hess_mlp_set_stream(hess_mlp* h, void* stream);
 HESS_API hess_status hess_mlp_set_operand_limit(hess_mlp* h, int64_t bytes);
 
 /* Blocks (one per SM) the Lanczos kernel of the OPG eigen step uses when the
- * Gram matrix's rows fit shared memory (0, the default: 7/12 of the SMs).
+ * Gram matrix's rows fit shared memory (0, the default: 8/15 of the SMs).
  * The kernel is bound by the latency of its grid barriers rather than by
  * arithmetic, so a grid smaller than the GPU costs it little and leaves SMs
  * to work that overlaps it: hess_curvature runs its contractions there.

@@ -2317,16 +2317,17 @@ size_t df_smem(int64_t n, int64_t g, int64_t mcap, int64_t m1) {
 }
 
 // Grid of the double-float kernel for an n x n matrix: the handle's
-// lz_blocks when set, else 7/12 of the SMs (the kernel waits on its grid
-// barriers far more than it computes: measured on this workload, 96 blocks
-// take the same time as 152, and the SMs left over run the contractions of
-// the fused call beside it; 86 blocks balance the two best there); 0 when the kernel does not apply (n above its
-// chunk table, or the owned rows and slices exceed shared memory even with a
-// block on every SM).
+// lz_blocks when set, else 8/15 of the SMs (the kernel waits on its grid
+// barriers far more than it computes, so a grid smaller than the GPU costs
+// it little, and the SMs left over run the contractions of the fused call
+// beside it: for 1024 examples on 152 SMs, 79 blocks of 13 rows balance the
+// two chains better than 86 blocks of 12); 0 when the kernel does not apply
+// (n above its chunk table, or the owned rows and slices exceed shared
+// memory even with a block on every SM).
 int df_grid(hess_mlp* h, int64_t n, int64_t mcap) {
   const int gmax = h->sm_count < kDfMaxGrid ? h->sm_count : kDfMaxGrid;
   if (gmax < 1 || n > (int64_t)kDfChunk * kDfMaxChunks || df_smem(n, gmax, mcap, mcap) > kEigSmemCap) return 0;
-  int g = h->lz_blocks > 0 ? h->lz_blocks : (h->sm_count * 7) / 12;
+  int g = h->lz_blocks > 0 ? h->lz_blocks : (h->sm_count * 8) / 15;
   if (g > gmax) g = gmax;
   if (g < 1) g = 1;
   if (n < g) g = (int)n;
