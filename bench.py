@@ -1287,7 +1287,7 @@ def main():
         "digits": "umma_gemm_kernel (exact-digit FP64 products of the Gram matrix and back-projection)",
         "lanczos": "lanczos kernel on the Gram matrix (cooperative launch)",
         "grads": "write_grads_kernel",
-        "tridiag": "bisect_cluster_kernel + inviter_kernel",
+        "tridiag": "bisect_cluster_kernel + inviter_df_kernel",
     }
 
     def class_roofline(cls):
