@@ -214,16 +214,19 @@ HESS_API hess_status opg_topk_eig_lowmem(hess_mlp* h, const void* X, const void*
  * eigenpairs (Sec. 5.4, Eq. J) of one data set in one call (any of them may
  * be left out: OPG or H NULL, k = 0).  The same results as
  * opg(), exact_hessian() and opg_topk_eig() with the same arguments, but
- * scheduled across four streams for BF16/BF16X3: the tensor-core operands and
+ * scheduled across five streams for BF16/BF16X3: the tensor-core operands and
  * contractions on the handle's stream, the FP64 eigen step (Gram matrix,
  * Lanczos, back-projection) concurrently on a second, higher-priority stream,
- * and the copies of host outputs behind their contractions, each matrix in two
- * halves on a third and a fourth stream.
+ * the copies of host outputs behind their contractions, each matrix in two
+ * halves on a third and a fourth stream, and the Hessian's operands and the
+ * eigen step's side work on a fifth; all of it is ordered before the
+ * handle's stream's later work.
  * X, Y float (double for HESS_FP64), host or device; OPG and H as in
  * opg()/exact_hessian(); evals/evecs as in opg_topk_eig().  Other precisions,
- * or nothing to overlap, run the single calls in turn.  The call returns
- * without waiting when every buffer is device memory.  Errors: those of the
- * three calls. */
+ * or nothing to overlap, run the single calls in turn.  When every buffer is
+ * device memory the call waits only for the Lanczos process's convergence
+ * flags (and the Ritz values that decide HESS_ERR_RANK_DEFICIENT), not for
+ * the rest of the work.  Errors: those of the three calls. */
 HESS_API hess_status hess_curvature(hess_mlp* h, const void* X, const void* Y, int64_t N, hess_precision prec,
                                     void* OPG, void* H, int k, double* evals, double* evecs);
 

@@ -2348,7 +2348,7 @@ constexpr uint64_t kLzKey = 0x5DEECE66Dull;  // the start vector's counter-based
 
 hess_status run_lz_df(hess_mlp* h, double* M, int k, LzBufs& b, int grid, int* m_out, bool* converged_out,
                       bool m_split, bool q0_ready, const std::function<hess_status(int)>* spec, int* spec_m,
-                      const std::function<hess_status()>* after_launch) {
+                      const std::function<hess_status()>* after_launch, double* theta_host) {
   if (spec_m) *spec_m = -1;
   const int64_t N = b.n, mcap = b.mcap;
   cudaStream_t s = h->stream;
@@ -2441,6 +2441,8 @@ hess_status run_lz_df(hess_mlp* h, double* M, int k, LzBufs& b, int grid, int* m
     HM_CUDA(cudaMemcpyAsync(hp, b.mx, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaMemcpyAsync(reinterpret_cast<int*>(hp + 2), b.err, sizeof(int), cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaMemcpyAsync(reinterpret_cast<int*>(hp + 2) + 1, b.stop, sizeof(int), cudaMemcpyDeviceToHost, s));
+    // (the Ritz values with them, for the caller's checks)
+    if (theta_host) HM_CUDA(cudaMemcpyAsync(theta_host, b.theta, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaStreamSynchronize(s));
     if (*reinterpret_cast<int*>(hp + 2)) return set_error(HESS_ERR_TIMEOUT, "Lanczos grid barrier gave up");
     const int stopped = reinterpret_cast<int*>(hp + 2)[1];
@@ -2918,9 +2920,12 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
 
   int m = 0, spec_m = -1;
   bool converged = false;
+  // the Ritz values reach the host with the convergence flags (room for k
+  // doubles after the flags in the handle's pinned scratch)
+  double* theta_host = k <= 500 ? hp + 4 : nullptr;
   if (dfg > 0) {
     const std::function<hess_status(int)> spec = tail;
-    HM_TRY(run_lz_df(h, M, k, lb, dfg, &m, &converged, true, true, &spec, &spec_m, &post_launch));
+    HM_TRY(run_lz_df(h, M, k, lb, dfg, &m, &converged, true, true, &spec, &spec_m, &post_launch, theta_host));
   } else {
     HM_TRY(post_launch());
     HM_TRY(run_lz(h, M, k, lb, &m, &converged));
@@ -2934,11 +2939,19 @@ hess_status topk_eig_gram(hess_mlp* h, const Net& net, const Caches<double>& c, 
     res->flops = f;
   }
   res->converged = converged ? 1 : 0;
+  if (spec_m == m && theta_host) {
+    // the tail queued with these Ritz values is the result: the null
+    // directions (the output pass's test) are known without waiting for it
+    int deficient = 0;
+    for (int c = 0; c < k; ++c)
+      if (!(theta_host[c] > 1e-13 * theta_host[0]) || !(theta_host[c] > 0.0)) deficient = 1;
+    res->rank_deficient = deficient;
+    return HESS_OK;
+  }
   if (spec_m != m) HM_TRY(tail(m));
   int* hi = reinterpret_cast<int*>(hp);
   HM_CUDA(cudaMemcpyAsync(hi, flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
   HM_CUDA(cudaStreamSynchronize(s));
-  if (narrow_side) HM_CUDA(cudaStreamSynchronize(side->s));
   res->rank_deficient = hi[0];
   return HESS_OK;
 }
