@@ -763,12 +763,13 @@ __global__ void last_beta_kernel(const double* npart, int nparts, double* out) {
 //      r^2 = nu - ||c||^2 (Pythagoras: q~_j - Q c is orthogonal to Q c; when
 //      ||c||^2 exceeds a quarter of nu the subtraction would lose digits, and
 //      ||q~_j - Q c||^2 is summed directly, one barrier more); r = beta_{j-1};
-//      q_j = (q~_j - Q c) / r and u = M q_j = (u~ - (MQ) c) / r on the owned
-//      slice, kept as column j of the slices of Q and MQ and as rows j of Q
-//      and MQ; with Q^T M Q = T_j (the tridiagonal matrix so far):
-//      alpha_j = q_j . u = (a~ - 2 c.g + c.T_j c) / r^2 and the first pass
-//      h = Q^T u = (g - T_j c) / r; w = u - Q h - alpha_j q_j on the owned
-//      slice, written as row j+1 of Q (q~_{j+1}); barrier.
+//      with Q^T M Q = T_j (the tridiagonal matrix so far): alpha_j =
+//      q_j . M q_j = (a~ - 2 c.g + c.T_j c) / r^2 and the first pass
+//      h = Q^T M q_j = (g - T_j c) / r; then, in one pass over the owned
+//      slices of Q and MQ, q_j = (q~_j - Q c) / r, M q_j = (u~ - (MQ) c) / r
+//      (column j of the slices, rows j of Q and MQ) and w = M q_j - Q h -
+//      alpha_j q_j = (u~ - alpha_j q~_j - (MQ) c - Q (r h - alpha_j c)) / r,
+//      written as row j+1 of Q (q~_{j+1}); barrier.
 // A launch over steps m0 .. m1-1 ends with a half step m1 (1 without the
 // product, then r) that gives beta_{m1-1} and leaves q~_{m1} in row m1 of Q,
 // where the next launch resumes.  M arrives scaled by 2^-e (e from the
@@ -836,12 +837,11 @@ __global__ void __launch_bounds__(kDfThreads, 1) lanczos_df_kernel(DfArgs a) {
   float2* qf = Msh + (int64_t)E * N;       // q~_j, N
   float2* Qs = qf + N;                     // owned slices of q_i, entry-major, E x qcap
   float2* MQs = Qs + (int64_t)E * qcap;    // owned slices of M q_i, E x qcap
-  float2* us = MQs + (int64_t)E * qcap;    // owned slice of u~ (then u), E
-  float2* qn = us + E;                     // owned slice of q~ - Q c (then q_j), E
-  float2* ws = qn + E;                     // owned slice of w, E
-  float2* cc = ws + E;                     // c, qcap + 1
+  float2* us = MQs + (int64_t)E * qcap;    // owned slice of u~, E
+  float2* qn = us + E;                     // owned slice of q~ - Q c (the rare direct norm), E
+  float2* cc = qn + E;                     // c, qcap + 1
   float2* cg = cc + (qcap + 1);            // g, qcap + 1
-  float2* ch = cg + (qcap + 1);            // T_j c, then h and alpha_j, qcap + 1
+  float2* ch = cg + (qcap + 1);            // T_j c, then d = r h - alpha_j c, qcap + 1
   float2* Ta = ch + (qcap + 1);            // alpha_i (scaled), qcap + 1
   float2* Tb = Ta + (qcap + 1);            // beta_i (scaled), qcap + 1
   float2* red = Tb + (qcap + 1);           // scratch, kDfRed
@@ -849,7 +849,7 @@ __global__ void __launch_bounds__(kDfThreads, 1) lanczos_df_kernel(DfArgs a) {
   const int ne = (int)(N - n0 < E ? (N - n0 > 0 ? N - n0 : 0) : E);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = (int)gridDim.x;
-  __shared__ float2 s_nu, s_at, s_cc, s_cgd, s_ctc, s_r2, s_rinv;
+  __shared__ float2 s_nu, s_at, s_cc, s_cgd, s_ctc, s_r2, s_rinv, s_al;
   __shared__ int s_brk, s_direct;
   __shared__ float s_scale;  // largest |alpha|, beta so far (scaled units)
   const double unscale = ldexp(1.0, *a.escale);
@@ -985,19 +985,14 @@ __global__ void __launch_bounds__(kDfThreads, 1) lanczos_df_kernel(DfArgs a) {
       if (lane == 0) s_at = t;
     }
     __syncthreads();
-    // q~_j - Q c and u~ - (MQ) c on the owned slice (the first warps), T_j c
-    // and the sums ||c||^2, c.g, c.T_j c (the last three)
-    if (warp < kDfWarps - 3) {
-      df_combine(Qs, qcap, cc, j, qf + n0, qn, ne, 0, kDfWarps - 3);
-      if (full) df_combine(MQs, qcap, cc, j, us, us, ne, 0, kDfWarps - 3);
-    } else {
-      const int w3 = warp - (kDfWarps - 3);
+    // T_j c and the sums ||c||^2, c.g, c.T_j c (three warps)
+    if (warp < 3) {
       float s = 0.0f, c = 0.0f;
       for (int i = lane; i < j; i += 32) {
         const float2 ci = cc[i];
-        if (w3 == 0) {
+        if (warp == 0) {
           df_mac(ci, ci, s, c);
-        } else if (w3 == 1) {
+        } else if (warp == 1) {
           df_mac(ci, cg[i], s, c);
         } else {
           // (T_j c)_i over the entries of T_j (indices below j)
@@ -1012,8 +1007,8 @@ __global__ void __launch_bounds__(kDfThreads, 1) lanczos_df_kernel(DfArgs a) {
       }
       const float2 t = df_warp_sum(s, c);
       if (lane == 0) {
-        if (w3 == 0) s_cc = t;
-        else if (w3 == 1) s_cgd = t;
+        if (warp == 0) s_cc = t;
+        else if (warp == 1) s_cgd = t;
         else s_ctc = t;
       }
     }
@@ -1025,6 +1020,9 @@ __global__ void __launch_bounds__(kDfThreads, 1) lanczos_df_kernel(DfArgs a) {
     }
     __syncthreads();
     if (s_direct) {
+      // ||q~_j - Q c||^2 summed directly, one barrier more
+      df_combine(Qs, qcap, cc, j, qf + n0, qn, ne);
+      __syncthreads();
       if (warp == 0) {
         float s = 0.0f, c = 0.0f;
         for (int e = lane; e < ne; e += 32) df_mac(qn[e], qn[e], s, c);
@@ -1063,30 +1061,43 @@ __global__ void __launch_bounds__(kDfThreads, 1) lanczos_df_kernel(DfArgs a) {
         const float2 al = df_mul(df_mul(num, ri), ri);
         sc = fmaxf(sc, fabsf(al.x));
         Ta[j] = al;
-        ch[j] = al;
+        s_al = al;
         if (blockIdx.x == 0) a.alpha[j] = df_val(al) * unscale;
       }
       s_scale = sc;
     }
     __syncthreads();
     if (s_brk || !full) return;  // the same decision in every block
-    const float2 rinv = s_rinv;
-    // h_i = (g_i - (T_j c)_i) / r; q_j, u on the slice
-    for (int i = tid; i < j; i += kDfThreads) ch[i] = df_mul(df_sub(cg[i], ch[i]), rinv);
-    for (int e = tid; e < ne; e += kDfThreads) {
-      const float2 q = df_mul(qn[e], rinv), u = df_mul(us[e], rinv);
-      qn[e] = q;
-      us[e] = u;
-      Qs[(int64_t)e * qcap + j] = q;
-      MQs[(int64_t)e * qcap + j] = u;
-      a.Q[(int64_t)j * N + n0 + e] = q;
-      a.MQ[(int64_t)j * N + n0 + e] = u;
+    const float2 rinv = s_rinv, al = s_al;
+    // d = (g - T_j c) - alpha_j c = r h - alpha_j c, so that
+    // r w = u~ - alpha_j q~_j - (MQ) c - Q d
+    for (int i = tid; i < j; i += kDfThreads) ch[i] = df_sub(df_sub(cg[i], ch[i]), df_mul(al, cc[i]));
+    __syncthreads();
+    // q_j = (q~_j - Q c) / r, M q_j = (u~ - (MQ) c) / r and w on the owned
+    // slice in one pass over the basis (a warp per entry, lanes over i)
+    for (int e = warp; e < ne; e += kDfWarps) {
+      const float2* qe = Qs + (int64_t)e * qcap;
+      const float2* me = MQs + (int64_t)e * qcap;
+      float s1 = 0.0f, c1 = 0.0f, s2 = 0.0f, c2 = 0.0f, s3 = 0.0f, c3 = 0.0f;
+      for (int i = lane; i < j; i += 32) {
+        const float2 qi = qe[i], ci = cc[i];
+        df_mac(ci, qi, s1, c1);
+        df_mac(ci, me[i], s2, c2);
+        df_mac(ch[i], qi, s3, c3);
+      }
+      const float2 t1 = df_warp_sum(s1, c1), t2 = df_warp_sum(s2, c2), t3 = df_warp_sum(s3, c3);
+      if (lane == 0) {
+        const float2 qt = qf[n0 + e], ut = us[e];
+        const float2 q = df_mul(df_sub(qt, t1), rinv);
+        const float2 u = df_mul(df_sub(ut, t2), rinv);
+        const float2 w = df_mul(df_sub(df_sub(df_sub(ut, df_mul(al, qt)), t2), t3), rinv);
+        Qs[(int64_t)e * qcap + j] = q;
+        MQs[(int64_t)e * qcap + j] = u;
+        a.Q[(int64_t)j * N + n0 + e] = q;
+        a.MQ[(int64_t)j * N + n0 + e] = u;
+        a.Q[(int64_t)(j + 1) * N + n0 + e] = w;  // q~_{j+1}
+      }
     }
-    __syncthreads();
-    // w = u - sum_{i<j} h_i q_i - alpha_j q_j, handed on as q~_{j+1}
-    df_combine(Qs, qcap, ch, j + 1, us, ws, ne);
-    __syncthreads();
-    for (int e = tid; e < ne; e += kDfThreads) a.Q[(int64_t)(j + 1) * N + n0 + e] = ws[e];
     if (!grid_barrier_at(a.bar, a.err, a.bar_limit)) return;
   }
 }
@@ -2312,7 +2323,7 @@ void plan_lz(Arena& ar, int64_t n, int k, LzBufs& b, double* Q, double* MQ) {
 size_t df_smem(int64_t n, int64_t g, int64_t mcap, int64_t m1) {
   (void)mcap;
   const int64_t E = cdiv(n, g), qcap = m1 + 1;
-  const int64_t f2 = E * n + n + 2 * E * qcap + 3 * E + 5 * (qcap + 1) + kDfRed;
+  const int64_t f2 = E * n + n + 2 * E * qcap + 2 * E + 5 * (qcap + 1) + kDfRed;
   return (size_t)f2 * sizeof(float2);
 }
 
