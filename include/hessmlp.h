@@ -515,16 +515,19 @@ HESS_API hess_status hess_timing_read(hess_mlp* h, int kernel_class, hess_kernel
 
 /* Test hooks (no counterpart in the paper).
  *
- * hess_check_devmath: for n device doubles x, writes four rows of n device
- * doubles to out (4 n entries, row-major): the refined FP64 reciprocal the
+ * hess_check_devmath: for n device doubles x, writes six rows of n device
+ * doubles to out (6 n entries, row-major): the refined FP64 reciprocal the
  * eigensolvers use (hardware estimate plus two Newton-Raphson steps; within
  * one ulp of 1/x), CUDA's correctly rounded 1.0 / x, the refined reciprocal
  * square root (within two ulps), and 1.0 / sqrt(x) (the last two 0 where
- * x <= 0).  The refined forms are meant for |x| in [2^-1022, 2^1022]: the
- * estimate flushes subnormal inputs and results to zero, so outside that
- * range they return 0 (|x| > 2^1022) or a value that is not finite
- * (subnormal x).  Queued on `stream`; returns without waiting.  Errors:
- * INVALID_ARG.
+ * x <= 0); then the hi and lo FP32 words of the double-float split that the
+ * double-float kernels take from the bits of an FP64 input (hi: x with its
+ * significand cut to 24 bits; hi + lo = x to 2^-48 relative for |x| in
+ * [2^-74, 2^128); both 0 for |x| below 2^-126).  The refined forms are meant
+ * for |x| in [2^-1022, 2^1022]: the estimate flushes subnormal inputs and
+ * results to zero, so outside that range they return 0 (|x| > 2^1022) or a
+ * value that is not finite (subnormal x).  Queued on `stream`; returns
+ * without waiting.  Errors: INVALID_ARG.
  *
  * hess_debug_set_barrier_limit: the number of SM clock cycles a block of the
  * OPG eigen step's cooperative Lanczos kernel waits at a grid barrier before

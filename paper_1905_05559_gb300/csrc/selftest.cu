@@ -1,6 +1,7 @@
 // Test hook for the refined FP64 reciprocal and reciprocal square root that
-// the eigensolvers use inside their dependent chains: evaluates them next to
-// CUDA's correctly rounded division and square root on the same inputs.
+// the eigensolvers use inside their dependent chains, evaluated next to
+// CUDA's correctly rounded division and square root on the same inputs, and
+// for the bit-level double-float split of FP64 inputs.
 #include "devmath.cuh"
 #include "internal.h"
 
@@ -14,6 +15,9 @@ __global__ void devmath_kernel(const double* x, int64_t n, double* out) {
     out[n + i] = 1.0 / v;
     out[2 * n + i] = v > 0.0 ? rsqrt64(v) : 0.0;
     out[3 * n + i] = v > 0.0 ? 1.0 / sqrt(v) : 0.0;
+    const float2 h = df_split_bits(v);
+    out[4 * n + i] = (double)h.x;
+    out[5 * n + i] = (double)h.y;
   }
 }
 

@@ -1,4 +1,5 @@
-"""The refined FP64 reciprocal and reciprocal square root of the eigensolvers.
+"""The refined FP64 reciprocal and reciprocal square root of the eigensolvers,
+and the bit-level double-float split of the double-float kernels.
 
 rcp64 and rsqrt64 start from the hardware estimates and take two
 Newton-Raphson steps.  Over their stated domain, |x| in [2^-1022, 2^1022],
@@ -7,7 +8,9 @@ rounded results, here computed exactly on the host with 60-digit decimal
 arithmetic (CUDA's IEEE division is checked to be that correctly rounded
 value).  Outside that domain the estimate flushes subnormals: the header
 states the results there (0 for huge inputs, not finite for subnormal ones),
-which are checked too.
+which are checked too.  The split's hi word is the input cut to 24
+significant bits and hi + lo (exact in FP64) must equal the input to 2^-48
+relative wherever lo stays in FP32's normal range.
 """
 
 import ctypes
@@ -34,7 +37,7 @@ def hm():
 def _run(hm, x):
     lib = hm.load()
     xd = torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64), device="cuda")
-    out = torch.full((4, x.size), float("nan"), dtype=torch.float64, device="cuda")
+    out = torch.full((6, x.size), float("nan"), dtype=torch.float64, device="cuda")
     st = lib.hess_check_devmath(ctypes.c_void_p(xd.data_ptr()), x.size, ctypes.c_void_p(out.data_ptr()),
                                 None)
     assert st == 0, hm.last_error()
@@ -96,3 +99,28 @@ def test_outside_the_domain_results_are_zero_or_not_finite(hm):
     out = _run(hm, np.concatenate([sub, big]))
     assert not np.isfinite(out[0][:3]).any()
     assert np.all(out[0][3:] == 0.0)
+
+
+def test_double_float_split_from_bits(hm):
+    rng = np.random.default_rng(3)
+    n = 4000
+    e = rng.integers(-74, 128, size=n)
+    x = np.ldexp(rng.uniform(1.0, 2.0, size=n), e) * rng.choice([-1.0, 1.0], size=n)
+    x = np.concatenate([x, [1.0, -1.0, 3.0, 1.0 / 3.0, np.nextafter(1.0, 2.0), np.ldexp(1.0, -74),
+                            np.ldexp(1.9999999999, 127)]])
+    out = _run(hm, x)
+    hi, lo = out[4], out[5]
+    # hi: x with its significand cut to 24 bits (toward zero, same sign)
+    trunc = (x.view(np.int64) & ~np.int64((1 << 29) - 1)).view(np.float64)
+    assert np.array_equal(hi, trunc)
+    assert np.all(np.abs(lo) <= np.ldexp(np.abs(hi), -23))
+    err = np.abs((hi + lo) - x) / np.abs(x)
+    assert err.max() <= 2.0 ** -48, err.max()
+    # below FP32's normal range: both words 0; in between, hi stays exact
+    tiny = np.array([0.0, -0.0, np.ldexp(1.0, -127), np.ldexp(1.5, -200), 1e-300])
+    out = _run(hm, tiny)
+    assert np.all(out[4] == 0.0) and np.all(out[5] == 0.0)
+    mid = np.ldexp(rng.uniform(1.0, 2.0, size=200), rng.integers(-126, -74, size=200))
+    out = _run(hm, mid)
+    assert np.array_equal(out[4], (mid.view(np.int64) & ~np.int64((1 << 29) - 1)).view(np.float64))
+    assert (np.abs(out[4] + out[5] - mid) / mid).max() <= 2.0 ** -23
