@@ -2352,9 +2352,17 @@ int eig_lanczos_blocks(hess_mlp* h, int64_t n, int k) {
   return (int)cdiv(n, cdiv(n, g));
 }
 
-// The Lanczos process of run_lz with the double-float kernel; M (FP64, n x n)
-// is overwritten by its scaled hi/lo pairs.  On return b.Q holds q_0 ..
-// q_{m-1} in FP64 (rows of n), as run_lz leaves them.
+// The Lanczos process of run_lz with the double-float kernel.  M is the
+// n x n matrix as scaled hi/lo pairs (m_split; otherwise FP64, overwritten by
+// its pairs here), q_0 is in row 0 of b.Q already when q0_ready.  On return
+// b.Q holds q_0 .. q_{m-1} as hi/lo pairs (rows of n) and b.theta, b.Y the
+// top-k eigenpairs of T_m.  Optional hooks: after_launch runs once, right
+// after the first Lanczos launch is queued (host work that the launch then
+// hides); spec(m) runs as soon as the tridiagonal eigenpairs of T_m are
+// queued, before the host reads the convergence flags, and *spec_m receives
+// the m of the last such call whose eigenpairs stand (-1 if none: the
+// caller repeats its work for the final m); theta_host (k doubles of pinned
+// memory) receives the Ritz values with the flags.
 constexpr uint64_t kLzKey = 0x5DEECE66Dull;  // the start vector's counter-based draw
 
 hess_status run_lz_df(hess_mlp* h, double* M, int k, LzBufs& b, int grid, int* m_out, bool* converged_out,
