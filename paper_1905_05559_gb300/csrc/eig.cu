@@ -1543,9 +1543,9 @@ __global__ void bisect_cluster_kernel(const double* a, const double* b, int m, i
   }
   lo = fmax(lo0, lo - 4e-6);
   hi = fmin(hi0, hi + 4e-6);
-  // double-float sweeps down to 2^-40 of ||T|| (<= 1 here), the bracket then
-  // widened by that much (far above the double-float count's error), so that
-  // the FP64 sweeps below start within a few multisections of the end
+  // double-float sweeps down to 2^-40 of ||T|| (<= 1 here): the midpoint is
+  // then within about 1e-12 ||T|| of the eigenvalue, the double-float count's
+  // error included
   for (int it = 0; it < 8; ++it) {
     if (hi - lo <= 9.1e-13) break;
     const double x = lo + (hi - lo) * (double)(g + 1) * inv_n;
