@@ -161,9 +161,15 @@ HESS_API hess_status exact_hessian(hess_mlp* h, const void* X, const void* Y, in
  * and the eigenvectors are q = G^T u / sqrt(N mu).  evals: k doubles in
  * descending (algebraic) order; evecs: P x k column-major doubles (column c is
  * q_c, unit norm, sign chosen so that its largest-magnitude entry is
- * positive).  X and Y are double for FP64 and float otherwise; the Gram
- * matrix, the eigensolver (Lanczos with full reorthogonalisation) and the
- * back-projection run in FP64 for every precision.  Requires 1 <= k <=
+ * positive).  X and Y are double for FP64 and float otherwise; for every
+ * precision the Gram matrix, the eigensolver (Lanczos with full
+ * reorthogonalisation, tridiagonal eigenpairs) and the back-projection are
+ * held to FP64 accuracy: exact-digit FP64 products on the tensor cores for
+ * the wide layers, and, where the Gram matrix's rows fit shared memory
+ * (N up to about 2048), double-float arithmetic (pairs of FP32 numbers,
+ * about 48 significant bits) for the Gram matrix, the Lanczos vectors and
+ * the wide layer's forward product, the eigenvalues then refined in FP64.
+ * Requires 1 <= k <=
  * min(N, P).  Returns HESS_ERR_RANK_DEFICIENT (after writing every output)
  * when mu_c <= 1e-13 mu_1 for some c; those columns are zero.  Errors:
  * INVALID_ARG, OOM, CUDA, NOT_CONVERGED. */
